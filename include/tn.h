@@ -1,0 +1,204 @@
+/*
+ * tn.h -- C ABI of the GB300 tensor-network contraction engine.
+ *
+ * The engine executes a FIXED pairwise contraction path (Sec. II-B of "Parallelizing
+ * Large-Scale Tensor Network Contraction on Multiple GPUs") on one GPU:
+ *   - every step A x B -> C is run as a GEMM A_MK x B_KN -> C_MN (Sec. II-B), with the
+ *     mode orders of all tensors chosen ahead of time by the GEMM-oriented backward
+ *     pass of Sec. IV-A so that no step needs a runtime transpose;
+ *   - sliced labels (Sec. II-C) become an on-device batch dimension, and the slice
+ *     results are summed in FP64 with compensated (Neumaier) summation.
+ *
+ * Conventions shared by every entry point:
+ *   - Row-major storage; the leftmost mode is outermost (Sec. IV-B, prefix distribution).
+ *   - Complex tensors are complex64 (interleaved re, im float32) on input; real
+ *     tensors are float32. Results are complex128 / float64.
+ *   - The caller owns every input and output buffer; the library never frees them.
+ *   - Every function returns a tn_status; no C++ exception and no device trap crosses
+ *     the ABI. tn_last_error() gives a thread-local message for the last failure.
+ *   - Device work is asynchronous on the caller's stream unless stated otherwise.
+ */
+#ifndef TN_GB300_H
+#define TN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TN_OK = 0,
+  TN_ERR_INVALID = 1,      /* malformed network/path/arguments */
+  TN_ERR_UNSUPPORTED = 2,  /* valid input the engine does not handle (hyper-edge, ...) */
+  TN_ERR_OOM = 3,          /* device memory for the plan workspace not available */
+  TN_ERR_CUDA = 4,         /* a CUDA call failed; message has the CUDA error string */
+  TN_ERR_BUSY = 5,         /* serve queue full */
+  TN_ERR_TIMEOUT = 6,      /* bounded wait expired (serve poll, device-side spin) */
+  TN_ERR_NOT_READY = 7     /* serve ticket still in flight */
+} tn_status;
+
+/* Arithmetic form of the pairwise GEMMs. C64_* take complex64 inputs, R32_* float32.
+ *   FP32_SIMT : FP32 FMA on the CUDA cores (the plain form).
+ *   TF32      : tcgen05 tensor cores, operands read as TF32, FP32 accumulation.
+ *   3XTF32    : tcgen05, each operand split hi + lo, three TF32 products, FP32 accum.
+ *   BF16X3    : tcgen05, each operand split hi + lo in BF16, three products, FP32 accum.
+ * Steps too small or too thin for a tensor-core tile run on the FP32 SIMT kernels
+ * whatever the form. */
+typedef enum {
+  TN_C64_FP32_SIMT = 0,
+  TN_C64_TF32 = 1,
+  TN_C64_3XTF32 = 2,
+  TN_C64_BF16X3 = 3,
+  TN_R32_FP32_SIMT = 4,
+  TN_R32_TF32 = 5,
+  TN_R32_3XTF32 = 6,
+  TN_R32_BF16X3 = 7
+} tn_precision;
+
+/* Plan flags. */
+#define TN_PLAN_HOST_ONLY 1u     /* plan and query only: no device memory, no contract */
+
+typedef struct {
+  int32_t prec;            /* tn_precision */
+  int32_t complex_mult;    /* 4 (4M) -- the only form built; 3 is rejected */
+  int32_t exp_scaling;     /* 1: per-intermediate power-of-two scaling, log scale in FP64 */
+  int32_t max_slice_batch; /* slices per device pass; 0 = as many as fit in free HBM */
+  uint32_t flags;          /* TN_PLAN_* */
+  int32_t reserved[3];
+} tn_dtype_policy;
+
+/* A network: tensor t has rank[t] modes modes[t][0..rank[t]-1] (labels in
+ * 0..n_labels-1, leftmost outermost). extent[label] is the label's dimension. A closed
+ * label appears in exactly two tensors; an open label in exactly one and in
+ * open_modes, which fixes the result's mode order (Sec. IV-A: the root order is given
+ * by the problem). */
+typedef struct {
+  int32_t n_tensors;
+  const int32_t* rank;
+  const int32_t* const* modes;
+  int32_t n_labels;
+  const int64_t* extent;
+  int32_t n_open;
+  const int32_t* open_modes;
+} tn_network;
+
+/* A contraction path in SSA form: leaves are 0..n_tensors-1 and step s contracts
+ * pair[2s], pair[2s+1] into tensor n_tensors+s. Must form one binary tree
+ * (n_steps = n_tensors - 1, every id consumed once). */
+typedef struct {
+  int32_t n_steps;
+  const int32_t* pair; /* 2*n_steps ids */
+} tn_path;
+
+typedef struct tn_plan_s* tn_plan_t;
+
+/* Kernel class chosen for a step (Sec. IV-C cost model t = max(D_rw/B, FLOPs/F)). */
+typedef enum { TN_CLASS_SIMT = 0, TN_CLASS_STREAM = 1, TN_CLASS_TC = 2 } tn_step_class;
+
+typedef struct {
+  int64_t n_steps, n_leaves, n_slices, slice_batch, n_passes;
+  double flops;            /* algorithmic: sum 8mnk (complex) or 2mnk (real), all slices */
+  double bytes;            /* algorithmic: sum e(mk+kn+mn) + leaf staging, all slices */
+  double Ct, Cm, Cs;       /* Sec. II-B Eqs. 1-3 for one slice (element counts) */
+  int64_t peak_elems;      /* largest tensor of one slice, elements */
+  int64_t workspace_bytes; /* device bytes the plan holds */
+  int64_t steps_per_class[3];
+  double flops_per_class[3];
+  int64_t leaf_permutes;   /* leaves whose planned order differs from the declared one
+                              (permuted once while staging; no step permutes) */
+} tn_plan_stats;
+
+typedef struct {
+  int64_t m, n, k;         /* GEMM view of the step */
+  int32_t a_id, b_id;      /* SSA ids of the operands in the A (rows) and B (cols) roles */
+  int32_t cls;             /* tn_step_class */
+  int32_t batched;         /* 1 if the step depends on a sliced label */
+} tn_step_info;
+
+/* Build a plan: validate, analyse each step (Sec. II-B), run the backward mode
+ * reordering pass (Sec. IV-A), choose a kernel per step, assign every tensor a
+ * place in one workspace by liveness, and (unless TN_PLAN_HOST_ONLY) allocate that
+ * workspace on the current CUDA device. sliced_modes lists the labels to slice
+ * (Sec. II-C); n_sliced may be 0. Returns TN_ERR_INVALID / TN_ERR_UNSUPPORTED for bad
+ * input and TN_ERR_OOM if the workspace does not fit. *out is set only on TN_OK. */
+tn_status tn_plan(const tn_network* net, const tn_path* path, const int32_t* sliced_modes,
+                  int32_t n_sliced, tn_dtype_policy policy, tn_plan_t* out);
+
+/* Plan statistics (host only). */
+tn_status tn_plan_info(tn_plan_t plan, tn_plan_stats* out);
+
+/* Planned mode order of tensor `id` (SSA id; leaves and intermediates, sliced labels
+ * removed). modes_out must hold at least the tensor's rank; *rank_out gets the rank.
+ * This is the layout the backward pass of Sec. IV-A assigns. */
+tn_status tn_plan_layout(tn_plan_t plan, int32_t id, int32_t* modes_out, int32_t* rank_out);
+
+/* Description of step s (host only). */
+tn_status tn_plan_step(tn_plan_t plan, int32_t s, tn_step_info* out);
+
+/* Contract all slices. inputs[t] is a DEVICE pointer to leaf t in its declared mode
+ * order (complex64 or float32, per the plan's precision). output is a DEVICE pointer
+ * to the result in open_modes order: complex128 (complex plans) or float64 (real).
+ * out_log_scale: DEVICE pointer to one double or NULL; when exp_scaling is on the
+ * result is output * exp(*out_log_scale). Asynchronous on `stream` (a cudaStream_t;
+ * NULL = legacy default stream). Calls on one plan must not overlap in time. */
+tn_status tn_contract(tn_plan_t plan, const void* const* inputs, void* output,
+                      double* out_log_scale, void* stream);
+
+/* As tn_contract, summing only slices [slice_begin, slice_begin + slice_count). With
+ * slice_count = 1 the output is that slice's partial result (Sec. V-A projection: time
+ * per slice). */
+tn_status tn_contract_slices(tn_plan_t plan, const void* const* inputs, int64_t slice_begin,
+                             int64_t slice_count, void* output, double* out_log_scale,
+                             void* stream);
+
+/* End-to-end form: inputs and output in HOST memory. Copies the leaves into the
+ * plan's device staging area, contracts all slices, copies the result back, and
+ * returns after the stream has finished. out_log_scale is a host pointer or NULL. */
+tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void* host_output,
+                           double* out_log_scale, void* stream);
+
+/* Free the plan and its device workspace (after any contract on it has finished). */
+tn_status tn_plan_destroy(tn_plan_t plan);
+
+/* ---- serving: continuous batching of contraction requests ------------------------ */
+
+typedef struct {
+  int32_t max_inflight;      /* requests on the GPU at once (slots) */
+  int32_t n_streams;         /* CUDA streams work is spread over */
+  int64_t hbm_budget_bytes;  /* admission limit on the sum of admitted workspaces */
+  int32_t queue_capacity;    /* pending requests beyond which submit returns TN_ERR_BUSY */
+  int32_t reserved[3];
+} tn_serve_config;
+
+typedef struct tn_server_s* tn_server_t;
+
+/* Start a server with its scheduler thread on the current device. */
+tn_status tn_serve_create(const tn_serve_config* cfg, tn_server_t* out);
+
+/* Submit a request: contract `plan` (all slices) on HOST inputs. The server copies the
+ * inputs before returning, so the caller may reuse its buffers. Admission waits until a
+ * slot and the plan's workspace fit the HBM budget. Returns TN_ERR_BUSY when the queue
+ * is full. The plan must stay alive until the ticket is polled to completion, and one
+ * plan must not have two requests in flight (its workspace is shared). */
+tn_status tn_serve_submit(tn_server_t srv, tn_plan_t plan, const void* const* host_inputs,
+                          uint64_t* ticket);
+
+/* Wait up to timeout_us (0 = do not wait, <0 = forever) for a ticket. On TN_OK writes
+ * the result (complex128 or float64, |open| elements) to host `result`, the log scale
+ * to *log_scale if non-NULL, and retires the ticket. TN_ERR_NOT_READY if still in
+ * flight after the wait; TN_ERR_INVALID for an unknown ticket. */
+tn_status tn_serve_poll(tn_server_t srv, uint64_t ticket, void* result, double* log_scale,
+                        int32_t timeout_us);
+
+/* Stop the scheduler (finishing admitted work) and free the server. */
+tn_status tn_serve_destroy(tn_server_t srv);
+
+/* Thread-local message for the last non-OK status on this thread. */
+const char* tn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_GB300_H */

@@ -1,0 +1,270 @@
+"""ctypes binding of the C ABI in include/tn.h (argument marshalling only).
+
+Every step of the contraction runs in the CUDA library; this module only converts
+Python network descriptions and tensor handles into the plain arrays and pointers
+the C functions take. Importing it fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtn_gb300.so")
+
+# tn_status
+TN_OK, TN_ERR_INVALID, TN_ERR_UNSUPPORTED, TN_ERR_OOM, TN_ERR_CUDA, TN_ERR_BUSY, \
+    TN_ERR_TIMEOUT, TN_ERR_NOT_READY = range(8)
+STATUS_NAMES = ["TN_OK", "TN_ERR_INVALID", "TN_ERR_UNSUPPORTED", "TN_ERR_OOM", "TN_ERR_CUDA",
+                "TN_ERR_BUSY", "TN_ERR_TIMEOUT", "TN_ERR_NOT_READY"]
+# tn_precision
+TN_C64_FP32_SIMT, TN_C64_TF32, TN_C64_3XTF32, TN_C64_BF16X3, TN_R32_FP32_SIMT, TN_R32_TF32, \
+    TN_R32_3XTF32, TN_R32_BF16X3 = range(8)
+PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
+TN_PLAN_HOST_ONLY = 1
+TN_CLASS_SIMT, TN_CLASS_STREAM, TN_CLASS_TC = range(3)
+
+
+class TnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class tn_network(C.Structure):
+    _fields_ = [("n_tensors", C.c_int32), ("rank", C.POINTER(C.c_int32)),
+                ("modes", C.POINTER(C.POINTER(C.c_int32))), ("n_labels", C.c_int32),
+                ("extent", C.POINTER(C.c_int64)), ("n_open", C.c_int32),
+                ("open_modes", C.POINTER(C.c_int32))]
+
+
+class tn_path(C.Structure):
+    _fields_ = [("n_steps", C.c_int32), ("pair", C.POINTER(C.c_int32))]
+
+
+class tn_dtype_policy(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("complex_mult", C.c_int32), ("exp_scaling", C.c_int32),
+                ("max_slice_batch", C.c_int32), ("flags", C.c_uint32), ("reserved", C.c_int32 * 3)]
+
+
+class tn_plan_stats(C.Structure):
+    _fields_ = [("n_steps", C.c_int64), ("n_leaves", C.c_int64), ("n_slices", C.c_int64),
+                ("slice_batch", C.c_int64), ("n_passes", C.c_int64), ("flops", C.c_double),
+                ("bytes", C.c_double), ("Ct", C.c_double), ("Cm", C.c_double), ("Cs", C.c_double),
+                ("peak_elems", C.c_int64), ("workspace_bytes", C.c_int64),
+                ("steps_per_class", C.c_int64 * 3), ("flops_per_class", C.c_double * 3),
+                ("leaf_permutes", C.c_int64)]
+
+
+class tn_step_info(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("k", C.c_int64), ("a_id", C.c_int32),
+                ("b_id", C.c_int32), ("cls", C.c_int32), ("batched", C.c_int32)]
+
+
+class tn_serve_config(C.Structure):
+    _fields_ = [("max_inflight", C.c_int32), ("n_streams", C.c_int32),
+                ("hbm_budget_bytes", C.c_int64), ("queue_capacity", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2606_01852_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    sig = {
+        "tn_plan": [C.POINTER(tn_network), C.POINTER(tn_path), C.POINTER(i32), i32, tn_dtype_policy,
+                    C.POINTER(vp)],
+        "tn_plan_info": [vp, C.POINTER(tn_plan_stats)],
+        "tn_plan_layout": [vp, i32, C.POINTER(i32), C.POINTER(i32)],
+        "tn_plan_step": [vp, i32, C.POINTER(tn_step_info)],
+        "tn_contract": [vp, C.POINTER(vp), vp, vp, vp],
+        "tn_contract_slices": [vp, C.POINTER(vp), i64, i64, vp, vp, vp],
+        "tn_contract_host": [vp, C.POINTER(vp), vp, vp, vp],
+        "tn_plan_destroy": [vp],
+        "tn_serve_create": [C.POINTER(tn_serve_config), C.POINTER(vp)],
+        "tn_serve_submit": [vp, vp, C.POINTER(vp), C.POINTER(u64)],
+        "tn_serve_poll": [vp, u64, vp, vp, i32],
+        "tn_serve_destroy": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.tn_last_error.argtypes = []
+    lib.tn_last_error.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def check(status):
+    if status != TN_OK:
+        raise TnError(status, lib.tn_last_error().decode())
+
+
+def last_error() -> str:
+    return lib.tn_last_error().decode()
+
+
+def _ptr(x):
+    """Raw address of a tensor/array/int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def make_policy(prec=TN_C64_FP32_SIMT, exp_scaling=False, max_slice_batch=0, host_only=False):
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    p = tn_dtype_policy()
+    p.prec = int(prec)
+    p.complex_mult = 4
+    p.exp_scaling = 1 if exp_scaling else 0
+    p.max_slice_batch = int(max_slice_batch)
+    p.flags = TN_PLAN_HOST_ONLY if host_only else 0
+    return p
+
+
+class _NetArrays:
+    """Keeps the ctypes arrays of a network description alive."""
+
+    def __init__(self, modes, extent, open_modes, pairs):
+        n_labels = (max(extent) + 1) if extent else 0
+        self.rank = (C.c_int32 * len(modes))(*[len(m) for m in modes])
+        self.mode_arrays = [(C.c_int32 * max(1, len(m)))(*m) for m in modes]
+        self.modes = (C.POINTER(C.c_int32) * len(modes))(
+            *[C.cast(a, C.POINTER(C.c_int32)) for a in self.mode_arrays])
+        ext = [1] * n_labels
+        for x, e in extent.items():
+            ext[x] = int(e)
+        self.extent = (C.c_int64 * max(1, n_labels))(*ext)
+        self.open = (C.c_int32 * max(1, len(open_modes)))(*open_modes)
+        flat = [int(v) for p in pairs for v in p]
+        self.pair = (C.c_int32 * max(1, len(flat)))(*flat)
+        self.net = tn_network(len(modes), self.rank, self.modes, n_labels, self.extent,
+                              len(open_modes), self.open)
+        self.path = tn_path(len(pairs), self.pair)
+
+
+class Plan:
+    """A contraction plan (tn_plan). `net` needs .modes, .extent, .open_modes;
+    `path` is a list of SSA pairs or an object with .pairs."""
+
+    def __init__(self, net, path, sliced=(), prec=TN_C64_FP32_SIMT, exp_scaling=False,
+                 max_slice_batch=0, host_only=False):
+        pairs = path.pairs if hasattr(path, "pairs") else path
+        self._arr = _NetArrays([tuple(m) for m in net.modes], dict(net.extent), tuple(net.open_modes),
+                               pairs)
+        sl = list(sliced)
+        self._sl = (C.c_int32 * max(1, len(sl)))(*sl)
+        self.policy = make_policy(prec, exp_scaling, max_slice_batch, host_only)
+        self.is_complex = self.policy.prec <= TN_C64_BF16X3
+        self.n_leaves = len(net.modes)
+        self.n_open = len(net.open_modes)
+        self.out_shape = tuple(net.extent[x] for x in net.open_modes)
+        h = C.c_void_p()
+        check(lib.tn_plan(C.byref(self._arr.net), C.byref(self._arr.path), self._sl, len(sl),
+                          self.policy, C.byref(h)))
+        self.handle = h
+
+    # -- queries
+    def info(self) -> dict:
+        s = tn_plan_stats()
+        check(lib.tn_plan_info(self.handle, C.byref(s)))
+        d = {f: getattr(s, f) for f, _ in tn_plan_stats._fields_}
+        d["steps_per_class"] = list(s.steps_per_class)
+        d["flops_per_class"] = list(s.flops_per_class)
+        return d
+
+    def layout(self, tid: int):
+        r = C.c_int32()
+        check(lib.tn_plan_layout(self.handle, tid, None, C.byref(r)))
+        buf = (C.c_int32 * max(1, r.value))()
+        check(lib.tn_plan_layout(self.handle, tid, buf, C.byref(r)))
+        return tuple(buf[: r.value])
+
+    def step(self, s: int) -> dict:
+        i = tn_step_info()
+        check(lib.tn_plan_step(self.handle, s, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in tn_step_info._fields_}
+
+    # -- execution
+    def _inputs(self, inputs):
+        if len(inputs) != self.n_leaves:
+            raise ValueError(f"expected {self.n_leaves} inputs, got {len(inputs)}")
+        arr = (C.c_void_p * self.n_leaves)(*[_ptr(t) for t in inputs])
+        return arr
+
+    def contract(self, inputs, output, log_scale=None, stream=None):
+        check(lib.tn_contract(self.handle, self._inputs(inputs), _ptr(output), _ptr(log_scale),
+                              _ptr_stream(stream)))
+
+    def contract_slices(self, inputs, begin, count, output, log_scale=None, stream=None):
+        check(lib.tn_contract_slices(self.handle, self._inputs(inputs), int(begin), int(count),
+                                     _ptr(output), _ptr(log_scale), _ptr_stream(stream)))
+
+    def contract_host(self, host_inputs, host_output, log_scale=None, stream=None):
+        check(lib.tn_contract_host(self.handle, self._inputs(host_inputs), _ptr(host_output),
+                                   _ptr(log_scale), _ptr_stream(stream)))
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib.tn_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _ptr_stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+class Server:
+    """Continuous-batching request loop (tn_serve_*)."""
+
+    def __init__(self, max_inflight=8, n_streams=4, hbm_budget_bytes=0, queue_capacity=4096):
+        cfg = tn_serve_config()
+        cfg.max_inflight = max_inflight
+        cfg.n_streams = n_streams
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        cfg.queue_capacity = queue_capacity
+        h = C.c_void_p()
+        check(lib.tn_serve_create(C.byref(cfg), C.byref(h)))
+        self.handle = h
+
+    def submit(self, plan: Plan, host_inputs) -> int:
+        t = C.c_uint64()
+        check(lib.tn_serve_submit(self.handle, plan.handle, plan._inputs(host_inputs), C.byref(t)))
+        return t.value
+
+    def try_submit(self, plan: Plan, host_inputs):
+        t = C.c_uint64()
+        s = lib.tn_serve_submit(self.handle, plan.handle, plan._inputs(host_inputs), C.byref(t))
+        return s, t.value
+
+    def poll(self, ticket, result, log_scale=None, timeout_us=-1):
+        return lib.tn_serve_poll(self.handle, C.c_uint64(ticket), _ptr(result), _ptr(log_scale),
+                                 int(timeout_us))
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            check(lib.tn_serve_destroy(self.handle))
+            self.handle = None

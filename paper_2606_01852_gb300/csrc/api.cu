@@ -1,0 +1,340 @@
+// C ABI entry points and the executor that replays a plan on a CUDA stream.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "tn_internal.h"
+
+namespace tn {
+
+namespace {
+thread_local std::string g_last_error;
+
+#define TN_CUDA_TRY(expr)                                                         \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      err = std::string(#expr) + ": " + cudaGetErrorString(e_);                   \
+      return TN_ERR_CUDA;                                                         \
+    }                                                                             \
+  } while (0)
+
+int64_t batch_footprint(Plan& P, int64_t b) {
+  assign_workspace(P, b);
+  return P.total_bytes;
+}
+
+StepArgs step_args(const Plan& P, const StepRec& st) {
+  const TensorRec& A = P.tensors[st.a];
+  const TensorRec& B = P.tensors[st.b];
+  const TensorRec& C = P.tensors[st.out];
+  const int64_t np = P.is_complex ? 2 : 1;
+  StepArgs a{};
+  a.A = reinterpret_cast<const float*>(P.dev + A.offset);
+  a.B = reinterpret_cast<const float*>(P.dev + B.offset);
+  a.C = reinterpret_cast<float*>(P.dev + C.offset);
+  a.m = st.m;
+  a.n = st.n;
+  a.k = st.k;
+  a.a_plane = A.size;
+  a.b_plane = B.size;
+  a.c_plane = C.size;
+  a.a_bstride = A.batched ? np * A.size : 0;
+  a.b_bstride = B.batched ? np * B.size : 0;
+  a.c_bstride = C.batched ? np * C.size : 0;
+  a.rows = st.rows;
+  a.cols = st.cols;
+  a.recs = P.policy.exp_scaling ? reinterpret_cast<ScaleRec*>(P.dev + P.off_scale) : nullptr;
+  a.rec_a = P.rec_index[st.a];
+  a.rec_b = P.rec_index[st.b];
+  a.rec_c = P.rec_index[st.out];
+  return a;
+}
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t count, void* output,
+                     double* log_scale, void* stream, std::string& err) {
+  if (!P.dev) {
+    err = "plan was built with TN_PLAN_HOST_ONLY (no device workspace)";
+    return TN_ERR_INVALID;
+  }
+  if (!inputs || !output) {
+    err = "null inputs or output";
+    return TN_ERR_INVALID;
+  }
+  if (begin < 0 || count <= 0 || begin + count > P.n_slices) {
+    err = "slice range out of bounds";
+    return TN_ERR_INVALID;
+  }
+  for (int32_t t = 0; t < P.n_leaves; ++t)
+    if (!inputs[t]) {
+      err = "null input pointer";
+      return TN_ERR_INVALID;
+    }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const bool cplx = P.is_complex;
+  const bool scaling = P.policy.exp_scaling != 0;
+  const int32_t T = P.n_leaves, S = (int32_t)P.steps.size();
+  const int32_t root = T + S - 1;
+  for (int32_t t = 0; t < T; ++t) {
+    P.leafdesc[t].src = inputs[t];
+    P.leafdesc[t].dst = P.tensors[t].offset;
+  }
+  // descriptors from pageable memory: the copy is staged before the call returns
+  TN_CUDA_TRY(cudaMemcpyAsync(P.dev + P.off_leafdesc, P.leafdesc.data(),
+                              sizeof(LeafDesc) * P.leafdesc.size(), cudaMemcpyHostToDevice, st));
+  ScaleRec* recs = scaling ? reinterpret_cast<ScaleRec*>(P.dev + P.off_scale) : nullptr;
+  int32_t* recidx = reinterpret_cast<int32_t*>(P.dev + P.off_recidx);
+  if (scaling) {
+    TN_CUDA_TRY(cudaMemcpyAsync(recidx, P.rec_index.data(), sizeof(int32_t) * T,
+                                cudaMemcpyHostToDevice, st));
+  }
+  const LeafDesc* descs = reinterpret_cast<const LeafDesc*>(P.dev + P.off_leafdesc);
+  double* acc = reinterpret_cast<double*>(P.dev + P.off_acc);
+  int64_t* ref = reinterpret_cast<int64_t*>(P.dev + P.off_ref);
+  const int64_t npass = (count + P.batch - 1) / P.batch;
+  for (int64_t p = 0; p < npass; ++p) {
+    const int32_t nb = (int32_t)std::min<int64_t>(P.batch, count - p * P.batch);
+    const int64_t sb = begin + p * P.batch;
+    if (scaling) {
+      // 0x80 bytes make every emax very negative (the atomicMax identity)
+      if (p == 0)
+        TN_CUDA_TRY(cudaMemsetAsync(recs, 0x80, sizeof(ScaleRec) * P.n_rec_total, st));
+      else
+        TN_CUDA_TRY(cudaMemsetAsync(recs + P.n_rec_unbatched, 0x80,
+                                    sizeof(ScaleRec) * (P.n_rec_total - P.n_rec_unbatched), st));
+    }
+    launch_stage_leaves(descs, T, P.dev, sb, nb, p > 0, cplx, recs, recidx, st);
+    for (int32_t s = 0; s < S; ++s) {
+      const StepRec& sr = P.steps[s];
+      if (!sr.batched && p > 0) continue;  // slice-invariant: computed once, kept
+      StepArgs a = step_args(P, sr);
+      const int32_t nbs = sr.batched ? nb : 1;
+      if (sr.cls == TN_CLASS_TC) {
+        TN_CUDA_TRY(launch_contract_tc(a, nbs, P.policy.prec, cplx, st));
+      } else if (sr.cls == TN_CLASS_STREAM) {
+        launch_contract_stream(a, nbs, cplx, P.num_sms, st);
+      } else {
+        launch_contract_simt(a, nbs, cplx, st);
+      }
+    }
+    const TensorRec& R = P.tensors[root];
+    const int64_t np = cplx ? 2 : 1;
+    launch_accumulate_root(reinterpret_cast<const float*>(P.dev + R.offset), R.size,
+                           R.batched ? nb : 1, R.batched ? np * R.size : 0, R.size, cplx, acc, recs,
+                           P.rec_index[root], R.batched, ref, p == 0, st);
+  }
+  launch_finalize_output(acc, P.out_elems, cplx, output, log_scale, scaling ? ref : nullptr, st);
+  TN_CUDA_TRY(cudaGetLastError());
+  return TN_OK;
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+
+extern "C" {
+
+const char* tn_last_error(void) { return g_last_error.c_str(); }
+
+tn_status tn_plan(const tn_network* net, const tn_path* path, const int32_t* sliced_modes,
+                  int32_t n_sliced, tn_dtype_policy policy, tn_plan_t* out) {
+  if (!out) {
+    set_error("null output handle");
+    return TN_ERR_INVALID;
+  }
+  tn_plan_s* h = new (std::nothrow) tn_plan_s();
+  if (!h) {
+    set_error("host allocation failed");
+    return TN_ERR_OOM;
+  }
+  std::string err;
+  tn_status s;
+  try {
+    s = build_plan(net, path, sliced_modes, n_sliced, policy, h->P, err);
+  } catch (const std::exception& e) {
+    err = std::string("planner exception: ") + e.what();
+    s = TN_ERR_INVALID;
+  }
+  if (s != TN_OK) {
+    set_error(err);
+    delete h;
+    return s;
+  }
+  Plan& P = h->P;
+  static std::atomic<uint64_t> next_uid{1};
+  P.uid = next_uid++;
+  const bool host_only = (policy.flags & TN_PLAN_HOST_ONLY) != 0;
+  int64_t want = policy.max_slice_batch > 0 ? std::min<int64_t>(P.n_slices, policy.max_slice_batch)
+                                            : P.n_slices;
+  want = std::min<int64_t>(want, 65535);  // the batch is a grid dimension
+  if (host_only) {
+    if (policy.max_slice_batch <= 0) want = 1;
+    assign_workspace(P, want);
+    if (!P.workspace_ok) {
+      set_error("internal error: workspace assignment failed its self-check");
+      delete h;
+      return TN_ERR_INVALID;
+    }
+    *out = h;
+    return TN_OK;
+  }
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  size_t free_b = 0, total_b = 0;
+  if (ce == cudaSuccess) ce = cudaMemGetInfo(&free_b, &total_b);
+  if (ce != cudaSuccess) {
+    set_error(std::string("CUDA unavailable: ") + cudaGetErrorString(ce));
+    delete h;
+    return TN_ERR_CUDA;
+  }
+  const int64_t budget = int64_t(double(free_b) * 0.9);
+  int64_t b = want;
+  while (b > 1 && batch_footprint(P, b) > budget) b = (b + 1) / 2;
+  if (batch_footprint(P, b) > budget || !P.workspace_ok) {
+    if (!P.workspace_ok) {
+      set_error("internal error: workspace assignment failed its self-check");
+      delete h;
+      return TN_ERR_INVALID;
+    }
+    set_error("workspace of " + std::to_string(P.total_bytes) + " bytes exceeds free device memory");
+    delete h;
+    return TN_ERR_OOM;
+  }
+  void* mem = nullptr;
+  ce = cudaMalloc(&mem, (size_t)P.total_bytes);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMalloc of workspace failed: ") + cudaGetErrorString(ce));
+    delete h;
+    return TN_ERR_OOM;
+  }
+  P.dev = static_cast<char*>(mem);
+  *out = h;
+  return TN_OK;
+}
+
+tn_status tn_plan_info(tn_plan_t plan, tn_plan_stats* out) {
+  if (!plan || !out) {
+    set_error("null argument");
+    return TN_ERR_INVALID;
+  }
+  *out = plan->P.stats;
+  return TN_OK;
+}
+
+tn_status tn_plan_layout(tn_plan_t plan, int32_t id, int32_t* modes_out, int32_t* rank_out) {
+  if (!plan || !rank_out || id < 0 || id >= (int32_t)plan->P.tensors.size()) {
+    set_error("bad plan or tensor id");
+    return TN_ERR_INVALID;
+  }
+  const auto& m = plan->P.tensors[id].modes;
+  *rank_out = (int32_t)m.size();
+  if (modes_out) std::copy(m.begin(), m.end(), modes_out);
+  return TN_OK;
+}
+
+tn_status tn_plan_step(tn_plan_t plan, int32_t s, tn_step_info* out) {
+  if (!plan || !out || s < 0 || s >= (int32_t)plan->P.steps.size()) {
+    set_error("bad plan or step");
+    return TN_ERR_INVALID;
+  }
+  const StepRec& st = plan->P.steps[s];
+  out->m = st.m;
+  out->n = st.n;
+  out->k = st.k;
+  out->a_id = st.a;
+  out->b_id = st.b;
+  out->cls = st.cls;
+  out->batched = st.batched ? 1 : 0;
+  return TN_OK;
+}
+
+tn_status tn_contract_slices(tn_plan_t plan, const void* const* inputs, int64_t slice_begin,
+                             int64_t slice_count, void* output, double* out_log_scale, void* stream) {
+  if (!plan) {
+    set_error("null plan");
+    return TN_ERR_INVALID;
+  }
+  std::string err;
+  tn_status s = run_slices(plan->P, inputs, slice_begin, slice_count, output, out_log_scale, stream, err);
+  if (s != TN_OK) set_error(err);
+  return s;
+}
+
+tn_status tn_contract(tn_plan_t plan, const void* const* inputs, void* output, double* out_log_scale,
+                      void* stream) {
+  if (!plan) {
+    set_error("null plan");
+    return TN_ERR_INVALID;
+  }
+  return tn_contract_slices(plan, inputs, 0, plan->P.n_slices, output, out_log_scale, stream);
+}
+
+tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void* host_output,
+                           double* out_log_scale, void* stream) {
+  if (!plan || !host_inputs || !host_output) {
+    set_error("null argument");
+    return TN_ERR_INVALID;
+  }
+  Plan& P = plan->P;
+  if (!P.dev) {
+    set_error("plan was built with TN_PLAN_HOST_ONLY (no device workspace)");
+    return TN_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t eb = elem_bytes(P);
+  std::vector<const void*> dptr(P.n_leaves);
+  std::string err;
+  auto fail = [&](cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return TN_ERR_CUDA;
+  };
+  for (int32_t t = 0; t < P.n_leaves; ++t) {
+    if (!host_inputs[t]) {
+      set_error("null input pointer");
+      return TN_ERR_INVALID;
+    }
+    int64_t full = 1;
+    for (int32_t x : P.tensors[t].decl) full *= P.extent[x];
+    char* d = P.dev + P.stage_in_off[t];
+    cudaError_t e = cudaMemcpyAsync(d, host_inputs[t], full * eb, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(e, "host-to-device copy of an input");
+    dptr[t] = d;
+  }
+  char* dout = P.dev + P.total_bytes - ((P.out_elems * 16 + 16 + 255) / 256 * 256);
+  double* dls = reinterpret_cast<double*>(dout + P.out_elems * 16);
+  tn_status s = run_slices(P, dptr.data(), 0, P.n_slices, dout, dls, stream, err);
+  if (s != TN_OK) {
+    set_error(err);
+    return s;
+  }
+  const int64_t ob = P.out_elems * (P.is_complex ? 16 : 8);
+  cudaError_t e = cudaMemcpyAsync(host_output, dout, ob, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return fail(e, "device-to-host copy of the result");
+  if (out_log_scale) {
+    e = cudaMemcpyAsync(out_log_scale, dls, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return fail(e, "device-to-host copy of the log scale");
+  }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(e, "stream synchronize");
+  return TN_OK;
+}
+
+tn_status tn_plan_destroy(tn_plan_t plan) {
+  if (!plan) return TN_OK;
+  if (plan->P.dev) cudaFree(plan->P.dev);
+  delete plan;
+  return TN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// Launch interface of the device kernels (internal).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+// Per tensor (and per batch entry of a batched tensor): the largest binary exponent
+// of the stored values, and the power of two the stored values must be multiplied by
+// to give the true tensor (exponent scaling).
+struct ScaleRec {
+  int32_t emax;
+  int32_t pad;
+  int64_t log2;
+};
+
+// One pairwise step C[b] = A[b] (m x k, row-major) . B[b] (n x k, row-major)^T.
+// Planar complex: the imaginary plane of each tensor copy follows its real plane at
+// +*_plane floats. C is written at rows(m) + cols(n). Batch strides are 0 for tensors
+// that do not depend on a sliced label.
+struct StepArgs {
+  const float* A;
+  const float* B;
+  float* C;
+  int64_t m, n, k;
+  int64_t a_bstride, b_bstride, c_bstride;  // floats
+  int64_t a_plane, b_plane, c_plane;        // floats
+  OffsetMap rows, cols;
+  ScaleRec* recs;                           // null: no exponent scaling
+  int32_t rec_a, rec_b, rec_c;
+  int32_t pad;
+};
+
+void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int64_t slice_begin,
+                         int32_t nb, bool only_batched, bool is_complex, ScaleRec* recs,
+                         const int32_t* rec_index, cudaStream_t st);
+void launch_contract_simt(const StepArgs& a, int32_t nb, bool cplx, cudaStream_t st);
+void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, cudaStream_t st);
+void launch_accumulate_root(const float* root, int64_t size, int32_t nb, int64_t bstride,
+                            int64_t plane, bool cplx, double* acc, const ScaleRec* recs,
+                            int32_t rec_root, bool root_batched, int64_t* ref_exp, bool first,
+                            cudaStream_t st);
+void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* out, double* log_scale,
+                            const int64_t* ref_exp, cudaStream_t st);
+
+// tensor-core path (tcgen05); returns false if the step cannot take it
+bool tc_supported();
+cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, cudaStream_t st);
+
+}  // namespace tn

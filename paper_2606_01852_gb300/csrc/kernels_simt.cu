@@ -1,0 +1,395 @@
+// CUDA-core kernels of the contraction engine (sm_103a):
+//   stage_leaves      : leaf staging and slicing (declared order -> planned order,
+//                       sliced labels fixed per batch entry, complex64 -> planar fp32)
+//   contract_simt     : any pairwise step C[b] = A[b](m x k) . B[b](n x k)^T, FP32 FMA,
+//                       written through the separable row/column offset maps
+//   contract_stream   : big x small steps (n*k tiny), one pass over the big operand
+//   accumulate_root   : compensated FP64 sum of the root over the slice batch
+//   finalize_output   : writes the FP64 result and its log scale
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace tn {
+
+// ---------------------------------------------------------------------------------
+// helpers
+
+__device__ __forceinline__ int64_t map_offset(const OffsetMap& om, int64_t idx) {
+  int64_t off = 0;
+  for (int d = om.n - 1; d >= 0; --d) {
+    const uint32_t e = om.ext[d];
+    off += (idx % e) * om.stride[d];
+    idx /= e;
+  }
+  return off;
+}
+
+// floor(log2 |v|) from the IEEE-754 exponent field; very small values map to -127.
+__device__ __forceinline__ int exp_of(float v) {
+  return ((__float_as_int(v) >> 23) & 0xff) - 127;
+}
+
+// 2^-e as a float, e clamped to the normal range.
+__device__ __forceinline__ float pow2_neg(int e) {
+  e = max(-126, min(127, e));
+  return __int_as_float((127 - e) << 23);
+}
+
+__device__ __forceinline__ int scale_exp(const ScaleRec* r) {
+  int e = r->emax;
+  return e < -126 ? 0 : e;  // an all-zero tensor is not rescaled
+}
+
+// ---------------------------------------------------------------------------------
+// leaf staging (a4)
+
+__global__ void stage_leaves_kernel(const LeafDesc* __restrict__ descs, char* __restrict__ ws,
+                                    int64_t slice_begin, int32_t nb, int32_t only_batched,
+                                    int32_t is_complex, ScaleRec* recs, const int32_t* rec_index,
+                                    int32_t rec_batched_base) {
+  const LeafDesc& d = descs[blockIdx.x];
+  if (only_batched && !d.batched) return;
+  const int32_t copies = d.batched ? nb : 1;
+  const int64_t total = d.size * copies;
+  int lmax = -127;
+  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const int64_t b = i / d.size;
+    int64_t e = i - b * d.size;
+    int64_t src = 0;
+    for (int r = d.rank - 1; r >= 0; --r) {
+      const uint32_t x = d.ext[r];
+      src += (e % x) * d.sstride[r];
+      e /= x;
+    }
+    const int64_t sid = slice_begin + b;
+    for (int q = 0; q < d.n_sl; ++q) src += ((sid / d.sl_div[q]) % d.sl_ext[q]) * d.sl_stride[q];
+    const int64_t el = i - b * d.size;
+    if (is_complex) {
+      const float2 v = reinterpret_cast<const float2*>(d.src)[src];
+      float* dst = reinterpret_cast<float*>(ws + d.dst) + b * 2 * d.size;
+      dst[el] = v.x;
+      dst[d.size + el] = v.y;
+      if (recs) lmax = max(lmax, exp_of(fmaxf(fabsf(v.x), fabsf(v.y))));
+    } else {
+      const float v = reinterpret_cast<const float*>(d.src)[src];
+      float* dst = reinterpret_cast<float*>(ws + d.dst) + b * d.size;
+      dst[el] = v;
+      if (recs) lmax = max(lmax, exp_of(fabsf(v)));
+    }
+  }
+  if (recs) {
+    // one block per leaf: the leaf's copies share a record per batch entry; a leaf
+    // copy is tiny, so take the block-wide max over all copies (same for every b).
+    __shared__ int smax;
+    if (threadIdx.x == 0) smax = -127;
+    __syncthreads();
+    atomicMax(&smax, lmax);
+    __syncthreads();
+    for (int q = threadIdx.x; q < copies; q += blockDim.x) {
+      ScaleRec* r = recs + rec_index[blockIdx.x] + (d.batched ? q : 0);
+      r->emax = smax;
+      r->log2 = 0;
+    }
+  }
+}
+
+void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int64_t slice_begin,
+                         int32_t nb, bool only_batched, bool is_complex, ScaleRec* recs,
+                         const int32_t* rec_index, cudaStream_t st) {
+  if (n_leaves <= 0) return;
+  stage_leaves_kernel<<<n_leaves, 128, 0, st>>>(descs, ws, slice_begin, nb, only_batched ? 1 : 0,
+                                                is_complex ? 1 : 0, recs, rec_index, 0);
+}
+
+// ---------------------------------------------------------------------------------
+// generic step kernel: 64 x 64 output tile, 16-deep k slices, 256 threads, 4 x 4
+// outputs per thread (rows ty*4.., columns tx + 16j so a half-warp stores 16
+// consecutive columns).
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
+  constexpr int BM = 64, BN = 64, BK = 16, NP = CPLX ? 2 : 1;
+  __shared__ float As[NP][BK][BM + 4];
+  __shared__ float Bs[NP][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t tiles_n = (a.n + BN - 1) / BN;
+  const int64_t tile = blockIdx.x;
+  const int64_t m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+  const int b = blockIdx.y;
+  const float* A = a.A + b * a.a_bstride;
+  const float* B = a.B + b * a.b_bstride;
+  float* C = a.C + b * a.c_bstride;
+  float sa = 1.f, sb = 1.f;
+  if (a.recs) {
+    const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
+    const ScaleRec* rb = a.recs + a.rec_b + (a.b_bstride ? b : 0);
+    sa = pow2_neg(scale_exp(ra));
+    sb = pow2_neg(scale_exp(rb));
+  }
+  float accr[4][4], acci[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.f;
+
+  const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: row lr, k lk..lk+3
+  for (int64_t k0 = 0; k0 < a.k; k0 += BK) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t kk = k0 + lk + q;
+        const int64_t ra = m0 + lr, rb = n0 + lr;
+        float va = 0.f, vb = 0.f;
+        if (ra < a.m && kk < a.k) va = A[p * a.a_plane + ra * a.k + kk] * sa;
+        if (rb < a.n && kk < a.k) vb = B[p * a.b_plane + rb * a.k + kk] * sb;
+        As[p][lk + q][lr] = va;
+        Bs[p][lk + q][lr] = vb;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float ar[4], br[4], ai[4], bi[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ar[i] = As[0][kk][ty * 4 + i];
+        br[i] = Bs[0][kk][tx + 16 * i];
+        if (CPLX) {
+          ai[i] = As[1][kk][ty * 4 + i];
+          bi[i] = Bs[1][kk][tx + 16 * i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (CPLX) {
+            accr[i][j] = fmaf(ar[i], br[j], accr[i][j]);
+            accr[i][j] = fmaf(-ai[i], bi[j], accr[i][j]);
+            acci[i][j] = fmaf(ar[i], bi[j], acci[i][j]);
+            acci[i][j] = fmaf(ai[i], br[j], acci[i][j]);
+          } else {
+            accr[i][j] = fmaf(ar[i], br[j], accr[i][j]);
+          }
+        }
+    }
+    __syncthreads();
+  }
+  // epilogue through the offset maps
+  int64_t coff[4];
+  bool cok[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t n = n0 + tx + 16 * j;
+    cok[j] = n < a.n;
+    coff[j] = cok[j] ? map_offset(a.cols, n) : 0;
+  }
+  int lmax = -127;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t m = m0 + ty * 4 + i;
+    if (m >= a.m) continue;
+    const int64_t ro = map_offset(a.rows, m);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!cok[j]) continue;
+      C[ro + coff[j]] = accr[i][j];
+      if (CPLX) C[a.c_plane + ro + coff[j]] = acci[i][j];
+      if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(accr[i][j]), fabsf(acci[i][j]))
+                                               : fabsf(accr[i][j])));
+    }
+  }
+  if (a.recs) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    ScaleRec* rc = a.recs + a.rec_c + (a.c_bstride ? b : 0);
+    if ((tid & 31) == 0) atomicMax(&rc->emax, lmax);
+    if (tile == 0 && tid == 0) {
+      const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
+      const ScaleRec* rb = a.recs + a.rec_b + (a.b_bstride ? b : 0);
+      rc->log2 = ra->log2 + rb->log2 + scale_exp(ra) + scale_exp(rb);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// big x small steps (n*k <= 256, n <= 16): the small operand sits in shared memory
+// and every thread streams rows of the big one; one HBM pass over A and C.
+
+template <bool CPLX, int NMAX>
+__global__ void __launch_bounds__(256) contract_stream_kernel(StepArgs a) {
+  __shared__ float Bs[2][256];
+  const int b = blockIdx.y;
+  const float* A = a.A + b * a.a_bstride;
+  const float* Bp = a.B + b * a.b_bstride;
+  float* C = a.C + b * a.c_bstride;
+  float sa = 1.f, sb = 1.f;
+  if (a.recs) {
+    sa = pow2_neg(scale_exp(a.recs + a.rec_a + (a.a_bstride ? b : 0)));
+    sb = pow2_neg(scale_exp(a.recs + a.rec_b + (a.b_bstride ? b : 0)));
+  }
+  const int nk = (int)(a.n * a.k);
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+    Bs[0][i] = Bp[i] * sb;
+    if (CPLX) Bs[1][i] = Bp[a.b_plane + i] * sb;
+  }
+  __syncthreads();
+  const int n = (int)a.n, k = (int)a.k;
+  int64_t coff[NMAX];
+#pragma unroll
+  for (int j = 0; j < NMAX; ++j) coff[j] = j < n ? map_offset(a.cols, j) : 0;
+  int lmax = -127;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.m;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    float cr[NMAX], ci[NMAX];
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) cr[j] = ci[j] = 0.f;
+    const float* arow = A + r * k;
+    for (int kk = 0; kk < k; ++kk) {
+      const float xr = arow[kk] * sa;
+      const float xi = CPLX ? arow[a.a_plane + kk] * sa : 0.f;
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+          const float yr = Bs[0][j * k + kk];
+          if (CPLX) {
+            const float yi = Bs[1][j * k + kk];
+            cr[j] = fmaf(xr, yr, cr[j]);
+            cr[j] = fmaf(-xi, yi, cr[j]);
+            ci[j] = fmaf(xr, yi, ci[j]);
+            ci[j] = fmaf(xi, yr, ci[j]);
+          } else {
+            cr[j] = fmaf(xr, yr, cr[j]);
+          }
+        }
+      }
+    }
+    const int64_t ro = map_offset(a.rows, r);
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+      if (j < n) {
+        C[ro + coff[j]] = cr[j];
+        if (CPLX) C[a.c_plane + ro + coff[j]] = ci[j];
+        if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(cr[j]), fabsf(ci[j])) : fabsf(cr[j])));
+      }
+    }
+  }
+  if (a.recs) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    ScaleRec* rc = a.recs + a.rec_c + (a.c_bstride ? b : 0);
+    if ((threadIdx.x & 31) == 0) atomicMax(&rc->emax, lmax);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
+      const ScaleRec* rb = a.recs + a.rec_b + (a.b_bstride ? b : 0);
+      rc->log2 = ra->log2 + rb->log2 + scale_exp(ra) + scale_exp(rb);
+    }
+  }
+}
+
+void launch_contract_simt(const StepArgs& a, int32_t nb, bool cplx, cudaStream_t st) {
+  const int64_t tiles = ((a.m + 63) / 64) * ((a.n + 63) / 64);
+  dim3 grid((unsigned)tiles, (unsigned)nb);
+  if (cplx) contract_simt_kernel<true><<<grid, 256, 0, st>>>(a);
+  else contract_simt_kernel<false><<<grid, 256, 0, st>>>(a);
+}
+
+void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, cudaStream_t st) {
+  int64_t blocks = (a.m + 255) / 256;
+  const int64_t cap = (int64_t)num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  dim3 grid((unsigned)blocks, (unsigned)nb);
+#define TN_STREAM_CASE(NM)                                                            \
+  if (a.n <= NM) {                                                                     \
+    if (cplx) contract_stream_kernel<true, NM><<<grid, 256, 0, st>>>(a);               \
+    else contract_stream_kernel<false, NM><<<grid, 256, 0, st>>>(a);                   \
+    return;                                                                            \
+  }
+  TN_STREAM_CASE(2)
+  TN_STREAM_CASE(4)
+  TN_STREAM_CASE(8)
+  TN_STREAM_CASE(16)
+#undef TN_STREAM_CASE
+}
+
+// ---------------------------------------------------------------------------------
+// cross-slice accumulation (a7): per output element, add the nb slice results of
+// this pass in slice order with Neumaier compensation; with exponent scaling each
+// slice's value is brought to the reference exponent of the first slice ever added.
+
+__global__ void accumulate_root_kernel(const float* __restrict__ root, int64_t size, int32_t nb,
+                                       int64_t bstride, int64_t plane, int32_t cplx, double* acc,
+                                       const ScaleRec* recs, int32_t rec_root, int32_t root_batched,
+                                       int64_t* ref_exp, int32_t first) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= size) return;
+  double* s = acc + e * 4;  // [sum re, sum im, comp re, comp im]
+  double sr = first ? 0.0 : s[0], si = first ? 0.0 : s[1];
+  double cr = first ? 0.0 : s[2], ci = first ? 0.0 : s[3];
+  int64_t ref = 0;
+  if (recs) {
+    const ScaleRec* r0 = recs + rec_root;
+    ref = first ? r0->log2 : *ref_exp;
+  }
+  for (int b = 0; b < nb; ++b) {
+    double vr = root[b * bstride + e];
+    double vi = cplx ? root[b * bstride + plane + e] : 0.0;
+    if (recs) {
+      const ScaleRec* r = recs + rec_root + (root_batched ? b : 0);
+      // stored values are unscaled outputs of the last step: true = v * 2^log2
+      const int64_t sh = r->log2 - ref;
+      vr = ldexp(vr, (int)sh);
+      vi = ldexp(vi, (int)sh);
+    }
+    double t = sr + vr;
+    cr += fabs(sr) >= fabs(vr) ? (sr - t) + vr : (vr - t) + sr;
+    sr = t;
+    t = si + vi;
+    ci += fabs(si) >= fabs(vi) ? (si - t) + vi : (vi - t) + si;
+    si = t;
+  }
+  s[0] = sr;
+  s[1] = si;
+  s[2] = cr;
+  s[3] = ci;
+  if (recs && first && e == 0) *ref_exp = ref;
+}
+
+void launch_accumulate_root(const float* root, int64_t size, int32_t nb, int64_t bstride,
+                            int64_t plane, bool cplx, double* acc, const ScaleRec* recs,
+                            int32_t rec_root, bool root_batched, int64_t* ref_exp, bool first,
+                            cudaStream_t st) {
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((size + threads - 1) / threads);
+  accumulate_root_kernel<<<blocks, threads, 0, st>>>(root, size, nb, bstride, plane, cplx ? 1 : 0, acc,
+                                                     recs, rec_root, root_batched ? 1 : 0, ref_exp,
+                                                     first ? 1 : 0);
+}
+
+__global__ void finalize_output_kernel(const double* acc, int64_t size, int32_t cplx, void* out,
+                                       double* log_scale, const int64_t* ref_exp) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < size) {
+    const double* s = acc + e * 4;
+    if (cplx) {
+      reinterpret_cast<double2*>(out)[e] = make_double2(s[0] + s[2], s[1] + s[3]);
+    } else {
+      reinterpret_cast<double*>(out)[e] = s[0] + s[2];
+    }
+  }
+  if (e == 0 && log_scale) *log_scale = ref_exp ? double(*ref_exp) * 0.69314718055994530942 : 0.0;
+}
+
+void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* out, double* log_scale,
+                            const int64_t* ref_exp, cudaStream_t st) {
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((size + threads - 1) / threads);
+  finalize_output_kernel<<<blocks, threads, 0, st>>>(acc, size, cplx ? 1 : 0, out, log_scale, ref_exp);
+}
+
+}  // namespace tn

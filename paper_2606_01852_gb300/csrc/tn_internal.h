@@ -1,0 +1,124 @@
+// Internal declarations shared by the planner, the executor and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tn.h"
+
+namespace tn {
+
+constexpr int kMaxDims = 12;     // merged output-offset dims per GEMM side
+constexpr int kMaxLeafRank = 24; // planned rank of a leaf the staging kernel handles
+constexpr int kMaxSliced = 24;   // sliced labels carried by one leaf
+
+// Maps a GEMM row (or column) index to an output offset: the index is read as
+// mixed radix over `n` merged dims (last dim fastest) and each digit is scaled by
+// that dim's output stride. Sec. IV-A lets an output interleave the modes of its two
+// operands; this is how the kernels write such an output without a transpose.
+struct OffsetMap {
+  int32_t n;
+  uint32_t ext[kMaxDims];
+  int64_t stride[kMaxDims];
+};
+
+// Per-leaf staging descriptor (a4): copy leaf t from its declared order into its
+// planned order, fixing sliced labels from the slice id, and split complex64 into
+// planar float32 (re plane, im plane).
+struct LeafDesc {
+  const void* src;          // caller's leaf, declared order
+  int64_t dst;              // byte offset of the staged tensor in the workspace
+  int64_t size;             // elements of one staged copy (sliced labels removed)
+  int32_t rank;             // planned rank
+  int32_t batched;          // carries a sliced label
+  int32_t n_sl;             // sliced labels on this leaf
+  int32_t pad;
+  uint32_t ext[kMaxLeafRank];      // planned extents
+  int64_t sstride[kMaxLeafRank];   // source stride (elements) of each planned position
+  int64_t sl_div[kMaxSliced];      // slice id -> label value: (sid / div) % ext
+  uint32_t sl_ext[kMaxSliced];
+  int64_t sl_stride[kMaxSliced];   // source stride of that sliced label
+};
+
+struct TensorRec {
+  std::vector<int32_t> decl;   // declared modes (leaves only; incl. sliced)
+  std::vector<int32_t> modes;  // planned order, sliced labels removed
+  int64_t size = 1;            // elements per slice
+  bool batched = false;
+  int32_t producer = -1;       // step, or -1 for a leaf
+  int32_t consumer = -1;       // step, or -1 for the root
+  bool pinned = false;         // unbatched, consumed by a batched step: kept for all passes
+  int64_t offset = 0;          // byte offset in the workspace
+  int64_t bytes = 0;           // bytes including the batch copies
+};
+
+struct StepRec {
+  int32_t a = -1, b = -1, out = -1;  // SSA ids; a is the row operand
+  std::vector<int32_t> M, N, K;
+  int64_t m = 1, n = 1, k = 1;
+  int32_t cls = TN_CLASS_SIMT;
+  bool batched = false;
+  OffsetMap rows{}, cols{};
+};
+
+struct Plan {
+  // network
+  int32_t n_leaves = 0, n_labels = 0;
+  std::vector<int64_t> extent;
+  std::vector<int32_t> open_modes;
+  std::vector<int32_t> sliced;
+  std::vector<int64_t> slice_div;   // per sliced label position
+  int64_t n_slices = 1;
+  bool is_complex = true;
+  tn_dtype_policy policy{};
+  // plan
+  std::vector<TensorRec> tensors;   // SSA ids
+  std::vector<StepRec> steps;
+  int64_t batch = 1;                // slices per pass
+  int64_t arena_bytes = 0;
+  int64_t out_elems = 1;
+  // workspace regions (byte offsets from the workspace base)
+  int64_t off_acc = 0;              // FP64 Neumaier accumulator: [sum, comp] x re/im x out
+  int64_t off_scale = 0;            // per tensor x batch: int32 emax, int32 pad, int64 log2
+  int64_t off_recidx = 0;           // int32 record index of each leaf (device copy)
+  int64_t off_ref = 0;              // int64 reference exponent of the accumulator
+  std::vector<int32_t> rec_index;   // per tensor: first scale record
+  int64_t n_rec_unbatched = 0, n_rec_total = 0;
+  int64_t off_leafdesc = 0;         // LeafDesc table
+  int64_t off_stage_in = 0;         // device copies of host inputs (tn_contract_host)
+  std::vector<int64_t> stage_in_off;
+  int64_t total_bytes = 0;
+  bool workspace_ok = false;        // liveness assignment passed its self-check
+  // device state
+  char* dev = nullptr;
+  std::vector<LeafDesc> leafdesc;   // host copy; src filled per call
+  int num_sms = 148;
+  uint64_t uid = 0;                 // unique per plan (serve pools key on it)
+  // stats
+  tn_plan_stats stats{};
+};
+
+// planner (host only)
+tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* sliced,
+                     int32_t n_sliced, const tn_dtype_policy& pol, Plan& P, std::string& err);
+// liveness assignment of workspace offsets for a given slice batch
+void assign_workspace(Plan& P, int64_t batch);
+
+// executor
+tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t count,
+                     void* output, double* log_scale, void* stream, std::string& err);
+
+void set_error(const std::string& msg);
+
+// true when the tcgen05 kernels are compiled in
+bool tc_supported();
+
+inline int64_t elem_bytes(const Plan& P) { return P.is_complex ? 8 : 4; }
+
+}  // namespace tn
+
+// opaque handle of the C ABI
+struct tn_plan_s {
+  tn::Plan P;
+};

@@ -1,0 +1,139 @@
+"""The C-ABI library loads and exports every symbol include/tn.h declares, and the
+host-only planner follows Sec. IV-A (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from tests._lib import ROOT, ensure_built
+from tn_inputs import greedy, workloads, circuits
+from tn_inputs.network import Network, Path
+
+
+def declared_functions():
+    hdr = open(os.path.join(ROOT, "include", "tn.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(tn_[a-z_0-9]+)\s*\(", hdr)))
+
+
+def test_library_exports_every_declared_symbol():
+    tn = ensure_built()
+    lib = ctypes.CDLL(tn.LIB_PATH)
+    names = declared_functions()
+    assert "tn_plan" in names and "tn_serve_poll" in names and "tn_last_error" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def _fig2_network():
+    a, b, c, d, e, f, g, h = range(8)
+    ext = {x: 2 for x in range(8)}
+    rng = np.random.default_rng(0)
+    I1 = (c, a, d, b)   # arbitrary local orders (panel A)
+    I2 = (f, d, e, c)
+    I3 = (b, h, f, g)
+    mk = lambda ms: rng.standard_normal((2,) * len(ms)) + 0j
+    net = Network([mk(I1), mk(I2), mk(I3)], [I1, I2, I3], ext, (g, a, h, e))
+    net.check()
+    return net, Path([(0, 1), (3, 2)])
+
+
+def test_fig2_worked_example_golden():
+    tn = ensure_built()
+    net, path = _fig2_network()
+    plan = tn.Plan(net, path, host_only=True)
+    want = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "fig2_mode_reorder.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            want[k] = v
+    name = lambda ms: "".join("abcdefgh"[x] for x in ms)
+    ids = {"I1": 0, "I2": 1, "I3": 2, "I4": 3, "I5": 4}
+    for k, v in want.items():
+        assert name(plan.layout(ids[k])) == v, (k, name(plan.layout(ids[k])), v)
+    # step 1's output interleaves the two operands' modes (e outlives b)
+    assert plan.info()["leaf_permutes"] == 3
+
+
+def _lifetimes(net, path):
+    """Step index at which each label is summed; open labels never are."""
+    T = net.n_tensors
+    sets = [set(m) for m in net.modes]
+    when = {}
+    for s, (i, j) in enumerate(path.pairs):
+        for x in sets[i] & sets[j]:
+            when[x] = s
+        sets.append((sets[i] | sets[j]) - (sets[i] & sets[j]))
+    return when
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_reorder_invariants_random_trees(seed):
+    """Every operand is [retained in output order | reduced]; every tensor's modes are
+    sorted by remaining lifetime, longest-lived leftmost (Sec. IV-A); no label is
+    created or dropped."""
+    tn = ensure_built()
+    net = circuits.amplitude_network(3, 3, 6, seed)
+    path = greedy.greedy_path(net, seed=seed, temperature=0.3)
+    plan = tn.Plan(net, path, host_only=True)
+    T = net.n_tensors
+    when = _lifetimes(net, path)
+    inf = 10**9
+    sets = [set(m) for m in net.modes]
+    for s, (i, j) in enumerate(path.pairs):
+        sets.append((sets[i] | sets[j]) - (sets[i] & sets[j]))
+    for tid in range(T + len(path.pairs)):
+        lay = plan.layout(tid)
+        assert set(lay) == sets[tid]
+        life = [when.get(x, inf) for x in lay]
+        assert life == sorted(life, reverse=True), (tid, lay, life)
+    for s, (i, j) in enumerate(path.pairs):
+        out = plan.layout(T + s)
+        K = sorted(sets[i] & sets[j])
+        for op in (i, j):
+            lay = plan.layout(op)
+            kept = [x for x in out if x in sets[op]]
+            assert list(lay) == kept + K
+
+
+def test_plan_step_costs_match_oracle_counts():
+    """tn_plan_info's C_t, C_m, C_s (Sec. II-B Eqs. 1-3) equal the oracle's counts."""
+    import oracle
+    tn = ensure_built()
+    w = workloads.rc12()
+    plan = tn.Plan(w.net, w.path, host_only=True)
+    info = plan.info()
+    want = oracle.path_costs(w.net, w.path)
+    assert info["Ct"] == want["Ct"] and info["Cm"] == want["Cm"] and info["Cs"] == want["Cs"]
+    assert info["flops"] == 8 * want["Ct"]
+    for s, c in enumerate(oracle.step_costs(w.net, w.path)):
+        st = plan.step(s)
+        assert st["m"] * st["n"] * st["k"] == c["Ct"]
+        assert sorted([st["m"], st["n"]]) == sorted([c["m"], c["n"]]) and st["k"] == c["k"]
+
+
+def test_plan_rejects_bad_input():
+    tn = ensure_built()
+    net, path = _fig2_network()
+    with pytest.raises(tn.TnError) as e:
+        tn.Plan(net, Path([(0, 1)]), host_only=True)       # not a full tree
+    assert e.value.status == tn.TN_ERR_INVALID
+    with pytest.raises(tn.TnError):
+        tn.Plan(net, Path([(0, 1), (3, 3)]), host_only=True)  # reused operand
+    bad = Network(net.tensors, [net.modes[0], net.modes[1], net.modes[0]], net.extent, net.open_modes)
+    with pytest.raises(tn.TnError) as e:
+        tn.Plan(bad, path, host_only=True)                  # label in three tensors
+    assert e.value.status in (tn.TN_ERR_UNSUPPORTED, tn.TN_ERR_INVALID)
+    with pytest.raises(tn.TnError) as e:
+        tn.Plan(net, path, sliced=[6], host_only=True)       # slicing an open label
+    assert e.value.status == tn.TN_ERR_UNSUPPORTED
+
+
+def test_sliced_plan_batches():
+    tn = ensure_built()
+    w = workloads.random_circuit(3, 4, 8, 3, n_sliced=4)
+    plan = tn.Plan(w.net, w.path, w.sliced, max_slice_batch=4, host_only=True)
+    info = plan.info()
+    assert info["n_slices"] == 16 and info["slice_batch"] == 4 and info["n_passes"] == 4
