@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Benchmark: exact contraction of a sliced 40-qubit random-circuit amplitude on one GB300.
+
+One step = one tn_contract over all 256 slices of the workload (leaf staging and
+slicing, every pairwise step, the FP64 cross-slice sum), inputs resident in HBM.
+Prints one JSON line (see the keys below). `--impl reference` times the CPU
+complex128 oracle instead, on a bounded sample of the same workload per step.
+Under torchrun every rank contracts its own full copy of the workload (independent
+units, no data-path collective: weak scaling); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from tn_inputs import workloads  # noqa: E402
+
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+NOMINAL_TF32_PER_BF16 = 1.1 / 2.25     # nominal dense tf32 / bf16 rate of the part
+SM_COUNT, FP32_LANES = 152, 128
+WORKLOAD_DESC = {
+    "rc40": "40-qubit 5x8 grid random circuit, 13 brick-wall cycles of Haar 2-qubit gates, "
+            "one amplitude, greedy path, 8 sliced labels (256 slices), complex64",
+    "kising44": "4x4 kicked Ising, 10 Trotter steps (J=1, dt=0.25, h=0.9), <Z_centre>, complex64",
+    "rc12": "12-qubit 3x4 random circuit, 8 cycles, one amplitude, complex64",
+}
+PREC = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    d = dict(FALLBACK_PEAKS)
+    d["_source"] = "fallback"
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(w, budget_s, slice_id=0):
+    """The CPU oracle, as it stands, on one slice of the workload, step by step in path
+    order until `budget_s` of CPU time: returns (flops done, seconds, steps done)."""
+    import oracle
+    from oracle import core
+    vals = core.slice_assignment(w.net, w.sliced, slice_id)
+    arrays, modes = core.restrict_leaves(w.net, vals)
+    ts = [np.asarray(t, dtype=np.complex128) for t in arrays]
+    ms = [tuple(m) for m in modes]
+    keep = set(w.net.open_modes)
+    costs = oracle.step_costs(w.net, w.path, w.sliced)
+    flops, done = 0.0, 0
+    t0 = time.perf_counter()
+    for s, (i, j) in enumerate(w.path.pairs):
+        c, mc = core.pairwise(ts[i], ms[i], ts[j], ms[j], keep)
+        ts.append(c)
+        ms.append(mc)
+        ts[i] = ts[j] = None
+        flops += 8.0 * costs[s]["Ct"]
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return flops, time.perf_counter() - t0, done
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workloads.BY_NAME[args.workload]()
+    budget = args.ref_budget
+    for _ in range(args.warmup):
+        oracle_sample(w, min(1.0, budget))
+    vals, secs, samples = [], [], []
+    for k in range(args.steps):
+        f, s, done = oracle_sample(w, budget, slice_id=k % max(1, w.n_slices))
+        vals.append(f / s / 1e12)
+        secs.append(s)
+        samples.append(done)
+    v = statistics.mean(vals)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "contraction TFLOP/s", "value": v, "unit": "TFLOP/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, ""),
+                   "slices": w.n_slices},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {min(samples)}-{max(samples)} of {len(w.path.pairs)} path steps of "
+                                   f"one slice per step, {budget:.0f} s budget per step"},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_2606_01852_gb300 as tn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    peaks = load_peaks()
+    w = workloads.BY_NAME[args.workload]()
+    prec = PREC[args.prec]
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=args.max_slice_batch)
+    info = plan.info()
+    stream = torch.cuda.current_stream()
+    ins = [torch.tensor(np.asarray(t), dtype=torch.complex64, device="cuda") for t in w.net.tensors]
+    out = torch.zeros((), dtype=torch.complex128, device="cuda")
+    ls = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    for _ in range(args.warmup):
+        plan.contract(ins, out, ls, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    plan.profile(True)
+    plan.profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps, outside the events
+        ev[k][0].record(stream)
+        plan.contract(ins, out, ls, stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    plan.profile(False)
+    prof = plan.profile_read(reset=True)
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(times)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    flops = info["flops"]
+    value = ws * flops / (ms_max / 1e3) / 1e12
+    result = complex(out.cpu())
+
+    # dominant kernel class by device time, and its roofline
+    cls = max(range(3), key=lambda c: prof["ms"][c])
+    names = {0: "contract_simt", 1: "contract_stream", 2: "contract_tc"}
+    launches = prof["launches"][cls]
+    per_launch_ms = prof["ms"][cls] / max(1, launches)
+    if cls == 1:
+        achieved = prof["bytes"][cls] / (prof["ms"][cls] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    elif cls == 2:
+        bf = peaks["bf16_tflops_sustained"]
+        tf32 = bf * NOMINAL_TF32_PER_BF16
+        form_peak = {1: tf32, 2: tf32 / 3.0, 3: bf / 3.0}[prec]
+        achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": form_peak, "unit": "TFLOP/s"}
+    else:
+        alu = SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = names[cls]
+    roof["launches_per_step"] = launches / args.steps
+    roof["ms_per_launch"] = per_launch_ms
+    roof["share_of_step"] = prof["ms"][cls] / sum(prof["ms"])
+    roof["peak_source"] = peaks["_source"]
+
+    # end to end through the public C ABI with host buffers
+    host_in = [np.ascontiguousarray(np.asarray(t, dtype=np.complex64)) for t in w.net.tensors]
+    host_out = np.zeros((), dtype=np.complex128)
+    host_ls = np.zeros(1)
+    h2d = int(sum(a.nbytes for a in host_in))
+    plan.contract_host(host_in, host_out, host_ls)
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.contract_host(host_in, host_out, host_ls)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_val = ws * flops / e2e_s / 1e12
+
+    line = {
+        "metric": "contraction TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, ""),
+                   "prec": args.prec, "slices": info["n_slices"], "slice_batch": info["slice_batch"],
+                   "passes": info["n_passes"], "flops_per_step": flops,
+                   "algorithmic_bytes_per_step": info["bytes"],
+                   "l2": "256 MiB buffer written between timed steps (L2 is 129 MB); "
+                         "intermediates are GBs", "parallelism": f"replicas{ws}"},
+        "slices_per_s": ws * info["n_slices"] / (ms_max / 1e3),
+        "result": [result.real, result.imag],
+        "roofline": roof,
+        "per_class": {names[c]: {"launches": prof["launches"][c], "ms": prof["ms"][c],
+                                 "flops": prof["flops"][c], "bytes": prof["bytes"][c]} for c in range(3)},
+        "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
+        "gpu_launches": plan.launches_per_call() * args.steps,
+        "clocks": ck,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        f, s, done = oracle_sample(w, args.ref_budget)
+        line["cpu_baseline"] = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"first {done} of {len(w.path.pairs)} path steps of slice 0 "
+                                          f"({f:.3g} of {info['flops'] / info['n_slices']:.3g} flops of one "
+                                          f"slice, {s:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.destroy()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rc40", choices=sorted(workloads.BY_NAME))
+    ap.add_argument("--prec", default="fp32", choices=sorted(PREC))
+    ap.add_argument("--max-slice-batch", type=int, default=0)
+    ap.add_argument("--ref-budget", type=float, default=20.0, help="oracle seconds per sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

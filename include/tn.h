@@ -162,6 +162,27 @@ tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void*
 /* Free the plan and its device workspace (after any contract on it has finished). */
 tn_status tn_plan_destroy(tn_plan_t plan);
 
+/* ---- per-kernel-class timing (the roofline evidence) ------------------------------ */
+
+/* Per kernel class (index tn_step_class): launches, device milliseconds measured with
+ * CUDA events recorded on the contract's stream around each step launch, and the
+ * algorithmic flops (8mnk complex, 2mnk real) and bytes (e(mk+kn+mn), each operand
+ * and the output counted once per batch entry that reads or writes it). */
+typedef struct {
+  int64_t launches[3];
+  double ms[3];
+  double flops[3];
+  double bytes[3];
+} tn_profile;
+
+/* enable != 0: later contract calls on this plan record events around every step
+ * launch (a few microseconds per launch). enable == 0 stops recording. */
+tn_status tn_plan_profile(tn_plan_t plan, int32_t enable);
+
+/* Wait for the recorded events and write the totals accumulated since the last reset
+ * to *out; reset != 0 clears the totals after reading. */
+tn_status tn_plan_profile_read(tn_plan_t plan, tn_profile* out, int32_t reset);
+
 /* ---- serving: continuous batching of contraction requests ------------------------ */
 
 typedef struct {

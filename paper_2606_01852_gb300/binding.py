@@ -63,6 +63,11 @@ class tn_step_info(C.Structure):
                 ("b_id", C.c_int32), ("cls", C.c_int32), ("batched", C.c_int32)]
 
 
+class tn_profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 3), ("ms", C.c_double * 3), ("flops", C.c_double * 3),
+                ("bytes", C.c_double * 3)]
+
+
 class tn_serve_config(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("n_streams", C.c_int32),
                 ("hbm_budget_bytes", C.c_int64), ("queue_capacity", C.c_int32),
@@ -84,6 +89,8 @@ def _load():
         "tn_contract_slices": [vp, C.POINTER(vp), i64, i64, vp, vp, vp],
         "tn_contract_host": [vp, C.POINTER(vp), vp, vp, vp],
         "tn_plan_destroy": [vp],
+        "tn_plan_profile": [vp, i32],
+        "tn_plan_profile_read": [vp, C.POINTER(tn_profile), i32],
         "tn_serve_create": [C.POINTER(tn_serve_config), C.POINTER(vp)],
         "tn_serve_submit": [vp, vp, C.POINTER(vp), C.POINTER(u64)],
         "tn_serve_poll": [vp, u64, vp, vp, i32],
@@ -216,6 +223,25 @@ class Plan:
     def contract_host(self, host_inputs, host_output, log_scale=None, stream=None):
         check(lib.tn_contract_host(self.handle, self._inputs(host_inputs), _ptr(host_output),
                                    _ptr(log_scale), _ptr_stream(stream)))
+
+    def profile(self, enable: bool):
+        check(lib.tn_plan_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self, reset=True) -> dict:
+        p = tn_profile()
+        check(lib.tn_plan_profile_read(self.handle, C.byref(p), 1 if reset else 0))
+        return {f: list(getattr(p, f)) for f, _ in tn_profile._fields_}
+
+    def launches_per_call(self, count=None) -> int:
+        """Kernel launches of one contract over `count` slices (default all)."""
+        info = self.info()
+        count = info["n_slices"] if count is None else count
+        b = info["slice_batch"]
+        passes = (count + b - 1) // b
+        S = info["n_steps"]
+        batched = sum(1 for s in range(S) if self.step(s)["batched"])
+        # per pass: staging + steps + root accumulation; once: the output write
+        return passes * 2 + S + (passes - 1) * batched + 1
 
     def destroy(self):
         if getattr(self, "handle", None):

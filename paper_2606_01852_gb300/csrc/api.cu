@@ -55,6 +55,16 @@ StepArgs step_args(const Plan& P, const StepRec& st) {
   a.rec_c = P.rec_index[st.out];
   return a;
 }
+void* take_event(Plan& P) {
+  if (!P.prof_pool.empty()) {
+    void* e = P.prof_pool.back();
+    P.prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -117,12 +127,27 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
       if (!sr.batched && p > 0) continue;  // slice-invariant: computed once, kept
       StepArgs a = step_args(P, sr);
       const int32_t nbs = sr.batched ? nb : 1;
+      Plan::ProfRec pr{};
+      if (P.prof_on) {
+        pr.e0 = take_event(P);
+        pr.e1 = take_event(P);
+        pr.cls = sr.cls;
+        const double eb = cplx ? 8.0 : 4.0;
+        const double m = double(sr.m), n = double(sr.n), k = double(sr.k);
+        pr.flops = (cplx ? 8.0 : 2.0) * m * n * k * nbs;
+        pr.bytes = eb * (m * k * (a.a_bstride ? nbs : 1) + n * k * (a.b_bstride ? nbs : 1) + m * n * nbs);
+        TN_CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(pr.e0), st));
+      }
       if (sr.cls == TN_CLASS_TC) {
         TN_CUDA_TRY(launch_contract_tc(a, nbs, P.policy.prec, cplx, st));
       } else if (sr.cls == TN_CLASS_STREAM) {
         launch_contract_stream(a, nbs, cplx, P.num_sms, st);
       } else {
         launch_contract_simt(a, nbs, cplx, st);
+      }
+      if (P.prof_on) {
+        TN_CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(pr.e1), st));
+        P.prof_pending.push_back(pr);
       }
     }
     const TensorRec& R = P.tensors[root];
@@ -333,7 +358,49 @@ tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void*
 tn_status tn_plan_destroy(tn_plan_t plan) {
   if (!plan) return TN_OK;
   if (plan->P.dev) cudaFree(plan->P.dev);
+  for (auto& r : plan->P.prof_pending) {
+    cudaEventDestroy(static_cast<cudaEvent_t>(r.e0));
+    cudaEventDestroy(static_cast<cudaEvent_t>(r.e1));
+  }
+  for (void* e : plan->P.prof_pool) cudaEventDestroy(static_cast<cudaEvent_t>(e));
   delete plan;
+  return TN_OK;
+}
+
+tn_status tn_plan_profile(tn_plan_t plan, int32_t enable) {
+  if (!plan) {
+    set_error("null plan");
+    return TN_ERR_INVALID;
+  }
+  plan->P.prof_on = enable != 0;
+  return TN_OK;
+}
+
+tn_status tn_plan_profile_read(tn_plan_t plan, tn_profile* out, int32_t reset) {
+  if (!plan || !out) {
+    set_error("null argument");
+    return TN_ERR_INVALID;
+  }
+  Plan& P = plan->P;
+  for (auto& r : P.prof_pending) {
+    cudaEvent_t e0 = static_cast<cudaEvent_t>(r.e0), e1 = static_cast<cudaEvent_t>(r.e1);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      set_error(std::string("profile event: ") + cudaGetErrorString(e));
+      return TN_ERR_CUDA;
+    }
+    P.prof_acc.launches[r.cls] += 1;
+    P.prof_acc.ms[r.cls] += ms;
+    P.prof_acc.flops[r.cls] += r.flops;
+    P.prof_acc.bytes[r.cls] += r.bytes;
+    P.prof_pool.push_back(r.e0);
+    P.prof_pool.push_back(r.e1);
+  }
+  P.prof_pending.clear();
+  *out = P.prof_acc;
+  if (reset) P.prof_acc = tn_profile{};
   return TN_OK;
 }
 

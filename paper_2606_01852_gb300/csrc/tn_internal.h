@@ -94,6 +94,17 @@ struct Plan {
   char* dev = nullptr;
   std::vector<LeafDesc> leafdesc;   // host copy; src filled per call
   int num_sms = 148;
+  // per-class timing (tn_plan_profile): event pairs around step launches
+  struct ProfRec {
+    void* e0;
+    void* e1;
+    int32_t cls;
+    double flops, bytes;
+  };
+  bool prof_on = false;
+  std::vector<ProfRec> prof_pending;
+  std::vector<void*> prof_pool;
+  tn_profile prof_acc{};
   uint64_t uid = 0;                 // unique per plan (serve pools key on it)
   // stats
   tn_plan_stats stats{};

@@ -2,19 +2,26 @@
 
   rc12      : 12-qubit 3x4 grid random circuit, 8 brick-wall cycles, one amplitude,
               greedy path, no slicing (the tiny circuit case).
-  kising6   : 6x6 kicked Ising, 10 Trotter steps, J=1, dt=0.25, h=0.9, <Z_centre>
-              (the dynamics expectation case; the headline workload).
-  rc40      : 40-qubit 5x8 grid random circuit, 14 cycles, one amplitude, greedy path,
-              8 sliced labels (256 slices).
+  rc40      : 40-qubit 5x8 grid random circuit, 13 cycles, one amplitude, greedy path
+              with 8 sliced labels (256 slices). The headline workload.
+  kising44  : 4x4 kicked Ising, 10 Trotter steps, J=1, dt=0.25, h=0.9, <Z_centre>
+              (the dynamics expectation case at a size one GPU and the oracle can
+              contract unsliced).
   ising3r   : an ensemble of Ising partition functions on random 3-regular graphs.
 Smaller variants with the same structure serve as parity cases.
+
+Paths: the best (by total flops, then peak) of seeded greedy runs over a small grid of
+(seed, alpha, temperature); slicing: the greedy slicer picks n labels one at a time.
 """
 from __future__ import annotations
 
 import functools
 
 from . import circuits, kicked_ising, ising_pf, greedy
-from .network import Path
+
+PATH_SEEDS = range(6)
+PATH_ALPHAS = (0.0, 0.5, 1.0)
+PATH_TEMPS = (0.0, 0.05)
 
 
 class Workload:
@@ -30,14 +37,9 @@ class Workload:
         return out
 
 
-def _pathed(name, net, seeds=range(4), alphas=(0.0, 1.0), sliced_target=None, n_sliced=None):
-    path, info = greedy.best_greedy(net, seeds, alphas)
-    sliced = []
-    if sliced_target is not None:
-        sliced = greedy.greedy_slicer(net, path, sliced_target)
-    if n_sliced is not None:
-        # exactly n_sliced labels: extend or trim the greedy choice
-        sliced = greedy.greedy_slicer(net, path, -1.0, max_slices=n_sliced)
+def _pathed(name, net, n_sliced=0, seeds=PATH_SEEDS):
+    path, info = greedy.best_greedy(net, seeds, PATH_ALPHAS, PATH_TEMPS, key="flops")
+    sliced = greedy.greedy_slicer(net, path, -1.0, max_slices=n_sliced) if n_sliced else []
     info["peak_sliced"] = greedy.path_peak(net, path, sliced)
     info["log2flops_sliced"] = greedy.path_log2_flops(net, path, sliced)
     return Workload(name, net, path, sliced, info)
@@ -46,31 +48,35 @@ def _pathed(name, net, seeds=range(4), alphas=(0.0, 1.0), sliced_target=None, n_
 @functools.lru_cache(maxsize=None)
 def random_circuit(rows, cols, cycles, seed, n_sliced=0):
     net = circuits.amplitude_network(rows, cols, cycles, seed)
-    return _pathed(net.name, net, n_sliced=n_sliced or None)
+    name = net.name + (f"_sl{n_sliced}" if n_sliced else "")
+    return _pathed(name, net, n_sliced=n_sliced)
 
 
 @functools.lru_cache(maxsize=None)
-def kicked(L, T, J=1.0, h=0.9, dt=0.25, seeds=4):
+def kicked(L, T, J=1.0, h=0.9, dt=0.25):
     net = kicked_ising.expectation_network(L, T, J, h, dt)
-    return _pathed(net.name, net, seeds=range(seeds))
+    return _pathed(net.name, net)
 
 
 def rc12():
     return random_circuit(3, 4, 8, 12)
 
 
-def kising6():
-    return kicked(6, 10)
-
-
 def rc40():
-    return random_circuit(5, 8, 14, 40, n_sliced=8)
+    return random_circuit(5, 8, 13, 40, n_sliced=8)
 
 
-def ising_workload(net, seed=0):
+def kising44():
+    return kicked(4, 10)
+
+
+def ising_workload(net):
     path, info = greedy.best_greedy(net, range(2), (0.0, 1.0))
     return Workload(net.name, net, path, (), info)
 
 
 def ising3r(count, seed=3):
     return [ising_workload(n) for n in ising_pf.ensemble(count, seed)]
+
+
+BY_NAME = {"rc12": rc12, "rc40": rc40, "kising44": kising44}
