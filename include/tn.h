@@ -115,7 +115,23 @@ typedef struct {
   int32_t a_id, b_id;      /* SSA ids of the operands in the A (rows) and B (cols) roles */
   int32_t cls;             /* tn_step_class */
   int32_t batched;         /* 1 if the step depends on a sliced label */
+  /* Output placement: row index r (mixed radix over row_ext, last fastest) lands at
+   * sum_d digit_d * row_stride[d] elements, columns likewise; C[r, c] is stored at
+   * rows(r) + cols(c) of the output's planned layout. */
+  int32_t n_row_dims, n_col_dims;
+  int64_t row_ext[12], row_stride[12], col_ext[12], col_stride[12];
 } tn_step_info;
+
+/* Where a tensor lives in the plan's workspace (introspection). */
+typedef struct {
+  int64_t size;            /* elements of one slice copy (sliced labels removed) */
+  int64_t offset;          /* byte offset from the workspace base */
+  int64_t bytes;           /* bytes reserved, all batch copies */
+  int32_t batched;         /* one copy per slice of a pass (else one copy) */
+  int32_t pinned;          /* made in the first pass, kept for every pass */
+  int32_t producer;        /* step index, -1 for a leaf */
+  int32_t consumer;        /* step index, -1 for the root */
+} tn_tensor_info;
 
 /* Build a plan: validate, analyse each step (Sec. II-B), run the backward mode
  * reordering pass (Sec. IV-A), choose a kernel per step, assign every tensor a
@@ -136,6 +152,11 @@ tn_status tn_plan_layout(tn_plan_t plan, int32_t id, int32_t* modes_out, int32_t
 
 /* Description of step s (host only). */
 tn_status tn_plan_step(tn_plan_t plan, int32_t s, tn_step_info* out);
+
+/* Workspace placement of tensor `id` (SSA id) for the plan's slice batch (host only).
+ * Complex tensors are planar: copy b of a batched tensor holds its real plane at
+ * offset + 8*b*size bytes and its imaginary plane right after (size floats later). */
+tn_status tn_plan_tensor(tn_plan_t plan, int32_t id, tn_tensor_info* out);
 
 /* Contract all slices. inputs[t] is a DEVICE pointer to leaf t in its declared mode
  * order (complex64 or float32, per the plan's precision). output is a DEVICE pointer

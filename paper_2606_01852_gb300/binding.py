@@ -60,7 +60,16 @@ class tn_plan_stats(C.Structure):
 
 class tn_step_info(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("k", C.c_int64), ("a_id", C.c_int32),
-                ("b_id", C.c_int32), ("cls", C.c_int32), ("batched", C.c_int32)]
+                ("b_id", C.c_int32), ("cls", C.c_int32), ("batched", C.c_int32),
+                ("n_row_dims", C.c_int32), ("n_col_dims", C.c_int32),
+                ("row_ext", C.c_int64 * 12), ("row_stride", C.c_int64 * 12),
+                ("col_ext", C.c_int64 * 12), ("col_stride", C.c_int64 * 12)]
+
+
+class tn_tensor_info(C.Structure):
+    _fields_ = [("size", C.c_int64), ("offset", C.c_int64), ("bytes", C.c_int64),
+                ("batched", C.c_int32), ("pinned", C.c_int32), ("producer", C.c_int32),
+                ("consumer", C.c_int32)]
 
 
 class tn_profile(C.Structure):
@@ -85,6 +94,7 @@ def _load():
         "tn_plan_info": [vp, C.POINTER(tn_plan_stats)],
         "tn_plan_layout": [vp, i32, C.POINTER(i32), C.POINTER(i32)],
         "tn_plan_step": [vp, i32, C.POINTER(tn_step_info)],
+        "tn_plan_tensor": [vp, i32, C.POINTER(tn_tensor_info)],
         "tn_contract": [vp, C.POINTER(vp), vp, vp, vp],
         "tn_contract_slices": [vp, C.POINTER(vp), i64, i64, vp, vp, vp],
         "tn_contract_host": [vp, C.POINTER(vp), vp, vp, vp],
@@ -203,7 +213,15 @@ class Plan:
     def step(self, s: int) -> dict:
         i = tn_step_info()
         check(lib.tn_plan_step(self.handle, s, C.byref(i)))
-        return {f: getattr(i, f) for f, _ in tn_step_info._fields_}
+        d = {f: getattr(i, f) for f, _ in tn_step_info._fields_[:7]}
+        d["rows"] = [(i.row_ext[x], i.row_stride[x]) for x in range(i.n_row_dims)]
+        d["cols"] = [(i.col_ext[x], i.col_stride[x]) for x in range(i.n_col_dims)]
+        return d
+
+    def tensor(self, tid: int) -> dict:
+        i = tn_tensor_info()
+        check(lib.tn_plan_tensor(self.handle, tid, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in tn_tensor_info._fields_}
 
     # -- execution
     def _inputs(self, inputs):

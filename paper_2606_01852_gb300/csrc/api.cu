@@ -69,6 +69,22 @@ void* take_event(Plan& P) {
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+// After the stream has been synchronized: a kernel whose bounded wait expired left a
+// nonzero code in the plan's error word.
+tn_status check_device_error(Plan& P) {
+  int code = 0;
+  cudaError_t e = cudaMemcpy(&code, P.dev + P.off_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_error(std::string("reading the device error word: ") + cudaGetErrorString(e));
+    return TN_ERR_CUDA;
+  }
+  if (code != 0) {
+    set_error("a tensor-core kernel gave up a bounded wait (code " + std::to_string(code) + ")");
+    return TN_ERR_TIMEOUT;
+  }
+  return TN_OK;
+}
+
 tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t count, void* output,
                      double* log_scale, void* stream, std::string& err) {
   if (!P.dev) {
@@ -109,6 +125,8 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
   const LeafDesc* descs = reinterpret_cast<const LeafDesc*>(P.dev + P.off_leafdesc);
   double* acc = reinterpret_cast<double*>(P.dev + P.off_acc);
   int64_t* ref = reinterpret_cast<int64_t*>(P.dev + P.off_ref);
+  int* errw = reinterpret_cast<int*>(P.dev + P.off_err);
+  TN_CUDA_TRY(cudaMemsetAsync(errw, 0, sizeof(int), st));
   const int64_t npass = (count + P.batch - 1) / P.batch;
   for (int64_t p = 0; p < npass; ++p) {
     const int32_t nb = (int32_t)std::min<int64_t>(P.batch, count - p * P.batch);
@@ -139,7 +157,7 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
         TN_CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(pr.e0), st));
       }
       if (sr.cls == TN_CLASS_TC) {
-        TN_CUDA_TRY(launch_contract_tc(a, nbs, P.policy.prec, cplx, st));
+        TN_CUDA_TRY(launch_contract_tc(a, nbs, P.policy.prec, cplx, errw, st));
       } else if (sr.cls == TN_CLASS_STREAM) {
         launch_contract_stream(a, nbs, cplx, P.num_sms, st);
       } else {
@@ -281,6 +299,30 @@ tn_status tn_plan_step(tn_plan_t plan, int32_t s, tn_step_info* out) {
   out->b_id = st.b;
   out->cls = st.cls;
   out->batched = st.batched ? 1 : 0;
+  out->n_row_dims = st.rows.n;
+  out->n_col_dims = st.cols.n;
+  for (int d = 0; d < 12; ++d) {
+    out->row_ext[d] = d < st.rows.n ? st.rows.ext[d] : 0;
+    out->row_stride[d] = d < st.rows.n ? st.rows.stride[d] : 0;
+    out->col_ext[d] = d < st.cols.n ? st.cols.ext[d] : 0;
+    out->col_stride[d] = d < st.cols.n ? st.cols.stride[d] : 0;
+  }
+  return TN_OK;
+}
+
+tn_status tn_plan_tensor(tn_plan_t plan, int32_t id, tn_tensor_info* out) {
+  if (!plan || !out || id < 0 || id >= (int32_t)plan->P.tensors.size()) {
+    set_error("bad plan or tensor id");
+    return TN_ERR_INVALID;
+  }
+  const TensorRec& R = plan->P.tensors[id];
+  out->size = R.size;
+  out->offset = R.offset;
+  out->bytes = R.bytes;
+  out->batched = R.batched ? 1 : 0;
+  out->pinned = R.pinned ? 1 : 0;
+  out->producer = R.producer;
+  out->consumer = R.consumer;
   return TN_OK;
 }
 
@@ -352,7 +394,7 @@ tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void*
   }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(e, "stream synchronize");
-  return TN_OK;
+  return check_device_error(P);
 }
 
 tn_status tn_plan_destroy(tn_plan_t plan) {
@@ -399,6 +441,8 @@ tn_status tn_plan_profile_read(tn_plan_t plan, tn_profile* out, int32_t reset) {
     P.prof_pool.push_back(r.e1);
   }
   P.prof_pending.clear();
+  tn_status ds = check_device_error(P);
+  if (ds != TN_OK) return ds;
   *out = P.prof_acc;
   if (reset) P.prof_acc = tn_profile{};
   return TN_OK;

@@ -1,9 +1,404 @@
-// Tensor-core (tcgen05) path: not built yet.
+// Tensor-core path for the dense pairwise steps (sm_103a): planar complex GEMM
+//   C[b] = A[b] (m x k) . B[b] (n x k)^T      (complex, 4M real decomposition)
+// with both operands K-major, written through the separable row/column offset maps.
+//
+// One CTA computes a 128 x 128 output tile. Warp roles (192 threads):
+//   warp 0      : TMA producer -- A_re, A_im, B_re, B_im tiles (128 x 32 fp32, 128-byte
+//                 swizzle) into a ring of shared-memory stages, mbarrier tx-count signalled;
+//   warp 1      : allocates tensor memory and issues tcgen05.mma (kind::tf32) from one lane;
+//   warps 2..5  : (3xTF32 only) split each staged tile into hi = TF32-truncated value (in
+//                 place) and lo = value - hi (separate buffer); then the epilogue: tcgen05.ld of
+//                 the accumulators and the offset-mapped stores.
+// Accumulators in TMEM (fp32): D_rr = sum A_re B_re, D_ii = sum A_im B_im,
+// D_x = sum (A_re B_im + A_im B_re); Re C = D_rr - D_ii, Im C = D_x.
+// 3xTF32: a.b ~ ah.bh + al.bh + ah.bl (the al.bl term, ~2^-22 relative, is dropped).
+// Every mbarrier wait is bounded by wall time; on expiry the CTA records an error code,
+// drains its copies, frees its tensor memory and returns.
+#include <cstdint>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
 #include "kernels.h"
 
 namespace tn {
-bool tc_supported() { return false; }
-cudaError_t launch_contract_tc(const StepArgs&, int32_t, int32_t, bool, cudaStream_t) {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32;                 // BK fp32 = one 128-byte row
+constexpr int TILE_A = BM * BK * 4;                         // 16 KiB
+constexpr int TILE_B = BN * BK * 4;                         // 16 KiB
+constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;        // 64 KiB: A_re A_im B_re B_im
+constexpr int NTHREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;                         // D_rr @0, D_ii @128, D_x @256
+constexpr int GROUP_M = 16;                                 // raster: tiles grouped along M
+constexpr uint64_t kWaitNs = 4000000000ull;                 // 4 s bound on any wait
+
+template <int SPLIT>
+struct Cfg {
+  static constexpr int STAGES = SPLIT == 1 ? 3 : 2;
+  static constexpr int LO = SPLIT == 1 ? 0 : 1;
+  static constexpr int SMEM = (STAGES + LO) * STAGE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of parity `parity` to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  if (mbar_test(b, parity)) return true;
+  const uint64_t t0 = gtime();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_test(b, parity)) return true;
+    if (gtime() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte swizzle,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFF) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused here)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;            // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+#define TN_R8(i) "=r"(r[i + 0]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), "=r"(r[i + 4]), \
+                 "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : TN_R8(0), TN_R8(8), TN_R8(16), TN_R8(24)
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+#undef TN_R8
+
+__device__ __forceinline__ int64_t map_off(const OffsetMap& om, int64_t idx) {
+  int64_t off = 0;
+  for (int d = om.n - 1; d >= 0; --d) {
+    const uint32_t e = om.ext[d];
+    off += (idx % e) * om.stride[d];
+    idx /= e;
+  }
+  return off;
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    contract_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                       StepArgs a, int* err) {
+  constexpr int STAGES = Cfg<SPLIT>::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* lo_base = smem + STAGES * STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(lo_base + Cfg<SPLIT>::LO * STAGE_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* conv_full = bars + 2 * STAGES;
+  uint64_t* lo_empty = conv_full + 1;
+  uint64_t* acc_full = lo_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // grouped raster over output tiles for L2 reuse of A and B tiles
+  const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
+  const int64_t t = blockIdx.x;
+  const int64_t per_group = GROUP_M * tiles_n;
+  const int64_t first_m = (t / per_group) * GROUP_M;
+  const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
+  const int64_t tm = first_m + (t % per_group) % gm, tn = (t % per_group) / gm;
+  const int m0 = static_cast<int>(tm * BM), n0 = static_cast<int>(tn * BN);
+  const int b = blockIdx.y;
+  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);
+  const int pa = a.a_bstride ? 2 * b : 0, pb = a.b_bstride ? 2 * b : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(conv_full, 128);
+    mbar_init(lo_empty, 1);
+    mbar_init(acc_full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1)) {
+          atomicExch(err, 1);
+          break;
+        }
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const int k0 = kb * BK;
+        tma_load_3d(st, &tmA, &full[s], k0, m0, pa);
+        tma_load_3d(st + TILE_A, &tmA, &full[s], k0, m0, pa + 1);
+        tma_load_3d(st + 2 * TILE_A, &tmB, &full[s], k0, n0, pb);
+        tma_load_3d(st + 2 * TILE_A + TILE_B, &tmB, &full[s], k0, n0, pb + 1);
+        issued = kb + 1;
+      }
+      // drain: every stage's last issued load has landed before the CTA can exit
+      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+        if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) atomicExch(err, 2);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(BM, BN);
+      const uint32_t d_rr = tmem, d_ii = tmem + 128, d_x = tmem + 256;
+      bool ok = true;
+      for (int kb = 0; kb < num_kb && ok; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(&full[s], ph)) {
+          atomicExch(err, 3);
+          ok = false;
+          break;
+        }
+        if (SPLIT == 3 && !mbar_wait(conv_full, kb & 1)) {
+          atomicExch(err, 4);
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t st = su32(smem + s * STAGE_BYTES);
+        const uint32_t lo = su32(lo_base);
+#pragma unroll
+        for (int j = 0; j < BK / 8; ++j) {
+          const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
+          const uint64_t ar = sw128_desc(st + j * 32), ai = sw128_desc(st + TILE_A + j * 32);
+          const uint64_t br = sw128_desc(st + 2 * TILE_A + j * 32);
+          const uint64_t bi = sw128_desc(st + 2 * TILE_A + TILE_B + j * 32);
+          mma_tf32(d_rr, ar, br, idesc, acc);
+          mma_tf32(d_ii, ai, bi, idesc, acc);
+          mma_tf32(d_x, ar, bi, idesc, acc);
+          mma_tf32(d_x, ai, br, idesc, 1u);
+          if (SPLIT == 3) {
+            const uint64_t arl = sw128_desc(lo + j * 32), ail = sw128_desc(lo + TILE_A + j * 32);
+            const uint64_t brl = sw128_desc(lo + 2 * TILE_A + j * 32);
+            const uint64_t bil = sw128_desc(lo + 2 * TILE_A + TILE_B + j * 32);
+            mma_tf32(d_rr, arl, br, idesc, 1u);
+            mma_tf32(d_rr, ar, brl, idesc, 1u);
+            mma_tf32(d_ii, ail, bi, idesc, 1u);
+            mma_tf32(d_ii, ai, bil, idesc, 1u);
+            mma_tf32(d_x, arl, bi, idesc, 1u);
+            mma_tf32(d_x, ar, bil, idesc, 1u);
+            mma_tf32(d_x, ail, br, idesc, 1u);
+            mma_tf32(d_x, ai, brl, idesc, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+        if (SPLIT == 3) mma_commit(lo_empty);
+      }
+      mma_commit(acc_full);  // also on error: lets the epilogue see in-flight MMAs retire
+    }
+  } else {
+    const int et = threadIdx.x - 64;  // 0..127
+    if (SPLIT == 3) {
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(lo_empty, (kb & 1) ^ 1)) {
+          atomicExch(err, 5);
+          break;
+        }
+        float4* src = reinterpret_cast<float4*>(smem + s * STAGE_BYTES);
+        float4* dst = reinterpret_cast<float4*>(lo_base);
+        for (int i = et; i < STAGE_BYTES / 16; i += 128) {
+          float4 v = src[i], h, l;
+          h.x = __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
+          h.y = __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
+          h.z = __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
+          h.w = __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
+          l.x = v.x - h.x;
+          l.y = v.y - h.y;
+          l.z = v.z - h.z;
+          l.w = v.w - h.w;
+          src[i] = h;
+          dst[i] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(conv_full);
+      }
+    }
+    // epilogue: TMEM lane quarter of this warp = warp % 4
+    const bool ok = mbar_wait(acc_full, 0);
+    if (!ok) atomicExch(err, 6);
+    fence_after();
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int64_t m = static_cast<int64_t>(m0) + row;
+    const bool row_ok = ok && m < a.m;
+    const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
+    float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
+    const int last = a.cols.n - 1;
+    const bool fast = last >= 0 && (a.cols.ext[last] % 32u) == 0u;
+    const int64_t sl = last >= 0 ? a.cols.stride[last] : 0;
+    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    for (int c = 0; c < BN / 32; ++c) {
+      float rr[32], ii[32], xx[32];
+      tmem_ld32(tmem + lane_base + c * 32, rr);
+      tmem_ld32(tmem + lane_base + 128 + c * 32, ii);
+      tmem_ld32(tmem + lane_base + 256 + c * 32, xx);
+      if (!row_ok) continue;
+      const int64_t nb0 = static_cast<int64_t>(n0) + c * 32;
+      const int64_t co0 = (fast && nb0 < a.n) ? map_off(a.cols, nb0) : 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t n = nb0 + j;
+        if (n >= a.n) break;
+        const int64_t off = ro + (fast ? co0 + j * sl : map_off(a.cols, n));
+        C[off] = rr[j] - ii[j];
+        C[a.c_plane + off] = xx[j];
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3-D map over one operand: (k, rows, plane), plane = 2*batch + {re, im}.
+bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t k, int64_t planes, int64_t plane_elems,
+              int box_rows) {
+  auto enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows),
+                        static_cast<cuuint64_t>(planes)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(k * 4), static_cast<cuuint64_t>(plane_elems * 4)};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int SPLIT>
+cudaError_t launch_split(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<SPLIT>::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  CUtensorMap ta, tb;
+  const int64_t pa = a.a_bstride ? 2 * static_cast<int64_t>(nb) : 2;
+  const int64_t pb = a.b_bstride ? 2 * static_cast<int64_t>(nb) : 2;
+  if (!make_map(&ta, a.A, a.m, a.k, pa, a.a_plane, BM) || !make_map(&tb, a.B, a.n, a.k, pb, a.b_plane, BN))
+    return cudaErrorInvalidValue;
+  const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
+  dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));
+  contract_tc_kernel<SPLIT><<<grid, NTHREADS, Cfg<SPLIT>::SMEM, st>>>(ta, tb, a, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_supported() { return true; }
+
+bool tc_step_ok(int64_t m, int64_t n, int64_t k) {
+  return m >= BM && n >= 64 && k >= 16 && k % 4 == 0 && k <= (int64_t(1) << 30) && m < (int64_t(1) << 31) &&
+         n < (int64_t(1) << 31);
+}
+
+cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
+                               cudaStream_t st) {
+  if (!cplx || a.recs) return cudaErrorNotSupported;
+  if (prec == TN_C64_TF32) return launch_split<1>(a, nb, err, st);
+  if (prec == TN_C64_3XTF32) return launch_split<3>(a, nb, err, st);
   return cudaErrorNotSupported;
 }
+
 }  // namespace tn

@@ -23,6 +23,8 @@ inline int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 constexpr double kHbm = 6.6e12;
 constexpr double kSimtFlops = 45e12;
 
+bool tc_prec_built(int32_t p) { return p == TN_C64_TF32 || p == TN_C64_3XTF32; }
+
 bool is_tc_prec(int32_t p) {
   return p == TN_C64_TF32 || p == TN_C64_3XTF32 || p == TN_C64_BF16X3 || p == TN_R32_TF32 ||
          p == TN_R32_3XTF32 || p == TN_R32_BF16X3;
@@ -318,6 +320,15 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
       std::swap(st.M, st.N);
       std::swap(st.m, st.n);
     }
+    // The tensor-core kernel tiles 128 rows: give the row role to the operand that
+    // fills them when only one orientation qualifies.
+    const bool tc_form_here = tc_form && P.is_complex && !pol.exp_scaling && tc_prec_built(pol.prec) &&
+                              tc_supported();
+    if (tc_form_here && !tc_step_ok(st.m, st.n, st.k) && tc_step_ok(st.n, st.m, st.k)) {
+      std::swap(st.a, st.b);
+      std::swap(st.M, st.N);
+      std::swap(st.m, st.n);
+    }
     if (!build_offset_map(st.M, O, P.extent, st.rows) ||
         !build_offset_map(st.N, O, P.extent, st.cols)) {
       err = "output interleaving too fine for the offset maps";
@@ -327,11 +338,7 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     const double bytes = eb * (double(st.m) * st.k + double(st.n) * st.k + double(st.m) * st.n);
     const double t_simt = std::max(bytes / kHbm, flops / kSimtFlops);
     st.cls = TN_CLASS_SIMT;
-    // The tensor-core kernel needs full 128-row tiles of A, K-rows that are whole
-    // 32-byte TMA/MMA atoms, and enough columns to fill its N tile.
-    const bool tc_ok = tc_form && tc_supported() && st.m >= 128 && st.n >= 32 && st.k >= 8 && st.k % 8 == 0 &&
-                       (st.m % 128 == 0) && (st.n % 16 == 0);
-    if (tc_ok) {
+    if (tc_form_here && tc_step_ok(st.m, st.n, st.k)) {
       const double t_tc = std::max(bytes / kHbm, flops / tc_flops(pol.prec));
       if (t_tc < t_simt) st.cls = TN_CLASS_TC;
     }
@@ -426,9 +433,12 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
 }
 
 // Liveness: a leaf is born when the pass stages it (event -1) and a step output at its
-// step; each dies at its consuming step (the root after the final accumulation); a
-// pinned tensor lives for the whole call. Two tensors share memory only if their
-// lifetimes are disjoint. Offsets are static, so every pass uses the same layout.
+// step; each dies at its consuming step (the root after the final accumulation). Two
+// tensors share memory only if their lifetimes are disjoint. Offsets are static, so
+// every pass replays the same layout -- which is why a pinned tensor (made once in the
+// first pass, read by every pass) is reserved over the whole timeline [-1, inf]: a
+// tensor that dies before the pinned one is made in the first pass is made again in
+// later passes, and must not land on it.
 void assign_workspace(Plan& P, int64_t batch) {
   P.batch = batch;
   const int32_t T = P.n_leaves, S = (int32_t)P.steps.size();
@@ -440,7 +450,10 @@ void assign_workspace(Plan& P, int64_t batch) {
     TensorRec& R = P.tensors[t];
     birth[t] = t < T ? -1 : R.producer;
     death[t] = R.consumer < 0 ? S : R.consumer;
-    if (R.pinned) death[t] = kInf;
+    if (R.pinned) {
+      birth[t] = -1;
+      death[t] = kInf;
+    }
     R.bytes = align_up(std::max<int64_t>(1, R.size) * eb * (R.batched ? batch : 1), kAlign);
   }
   std::vector<int32_t> order(N);
@@ -534,6 +547,8 @@ void assign_workspace(Plan& P, int64_t batch) {
   P.off_recidx = cur;
   cur += align_up(int64_t(T) * 4, kAlign);
   P.off_ref = cur;
+  cur += kAlign;
+  P.off_err = cur;
   cur += kAlign;
   P.off_leafdesc = cur;
   cur += align_up(int64_t(T) * (int64_t)sizeof(LeafDesc), kAlign);

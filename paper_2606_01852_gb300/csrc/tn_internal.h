@@ -83,6 +83,7 @@ struct Plan {
   int64_t off_scale = 0;            // per tensor x batch: int32 emax, int32 pad, int64 log2
   int64_t off_recidx = 0;           // int32 record index of each leaf (device copy)
   int64_t off_ref = 0;              // int64 reference exponent of the accumulator
+  int64_t off_err = 0;              // int error word set by kernels whose bounded waits expire
   std::vector<int32_t> rec_index;   // per tensor: first scale record
   int64_t n_rec_unbatched = 0, n_rec_total = 0;
   int64_t off_leafdesc = 0;         // LeafDesc table
@@ -121,9 +122,12 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
                      void* output, double* log_scale, void* stream, std::string& err);
 
 void set_error(const std::string& msg);
+tn_status check_device_error(Plan& P);
 
 // true when the tcgen05 kernels are compiled in
 bool tc_supported();
+// the tensor-core kernel's shape limits for a step (rows m, columns n, depth k)
+bool tc_step_ok(int64_t m, int64_t n, int64_t k);
 
 inline int64_t elem_bytes(const Plan& P) { return P.is_complex ? 8 : 4; }
 

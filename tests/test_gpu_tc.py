@@ -1,0 +1,133 @@
+"""GPU parity of the tensor-core (tcgen05) GEMM path against the CPU oracle.
+
+Tolerances, derived from the arithmetic of each form:
+  * TF32: operands keep 10 explicit mantissa bits (truncated), u_tf32 = 2^-10 ~ 1e-3
+    relative per product; FP32 accumulation adds little. A single GEMM step is then
+    within ~1e-3 relative (Frobenius), and a path of several TF32 steps within a few
+    1e-3: tested at 5e-3 per step and 3e-2 along a path.
+  * 3xTF32: hi + lo carry 21 bits; the dropped lo*lo term and lo's own truncation are
+    ~2^-20 relative per product, below FP32 accumulation error: held to the FP32 bar,
+    1e-5 (relative), the bar the method is held to.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests._lib import ensure_built
+from tests.test_gpu_parity import rel_err, run
+from tn_inputs import workloads
+from tn_inputs.network import Network, Path
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tn():
+    return ensure_built()
+
+
+def gemm_network(dims_m, dims_n, dims_k, out_order, seed=0, sliced_dim=None, vec_slice=None):
+    """A[m..., k...] x B[n..., k...] with the open result in `out_order` (labels)."""
+    rng = np.random.default_rng(seed)
+    ext = {}
+    lab = 0
+    M, N, K = [], [], []
+    for grp, dims in ((M, dims_m), (N, dims_n), (K, dims_k)):
+        for d in dims:
+            ext[lab] = d
+            grp.append(lab)
+            lab += 1
+    tensors, modes = [], []
+    am = tuple(M + K)
+    bm = tuple(N + K)
+    if sliced_dim is not None:      # a closed label on both operands, sliced
+        ext[lab] = sliced_dim
+        am = (lab,) + am
+        bm = (lab,) + bm
+        lab += 1
+    if vec_slice is not None:       # a label joining A to a vector only (A batched, B not)
+        ext[lab] = vec_slice
+        am = am + (lab,)
+        v = rng.standard_normal(vec_slice) + 1j * rng.standard_normal(vec_slice)
+        vlab = lab
+        lab += 1
+    shp = lambda ms: tuple(ext[x] for x in ms)
+    A = rng.standard_normal(shp(am)) + 1j * rng.standard_normal(shp(am))
+    B = rng.standard_normal(shp(bm)) + 1j * rng.standard_normal(shp(bm))
+    tensors = [A, B]
+    modes = [am, bm]
+    open_ = tuple(M[i] if kind == "m" else N[i] for kind, i in out_order)
+    if vec_slice is not None:
+        tensors.append(v)
+        modes.append((vlab,))
+        path = Path([(0, 2), (3, 1)])
+    else:
+        path = Path([(0, 1)])
+    net = Network(tensors, modes, ext, open_)
+    net.check()
+    sliced = [lab - 1] if (sliced_dim is not None or vec_slice is not None) else []
+    return net, path, sliced
+
+
+CASES = [
+    # (m dims, n dims, k dims, output interleaving)
+    ((2, 64), (2, 64), (64,), [("m", 0), ("m", 1), ("n", 0), ("n", 1)]),         # full tiles
+    ((5, 40), (3, 50), (72,), [("m", 0), ("n", 0), ("m", 1), ("n", 1)]),         # ragged m, n, k tails
+    ((128,), (2, 2, 32), (8, 4), [("n", 0), ("m", 0), ("n", 1), ("n", 2)]),      # interleaved columns
+    ((256,), (96,), (16,), [("n", 0), ("m", 0)]),                                 # rows land strided
+]
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32", 5e-3), ("3xtf32", 1e-5)])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_single_gemm_step(tn, prec, tol, case):
+    dm, dn, dk, order = CASES[case]
+    net, path, sliced = gemm_network(dm, dn, dk, order, seed=case)
+    plan = tn.Plan(net, path, prec=prec)
+    assert plan.step(0)["cls"] == tn.TN_CLASS_TC
+    got, _ = run(tn, plan, net)
+    assert rel_err(got, oracle.contract(net, path)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32", 5e-3), ("3xtf32", 1e-5)])
+def test_batched_both_operands(tn, prec, tol):
+    """A sliced label on both operands: the batch runs as TMA planes of both maps."""
+    net, path, sliced = gemm_network((2, 64), (160,), (32,), [("m", 1), ("n", 0), ("m", 0)], seed=7,
+                                     sliced_dim=3)
+    plan = tn.Plan(net, path, sliced, prec=prec)
+    assert plan.step(0)["cls"] == tn.TN_CLASS_TC and plan.step(0)["batched"] == 1
+    got, _ = run(tn, plan, net)
+    want, parts = oracle.contract_slices(net, path, sliced, return_partials=True)
+    assert rel_err(got, want) < tol
+    g1, _ = run(tn, plan, net, begin=1, count=1)
+    assert rel_err(g1, parts[1]) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32", 5e-3), ("3xtf32", 1e-5)])
+def test_batched_row_operand_only(tn, prec, tol):
+    """Only the row operand depends on the slice (the column operand is shared)."""
+    net, path, sliced = gemm_network((192,), (128,), (64,), [("m", 0), ("n", 0)], seed=8, vec_slice=4)
+    plan = tn.Plan(net, path, sliced, prec=prec, max_slice_batch=3)
+    st = plan.step(1)
+    assert st["cls"] == tn.TN_CLASS_TC and st["batched"] == 1
+    got, _ = run(tn, plan, net)
+    assert rel_err(got, oracle.contract(net, path, sliced)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32", 3e-2), ("3xtf32", 1e-5)])
+def test_circuit_path_with_tc_steps(tn, prec, tol):
+    w = workloads.random_circuit(4, 5, 12, 40)
+    plan = tn.Plan(w.net, w.path, prec=prec)
+    n_tc = sum(1 for s in range(len(w.path.pairs)) if plan.step(s)["cls"] == tn.TN_CLASS_TC)
+    assert n_tc >= 1
+    got, _ = run(tn, plan, w.net)
+    assert rel_err(got, oracle.contract(w.net, w.path)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32", 3e-2), ("3xtf32", 1e-5)])
+def test_sliced_circuit_with_tc_steps(tn, prec, tol):
+    w = workloads.random_circuit(4, 5, 12, 40, n_sliced=3)
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=4)
+    got, _ = run(tn, plan, w.net)
+    assert rel_err(got, oracle.contract(w.net, w.path, w.sliced)) < tol
