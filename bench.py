@@ -205,11 +205,18 @@ def run_ours(args):
     result = complex(out.cpu())
 
     # dominant kernel class by device time, and its roofline
-    cls = max(range(3), key=lambda c: prof["ms"][c])
-    names = {0: "contract_simt", 1: "contract_stream", 2: "contract_tc"}
+    cls = max(range(4), key=lambda c: prof["ms"][c])
+    names = dict(enumerate(tn.binding.CLASS_NAMES))
     launches = prof["launches"][cls]
     per_launch_ms = prof["ms"][cls] / max(1, launches)
-    if cls == 1:
+    step_ms = plan.profile_steps()
+    top = sorted(range(len(step_ms)), key=lambda s: -step_ms[s])[:8]
+    top_steps = []
+    for s in top:
+        st = plan.step(s)
+        top_steps.append({"step": s, "kernel": names[st["cls"]], "m": st["m"], "n": st["n"], "k": st["k"],
+                          "ms_per_step": step_ms[s] / args.steps})
+    if cls in (1, 3):
         achieved = prof["bytes"][cls] / (prof["ms"][cls] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     elif cls == 2:
@@ -257,7 +264,8 @@ def run_ours(args):
         "result": [result.real, result.imag],
         "roofline": roof,
         "per_class": {names[c]: {"launches": prof["launches"][c], "ms": prof["ms"][c],
-                                 "flops": prof["flops"][c], "bytes": prof["bytes"][c]} for c in range(3)},
+                                 "flops": prof["flops"][c], "bytes": prof["bytes"][c]} for c in range(4)},
+        "top_steps": top_steps,
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 24},
         "gpu_launches": plan.launches_per_call() * args.steps,
         "clocks": ck,

@@ -95,7 +95,13 @@ typedef struct {
 typedef struct tn_plan_s* tn_plan_t;
 
 /* Kernel class chosen for a step (Sec. IV-C cost model t = max(D_rw/B, FLOPs/F)). */
-typedef enum { TN_CLASS_SIMT = 0, TN_CLASS_STREAM = 1, TN_CLASS_TC = 2 } tn_step_class;
+typedef enum {
+  TN_CLASS_SIMT = 0,   /* tiled FP32 GEMM on the CUDA cores (any shape) */
+  TN_CLASS_STREAM = 1, /* big x small: one pass over the big operand */
+  TN_CLASS_TC = 2,     /* tcgen05 tensor-core GEMM */
+  TN_CLASS_SPLITK = 3  /* few outputs, long k: split-K partials in FP64, fixed-order sum */
+} tn_step_class;
+#define TN_N_CLASSES 4
 
 typedef struct {
   int64_t n_steps, n_leaves, n_slices, slice_batch, n_passes;
@@ -104,8 +110,8 @@ typedef struct {
   double Ct, Cm, Cs;       /* Sec. II-B Eqs. 1-3 for one slice (element counts) */
   int64_t peak_elems;      /* largest tensor of one slice, elements */
   int64_t workspace_bytes; /* device bytes the plan holds */
-  int64_t steps_per_class[3];
-  double flops_per_class[3];
+  int64_t steps_per_class[TN_N_CLASSES];
+  double flops_per_class[TN_N_CLASSES];
   int64_t leaf_permutes;   /* leaves whose planned order differs from the declared one
                               (permuted once while staging; no step permutes) */
 } tn_plan_stats;
@@ -190,10 +196,10 @@ tn_status tn_plan_destroy(tn_plan_t plan);
  * algorithmic flops (8mnk complex, 2mnk real) and bytes (e(mk+kn+mn), each operand
  * and the output counted once per batch entry that reads or writes it). */
 typedef struct {
-  int64_t launches[3];
-  double ms[3];
-  double flops[3];
-  double bytes[3];
+  int64_t launches[TN_N_CLASSES];
+  double ms[TN_N_CLASSES];
+  double flops[TN_N_CLASSES];
+  double bytes[TN_N_CLASSES];
 } tn_profile;
 
 /* enable != 0: later contract calls on this plan record events around every step
@@ -203,6 +209,10 @@ tn_status tn_plan_profile(tn_plan_t plan, int32_t enable);
 /* Wait for the recorded events and write the totals accumulated since the last reset
  * to *out; reset != 0 clears the totals after reading. */
 tn_status tn_plan_profile_read(tn_plan_t plan, tn_profile* out, int32_t reset);
+
+/* Device milliseconds per step accumulated by the same events (ms_out holds n_steps
+ * doubles), for the recordings folded in by tn_plan_profile_read since its last reset. */
+tn_status tn_plan_profile_steps(tn_plan_t plan, double* ms_out, int32_t n_steps);
 
 /* ---- serving: continuous batching of contraction requests ------------------------ */
 

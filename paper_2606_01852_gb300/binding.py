@@ -24,7 +24,8 @@ TN_C64_FP32_SIMT, TN_C64_TF32, TN_C64_3XTF32, TN_C64_BF16X3, TN_R32_FP32_SIMT, T
     TN_R32_3XTF32, TN_R32_BF16X3 = range(8)
 PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
 TN_PLAN_HOST_ONLY = 1
-TN_CLASS_SIMT, TN_CLASS_STREAM, TN_CLASS_TC = range(3)
+TN_CLASS_SIMT, TN_CLASS_STREAM, TN_CLASS_TC, TN_CLASS_SPLITK = range(4)
+CLASS_NAMES = ["contract_simt", "contract_stream", "contract_tc", "contract_splitk"]
 
 
 class TnError(RuntimeError):
@@ -54,7 +55,7 @@ class tn_plan_stats(C.Structure):
                 ("slice_batch", C.c_int64), ("n_passes", C.c_int64), ("flops", C.c_double),
                 ("bytes", C.c_double), ("Ct", C.c_double), ("Cm", C.c_double), ("Cs", C.c_double),
                 ("peak_elems", C.c_int64), ("workspace_bytes", C.c_int64),
-                ("steps_per_class", C.c_int64 * 3), ("flops_per_class", C.c_double * 3),
+                ("steps_per_class", C.c_int64 * 4), ("flops_per_class", C.c_double * 4),
                 ("leaf_permutes", C.c_int64)]
 
 
@@ -73,8 +74,8 @@ class tn_tensor_info(C.Structure):
 
 
 class tn_profile(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 3), ("ms", C.c_double * 3), ("flops", C.c_double * 3),
-                ("bytes", C.c_double * 3)]
+    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4), ("flops", C.c_double * 4),
+                ("bytes", C.c_double * 4)]
 
 
 class tn_serve_config(C.Structure):
@@ -101,6 +102,7 @@ def _load():
         "tn_plan_destroy": [vp],
         "tn_plan_profile": [vp, i32],
         "tn_plan_profile_read": [vp, C.POINTER(tn_profile), i32],
+        "tn_plan_profile_steps": [vp, C.POINTER(C.c_double), i32],
         "tn_serve_create": [C.POINTER(tn_serve_config), C.POINTER(vp)],
         "tn_serve_submit": [vp, vp, C.POINTER(vp), C.POINTER(u64)],
         "tn_serve_poll": [vp, u64, vp, vp, i32],
@@ -250,6 +252,13 @@ class Plan:
         check(lib.tn_plan_profile_read(self.handle, C.byref(p), 1 if reset else 0))
         return {f: list(getattr(p, f)) for f, _ in tn_profile._fields_}
 
+    def profile_steps(self):
+        """Per-step device milliseconds of the last profile_read(reset=True)."""
+        n = self.info()["n_steps"]
+        buf = (C.c_double * max(1, n))()
+        check(lib.tn_plan_profile_steps(self.handle, buf, n))
+        return list(buf[:n])
+
     def launches_per_call(self, count=None) -> int:
         """Kernel launches of one contract over `count` slices (default all)."""
         info = self.info()
@@ -257,9 +266,11 @@ class Plan:
         b = info["slice_batch"]
         passes = (count + b - 1) // b
         S = info["n_steps"]
-        batched = sum(1 for s in range(S) if self.step(s)["batched"])
+        steps = [self.step(s) for s in range(S)]
+        per = [2 if st["cls"] == TN_CLASS_SPLITK else 1 for st in steps]
+        batched = sum(p for p, st in zip(per, steps) if st["batched"])
         # per pass: staging + steps + root accumulation; once: the output write
-        return passes * 2 + S + (passes - 1) * batched + 1
+        return passes * 2 + sum(per) + (passes - 1) * batched + 1
 
     def destroy(self):
         if getattr(self, "handle", None):

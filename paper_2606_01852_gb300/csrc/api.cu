@@ -150,6 +150,7 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
         pr.e0 = take_event(P);
         pr.e1 = take_event(P);
         pr.cls = sr.cls;
+        pr.step = s;
         const double eb = cplx ? 8.0 : 4.0;
         const double m = double(sr.m), n = double(sr.n), k = double(sr.k);
         pr.flops = (cplx ? 8.0 : 2.0) * m * n * k * nbs;
@@ -160,6 +161,8 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
         TN_CUDA_TRY(launch_contract_tc(a, nbs, P.policy.prec, cplx, errw, st));
       } else if (sr.cls == TN_CLASS_STREAM) {
         launch_contract_stream(a, nbs, cplx, P.num_sms, st);
+      } else if (sr.cls == TN_CLASS_SPLITK) {
+        launch_contract_splitk(a, nbs, cplx, reinterpret_cast<double*>(P.dev + P.off_scratch), st);
       } else {
         launch_contract_simt(a, nbs, cplx, st);
       }
@@ -409,6 +412,21 @@ tn_status tn_plan_destroy(tn_plan_t plan) {
   return TN_OK;
 }
 
+tn_status tn_plan_profile_steps(tn_plan_t plan, double* ms_out, int32_t n_steps) {
+  if (!plan || !ms_out || n_steps != (int32_t)plan->P.steps.size()) {
+    set_error("bad plan, buffer or step count");
+    return TN_ERR_INVALID;
+  }
+  // totals of the last read with reset, else those accumulated since
+  const std::vector<double>& v =
+      plan->P.prof_step_ms.empty() || std::all_of(plan->P.prof_step_ms.begin(), plan->P.prof_step_ms.end(),
+                                                   [](double x) { return x == 0.0; })
+          ? plan->P.prof_last_step_ms
+          : plan->P.prof_step_ms;
+  for (int32_t s = 0; s < n_steps; ++s) ms_out[s] = s < (int32_t)v.size() ? v[s] : 0.0;
+  return TN_OK;
+}
+
 tn_status tn_plan_profile(tn_plan_t plan, int32_t enable) {
   if (!plan) {
     set_error("null plan");
@@ -434,6 +452,8 @@ tn_status tn_plan_profile_read(tn_plan_t plan, tn_profile* out, int32_t reset) {
       return TN_ERR_CUDA;
     }
     P.prof_acc.launches[r.cls] += 1;
+    if (P.prof_step_ms.size() != P.steps.size()) P.prof_step_ms.assign(P.steps.size(), 0.0);
+    P.prof_step_ms[r.step] += ms;
     P.prof_acc.ms[r.cls] += ms;
     P.prof_acc.flops[r.cls] += r.flops;
     P.prof_acc.bytes[r.cls] += r.bytes;
@@ -444,7 +464,11 @@ tn_status tn_plan_profile_read(tn_plan_t plan, tn_profile* out, int32_t reset) {
   tn_status ds = check_device_error(P);
   if (ds != TN_OK) return ds;
   *out = P.prof_acc;
-  if (reset) P.prof_acc = tn_profile{};
+  if (reset) {
+    P.prof_last_step_ms = P.prof_step_ms;
+    P.prof_acc = tn_profile{};
+    P.prof_step_ms.assign(P.steps.size(), 0.0);
+  }
   return TN_OK;
 }
 

@@ -40,6 +40,13 @@ void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int6
                          const int32_t* rec_index, cudaStream_t st);
 void launch_contract_simt(const StepArgs& a, int32_t nb, bool cplx, cudaStream_t st);
 void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, cudaStream_t st);
+
+// split-K steps: at most kSplitMaxOut outputs, k cut in chunks of kSplitChunk; scratch
+// holds nb * splitk_chunks(k) * m*n complex doubles
+constexpr int kSplitMaxOut = 16;
+constexpr int64_t kSplitChunk = 4096;
+int32_t splitk_chunks(int64_t k);
+void launch_contract_splitk(const StepArgs& a, int32_t nb, bool cplx, double* scratch, cudaStream_t st);
 void launch_accumulate_root(const float* root, int64_t size, int32_t nb, int64_t bstride,
                             int64_t plane, bool cplx, double* acc, const ScaleRec* recs,
                             int32_t rec_root, bool root_batched, int64_t* ref_exp, bool first,

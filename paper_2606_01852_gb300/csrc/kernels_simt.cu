@@ -392,4 +392,119 @@ void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* ou
   finalize_output_kernel<<<blocks, threads, 0, st>>>(acc, size, cplx ? 1 : 0, out, log_scale, ref_exp);
 }
 
+// ---------------------------------------------------------------------------------
+// split-K steps (m*n <= kSplitMaxOut outputs, very long k; e.g. the final scalar of a
+// closed network, a dot product of two large tensors). Pass 1: CTA (chunk, b) sums
+// its k-range for every output -- FP32 over the few terms each thread owns, FP64
+// across threads -- and writes one FP64 partial per output to scratch[b][chunk].
+// Pass 2: per (b, output), the partials are added in chunk order in FP64 and the
+// result stored through the offset maps. Deterministic: no atomics.
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) splitk_partial_kernel(StepArgs a, double* scratch, int64_t kc,
+                                                             int32_t chunks) {
+  const int chunk = blockIdx.x, b = blockIdx.y;
+  const int m = (int)a.m, n = (int)a.n, mn = m * n;
+  const float* A = a.A + b * a.a_bstride;
+  const float* B = a.B + b * a.b_bstride;
+  float sa = 1.f, sb = 1.f;
+  if (a.recs) {
+    sa = pow2_neg(scale_exp(a.recs + a.rec_a + (a.a_bstride ? b : 0)));
+    sb = pow2_neg(scale_exp(a.recs + a.rec_b + (a.b_bstride ? b : 0)));
+  }
+  float accr[kSplitMaxOut], acci[kSplitMaxOut];
+#pragma unroll
+  for (int o = 0; o < kSplitMaxOut; ++o) accr[o] = acci[o] = 0.f;
+  const int64_t k0 = (int64_t)chunk * kc;
+  const int64_t k1 = min(a.k, k0 + kc);
+  for (int64_t kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < kSplitMaxOut; ++i) {
+      if (i >= m) break;
+      const float xr = A[i * a.k + kk] * sa;
+      const float xi = CPLX ? A[a.a_plane + i * a.k + kk] * sa : 0.f;
+#pragma unroll
+      for (int j = 0; j < kSplitMaxOut; ++j) {
+        if (j >= n || i * n + j >= kSplitMaxOut) break;
+        const float yr = B[j * a.k + kk] * sb;
+        const int o = i * n + j;
+        if (CPLX) {
+          const float yi = B[a.b_plane + j * a.k + kk] * sb;
+          accr[o] = fmaf(xr, yr, fmaf(-xi, yi, accr[o]));
+          acci[o] = fmaf(xr, yi, fmaf(xi, yr, acci[o]));
+        } else {
+          accr[o] = fmaf(xr, yr, accr[o]);
+        }
+      }
+    }
+  }
+  __shared__ double red[2][kSplitMaxOut][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 0; o < kSplitMaxOut; ++o) {
+    if (o >= mn) break;
+    double vr = accr[o], vi = acci[o];
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      vr += __shfl_xor_sync(0xffffffffu, vr, s);
+      vi += __shfl_xor_sync(0xffffffffu, vi, s);
+    }
+    if (lane == 0) {
+      red[0][o][warp] = vr;
+      red[1][o][warp] = vi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < mn) {
+    const int o = threadIdx.x;
+    double vr = 0.0, vi = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      vr += red[0][o][w];
+      vi += red[1][o][w];
+    }
+    double* dst = scratch + (((int64_t)b * chunks + chunk) * mn + o) * 2;
+    dst[0] = vr;
+    dst[1] = vi;
+  }
+}
+
+__global__ void splitk_final_kernel(StepArgs a, const double* scratch, int32_t chunks, int32_t cplx) {
+  const int b = blockIdx.x;
+  const int m = (int)a.m, n = (int)a.n, mn = m * n;
+  float* C = a.C + b * a.c_bstride;
+  int lmax = -127;
+  for (int o = threadIdx.x; o < mn; o += blockDim.x) {
+    double vr = 0.0, vi = 0.0;
+    for (int c = 0; c < chunks; ++c) {
+      const double* p = scratch + (((int64_t)b * chunks + c) * mn + o) * 2;
+      vr += p[0];
+      vi += p[1];
+    }
+    const int i = o / n, j = o % n;
+    const int64_t off = map_offset(a.rows, i) + map_offset(a.cols, j);
+    C[off] = (float)vr;
+    if (cplx) C[a.c_plane + off] = (float)vi;
+    if (a.recs) lmax = max(lmax, exp_of(cplx ? fmaxf(fabsf((float)vr), fabsf((float)vi)) : fabsf((float)vr)));
+  }
+  if (a.recs) {
+    ScaleRec* rc = a.recs + a.rec_c + (a.c_bstride ? b : 0);
+    atomicMax(&rc->emax, lmax);
+    if (threadIdx.x == 0) {
+      const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
+      const ScaleRec* rb = a.recs + a.rec_b + (a.b_bstride ? b : 0);
+      rc->log2 = ra->log2 + rb->log2 + scale_exp(ra) + scale_exp(rb);
+    }
+  }
+}
+
+int32_t splitk_chunks(int64_t k) { return (int32_t)((k + kSplitChunk - 1) / kSplitChunk); }
+
+void launch_contract_splitk(const StepArgs& a, int32_t nb, bool cplx, double* scratch, cudaStream_t st) {
+  const int32_t chunks = splitk_chunks(a.k);
+  dim3 grid((unsigned)chunks, (unsigned)nb);
+  if (cplx) splitk_partial_kernel<true><<<grid, 256, 0, st>>>(a, scratch, kSplitChunk, chunks);
+  else splitk_partial_kernel<false><<<grid, 256, 0, st>>>(a, scratch, kSplitChunk, chunks);
+  splitk_final_kernel<<<(unsigned)nb, 64, 0, st>>>(a, scratch, chunks, cplx ? 1 : 0);
+}
+
 }  // namespace tn

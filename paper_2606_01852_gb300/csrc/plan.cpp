@@ -8,6 +8,7 @@
 #include <set>
 #include <sstream>
 
+#include "kernels.h"
 #include "tn_internal.h"
 
 namespace tn {
@@ -343,6 +344,10 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
       if (t_tc < t_simt) st.cls = TN_CLASS_TC;
     }
     if (st.cls == TN_CLASS_SIMT && stream_ok(st.m, st.n, st.k)) st.cls = TN_CLASS_STREAM;
+    // few outputs over a long reduction: the tiled kernel would leave all but a few
+    // threads idle and sum k terms serially in FP32
+    if (st.cls == TN_CLASS_SIMT && st.m * st.n <= kSplitMaxOut && st.k >= kSplitChunk)
+      st.cls = TN_CLASS_SPLITK;
   }
   // ---- pinned tensors: unbatched but consumed by a batched step (kept for all passes)
   for (int32_t s = 0; s < S; ++s) {
@@ -550,6 +555,15 @@ void assign_workspace(Plan& P, int64_t batch) {
   cur += kAlign;
   P.off_err = cur;
   cur += kAlign;
+  // split-K partials: the largest need of any split-K step (one pass)
+  int64_t scratch = 0;
+  for (const StepRec& st : P.steps)
+    if (st.cls == TN_CLASS_SPLITK)
+      scratch = std::max(scratch, (st.batched ? batch : 1) * ((st.k + kSplitChunk - 1) / kSplitChunk) *
+                                      st.m * st.n * 16);
+  P.off_scratch = cur;
+  P.scratch_bytes = scratch;
+  cur += align_up(scratch, kAlign);
   P.off_leafdesc = cur;
   cur += align_up(int64_t(T) * (int64_t)sizeof(LeafDesc), kAlign);
   P.off_stage_in = cur;

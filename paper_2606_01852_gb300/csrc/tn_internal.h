@@ -84,6 +84,8 @@ struct Plan {
   int64_t off_recidx = 0;           // int32 record index of each leaf (device copy)
   int64_t off_ref = 0;              // int64 reference exponent of the accumulator
   int64_t off_err = 0;              // int error word set by kernels whose bounded waits expire
+  int64_t off_scratch = 0;          // split-K partial sums (complex double)
+  int64_t scratch_bytes = 0;
   std::vector<int32_t> rec_index;   // per tensor: first scale record
   int64_t n_rec_unbatched = 0, n_rec_total = 0;
   int64_t off_leafdesc = 0;         // LeafDesc table
@@ -100,12 +102,14 @@ struct Plan {
     void* e0;
     void* e1;
     int32_t cls;
+    int32_t step;
     double flops, bytes;
   };
   bool prof_on = false;
   std::vector<ProfRec> prof_pending;
   std::vector<void*> prof_pool;
   tn_profile prof_acc{};
+  std::vector<double> prof_step_ms, prof_last_step_ms;
   uint64_t uid = 0;                 // unique per plan (serve pools key on it)
   // stats
   tn_plan_stats stats{};

@@ -184,3 +184,48 @@ def test_contract_host_roundtrip(tn):
     plan.contract_host(host, out, ls)
     want = oracle.contract(w.net, w.path)
     assert rel_err(out, want) < REL and ls[0] == 0.0
+
+
+def dot_network(out_a, out_b, k_dims, seed=9, sliced_dim=None):
+    """A[a..., k...] . B[b..., k...] with few open labels and a long reduction."""
+    from tn_inputs.network import Network
+    rng = np.random.default_rng(seed)
+    ext, lab = {}, 0
+    A_open, B_open, K = [], [], []
+    for grp, dims in ((A_open, out_a), (B_open, out_b), (K, k_dims)):
+        for d in dims:
+            ext[lab] = d
+            grp.append(lab)
+            lab += 1
+    am, bm = tuple(A_open + K), tuple(B_open + K)
+    if sliced_dim:
+        ext[lab] = sliced_dim
+        am, bm = am + (lab,), (lab,) + bm
+        lab += 1
+    shp = lambda ms: tuple(ext[x] for x in ms)
+    A = rng.standard_normal(shp(am)) + 1j * rng.standard_normal(shp(am))
+    B = rng.standard_normal(shp(bm)) + 1j * rng.standard_normal(shp(bm))
+    net = Network([A, B], [am, bm], ext, tuple(B_open + A_open))
+    net.check()
+    from tn_inputs.network import Path
+    return net, Path([(0, 1)]), ([lab - 1] if sliced_dim else [])
+
+
+@pytest.mark.parametrize("out_a,out_b,k_dims", [((), (), (2,) * 16), ((2,), (2,), (5, 7, 500)),
+                                                ((4,), (2, 2), (2,) * 14)])
+def test_splitk_long_reduction(tn, out_a, out_b, k_dims):
+    """Few outputs and a long k (a dot product of two big tensors): split-K partials in
+    FP64, summed in a fixed order; includes a ragged last chunk (k = 17500)."""
+    net, path, _ = dot_network(out_a, out_b, k_dims)
+    plan = tn.Plan(net, path)
+    assert plan.step(0)["cls"] == tn.TN_CLASS_SPLITK
+    got, _ = run(tn, plan, net)
+    assert rel_err(got, oracle.contract(net, path)) < REL
+
+
+def test_splitk_sliced_batch(tn):
+    net, path, sliced = dot_network((2,), (), (2,) * 13, sliced_dim=4)
+    plan = tn.Plan(net, path, sliced, max_slice_batch=3)
+    assert plan.step(0)["cls"] == tn.TN_CLASS_SPLITK and plan.step(0)["batched"] == 1
+    got, _ = run(tn, plan, net)
+    assert rel_err(got, oracle.contract(net, path, sliced)) < REL
