@@ -3,15 +3,18 @@
 // with both operands K-major, written through the separable row/column offset maps.
 //
 // One CTA computes a 128 x 128 output tile. Warp roles (192 threads):
-//   warp 0      : TMA producer -- A_re, A_im, B_re, B_im tiles (128 x 32 fp32, 128-byte
-//                 swizzle) into a ring of shared-memory stages, mbarrier tx-count signalled;
+//   warp 0      : TMA producer -- A_re, A_im, B_re, B_im tiles (128 rows x BK fp32,
+//                 swizzled) into a ring of shared-memory stages, mbarrier tx-count signalled;
 //   warp 1      : allocates tensor memory and issues tcgen05.mma (kind::tf32) from one lane;
 //   warps 2..5  : (3xTF32 only) split each staged tile into hi = TF32-truncated value (in
-//                 place) and lo = value - hi (separate buffer); then the epilogue: tcgen05.ld of
+//                 place) and lo = value - hi (a double-buffered side buffer, so splitting
+//                 stage s+1 overlaps the MMAs of stage s); then the epilogue: tcgen05.ld of
 //                 the accumulators and the offset-mapped stores.
 // Accumulators in TMEM (fp32): D_rr = sum A_re B_re, D_ii = sum A_im B_im,
 // D_x = sum (A_re B_im + A_im B_re); Re C = D_rr - D_ii, Im C = D_x.
 // 3xTF32: a.b ~ ah.bh + al.bh + ah.bl (the al.bl term, ~2^-22 relative, is dropped).
+// TF32 form: BK = 32 (128-byte rows, 128-byte swizzle), 3 stages. 3xTF32 form: BK = 16
+// (64-byte rows, 64-byte swizzle), 4 stages + 2 lo buffers.
 // Every mbarrier wait is bounded by wall time; on expiry the CTA records an error code,
 // drains its copies, frees its tensor memory and returns.
 #include <cstdint>
@@ -25,10 +28,7 @@
 namespace tn {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 32;                 // BK fp32 = one 128-byte row
-constexpr int TILE_A = BM * BK * 4;                         // 16 KiB
-constexpr int TILE_B = BN * BK * 4;                         // 16 KiB
-constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;        // 64 KiB: A_re A_im B_re B_im
+constexpr int BM = 128, BN = 128;
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;                         // D_rr @0, D_ii @128, D_x @256
 constexpr int GROUP_M = 16;                                 // raster: tiles grouped along M
@@ -36,9 +36,14 @@ constexpr uint64_t kWaitNs = 4000000000ull;                 // 4 s bound on any 
 
 template <int SPLIT>
 struct Cfg {
-  static constexpr int STAGES = SPLIT == 1 ? 3 : 2;
-  static constexpr int LO = SPLIT == 1 ? 0 : 1;
-  static constexpr int SMEM = (STAGES + LO) * STAGE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
+  static constexpr int BK = SPLIT == 1 ? 32 : 16;           // fp32 elements per k-block
+  static constexpr int ROWB = BK * 4;                       // bytes per tile row (= swizzle span)
+  static constexpr int TILE_A = BM * ROWB;
+  static constexpr int TILE_B = BN * ROWB;
+  static constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;     // A_re A_im B_re B_im
+  static constexpr int STAGES = SPLIT == 1 ? 3 : 4;
+  static constexpr int LO = SPLIT == 1 ? 0 : 2;             // lo buffers
+  static constexpr int SMEM = (STAGES + LO) * STAGE + 1024 /*barriers*/ + 1024 /*align*/;
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -87,15 +92,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
 }
-// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte swizzle,
-// 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major tile whose rows are ROWB bytes with the
+// matching swizzle (128 B -> mode 2, 64 B -> mode 4); 8-row groups 8*ROWB bytes apart.
+template <int ROWB>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr & 0x3FFFF) >> 4);
-  d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused here)
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset
-  d |= static_cast<uint64_t>(1) << 46;            // descriptor version
-  d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
+  d |= static_cast<uint64_t>(1) << 16;                 // leading byte offset (unused here)
+  d |= static_cast<uint64_t>((8 * ROWB) >> 4) << 32;   // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                 // descriptor version
+  d |= static_cast<uint64_t>(ROWB == 128 ? 2 : 4) << 61;
   return d;
 }
 // Instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, shape M x N.
@@ -143,20 +149,24 @@ __device__ __forceinline__ int64_t map_off(const OffsetMap& om, int64_t idx) {
   return off;
 }
 
+__device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
+
 template <int SPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                        StepArgs a, int* err) {
-  constexpr int STAGES = Cfg<SPLIT>::STAGES;
+  using G = Cfg<SPLIT>;
+  constexpr int STAGES = G::STAGES, BK = G::BK, ROWB = G::ROWB;
+  constexpr int TILE_A = G::TILE_A, TILE_B = G::TILE_B, STAGE = G::STAGE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* lo_base = smem + STAGES * STAGE_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(lo_base + Cfg<SPLIT>::LO * STAGE_BYTES);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + STAGES;
-  uint64_t* conv_full = bars + 2 * STAGES;
-  uint64_t* lo_empty = conv_full + 1;
-  uint64_t* acc_full = lo_empty + 1;
+  uint8_t* lo_base = smem + STAGES * STAGE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(lo_base + G::LO * STAGE);
+  uint64_t* full = bars;                     // [STAGES]
+  uint64_t* empty = bars + STAGES;           // [STAGES]
+  uint64_t* conv_full = bars + 2 * STAGES;   // [2]
+  uint64_t* lo_empty = conv_full + 2;        // [2]
+  uint64_t* acc_full = lo_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -177,8 +187,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(conv_full, 128);
-    mbar_init(lo_empty, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&conv_full[i], 128);
+      mbar_init(&lo_empty[i], 1);
+    }
     mbar_init(acc_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
@@ -204,8 +216,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           atomicExch(err, 1);
           break;
         }
-        mbar_expect_tx(&full[s], STAGE_BYTES);
-        uint8_t* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE);
+        uint8_t* st = smem + s * STAGE;
         const int k0 = kb * BK;
         tma_load_3d(st, &tmA, &full[s], k0, m0, pa);
         tma_load_3d(st + TILE_A, &tmA, &full[s], k0, m0, pa + 1);
@@ -221,37 +233,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_tf32(BM, BN);
       const uint32_t d_rr = tmem, d_ii = tmem + 128, d_x = tmem + 256;
-      bool ok = true;
-      for (int kb = 0; kb < num_kb && ok; ++kb) {
+      for (int kb = 0; kb < num_kb; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
         if (!mbar_wait(&full[s], ph)) {
           atomicExch(err, 3);
-          ok = false;
           break;
         }
-        if (SPLIT == 3 && !mbar_wait(conv_full, kb & 1)) {
+        if (SPLIT == 3 && !mbar_wait(&conv_full[kb & 1], (kb >> 1) & 1)) {
           atomicExch(err, 4);
-          ok = false;
           break;
         }
         fence_after();
-        const uint32_t st = su32(smem + s * STAGE_BYTES);
-        const uint32_t lo = su32(lo_base);
+        const uint32_t st = su32(smem + s * STAGE);
+        const uint32_t lo = su32(lo_base + (kb & 1) * STAGE);
 #pragma unroll
         for (int j = 0; j < BK / 8; ++j) {
           const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
-          const uint64_t ar = sw128_desc(st + j * 32), ai = sw128_desc(st + TILE_A + j * 32);
-          const uint64_t br = sw128_desc(st + 2 * TILE_A + j * 32);
-          const uint64_t bi = sw128_desc(st + 2 * TILE_A + TILE_B + j * 32);
+          const uint64_t ar = smem_desc<ROWB>(st + j * 32), ai = smem_desc<ROWB>(st + TILE_A + j * 32);
+          const uint64_t br = smem_desc<ROWB>(st + 2 * TILE_A + j * 32);
+          const uint64_t bi = smem_desc<ROWB>(st + 2 * TILE_A + TILE_B + j * 32);
           mma_tf32(d_rr, ar, br, idesc, acc);
           mma_tf32(d_ii, ai, bi, idesc, acc);
           mma_tf32(d_x, ar, bi, idesc, acc);
           mma_tf32(d_x, ai, br, idesc, 1u);
           if (SPLIT == 3) {
-            const uint64_t arl = sw128_desc(lo + j * 32), ail = sw128_desc(lo + TILE_A + j * 32);
-            const uint64_t brl = sw128_desc(lo + 2 * TILE_A + j * 32);
-            const uint64_t bil = sw128_desc(lo + 2 * TILE_A + TILE_B + j * 32);
+            const uint64_t arl = smem_desc<ROWB>(lo + j * 32), ail = smem_desc<ROWB>(lo + TILE_A + j * 32);
+            const uint64_t brl = smem_desc<ROWB>(lo + 2 * TILE_A + j * 32);
+            const uint64_t bil = smem_desc<ROWB>(lo + 2 * TILE_A + TILE_B + j * 32);
             mma_tf32(d_rr, arl, br, idesc, 1u);
             mma_tf32(d_rr, ar, brl, idesc, 1u);
             mma_tf32(d_ii, ail, bi, idesc, 1u);
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         mma_commit(&empty[s]);
-        if (SPLIT == 3) mma_commit(lo_empty);
+        if (SPLIT == 3) mma_commit(&lo_empty[kb & 1]);
       }
       mma_commit(acc_full);  // also on error: lets the epilogue see in-flight MMAs retire
     }
@@ -272,18 +281,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (SPLIT == 3) {
       for (int kb = 0; kb < num_kb; ++kb) {
         const int s = kb % STAGES;
-        if (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(lo_empty, (kb & 1) ^ 1)) {
+        if (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(&lo_empty[kb & 1], ((kb >> 1) & 1) ^ 1)) {
           atomicExch(err, 5);
           break;
         }
-        float4* src = reinterpret_cast<float4*>(smem + s * STAGE_BYTES);
-        float4* dst = reinterpret_cast<float4*>(lo_base);
-        for (int i = et; i < STAGE_BYTES / 16; i += 128) {
-          float4 v = src[i], h, l;
-          h.x = __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
-          h.y = __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
-          h.z = __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
-          h.w = __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
+        float4* src = reinterpret_cast<float4*>(smem + s * STAGE);
+        float4* dst = reinterpret_cast<float4*>(lo_base + (kb & 1) * STAGE);
+#pragma unroll 4
+        for (int i = et; i < STAGE / 16; i += 128) {
+          const float4 v = src[i];
+          float4 h, l;
+          h.x = tf32_trunc(v.x);
+          h.y = tf32_trunc(v.y);
+          h.z = tf32_trunc(v.z);
+          h.w = tf32_trunc(v.w);
           l.x = v.x - h.x;
           l.y = v.y - h.y;
           l.z = v.z - h.z;
@@ -292,7 +303,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           dst[i] = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(conv_full);
+        mbar_arrive(&conv_full[kb & 1]);
       }
     }
     // epilogue: TMEM lane quarter of this warp = warp % 4
@@ -305,25 +316,48 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const bool row_ok = ok && m < a.m;
     const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
-    const int last = a.cols.n - 1;
-    const bool fast = last >= 0 && (a.cols.ext[last] % 32u) == 0u;
-    const int64_t sl = last >= 0 ? a.cols.stride[last] : 0;
     const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    // Store pattern: a warp instruction should write 32 consecutive addresses. If the
+    // rows are the unit-stride side, thread = row already does; otherwise each 32 x 32
+    // block goes through shared memory (the drained stage buffers) and thread =
+    // column, row by row.
+    const bool rows_unit = a.rows.n > 0 && a.rows.stride[a.rows.n - 1] == 1;
+    float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 33;  // [2][32][33]
     for (int c = 0; c < BN / 32; ++c) {
       float rr[32], ii[32], xx[32];
       tmem_ld32(tmem + lane_base + c * 32, rr);
       tmem_ld32(tmem + lane_base + 128 + c * 32, ii);
       tmem_ld32(tmem + lane_base + 256 + c * 32, xx);
-      if (!row_ok) continue;
       const int64_t nb0 = static_cast<int64_t>(n0) + c * 32;
-      const int64_t co0 = (fast && nb0 < a.n) ? map_off(a.cols, nb0) : 0;
+      if (rows_unit) {
+        if (!row_ok) continue;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int64_t n = nb0 + j;
-        if (n >= a.n) break;
-        const int64_t off = ro + (fast ? co0 + j * sl : map_off(a.cols, n));
-        C[off] = rr[j] - ii[j];
-        C[a.c_plane + off] = xx[j];
+        for (int j = 0; j < 32; ++j) {
+          const int64_t n = nb0 + j;
+          if (n >= a.n) break;
+          const int64_t off = ro + map_off(a.cols, n);
+          C[off] = rr[j] - ii[j];
+          C[a.c_plane + off] = xx[j];
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          tr[lane * 33 + j] = rr[j] - ii[j];
+          tr[32 * 33 + lane * 33 + j] = xx[j];
+        }
+        __syncwarp();
+        const int64_t n = nb0 + lane;
+        const bool col_ok = ok && n < a.n;
+        const int64_t co = col_ok ? map_off(a.cols, n) : 0;
+        for (int r = 0; r < 32; ++r) {
+          const int64_t ro_r = __shfl_sync(0xffffffffu, ro, r);
+          const bool ok_r = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, r) != 0;
+          if (ok_r && col_ok) {
+            C[ro_r + co] = tr[r * 33 + lane];
+            C[a.c_plane + ro_r + co] = tr[32 * 33 + r * 33 + lane];
+          }
+        }
+        __syncwarp();
       }
     }
   }
@@ -348,18 +382,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-// 3-D map over one operand: (k, rows, plane), plane = 2*batch + {re, im}.
+// 3-D map over one operand: (k, rows, plane), plane = 2*batch + {re, im}; box BK x rows.
 bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t k, int64_t planes, int64_t plane_elems,
-              int box_rows) {
+              int box_rows, int bk) {
   auto enc = encoder();
   if (!enc) return false;
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows),
                         static_cast<cuuint64_t>(planes)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(k * 4), static_cast<cuuint64_t>(plane_elems * 4)};
-  cuuint32_t box[3] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows), 1};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows), 1};
   cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapSwizzle sw = bk * 4 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -376,7 +411,8 @@ cudaError_t launch_split(const StepArgs& a, int32_t nb, int* err, cudaStream_t s
   CUtensorMap ta, tb;
   const int64_t pa = a.a_bstride ? 2 * static_cast<int64_t>(nb) : 2;
   const int64_t pb = a.b_bstride ? 2 * static_cast<int64_t>(nb) : 2;
-  if (!make_map(&ta, a.A, a.m, a.k, pa, a.a_plane, BM) || !make_map(&tb, a.B, a.n, a.k, pb, a.b_plane, BN))
+  constexpr int bk = Cfg<SPLIT>::BK;
+  if (!make_map(&ta, a.A, a.m, a.k, pa, a.a_plane, BM, bk) || !make_map(&tb, a.B, a.n, a.k, pb, a.b_plane, BN, bk))
     return cudaErrorInvalidValue;
   const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
   dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));

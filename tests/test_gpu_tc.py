@@ -125,6 +125,26 @@ def test_circuit_path_with_tc_steps(tn, prec, tol):
     assert rel_err(got, oracle.contract(w.net, w.path)) < tol
 
 
+def test_tf32_operand_rounding(tn):
+    """How tcgen05 kind::tf32 reads an FP32 operand: with A = 1 + 3*2^-12 and B = 1,
+    truncation to 10 mantissa bits gives 1, round-to-nearest 1 + 2^-10. The 3xTF32
+    form does not depend on the answer (it feeds an explicitly truncated hi), but the
+    TF32 error budget above assumes at most one TF32 ulp per operand either way."""
+    from tn_inputs.network import Network, Path
+    ext = {0: 128, 1: 64, 2: 16}
+    A = np.full((128, 16), 1.0 + 3.0 * 2.0**-12, dtype=np.complex128)
+    B = np.ones((64, 16), dtype=np.complex128)
+    net = Network([A, B], [(0, 2), (1, 2)], ext, (0, 1))
+    plan = tn.Plan(net, Path([(0, 1)]), prec="tf32")
+    assert plan.step(0)["cls"] == tn.TN_CLASS_TC
+    got, _ = run(tn, plan, net)
+    vals = np.unique(got.real)
+    assert vals.size == 1 and vals[0] in (16.0, 16.0 * (1 + 2.0**-10)), vals
+    exact = tn.Plan(net, Path([(0, 1)]), prec="3xtf32")
+    g3, _ = run(tn, exact, net)
+    assert np.allclose(g3.real, 16.0 * (1.0 + 3.0 * 2.0**-12), rtol=0, atol=1e-6)
+
+
 @pytest.mark.parametrize("prec,tol", [("tf32", 3e-2), ("3xtf32", 1e-5)])
 def test_sliced_circuit_with_tc_steps(tn, prec, tol):
     w = workloads.random_circuit(4, 5, 12, 40, n_sliced=3)
