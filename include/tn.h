@@ -247,6 +247,30 @@ tn_status tn_serve_poll(tn_server_t srv, uint64_t ticket, void* result, double* 
 /* Stop the scheduler (finishing admitted work) and free the server. */
 tn_status tn_serve_destroy(tn_server_t srv);
 
+/* ---- allocation-free batched dot products ----------------------------------------- */
+
+/* The paper has no counterpart to this call. It exists for callers that must not
+ * allocate device memory on this path -- a host process whose device memory is already
+ * handed out by another allocator, or a latency-critical loop where cudaMalloc (which
+ * may synchronize the device) is not acceptable. It runs the engine's split-K reduction
+ * (the kernel behind few-output steps with a long contracted index) with its FP64
+ * partial sums in a fixed file-scope device array of 2^18 complex doubles (4 MiB) that
+ * every device using the library holds until the process exits.
+ *
+ *   out[b][i][j] = sum_t a[b][i][t] * b[b][j][t]      (no conjugation)
+ *
+ * a: DEVICE complex64, [batch][m][k] row-major; b: DEVICE complex64, [batch][n][k];
+ * out: DEVICE complex128, [batch][m][n]. All three are owned by the caller.
+ * Limits: m*n <= 16, batch <= 65535, batch * ceil(k/4096) * m*n <= 2^18; larger sizes
+ * return TN_ERR_INVALID with a message. Allocates nothing (no cudaMalloc/cudaFree, no
+ * allocating library call). Asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ * default stream). The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture. All calls share the array: each call overwrites every partial it
+ * reads, so calls in sequence need no clearing, but calls that overlap on the GPU race. */
+tn_status tn_dot_noalloc(const void* a, const void* b, int64_t batch, int64_t m, int64_t n, int64_t k,
+                         void* out, void* stream);
+
 /* Thread-local message for the last non-OK status on this thread. */
 const char* tn_last_error(void);
 

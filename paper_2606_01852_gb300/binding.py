@@ -107,6 +107,7 @@ def _load():
         "tn_serve_submit": [vp, vp, C.POINTER(vp), C.POINTER(u64)],
         "tn_serve_poll": [vp, u64, vp, vp, i32],
         "tn_serve_destroy": [vp],
+        "tn_dot_noalloc": [vp, vp, i64, i64, i64, i64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -282,6 +283,13 @@ class Plan:
             self.destroy()
         except Exception:
             pass
+
+
+def dot_noalloc(a, b, batch, m, n, k, out, stream=None):
+    """tn_dot_noalloc: out[b][i][j] = sum_t a[b][i][t] b[b][j][t] with no device allocation
+    (device complex64 inputs, device complex128 output, caller-owned)."""
+    check(lib.tn_dot_noalloc(_ptr(a), _ptr(b), int(batch), int(m), int(n), int(k), _ptr(out),
+                             _ptr_stream(stream)))
 
 
 def _ptr_stream(stream):
