@@ -292,7 +292,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rc40", choices=sorted(workloads.BY_NAME))
-    ap.add_argument("--prec", default="fp32", choices=sorted(PREC))
+    ap.add_argument("--prec", default="3xtf32", choices=sorted(PREC),
+                    help="GEMM form: 3xtf32 (default; FP32-accurate), tf32, fp32 (the plain CUDA-core form)")
     ap.add_argument("--max-slice-batch", type=int, default=0)
     ap.add_argument("--ref-budget", type=float, default=20.0, help="oracle seconds per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
