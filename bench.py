@@ -285,13 +285,83 @@ def run_ours(args):
     return 0
 
 
+def run_batch_bench(args):
+    """Many small networks: 4096 Ising partition functions on random 3-regular graphs
+    (20-60 spins, J = +-1, beta = 0.5), FP32 with exponent scaling, one persistent
+    graph-replayed launch (launch shape from the autotuner), against one tn_contract
+    launch sequence per network. Metric: networks/s."""
+    import torch
+    import paper_2606_01852_gb300 as tn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    count = args.networks
+    wl = workloads.ising3r(count, seed=3)
+    nets, paths = [w.net for w in wl], [w.path for w in wl]
+    b = tn.Batch(nets, paths, complex_=False, exp_scaling=True)
+    packed = torch.tensor(b.pack(nets), device="cuda")
+    vals = torch.zeros((count, 2), dtype=torch.float64, device="cuda")
+    logs = torch.zeros(count, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    b.autotune(packed, vals, logs, stream)
+    for _ in range(args.warmup):
+        b.contract(packed, vals, logs, stream, graph=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        b.contract(packed, vals, logs, stream, graph=True)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = statistics.mean(a.elapsed_time(c) for a, c in ev)
+    # one launch sequence per network (the per-contraction baseline)
+    plans = [tn.Plan(n, p, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True) for n, p in zip(nets, paths)]
+    dins = [[torch.tensor(np.asarray(t, dtype=np.float32), device="cuda") for t in n.tensors] for n in nets]
+    outs = torch.zeros(count, dtype=torch.float64, device="cuda")
+    lss = torch.zeros(count, dtype=torch.float64, device="cuda")
+    for i in range(count):
+        plans[i].contract(dins[i], outs[i:i + 1], lss[i:i + 1], stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(count):
+        plans[i].contract(dins[i], outs[i:i + 1], lss[i:i + 1], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    lnz_b = np.log(vals[:, 0].cpu().numpy()) + logs.cpu().numpy()
+    lnz_s = np.log(outs.cpu().numpy()) + lss.cpu().numpy()
+    t, c = b.launch_shape()
+    alu = SM_COUNT * FP32_LANES * 2 * load_peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    line = {
+        "metric": "networks/s", "value": ws * count / (ms / 1e3), "unit": "networks/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ising3r", "networks": count, "desc": "Ising partition functions, random "
+                   "3-regular graphs, 20-60 spins, J=+-1, beta=0.5, FP32 + exponent scaling",
+                   "launch_shape": {"threads": t, "ctas_per_sm": c}, "graph": True},
+        "one_launch_per_contraction": {"ms": ms_seq, "networks_per_s": count / (ms_seq / 1e3),
+                                       "speedup_of_persistent": ms_seq / ms},
+        "max_abs_lnz_diff_vs_per_contraction": float(np.max(np.abs(lnz_b - lnz_s))),
+        "roofline": {"bound": "alu", "achieved": b.flops / (ms / 1e3) / 1e12, "peak": alu, "unit": "TFLOP/s",
+                     "frac": b.flops / (ms / 1e3) / 1e12 / alu, "traffic": None, "kernel": "batch_kernel"},
+        "gpu_launches": args.steps, "clocks": ck,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rc40", choices=sorted(workloads.BY_NAME))
+    ap.add_argument("--workload", default="rc40", choices=sorted(workloads.BY_NAME) + ["ising3r"])
+    ap.add_argument("--networks", type=int, default=4096, help="ising3r: networks per launch")
     ap.add_argument("--prec", default="3xtf32", choices=sorted(PREC),
                     help="GEMM form: 3xtf32 (default; FP32-accurate), tf32, fp32 (the plain CUDA-core form)")
     ap.add_argument("--max-slice-batch", type=int, default=0)
@@ -300,6 +370,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "ising3r" and args.impl == "ours":
+        return run_batch_bench(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

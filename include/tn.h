@@ -247,6 +247,48 @@ tn_status tn_serve_poll(tn_server_t srv, uint64_t ticket, void* result, double* 
 /* Stop the scheduler (finishing admitted work) and free the server. */
 tn_status tn_serve_destroy(tn_server_t srv);
 
+/* ---- many small independent networks in one launch -------------------------------- */
+
+typedef struct tn_batch_s* tn_batch_t;
+
+/* Plan n_nets independent CLOSED networks (each with its own path; no slicing) for one
+ * persistent launch: every network gets the same analysis and mode reordering as
+ * tn_plan (Sec. II-B, Sec. IV-A) and its own arena; one CTA contracts one network at a
+ * time, taking networks from an atomic queue. policy.prec must be TN_C64_FP32_SIMT or
+ * TN_R32_FP32_SIMT; policy.exp_scaling renormalises every tensor by an exact power of two
+ * as it is made and sums the exponents per network in an int64. With
+ * TN_PLAN_HOST_ONLY no device memory is taken (tables only, for tn_batch_info). */
+tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* paths, tn_dtype_policy policy,
+                        tn_batch_t* out);
+
+/* leaf_offsets (total leaves + 1 int64, or NULL): element offset of every leaf in the
+ * packed input buffer (network 0's leaves in order, then network 1's, ...; each leaf in
+ * its declared order, row-major); the last entry is the buffer's length in elements.
+ * flops (or NULL): algorithmic flops of one launch. threads/ctas_per_sm (or NULL): the
+ * launch shape currently chosen (see tn_batch_autotune). */
+tn_status tn_batch_info(tn_batch_t b, int64_t* leaf_offsets, double* flops, int32_t* threads,
+                        int32_t* ctas_per_sm);
+
+/* Contract every network. packed_inputs: DEVICE buffer laid out as tn_batch_info says
+ * (complex64 or float32). values: DEVICE, 2 doubles per network (real, imaginary; 0 for
+ * real networks); log_scales: DEVICE, 1 double per network; result = value * exp(log).
+ * Asynchronous on `stream`; calls on one batch must not overlap. */
+tn_status tn_batch_contract(tn_batch_t b, const void* packed_inputs, double* values, double* log_scales,
+                            void* stream);
+
+/* As tn_batch_contract, replayed from a CUDA graph (queue reset + kernel) captured on
+ * the first call and re-captured when any pointer or the stream changes. */
+tn_status tn_batch_contract_graph(tn_batch_t b, const void* packed_inputs, double* values, double* log_scales,
+                                  void* stream);
+
+/* Time the batch under candidate launch shapes (threads per network x CTAs per SM), keep
+ * the fastest for later calls. Writes results into values/log_scales as a side effect.
+ * Synchronous. */
+tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* values, double* log_scales,
+                            void* stream);
+
+tn_status tn_batch_destroy(tn_batch_t b);
+
 /* ---- allocation-free batched dot products ----------------------------------------- */
 
 /* The paper has no counterpart to this call. It exists for callers that must not

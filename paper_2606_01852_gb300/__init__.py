@@ -3,7 +3,7 @@
 The compute path lives in the CUDA library libtn_gb300.so (C ABI: include/tn.h);
 this package is its thin Python binding. See `binding` for the wrappers.
 """
-from .binding import (Plan, Server, TnError, check, last_error, make_policy, lib, LIB_PATH,
+from .binding import (Plan, Server, Batch, TnError, check, last_error, make_policy, lib, LIB_PATH,
                       TN_OK, TN_ERR_INVALID, TN_ERR_UNSUPPORTED, TN_ERR_OOM, TN_ERR_CUDA,
                       TN_ERR_BUSY, TN_ERR_TIMEOUT, TN_ERR_NOT_READY,
                       TN_C64_FP32_SIMT, TN_C64_TF32, TN_C64_3XTF32, TN_C64_BF16X3,

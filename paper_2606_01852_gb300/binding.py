@@ -108,6 +108,12 @@ def _load():
         "tn_serve_poll": [vp, u64, vp, vp, i32],
         "tn_serve_destroy": [vp],
         "tn_dot_noalloc": [vp, vp, i64, i64, i64, i64, vp, vp],
+        "tn_batch_plan": [i32, C.POINTER(tn_network), C.POINTER(tn_path), tn_dtype_policy, C.POINTER(vp)],
+        "tn_batch_info": [vp, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i32)],
+        "tn_batch_contract": [vp, vp, vp, vp, vp],
+        "tn_batch_contract_graph": [vp, vp, vp, vp, vp],
+        "tn_batch_autotune": [vp, vp, vp, vp, vp],
+        "tn_batch_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -276,6 +282,63 @@ class Plan:
     def destroy(self):
         if getattr(self, "handle", None):
             lib.tn_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many small closed networks, one persistent launch (tn_batch_*)."""
+
+    def __init__(self, nets, paths, complex_=False, exp_scaling=True, host_only=False):
+        self._arrs = [_NetArrays([tuple(m) for m in n.modes], dict(n.extent), tuple(n.open_modes),
+                                 p.pairs if hasattr(p, "pairs") else p) for n, p in zip(nets, paths)]
+        self.n_nets = len(nets)
+        self.complex = complex_
+        netv = (tn_network * self.n_nets)(*[a.net for a in self._arrs])
+        pathv = (tn_path * self.n_nets)(*[a.path for a in self._arrs])
+        pol = make_policy(TN_C64_FP32_SIMT if complex_ else TN_R32_FP32_SIMT, exp_scaling, 1, host_only)
+        h = C.c_void_p()
+        check(lib.tn_batch_plan(self.n_nets, netv, pathv, pol, C.byref(h)))
+        self.handle = h
+        self.n_leaves = sum(len(n.modes) for n in nets)
+        off = (C.c_int64 * (self.n_leaves + 1))()
+        fl = C.c_double()
+        check(lib.tn_batch_info(h, off, C.byref(fl), None, None))
+        self.leaf_offsets = list(off)
+        self.flops = fl.value
+
+    def pack(self, nets):
+        """Concatenate every leaf (declared order) into one host array."""
+        dt = np.complex64 if self.complex else np.float32
+        out = np.empty(self.leaf_offsets[-1], dtype=dt)
+        i = 0
+        for n in nets:
+            for t in n.tensors:
+                a = np.asarray(t, dtype=dt).ravel()
+                out[self.leaf_offsets[i]: self.leaf_offsets[i] + a.size] = a
+                i += 1
+        return out
+
+    def launch_shape(self):
+        t, c = C.c_int32(), C.c_int32()
+        check(lib.tn_batch_info(self.handle, None, None, C.byref(t), C.byref(c)))
+        return t.value, c.value
+
+    def contract(self, packed, values, logs, stream=None, graph=False):
+        f = lib.tn_batch_contract_graph if graph else lib.tn_batch_contract
+        check(f(self.handle, _ptr(packed), _ptr(values), _ptr(logs), _ptr_stream(stream)))
+
+    def autotune(self, packed, values, logs, stream=None):
+        check(lib.tn_batch_autotune(self.handle, _ptr(packed), _ptr(values), _ptr(logs), _ptr_stream(stream)))
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib.tn_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libtn_gb300.so")
-SOURCES = ["plan.cpp", "api.cu", "kernels_simt.cu", "gemm_tc.cu", "serve.cpp", "noalloc.cu"]
+SOURCES = ["plan.cpp", "api.cu", "kernels_simt.cu", "gemm_tc.cu", "serve.cpp", "noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

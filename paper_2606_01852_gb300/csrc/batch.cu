@@ -1,0 +1,503 @@
+// Batched independent small networks in one persistent launch.
+//
+// Each network has its own path and its own plan (the same planner as tn_plan: step
+// analysis, GEMM-oriented reordering of Sec. IV-A, liveness offsets), flattened into
+// compact device tables. One CTA takes the next network from an atomic queue and runs
+// its whole path: stage the leaves into the network's arena (planned orders), then for
+// each step C = A (m x k) . B (n x k)^T written through the output offset maps, with
+// every thread of the CTA working on the step. With exponent scaling each tensor is
+// renormalised in place after it is made (an exact power of two chosen from its largest
+// entry) and the exponents are summed per network in an int64; the network's result is
+// (value, log2 scale) and ln|Z| = ln|value| + log2 * ln 2 in FP64 on the host side.
+// The CTA width (threads per network) and CTAs per SM are chosen by an autotuner that
+// times the real batch; the launch (queue reset + kernel) can be replayed as a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "tn_internal.h"
+
+namespace tn {
+namespace {
+
+constexpr int kBMaxDims = 8;    // merged offset dims per side in the batch tables
+constexpr int kBMaxRank = 8;    // planned leaf rank in the batch tables
+
+struct BLeaf {
+  int64_t src;                  // element offset in the packed input buffer
+  int32_t dst;                  // float offset in the network's arena (real plane)
+  int32_t size;
+  int32_t rank;
+  int32_t pad;
+  int32_t ext[kBMaxRank];
+  int32_t sstride[kBMaxRank];   // declared stride of each planned position
+};
+
+struct BStep {
+  int32_t a, b, c;              // float offsets in the arena (real planes)
+  int32_t a_size, b_size, c_size;
+  int32_t m, n, k;
+  int8_t nr, nc;
+  int16_t pad;
+  int32_t rext[kBMaxDims], rstr[kBMaxDims];
+  int32_t cext[kBMaxDims], cstr[kBMaxDims];
+};
+
+struct BNet {
+  int64_t arena;                // float offset of the network's arena in the batch arena
+  int32_t leaf0, n_leaves;      // index range in the leaf table
+  int32_t step0, n_steps;       // index range in the step table
+  int32_t root, root_size;      // float offset and size of the result tensor
+};
+
+__device__ __forceinline__ int bexp_of(float v) { return ((__float_as_int(v) >> 23) & 0xff) - 127; }
+__device__ __forceinline__ float bpow2_neg(int e) {
+  e = max(-126, min(127, e));
+  return __int_as_float((127 - e) << 23);
+}
+
+template <bool CPLX>
+__device__ void renormalise(float* t, int size, int* smax, long long* slog) {
+  int lmax = -127;
+  for (int i = threadIdx.x; i < size; i += blockDim.x) {
+    float v = fabsf(t[i]);
+    if (CPLX) v = fmaxf(v, fabsf(t[size + i]));
+    lmax = max(lmax, bexp_of(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(smax, lmax);
+  __syncthreads();
+  const int e = *smax < -126 ? 0 : *smax;  // an all-zero tensor is left as is
+  if (e != 0) {
+    const float s = bpow2_neg(e);
+    for (int i = threadIdx.x; i < size; i += blockDim.x) {
+      t[i] *= s;
+      if (CPLX) t[size + i] *= s;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *slog += e;
+    *smax = -127;
+  }
+  __syncthreads();
+}
+
+template <bool CPLX>
+__global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restrict__ leaves,
+                             const BStep* __restrict__ steps, int32_t n_nets, const float* __restrict__ in,
+                             float* arena, int32_t* queue, int32_t scaling, double* values, double* logs) {
+  __shared__ int s_net;
+  __shared__ int s_max;
+  __shared__ long long s_log;
+  constexpr int NP = CPLX ? 2 : 1;
+  if (threadIdx.x == 0) s_max = -127;
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_net = atomicAdd(queue, 1);
+      s_log = 0;
+    }
+    __syncthreads();
+    const int w = s_net;
+    if (w >= n_nets) break;
+    const BNet net = nets[w];
+    float* ar = arena + net.arena;
+    // stage the leaves (declared order -> planned order; complex64 -> planar)
+    for (int l = 0; l < net.n_leaves; ++l) {
+      const BLeaf& L = leaves[net.leaf0 + l];
+      for (int e = threadIdx.x; e < L.size; e += blockDim.x) {
+        int r = e, src = 0;
+        for (int d = L.rank - 1; d >= 0; --d) {
+          src += (r % L.ext[d]) * L.sstride[d];
+          r /= L.ext[d];
+        }
+        if (CPLX) {
+          const float2 v = reinterpret_cast<const float2*>(in)[L.src + src];
+          ar[L.dst + e] = v.x;
+          ar[L.dst + L.size + e] = v.y;
+        } else {
+          ar[L.dst + e] = in[L.src + src];
+        }
+      }
+    }
+    __syncthreads();
+    if (scaling)
+      for (int l = 0; l < net.n_leaves; ++l) {
+        const BLeaf& L = leaves[net.leaf0 + l];
+        renormalise<CPLX>(ar + L.dst, L.size, &s_max, &s_log);
+      }
+    for (int s = 0; s < net.n_steps; ++s) {
+      const BStep& S = steps[net.step0 + s];
+      const int mn = S.m * S.n;
+      for (int o = threadIdx.x; o < mn; o += blockDim.x) {
+        const int i = o / S.n, j = o - i * S.n;
+        const float* A = ar + S.a + i * S.k;
+        const float* B = ar + S.b + j * S.k;
+        float cr = 0.f, ci = 0.f;
+        for (int t = 0; t < S.k; ++t) {
+          if (CPLX) {
+            const float xr = A[t], xi = A[S.a_size + t], yr = B[t], yi = B[S.b_size + t];
+            cr = fmaf(xr, yr, fmaf(-xi, yi, cr));
+            ci = fmaf(xr, yi, fmaf(xi, yr, ci));
+          } else {
+            cr = fmaf(A[t], B[t], cr);
+          }
+        }
+        int ro = 0, co = 0, r = i, c = j;
+        for (int d = S.nr - 1; d >= 0; --d) {
+          ro += (r % S.rext[d]) * S.rstr[d];
+          r /= S.rext[d];
+        }
+        for (int d = S.nc - 1; d >= 0; --d) {
+          co += (c % S.cext[d]) * S.cstr[d];
+          c /= S.cext[d];
+        }
+        ar[S.c + ro + co] = cr;
+        if (CPLX) ar[S.c + S.c_size + ro + co] = ci;
+      }
+      __syncthreads();
+      if (scaling) renormalise<CPLX>(ar + S.c, S.c_size, &s_max, &s_log);
+    }
+    if (threadIdx.x == 0) {
+      // scalar results (closed networks): value and log2 scale
+      values[2 * (int64_t)w] = ar[net.root];
+      values[2 * (int64_t)w + 1] = CPLX ? ar[net.root + net.root_size] : 0.0;
+      logs[w] = double(s_log) * 0.69314718055994530942;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+}  // namespace tn
+
+using namespace tn;
+
+struct tn_batch_s {
+  int32_t n_nets = 0;
+  bool cplx = false, scaling = false;
+  std::vector<BNet> nets;
+  std::vector<BLeaf> leaves;
+  std::vector<BStep> steps;
+  std::vector<int64_t> leaf_offset;  // packed input offset of every leaf (+ total)
+  int64_t arena_floats = 0;
+  char* dev = nullptr;               // tables + arena + queue
+  BNet* d_nets = nullptr;
+  BLeaf* d_leaves = nullptr;
+  BStep* d_steps = nullptr;
+  float* d_arena = nullptr;
+  int32_t* d_queue = nullptr;
+  int threads = 128, ctas_per_sm = 4, num_sms = 148;
+  double flops = 0;
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_in = nullptr;
+  void* g_vals = nullptr;
+  void* g_logs = nullptr;
+  cudaStream_t g_stream = nullptr;
+};
+
+namespace {
+tn_status launch_batch(tn_batch_s* B, const void* packed, double* values, double* logs, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(B->d_queue, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) {
+    set_error(std::string("batch queue reset: ") + cudaGetErrorString(e));
+    return TN_ERR_CUDA;
+  }
+  const int grid = std::min<int64_t>(B->n_nets, (int64_t)B->num_sms * B->ctas_per_sm);
+  if (B->cplx)
+    batch_kernel<true><<<grid, B->threads, 0, st>>>(B->d_nets, B->d_leaves, B->d_steps, B->n_nets,
+                                                     static_cast<const float*>(packed), B->d_arena, B->d_queue,
+                                                     B->scaling ? 1 : 0, values, logs);
+  else
+    batch_kernel<false><<<grid, B->threads, 0, st>>>(B->d_nets, B->d_leaves, B->d_steps, B->n_nets,
+                                                      static_cast<const float*>(packed), B->d_arena, B->d_queue,
+                                                      B->scaling ? 1 : 0, values, logs);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("batch kernel launch: ") + cudaGetErrorString(e));
+    return TN_ERR_CUDA;
+  }
+  return TN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* paths, tn_dtype_policy policy,
+                        tn_batch_t* out) {
+  if (n_nets <= 0 || !nets || !paths || !out) {
+    set_error("tn_batch_plan: bad arguments");
+    return TN_ERR_INVALID;
+  }
+  if (policy.prec != TN_C64_FP32_SIMT && policy.prec != TN_R32_FP32_SIMT) {
+    set_error("tn_batch_plan: batched small networks run the FP32 form (C64_FP32_SIMT or R32_FP32_SIMT)");
+    return TN_ERR_UNSUPPORTED;
+  }
+  auto B = std::make_unique<tn_batch_s>();
+  B->n_nets = n_nets;
+  B->cplx = policy.prec == TN_C64_FP32_SIMT;
+  B->scaling = policy.exp_scaling != 0;
+  const int np = B->cplx ? 2 : 1;
+  int64_t in_off = 0;
+  tn_dtype_policy hp = policy;
+  hp.flags |= TN_PLAN_HOST_ONLY;
+  hp.max_slice_batch = 1;
+  for (int32_t w = 0; w < n_nets; ++w) {
+    Plan P;
+    std::string err;
+    tn_status s = build_plan(&nets[w], &paths[w], nullptr, 0, hp, P, err);
+    if (s != TN_OK) {
+      set_error("network " + std::to_string(w) + ": " + err);
+      return s;
+    }
+    if (!P.open_modes.empty()) {
+      set_error("tn_batch_plan: network " + std::to_string(w) + " has open labels (closed networks only)");
+      return TN_ERR_UNSUPPORTED;
+    }
+    assign_workspace(P, 1);
+    if (!P.workspace_ok) {
+      set_error("tn_batch_plan: workspace self-check failed");
+      return TN_ERR_INVALID;
+    }
+    const int64_t eb = elem_bytes(P);
+    if (P.arena_bytes / 4 > (int64_t(1) << 30)) {
+      set_error("tn_batch_plan: network too large for the batched kernel");
+      return TN_ERR_UNSUPPORTED;
+    }
+    // float offsets of each tensor's real plane (tensor bytes are eb per element)
+    auto foff = [&](int32_t t) { return static_cast<int32_t>(P.tensors[t].offset / 4); };
+    BNet bn{};
+    bn.arena = B->arena_floats;
+    bn.leaf0 = (int32_t)B->leaves.size();
+    bn.n_leaves = P.n_leaves;
+    bn.step0 = (int32_t)B->steps.size();
+    bn.n_steps = (int32_t)P.steps.size();
+    const int32_t root = P.n_leaves + (int32_t)P.steps.size() - 1;
+    bn.root = foff(root);
+    bn.root_size = (int32_t)P.tensors[root].size;
+    for (int32_t t = 0; t < P.n_leaves; ++t) {
+      const TensorRec& R = P.tensors[t];
+      const LeafDesc& d = P.leafdesc[t];
+      if (d.rank > kBMaxRank) {
+        set_error("tn_batch_plan: leaf rank too large");
+        return TN_ERR_UNSUPPORTED;
+      }
+      BLeaf L{};
+      L.src = in_off;
+      L.dst = foff(t);
+      L.size = (int32_t)R.size;
+      L.rank = d.rank;
+      for (int r = 0; r < d.rank; ++r) {
+        L.ext[r] = (int32_t)d.ext[r];
+        L.sstride[r] = (int32_t)d.sstride[r];
+      }
+      B->leaf_offset.push_back(in_off);
+      int64_t full = 1;
+      for (int32_t x : R.decl) full *= P.extent[x];
+      in_off += full;
+      B->leaves.push_back(L);
+    }
+    for (const StepRec& st : P.steps) {
+      if (st.rows.n > kBMaxDims || st.cols.n > kBMaxDims) {
+        set_error("tn_batch_plan: output interleaving too fine");
+        return TN_ERR_UNSUPPORTED;
+      }
+      BStep S{};
+      S.a = foff(st.a);
+      S.b = foff(st.b);
+      S.c = foff(st.out);
+      S.a_size = (int32_t)P.tensors[st.a].size;
+      S.b_size = (int32_t)P.tensors[st.b].size;
+      S.c_size = (int32_t)P.tensors[st.out].size;
+      S.m = (int32_t)st.m;
+      S.n = (int32_t)st.n;
+      S.k = (int32_t)st.k;
+      S.nr = (int8_t)st.rows.n;
+      S.nc = (int8_t)st.cols.n;
+      for (int d = 0; d < st.rows.n; ++d) {
+        S.rext[d] = (int32_t)st.rows.ext[d];
+        S.rstr[d] = (int32_t)st.rows.stride[d];
+      }
+      for (int d = 0; d < st.cols.n; ++d) {
+        S.cext[d] = (int32_t)st.cols.ext[d];
+        S.cstr[d] = (int32_t)st.cols.stride[d];
+      }
+      B->steps.push_back(S);
+      B->flops += (B->cplx ? 8.0 : 2.0) * double(st.m) * double(st.n) * double(st.k);
+    }
+    (void)eb;
+    (void)np;
+    B->arena_floats += (P.arena_bytes + 255) / 256 * 64;  // keep every arena 256-byte aligned
+    B->nets.push_back(bn);
+  }
+  B->leaf_offset.push_back(in_off);
+  if ((policy.flags & TN_PLAN_HOST_ONLY) == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      set_error("tn_batch_plan: no CUDA device");
+      return TN_ERR_CUDA;
+    }
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t b_nets = al(sizeof(BNet) * B->nets.size()), b_leaves = al(sizeof(BLeaf) * B->leaves.size());
+    const size_t b_steps = al(sizeof(BStep) * std::max<size_t>(1, B->steps.size()));
+    const size_t b_arena = al(sizeof(float) * B->arena_floats);
+    const size_t total = b_nets + b_leaves + b_steps + b_arena + 256;
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, total) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("tn_batch_plan: cudaMalloc failed");
+      return TN_ERR_OOM;
+    }
+    B->dev = static_cast<char*>(mem);
+    B->d_nets = reinterpret_cast<BNet*>(B->dev);
+    B->d_leaves = reinterpret_cast<BLeaf*>(B->dev + b_nets);
+    B->d_steps = reinterpret_cast<BStep*>(B->dev + b_nets + b_leaves);
+    B->d_arena = reinterpret_cast<float*>(B->dev + b_nets + b_leaves + b_steps);
+    B->d_queue = reinterpret_cast<int32_t*>(B->dev + b_nets + b_leaves + b_steps + b_arena);
+    if (cudaMemcpy(B->d_nets, B->nets.data(), sizeof(BNet) * B->nets.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(B->d_leaves, B->leaves.data(), sizeof(BLeaf) * B->leaves.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        (!B->steps.empty() && cudaMemcpy(B->d_steps, B->steps.data(), sizeof(BStep) * B->steps.size(),
+                                         cudaMemcpyHostToDevice) != cudaSuccess)) {
+      cudaFree(mem);
+      set_error("tn_batch_plan: table upload failed");
+      return TN_ERR_CUDA;
+    }
+  }
+  *out = B.release();
+  return TN_OK;
+}
+
+tn_status tn_batch_info(tn_batch_t b, int64_t* leaf_offsets, double* flops, int32_t* threads,
+                        int32_t* ctas_per_sm) {
+  if (!b) {
+    set_error("null batch");
+    return TN_ERR_INVALID;
+  }
+  if (leaf_offsets) std::copy(b->leaf_offset.begin(), b->leaf_offset.end(), leaf_offsets);
+  if (flops) *flops = b->flops;
+  if (threads) *threads = b->threads;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  return TN_OK;
+}
+
+tn_status tn_batch_contract(tn_batch_t b, const void* packed_inputs, double* values, double* log_scales,
+                            void* stream) {
+  if (!b || !b->dev || !packed_inputs || !values || !log_scales) {
+    set_error("tn_batch_contract: bad arguments (or a host-only batch)");
+    return TN_ERR_INVALID;
+  }
+  return launch_batch(b, packed_inputs, values, log_scales, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tn_status tn_batch_contract_graph(tn_batch_t b, const void* packed_inputs, double* values, double* log_scales,
+                                  void* stream) {
+  if (!b || !b->dev || !packed_inputs || !values || !log_scales) {
+    set_error("tn_batch_contract_graph: bad arguments (or a host-only batch)");
+    return TN_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!b->gexec || b->g_in != packed_inputs || b->g_vals != values || b->g_logs != log_scales ||
+      b->g_stream != st) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+      set_error("graph capture stream");
+      return TN_ERR_CUDA;
+    }
+    cudaGraph_t g = nullptr;
+    tn_status s = TN_OK;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) s = TN_ERR_CUDA;
+    if (s == TN_OK) s = launch_batch(b, packed_inputs, values, log_scales, cap);
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (s == TN_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (s != TN_OK || e != cudaSuccess) {
+      cudaGetLastError();
+      set_error(std::string("batch graph capture failed: ") + cudaGetErrorString(e));
+      return TN_ERR_CUDA;
+    }
+    b->g_in = packed_inputs;
+    b->g_vals = values;
+    b->g_logs = log_scales;
+    b->g_stream = st;
+  }
+  cudaError_t e = cudaGraphLaunch(b->gexec, st);
+  if (e != cudaSuccess) {
+    set_error(std::string("graph launch: ") + cudaGetErrorString(e));
+    return TN_ERR_CUDA;
+  }
+  return TN_OK;
+}
+
+tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* values, double* log_scales,
+                            void* stream) {
+  if (!b || !b->dev) {
+    set_error("tn_batch_autotune: bad batch");
+    return TN_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int cand_threads[] = {32, 64, 128, 256};
+  const int cand_ctas[] = {2, 4, 8, 16};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bt = b->threads, bc = b->ctas_per_sm;
+  for (int t : cand_threads)
+    for (int c : cand_ctas) {
+      if (t * c > 2048) continue;
+      b->threads = t;
+      b->ctas_per_sm = c;
+      float ms_best = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, st);
+        tn_status s = launch_batch(b, packed_inputs, values, log_scales, st);
+        cudaEventRecord(e1, st);
+        if (s != TN_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          set_error("tn_batch_autotune: a candidate failed");
+          return TN_ERR_CUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_best = std::min(ms_best, ms);
+      }
+      if (ms_best < best) {
+        best = ms_best;
+        bt = t;
+        bc = c;
+      }
+    }
+  b->threads = bt;
+  b->ctas_per_sm = bc;
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return TN_OK;
+}
+
+tn_status tn_batch_destroy(tn_batch_t b) {
+  if (!b) return TN_OK;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->dev) cudaFree(b->dev);
+  delete b;
+  return TN_OK;
+}
+
+}  // extern "C"

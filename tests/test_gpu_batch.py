@@ -1,0 +1,83 @@
+"""Many small networks in one persistent launch (tn_batch_*) against the CPU oracle.
+
+Partition functions are compared on ln Z (absolute 1e-5: FP32 arithmetic along paths
+of ~60 steps, every intermediate renormalised by an exact power of two), amplitudes at
+the relative 1e-5 bar of the other GPU tests.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests._lib import ensure_built
+from tn_inputs import circuits, greedy, ising_pf, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tn():
+    return ensure_built()
+
+
+def run_batch(tn, nets, paths, complex_=False, scaling=True, graph=False, autotune=False):
+    b = tn.Batch(nets, paths, complex_=complex_, exp_scaling=scaling)
+    packed = torch.tensor(b.pack(nets), device="cuda")
+    vals = torch.zeros((len(nets), 2), dtype=torch.float64, device="cuda")
+    logs = torch.zeros(len(nets), dtype=torch.float64, device="cuda")
+    if autotune:
+        b.autotune(packed, vals, logs)
+    b.contract(packed, vals, logs, graph=graph)
+    torch.cuda.synchronize()
+    v, l = vals.cpu().numpy(), logs.cpu().numpy()
+    return b, v, l
+
+
+def test_ising_ensemble_lnz(tn):
+    ws = workloads.ising3r(128, seed=11)
+    b, v, l = run_batch(tn, [w.net for w in ws], [w.path for w in ws])
+    for i, w in enumerate(ws):
+        want = oracle.contract(w.net, w.path)
+        assert v[i, 0] > 0
+        assert abs(np.log(v[i, 0]) + l[i] - np.log(want)) < 1e-5, i
+
+
+def test_overflowing_rings_need_scaling(tn):
+    """Rings of 200-400 spins at beta = 1: Z ~ 1e100-1e200 (beyond FP32 and, for some,
+    FP64 without the log scale); checked against the transfer-matrix closed form."""
+    nets, paths, want = [], [], []
+    for n in (200, 300, 400):
+        net = ising_pf.ring_network(n, 1.0, 1.0)
+        nets.append(net)
+        paths.append(greedy.greedy_path(net, seed=0))
+        want.append(n * np.log(2 * np.cosh(1.0)) + np.log1p(np.tanh(1.0) ** n))
+    b, v, l = run_batch(tn, nets, paths)
+    for i in range(3):
+        assert abs(np.log(v[i, 0]) + l[i] - want[i]) < 1e-5 * want[i]
+
+
+@pytest.mark.parametrize("scaling", [False, True])
+def test_complex_amplitudes(tn, scaling):
+    nets, paths = [], []
+    for s in range(24):
+        net = circuits.amplitude_network(3, 3, 8, 100 + s)
+        nets.append(net)
+        paths.append(greedy.greedy_path(net, seed=s, alpha=1.0))
+    b, v, l = run_batch(tn, nets, paths, complex_=True, scaling=scaling)
+    for i in range(len(nets)):
+        got = complex(v[i, 0], v[i, 1]) * np.exp(l[i])
+        want = oracle.contract(nets[i], paths[i])
+        assert abs(got - want) / abs(want) < 1e-5, i
+
+
+def test_graph_replay_and_autotune_match(tn):
+    ws = workloads.ising3r(64, seed=12)
+    nets, paths = [w.net for w in ws], [w.path for w in ws]
+    _, v0, l0 = run_batch(tn, nets, paths)
+    _, v1, l1 = run_batch(tn, nets, paths, graph=True)
+    b2, v2, l2 = run_batch(tn, nets, paths, autotune=True, graph=True)
+    t, c = b2.launch_shape()
+    assert t in (32, 64, 128, 256) and c in (2, 4, 8, 16)
+    # same per-network arithmetic whatever the launch shape: bitwise equal
+    assert np.array_equal(v0, v1) and np.array_equal(l0, l1)
+    assert np.array_equal(v0, v2) and np.array_equal(l0, l2)

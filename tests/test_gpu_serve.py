@@ -1,0 +1,124 @@
+"""The serve loop (tn_serve_*): continuous admission, results independent of the mix,
+refusals returned as statuses."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2606_01852_gb300  # noqa: F401  (built by the fixture)
+from tests._lib import ensure_built
+from tn_inputs import circuits, greedy, ising_pf, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tn():
+    return ensure_built()
+
+
+def amp_requests(n, seed=0):
+    """n amplitude requests of one 3x4 circuit with different bitstrings (one plan)."""
+    rng = np.random.default_rng(seed)
+    nets = []
+    for _ in range(n):
+        bits = tuple(int(b) for b in rng.integers(0, 2, size=12))
+        nets.append(circuits.amplitude_network(3, 4, 8, 12, bitstring=bits))
+    return nets
+
+
+def host_inputs(net, cplx=True):
+    dt = np.complex64 if cplx else np.float32
+    return [np.ascontiguousarray(np.asarray(t, dtype=dt)) for t in net.tensors]
+
+
+def test_mixed_results_equal_alone(tn):
+    amps = amp_requests(24)
+    path = greedy.greedy_path(amps[0], seed=0, alpha=1.0)
+    p_amp = tn.Plan(amps[0], path)
+    ising = [ising_pf.random_3regular_network(n, s) for n, s in ((20, 1), (40, 2), (60, 3))]
+    i_paths = [greedy.greedy_path(n, seed=0, alpha=1.0) for n in ising]
+    p_ising = [tn.Plan(n, p, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True) for n, p in zip(ising, i_paths)]
+    big = workloads.random_circuit(4, 5, 12, 40)
+    p_big = tn.Plan(big.net, big.path, prec="3xtf32")
+
+    jobs = [(p_amp, n, True) for n in amps] + [(p, n, False) for p, n in zip(p_ising, ising)]
+    jobs += [(p_big, big.net, True)] * 2
+    rng = np.random.default_rng(3)
+    order = rng.permutation(len(jobs))
+    # alone: the synchronous host entry point, one at a time
+    alone = {}
+    for j in order:
+        plan, net, cplx = jobs[j]
+        out = np.zeros((), dtype=np.complex128 if cplx else np.float64)
+        ls = np.zeros(1)
+        plan.contract_host(host_inputs(net, cplx), out, ls)
+        alone[j] = (out.copy(), ls[0])
+    srv = tn.Server(max_inflight=6, n_streams=3)
+    tickets = {}
+    for j in order:
+        plan, net, cplx = jobs[j]
+        tickets[j] = srv.submit(plan, host_inputs(net, cplx))
+    for j, t in tickets.items():
+        plan, net, cplx = jobs[j]
+        out = np.zeros((), dtype=np.complex128 if cplx else np.float64)
+        ls = np.zeros(1)
+        assert srv.poll(t, out, ls, timeout_us=-1) == tn.TN_OK
+        # same launch sequence on the same data: bit-for-bit the same result
+        assert out == alone[j][0] and ls[0] == alone[j][1], j
+    srv.destroy()
+    # and the values are right
+    for j in (0, 7, 23):
+        want = oracle.contract(amps[j], path)
+        assert abs(complex(alone[j][0]) - want) / abs(want) < 1e-5
+    for j in range(3):
+        v, ls = alone[len(amps) + j]
+        assert abs(np.log(v) + ls - np.log(oracle.contract(ising[j], i_paths[j]))) < 1e-5
+
+
+def test_busy_and_unknown_ticket(tn):
+    big = workloads.random_circuit(4, 5, 12, 40)
+    p_big = tn.Plan(big.net, big.path, prec="fp32")
+    srv = tn.Server(max_inflight=1, n_streams=1, queue_capacity=1)
+    ins = host_inputs(big.net)
+    saw_busy = False
+    tickets = []
+    for _ in range(200):
+        s, t = srv.try_submit(p_big, ins)
+        if s == tn.TN_ERR_BUSY:
+            saw_busy = True
+            break
+        assert s == tn.TN_OK
+        tickets.append(t)
+    assert saw_busy
+    out = np.zeros((), dtype=np.complex128)
+    assert srv.poll(10**12, out) == tn.TN_ERR_INVALID
+    for t in tickets:
+        assert srv.poll(t, out, timeout_us=-1) == tn.TN_OK
+    srv.destroy()
+
+
+def test_hbm_budget_refusal(tn):
+    big = workloads.random_circuit(4, 5, 12, 40)
+    p_big = tn.Plan(big.net, big.path, prec="fp32")
+    srv = tn.Server(max_inflight=2, n_streams=1, hbm_budget_bytes=1024)
+    t = srv.submit(p_big, host_inputs(big.net))
+    out = np.zeros((), dtype=np.complex128)
+    assert srv.poll(t, out, timeout_us=-1) == tn.TN_ERR_OOM
+    srv.destroy()
+
+
+def test_poll_not_ready_then_done(tn):
+    big = workloads.random_circuit(4, 5, 12, 40)
+    p_big = tn.Plan(big.net, big.path, prec="fp32")
+    srv = tn.Server(max_inflight=1, n_streams=1)
+    t = srv.submit(p_big, host_inputs(big.net))
+    out = np.zeros((), dtype=np.complex128)
+    s = srv.poll(t, out, timeout_us=0)
+    assert s in (tn.TN_ERR_NOT_READY, tn.TN_OK)
+    if s == tn.TN_ERR_NOT_READY:
+        assert srv.poll(t, out, timeout_us=-1) == tn.TN_OK
+    want = oracle.contract(big.net, big.path)
+    assert abs(complex(out) - want) / abs(want) < 1e-5
+    srv.destroy()
