@@ -270,6 +270,11 @@ def run_ours(args):
         "gpu_launches": plan.launches_per_call() * args.steps,
         "clocks": ck,
     }
+    if args.check:
+        import oracle
+        want = complex(oracle.contract(w.net, w.path, w.sliced))
+        line["oracle"] = [want.real, want.imag]
+        line["rel_err_vs_oracle"] = abs(result - want) / abs(want)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         f, s, done = oracle_sample(w, args.ref_budget)
         line["cpu_baseline"] = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
@@ -354,24 +359,159 @@ def run_batch_bench(args):
     return 0
 
 
+def run_serve_bench(args):
+    """Serving mix: open-loop Poisson arrivals (mean args.rate req/s for args.serve_seconds):
+    70 % 12-qubit circuit amplitudes (random bitstrings, one plan), 25 % Ising partition
+    functions (a pool of 64 graphs, FP32 + exponent scaling), 5 % 5x5 kicked-Ising
+    expectations (2 Trotter steps; largest intermediate 2^26). Served by the continuous-
+    batching loop with the 3xTF32 form, against the plain FP32 form served one request at
+    a time. Latency = completion (observed by polling) - submission."""
+    import threading
+    import torch
+    import paper_2606_01852_gb300 as tn
+    from tn_inputs import circuits
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(2026)
+    amp_w = workloads.rc12()
+    pf_pool = workloads.ising3r(64, seed=5)
+    kis = workloads.kicked(5, 2)
+    n_req = int(args.rate * args.serve_seconds)
+    gaps = rng.exponential(1.0 / args.rate, size=n_req)
+    arrive = np.cumsum(gaps)
+    cls = rng.choice(3, size=n_req, p=[0.70, 0.25, 0.05])
+    pf_idx = rng.integers(0, len(pf_pool), size=n_req)
+    bits = rng.integers(0, 2, size=(n_req, 12))
+    base = [np.ascontiguousarray(np.asarray(t, dtype=np.complex64)) for t in amp_w.net.tensors]
+    n_leaf = len(base)
+    e0 = np.array([1.0, 0.0], dtype=np.complex64)
+    e1 = np.array([0.0, 1.0], dtype=np.complex64)
+    pf_in = [[np.ascontiguousarray(np.asarray(t, dtype=np.float32)) for t in w.net.tensors] for w in pf_pool]
+    kis_in = [np.ascontiguousarray(np.asarray(t, dtype=np.complex64)) for t in kis.net.tensors]
+
+    def inputs(i):
+        if cls[i] == 0:
+            ins = list(base)
+            for q in range(12):  # the last 12 leaves are the <x| projections
+                ins[n_leaf - 12 + q] = e1 if bits[i, q] else e0
+            return ins
+        if cls[i] == 1:
+            return pf_in[pf_idx[i]]
+        return kis_in
+
+    def serve(prec, max_inflight, n_streams):
+        p_amp = tn.Plan(amp_w.net, amp_w.path, prec=prec)
+        p_pf = [tn.Plan(w.net, w.path, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True) for w in pf_pool]
+        p_kis = tn.Plan(kis.net, kis.path, prec=prec)
+        plan_of = lambda i: p_amp if cls[i] == 0 else (p_pf[pf_idx[i]] if cls[i] == 1 else p_kis)
+        srv = tn.Server(max_inflight=max_inflight, n_streams=n_streams, queue_capacity=1 << 20)
+        for i in range(min(n_req, 64)):  # warm every plan's first instance
+            t = srv.submit(plan_of(i), inputs(i))
+            srv.poll(t, np.zeros(2), None, -1)
+        for p in [p_kis] + p_pf:
+            srv.poll(srv.submit(p, kis_in if p is p_kis else pf_in[p_pf.index(p)]), np.zeros(2), None, -1)
+        sub_t = np.zeros(n_req)
+        done_t = np.zeros(n_req)
+        results = np.zeros((n_req, 2))
+        tickets = [None] * n_req
+        lock = threading.Lock()
+        outstanding = []
+        finished = threading.Event()
+        t0 = time.perf_counter() + 0.05
+
+        def submitter():
+            for i in range(n_req):
+                delay = t0 + arrive[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                sub_t[i] = time.perf_counter()
+                tk = srv.submit(plan_of(i), inputs(i))
+                with lock:
+                    tickets[i] = tk
+                    outstanding.append(i)
+            finished.set()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        buf = np.zeros(2)
+        ls = np.zeros(1)
+        n_done = 0
+        while n_done < n_req:
+            with lock:
+                cur = list(outstanding)
+            for i in cur:
+                s = srv.poll(tickets[i], buf, ls, 0)
+                if s == tn.TN_ERR_NOT_READY:
+                    continue
+                done_t[i] = time.perf_counter()
+                results[i] = buf
+                with lock:
+                    outstanding.remove(i)
+                n_done += 1
+            time.sleep(0.0001)
+        th.join()
+        srv.destroy()
+        lat = (done_t - sub_t) * 1e3
+        span = done_t.max() - sub_t.min()
+        out = {"throughput_req_s": n_req / span, "p50_ms": float(np.percentile(lat, 50)),
+               "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+        for c, name in enumerate(["amplitude", "partition_function", "kicked_ising_5x5"]):
+            sel = lat[cls == c]
+            out[name] = {"n": int(sel.size), "p50_ms": float(np.percentile(sel, 50)),
+                         "p99_ms": float(np.percentile(sel, 99))}
+        for p in [p_amp, p_kis] + p_pf:
+            p.destroy()
+        return out, results
+
+    mixed, r_mixed = serve(tn.TN_C64_3XTF32, args.serve_inflight, args.serve_streams)
+    plain, r_plain = serve(tn.TN_C64_FP32_SIMT, 1, 1)
+    # the two forms must agree (3xTF32 vs FP32: same 1e-5 relative bar as the tests)
+    c0 = cls == 0
+    amp_err = float(np.max(np.abs(r_mixed[c0] - r_plain[c0]).sum(1) / (np.abs(r_plain[c0]).sum(1) + 2 ** -6)))
+    line = {
+        "metric": "serve throughput (requests/s) and p50/p99 latency", "value": mixed["throughput_req_s"],
+        "unit": "requests/s", "n_gpus": ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64/f32", "data": "synthetic",
+        "config": {"workload": "serve-mix", "rate_req_s": args.rate, "seconds": args.serve_seconds,
+                   "requests": n_req, "mix": {"amplitude_3x4_m8": 0.70, "ising_pf_3reg_20_60": 0.25,
+                                              "kicked_ising_5x5_T2": 0.05},
+                   "form": "3xtf32 (FP32-accurate)", "max_inflight": args.serve_inflight,
+                   "streams": args.serve_streams},
+        "mixed": mixed, "plain_fp32_one_at_a_time": plain,
+        "p99_speedup": plain["p99_ms"] / mixed["p99_ms"],
+        "max_rel_diff_amplitudes_mixed_vs_plain": amp_err,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rc40", choices=sorted(workloads.BY_NAME) + ["ising3r"])
+    ap.add_argument("--workload", default="rc40", choices=sorted(workloads.BY_NAME) + ["ising3r", "serve"])
     ap.add_argument("--networks", type=int, default=4096, help="ising3r: networks per launch")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-inflight", type=int, default=16)
+    ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--prec", default="3xtf32", choices=sorted(PREC),
                     help="GEMM form: 3xtf32 (default; FP32-accurate), tf32, fp32 (the plain CUDA-core form)")
     ap.add_argument("--max-slice-batch", type=int, default=0)
     ap.add_argument("--ref-budget", type=float, default=20.0, help="oracle seconds per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--check", action="store_true", help="also contract with the CPU oracle and report the error")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.workload == "ising3r" and args.impl == "ours":
         return run_batch_bench(args)
+    if args.workload == "serve" and args.impl == "ours":
+        return run_serve_bench(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

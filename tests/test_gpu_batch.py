@@ -64,10 +64,14 @@ def test_complex_amplitudes(tn, scaling):
         nets.append(net)
         paths.append(greedy.greedy_path(net, seed=s, alpha=1.0))
     b, v, l = run_batch(tn, nets, paths, complex_=True, scaling=scaling)
+    # Amplitudes of a normalised 9-qubit state are ~2^-4.5 in size; one that happens to
+    # be much smaller comes out of cancellation between terms of that size, so FP32
+    # rounding bounds its error relative to the typical size, not to itself.
+    typical = 2.0 ** (-9 / 2)
     for i in range(len(nets)):
         got = complex(v[i, 0], v[i, 1]) * np.exp(l[i])
         want = oracle.contract(nets[i], paths[i])
-        assert abs(got - want) / abs(want) < 1e-5, i
+        assert abs(got - want) / max(abs(want), typical) < 1e-5, i
 
 
 def test_graph_replay_and_autotune_match(tn):
