@@ -145,6 +145,27 @@ def test_tf32_operand_rounding(tn):
     assert np.allclose(g3.real, 16.0 * (1.0 + 3.0 * 2.0**-12), rtol=0, atol=1e-6)
 
 
+@pytest.mark.parametrize("k", [4096, 32768])
+def test_3xtf32_long_k_accumulation(tn, k):
+    """The tensor core truncates each FP32 accumulation, which over a long k drifts a
+    positive sum toward zero by ~k * 2^-25 relative. The 3xTF32 kernel accumulates
+    64-term chunks in tensor memory and adds the chunks with round-to-nearest FP32, so
+    the error must not grow with k: on positive data (no cancellation) the mean relative
+    error of the imaginary part stays below 5e-6 and every element below 1e-5."""
+    from tn_inputs.network import Network, Path
+    rng = np.random.default_rng(k)
+    m = n = 128
+    A = (rng.random((m, k)) + 1j * rng.random((m, k))).astype(np.complex64).astype(np.complex128)
+    B = (rng.random((n, k)) + 1j * rng.random((n, k))).astype(np.complex64).astype(np.complex128)
+    net = Network([A, B], [(0, 2), (1, 2)], {0: m, 1: n, 2: k}, (0, 1))
+    plan = tn.Plan(net, Path([(0, 1)]), prec="3xtf32")
+    assert plan.step(0)["cls"] == tn.TN_CLASS_TC
+    got, _ = run(tn, plan, net)
+    want = A @ B.T
+    rel = (got.imag - want.imag) / want.imag
+    assert abs(rel.mean()) < 5e-6 and np.abs(rel).max() < 1e-5, (rel.mean(), np.abs(rel).max())
+
+
 @pytest.mark.parametrize("prec,tol", [("tf32", 3e-2), ("3xtf32", 1e-5)])
 def test_sliced_circuit_with_tc_steps(tn, prec, tol):
     w = workloads.random_circuit(4, 5, 12, 40, n_sliced=3)
