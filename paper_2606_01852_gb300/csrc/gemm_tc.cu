@@ -374,39 +374,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 //
 // The tensor core's FP32 accumulator truncates each addition, so a long TMEM
 // accumulation drifts toward zero by ~k * 2^-25 relative (measured). Here the MMAs
-// accumulate only CK k-blocks (CK * 16 terms) into a chunk accumulator; two chunk
-// buffers alternate, and four drain warps add each finished chunk into running
-// totals kept in TMEM with ordinary round-to-nearest FP32 additions while the MMAs
-// fill the other buffer. Tile 128 x 64 so that both chunk buffers and the running
-// totals fit the 512 TMEM columns: chunk u re @128u, im @128u+64; totals re @256, im @320.
-// Re C = sum ar.br + (-ai).bi uses the instruction's negate-A bit; Im C = ar.bi + ai.br.
-// Warps: 0 TMA, 1 MMA, 2-5 hi/lo split, 6-9 drain + epilogue (320 threads).
+// accumulate only CK k-blocks (CK * 16 terms) into the TMEM chunk accumulator
+// (re @0, im @128; Re uses the instruction's negate-A bit for -A_im.B_im); eight
+// warps then add the chunk into running totals held in their registers with ordinary
+// round-to-nearest FP32 additions, and release the accumulator for the next chunk.
+// The same eight warps split every staged tile into hi/lo (so the MMA pipe waits only
+// for the short drain), and finally write the totals out. 128 x 128 tiles: the kernel is
+// bound by shared-memory operand reads (each 3xTF32 MMA re-reads its tiles), so the
+// wide tile keeps reads per flop low.
+// Warps: 0 TMA, 1 MMA + TMEM, 2-9 split / drain / epilogue (320 threads); warp w of
+// 2-9 drains TMEM lane quarter w % 4, columns 64 * ((w - 2) / 4) .. +63.
 
 struct C3 {
-  static constexpr int BN3 = 64, BK = 16, ROWB = 64, CK = 4;
+  static constexpr int BK = 16, ROWB = 64, CK = 4;
   static constexpr int TILE_A = BM * ROWB;                  // 8 KiB
-  static constexpr int TILE_B = BN3 * ROWB;                 // 4 KiB
-  static constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;     // 24 KiB
-  static constexpr int STAGES = 6, LO = 2;
+  static constexpr int TILE_B = BN * ROWB;                  // 8 KiB
+  static constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;     // 32 KiB
+  static constexpr int STAGES = 4, LO = 2;
   static constexpr int THREADS = 320;
   static constexpr int SMEM = (STAGES + LO) * STAGE + 1024 + 1024;
+  static constexpr uint32_t COLS = 256;
 };
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
-      "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]),
-      "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]),
-      "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
-      : "memory");
-}
 
 __global__ void __launch_bounds__(C3::THREADS, 1)
     contract_tc3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         StepArgs a, int* err) {
-  constexpr int STAGES = C3::STAGES, BK = C3::BK, ROWB = C3::ROWB, BN3 = C3::BN3, CK = C3::CK;
+  constexpr int STAGES = C3::STAGES, BK = C3::BK, ROWB = C3::ROWB, CK = C3::CK;
   constexpr int TILE_A = C3::TILE_A, TILE_B = C3::TILE_B, STAGE = C3::STAGE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -416,18 +409,18 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
   uint64_t* empty = bars + STAGES;           // [STAGES]
   uint64_t* conv_full = bars + 2 * STAGES;   // [2]
   uint64_t* lo_empty = conv_full + 2;        // [2]
-  uint64_t* acc_full = lo_empty + 2;         // [2] chunk buffer ready to drain
-  uint64_t* acc_empty = acc_full + 2;        // [2] chunk buffer drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* acc_full = lo_empty + 2;         // chunk accumulated
+  uint64_t* acc_empty = acc_full + 1;        // chunk drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN3 - 1) / BN3;
+  const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
   const int64_t t = blockIdx.x;
   const int64_t per_group = GROUP_M * tiles_n;
   const int64_t first_m = (t / per_group) * GROUP_M;
   const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
   const int64_t tm = first_m + (t % per_group) % gm, tn = (t % per_group) / gm;
-  const int m0 = static_cast<int>(tm * BM), n0 = static_cast<int>(tn * BN3);
+  const int m0 = static_cast<int>(tm * BM), n0 = static_cast<int>(tn * BN);
   const int b = blockIdx.y;
   const int num_kb = static_cast<int>((a.k + BK - 1) / BK);
   const int n_chunks = (num_kb + CK - 1) / CK;
@@ -439,18 +432,18 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
       mbar_init(&empty[s], 1);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&conv_full[i], 128);
+      mbar_init(&conv_full[i], 256);
       mbar_init(&lo_empty[i], 1);
-      mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 4);
     }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 8);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                 "r"(TMEM_COLS));
+                 "r"(C3::COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -481,17 +474,16 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(BM, BN3);
+      constexpr uint32_t idesc = idesc_tf32(BM, BN);
       constexpr uint32_t idesc_neg = idesc | (1u << 13);  // D += (-A) . B
+      const uint32_t d_re = tmem, d_im = tmem + 128;
       bool ok = true;
       for (int c = 0; c < n_chunks && ok; ++c) {
-        const int u = c & 1;
-        if (!mbar_wait(&acc_empty[u], ((c >> 1) & 1) ^ 1)) {
+        if (!mbar_wait(acc_empty, (c & 1) ^ 1)) {
           atomicExch(err, 13);
           break;
         }
         fence_after();
-        const uint32_t d_re = tmem + 128 * u, d_im = tmem + 128 * u + 64;
         const int kb_end = min(num_kb, (c + 1) * CK);
         for (int kb = c * CK; kb < kb_end; ++kb) {
           const int s = kb % STAGES;
@@ -528,96 +520,101 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
           mma_commit(&empty[s]);
           mma_commit(&lo_empty[kb & 1]);
         }
-        mma_commit(&acc_full[u]);  // also on error, so the drain sees issued MMAs retire
+        mma_commit(acc_full);  // also on error, so the drain sees issued MMAs retire
       }
-    }
-  } else if (warp < 6) {
-    const int et = threadIdx.x - 64;  // 0..127: the hi/lo split
-    for (int kb = 0; kb < num_kb; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(&lo_empty[kb & 1], ((kb >> 1) & 1) ^ 1)) {
-        atomicExch(err, 15);
-        break;
-      }
-      float4* src = reinterpret_cast<float4*>(smem + s * STAGE);
-      float4* dst = reinterpret_cast<float4*>(lo_base + (kb & 1) * STAGE);
-#pragma unroll 4
-      for (int i = et; i < STAGE / 16; i += 128) {
-        const float4 v = src[i];
-        float4 h, l;
-        h.x = tf32_trunc(v.x);
-        h.y = tf32_trunc(v.y);
-        h.z = tf32_trunc(v.z);
-        h.w = tf32_trunc(v.w);
-        l.x = v.x - h.x;
-        l.y = v.y - h.y;
-        l.z = v.z - h.z;
-        l.w = v.w - h.w;
-        src[i] = h;
-        dst[i] = l;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&conv_full[kb & 1]);
     }
   } else {
-    // drain: fold every finished chunk into the running totals (round-to-nearest)
-    const int q = warp & 3;
+    const int et = threadIdx.x - 64;  // 0..255
+    const int q = warp & 3, half = (warp - 2) >> 2;
     const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    float run_re[64], run_im[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) run_re[i] = run_im[i] = 0.f;
     bool ok = true;
-    for (int c = 0; c < n_chunks; ++c) {
-      const int u = c & 1;
-      if (!mbar_wait(&acc_full[u], (c >> 1) & 1)) {
+    // fold chunk c of the TMEM accumulator into the register totals, then release it
+    auto drain = [&](int c) {
+      if (!ok) return;
+      if (!mbar_wait(acc_full, c & 1)) {
         atomicExch(err, 16);
         ok = false;
-        break;
+        return;
       }
       fence_after();
-#pragma unroll 1
-      for (int part = 0; part < 4; ++part) {  // re cols 0-31, 32-63, im cols 0-31, 32-63
-        const uint32_t col = (part < 2 ? 0 : 64) + (part & 1) * 32;
-        float v[32], r[32];
-        tmem_ld32(tmem + lane_base + 128 * u + col, v);
-        if (c > 0) {
-          tmem_ld32(tmem + lane_base + 256 + col, r);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += r[i];
-        }
-        tmem_st32(tmem + lane_base + 256 + col, v);
+      for (int p = 0; p < 2; ++p) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + half * 64 + p * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+        tmem_ld32(tmem + lane_base + 128 + half * 64 + p * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
       }
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[u]);
+      if (lane == 0) mbar_arrive(acc_empty);
+    };
+    for (int kb = 0; kb < num_kb; ++kb) {
+      const int s = kb % STAGES;
+      if (ok && (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(&lo_empty[kb & 1], ((kb >> 1) & 1) ^ 1))) {
+        atomicExch(err, 15);
+        ok = false;
+      }
+      if (ok) {
+        float4* src = reinterpret_cast<float4*>(smem + s * STAGE);
+        float4* dst = reinterpret_cast<float4*>(lo_base + (kb & 1) * STAGE);
+#pragma unroll 4
+        for (int i = et; i < STAGE / 16; i += 256) {
+          const float4 v = src[i];
+          float4 h, l;
+          h.x = tf32_trunc(v.x);
+          h.y = tf32_trunc(v.y);
+          h.z = tf32_trunc(v.z);
+          h.w = tf32_trunc(v.w);
+          l.x = v.x - h.x;
+          l.y = v.y - h.y;
+          l.z = v.z - h.z;
+          l.w = v.w - h.w;
+          src[i] = h;
+          dst[i] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&conv_full[kb & 1]);
+      }
+      // one k-block into chunk c+1 is split, so the MMA pipe can restart at once
+      if (kb % CK == 0 && kb > 0) drain(kb / CK - 1);
     }
-    // epilogue from the running totals
-    fence_after();
+    drain(n_chunks - 1);
+    // epilogue: thread = TMEM lane (row); this warp's 64 columns
     const int row = q * 32 + lane;
     const int64_t m = static_cast<int64_t>(m0) + row;
     const bool row_ok = ok && m < a.m;
     const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
     const bool rows_unit = a.rows.n > 0 && a.rows.stride[a.rows.n - 1] == 1;
-    float* tr = reinterpret_cast<float*>(smem) + (warp - 6) * 2 * 32 * 33;  // [2][32][33]
-    for (int cb = 0; cb < BN3 / 32; ++cb) {
-      float re[32], im[32];
-      tmem_ld32(tmem + lane_base + 256 + cb * 32, re);
-      tmem_ld32(tmem + lane_base + 320 + cb * 32, im);
-      const int64_t nb0 = static_cast<int64_t>(n0) + cb * 32;
-      if (rows_unit) {
-        if (!row_ok) continue;
+    // The stage buffers are free here: this warp's last drain waited for the final MMA,
+    // which waited for every warp's last split; no TMA load is outstanding.
+    float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 33;  // [2][32][33]
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t n = nb0 + j;
-          if (n >= a.n) break;
-          const int64_t off = ro + map_off(a.cols, n);
-          C[off] = re[j];
-          C[a.c_plane + off] = im[j];
+    for (int cb = 0; cb < 2; ++cb) {
+      const int64_t nb0 = static_cast<int64_t>(n0) + half * 64 + cb * 32;
+      if (rows_unit) {
+        if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t n = nb0 + j;
+            if (n < a.n) {
+              const int64_t off = ro + map_off(a.cols, n);
+              C[off] = run_re[cb * 32 + j];
+              C[a.c_plane + off] = run_im[cb * 32 + j];
+            }
+          }
         }
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          tr[lane * 33 + j] = re[j];
-          tr[32 * 33 + lane * 33 + j] = im[j];
+          tr[lane * 33 + j] = run_re[cb * 32 + j];
+          tr[32 * 33 + lane * 33 + j] = run_im[cb * 32 + j];
         }
         __syncwarp();
         const int64_t n = nb0 + lane;
@@ -639,7 +636,7 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C3::COLS));
   }
 }
 
@@ -706,9 +703,9 @@ cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
   const int64_t pa = a.a_bstride ? 2 * static_cast<int64_t>(nb) : 2;
   const int64_t pb = a.b_bstride ? 2 * static_cast<int64_t>(nb) : 2;
   if (!make_map(&ta, a.A, a.m, a.k, pa, a.a_plane, BM, C3::BK) ||
-      !make_map(&tb, a.B, a.n, a.k, pb, a.b_plane, C3::BN3, C3::BK))
+      !make_map(&tb, a.B, a.n, a.k, pb, a.b_plane, BN, C3::BK))
     return cudaErrorInvalidValue;
-  const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + C3::BN3 - 1) / C3::BN3);
+  const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
   dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));
   contract_tc3_kernel<<<grid, C3::THREADS, C3::SMEM, st>>>(ta, tb, a, err);
   return cudaGetLastError();
