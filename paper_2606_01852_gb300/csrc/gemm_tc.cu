@@ -393,7 +393,7 @@ struct C3 {
   static constexpr int STAGES = 4, LO = 2;
   static constexpr int THREADS = 320;
   static constexpr int SMEM = (STAGES + LO) * STAGE + 1024 + 1024;
-  static constexpr uint32_t COLS = 256;
+  static constexpr uint32_t COLS = 512;  // re @0, im @128, re_lo @256, im_lo @384
 };
 
 __global__ void __launch_bounds__(C3::THREADS, 1)
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_tf32(BM, BN);
       constexpr uint32_t idesc_neg = idesc | (1u << 13);  // D += (-A) . B
-      const uint32_t d_re = tmem, d_im = tmem + 128;
+      const uint32_t d_re = tmem, d_im = tmem + 128, d_re_lo = tmem + 256, d_im_lo = tmem + 384;
       bool ok = true;
       for (int c = 0; c < n_chunks && ok; ++c) {
         if (!mbar_wait(acc_empty, (c & 1) ^ 1)) {
@@ -504,18 +504,20 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
             const uint64_t arl = smem_desc<ROWB>(lo + j * 32), ail = smem_desc<ROWB>(lo + TILE_A + j * 32);
             const uint64_t brl = smem_desc<ROWB>(lo + 2 * TILE_A + j * 32);
             const uint64_t bil = smem_desc<ROWB>(lo + 2 * TILE_A + TILE_B + j * 32);
+            // hi.hi products into the main accumulators; the small cross terms into their
+            // own, so the main sums take only two truncating additions per 8 terms
             mma_tf32(d_re, ar, br, idesc, acc);
             mma_tf32(d_re, ai, bi, idesc_neg, 1u);
-            mma_tf32(d_re, arl, br, idesc, 1u);
-            mma_tf32(d_re, ar, brl, idesc, 1u);
-            mma_tf32(d_re, ail, bi, idesc_neg, 1u);
-            mma_tf32(d_re, ai, bil, idesc_neg, 1u);
             mma_tf32(d_im, ar, bi, idesc, acc);
             mma_tf32(d_im, ai, br, idesc, 1u);
-            mma_tf32(d_im, arl, bi, idesc, 1u);
-            mma_tf32(d_im, ar, bil, idesc, 1u);
-            mma_tf32(d_im, ail, br, idesc, 1u);
-            mma_tf32(d_im, ai, brl, idesc, 1u);
+            mma_tf32(d_re_lo, arl, br, idesc, acc);
+            mma_tf32(d_re_lo, ar, brl, idesc, 1u);
+            mma_tf32(d_re_lo, ail, bi, idesc_neg, 1u);
+            mma_tf32(d_re_lo, ai, bil, idesc_neg, 1u);
+            mma_tf32(d_im_lo, arl, bi, idesc, acc);
+            mma_tf32(d_im_lo, ar, bil, idesc, 1u);
+            mma_tf32(d_im_lo, ail, br, idesc, 1u);
+            mma_tf32(d_im_lo, ai, brl, idesc, 1u);
           }
           mma_commit(&empty[s]);
           mma_commit(&lo_empty[kb & 1]);
@@ -531,36 +533,20 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
 #pragma unroll
     for (int i = 0; i < 64; ++i) run_re[i] = run_im[i] = 0.f;
     bool ok = true;
-    // fold chunk c of the TMEM accumulator into the register totals, then release it
-    auto drain = [&](int c) {
-      if (!ok) return;
-      if (!mbar_wait(acc_full, c & 1)) {
-        atomicExch(err, 16);
-        ok = false;
-        return;
+    for (int kb = 0; kb <= num_kb; ++kb) {
+      // Fold chunk dc of the TMEM accumulators into the register totals and release
+      // them: once one k-block into the next chunk is split (so the MMA pipe restarts at
+      // once), and after the last k-block.
+      const int dc = kb == num_kb ? n_chunks - 1 : (kb % CK == 0 && kb > 0 ? kb / CK - 1 : -1);
+      if (kb < num_kb) {
+        const int s = kb % STAGES;
+        if (ok && (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(&lo_empty[kb & 1], ((kb >> 1) & 1) ^ 1))) {
+          atomicExch(err, 15);
+          ok = false;
+        }
       }
-      fence_after();
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        float v[32];
-        tmem_ld32(tmem + lane_base + half * 64 + p * 32, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
-        tmem_ld32(tmem + lane_base + 128 + half * 64 + p * 32, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
-      }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
-    };
-    for (int kb = 0; kb < num_kb; ++kb) {
-      const int s = kb % STAGES;
-      if (ok && (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(&lo_empty[kb & 1], ((kb >> 1) & 1) ^ 1))) {
-        atomicExch(err, 15);
-        ok = false;
-      }
-      if (ok) {
+      if (kb < num_kb && ok) {
+        const int s = kb % STAGES;
         float4* src = reinterpret_cast<float4*>(smem + s * STAGE);
         float4* dst = reinterpret_cast<float4*>(lo_base + (kb & 1) * STAGE);
 #pragma unroll 4
@@ -581,10 +567,35 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&conv_full[kb & 1]);
       }
-      // one k-block into chunk c+1 is split, so the MMA pipe can restart at once
-      if (kb % CK == 0 && kb > 0) drain(kb / CK - 1);
+      if (dc >= 0 && ok) {
+        if (!mbar_wait(acc_full, dc & 1)) {
+          atomicExch(err, 16);
+          ok = false;
+        } else {
+          fence_after();
+          float v[32];
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            const uint32_t col = lane_base + half * 64 + p * 32;
+            tmem_ld32(tmem + col, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+            tmem_ld32(tmem + 256 + col, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+            tmem_ld32(tmem + 128 + col, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+            tmem_ld32(tmem + 384 + col, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+          }
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty);
+        }
+      }
     }
-    drain(n_chunks - 1);
     // epilogue: thread = TMEM lane (row); this warp's 64 columns
     const int row = q * 32 + lane;
     const int64_t m = static_cast<int64_t>(m0) + row;
