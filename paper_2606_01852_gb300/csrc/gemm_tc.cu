@@ -549,19 +549,17 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
         const int s = kb % STAGES;
         float4* src = reinterpret_cast<float4*>(smem + s * STAGE);
         float4* dst = reinterpret_cast<float4*>(lo_base + (kb & 1) * STAGE);
+        // kind::tf32 reads an FP32 operand by dropping its low 13 mantissa bits (checked by
+        // tests/test_gpu_tc.py::test_tf32_operand_rounding), so the staged value itself
+        // serves as hi and only lo = value - hi is written
 #pragma unroll 4
         for (int i = et; i < STAGE / 16; i += 256) {
           const float4 v = src[i];
-          float4 h, l;
-          h.x = tf32_trunc(v.x);
-          h.y = tf32_trunc(v.y);
-          h.z = tf32_trunc(v.z);
-          h.w = tf32_trunc(v.w);
-          l.x = v.x - h.x;
-          l.y = v.y - h.y;
-          l.z = v.z - h.z;
-          l.w = v.w - h.w;
-          src[i] = h;
+          float4 l;
+          l.x = v.x - tf32_trunc(v.x);
+          l.y = v.y - tf32_trunc(v.y);
+          l.z = v.z - tf32_trunc(v.z);
+          l.w = v.w - tf32_trunc(v.w);
           dst[i] = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -727,7 +725,7 @@ cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
 bool tc_supported() { return true; }
 
 bool tc_step_ok(int64_t m, int64_t n, int64_t k) {
-  return m >= BM && n >= 64 && k >= 16 && k % 4 == 0 && k <= (int64_t(1) << 30) && m < (int64_t(1) << 31) &&
+  return m >= BM && n >= 64 && k >= 8 && k % 4 == 0 && k <= (int64_t(1) << 30) && m < (int64_t(1) << 31) &&
          n < (int64_t(1) << 31);
 }
 

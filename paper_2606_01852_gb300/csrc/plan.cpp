@@ -341,7 +341,9 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     st.cls = TN_CLASS_SIMT;
     if (tc_form_here && tc_step_ok(st.m, st.n, st.k)) {
       const double t_tc = std::max(bytes / kHbm, flops / tc_flops(pol.prec));
-      if (t_tc < t_simt) st.cls = TN_CLASS_TC;
+      // ties (both bound by the same HBM bytes) go to the tensor-core kernel, whose
+      // epilogue stores are the better coalesced
+      if (t_tc <= t_simt) st.cls = TN_CLASS_TC;
     }
     if (st.cls == TN_CLASS_SIMT && stream_ok(st.m, st.n, st.k)) st.cls = TN_CLASS_STREAM;
     // few outputs over a long reduction: the tiled kernel would leave all but a few

@@ -76,6 +76,7 @@ CASES = [
     ((5, 40), (3, 50), (72,), [("m", 0), ("n", 0), ("m", 1), ("n", 1)]),         # ragged m, n, k tails
     ((128,), (2, 2, 32), (8, 4), [("n", 0), ("m", 0), ("n", 1), ("n", 2)]),      # interleaved columns
     ((256,), (96,), (16,), [("n", 0), ("m", 0)]),                                 # rows land strided
+    ((2, 128), (128,), (8,), [("m", 0), ("n", 0), ("m", 1)]),                     # k = 8: half a k-block
 ]
 
 
@@ -128,8 +129,9 @@ def test_circuit_path_with_tc_steps(tn, prec, tol):
 def test_tf32_operand_rounding(tn):
     """How tcgen05 kind::tf32 reads an FP32 operand: with A = 1 + 3*2^-12 and B = 1,
     truncation to 10 mantissa bits gives 1, round-to-nearest 1 + 2^-10. The 3xTF32
-    form does not depend on the answer (it feeds an explicitly truncated hi), but the
-    TF32 error budget above assumes at most one TF32 ulp per operand either way."""
+    kernel relies on truncation (it uses the staged FP32 value itself as hi and adds
+    lo = value - trunc(value)); if this ever read as round-to-nearest, its hi + lo would
+    no longer equal the value."""
     from tn_inputs.network import Network, Path
     ext = {0: 128, 1: 64, 2: 16}
     A = np.full((128, 16), 1.0 + 3.0 * 2.0**-12, dtype=np.complex128)
@@ -139,7 +141,7 @@ def test_tf32_operand_rounding(tn):
     assert plan.step(0)["cls"] == tn.TN_CLASS_TC
     got, _ = run(tn, plan, net)
     vals = np.unique(got.real)
-    assert vals.size == 1 and vals[0] in (16.0, 16.0 * (1 + 2.0**-10)), vals
+    assert vals.size == 1 and vals[0] == 16.0, vals  # truncation
     exact = tn.Plan(net, Path([(0, 1)]), prec="3xtf32")
     g3, _ = run(tn, exact, net)
     assert np.allclose(g3.real, 16.0 * (1.0 + 3.0 * 2.0**-12), rtol=0, atol=1e-6)
