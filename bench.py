@@ -40,6 +40,10 @@ WORKLOAD_DESC = {
     "rc12": "12-qubit 3x4 random circuit, 8 cycles, one amplitude, complex64",
 }
 PREC = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
+# DRAM bytes (read + write) per launch of the dominant kernel, averaged over its launches,
+# from the ncu launch-list capture of this same command (profiles/launches_rc40_3xtf32.md).
+# Only valid for the kernel build the capture was taken on: reset to None when it changes.
+NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 60.903e9}
 
 
 def load_peaks():
@@ -230,7 +234,8 @@ def run_ours(args):
         achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = NCU_TRAFFIC_PER_LAUNCH.get((args.workload, args.prec, names[cls]))
+    roof["algorithmic_bytes_per_launch"] = prof["bytes"][cls] / max(1, launches)
     roof["kernel"] = names[cls]
     roof["launches_per_step"] = launches / args.steps
     roof["ms_per_launch"] = per_launch_ms
