@@ -385,12 +385,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // Warps: 0 TMA, 1 MMA + TMEM, 2-9 split / drain / epilogue (320 threads); warp w of
 // 2-9 drains TMEM lane quarter w % 4, columns 64 * ((w - 2) / 4) .. +63.
 
+// Stage layout (raw values and, in the lo buffers, their lo parts), 8 KiB tiles:
+//   A_re | A_im | -B_im | B_re | B_im
+// so that [B_re | B_im] and [-B_im | B_re] are each one 256-row operand: per k-atom
+// A_re.[B_re|B_im] and A_im.[-B_im|B_re] add into (Re, Im) with one 128 x 256 MMA each.
 struct C3 {
   static constexpr int BK = 16, ROWB = 64, CK = 4;
   static constexpr int TILE_A = BM * ROWB;                  // 8 KiB
   static constexpr int TILE_B = BN * ROWB;                  // 8 KiB
-  static constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;     // 32 KiB
-  static constexpr int STAGES = 4, LO = 2;
+  static constexpr int OFF_AI = TILE_A, OFF_BNEG = 2 * TILE_A;
+  static constexpr int OFF_BR = 2 * TILE_A + TILE_B, OFF_BI = 2 * TILE_A + 2 * TILE_B;
+  static constexpr int TMA_BYTES = 2 * TILE_A + 2 * TILE_B; // 32 KiB per stage by TMA
+  static constexpr int STAGE = 2 * TILE_A + 3 * TILE_B;     // 40 KiB
+  static constexpr int STAGES = 3, LO = 2;
   static constexpr int THREADS = 320;
   static constexpr int SMEM = (STAGES + LO) * STAGE + 1024 + 1024;
   static constexpr uint32_t COLS = 512;  // re @0, im @128, re_lo @256, im_lo @384
@@ -460,13 +467,13 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
           atomicExch(err, 11);
           break;
         }
-        mbar_expect_tx(&full[s], STAGE);
+        mbar_expect_tx(&full[s], C3::TMA_BYTES);
         uint8_t* st = smem + s * STAGE;
         const int k0 = kb * BK;
         tma_load_3d(st, &tmA, &full[s], k0, m0, pa);
-        tma_load_3d(st + TILE_A, &tmA, &full[s], k0, m0, pa + 1);
-        tma_load_3d(st + 2 * TILE_A, &tmB, &full[s], k0, n0, pb);
-        tma_load_3d(st + 2 * TILE_A + TILE_B, &tmB, &full[s], k0, n0, pb + 1);
+        tma_load_3d(st + C3::OFF_AI, &tmA, &full[s], k0, m0, pa + 1);
+        tma_load_3d(st + C3::OFF_BR, &tmB, &full[s], k0, n0, pb);
+        tma_load_3d(st + C3::OFF_BI, &tmB, &full[s], k0, n0, pb + 1);
         issued = kb + 1;
       }
       for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
@@ -474,9 +481,8 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(BM, BN);
-      constexpr uint32_t idesc_neg = idesc | (1u << 13);  // D += (-A) . B
-      const uint32_t d_re = tmem, d_im = tmem + 128, d_re_lo = tmem + 256, d_im_lo = tmem + 384;
+      constexpr uint32_t idesc = idesc_tf32(BM, 2 * BN);  // 128 x 256: (Re | Im) at once
+      const uint32_t d_hi = tmem, d_lo = tmem + 256;
       bool ok = true;
       for (int c = 0; c < n_chunks && ok; ++c) {
         if (!mbar_wait(acc_empty, (c & 1) ^ 1)) {
@@ -498,26 +504,20 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
 #pragma unroll
           for (int j = 0; j < BK / 8; ++j) {
             const uint32_t acc = (kb > c * CK || j > 0) ? 1u : 0u;
-            const uint64_t ar = smem_desc<ROWB>(st + j * 32), ai = smem_desc<ROWB>(st + TILE_A + j * 32);
-            const uint64_t br = smem_desc<ROWB>(st + 2 * TILE_A + j * 32);
-            const uint64_t bi = smem_desc<ROWB>(st + 2 * TILE_A + TILE_B + j * 32);
-            const uint64_t arl = smem_desc<ROWB>(lo + j * 32), ail = smem_desc<ROWB>(lo + TILE_A + j * 32);
-            const uint64_t brl = smem_desc<ROWB>(lo + 2 * TILE_A + j * 32);
-            const uint64_t bil = smem_desc<ROWB>(lo + 2 * TILE_A + TILE_B + j * 32);
-            // hi.hi products into the main accumulators; the small cross terms into their
-            // own, so the main sums take only two truncating additions per 8 terms
-            mma_tf32(d_re, ar, br, idesc, acc);
-            mma_tf32(d_re, ai, bi, idesc_neg, 1u);
-            mma_tf32(d_im, ar, bi, idesc, acc);
-            mma_tf32(d_im, ai, br, idesc, 1u);
-            mma_tf32(d_re_lo, arl, br, idesc, acc);
-            mma_tf32(d_re_lo, ar, brl, idesc, 1u);
-            mma_tf32(d_re_lo, ail, bi, idesc_neg, 1u);
-            mma_tf32(d_re_lo, ai, bil, idesc_neg, 1u);
-            mma_tf32(d_im_lo, arl, bi, idesc, acc);
-            mma_tf32(d_im_lo, ar, bil, idesc, 1u);
-            mma_tf32(d_im_lo, ail, br, idesc, 1u);
-            mma_tf32(d_im_lo, ai, brl, idesc, 1u);
+            const uint64_t ar = smem_desc<ROWB>(st + j * 32), ai = smem_desc<ROWB>(st + C3::OFF_AI + j * 32);
+            const uint64_t b_ri = smem_desc<ROWB>(st + C3::OFF_BR + j * 32);    // [B_re | B_im]
+            const uint64_t b_nr = smem_desc<ROWB>(st + C3::OFF_BNEG + j * 32);  // [-B_im | B_re]
+            const uint64_t arl = smem_desc<ROWB>(lo + j * 32), ail = smem_desc<ROWB>(lo + C3::OFF_AI + j * 32);
+            const uint64_t bl_ri = smem_desc<ROWB>(lo + C3::OFF_BR + j * 32);
+            const uint64_t bl_nr = smem_desc<ROWB>(lo + C3::OFF_BNEG + j * 32);
+            // hi.hi products into the main accumulators (Re | Im); the small cross terms into
+            // their own, so the main sums take only two truncating additions per 8 terms
+            mma_tf32(d_hi, ar, b_ri, idesc, acc);
+            mma_tf32(d_hi, ai, b_nr, idesc, 1u);
+            mma_tf32(d_lo, arl, b_ri, idesc, acc);
+            mma_tf32(d_lo, ail, b_nr, idesc, 1u);
+            mma_tf32(d_lo, ar, bl_ri, idesc, 1u);
+            mma_tf32(d_lo, ai, bl_nr, idesc, 1u);
           }
           mma_commit(&empty[s]);
           mma_commit(&lo_empty[kb & 1]);
@@ -551,16 +551,24 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
         float4* dst = reinterpret_cast<float4*>(lo_base + (kb & 1) * STAGE);
         // kind::tf32 reads an FP32 operand by dropping its low 13 mantissa bits (checked by
         // tests/test_gpu_tc.py::test_tf32_operand_rounding), so the staged value itself
-        // serves as hi and only lo = value - hi is written
+        // serves as hi and only lo = value - hi is written; for B_im also -value and -lo
+        // (truncation is symmetric, so the hardware reads -value as -hi)
+        constexpr int NA = 2 * TILE_A / 16;  // float4s of A_re, A_im
 #pragma unroll 4
-        for (int i = et; i < STAGE / 16; i += 256) {
-          const float4 v = src[i];
+        for (int i = et; i < C3::TMA_BYTES / 16; i += 256) {
+          const int f = i < NA ? i : i + TILE_B / 16;  // skip the -B_im slot
+          const float4 v = src[f];
           float4 l;
           l.x = v.x - tf32_trunc(v.x);
           l.y = v.y - tf32_trunc(v.y);
           l.z = v.z - tf32_trunc(v.z);
           l.w = v.w - tf32_trunc(v.w);
-          dst[i] = l;
+          dst[f] = l;
+          if (f >= C3::OFF_BI / 16) {
+            const int g = f - (C3::OFF_BI - C3::OFF_BNEG) / 16;
+            src[g] = make_float4(-v.x, -v.y, -v.z, -v.w);
+            dst[g] = make_float4(-l.x, -l.y, -l.z, -l.w);
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&conv_full[kb & 1]);
