@@ -514,7 +514,9 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
             // their own, so the main sums take only two truncating additions per 8 terms
             mma_tf32(d_hi, ar, b_ri, idesc, acc);
             mma_tf32(d_hi, ai, b_nr, idesc, 1u);
-            mma_tf32(d_lo, arl, b_ri, idesc, acc);
+            // the cross-term accumulator runs over all of k (it is ~2^-11 of the result,
+            // so its own truncation is negligible) and is read once, after the last chunk
+            mma_tf32(d_lo, arl, b_ri, idesc, (kb > 0 || j > 0) ? 1u : 0u);
             mma_tf32(d_lo, ail, b_nr, idesc, 1u);
             mma_tf32(d_lo, ar, bl_ri, idesc, 1u);
             mma_tf32(d_lo, ai, bl_nr, idesc, 1u);
@@ -586,15 +588,17 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
             tmem_ld32(tmem + col, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
-            tmem_ld32(tmem + 256 + col, v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
             tmem_ld32(tmem + 128 + col, v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
-            tmem_ld32(tmem + 384 + col, v);
+            if (dc == n_chunks - 1) {  // last chunk: the cross terms too
+              tmem_ld32(tmem + 256 + col, v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+              for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+              tmem_ld32(tmem + 384 + col, v);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+            }
           }
           fence_before();
           __syncwarp();
