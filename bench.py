@@ -117,6 +117,20 @@ def oracle_sample(w, budget_s, slice_id=0):
     return flops, time.perf_counter() - t0, done
 
 
+def replica_throughput(ms_local, units_local, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas (one per rank, no data-path
+    collective): the units all ranks processed over the slowest rank's time. Returns
+    (units per second, max milliseconds over ranks)."""
+    import torch
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        mx = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+        tot = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        return float(tot.item()) / (float(mx.item()) / 1e3), float(mx.item())
+    return units_local / (ms_local / 1e3), ms_local
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -199,13 +213,9 @@ def run_ours(args):
     ck = clocks.stop()
     times = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(times)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
     flops = info["flops"]
-    value = ws * flops / (ms_max / 1e3) / 1e12
+    tflop_per_s, ms_max = replica_throughput(ms, flops / 1e12, dist, device="cuda")
+    value = tflop_per_s
     result = complex(out.cpu())
 
     # dominant kernel class by device time, and its roofline

@@ -417,18 +417,17 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(StepArgs a, double*
   for (int o = 0; o < kSplitMaxOut; ++o) accr[o] = acci[o] = 0.f;
   const int64_t k0 = (int64_t)chunk * kc;
   const int64_t k1 = min(a.k, k0 + kc);
+  // the output index o is a compile-time constant in every unrolled iteration, so the
+  // accumulators stay in registers
   for (int64_t kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
 #pragma unroll
-    for (int i = 0; i < kSplitMaxOut; ++i) {
-      if (i >= m) break;
-      const float xr = A[i * a.k + kk] * sa;
-      const float xi = CPLX ? A[a.a_plane + i * a.k + kk] * sa : 0.f;
-#pragma unroll
-      for (int j = 0; j < kSplitMaxOut; ++j) {
-        if (j >= n || i * n + j >= kSplitMaxOut) break;
+    for (int o = 0; o < kSplitMaxOut; ++o) {
+      if (o < mn) {
+        const int i = o / n, j = o - (o / n) * n;
+        const float xr = A[i * a.k + kk] * sa;
         const float yr = B[j * a.k + kk] * sb;
-        const int o = i * n + j;
         if (CPLX) {
+          const float xi = A[a.a_plane + i * a.k + kk] * sa;
           const float yi = B[a.b_plane + j * a.k + kk] * sb;
           accr[o] = fmaf(xr, yr, fmaf(-xi, yi, accr[o]));
           acci[o] = fmaf(xr, yi, fmaf(xi, yr, acci[o]));
