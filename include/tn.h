@@ -210,6 +210,15 @@ tn_status tn_plan_profile(tn_plan_t plan, int32_t enable);
  * to *out; reset != 0 clears the totals after reading. */
 tn_status tn_plan_profile_read(tn_plan_t plan, tn_profile* out, int32_t reset);
 
+/* Self-test of the device-side failure path (the paper has no counterpart). Every
+ * mbarrier wait in the tensor-core kernels is bounded; on expiry the kernel writes a
+ * code to the plan's error word, releases what it holds and returns, and the
+ * synchronising calls report TN_ERR_TIMEOUT. This runs that same bounded wait in a
+ * one-thread kernel on a barrier that is completed only if `arrive` != 0, with a limit of
+ * limit_us microseconds (<= 10 s). Synchronous. Returns TN_OK when the barrier completed,
+ * TN_ERR_TIMEOUT when the wait ran out; the CUDA context stays usable either way. */
+tn_status tn_selftest_bounded_wait(tn_plan_t plan, int32_t arrive, int64_t limit_us, void* stream);
+
 /* Device milliseconds per step accumulated by the same events (ms_out holds n_steps
  * doubles), for the recordings folded in by tn_plan_profile_read since its last reset. */
 tn_status tn_plan_profile_steps(tn_plan_t plan, double* ms_out, int32_t n_steps);

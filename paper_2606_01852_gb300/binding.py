@@ -103,6 +103,7 @@ def _load():
         "tn_plan_profile": [vp, i32],
         "tn_plan_profile_read": [vp, C.POINTER(tn_profile), i32],
         "tn_plan_profile_steps": [vp, C.POINTER(C.c_double), i32],
+        "tn_selftest_bounded_wait": [vp, i32, i64, vp],
         "tn_serve_create": [C.POINTER(tn_serve_config), C.POINTER(vp)],
         "tn_serve_submit": [vp, vp, C.POINTER(vp), C.POINTER(u64)],
         "tn_serve_poll": [vp, u64, vp, vp, i32],
@@ -258,6 +259,11 @@ class Plan:
         p = tn_profile()
         check(lib.tn_plan_profile_read(self.handle, C.byref(p), 1 if reset else 0))
         return {f: list(getattr(p, f)) for f, _ in tn_profile._fields_}
+
+    def selftest_bounded_wait(self, arrive: bool, limit_us: int, stream=None) -> int:
+        """Run the kernels' bounded mbarrier wait on a barrier completed only if `arrive`;
+        returns the status (TN_OK, or TN_ERR_TIMEOUT when the wait ran out)."""
+        return lib.tn_selftest_bounded_wait(self.handle, 1 if arrive else 0, int(limit_us), _ptr_stream(stream))
 
     def profile_steps(self):
         """Per-step device milliseconds of the last profile_read(reset=True)."""

@@ -427,6 +427,24 @@ tn_status tn_plan_profile_steps(tn_plan_t plan, double* ms_out, int32_t n_steps)
   return TN_OK;
 }
 
+tn_status tn_selftest_bounded_wait(tn_plan_t plan, int32_t arrive, int64_t limit_us, void* stream) {
+  if (!plan || !plan->P.dev || limit_us <= 0 || limit_us > 10000000) {
+    set_error("tn_selftest_bounded_wait: needs a device plan and 0 < limit_us <= 1e7");
+    return TN_ERR_INVALID;
+  }
+  Plan& P = plan->P;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int* errw = reinterpret_cast<int*>(P.dev + P.off_err);
+  cudaError_t e = cudaMemsetAsync(errw, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_bounded_wait_selftest(arrive ? 1 : 0, uint64_t(limit_us) * 1000ull, errw, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error(std::string("tn_selftest_bounded_wait: ") + cudaGetErrorString(e));
+    return TN_ERR_CUDA;
+  }
+  return check_device_error(P);
+}
+
 tn_status tn_plan_profile(tn_plan_t plan, int32_t enable) {
   if (!plan) {
     set_error("null plan");

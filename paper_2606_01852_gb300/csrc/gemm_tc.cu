@@ -75,14 +75,26 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 // Wait for the phase of parity `parity` to complete; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns = kWaitNs) {
   if (mbar_test(b, parity)) return true;
   const uint64_t t0 = gtime();
   while (true) {
     for (int i = 0; i < 64; ++i)
       if (mbar_test(b, parity)) return true;
-    if (gtime() - t0 > kWaitNs) return false;
+    if (gtime() - t0 > limit_ns) return false;
   }
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that is completed only
+// if `arrive` is set. Without the arrival the wait runs out after limit_ns, the kernel
+// records code 99 in the error word and returns normally.
+__global__ void bounded_wait_selftest_kernel(int arrive, uint64_t limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (arrive) mbar_arrive(&bar);
+  if (!mbar_wait(&bar, 0, limit_ns)) atomicExch(err, 99);
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
                                             int c2) {
@@ -735,6 +747,11 @@ cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
 }  // namespace
 
 bool tc_supported() { return true; }
+
+cudaError_t launch_bounded_wait_selftest(int arrive, uint64_t limit_ns, int* err, cudaStream_t st) {
+  bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(arrive, limit_ns, err);
+  return cudaGetLastError();
+}
 
 bool tc_step_ok(int64_t m, int64_t n, int64_t k) {
   return m >= BM && n >= 64 && k >= 8 && k % 4 == 0 && k <= (int64_t(1) << 30) && m < (int64_t(1) << 31) &&

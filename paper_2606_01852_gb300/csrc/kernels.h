@@ -56,6 +56,7 @@ void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* ou
 
 // tensor-core path (tcgen05); returns false if the step cannot take it
 bool tc_supported();
+cudaError_t launch_bounded_wait_selftest(int arrive, uint64_t limit_ns, int* err, cudaStream_t st);
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
                                cudaStream_t st);
 

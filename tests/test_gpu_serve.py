@@ -122,3 +122,19 @@ def test_poll_not_ready_then_done(tn):
     want = oracle.contract(big.net, big.path)
     assert abs(complex(out) - want) / abs(want) < 1e-5
     srv.destroy()
+
+
+def test_device_wait_timeout_is_a_status(tn):
+    """A device wait that nothing completes runs out (100 ms limit), is reported as
+    TN_ERR_TIMEOUT, and the context stays usable: a contraction right after is correct."""
+    w = workloads.rc12()
+    plan = tn.Plan(w.net, w.path)
+    assert plan.selftest_bounded_wait(True, 100000) == tn.TN_OK
+    t0 = time.time()
+    assert plan.selftest_bounded_wait(False, 100000) == tn.TN_ERR_TIMEOUT
+    assert time.time() - t0 < 5.0
+    assert "bounded wait" in tn.last_error()
+    out = np.zeros((), dtype=np.complex128)
+    plan.contract_host(host_inputs(w.net), out)
+    want = oracle.contract(w.net, w.path)
+    assert abs(complex(out) - want) / abs(want) < 1e-5
