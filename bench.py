@@ -43,7 +43,7 @@ PREC = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
 # DRAM bytes (read + write) per launch of the dominant kernel, averaged over its launches,
 # from the ncu launch-list capture of this same command (profiles/launches_rc40_3xtf32.md).
 # Only valid for the kernel build the capture was taken on: reset to None when it changes.
-NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 60.903e9}
+NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 53.463e9}
 
 
 def load_peaks():
