@@ -5,7 +5,9 @@ Calls only the oracle and the seeded input generators:
   * rc40 (40-qubit 5x8 circuit, 13 cycles, 256 slices): the partial results of 4 slices
     drawn with a fixed seed (one slice takes ~10 s here; all 256 would take ~1 h);
   * kising44 (4x4 kicked Ising, 10 Trotter steps): the full value;
-  * rc12 (12-qubit circuit): the full value.
+  * rc12 (12-qubit circuit): the full value;
+  * rc40open (rc40 with four qubits left open): the [2,2,2,2] partial tensors of 4 slices
+    drawn with a second fixed seed.
 Run from the repository root: python tests/golden/make_oracle_values.py
 """
 import json
@@ -23,6 +25,7 @@ from tn_inputs import workloads  # noqa: E402
 
 RC40_SAMPLE_SEED = 20261202
 RC40_SAMPLES = 4
+RC40OPEN_SAMPLE_SEED = 20261203
 
 
 def main():
@@ -33,6 +36,12 @@ def main():
     ids = sorted(int(x) for x in rng.choice(w.n_slices, size=RC40_SAMPLES, replace=False))
     _, parts = oracle.contract_slices(w.net, w.path, w.sliced, slice_ids=ids, return_partials=True)
     out["rc40"] = {"slices": ids, "partials": [[float(np.real(p)), float(np.imag(p))] for p in parts]}
+    w = workloads.rc40open()
+    rng = np.random.default_rng(RC40OPEN_SAMPLE_SEED)
+    ids = sorted(int(x) for x in rng.choice(w.n_slices, size=RC40_SAMPLES, replace=False))
+    _, parts = oracle.contract_slices(w.net, w.path, w.sliced, slice_ids=ids, return_partials=True)
+    out["rc40open"] = {"slices": ids, "shape": list(np.shape(parts[0])),
+                       "partials": [[[float(v.real), float(v.imag)] for v in np.ravel(p)] for p in parts]}
     for name in ("kising44", "rc12"):
         wl = workloads.BY_NAME[name]()
         v = complex(oracle.contract(wl.net, wl.path, wl.sliced))

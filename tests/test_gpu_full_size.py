@@ -51,6 +51,27 @@ def test_rc40_sampled_slices_bench_config(tn, prec):
     plan.destroy()
 
 
+@pytest.mark.parametrize("prec", ["3xtf32", "fp32"])
+def test_rc40open_sampled_slices_bench_config(tn, prec):
+    """The open-output variant: each slice yields a [2,2,2,2] tensor of partial amplitudes;
+    every entry is held to the same bound, relative to the RMS entry of the samples."""
+    w = workloads.rc40open()
+    gold = GOLD["rc40open"]
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=128)
+    assert plan.info()["slice_batch"] == 128 and list(plan.out_shape) == gold["shape"]
+    ins = dev(w.net)
+    want = np.array([[complex(*v) for v in p] for p in gold["partials"]])
+    typical = np.sqrt(np.mean(np.abs(want) ** 2))
+    out = torch.zeros(plan.out_shape, dtype=torch.complex128, device="cuda")
+    for sid, wv in zip(gold["slices"], want):
+        plan.contract_slices(ins, sid, 1, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().ravel()
+        err = np.max(np.abs(got - wv)) / typical
+        assert err < 2e-5, (sid, err)
+    plan.destroy()
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("3xtf32", 1e-4), ("tf32", 1e-1)])
 def test_kising44_full(tn, prec, tol):
     w = workloads.kising44()

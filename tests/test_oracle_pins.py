@@ -98,6 +98,30 @@ def test_circuit_amplitude_vs_statevector():
         assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (got, want)
 
 
+def test_open_qubit_amplitudes_vs_statevector():
+    """Leaving qubits unprojected gives the tensor of the amplitudes that share the other
+    bits: entry [b_0, b_1, ...] (open qubits in the given order) is <x'|C|0> where x' is
+    the bitstring with those qubits set to b_i. Sliced over two labels, the sum agrees."""
+    for (r, c, m, seed, open_q) in [(2, 3, 6, 1, (4, 0)), (3, 3, 8, 2, (7, 8, 5))]:
+        net = circuits.amplitude_network(r, c, m, seed, open_qubits=open_q)
+        assert net.open_modes and len(net.open_modes) == len(open_q)
+        path = greedy.greedy_path(net, seed=0, alpha=1.0)
+        got = np.asarray(oracle.contract(net, path))
+        assert got.shape == (2,) * len(open_q)
+        psi = pins.statevector_circuit(r * c, net.meta["gates"])
+        base = list(net.meta["bitstring"])
+        for bits in np.ndindex(*got.shape):
+            x = list(base)
+            for q, b in zip(open_q, bits):
+                x[q] = b
+            idx = int("".join(map(str, x)), 2)
+            assert abs(got[bits] - psi[idx]) <= 1e-12, (bits, got[bits], psi[idx])
+        closed = [x for x in net.extent if x not in net.open_modes
+                  and sum(x in m_ for m_ in net.modes) == 2][:2]
+        sliced = np.asarray(oracle.contract_slices(net, path, closed))
+        assert np.allclose(sliced, got, rtol=0, atol=1e-12)
+
+
 def test_circuit_normalisation():
     r, c, m, seed = 3, 3, 8, 5
     gates = circuits.circuit_gates(r, c, m, seed)

@@ -59,8 +59,11 @@ class _Builder:
         self.modes.append(tuple(modes))
 
 
-def amplitude_network(rows: int, cols: int, cycles: int, seed: int, bitstring=None) -> Network:
-    """Closed network for <x|C|0>; x is drawn from the same seed unless given."""
+def amplitude_network(rows: int, cols: int, cycles: int, seed: int, bitstring=None, open_qubits=()) -> Network:
+    """Closed network for <x|C|0>; x is drawn from the same seed unless given. Qubits in
+    `open_qubits` get no projection: their output wires stay open (in that order), so the
+    network is the tensor of the 2^len(open_qubits) amplitudes that share the other bits
+    (a batch of correlated amplitudes from one contraction)."""
     n = rows * cols
     gates = circuit_gates(rows, cols, cycles, seed)
     if bitstring is None:
@@ -78,11 +81,15 @@ def amplitude_network(rows: int, cols: int, cycles: int, seed: int, bitstring=No
         b.add(g, (o0, o1, wire[q0], wire[q1]))
         wire[q0], wire[q1] = o0, o1
     for q in range(n):
+        if q in open_qubits:
+            continue
         e = np.zeros(2, dtype=np.complex128)
         e[bitstring[q]] = 1.0
         b.add(e, (wire[q],))
-    net = Network(b.tensors, b.modes, b.extent, (), name=f"rc_{rows}x{cols}_m{cycles}_s{seed}",
+    suffix = f"_open{len(open_qubits)}" if open_qubits else ""
+    net = Network(b.tensors, b.modes, b.extent, tuple(wire[q] for q in open_qubits),
+                  name=f"rc_{rows}x{cols}_m{cycles}_s{seed}{suffix}",
                   meta=dict(rows=rows, cols=cols, cycles=cycles, seed=seed, bitstring=bitstring,
-                            gates=gates))
+                            gates=gates, open_qubits=tuple(open_qubits)))
     net.check()
     return net

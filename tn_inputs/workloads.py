@@ -4,6 +4,8 @@
               greedy path, no slicing (the tiny circuit case).
   rc40      : 40-qubit 5x8 grid random circuit, 13 cycles, one amplitude, greedy path
               with 8 sliced labels (256 slices). The headline workload.
+  rc40open  : rc40 with the 2x2 corner block of qubits left open, so one contraction
+              yields 16 correlated amplitudes (a [2,2,2,2] output tensor); 256 slices.
   kising44  : 4x4 kicked Ising, 10 Trotter steps, J=1, dt=0.25, h=0.9, <Z_centre>
               (the dynamics expectation case at a size one GPU and the oracle can
               contract unsliced).
@@ -46,8 +48,8 @@ def _pathed(name, net, n_sliced=0, seeds=PATH_SEEDS):
 
 
 @functools.lru_cache(maxsize=None)
-def random_circuit(rows, cols, cycles, seed, n_sliced=0):
-    net = circuits.amplitude_network(rows, cols, cycles, seed)
+def random_circuit(rows, cols, cycles, seed, n_sliced=0, open_qubits=()):
+    net = circuits.amplitude_network(rows, cols, cycles, seed, open_qubits=open_qubits)
     name = net.name + (f"_sl{n_sliced}" if n_sliced else "")
     return _pathed(name, net, n_sliced=n_sliced)
 
@@ -66,6 +68,16 @@ def rc40():
     return random_circuit(5, 8, 13, 40, n_sliced=8)
 
 
+# the 2x2 block of qubits in the grid's last corner (rows 3-4, columns 6-7) stays open
+RC40_OPEN = (30, 31, 38, 39)
+
+
+def rc40open():
+    """rc40 with four output qubits left open: the 16 correlated amplitudes that share
+    the other 36 bits, from one sliced contraction (output tensor [2,2,2,2])."""
+    return random_circuit(5, 8, 13, 40, n_sliced=8, open_qubits=RC40_OPEN)
+
+
 def kising44():
     return kicked(4, 10)
 
@@ -79,4 +91,4 @@ def ising3r(count, seed=3):
     return [ising_workload(n) for n in ising_pf.ensemble(count, seed)]
 
 
-BY_NAME = {"rc12": rc12, "rc40": rc40, "kising44": kising44}
+BY_NAME = {"rc12": rc12, "rc40": rc40, "kising44": kising44, "rc40open": rc40open}
