@@ -43,7 +43,10 @@ typedef enum {
  *   FP32_SIMT : FP32 FMA on the CUDA cores (the plain form).
  *   TF32      : tcgen05 tensor cores, operands read as TF32, FP32 accumulation.
  *   3XTF32    : tcgen05, each operand split hi + lo, three TF32 products, FP32 accum.
- *   BF16X3    : tcgen05, each operand split hi + lo in BF16, three products, FP32 accum.
+ *   BF16X3    : tcgen05 kind::f16, each operand split hi + lo in BF16 (rounded to
+ *               nearest) by the kernel that produces it, three products hi.hi +
+ *               hi.lo + lo.hi (complex only; relative error per product <= ~3 * 2^-16),
+ *               FP32 accumulation.
  * Steps too small or too thin for a tensor-core tile run on the FP32 SIMT kernels
  * whatever the form. */
 typedef enum {
@@ -128,6 +131,13 @@ typedef struct {
   int64_t row_ext[12], row_stride[12], col_ext[12], col_stride[12];
 } tn_step_info;
 
+/* How a tensor's copies are stored in the workspace. PLANAR: FP32 (complex: the real
+ * plane, then the imaginary plane). SPLIT_BF16 (complex, BF16X3 plans only): the
+ * operands of tensor-core steps are written by their producers as four BF16 planes
+ * [re_hi | im_hi | re_lo | im_lo] with hi = RN_bf16(v), lo = RN_bf16(v - hi); same
+ * bytes per element as PLANAR. */
+typedef enum { TN_FORMAT_PLANAR = 0, TN_FORMAT_SPLIT_BF16 = 1 } tn_storage_format;
+
 /* Where a tensor lives in the plan's workspace (introspection). */
 typedef struct {
   int64_t size;            /* elements of one slice copy (sliced labels removed) */
@@ -137,6 +147,8 @@ typedef struct {
   int32_t pinned;          /* made in the first pass, kept for every pass */
   int32_t producer;        /* step index, -1 for a leaf */
   int32_t consumer;        /* step index, -1 for the root */
+  int32_t format;          /* tn_storage_format of the tensor's copies */
+  int32_t reserved;
 } tn_tensor_info;
 
 /* Build a plan: validate, analyse each step (Sec. II-B), run the backward mode

@@ -70,7 +70,9 @@ class tn_step_info(C.Structure):
 class tn_tensor_info(C.Structure):
     _fields_ = [("size", C.c_int64), ("offset", C.c_int64), ("bytes", C.c_int64),
                 ("batched", C.c_int32), ("pinned", C.c_int32), ("producer", C.c_int32),
-                ("consumer", C.c_int32)]
+                ("consumer", C.c_int32),
+                ("format", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class tn_profile(C.Structure):

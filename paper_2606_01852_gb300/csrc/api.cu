@@ -53,6 +53,7 @@ StepArgs step_args(const Plan& P, const StepRec& st) {
   a.rec_a = P.rec_index[st.a];
   a.rec_b = P.rec_index[st.b];
   a.rec_c = P.rec_index[st.out];
+  a.c_split = C.split ? 1 : 0;
   return a;
 }
 void* take_event(Plan& P) {
@@ -326,6 +327,8 @@ tn_status tn_plan_tensor(tn_plan_t plan, int32_t id, tn_tensor_info* out) {
   out->pinned = R.pinned ? 1 : 0;
   out->producer = R.producer;
   out->consumer = R.consumer;
+  out->format = R.split ? TN_FORMAT_SPLIT_BF16 : TN_FORMAT_PLANAR;
+  out->reserved = 0;
   return TN_OK;
 }
 

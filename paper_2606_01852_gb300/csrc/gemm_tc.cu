@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "split_bf16.cuh"
 
 namespace tn {
 namespace {
@@ -673,6 +674,258 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------------
+// BF16x3 (split-BF16) form, kind::f16 with BF16 operands.
+//
+// Both operands arrive in the split-BF16 form (split_bf16.cuh), written by the kernels
+// that produced them, so this kernel does no conversion: per k-block one TMA box of
+// (32 k) x (128 rows) x (4 planes) per operand lands as the tiles
+//   [re_hi | im_hi | re_lo | im_lo], 128 rows of 64 bytes each, 64-byte swizzle,
+// and [B_re | B_im] of either precision is one 256-row operand. Per 16-deep k-atom:
+//   hi:  D_hi(Re|Im) += A_re_h.[B_re_h|B_im_h];  D_hi.Re -= A_im_h.B_im_h;  D_hi.Im += A_im_h.B_re_h
+//   lo:  the same three with (A_lo, B_hi) and with (A_hi, B_lo), into D_lo
+// (the A_lo.B_lo term, <= 2^-16 relative, is dropped). -A_im uses the instruction's
+// negate-A bit. D_lo spans all of k; D_hi is folded into round-to-nearest register
+// totals every CK k-blocks (256 terms) as in the 3xTF32 kernel, and the lo MMAs of a
+// chunk's first k-block are issued before the wait for that fold, so the fold overlaps
+// tensor-core work. Warps: 0 TMA, 1 MMA + TMEM, 2-9 fold / epilogue (320 threads).
+struct CB {
+  static constexpr int BK = 32, ROWB = 64, CK = 8;
+  static constexpr int PLANE = BM * ROWB;                   // 8 KiB: one plane of one operand
+  static constexpr int OFF_B = 4 * PLANE;
+  static constexpr int STAGE = 8 * PLANE;                   // 64 KiB: A and B, 4 planes each
+  static constexpr int STAGES = 3;
+  static constexpr int THREADS = 320;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 1024;
+  static constexpr uint32_t COLS = 512;  // hi: re @0, im @128; lo: re @256, im @384
+};
+static_assert(BM == BN, "the split-BF16 tiles share one plane size");
+
+// Instruction descriptor, kind::f16: D f32, A/B bf16, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+constexpr uint32_t kNegateA = 1u << 13;
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__global__ void __launch_bounds__(CB::THREADS, 1)
+    contract_tcb_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        StepArgs a, int* err) {
+  constexpr int STAGES = CB::STAGES, BK = CB::BK, ROWB = CB::ROWB, CK = CB::CK;
+  constexpr int PLANE = CB::PLANE, STAGE = CB::STAGE;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint64_t* full = bars;                 // [STAGES]
+  uint64_t* empty = bars + STAGES;       // [STAGES]
+  uint64_t* acc_full = bars + 2 * STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
+  const int64_t t = blockIdx.x;
+  const int64_t per_group = GROUP_M * tiles_n;
+  const int64_t first_m = (t / per_group) * GROUP_M;
+  const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
+  const int64_t tm = first_m + (t % per_group) % gm, tn = (t % per_group) / gm;
+  const int m0 = static_cast<int>(tm * BM), n0 = static_cast<int>(tn * BN);
+  const int b = blockIdx.y;
+  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);
+  const int n_chunks = (num_kb + CK - 1) / CK;
+  const int pa = a.a_bstride ? 4 * b : 0, pb = a.b_bstride ? 4 * b : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 8);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(CB::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) {
+          atomicExch(err, 21);
+          break;
+        }
+        mbar_expect_tx(&full[s], STAGE);
+        uint8_t* st = smem + s * STAGE;
+        const int k0 = kb * BK;
+        tma_load_3d(st, &tmA, &full[s], k0, m0, pa);
+        tma_load_3d(st + CB::OFF_B, &tmB, &full[s], k0, n0, pb);
+        issued = kb + 1;
+      }
+      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+        if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) atomicExch(err, 22);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t id_w = idesc_bf16(BM, 2 * BN);   // A . [B_re | B_im] -> (Re | Im)
+      constexpr uint32_t id_n = idesc_bf16(BM, BN);
+      const uint32_t d_hi = tmem, d_lo = tmem + 256;
+      bool ok = true;
+      for (int c = 0; c < n_chunks && ok; ++c) {
+        const int kb_end = min(num_kb, (c + 1) * CK);
+        for (int kb = c * CK; kb < kb_end; ++kb) {
+          const int s = kb % STAGES;
+          if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+            atomicExch(err, 23);
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sa = su32(smem + s * STAGE), sb = sa + CB::OFF_B;
+#pragma unroll
+          for (int j = 0; j < BK / 16; ++j) {
+            const uint32_t o = j * 32;
+            const uint64_t ar_l = smem_desc<ROWB>(sa + 2 * PLANE + o), ai_l = smem_desc<ROWB>(sa + 3 * PLANE + o);
+            const uint64_t ar_h = smem_desc<ROWB>(sa + o), ai_h = smem_desc<ROWB>(sa + PLANE + o);
+            const uint64_t b_h = smem_desc<ROWB>(sb + o), bi_h = smem_desc<ROWB>(sb + PLANE + o);
+            const uint64_t b_l = smem_desc<ROWB>(sb + 2 * PLANE + o), bi_l = smem_desc<ROWB>(sb + 3 * PLANE + o);
+            const uint32_t first = (kb > 0 || j > 0) ? 1u : 0u;
+            mma_bf16(d_lo, ar_l, b_h, id_w, first);              // A_re_lo . [B_re_h | B_im_h]
+            mma_bf16(d_lo, ai_l, bi_h, id_n | kNegateA, 1u);     // Re -= A_im_lo . B_im_h
+            mma_bf16(d_lo + 128, ai_l, b_h, id_n, 1u);           // Im += A_im_lo . B_re_h
+            mma_bf16(d_lo, ar_h, b_l, id_w, 1u);                 // A_re_h . [B_re_lo | B_im_lo]
+            mma_bf16(d_lo, ai_h, bi_l, id_n | kNegateA, 1u);
+            mma_bf16(d_lo + 128, ai_h, b_l, id_n, 1u);
+          }
+          if (kb == c * CK) {
+            // the chunk accumulator must have been folded before the hi MMAs reuse it
+            if (!mbar_wait(acc_empty, (c & 1) ^ 1)) {
+              atomicExch(err, 24);
+              ok = false;
+              mma_commit(&empty[s]);
+              break;
+            }
+            fence_after();
+          }
+#pragma unroll
+          for (int j = 0; j < BK / 16; ++j) {
+            const uint32_t o = j * 32;
+            const uint64_t ar_h = smem_desc<ROWB>(sa + o), ai_h = smem_desc<ROWB>(sa + PLANE + o);
+            const uint64_t b_h = smem_desc<ROWB>(sb + o), bi_h = smem_desc<ROWB>(sb + PLANE + o);
+            const uint32_t acc = (kb > c * CK || j > 0) ? 1u : 0u;
+            mma_bf16(d_hi, ar_h, b_h, id_w, acc);
+            mma_bf16(d_hi, ai_h, bi_h, id_n | kNegateA, 1u);
+            mma_bf16(d_hi + 128, ai_h, b_h, id_n, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(acc_full);  // also on error, so the fold sees issued MMAs retire
+      }
+    }
+  } else {
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    float run_re[64], run_im[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) run_re[i] = run_im[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < n_chunks && ok; ++c) {
+      if (!mbar_wait(acc_full, c & 1)) {
+        atomicExch(err, 25);
+        ok = false;
+        break;
+      }
+      fence_after();
+      float v[32];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const uint32_t col = lane_base + half * 64 + p * 32;
+        tmem_ld32(tmem + col, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+        tmem_ld32(tmem + 128 + col, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+        if (c == n_chunks - 1) {  // after the last chunk: the cross terms too
+          tmem_ld32(tmem + 256 + col, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+          tmem_ld32(tmem + 384 + col, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+    }
+    // epilogue: thread = TMEM lane (row); this warp's 64 columns
+    const int row = q * 32 + lane;
+    const int64_t m = static_cast<int64_t>(m0) + row;
+    const bool row_ok = ok && m < a.m;
+    const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
+    float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
+    const bool split = a.c_split != 0;
+    const bool rows_unit = a.rows.n > 0 && a.rows.stride[a.rows.n - 1] == 1;
+    // The stage buffers are free here: the last fold waited for the final MMA, which
+    // consumed every staged tile; no TMA load is outstanding.
+    float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 33;  // [2][32][33]
+#pragma unroll
+    for (int cb = 0; cb < 2; ++cb) {
+      const int64_t nb0 = static_cast<int64_t>(n0) + half * 64 + cb * 32;
+      if (rows_unit) {
+        if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t n = nb0 + j;
+            if (n < a.n)
+              store_cplx(C, a.c_plane, ro + map_off(a.cols, n), run_re[cb * 32 + j], run_im[cb * 32 + j], split);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          tr[lane * 33 + j] = run_re[cb * 32 + j];
+          tr[32 * 33 + lane * 33 + j] = run_im[cb * 32 + j];
+        }
+        __syncwarp();
+        const int64_t n = nb0 + lane;
+        const bool col_ok = ok && n < a.n;
+        const int64_t co = col_ok ? map_off(a.cols, n) : 0;
+        for (int r = 0; r < 32; ++r) {
+          const int64_t ro_r = __shfl_sync(0xffffffffu, ro, r);
+          const bool ok_r = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, r) != 0;
+          if (ok_r && col_ok) store_cplx(C, a.c_plane, ro_r + co, tr[r * 33 + lane], tr[32 * 33 + r * 33 + lane], split);
+        }
+        __syncwarp();
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CB::COLS));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -699,6 +952,23 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t k, int6
   const CUtensorMapSwizzle sw = bk * 4 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// 3-D map over a split-BF16 operand: (k, rows, plane), plane = 4*copy + {re_hi, im_hi,
+// re_lo, im_lo}; box 32 x rows x 4 planes, 64-byte swizzle.
+bool make_map_split(CUtensorMap* map, const float* base, int64_t rows, int64_t k, int64_t copies,
+                    int64_t plane_elems, int box_rows) {
+  auto enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows),
+                        static_cast<cuuint64_t>(4 * copies)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(k * 2), static_cast<cuuint64_t>(plane_elems * 2)};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(CB::BK), static_cast<cuuint32_t>(box_rows), 4};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<float*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -744,6 +1014,25 @@ cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
   return cudaGetLastError();
 }
 
+cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(contract_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  CUtensorMap ta, tb;
+  const int64_t ca = a.a_bstride ? static_cast<int64_t>(nb) : 1;
+  const int64_t cb = a.b_bstride ? static_cast<int64_t>(nb) : 1;
+  if (!make_map_split(&ta, a.A, a.m, a.k, ca, a.a_plane, BM) || !make_map_split(&tb, a.B, a.n, a.k, cb, a.b_plane, BN))
+    return cudaErrorInvalidValue;
+  const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
+  dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));
+  contract_tcb_kernel<<<grid, CB::THREADS, CB::SMEM, st>>>(ta, tb, a, err);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool tc_supported() { return true; }
@@ -753,8 +1042,11 @@ cudaError_t launch_bounded_wait_selftest(int arrive, uint64_t limit_ns, int* err
   return cudaGetLastError();
 }
 
-bool tc_step_ok(int64_t m, int64_t n, int64_t k) {
-  return m >= BM && n >= 64 && k >= 8 && k % 4 == 0 && k <= (int64_t(1) << 30) && m < (int64_t(1) << 31) &&
+bool tc_step_ok(int64_t m, int64_t n, int64_t k, int32_t prec) {
+  // TMA rows are k * element bytes and must be whole 16-byte units: k % 4 for the FP32
+  // operands, k % 8 for the split-BF16 ones
+  const int64_t kq = prec == TN_C64_BF16X3 ? 8 : 4;
+  return m >= BM && n >= 64 && k >= 8 && k % kq == 0 && k <= (int64_t(1) << 30) && m < (int64_t(1) << 31) &&
          n < (int64_t(1) << 31);
 }
 
@@ -763,6 +1055,7 @@ cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool
   if (!cplx || a.recs) return cudaErrorNotSupported;
   if (prec == TN_C64_TF32) return launch_split<1>(a, nb, err, st);
   if (prec == TN_C64_3XTF32) return launch_tc3(a, nb, err, st);
+  if (prec == TN_C64_BF16X3) return launch_tcb(a, nb, err, st);
   return cudaErrorNotSupported;
 }
 

@@ -21,7 +21,8 @@ struct ScaleRec {
 // One pairwise step C[b] = A[b] (m x k, row-major) . B[b] (n x k, row-major)^T.
 // Planar complex: the imaginary plane of each tensor copy follows its real plane at
 // +*_plane floats. C is written at rows(m) + cols(n). Batch strides are 0 for tensors
-// that do not depend on a sliced label.
+// that do not depend on a sliced label. With c_split, C is written as the four BF16
+// planes of the split form (split_bf16.cuh): the operand layout of a BF16x3 step.
 struct StepArgs {
   const float* A;
   const float* B;
@@ -32,7 +33,7 @@ struct StepArgs {
   OffsetMap rows, cols;
   ScaleRec* recs;                           // null: no exponent scaling
   int32_t rec_a, rec_b, rec_c;
-  int32_t pad;
+  int32_t c_split;                          // 1: write C in the split-BF16 form (complex)
 };
 
 void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int64_t slice_begin,
@@ -57,6 +58,7 @@ void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* ou
 // tensor-core path (tcgen05); returns false if the step cannot take it
 bool tc_supported();
 cudaError_t launch_bounded_wait_selftest(int arrive, uint64_t limit_ns, int* err, cudaStream_t st);
+// A and B of a BF16X3 step are in the split-BF16 form.
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
                                cudaStream_t st);
 

@@ -1,6 +1,7 @@
 // CUDA-core kernels of the contraction engine (sm_103a):
 //   stage_leaves      : leaf staging and slicing (declared order -> planned order,
-//                       sliced labels fixed per batch entry, complex64 -> planar fp32)
+//                       sliced labels fixed per batch entry, complex64 -> planar fp32
+//                       or, for operands of BF16x3 steps, split BF16)
 //   contract_simt     : any pairwise step C[b] = A[b](m x k) . B[b](n x k)^T, FP32 FMA,
 //                       written through the separable row/column offset maps
 //   contract_stream   : big x small steps (n*k tiny), one pass over the big operand
@@ -11,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "split_bf16.cuh"
 
 namespace tn {
 
@@ -70,8 +72,7 @@ __global__ void stage_leaves_kernel(const LeafDesc* __restrict__ descs, char* __
     if (is_complex) {
       const float2 v = reinterpret_cast<const float2*>(d.src)[src];
       float* dst = reinterpret_cast<float*>(ws + d.dst) + b * 2 * d.size;
-      dst[el] = v.x;
-      dst[d.size + el] = v.y;
+      store_cplx(dst, d.size, el, v.x, v.y, d.split != 0);
       if (recs) lmax = max(lmax, exp_of(fmaxf(fabsf(v.x), fabsf(v.y))));
     } else {
       const float v = reinterpret_cast<const float*>(d.src)[src];
@@ -198,8 +199,8 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (!cok[j]) continue;
-      C[ro + coff[j]] = accr[i][j];
-      if (CPLX) C[a.c_plane + ro + coff[j]] = acci[i][j];
+      if (CPLX) store_cplx(C, a.c_plane, ro + coff[j], accr[i][j], acci[i][j], a.c_split != 0);
+      else C[ro + coff[j]] = accr[i][j];
       if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(accr[i][j]), fabsf(acci[i][j]))
                                                : fabsf(accr[i][j])));
     }
@@ -273,8 +274,8 @@ __global__ void __launch_bounds__(256) contract_stream_kernel(StepArgs a) {
 #pragma unroll
     for (int j = 0; j < NMAX; ++j) {
       if (j < n) {
-        C[ro + coff[j]] = cr[j];
-        if (CPLX) C[a.c_plane + ro + coff[j]] = ci[j];
+        if (CPLX) store_cplx(C, a.c_plane, ro + coff[j], cr[j], ci[j], a.c_split != 0);
+        else C[ro + coff[j]] = cr[j];
         if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(cr[j]), fabsf(ci[j])) : fabsf(cr[j])));
       }
     }
@@ -481,8 +482,8 @@ __global__ void splitk_final_kernel(StepArgs a, const double* scratch, int32_t c
     }
     const int i = o / n, j = o % n;
     const int64_t off = map_offset(a.rows, i) + map_offset(a.cols, j);
-    C[off] = (float)vr;
-    if (cplx) C[a.c_plane + off] = (float)vi;
+    if (cplx) store_cplx(C, a.c_plane, off, (float)vr, (float)vi, a.c_split != 0);
+    else C[off] = (float)vr;
     if (a.recs) lmax = max(lmax, exp_of(cplx ? fmaxf(fabsf((float)vr), fabsf((float)vi)) : fabsf((float)vr)));
   }
   if (a.recs) {

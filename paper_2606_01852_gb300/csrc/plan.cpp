@@ -24,7 +24,7 @@ inline int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 constexpr double kHbm = 6.6e12;
 constexpr double kSimtFlops = 45e12;
 
-bool tc_prec_built(int32_t p) { return p == TN_C64_TF32 || p == TN_C64_3XTF32; }
+bool tc_prec_built(int32_t p) { return p == TN_C64_TF32 || p == TN_C64_3XTF32 || p == TN_C64_BF16X3; }
 
 bool is_tc_prec(int32_t p) {
   return p == TN_C64_TF32 || p == TN_C64_3XTF32 || p == TN_C64_BF16X3 || p == TN_R32_TF32 ||
@@ -35,7 +35,7 @@ double tc_flops(int32_t p) {
   switch (p) {
     case TN_C64_TF32: case TN_R32_TF32: return 700e12;
     case TN_C64_3XTF32: case TN_R32_3XTF32: return 250e12;
-    case TN_C64_BF16X3: case TN_R32_BF16X3: return 400e12;
+    case TN_C64_BF16X3: case TN_R32_BF16X3: return 450e12;
     default: return 0;
   }
 }
@@ -325,7 +325,7 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     // fills them when only one orientation qualifies.
     const bool tc_form_here = tc_form && P.is_complex && !pol.exp_scaling && tc_prec_built(pol.prec) &&
                               tc_supported();
-    if (tc_form_here && !tc_step_ok(st.m, st.n, st.k) && tc_step_ok(st.n, st.m, st.k)) {
+    if (tc_form_here && !tc_step_ok(st.m, st.n, st.k, pol.prec) && tc_step_ok(st.n, st.m, st.k, pol.prec)) {
       std::swap(st.a, st.b);
       std::swap(st.M, st.N);
       std::swap(st.m, st.n);
@@ -339,7 +339,7 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     const double bytes = eb * (double(st.m) * st.k + double(st.n) * st.k + double(st.m) * st.n);
     const double t_simt = std::max(bytes / kHbm, flops / kSimtFlops);
     st.cls = TN_CLASS_SIMT;
-    if (tc_form_here && tc_step_ok(st.m, st.n, st.k)) {
+    if (tc_form_here && tc_step_ok(st.m, st.n, st.k, pol.prec)) {
       const double t_tc = std::max(bytes / kHbm, flops / tc_flops(pol.prec));
       // ties (both bound by the same HBM bytes) go to the tensor-core kernel, whose
       // epilogue stores are the better coalesced
@@ -357,6 +357,16 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     if (!st.batched) continue;
     if (!P.tensors[st.a].batched) P.tensors[st.a].pinned = true;
     if (!P.tensors[st.b].batched) P.tensors[st.b].pinned = true;
+  }
+  // ---- split-BF16 operands: a BF16x3 tensor-core step reads both operands in the split
+  // form, so their producers (leaf staging or the producing step) write that form
+  if (pol.prec == TN_C64_BF16X3) {
+    for (int32_t s = 0; s < S; ++s) {
+      const StepRec& st = P.steps[s];
+      if (st.cls != TN_CLASS_TC) continue;
+      P.tensors[st.a].split = true;
+      P.tensors[st.b].split = true;
+    }
   }
   // ---- leaf descriptors (sources filled per call)
   P.leafdesc.assign(T, LeafDesc{});
@@ -377,6 +387,7 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     d.rank = (int32_t)R.modes.size();
     d.size = R.size;
     d.batched = R.batched ? 1 : 0;
+    d.split = R.split ? 1 : 0;
     for (int i = 0; i < d.rank; ++i) {
       int32_t x = R.modes[i];
       int pos = int(std::find(R.decl.begin(), R.decl.end(), x) - R.decl.begin());

@@ -33,7 +33,7 @@ struct LeafDesc {
   int32_t rank;             // planned rank
   int32_t batched;          // carries a sliced label
   int32_t n_sl;             // sliced labels on this leaf
-  int32_t pad;
+  int32_t split;            // stage in the split-BF16 form (operand of a BF16x3 step)
   uint32_t ext[kMaxLeafRank];      // planned extents
   int64_t sstride[kMaxLeafRank];   // source stride (elements) of each planned position
   int64_t sl_div[kMaxSliced];      // slice id -> label value: (sid / div) % ext
@@ -49,6 +49,7 @@ struct TensorRec {
   int32_t producer = -1;       // step, or -1 for a leaf
   int32_t consumer = -1;       // step, or -1 for the root
   bool pinned = false;         // unbatched, consumed by a batched step: kept for all passes
+  bool split = false;          // stored as split BF16 (its consumer is a BF16x3 TC step)
   int64_t offset = 0;          // byte offset in the workspace
   int64_t bytes = 0;           // bytes including the batch copies
 };
@@ -130,8 +131,8 @@ tn_status check_device_error(Plan& P);
 
 // true when the tcgen05 kernels are compiled in
 bool tc_supported();
-// the tensor-core kernel's shape limits for a step (rows m, columns n, depth k)
-bool tc_step_ok(int64_t m, int64_t n, int64_t k);
+// the tensor-core kernel's shape limits for a step (rows m, columns n, depth k) in form prec
+bool tc_step_ok(int64_t m, int64_t n, int64_t k, int32_t prec);
 
 inline int64_t elem_bytes(const Plan& P) { return P.is_complex ? 8 : 4; }
 

@@ -137,3 +137,24 @@ def test_sliced_plan_batches():
     plan = tn.Plan(w.net, w.path, w.sliced, max_slice_batch=4, host_only=True)
     info = plan.info()
     assert info["n_slices"] == 16 and info["slice_batch"] == 4 and info["n_passes"] == 4
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32", "fp32"])
+def test_split_bf16_operands_exactly_the_tc_operands(prec):
+    """In a BF16x3 plan every operand of a tensor-core step (and nothing else) is stored
+    in the split-BF16 form, so its producer writes hi/lo planes and the GEMM reads them
+    as they are; the other forms store everything planar."""
+    tn = ensure_built()
+    w = workloads.random_circuit(4, 5, 12, 40, n_sliced=3)
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=4, host_only=True)
+    n_t = len(w.net.tensors) + len(w.path.pairs)
+    tc_operands = set()
+    for s in range(len(w.path.pairs)):
+        st = plan.step(s)
+        if st["cls"] == tn.TN_CLASS_TC:
+            tc_operands |= {st["a_id"], st["b_id"]}
+    if prec != "fp32":
+        assert tc_operands, "the circuit should have tensor-core steps"
+    split = {t for t in range(n_t) if plan.tensor(t)["format"] == 1}
+    assert split == (tc_operands if prec == "bf16x3" else set())
+    plan.destroy()
