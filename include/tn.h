@@ -334,6 +334,89 @@ tn_status tn_batch_destroy(tn_batch_t b);
 tn_status tn_dot_noalloc(const void* a, const void* b, int64_t batch, int64_t m, int64_t n, int64_t k,
                          void* out, void* stream);
 
+/* ---- offline distribution planning (Sec. IV-B), host only ------------------------- */
+/* For a built plan and a device count P, decide which steps run distributed over P
+ * devices, which modes of each distributed intermediate are split across them, and where
+ * along each use-chain to redistribute or gather; report the simulated time of one slice
+ * under the cost model of Sec. IV-B. Nothing is executed and no device memory is used
+ * (this library runs one GPU; the plan is the schedule a multi-GPU executor would follow).
+ *
+ *  * A step is large (Sec. IV-B) if an operand or its output holds >= large_bytes.
+ *  * The first large step of a lineage activates distribution of its output: the modes
+ *    split are the shortest leading prefix of the output's planned order (Sec. IV-A puts
+ *    the longest-lived modes first) whose extents multiply to >= P (Eq. 4), skipping any
+ *    mode the next step contracts.
+ *  * Distribution follows the output into its consumer while the output holds >=
+ *    gather_bytes; where two distributed tensors meet, the larger one carries on and the
+ *    other is gathered (replicated). Each step of a use-chain keeps the modes it
+ *    inherits (no communication) or redistributes its output to a fresh prefix (an
+ *    all-to-all); keeping is not allowed when an inherited mode is contracted by the next
+ *    step (a forced redistribution). A chain ends with a gather of its last output.
+ *  * Step time (Eq. 6): t_gemm = max(bytes read and written per device / dev_bw,
+ *    flops per device / dev_flops); a chain step splits its distributed operand, its
+ *    output and its flops P ways and holds the other operand whole; other steps run
+ *    whole on every device.
+ *  * Redistribution of output C (Eq. 7): |C| (P-1) / (P net_bw) + n_blk max(latency,
+ *    block_bytes / net_bw), where n_blk = |C| / (P * run) and run is the contiguous run of
+ *    C's row-major layout below the innermost mode split before or after the shuffle
+ *    (block_bytes: the base block size). A gather costs the same with nothing split after.
+ *  * The keep/redistribute choices of each chain minimise its summed step and
+ *    communication times by dynamic programming over the set of split modes (Sec. IV-B),
+ *    with the gather added at the end; backtracking gives the redistribution points. */
+typedef struct {
+  int32_t n_gpus;        /* P >= 1 (P = 1: nothing is distributed) */
+  int32_t reserved0;
+  double large_bytes;    /* s of Sec. IV-B (8 GiB there) */
+  double gather_bytes;   /* distributed outputs below this size are gathered; 0 = large_bytes */
+  double dev_bw;         /* B_dev, bytes/s per device */
+  double dev_flops;      /* F_dev, algorithmic flops/s per device (8 per complex MAC) */
+  double net_bw;         /* B_net, bytes/s per device */
+  double latency;        /* lambda, seconds per message */
+  double block_bytes;    /* s_blk, base block size in bytes */
+} tn_dist_config;
+
+typedef enum {
+  TN_DIST_NONE = 0,          /* runs whole on every device */
+  TN_DIST_ACTIVATE = 1,      /* first step of a use-chain: its output is split (Eq. 4) */
+  TN_DIST_KEEP = 2,          /* output inherits the split modes, no communication */
+  TN_DIST_REDISTRIBUTE = 3,  /* output shuffled to fresh split modes (all-to-all) */
+  TN_DIST_GATHER = 4         /* last step of a use-chain: output replicated */
+} tn_dist_state;
+
+#define TN_DIST_MAX_MODES 16
+
+typedef struct {
+  int32_t state;             /* tn_dist_state */
+  int32_t forced;            /* REDISTRIBUTE only: 1 if keeping was not allowed */
+  int32_t chain;             /* use-chain index, -1 if the step is not on one */
+  int32_t n_dist;            /* modes of the output split across devices after the step */
+  int32_t dist_modes[TN_DIST_MAX_MODES]; /* their labels, in the output's planned order */
+  double t_gemm;             /* Eq. 6, seconds */
+  double t_comm;             /* Eq. 7 redistribution or gather after the step, seconds */
+  double out_bytes;          /* |C| of one slice */
+  int64_t n_blk;             /* blocks per device of that redistribution or gather */
+} tn_dist_step;
+
+typedef struct {
+  int32_t n_chains, n_redistributions, n_forced, n_gathers;
+  int64_t n_large_steps;
+  int64_t dp_states;         /* DP state evaluations over all chains */
+  double t_total;            /* simulated seconds for one slice on P devices */
+  double t_single;           /* the same path on one device (sum of Eq. 6) */
+  double t_comm_total;       /* communication part of t_total */
+  double bytes_redistributed;/* sum of |C| over redistributions and gathers */
+  double speedup;            /* S_P = t_single / t_total (Eq. 9 with the path fixed) */
+  double extra_speedup;      /* E_P = S_P / P (Eq. 10) */
+  double projected_total;    /* T_P^proj = t_total * n_slices (Eq. 8) */
+} tn_dist_report;
+
+/* Plan the distribution of `plan` (any plan, host-only ones included) under `cfg`.
+ * steps: NULL, or an array of the plan's n_steps entries to receive the per-step
+ * schedule. TN_ERR_INVALID for a null plan/config, P < 1 or non-positive rates;
+ * TN_ERR_UNSUPPORTED if a chain cannot be split P ways (a tensor with too few modes). */
+tn_status tn_plan_distribute(tn_plan_t plan, const tn_dist_config* cfg, tn_dist_report* report,
+                             tn_dist_step* steps);
+
 /* Thread-local message for the last non-OK status on this thread. */
 const char* tn_last_error(void);
 

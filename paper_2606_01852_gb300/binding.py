@@ -86,6 +86,29 @@ class tn_serve_config(C.Structure):
                 ("reserved", C.c_int32 * 3)]
 
 
+class tn_dist_config(C.Structure):
+    _fields_ = [("n_gpus", C.c_int32), ("reserved0", C.c_int32), ("large_bytes", C.c_double),
+                ("gather_bytes", C.c_double), ("dev_bw", C.c_double), ("dev_flops", C.c_double),
+                ("net_bw", C.c_double), ("latency", C.c_double), ("block_bytes", C.c_double)]
+
+
+class tn_dist_step(C.Structure):
+    _fields_ = [("state", C.c_int32), ("forced", C.c_int32), ("chain", C.c_int32), ("n_dist", C.c_int32),
+                ("dist_modes", C.c_int32 * 16), ("t_gemm", C.c_double), ("t_comm", C.c_double),
+                ("out_bytes", C.c_double), ("n_blk", C.c_int64)]
+
+
+class tn_dist_report(C.Structure):
+    _fields_ = [("n_chains", C.c_int32), ("n_redistributions", C.c_int32), ("n_forced", C.c_int32),
+                ("n_gathers", C.c_int32), ("n_large_steps", C.c_int64), ("dp_states", C.c_int64),
+                ("t_total", C.c_double), ("t_single", C.c_double), ("t_comm_total", C.c_double),
+                ("bytes_redistributed", C.c_double), ("speedup", C.c_double), ("extra_speedup", C.c_double),
+                ("projected_total", C.c_double)]
+
+
+DIST_STATES = ("none", "activate", "keep", "redistribute", "gather")
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_2606_01852_gb300.build.build()")
@@ -117,6 +140,7 @@ def _load():
         "tn_batch_contract_graph": [vp, vp, vp, vp, vp],
         "tn_batch_autotune": [vp, vp, vp, vp, vp],
         "tn_batch_destroy": [vp],
+        "tn_plan_distribute": [vp, C.POINTER(tn_dist_config), C.POINTER(tn_dist_report), C.POINTER(tn_dist_step)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -273,6 +297,27 @@ class Plan:
         buf = (C.c_double * max(1, n))()
         check(lib.tn_plan_profile_steps(self.handle, buf, n))
         return list(buf[:n])
+
+    def distribute(self, n_gpus, large_bytes=8 * 2**30, gather_bytes=0.0, dev_bw=6.6e12, dev_flops=5.5e14,
+                   net_bw=9.0e11, latency=5e-6, block_bytes=4096.0):
+        """Offline distribution plan of Sec. IV-B (tn_plan_distribute): returns (report,
+        steps), the per-step schedule as dicts (state name, split modes, Eq. 6/7 times).
+        Defaults: one GB300 (measured HBM copy rate, the BF16x3 form's rate) on an NVLink
+        domain (900 GB/s per direction), 5 us per message, 4 KiB base blocks."""
+        cfg = tn_dist_config(n_gpus=n_gpus, large_bytes=large_bytes, gather_bytes=gather_bytes, dev_bw=dev_bw,
+                             dev_flops=dev_flops, net_bw=net_bw, latency=latency, block_bytes=block_bytes)
+        n = self.info()["n_steps"]
+        rep = tn_dist_report()
+        buf = (tn_dist_step * max(1, n))()
+        check(lib.tn_plan_distribute(self.handle, C.byref(cfg), C.byref(rep), buf))
+        report = {f: getattr(rep, f) for f, _ in tn_dist_report._fields_}
+        steps = []
+        for s in range(n):
+            r = buf[s]
+            steps.append({"state": DIST_STATES[r.state], "forced": bool(r.forced), "chain": r.chain,
+                          "dist_modes": list(r.dist_modes[:r.n_dist]), "t_gemm": r.t_gemm, "t_comm": r.t_comm,
+                          "out_bytes": r.out_bytes, "n_blk": r.n_blk})
+        return report, steps
 
     def launches_per_call(self, count=None) -> int:
         """Kernel launches of one contract over `count` slices (default all)."""
