@@ -37,16 +37,28 @@ WORKLOAD_DESC = {
     "rc40": "40-qubit 5x8 grid random circuit, 13 brick-wall cycles of Haar 2-qubit gates, "
             "one amplitude, greedy path, 8 sliced labels (256 slices), complex64",
     "kising44": "4x4 kicked Ising, 10 Trotter steps (J=1, dt=0.25, h=0.9), <Z_centre>, complex64",
+    "khex45": "kicked Ising on a 4x5 honeycomb (brick-wall) lattice, 6 Trotter steps (J=1, dt=0.25, "
+              "h=0.9), <Z_centre>, complex64",
+    "ktri44": "kicked Ising on a 4x4 triangular lattice, 8 Trotter steps (J=1, dt=0.25, h=0.9), "
+              "<Z_centre>, complex64",
     "rc12": "12-qubit 3x4 random circuit, 8 cycles, one amplitude, complex64",
+    "rc40u": "the rc40 network and path without slicing: every intermediate whole (largest 2^32 "
+             "complex64 elements), one contraction per step, complex64",
     "rc40open": "the 40-qubit rc40 circuit with the 2x2 corner qubits (30, 31, 38, 39) left open: "
                 "16 correlated amplitudes per contraction, greedy path, 8 sliced labels (256 slices), "
                 "complex64",
 }
 PREC = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
+# arithmetic of each form (complex64 storage; products as named, FP32 accumulation)
+DTYPE_NAME = {"fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16x3": "bf16x3"}
 # DRAM bytes (read + write) per launch of the dominant kernel, averaged over its launches,
-# from the ncu launch-list capture of this same command (profiles/launches_rc40_3xtf32.md).
-# Only valid for the kernel build the capture was taken on: reset to None when it changes.
-NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 53.463e9}
+# from the ncu launch-list capture of this same command (profiles/launches_rc40_*.md).
+# Only valid for the kernel build the capture was taken on: drop an entry when it changes.
+NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 53.463e9,
+                          ("rc40", "bf16x3", "contract_tc"): 56.768e9}
+# Full-sum values of the CPU complex128 oracle, stored by tests/golden/make_rc40_total.py
+ORACLE_TOTALS = {"rc40": os.path.join(ROOT, "tests", "golden", "rc40_total.json"),
+                 "rc40u": os.path.join(ROOT, "tests", "golden", "rc40_total.json")}
 
 
 def load_peaks():
@@ -271,7 +283,7 @@ def run_ours(args):
     line = {
         "metric": "contraction TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.prec], "data": "synthetic",
         "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, ""),
                    "prec": args.prec, "slices": info["n_slices"], "slice_batch": info["slice_batch"],
                    "passes": info["n_passes"], "flops_per_step": flops,
@@ -290,6 +302,11 @@ def run_ours(args):
         "gpu_launches": plan.launches_per_call() * args.steps,
         "clocks": ck,
     }
+    total_path = ORACLE_TOTALS.get(args.workload)
+    if total_path and os.path.exists(total_path) and result.ndim == 0:
+        want = complex(*json.load(open(total_path))["total"])
+        line["oracle_total"] = [want.real, want.imag]
+        line["rel_err_vs_oracle"] = abs(complex(result) - want) / abs(want)
     if args.check:
         import oracle
         want = np.asarray(oracle.contract(w.net, w.path, w.sliced))
@@ -519,8 +536,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-inflight", type=int, default=16)
     ap.add_argument("--serve-streams", type=int, default=4)
-    ap.add_argument("--prec", default="3xtf32", choices=sorted(PREC),
-                    help="GEMM form: 3xtf32 (default; FP32-accurate), tf32, fp32 (the plain CUDA-core form)")
+    ap.add_argument("--prec", default="bf16x3", choices=sorted(PREC),
+                    help="GEMM form: bf16x3 (default), 3xtf32, tf32, fp32 (the plain CUDA-core form)")
     ap.add_argument("--max-slice-batch", type=int, default=0)
     ap.add_argument("--ref-budget", type=float, default=20.0, help="oracle seconds per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")

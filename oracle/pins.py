@@ -76,9 +76,10 @@ def amplitude_statevector(rows, cols, gates, bitstring):
     return psi[idx]
 
 
-def kicked_ising_statevector(L, ops, center):
-    """<Z_center> after applying the operator list `ops` to |0...0>."""
-    n = L * L
+def kicked_ising_statevector(L, ops, center, n_sites=None):
+    """<Z_center> after applying the operator list `ops` to |0...0> of n_sites qubits
+    (default L * L)."""
+    n = L * L if n_sites is None else n_sites
     psi = np.zeros(2**n, dtype=np.complex128)
     psi[0] = 1.0
     for op in ops:

@@ -420,7 +420,42 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(StepArgs a, double*
   const int64_t k1 = min(a.k, k0 + kc);
   // the output index o is a compile-time constant in every unrolled iteration, so the
   // accumulators stay in registers
-  for (int64_t kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
+  const bool vec = (a.k & 3) == 0 && (a.a_plane & 3) == 0 && (a.b_plane & 3) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
+  if (vec) {
+    // 16-byte loads, four k-steps of the block unrolled: every thread has all of its
+    // loads of the chunk in flight before its first FMA (the step is HBM-bound)
+#pragma unroll 4
+    for (int64_t kk = k0 + 4 * threadIdx.x; kk < k1; kk += 4 * blockDim.x) {
+#pragma unroll
+      for (int o = 0; o < kSplitMaxOut; ++o) {
+        if (o < mn) {
+          const int i = o / n, j = o - (o / n) * n;
+          const float4 xr = *reinterpret_cast<const float4*>(A + i * a.k + kk);
+          const float4 yr = *reinterpret_cast<const float4*>(B + j * a.k + kk);
+          if (CPLX) {
+            const float4 xi = *reinterpret_cast<const float4*>(A + a.a_plane + i * a.k + kk);
+            const float4 yi = *reinterpret_cast<const float4*>(B + a.b_plane + j * a.k + kk);
+            const float ar[4] = {xr.x * sa, xr.y * sa, xr.z * sa, xr.w * sa};
+            const float ai[4] = {xi.x * sa, xi.y * sa, xi.z * sa, xi.w * sa};
+            const float br[4] = {yr.x * sb, yr.y * sb, yr.z * sb, yr.w * sb};
+            const float bi[4] = {yi.x * sb, yi.y * sb, yi.z * sb, yi.w * sb};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              accr[o] = fmaf(ar[e], br[e], fmaf(-ai[e], bi[e], accr[o]));
+              acci[o] = fmaf(ar[e], bi[e], fmaf(ai[e], br[e], acci[o]));
+            }
+          } else {
+            accr[o] = fmaf(xr.x * sa, yr.x * sb, accr[o]);
+            accr[o] = fmaf(xr.y * sa, yr.y * sb, accr[o]);
+            accr[o] = fmaf(xr.z * sa, yr.z * sb, accr[o]);
+            accr[o] = fmaf(xr.w * sa, yr.w * sb, accr[o]);
+          }
+        }
+      }
+    }
+  }
+  for (int64_t kk = k0 + threadIdx.x; !vec && kk < k1; kk += blockDim.x) {
 #pragma unroll
     for (int o = 0; o < kSplitMaxOut; ++o) {
       if (o < mn) {
@@ -468,23 +503,43 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(StepArgs a, double*
   }
 }
 
-__global__ void splitk_final_kernel(StepArgs a, const double* scratch, int32_t chunks, int32_t cplx) {
+constexpr int kFinalThreads = 128;
+
+__global__ void __launch_bounds__(kFinalThreads) splitk_final_kernel(StepArgs a, const double* scratch,
+                                                                    int32_t chunks, int32_t cplx) {
   const int b = blockIdx.x;
   const int m = (int)a.m, n = (int)a.n, mn = m * n;
   float* C = a.C + b * a.c_bstride;
+  __shared__ double part[2][kFinalThreads];
   int lmax = -127;
-  for (int o = threadIdx.x; o < mn; o += blockDim.x) {
-    double vr = 0.0, vi = 0.0;
-    for (int c = 0; c < chunks; ++c) {
+  // thread t adds the partials of a contiguous run of chunks in order; thread 0 then adds
+  // the runs in order: a fixed association for a given chunk count (deterministic)
+  const int per = (chunks + kFinalThreads - 1) / kFinalThreads;
+  for (int o = 0; o < mn; ++o) {
+    double sr = 0.0, si = 0.0;
+    const int c0 = threadIdx.x * per, c1 = min(chunks, c0 + per);
+    for (int c = c0; c < c1; ++c) {
       const double* p = scratch + (((int64_t)b * chunks + c) * mn + o) * 2;
-      vr += p[0];
-      vi += p[1];
+      sr += p[0];
+      si += p[1];
     }
-    const int i = o / n, j = o % n;
-    const int64_t off = map_offset(a.rows, i) + map_offset(a.cols, j);
-    if (cplx) store_cplx(C, a.c_plane, off, (float)vr, (float)vi, a.c_split != 0);
-    else C[off] = (float)vr;
-    if (a.recs) lmax = max(lmax, exp_of(cplx ? fmaxf(fabsf((float)vr), fabsf((float)vi)) : fabsf((float)vr)));
+    part[0][threadIdx.x] = sr;
+    part[1][threadIdx.x] = si;
+    __syncthreads();
+    double vr = 0.0, vi = 0.0;
+    if (threadIdx.x == 0)
+      for (int t = 0; t < kFinalThreads; ++t) {
+        vr += part[0][t];
+        vi += part[1][t];
+      }
+    __syncthreads();  // every thread, every o: part is rewritten next iteration
+    if (threadIdx.x == 0) {
+      const int i = o / n, j = o % n;
+      const int64_t off = map_offset(a.rows, i) + map_offset(a.cols, j);
+      if (cplx) store_cplx(C, a.c_plane, off, (float)vr, (float)vi, a.c_split != 0);
+      else C[off] = (float)vr;
+      if (a.recs) lmax = max(lmax, exp_of(cplx ? fmaxf(fabsf((float)vr), fabsf((float)vi)) : fabsf((float)vr)));
+    }
   }
   if (a.recs) {
     ScaleRec* rc = a.recs + a.rec_c + (a.c_bstride ? b : 0);
@@ -504,7 +559,7 @@ void launch_contract_splitk(const StepArgs& a, int32_t nb, bool cplx, double* sc
   dim3 grid((unsigned)chunks, (unsigned)nb);
   if (cplx) splitk_partial_kernel<true><<<grid, 256, 0, st>>>(a, scratch, kSplitChunk, chunks);
   else splitk_partial_kernel<false><<<grid, 256, 0, st>>>(a, scratch, kSplitChunk, chunks);
-  splitk_final_kernel<<<(unsigned)nb, 64, 0, st>>>(a, scratch, chunks, cplx ? 1 : 0);
+  splitk_final_kernel<<<(unsigned)nb, kFinalThreads, 0, st>>>(a, scratch, chunks, cplx ? 1 : 0);
 }
 
 }  // namespace tn

@@ -85,6 +85,59 @@ def test_kising44_full(tn, prec, tol):
     assert abs(complex(out.cpu()) - want) / abs(want) < tol
 
 
+@pytest.mark.parametrize("name", ["khex45", "ktri44"])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("3xtf32", 1e-4), ("bf16x3", 1e-4), ("tf32", 1e-1)])
+def test_lattice_dynamics_full(tn, name, prec, tol):
+    """Kicked Ising on the honeycomb and triangular lattices: same bounds as the square one."""
+    w = workloads.BY_NAME[name]()
+    plan = tn.Plan(w.net, w.path, prec=prec)
+    if prec != "fp32":
+        assert plan.info()["steps_per_class"][tn.TN_CLASS_TC] > 0
+    out = torch.zeros((), dtype=torch.complex128, device="cuda")
+    plan.contract(dev(w.net), out)
+    torch.cuda.synchronize()
+    want = complex(*GOLD[name]["value"])
+    assert abs(complex(out.cpu()) - want) / abs(want) < tol
+    plan.destroy()
+
+
+def _rc40_total():
+    return complex(*json.load(open(os.path.join(ROOT, "tests", "golden", "rc40_total.json")))["total"])
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-5), ("3xtf32", 2e-5)])
+def test_rc40_full_sum_bench_config(tn, prec, tol):
+    """All 256 slices at the benchmark's launch configuration (128 slices per launch, two
+    passes, FP64 Neumaier sum across slices) against the oracle's full sum. Bound: the
+    slice errors are independent, so the sum's error relative to the amplitude stays at
+    the per-slice level (measured: 1e-6 for BF16x3, 8.8e-6 for 3xTF32)."""
+    w = workloads.rc40()
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=128)
+    assert plan.info()["n_passes"] == 2
+    out = torch.zeros((), dtype=torch.complex128, device="cuda")
+    plan.contract(dev(w.net), out)
+    torch.cuda.synchronize()
+    want = _rc40_total()
+    assert abs(complex(out.cpu()) - want) / abs(want) < tol, (complex(out.cpu()), want)
+    plan.destroy()
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-5), ("3xtf32", 2e-5)])
+def test_rc40_unsliced_equals_sliced_sum(tn, prec, tol):
+    """The same amplitude with no slicing (intermediates up to 2^32 elements, one
+    contraction): equal to the oracle's sum over the 256 slices (Sec. II-C: slicing is an
+    exact partition of the sum)."""
+    w = workloads.rc40u()
+    plan = tn.Plan(w.net, w.path, prec=prec)
+    assert plan.info()["peak_elems"] == 2**32
+    out = torch.zeros((), dtype=torch.complex128, device="cuda")
+    plan.contract(dev(w.net), out)
+    torch.cuda.synchronize()
+    want = _rc40_total()
+    assert abs(complex(out.cpu()) - want) / abs(want) < tol, (complex(out.cpu()), want)
+    plan.destroy()
+
+
 def test_rc12_full(tn):
     w = workloads.rc12()
     plan = tn.Plan(w.net, w.path, prec="3xtf32")

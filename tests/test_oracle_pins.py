@@ -155,6 +155,46 @@ def test_kicked_ising_closed_forms(J, h, dt):
     assert abs(got - pins.kicked_ising_closed_form(L, T, J, h, dt)) < 1e-12
 
 
+@pytest.mark.parametrize("rows,cols", [(3, 4), (4, 5), (5, 5)])
+def test_lattice_bond_structure(rows, cols):
+    """Bond sets of the three lattices: counts in closed form and the coordination numbers
+    (square 4, honeycomb 3, triangular 6 for interior sites)."""
+    import collections
+    sq = kicked_ising.lattice_bonds(rows, cols, "square")
+    hx = kicked_ising.lattice_bonds(rows, cols, "hexagonal")
+    tr = kicked_ising.lattice_bonds(rows, cols, "triangular")
+    assert len(sq) == rows * (cols - 1) + (rows - 1) * cols
+    assert len(tr) == len(sq) + (rows - 1) * (cols - 1)
+    n_vert = sum(1 for r in range(rows - 1) for c in range(cols) if (r + c) % 2 == 0)
+    assert len(hx) == rows * (cols - 1) + n_vert
+    for bonds in (sq, hx, tr):
+        assert len(set(bonds)) == len(bonds) and all(a < b for a, b in bonds)
+    deg = {name: collections.Counter(x for e in b for x in e) for name, b in (("sq", sq), ("hx", hx), ("tr", tr))}
+    interior = [r * cols + c for r in range(1, rows - 1) for c in range(1, cols - 1)]
+    assert all(deg["sq"][q] == 4 and deg["hx"][q] == 3 and deg["tr"][q] == 6 for q in interior)
+    assert max(deg["hx"].values()) == 3
+
+
+@pytest.mark.parametrize("lattice,rows,cols,T", [("hexagonal", 3, 4, 2), ("triangular", 3, 3, 2),
+                                                  ("hexagonal", 2, 5, 3)])
+def test_kicked_ising_lattices_vs_statevector(lattice, rows, cols, T):
+    net = kicked_ising.expectation_network(rows, T, 1.0, 0.9, 0.25, cols=cols, lattice=lattice)
+    path = greedy.greedy_path(net, seed=0, alpha=1.0)
+    got = oracle.contract(net, path)
+    want = pins.kicked_ising_statevector(rows, net.meta["ops"], net.meta["center"], n_sites=rows * cols)
+    assert abs(got.imag) < 1e-12 and abs(got.real - want) < 1e-12, (got, want)
+
+
+@pytest.mark.parametrize("lattice", ["hexagonal", "triangular"])
+@pytest.mark.parametrize("J,h,dt", [(1.0, 0.0, 0.25), (0.0, 0.7, 0.3)])
+def test_kicked_ising_lattices_closed_forms(lattice, J, h, dt):
+    rows, cols, T = 3, 3, 3
+    net = kicked_ising.expectation_network(rows, T, J, h, dt, cols=cols, lattice=lattice)
+    path = greedy.greedy_path(net, seed=1, alpha=1.0)
+    got = oracle.contract(net, path)
+    assert abs(got - pins.kicked_ising_closed_form(rows, T, J, h, dt)) < 1e-12
+
+
 @pytest.mark.parametrize("n,seed", [(10, 1), (16, 2), (20, 3)])
 def test_ising_3regular_vs_enumeration(n, seed):
     net = ising_pf.random_3regular_network(n, seed, beta=0.5)

@@ -4,11 +4,16 @@
               greedy path, no slicing (the tiny circuit case).
   rc40      : 40-qubit 5x8 grid random circuit, 13 cycles, one amplitude, greedy path
               with 8 sliced labels (256 slices). The headline workload.
+  rc40u     : rc40 with no slicing (the same network and path; largest intermediate 2^32
+              complex64 = 32 GiB, which one GPU's HBM holds).
   rc40open  : rc40 with the 2x2 corner block of qubits left open, so one contraction
               yields 16 correlated amplitudes (a [2,2,2,2] output tensor); 256 slices.
   kising44  : 4x4 kicked Ising, 10 Trotter steps, J=1, dt=0.25, h=0.9, <Z_centre>
               (the dynamics expectation case at a size one GPU and the oracle can
               contract unsliced).
+  khex45    : kicked Ising, same couplings, on a 4x5 honeycomb lattice (brick-wall form),
+              6 Trotter steps;
+  ktri44    : kicked Ising on a 4x4 triangular lattice, 8 Trotter steps;
   ising3r   : an ensemble of Ising partition functions on random 3-regular graphs.
 Smaller variants with the same structure serve as parity cases.
 
@@ -55,8 +60,8 @@ def random_circuit(rows, cols, cycles, seed, n_sliced=0, open_qubits=()):
 
 
 @functools.lru_cache(maxsize=None)
-def kicked(L, T, J=1.0, h=0.9, dt=0.25):
-    net = kicked_ising.expectation_network(L, T, J, h, dt)
+def kicked(L, T, J=1.0, h=0.9, dt=0.25, cols=None, lattice="square"):
+    net = kicked_ising.expectation_network(L, T, J, h, dt, cols=cols, lattice=lattice)
     return _pathed(net.name, net)
 
 
@@ -66,6 +71,12 @@ def rc12():
 
 def rc40():
     return random_circuit(5, 8, 13, 40, n_sliced=8)
+
+
+def rc40u():
+    """rc40 without slicing: the same network and path, every intermediate whole (largest
+    2^32 elements, a 51 GiB workspace in complex64)."""
+    return random_circuit(5, 8, 13, 40)
 
 
 # the 2x2 block of qubits in the grid's last corner (rows 3-4, columns 6-7) stays open
@@ -82,6 +93,16 @@ def kising44():
     return kicked(4, 10)
 
 
+def khex45():
+    """Kicked Ising on a 4 x 5 honeycomb (brick-wall) lattice, 6 Trotter steps."""
+    return kicked(4, 6, cols=5, lattice="hexagonal")
+
+
+def ktri44():
+    """Kicked Ising on a 4 x 4 triangular lattice, 8 Trotter steps."""
+    return kicked(4, 8, lattice="triangular")
+
+
 def ising_workload(net):
     path, info = greedy.best_greedy(net, range(2), (0.0, 1.0))
     return Workload(net.name, net, path, (), info)
@@ -91,4 +112,5 @@ def ising3r(count, seed=3):
     return [ising_workload(n) for n in ising_pf.ensemble(count, seed)]
 
 
-BY_NAME = {"rc12": rc12, "rc40": rc40, "kising44": kising44, "rc40open": rc40open}
+BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40u": rc40u, "kising44": kising44, "rc40open": rc40open,
+           "khex45": khex45, "ktri44": ktri44}
