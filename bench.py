@@ -56,9 +56,25 @@ DTYPE_NAME = {"fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16x3": "bf16
 # Only valid for the kernel build the capture was taken on: drop an entry when it changes.
 NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 53.463e9,
                           ("rc40", "bf16x3", "contract_tc"): 56.768e9}
-# Full-sum values of the CPU complex128 oracle, stored by tests/golden/make_rc40_total.py
-ORACLE_TOTALS = {"rc40": os.path.join(ROOT, "tests", "golden", "rc40_total.json"),
-                 "rc40u": os.path.join(ROOT, "tests", "golden", "rc40_total.json")}
+# Full values of the CPU oracle stored by the scripts in tests/golden/ (they call only the
+# oracle): the 40-qubit sum over all slices, and the full values of the smaller workloads.
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def stored_oracle_value(workload):
+    if workload in ("rc40", "rc40u"):
+        path, key = os.path.join(GOLDEN, "rc40_total.json"), None
+    else:
+        path, key = os.path.join(GOLDEN, "oracle_values.json"), workload
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if key is not None:
+        d = d.get(key, {})
+        v = d.get("value")
+    else:
+        v = d.get("total")
+    return complex(*v) if v is not None else None
 
 
 def load_peaks():
@@ -109,23 +125,38 @@ class ClockSampler:
 
 def oracle_sample(w, budget_s, slice_id=0):
     """The CPU oracle, as it stands, on one slice of the workload, step by step in path
-    order until `budget_s` of CPU time: returns (flops done, seconds, steps done)."""
+    order until `budget_s` of CPU time: returns (flops done, seconds, steps done). A step
+    predicted to overrun the budget is not started (one step of an unsliced large network
+    can take minutes): the prediction uses the host's matrix-product rate, timed here, or
+    for the max-plus loop the rate of the steps done so far."""
     import oracle
     from oracle import core
     vals = core.slice_assignment(w.net, w.sliced, slice_id)
     arrays, modes = core.restrict_leaves(w.net, vals)
-    ts = [np.asarray(t, dtype=np.complex128) for t in arrays]
+    semiring = w.info.get("semiring", "standard")
+    ts = [np.asarray(t, dtype=np.complex128 if w.net.is_complex else np.float64) for t in arrays]
     ms = [tuple(m) for m in modes]
     keep = set(w.net.open_modes)
     costs = oracle.step_costs(w.net, w.path, w.sliced)
     flops, done = 0.0, 0
     t0 = time.perf_counter()
+    fm = 8.0 if w.net.is_complex else 2.0
+    probe = np.ones((512, 512), dtype=ts[0].dtype)
+    tp = time.perf_counter()
+    for _ in range(4):
+        probe = probe @ probe * 1e-3
+    host_rate = 4 * fm * 512.0 ** 3 / (time.perf_counter() - tp)
+    t0 = time.perf_counter()
     for s, (i, j) in enumerate(w.path.pairs):
-        c, mc = core.pairwise(ts[i], ms[i], ts[j], ms[j], keep)
+        el = time.perf_counter() - t0
+        rate = host_rate if semiring == "standard" else (flops / el if flops > 0 and el > 0 else None)
+        if done > 0 and rate and el + fm * costs[s]["Ct"] / rate > budget_s:
+            break
+        c, mc = core.pairwise(ts[i], ms[i], ts[j], ms[j], keep, semiring)
         ts.append(c)
         ms.append(mc)
         ts[i] = ts[j] = None
-        flops += 8.0 * costs[s]["Ct"]
+        flops += fm * costs[s]["Ct"]
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
@@ -197,12 +228,16 @@ def run_ours(args):
         dist.init_process_group("nccl")
     peaks = load_peaks()
     w = workloads.BY_NAME[args.workload]()
-    prec = PREC[args.prec]
-    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=args.max_slice_batch)
+    semiring = w.info.get("semiring", "standard")
+    cplx = w.net.is_complex
+    # real networks (the max-plus workloads) run the R32 FP32 form
+    prec = PREC[args.prec] if cplx else tn.TN_R32_FP32_SIMT
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=args.max_slice_batch, semiring=semiring)
     info = plan.info()
     stream = torch.cuda.current_stream()
-    ins = [torch.tensor(np.asarray(t), dtype=torch.complex64, device="cuda") for t in w.net.tensors]
-    out = torch.zeros(plan.out_shape, dtype=torch.complex128, device="cuda")
+    in_dt, out_dt = (torch.complex64, torch.complex128) if cplx else (torch.float32, torch.float64)
+    ins = [torch.tensor(np.asarray(t), dtype=in_dt, device="cuda") for t in w.net.tensors]
+    out = torch.zeros(plan.out_shape, dtype=out_dt, device="cuda")
     ls = torch.zeros(1, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     for _ in range(args.warmup):
@@ -255,7 +290,10 @@ def run_ours(args):
         achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": form_peak, "unit": "TFLOP/s"}
     else:
-        alu = SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        # FFMA: 2 flops per lane per cycle; max-plus: an FADD and an FMNMX per term, i.e. the
+        # 2 counted ops take 2 lane-cycles
+        ops_per_lane = 1 if semiring == "maxplus" else 2
+        alu = SM_COUNT * FP32_LANES * ops_per_lane * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -268,8 +306,9 @@ def run_ours(args):
     roof["peak_source"] = peaks["_source"]
 
     # end to end through the public C ABI with host buffers
-    host_in = [np.ascontiguousarray(np.asarray(t, dtype=np.complex64)) for t in w.net.tensors]
-    host_out = np.zeros(plan.out_shape, dtype=np.complex128)
+    host_in = [np.ascontiguousarray(np.asarray(t, dtype=np.complex64 if cplx else np.float32))
+               for t in w.net.tensors]
+    host_out = np.zeros(plan.out_shape, dtype=np.complex128 if cplx else np.float64)
     host_ls = np.zeros(1)
     h2d = int(sum(a.nbytes for a in host_in))
     plan.contract_host(host_in, host_out, host_ls)
@@ -283,9 +322,11 @@ def run_ours(args):
     line = {
         "metric": "contraction TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.prec], "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+        "dtype": DTYPE_NAME[args.prec] if cplx else ("f32 (max,+)" if semiring == "maxplus" else "f32"),
         "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, ""),
-                   "prec": args.prec, "slices": info["n_slices"], "slice_batch": info["slice_batch"],
+                   "prec": args.prec if cplx else "r32", "semiring": semiring,
+                   "slices": info["n_slices"], "slice_batch": info["slice_batch"],
                    "passes": info["n_passes"], "flops_per_step": flops,
                    "algorithmic_bytes_per_step": info["bytes"],
                    "l2": "256 MiB buffer written between timed steps (L2 is 129 MB); "
@@ -302,14 +343,13 @@ def run_ours(args):
         "gpu_launches": plan.launches_per_call() * args.steps,
         "clocks": ck,
     }
-    total_path = ORACLE_TOTALS.get(args.workload)
-    if total_path and os.path.exists(total_path) and result.ndim == 0:
-        want = complex(*json.load(open(total_path))["total"])
+    want = stored_oracle_value(args.workload)
+    if want is not None and result.ndim == 0:
         line["oracle_total"] = [want.real, want.imag]
         line["rel_err_vs_oracle"] = abs(complex(result) - want) / abs(want)
     if args.check:
         import oracle
-        want = np.asarray(oracle.contract(w.net, w.path, w.sliced))
+        want = np.asarray(oracle.contract(w.net, w.path, w.sliced, semiring=semiring))
         line["oracle"] = [float(want.flat[0].real), float(want.flat[0].imag)]
         line["rel_err_vs_oracle"] = float(np.max(np.abs(result - want)) / np.max(np.abs(want)))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
