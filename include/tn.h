@@ -60,6 +60,16 @@ typedef enum {
   TN_R32_BF16X3 = 7
 } tn_precision;
 
+/* The semiring the network is contracted over (Sec. III-C: counting and optimisation
+ * problems as contractions of local-constraint tensors).
+ *   STANDARD : (+, x), every form above.
+ *   MAXPLUS  : (max, +), the tropical semiring: a step computes
+ *              C[i, j] = max_k (A[i, k] + B[j, k]) and slices combine by maximum. Only
+ *              with TN_R32_FP32_SIMT and no exponent scaling (TN_ERR_UNSUPPORTED
+ *              otherwise); FP32 max and add, exact while the values are integers below
+ *              2^24; -inf is the semiring's zero (an excluded configuration). */
+typedef enum { TN_SEMIRING_STANDARD = 0, TN_SEMIRING_MAXPLUS = 1 } tn_semiring;
+
 /* Plan flags. */
 #define TN_PLAN_HOST_ONLY 1u     /* plan and query only: no device memory, no contract */
 
@@ -69,7 +79,8 @@ typedef struct {
   int32_t exp_scaling;     /* 1: per-intermediate power-of-two scaling, log scale in FP64 */
   int32_t max_slice_batch; /* slices per device pass; 0 = as many as fit in free HBM */
   uint32_t flags;          /* TN_PLAN_* */
-  int32_t reserved[3];
+  int32_t semiring;        /* tn_semiring */
+  int32_t reserved[2];
 } tn_dtype_policy;
 
 /* A network: tensor t has rank[t] modes modes[t][0..rank[t]-1] (labels in

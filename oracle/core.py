@@ -17,6 +17,11 @@ result does not depend on the order), in complex128 (float64 for real networks):
   3. permute the root into the requested open-mode order;
   4. sum the slice results with Neumaier's compensated summation in slice-id order.
 
+Semirings (Sec. III-C: counting and optimisation problems as contractions over other
+semirings): semiring="maxplus" replaces the sum over labels by a maximum and the product
+of tensors by a sum, so step 2 computes C[i, j] = max_k (A[i, k] + B[k, j]) (a plain loop
+over k) and step 4 takes the maximum over slices. The default is the ordinary (+, x).
+
 Also: the per-step cost counts of Sec. II-B (Eqs. 1-3), restated here on the oracle
 side from the same definitions, for checking plan statistics.
 """
@@ -48,7 +53,7 @@ def restrict_leaves(net, vals):
     return arrays, modes
 
 
-def pairwise(a, ma, b, mb, keep):
+def pairwise(a, ma, b, mb, keep, semiring="standard"):
     """One step: reduce the labels both operands carry (unless kept open)."""
     K = [x for x in ma if x in mb and x not in keep]
     M = [x for x in ma if x not in K]
@@ -62,18 +67,23 @@ def pairwise(a, ma, b, mb, keep):
     k = int(np.prod([a.shape[ma.index(x)] for x in K], dtype=np.int64))
     A = np.transpose(a, pa).reshape(m, k)
     B = np.transpose(b, pb).reshape(k, n)
-    C = A @ B
+    if semiring == "maxplus":
+        C = np.full((m, n), -np.inf)
+        for kk in range(k):
+            C = np.maximum(C, A[:, kk, None] + B[None, kk, :])
+    else:
+        C = A @ B
     shape = [a.shape[ma.index(x)] for x in M] + [b.shape[mb.index(x)] for x in N]
     return C.reshape(shape), tuple(M + N)
 
 
-def contract_one(net, path, arrays, modes):
+def contract_one(net, path, arrays, modes, semiring="standard"):
     dtype = np.complex128 if any(np.iscomplexobj(t) for t in arrays) else np.float64
     ts = [np.asarray(t, dtype=dtype) for t in arrays]
     ms = [tuple(m) for m in modes]
     keep = set(net.open_modes)
     for (i, j) in path.pairs:
-        c, mc = pairwise(ts[i], ms[i], ts[j], ms[j], keep)
+        c, mc = pairwise(ts[i], ms[i], ts[j], ms[j], keep, semiring)
         ts.append(c)
         ms.append(mc)
         ts[i] = ts[j] = None  # each tensor is consumed once
@@ -102,8 +112,8 @@ class Neumaier:
         return self.s + self.c
 
 
-def contract_slices(net, path, sliced=(), slice_ids=None, return_partials=False):
-    """Sum of the slice results over `slice_ids` (default: all slices)."""
+def contract_slices(net, path, sliced=(), slice_ids=None, return_partials=False, semiring="standard"):
+    """Sum (max-plus: maximum) of the slice results over `slice_ids` (default: all)."""
     sliced = list(sliced)
     n_slices = 1
     for x in sliced:
@@ -111,25 +121,32 @@ def contract_slices(net, path, sliced=(), slice_ids=None, return_partials=False)
     ids = range(n_slices) if slice_ids is None else list(slice_ids)
     partials = []
     acc_re = acc_im = None
+    best = None
     for sid in ids:
         vals = slice_assignment(net, sliced, sid)
         arrays, modes = restrict_leaves(net, vals)
-        r = contract_one(net, path, arrays, modes)
+        r = contract_one(net, path, arrays, modes, semiring)
         if return_partials:
             partials.append(r)
+        if semiring == "maxplus":
+            best = r if best is None else np.maximum(best, r)
+            continue
         if acc_re is None:
             acc_re, acc_im = Neumaier(np.real(r)), Neumaier(np.real(r))
         acc_re.add(np.real(r))
         acc_im.add(np.imag(r))
-    total = acc_re.value() + 1j * acc_im.value() if net.is_complex else acc_re.value()
+    if semiring == "maxplus":
+        total = best
+    else:
+        total = acc_re.value() + 1j * acc_im.value() if net.is_complex else acc_re.value()
     if return_partials:
         return total, partials
     return total
 
 
-def contract(net, path, sliced=()):
+def contract(net, path, sliced=(), semiring="standard"):
     """Exact result of the network along `path`, summing every slice."""
-    return contract_slices(net, path, sliced)
+    return contract_slices(net, path, sliced, semiring=semiring)
 
 
 # ---- cost counts (Sec. II-B, Eqs. 1-3), for plan-statistics checks -------------------

@@ -7,7 +7,9 @@ None of these evaluates a network pairwise; each reaches the same number another
     each gate to the two (or one) qubit axes it acts on;
   * ising_*: the Ising partition function by enumerating spin configurations, and the
     1D ring's transfer-matrix closed form Z = l1^N + l2^N with l = e^{bJ} +- e^{-bJ};
-  * kicked-Ising special cases with closed forms.
+  * kicked-Ising special cases with closed forms;
+  * independent sets: count and maximum size by checking every vertex subset, and the
+    closed forms for paths (Fibonacci), cycles (Lucas) and the full King's graph.
 """
 from __future__ import annotations
 
@@ -119,3 +121,52 @@ def ising_ring_closed_form(n, J, beta):
     l1 = math.exp(beta * J) + math.exp(-beta * J)
     l2 = math.exp(beta * J) - math.exp(-beta * J)
     return l1**n + l2**n
+
+
+# ---- independent sets (the semiring family of Sec. III-C) --------------------------------
+
+def independent_sets_enumerate(n, edges):
+    """(number of independent sets, size of a maximum one) by checking every vertex subset."""
+    adj = [0] * n
+    for u, v in edges:
+        adj[u] |= 1 << v
+        adj[v] |= 1 << u
+    count, best = 0, 0
+    for mask in range(1 << n):
+        ok = True
+        m = mask
+        while m:
+            u = (m & -m).bit_length() - 1
+            if adj[u] & mask:
+                ok = False
+                break
+            m &= m - 1
+        if ok:
+            count += 1
+            best = max(best, bin(mask).count("1"))
+    return count, best
+
+
+def _fib(k):
+    a, b = 0, 1
+    for _ in range(k):
+        a, b = b, a + b
+    return a
+
+
+def path_graph_closed_form(n):
+    """Path on n >= 1 vertices: F(n + 2) independent sets (Fibonacci, F(1) = F(2) = 1), and
+    a maximum one has ceil(n / 2) vertices."""
+    return _fib(n + 2), (n + 1) // 2
+
+
+def cycle_graph_closed_form(n):
+    """Cycle on n >= 3 vertices: the Lucas number L(n) = F(n - 1) + F(n + 1) independent
+    sets, and a maximum one has floor(n / 2) vertices."""
+    return _fib(n - 1) + _fib(n + 1), n // 2
+
+
+def kings_full_mis(L):
+    """The full L x L King's graph: every 2 x 2 block holds at most one vertex of an
+    independent set and the sites with even row and column reach that, ceil(L/2)^2."""
+    return ((L + 1) // 2) ** 2

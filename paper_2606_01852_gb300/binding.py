@@ -47,7 +47,8 @@ class tn_path(C.Structure):
 
 class tn_dtype_policy(C.Structure):
     _fields_ = [("prec", C.c_int32), ("complex_mult", C.c_int32), ("exp_scaling", C.c_int32),
-                ("max_slice_batch", C.c_int32), ("flags", C.c_uint32), ("reserved", C.c_int32 * 3)]
+                ("max_slice_batch", C.c_int32), ("flags", C.c_uint32), ("semiring", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class tn_plan_stats(C.Structure):
@@ -176,10 +177,14 @@ def _ptr(x):
     raise TypeError(f"cannot take the address of {type(x)}")
 
 
-def make_policy(prec=TN_C64_FP32_SIMT, exp_scaling=False, max_slice_batch=0, host_only=False):
+SEMIRINGS = {"standard": 0, "maxplus": 1}
+
+
+def make_policy(prec=TN_C64_FP32_SIMT, exp_scaling=False, max_slice_batch=0, host_only=False, semiring="standard"):
     if isinstance(prec, str):
         prec = PREC_NAMES[prec]
     p = tn_dtype_policy()
+    p.semiring = SEMIRINGS[semiring]
     p.prec = int(prec)
     p.complex_mult = 4
     p.exp_scaling = 1 if exp_scaling else 0
@@ -214,13 +219,13 @@ class Plan:
     `path` is a list of SSA pairs or an object with .pairs."""
 
     def __init__(self, net, path, sliced=(), prec=TN_C64_FP32_SIMT, exp_scaling=False,
-                 max_slice_batch=0, host_only=False):
+                 max_slice_batch=0, host_only=False, semiring="standard"):
         pairs = path.pairs if hasattr(path, "pairs") else path
         self._arr = _NetArrays([tuple(m) for m in net.modes], dict(net.extent), tuple(net.open_modes),
                                pairs)
         sl = list(sliced)
         self._sl = (C.c_int32 * max(1, len(sl)))(*sl)
-        self.policy = make_policy(prec, exp_scaling, max_slice_batch, host_only)
+        self.policy = make_policy(prec, exp_scaling, max_slice_batch, host_only, semiring)
         self.is_complex = self.policy.prec <= TN_C64_BF16X3
         self.n_leaves = len(net.modes)
         self.n_open = len(net.open_modes)

@@ -54,6 +54,7 @@ StepArgs step_args(const Plan& P, const StepRec& st) {
   a.rec_b = P.rec_index[st.b];
   a.rec_c = P.rec_index[st.out];
   a.c_split = C.split ? 1 : 0;
+  a.maxplus = P.policy.semiring == TN_SEMIRING_MAXPLUS ? 1 : 0;
   return a;
 }
 void* take_event(Plan& P) {
@@ -176,7 +177,8 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
     const int64_t np = cplx ? 2 : 1;
     launch_accumulate_root(reinterpret_cast<const float*>(P.dev + R.offset), R.size,
                            R.batched ? nb : 1, R.batched ? np * R.size : 0, R.size, cplx, acc, recs,
-                           P.rec_index[root], R.batched, ref, p == 0, st);
+                           P.rec_index[root], R.batched, ref, p == 0,
+                           P.policy.semiring == TN_SEMIRING_MAXPLUS, st);
   }
   launch_finalize_output(acc, P.out_elems, cplx, output, log_scale, scaling ? ref : nullptr, st);
   TN_CUDA_TRY(cudaGetLastError());

@@ -34,6 +34,8 @@ struct StepArgs {
   ScaleRec* recs;                           // null: no exponent scaling
   int32_t rec_a, rec_b, rec_c;
   int32_t c_split;                          // 1: write C in the split-BF16 form (complex)
+  int32_t maxplus;                          // 1: (max, +) semiring (real, unscaled)
+  int32_t pad;
 };
 
 void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int64_t slice_begin,
@@ -48,10 +50,11 @@ constexpr int kSplitMaxOut = 16;
 constexpr int64_t kSplitChunk = 4096;
 int32_t splitk_chunks(int64_t k);
 void launch_contract_splitk(const StepArgs& a, int32_t nb, bool cplx, double* scratch, cudaStream_t st);
+// maxplus: the slices combine by maximum instead of the compensated sum
 void launch_accumulate_root(const float* root, int64_t size, int32_t nb, int64_t bstride,
                             int64_t plane, bool cplx, double* acc, const ScaleRec* recs,
                             int32_t rec_root, bool root_batched, int64_t* ref_exp, bool first,
-                            cudaStream_t st);
+                            bool maxplus, cudaStream_t st);
 void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* out, double* log_scale,
                             const int64_t* ref_exp, cudaStream_t st);
 

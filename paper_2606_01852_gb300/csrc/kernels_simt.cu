@@ -108,10 +108,12 @@ void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int6
 // ---------------------------------------------------------------------------------
 // generic step kernel: 64 x 64 output tile, 16-deep k slices, 256 threads, 4 x 4
 // outputs per thread (rows ty*4.., columns tx + 16j so a half-warp stores 16
-// consecutive columns).
+// consecutive columns). MAXPLUS (real only): C = max_k (A + B), -inf padding.
 
-template <bool CPLX>
+template <bool CPLX, bool MAXPLUS = false>
 __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
+  static_assert(!(CPLX && MAXPLUS), "the max-plus semiring is real");
+  const float kZero = MAXPLUS ? __int_as_float(0xff800000) : 0.f;  // the semiring's zero (-inf)
   constexpr int BM = 64, BN = 64, BK = 16, NP = CPLX ? 2 : 1;
   __shared__ float As[NP][BK][BM + 4];
   __shared__ float Bs[NP][BK][BN + 4];
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = kZero;
 
   const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: row lr, k lk..lk+3
   for (int64_t k0 = 0; k0 < a.k; k0 += BK) {
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
       for (int q = 0; q < 4; ++q) {
         const int64_t kk = k0 + lk + q;
         const int64_t ra = m0 + lr, rb = n0 + lr;
-        float va = 0.f, vb = 0.f;
+        float va = kZero, vb = kZero;
         if (ra < a.m && kk < a.k) va = A[p * a.a_plane + ra * a.k + kk] * sa;
         if (rb < a.n && kk < a.k) vb = B[p * a.b_plane + rb * a.k + kk] * sb;
         As[p][lk + q][lr] = va;
@@ -174,6 +176,8 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
             accr[i][j] = fmaf(-ai[i], bi[j], accr[i][j]);
             acci[i][j] = fmaf(ar[i], bi[j], acci[i][j]);
             acci[i][j] = fmaf(ai[i], br[j], acci[i][j]);
+          } else if (MAXPLUS) {
+            accr[i][j] = fmaxf(accr[i][j], ar[i] + br[j]);
           } else {
             accr[i][j] = fmaf(ar[i], br[j], accr[i][j]);
           }
@@ -297,6 +301,7 @@ void launch_contract_simt(const StepArgs& a, int32_t nb, bool cplx, cudaStream_t
   const int64_t tiles = ((a.m + 63) / 64) * ((a.n + 63) / 64);
   dim3 grid((unsigned)tiles, (unsigned)nb);
   if (cplx) contract_simt_kernel<true><<<grid, 256, 0, st>>>(a);
+  else if (a.maxplus) contract_simt_kernel<false, true><<<grid, 256, 0, st>>>(a);
   else contract_simt_kernel<false><<<grid, 256, 0, st>>>(a);
 }
 
@@ -326,10 +331,17 @@ void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sm
 __global__ void accumulate_root_kernel(const float* __restrict__ root, int64_t size, int32_t nb,
                                        int64_t bstride, int64_t plane, int32_t cplx, double* acc,
                                        const ScaleRec* recs, int32_t rec_root, int32_t root_batched,
-                                       int64_t* ref_exp, int32_t first) {
+                                       int64_t* ref_exp, int32_t first, int32_t maxplus) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= size) return;
   double* s = acc + e * 4;  // [sum re, sum im, comp re, comp im]
+  if (maxplus) {  // slices combine by maximum (real, unscaled); comp stays 0
+    double best = first ? __longlong_as_double(static_cast<long long>(0xfff0000000000000ull)) : s[0];
+    for (int b = 0; b < nb; ++b) best = fmax(best, (double)root[b * bstride + e]);
+    s[0] = best;
+    s[1] = s[2] = s[3] = 0.0;
+    return;
+  }
   double sr = first ? 0.0 : s[0], si = first ? 0.0 : s[1];
   double cr = first ? 0.0 : s[2], ci = first ? 0.0 : s[3];
   int64_t ref = 0;
@@ -364,12 +376,12 @@ __global__ void accumulate_root_kernel(const float* __restrict__ root, int64_t s
 void launch_accumulate_root(const float* root, int64_t size, int32_t nb, int64_t bstride,
                             int64_t plane, bool cplx, double* acc, const ScaleRec* recs,
                             int32_t rec_root, bool root_batched, int64_t* ref_exp, bool first,
-                            cudaStream_t st) {
+                            bool maxplus, cudaStream_t st) {
   const int threads = 128;
   const unsigned blocks = (unsigned)((size + threads - 1) / threads);
   accumulate_root_kernel<<<blocks, threads, 0, st>>>(root, size, nb, bstride, plane, cplx ? 1 : 0, acc,
                                                      recs, rec_root, root_batched ? 1 : 0, ref_exp,
-                                                     first ? 1 : 0);
+                                                     first ? 1 : 0, maxplus ? 1 : 0);
 }
 
 __global__ void finalize_output_kernel(const double* acc, int64_t size, int32_t cplx, void* out,
@@ -401,9 +413,10 @@ void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* ou
 // Pass 2: per (b, output), the partials are added in chunk order in FP64 and the
 // result stored through the offset maps. Deterministic: no atomics.
 
-template <bool CPLX>
+template <bool CPLX, bool MAXPLUS = false>
 __global__ void __launch_bounds__(256) splitk_partial_kernel(StepArgs a, double* scratch, int64_t kc,
                                                              int32_t chunks) {
+  static_assert(!(CPLX && MAXPLUS), "the max-plus semiring is real");
   const int chunk = blockIdx.x, b = blockIdx.y;
   const int m = (int)a.m, n = (int)a.n, mn = m * n;
   const float* A = a.A + b * a.a_bstride;
@@ -414,13 +427,25 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(StepArgs a, double*
     sb = pow2_neg(scale_exp(a.recs + a.rec_b + (a.b_bstride ? b : 0)));
   }
   float accr[kSplitMaxOut], acci[kSplitMaxOut];
+  const float zero = MAXPLUS ? __int_as_float(0xff800000) : 0.f;  // the semiring's zero
 #pragma unroll
-  for (int o = 0; o < kSplitMaxOut; ++o) accr[o] = acci[o] = 0.f;
+  for (int o = 0; o < kSplitMaxOut; ++o) accr[o] = acci[o] = zero;
   const int64_t k0 = (int64_t)chunk * kc;
   const int64_t k1 = min(a.k, k0 + kc);
+  if (MAXPLUS) {
+    for (int64_t kk = k0 + threadIdx.x; kk < k1; kk += blockDim.x) {
+#pragma unroll
+      for (int o = 0; o < kSplitMaxOut; ++o) {
+        if (o < mn) {
+          const int i = o / n, j = o - (o / n) * n;
+          accr[o] = fmaxf(accr[o], A[i * a.k + kk] + B[j * a.k + kk]);
+        }
+      }
+    }
+  }
   // the output index o is a compile-time constant in every unrolled iteration, so the
   // accumulators stay in registers
-  const bool vec = (a.k & 3) == 0 && (a.a_plane & 3) == 0 && (a.b_plane & 3) == 0 &&
+  const bool vec = !MAXPLUS && (a.k & 3) == 0 && (a.a_plane & 3) == 0 && (a.b_plane & 3) == 0 &&
                    ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
   if (vec) {
     // 16-byte loads, four k-steps of the block unrolled: every thread has all of its
@@ -455,7 +480,7 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(StepArgs a, double*
       }
     }
   }
-  for (int64_t kk = k0 + threadIdx.x; !vec && kk < k1; kk += blockDim.x) {
+  for (int64_t kk = k0 + threadIdx.x; !MAXPLUS && !vec && kk < k1; kk += blockDim.x) {
 #pragma unroll
     for (int o = 0; o < kSplitMaxOut; ++o) {
       if (o < mn) {
@@ -481,8 +506,12 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(StepArgs a, double*
     double vr = accr[o], vi = acci[o];
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
-      vr += __shfl_xor_sync(0xffffffffu, vr, s);
-      vi += __shfl_xor_sync(0xffffffffu, vi, s);
+      if (MAXPLUS) {
+        vr = fmax(vr, __shfl_xor_sync(0xffffffffu, vr, s));
+      } else {
+        vr += __shfl_xor_sync(0xffffffffu, vr, s);
+        vi += __shfl_xor_sync(0xffffffffu, vi, s);
+      }
     }
     if (lane == 0) {
       red[0][o][warp] = vr;
@@ -492,10 +521,14 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(StepArgs a, double*
   __syncthreads();
   if (threadIdx.x < mn) {
     const int o = threadIdx.x;
-    double vr = 0.0, vi = 0.0;
+    double vr = MAXPLUS ? (double)zero : 0.0, vi = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      vr += red[0][o][w];
-      vi += red[1][o][w];
+      if (MAXPLUS) {
+        vr = fmax(vr, red[0][o][w]);
+      } else {
+        vr += red[0][o][w];
+        vi += red[1][o][w];
+      }
     }
     double* dst = scratch + (((int64_t)b * chunks + chunk) * mn + o) * 2;
     dst[0] = vr;
@@ -515,22 +548,31 @@ __global__ void __launch_bounds__(kFinalThreads) splitk_final_kernel(StepArgs a,
   // thread t adds the partials of a contiguous run of chunks in order; thread 0 then adds
   // the runs in order: a fixed association for a given chunk count (deterministic)
   const int per = (chunks + kFinalThreads - 1) / kFinalThreads;
+  const double zero = a.maxplus ? __longlong_as_double(static_cast<long long>(0xfff0000000000000ull)) : 0.0;
   for (int o = 0; o < mn; ++o) {
-    double sr = 0.0, si = 0.0;
+    double sr = zero, si = 0.0;
     const int c0 = threadIdx.x * per, c1 = min(chunks, c0 + per);
     for (int c = c0; c < c1; ++c) {
       const double* p = scratch + (((int64_t)b * chunks + c) * mn + o) * 2;
-      sr += p[0];
-      si += p[1];
+      if (a.maxplus) {
+        sr = fmax(sr, p[0]);
+      } else {
+        sr += p[0];
+        si += p[1];
+      }
     }
     part[0][threadIdx.x] = sr;
     part[1][threadIdx.x] = si;
     __syncthreads();
-    double vr = 0.0, vi = 0.0;
+    double vr = zero, vi = 0.0;
     if (threadIdx.x == 0)
       for (int t = 0; t < kFinalThreads; ++t) {
-        vr += part[0][t];
-        vi += part[1][t];
+        if (a.maxplus) {
+          vr = fmax(vr, part[0][t]);
+        } else {
+          vr += part[0][t];
+          vi += part[1][t];
+        }
       }
     __syncthreads();  // every thread, every o: part is rewritten next iteration
     if (threadIdx.x == 0) {
@@ -558,6 +600,7 @@ void launch_contract_splitk(const StepArgs& a, int32_t nb, bool cplx, double* sc
   const int32_t chunks = splitk_chunks(a.k);
   dim3 grid((unsigned)chunks, (unsigned)nb);
   if (cplx) splitk_partial_kernel<true><<<grid, 256, 0, st>>>(a, scratch, kSplitChunk, chunks);
+  else if (a.maxplus) splitk_partial_kernel<false, true><<<grid, 256, 0, st>>>(a, scratch, kSplitChunk, chunks);
   else splitk_partial_kernel<false><<<grid, 256, 0, st>>>(a, scratch, kSplitChunk, chunks);
   splitk_final_kernel<<<(unsigned)nb, kFinalThreads, 0, st>>>(a, scratch, chunks, cplx ? 1 : 0);
 }

@@ -86,6 +86,14 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     err = "unknown precision";
     return TN_ERR_INVALID;
   }
+  if (pol.semiring != TN_SEMIRING_STANDARD && pol.semiring != TN_SEMIRING_MAXPLUS) {
+    err = "unknown semiring";
+    return TN_ERR_INVALID;
+  }
+  if (pol.semiring == TN_SEMIRING_MAXPLUS && (pol.prec != TN_R32_FP32_SIMT || pol.exp_scaling)) {
+    err = "the max-plus semiring runs in the R32 FP32 form without exponent scaling";
+    return TN_ERR_UNSUPPORTED;
+  }
   if (pol.complex_mult != 0 && pol.complex_mult != 4) {
     err = "only the 4M complex form is built (complex_mult must be 4 or 0)";
     return TN_ERR_UNSUPPORTED;
@@ -345,7 +353,9 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
       // epilogue stores are the better coalesced
       if (t_tc <= t_simt) st.cls = TN_CLASS_TC;
     }
-    if (st.cls == TN_CLASS_SIMT && stream_ok(st.m, st.n, st.k)) st.cls = TN_CLASS_STREAM;
+    // (the streaming kernel computes in (+, x) only)
+    if (st.cls == TN_CLASS_SIMT && stream_ok(st.m, st.n, st.k) && pol.semiring == TN_SEMIRING_STANDARD)
+      st.cls = TN_CLASS_STREAM;
     // few outputs over a long reduction: the tiled kernel would leave all but a few
     // threads idle and sum k terms serially in FP32
     if (st.cls == TN_CLASS_SIMT && st.m * st.n <= kSplitMaxOut && st.k >= kSplitChunk)

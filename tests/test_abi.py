@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from tests._lib import ROOT, ensure_built
-from tn_inputs import greedy, workloads, circuits
+from tn_inputs import greedy, workloads, circuits, kings
 from tn_inputs.network import Network, Path
 
 
@@ -158,3 +158,17 @@ def test_split_bf16_operands_exactly_the_tc_operands(prec):
     split = {t for t in range(n_t) if plan.tensor(t)["format"] == 1}
     assert split == (tc_operands if prec == "bf16x3" else set())
     plan.destroy()
+
+
+def test_maxplus_policy_checks():
+    tn = ensure_built()
+    net = kings.kings_network(5, 0.8, 1)
+    path = greedy.greedy_path(net, seed=0, alpha=1.0)
+    plan = tn.Plan(net, path, prec=tn.TN_R32_FP32_SIMT, semiring="maxplus", host_only=True)
+    classes = {plan.step(s)["cls"] for s in range(len(path.pairs))}
+    assert classes <= {tn.TN_CLASS_SIMT, tn.TN_CLASS_SPLITK}
+    plan.destroy()
+    for kw in (dict(prec="3xtf32"), dict(prec=tn.TN_R32_FP32_SIMT, exp_scaling=True), dict(prec="fp32")):
+        with pytest.raises(tn.TnError) as e:
+            tn.Plan(net, path, semiring="maxplus", host_only=True, **kw)
+        assert "TN_ERR_UNSUPPORTED" in str(e.value)

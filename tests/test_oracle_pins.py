@@ -9,7 +9,7 @@ import pytest
 import oracle
 from oracle import pins
 from oracle import core as oc
-from tn_inputs import circuits, kicked_ising, ising_pf, greedy
+from tn_inputs import circuits, kicked_ising, ising_pf, greedy, kings
 from tn_inputs.network import Network, Path
 
 
@@ -67,13 +67,13 @@ def test_brute_force_catches_transposed_operand(monkeypatch):
     want = pins.brute_force(net)
     real_pairwise = oc.pairwise
 
-    def wrong(a, ma, b, mb, keep):
+    def wrong(a, ma, b, mb, keep, semiring="standard"):
         # operand B's data transposed against its labels (first two axes of equal extent)
         for i in range(b.ndim):
             for j in range(i + 1, b.ndim):
                 if b.shape[i] == b.shape[j]:
-                    return real_pairwise(a, ma, np.swapaxes(b, i, j), mb, keep)
-        return real_pairwise(a, ma, b, mb, keep)
+                    return real_pairwise(a, ma, np.swapaxes(b, i, j), mb, keep, semiring)
+        return real_pairwise(a, ma, b, mb, keep, semiring)
 
     monkeypatch.setattr(oc, "pairwise", wrong)
     got = oc.contract(net, path)
@@ -85,7 +85,8 @@ def test_brute_force_catches_conjugation(monkeypatch):
     path = greedy.greedy_path(net, seed=2)
     want = pins.brute_force(net)
     real_pairwise = oc.pairwise
-    monkeypatch.setattr(oc, "pairwise", lambda a, ma, b, mb, keep: real_pairwise(a, ma, np.conj(b), mb, keep))
+    monkeypatch.setattr(oc, "pairwise", lambda a, ma, b, mb, keep, semiring="standard":
+                        real_pairwise(a, ma, np.conj(b), mb, keep, semiring))
     assert not np.allclose(oc.contract(net, path), want, rtol=1e-8)
 
 
@@ -256,3 +257,50 @@ def test_step_costs_hand_counted():
     m, n, k = 6, 42, 20
     assert (s["m"], s["n"], s["k"]) == (m, n, k)
     assert s["Ct"] == 5040 and s["Cs"] == max(120, 840, 252) and s["Cm"] == 120 + 840 + 252
+
+
+# ---- semirings: independent sets (Sec. III-C) -------------------------------------------
+
+def _mis_and_count(n, edges, sliced_k=0, seed=0):
+    t = kings.independent_set_network(n, edges, "tropical")
+    c = kings.independent_set_network(n, edges, "counting")
+    path = greedy.greedy_path(t, seed=seed, alpha=1.0)
+    sl = list(range(min(sliced_k, len(edges))))
+    mis = oracle.contract(t, path, sl, semiring="maxplus")
+    cnt = oracle.contract(c, path, sl)
+    return float(mis), float(cnt)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_independent_sets_vs_enumeration(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(8, 15))
+    edges = sorted({(int(min(u, v)), int(max(u, v))) for u, v in rng.integers(0, n, size=(2 * n, 2)) if u != v})
+    want_count, want_mis = pins.independent_sets_enumerate(n, edges)
+    for k in (0, 3):  # unsliced, and 3 sliced labels (max / sum over the 8 slices)
+        mis, cnt = _mis_and_count(n, edges, sliced_k=k, seed=seed)
+        assert mis == want_mis and cnt == want_count, (k, mis, want_mis, cnt, want_count)
+
+
+@pytest.mark.parametrize("n", [5, 8, 13])
+def test_independent_sets_path_and_cycle_closed_forms(n):
+    path_edges = [(i, i + 1) for i in range(n - 1)]
+    cycle_edges = path_edges + [(0, n - 1)]
+    assert _mis_and_count(n, path_edges)[::-1] == tuple(float(x) for x in pins.path_graph_closed_form(n))
+    assert _mis_and_count(n, cycle_edges)[::-1] == tuple(float(x) for x in pins.cycle_graph_closed_form(n))
+
+
+@pytest.mark.parametrize("L", [3, 4, 5])
+def test_full_kings_graph_mis(L):
+    net = kings.kings_network(L, 1.0, 0)
+    assert net.meta["n"] == L * L and len(net.meta["edges"]) == 2 * (L - 1) * (2 * L - 1)
+    path = greedy.greedy_path(net, seed=0, alpha=1.0)
+    assert float(oracle.contract(net, path, semiring="maxplus")) == pins.kings_full_mis(L)
+
+
+def test_kings_subgraph_vs_enumeration():
+    net = kings.kings_network(5, 0.8, 11)
+    n, edges = net.meta["n"], net.meta["edges"]
+    want_count, want_mis = pins.independent_sets_enumerate(n, edges)
+    mis, cnt = _mis_and_count(n, edges)
+    assert (mis, cnt) == (want_mis, want_count)

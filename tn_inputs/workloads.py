@@ -14,6 +14,8 @@
   khex45    : kicked Ising, same couplings, on a 4x5 honeycomb lattice (brick-wall form),
               6 Trotter steps;
   ktri44    : kicked Ising on a 4x4 triangular lattice, 8 Trotter steps;
+  kings16   : maximum independent set of a 16x16 King's subgraph (site density 0.8, seed 1;
+              209 vertices), contracted in the max-plus semiring (FP32, exact integers);
   ising3r   : an ensemble of Ising partition functions on random 3-regular graphs.
 Smaller variants with the same structure serve as parity cases.
 
@@ -24,7 +26,7 @@ from __future__ import annotations
 
 import functools
 
-from . import circuits, kicked_ising, ising_pf, greedy
+from . import circuits, kicked_ising, ising_pf, greedy, kings
 
 PATH_SEEDS = range(6)
 PATH_ALPHAS = (0.0, 0.5, 1.0)
@@ -103,6 +105,21 @@ def ktri44():
     return kicked(4, 8, lattice="triangular")
 
 
+@functools.lru_cache(maxsize=None)
+def kings_mis(L, rho, seed, n_sliced=0):
+    """Maximum independent set of a King's subgraph: the max-plus (tropical) network."""
+    net = kings.kings_network(L, rho, seed, "tropical")
+    name = net.name + (f"_sl{n_sliced}" if n_sliced else "")
+    w = _pathed(name, net, n_sliced=n_sliced)
+    w.info["semiring"] = "maxplus"
+    return w
+
+
+def kings16():
+    """MIS of a 16 x 16 King's subgraph (site density 0.8, seed 1: 209 vertices)."""
+    return kings_mis(16, 0.8, 1)
+
+
 def ising_workload(net):
     path, info = greedy.best_greedy(net, range(2), (0.0, 1.0))
     return Workload(net.name, net, path, (), info)
@@ -113,4 +130,4 @@ def ising3r(count, seed=3):
 
 
 BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40u": rc40u, "kising44": kising44, "rc40open": rc40open,
-           "khex45": khex45, "ktri44": ktri44}
+           "khex45": khex45, "ktri44": ktri44, "kings16": kings16}
