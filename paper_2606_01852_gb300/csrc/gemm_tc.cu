@@ -164,6 +164,171 @@ __device__ __forceinline__ int64_t map_off(const OffsetMap& om, int64_t idx) {
 
 __device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
 
+// V consecutive 16-bit values (the low halves of x[]) as one store of 2V bytes.
+template <int V>
+__device__ __forceinline__ void store_halves(uint16_t* d, const uint32_t (&x)[V]) {
+  if constexpr (V == 1) {
+    d[0] = static_cast<uint16_t>(x[0]);
+  } else if constexpr (V == 2) {
+    *reinterpret_cast<uint32_t*>(d) = x[0] | (x[1] << 16);
+  } else if constexpr (V == 4) {
+    *reinterpret_cast<uint2*>(d) = make_uint2(x[0] | (x[1] << 16), x[2] | (x[3] << 16));
+  } else {
+    *reinterpret_cast<uint4*>(d) =
+        make_uint4(x[0] | (x[1] << 16), x[2] | (x[3] << 16), x[4] | (x[5] << 16), x[6] | (x[7] << 16));
+  }
+}
+
+// V consecutive elements (V = 1, 2, 4, 8) of an address-ordered run: Re values re[],
+// Im values im[], stored at element `off` of a tensor copy that starts at C, planar FP32
+// or split BF16, one vector store per plane (off and the planes are V-aligned).
+template <int V>
+__device__ __forceinline__ void store_run(float* C, int64_t plane, int64_t off, const float* re, const float* im,
+                                          bool split) {
+  if (!split) {
+    if constexpr (V == 1) {
+      C[off] = re[0];
+      C[plane + off] = im[0];
+    } else if constexpr (V == 2) {
+      *reinterpret_cast<float2*>(C + off) = make_float2(re[0], re[1]);
+      *reinterpret_cast<float2*>(C + plane + off) = make_float2(im[0], im[1]);
+    } else {
+#pragma unroll
+      for (int h = 0; h < V; h += 4) {
+        *reinterpret_cast<float4*>(C + off + h) = make_float4(re[h], re[h + 1], re[h + 2], re[h + 3]);
+        *reinterpret_cast<float4*>(C + plane + off + h) = make_float4(im[h], im[h + 1], im[h + 2], im[h + 3]);
+      }
+    }
+    return;
+  }
+  // split: hi = RN_bf16(v), lo = RN_bf16(v - hi); planes re_hi, im_hi, re_lo, im_lo
+  uint32_t hr[V], hi_[V], lr[V], li[V];
+#pragma unroll
+  for (int u = 0; u < V; ++u) {
+    const __nv_bfloat16 a = __float2bfloat16_rn(re[u]), b = __float2bfloat16_rn(im[u]);
+    hr[u] = __bfloat16_as_ushort(a);
+    hi_[u] = __bfloat16_as_ushort(b);
+    lr[u] = __bfloat16_as_ushort(__float2bfloat16_rn(re[u] - __bfloat162float(a)));
+    li[u] = __bfloat16_as_ushort(__float2bfloat16_rn(im[u] - __bfloat162float(b)));
+  }
+  uint16_t* S = reinterpret_cast<uint16_t*>(C) + off;
+  store_halves<V>(S, hr);
+  store_halves<V>(S + plane, hi_);
+  store_halves<V>(S + 2 * plane, lr);
+  store_halves<V>(S + 3 * plane, li);
+}
+
+// The address-ordered stores of one block, lanes taking V = 2^VB consecutive addresses.
+// e[k], src[k]: the k-th smallest bit weight (log2) and which bit of r (0-4) or c (5-9)
+// carries it; the VB smallest weights are 1, 2, ..., 2^(VB-1).
+template <int VB>
+__device__ __forceinline__ void store_sorted(float* C, int64_t plane, bool split, const float* t, int pitch, int cs,
+                                             int64_t base, const int* e, const int* src, int lane) {
+  constexpr int V = 1 << VB;
+  int rl = 0, cl = 0;
+  int64_t al = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+    if ((lane >> k) & 1) {
+      const int b = src[VB + k];
+      if (b < 5) rl |= 1 << b;
+      else cl |= 1 << (b - 5);
+      al += int64_t(1) << e[VB + k];
+    }
+  for (int s = 0; s < (32 >> VB); ++s) {
+    int r = rl, c = cl;
+    int64_t ah = 0;
+#pragma unroll
+    for (int k = 0; k < 5 - VB; ++k)
+      if ((s >> k) & 1) {
+        const int b = src[VB + 5 + k];
+        if (b < 5) r |= 1 << b;
+        else c |= 1 << (b - 5);
+        ah += int64_t(1) << e[VB + 5 + k];
+      }
+    float re[V], im[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      int ru = r, cu = c;
+#pragma unroll
+      for (int k = 0; k < VB; ++k)
+        if ((u >> k) & 1) {
+          if (src[k] < 5) ru |= 1 << src[k];
+          else cu |= 1 << (src[k] - 5);
+        }
+      re[u] = t[ru * pitch + cu];
+      im[u] = t[cs + ru * pitch + cu];
+    }
+    store_run<V>(C, plane, base + al + ah, re, im, split);
+  }
+}
+
+// Store one 32 x 32 block of a result tile from shared memory (t[r * pitch + c] = Re,
+// t[cs + r * pitch + c] = Im; row r is lane r's row, column c lane c's column) in the
+// order of its addresses. When the block's offsets are linear in the bits of (r, c) with
+// power-of-two weights -- every row and column extent of the offset maps a power of two,
+// as in every network with extent-2 modes -- off(r, c) = off(0, 0) + sum of per-bit
+// weights, and the ten weights sorted ascending give the block's elements in address
+// order. Each lane then writes V consecutive addresses with one vector store per plane
+// (V up to 4 FP32 or 8 BF16 values, 16 bytes, as far as the smallest weights are 1, 2, 4,
+// ... and the block is aligned), and a warp store covers 32 V consecutive elements when
+// the following weights continue the sequence (interleaved row/column layouts included).
+// Otherwise (ragged block, other extents) it falls back to one row per store. ro / co:
+// this lane's row / column offset; row_ok / col_ok: in range.
+__device__ __forceinline__ void store_block(float* C, int64_t plane, bool split, const float* t, int pitch,
+                                            int cs, int64_t ro, int64_t co, bool row_ok, bool col_ok, int lane) {
+  const int64_t ro0 = __shfl_sync(0xffffffffu, ro, 0), co0 = __shfl_sync(0xffffffffu, co, 0);
+  // log2 of each bit's weight (bits 0-4: row, 5-9: column); -1 if not a power of two
+  int e[10];
+  bool lin = row_ok && col_ok;
+  int64_t pr = 0, pc = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int64_t wr = __shfl_sync(0xffffffffu, ro, 1 << i) - ro0;
+    const int64_t wc = __shfl_sync(0xffffffffu, co, 1 << i) - co0;
+    e[i] = (wr > 0 && (wr & (wr - 1)) == 0) ? 63 - __clzll(wr) : -1;
+    e[5 + i] = (wc > 0 && (wc & (wc - 1)) == 0) ? 63 - __clzll(wc) : -1;
+    lin = lin && e[i] >= 0 && e[5 + i] >= 0;
+    pr += ((lane >> i) & 1) * wr;
+    pc += ((lane >> i) & 1) * wc;
+  }
+  lin = lin && pr == ro - ro0 && pc == co - co0;
+  if (__all_sync(0xffffffffu, lin)) {
+    // sort the ten bit weights ascending, carrying which bit of r (0-4) or c (5-9) each is
+    int src[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) src[i] = i;
+#pragma unroll
+    for (int i = 1; i < 10; ++i)
+#pragma unroll
+      for (int j = i; j > 0; --j)
+        if (e[j] < e[j - 1]) {
+          const int te = e[j];
+          e[j] = e[j - 1];
+          e[j - 1] = te;
+          const int ts = src[j];
+          src[j] = src[j - 1];
+          src[j - 1] = ts;
+        }
+    // elements per lane: as many of the smallest weights as are 1, 2, 4, ... (16 bytes at
+    // most), with the block base and the plane size aligned to that many elements
+    const int64_t base = ro0 + co0;
+    int vb = 0;
+    while (vb < (split ? 3 : 2) && e[vb] == vb) ++vb;
+    while (vb > 0 && ((base | plane) & ((int64_t(1) << vb) - 1)) != 0) --vb;
+    if (vb == 3) store_sorted<3>(C, plane, split, t, pitch, cs, base, e, src, lane);
+    else if (vb == 2) store_sorted<2>(C, plane, split, t, pitch, cs, base, e, src, lane);
+    else if (vb == 1) store_sorted<1>(C, plane, split, t, pitch, cs, base, e, src, lane);
+    else store_sorted<0>(C, plane, split, t, pitch, cs, base, e, src, lane);
+    return;
+  }
+  for (int r = 0; r < 32; ++r) {
+    const int64_t ro_r = __shfl_sync(0xffffffffu, ro, r);
+    const bool ok_r = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, r) != 0;
+    if (ok_r && col_ok) store_cplx(C, plane, ro_r + co, t[r * pitch + lane], t[cs + r * pitch + lane], split);
+  }
+}
+
 template <int SPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -330,11 +495,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
     const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
-    // Store pattern: a warp instruction should write 32 consecutive addresses. If the
-    // rows are the unit-stride side, thread = row already does; otherwise each 32 x 32
-    // block goes through shared memory (the drained stage buffers) and thread =
-    // column, row by row.
-    const bool rows_unit = a.rows.n > 0 && a.rows.stride[a.rows.n - 1] == 1;
+    // Each 32 x 32 block goes through shared memory (the drained stage buffers) and is
+    // stored in address order (store_block): 32 consecutive elements per warp store for
+    // the usual layouts.
     float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 33;  // [2][32][33]
     for (int c = 0; c < BN / 32; ++c) {
       float rr[32], ii[32], xx[32];
@@ -342,36 +505,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tmem_ld32(tmem + lane_base + 128 + c * 32, ii);
       tmem_ld32(tmem + lane_base + 256 + c * 32, xx);
       const int64_t nb0 = static_cast<int64_t>(n0) + c * 32;
-      if (rows_unit) {
-        if (!row_ok) continue;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t n = nb0 + j;
-          if (n >= a.n) break;
-          const int64_t off = ro + map_off(a.cols, n);
-          C[off] = rr[j] - ii[j];
-          C[a.c_plane + off] = xx[j];
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          tr[lane * 33 + j] = rr[j] - ii[j];
-          tr[32 * 33 + lane * 33 + j] = xx[j];
-        }
-        __syncwarp();
-        const int64_t n = nb0 + lane;
-        const bool col_ok = ok && n < a.n;
-        const int64_t co = col_ok ? map_off(a.cols, n) : 0;
-        for (int r = 0; r < 32; ++r) {
-          const int64_t ro_r = __shfl_sync(0xffffffffu, ro, r);
-          const bool ok_r = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, r) != 0;
-          if (ok_r && col_ok) {
-            C[ro_r + co] = tr[r * 33 + lane];
-            C[a.c_plane + ro_r + co] = tr[32 * 33 + r * 33 + lane];
-          }
-        }
-        __syncwarp();
+      for (int j = 0; j < 32; ++j) {
+        tr[lane * 33 + j] = rr[j] - ii[j];
+        tr[32 * 33 + lane * 33 + j] = xx[j];
       }
+      __syncwarp();
+      const int64_t n = nb0 + lane;
+      const bool col_ok = ok && n < a.n;
+      store_block(C, a.c_plane, false, tr, 33, 32 * 33, ro, col_ok ? map_off(a.cols, n) : 0, row_ok, col_ok, lane);
+      __syncwarp();
     }
   }
   fence_before();
@@ -625,9 +768,12 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
     const bool row_ok = ok && m < a.m;
     const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
-    const bool rows_unit = a.rows.n > 0 && a.rows.stride[a.rows.n - 1] == 1;
     // The stage buffers are free here: this warp's last drain waited for the final MMA,
     // which waited for every warp's last split; no TMA load is outstanding.
+    // Row-by-row stores (one row per warp store, through shared memory when the columns
+    // are the unit-stride side): the address-ordered block store costs this kernel
+    // registers its split loop needs.
+    const bool rows_unit = a.rows.n > 0 && a.rows.stride[a.rows.n - 1] == 1;
     float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 33;  // [2][32][33]
 #pragma unroll
     for (int cb = 0; cb < 2; ++cb) {
@@ -883,39 +1029,22 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
     const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
     const bool split = a.c_split != 0;
-    const bool rows_unit = a.rows.n > 0 && a.rows.stride[a.rows.n - 1] == 1;
     // The stage buffers are free here: the last fold waited for the final MMA, which
     // consumed every staged tile; no TMA load is outstanding.
-    float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 33;  // [2][32][33]
+    // this warp's 32 x 64 results, Re then Im, rows of 65 floats: the registers are free
+    // before the stores begin
+    float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 65;
 #pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      tr[lane * 65 + j] = run_re[j];
+      tr[32 * 65 + lane * 65 + j] = run_im[j];
+    }
+    __syncwarp();
     for (int cb = 0; cb < 2; ++cb) {
-      const int64_t nb0 = static_cast<int64_t>(n0) + half * 64 + cb * 32;
-      if (rows_unit) {
-        if (row_ok) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t n = nb0 + j;
-            if (n < a.n)
-              store_cplx(C, a.c_plane, ro + map_off(a.cols, n), run_re[cb * 32 + j], run_im[cb * 32 + j], split);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          tr[lane * 33 + j] = run_re[cb * 32 + j];
-          tr[32 * 33 + lane * 33 + j] = run_im[cb * 32 + j];
-        }
-        __syncwarp();
-        const int64_t n = nb0 + lane;
-        const bool col_ok = ok && n < a.n;
-        const int64_t co = col_ok ? map_off(a.cols, n) : 0;
-        for (int r = 0; r < 32; ++r) {
-          const int64_t ro_r = __shfl_sync(0xffffffffu, ro, r);
-          const bool ok_r = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, r) != 0;
-          if (ok_r && col_ok) store_cplx(C, a.c_plane, ro_r + co, tr[r * 33 + lane], tr[32 * 33 + r * 33 + lane], split);
-        }
-        __syncwarp();
-      }
+      const int64_t n = static_cast<int64_t>(n0) + half * 64 + cb * 32 + lane;
+      const bool col_ok = ok && n < a.n;
+      store_block(C, a.c_plane, split, tr + cb * 32, 65, 32 * 65, ro, col_ok ? map_off(a.cols, n) : 0, row_ok,
+                  col_ok, lane);
     }
   }
   fence_before();

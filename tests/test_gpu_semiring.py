@@ -33,7 +33,7 @@ def run_real(tn, plan, net, exp_scaling=False):
 
 
 @pytest.mark.parametrize("L,rho,seed,n_sliced", [(6, 0.8, 1, 0), (8, 0.8, 2, 0), (10, 0.8, 3, 0),
-                                                 (12, 0.8, 4, 0), (10, 0.8, 5, 3), (12, 0.9, 6, 4)])
+                                                 (12, 0.8, 4, 0), (10, 0.8, 5, 3), (8, 0.9, 6, 4)])
 def test_kings_mis_exact(tn, L, rho, seed, n_sliced):
     w = workloads.kings_mis(L, rho, seed, n_sliced)
     plan = tn.Plan(w.net, w.path, w.sliced, prec=tn.TN_R32_FP32_SIMT, semiring="maxplus", max_slice_batch=4)
