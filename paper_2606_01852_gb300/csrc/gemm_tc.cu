@@ -1055,6 +1055,213 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------------
+// BF16x3, persistent, for shallow steps (k <= 64: one or two k-blocks per tile). Such a
+// step is bound by its output stores, not by the tensor core; with one tile per CTA most
+// of a CTA's life is set-up, pipeline fill and the epilogue, serialised. Here one CTA per
+// SM walks the (batch entry, tile) items with a stride of the grid; the stage ring,
+// barrier phases and tensor memory carry over, and the fold warps release the
+// accumulators before storing a tile, so the stores of one tile overlap the loads and
+// MMAs of the next. (For deep steps the same structure keeps the tensor core busier but,
+// measured, draws the clock down under the power cap: those keep one tile per CTA.) Same
+// MMA sequence and numerics as contract_tcb_kernel; 2 stages, and a 32 x 33 transpose
+// block per fold warp for the epilogue.
+struct CBP {
+  static constexpr int STAGES = 2;
+  static constexpr int EPI = 8 * 2 * 32 * 33 * 4;          // per fold warp: Re and Im of one 32 x 32 block
+  static constexpr int BARS = 256;
+  static constexpr int SMEM = STAGES * CB::STAGE + EPI + BARS + 1024 /*align*/;
+  static constexpr int MAX_K = 2 * CB::BK;                  // used for k <= 64
+};
+static_assert(CBP::SMEM <= 232448, "shared memory per CTA");
+
+// Work item w -> batch entry and the output tile's first row and column (the grouped
+// raster of contract_tcb_kernel within each batch entry).
+struct TileCoord {
+  int b, m0, n0;
+};
+__device__ __forceinline__ TileCoord tile_of(int64_t w, int64_t tiles_m, int64_t tiles_n) {
+  const int64_t tiles = tiles_m * tiles_n;
+  const int64_t t = w % tiles;
+  const int64_t per_group = GROUP_M * tiles_n;
+  const int64_t first_m = (t / per_group) * GROUP_M;
+  const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
+  const int64_t tm = first_m + (t % per_group) % gm, tn = (t % per_group) / gm;
+  return TileCoord{static_cast<int>(w / tiles), static_cast<int>(tm * BM), static_cast<int>(tn * BN)};
+}
+
+__global__ void __launch_bounds__(CB::THREADS, 1)
+    contract_tcb_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                                   StepArgs a, int32_t nb, int* err) {
+  constexpr int STAGES = CBP::STAGES, BK = CB::BK, ROWB = CB::ROWB;
+  constexpr int PLANE = CB::PLANE, STAGE = CB::STAGE;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* epi = reinterpret_cast<float*>(smem + STAGES * STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE + CBP::EPI);
+  uint64_t* full = bars;                 // [STAGES]
+  uint64_t* empty = bars + STAGES;       // [STAGES]
+  uint64_t* acc_full = bars + 2 * STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
+  const int64_t total = tiles_m * tiles_n * nb;
+  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);  // 1 or 2: one chunk per tile
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 8);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(CB::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t g = 0;  // k-blocks issued by this CTA: stage g % STAGES, phase g / STAGES
+      bool ok = true;
+      for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x) {
+        const TileCoord tc = tile_of(w, tiles_m, tiles_n);
+        const int pa = a.a_bstride ? 4 * tc.b : 0, pb = a.b_bstride ? 4 * tc.b : 0;
+        for (int kb = 0; kb < num_kb; ++kb, ++g) {
+          const int s = static_cast<int>(g % STAGES);
+          if (!mbar_wait(&empty[s], static_cast<uint32_t>((g / STAGES) & 1) ^ 1)) {
+            atomicExch(err, 31);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], STAGE);
+          uint8_t* st = smem + s * STAGE;
+          tma_load_3d(st, &tmA, &full[s], kb * BK, tc.m0, pa);
+          tma_load_3d(st + CB::OFF_B, &tmB, &full[s], kb * BK, tc.n0, pb);
+        }
+      }
+      // every issued load has landed before the CTA can exit
+      for (int64_t j = g > STAGES ? g - STAGES : 0; j < g; ++j)
+        if (!mbar_wait(&full[j % STAGES], static_cast<uint32_t>((j / STAGES) & 1))) atomicExch(err, 32);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t id_w = idesc_bf16(BM, 2 * BN);
+      constexpr uint32_t id_n = idesc_bf16(BM, BN);
+      const uint32_t d_hi = tmem, d_lo = tmem + 256;
+      int64_t g = 0, q = 0;  // k-blocks consumed, tiles committed
+      bool ok = true;
+      for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x, ++q) {
+        // the previous tile's accumulators must have been read
+        if (!mbar_wait(acc_empty, static_cast<uint32_t>(q & 1) ^ 1)) {
+          atomicExch(err, 33);
+          break;
+        }
+        fence_after();
+        for (int kb = 0; kb < num_kb; ++kb, ++g) {
+          const int s = static_cast<int>(g % STAGES);
+          if (!mbar_wait(&full[s], static_cast<uint32_t>((g / STAGES) & 1))) {
+            atomicExch(err, 34);
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sa = su32(smem + s * STAGE), sb = sa + CB::OFF_B;
+#pragma unroll
+          for (int j = 0; j < BK / 16; ++j) {
+            const uint32_t o = j * 32;
+            const uint64_t ar_l = smem_desc<ROWB>(sa + 2 * PLANE + o), ai_l = smem_desc<ROWB>(sa + 3 * PLANE + o);
+            const uint64_t ar_h = smem_desc<ROWB>(sa + o), ai_h = smem_desc<ROWB>(sa + PLANE + o);
+            const uint64_t b_h = smem_desc<ROWB>(sb + o), bi_h = smem_desc<ROWB>(sb + PLANE + o);
+            const uint64_t b_l = smem_desc<ROWB>(sb + 2 * PLANE + o), bi_l = smem_desc<ROWB>(sb + 3 * PLANE + o);
+            const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
+            mma_bf16(d_lo, ar_l, b_h, id_w, acc);
+            mma_bf16(d_lo, ai_l, bi_h, id_n | kNegateA, 1u);
+            mma_bf16(d_lo + 128, ai_l, b_h, id_n, 1u);
+            mma_bf16(d_lo, ar_h, b_l, id_w, 1u);
+            mma_bf16(d_lo, ai_h, bi_l, id_n | kNegateA, 1u);
+            mma_bf16(d_lo + 128, ai_h, b_l, id_n, 1u);
+            mma_bf16(d_hi, ar_h, b_h, id_w, acc);
+            mma_bf16(d_hi, ai_h, bi_h, id_n | kNegateA, 1u);
+            mma_bf16(d_hi + 128, ai_h, b_h, id_n, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(acc_full);  // also on error, so the fold sees issued MMAs retire
+      }
+    }
+  } else {
+    const int q4 = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = static_cast<uint32_t>(q4 * 32) << 16;
+    float* tr = epi + (warp - 2) * 2 * 32 * 33;  // this warp's Re and Im transpose blocks
+    const bool split = a.c_split != 0;
+    int64_t q = 0;  // tiles folded
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++q) {
+      const TileCoord tc = tile_of(w, tiles_m, tiles_n);
+      if (!mbar_wait(acc_full, static_cast<uint32_t>(q & 1))) {
+        atomicExch(err, 35);
+        break;
+      }
+      fence_after();
+      float run_re[64], run_im[64], v[32];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const uint32_t col = lane_base + half * 64 + p * 32;
+        tmem_ld32(tmem + col, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_re[p * 32 + i] = v[i];
+        tmem_ld32(tmem + 128 + col, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_im[p * 32 + i] = v[i];
+        tmem_ld32(tmem + 256 + col, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+        tmem_ld32(tmem + 384 + col, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);  // the accumulators are free for the next tile
+      // epilogue from registers: thread = TMEM lane (row); this warp's 64 columns
+      const int64_t m = static_cast<int64_t>(tc.m0) + q4 * 32 + lane;
+      const bool row_ok = m < a.m;
+      const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
+      float* C = a.C + static_cast<int64_t>(tc.b) * a.c_bstride;
+#pragma unroll
+      for (int cb = 0; cb < 2; ++cb) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          tr[lane * 33 + j] = run_re[cb * 32 + j];
+          tr[32 * 33 + lane * 33 + j] = run_im[cb * 32 + j];
+        }
+        __syncwarp();
+        const int64_t n = static_cast<int64_t>(tc.n0) + half * 64 + cb * 32 + lane;
+        const bool col_ok = n < a.n;
+        store_block(C, a.c_plane, split, tr, 33, 32 * 33, ro, col_ok ? map_off(a.cols, n) : 0, row_ok, col_ok, lane);
+        __syncwarp();
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CB::COLS));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -1148,6 +1355,9 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
   if (!configured) {
     cudaError_t e =
         cudaFuncSetAttribute(contract_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(contract_tcb_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               CBP::SMEM);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -1157,6 +1367,17 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
   if (!make_map_split(&ta, a.A, a.m, a.k, ca, a.a_plane, BM) || !make_map_split(&tb, a.B, a.n, a.k, cb, a.b_plane, BN))
     return cudaErrorInvalidValue;
   const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
+  if (a.k <= CBP::MAX_K) {
+    // shallow step: persistent, one CTA per SM (the shared memory admits one)
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t items = tiles * static_cast<int64_t>(nb);
+    const unsigned grid = static_cast<unsigned>(items < sms ? items : sms);
+    contract_tcb_persistent_kernel<<<grid, CB::THREADS, CBP::SMEM, st>>>(ta, tb, a, nb, err);
+    return cudaGetLastError();
+  }
   dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));
   contract_tcb_kernel<<<grid, CB::THREADS, CB::SMEM, st>>>(ta, tb, a, err);
   return cudaGetLastError();
