@@ -1396,7 +1396,9 @@ bool tc_step_ok(int64_t m, int64_t n, int64_t k, int32_t prec) {
   // TMA rows are k * element bytes and must be whole 16-byte units: k % 4 for the FP32
   // operands, k % 8 for the split-BF16 ones
   const int64_t kq = prec == TN_C64_BF16X3 ? 8 : 4;
-  return m >= BM && n >= 64 && k >= 8 && k % kq == 0 && k <= (int64_t(1) << 30) && m < (int64_t(1) << 31) &&
+  // n below the 128-column tile is allowed (the B box is zero-filled past n, the epilogue
+  // masks the columns): a quarter-filled tile still beats the CUDA cores several-fold
+  return m >= BM && n >= 16 && k >= 8 && k % kq == 0 && k <= (int64_t(1) << 30) && m < (int64_t(1) << 31) &&
          n < (int64_t(1) << 31);
 }
 

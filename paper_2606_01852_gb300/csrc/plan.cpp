@@ -348,7 +348,9 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     const double t_simt = std::max(bytes / kHbm, flops / kSimtFlops);
     st.cls = TN_CLASS_SIMT;
     if (tc_form_here && tc_step_ok(st.m, st.n, st.k, pol.prec)) {
-      const double t_tc = std::max(bytes / kHbm, flops / tc_flops(pol.prec));
+      // a step narrower than the 128-column tile uses that fraction of the tensor core
+      const double fill = std::min(1.0, double(st.n) / 128.0);
+      const double t_tc = std::max(bytes / kHbm, flops / (tc_flops(pol.prec) * fill));
       // ties (both bound by the same HBM bytes) go to the tensor-core kernel, whose
       // epilogue stores are the better coalesced
       if (t_tc <= t_simt) st.cls = TN_CLASS_TC;

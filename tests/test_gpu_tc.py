@@ -81,6 +81,7 @@ CASES = [
     ((128,), (2, 2, 32), (8, 4), [("n", 0), ("m", 0), ("n", 1), ("n", 2)]),      # interleaved columns
     ((256,), (96,), (16,), [("n", 0), ("m", 0)]),                                 # rows land strided
     ((2, 128), (128,), (8,), [("m", 0), ("n", 0), ("m", 1)]),                     # k = 8: half a k-block
+    ((4, 512), (32,), (2, 32), [("m", 0), ("n", 0), ("m", 1)]),                   # n = 32: a quarter tile
 ]
 
 
