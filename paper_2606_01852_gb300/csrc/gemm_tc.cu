@@ -225,39 +225,39 @@ template <int VB>
 __device__ __forceinline__ void store_sorted(float* C, int64_t plane, bool split, const float* t, int pitch, int cs,
                                              int64_t base, const int* e, const int* src, int lane) {
   constexpr int V = 1 << VB;
-  int rl = 0, cl = 0;
+  // r and c take disjoint bits, so t's index r * pitch + c is a sum of one increment per
+  // set bit: the lane's part, the store's part and, per element of the run, du[u]
+  auto step = [&](int k) { return src[k] < 5 ? pitch << src[k] : 1 << (src[k] - 5); };
+  int du[V];
+#pragma unroll
+  for (int u = 0; u < V; ++u) {
+    du[u] = 0;
+#pragma unroll
+    for (int k = 0; k < VB; ++k)
+      if ((u >> k) & 1) du[u] += step(k);
+  }
+  int il = 0;
   int64_t al = 0;
 #pragma unroll
   for (int k = 0; k < 5; ++k)
     if ((lane >> k) & 1) {
-      const int b = src[VB + k];
-      if (b < 5) rl |= 1 << b;
-      else cl |= 1 << (b - 5);
+      il += step(VB + k);
       al += int64_t(1) << e[VB + k];
     }
   for (int s = 0; s < (32 >> VB); ++s) {
-    int r = rl, c = cl;
+    int is = il;
     int64_t ah = 0;
 #pragma unroll
     for (int k = 0; k < 5 - VB; ++k)
       if ((s >> k) & 1) {
-        const int b = src[VB + 5 + k];
-        if (b < 5) r |= 1 << b;
-        else c |= 1 << (b - 5);
+        is += step(VB + 5 + k);
         ah += int64_t(1) << e[VB + 5 + k];
       }
     float re[V], im[V];
 #pragma unroll
     for (int u = 0; u < V; ++u) {
-      int ru = r, cu = c;
-#pragma unroll
-      for (int k = 0; k < VB; ++k)
-        if ((u >> k) & 1) {
-          if (src[k] < 5) ru |= 1 << src[k];
-          else cu |= 1 << (src[k] - 5);
-        }
-      re[u] = t[ru * pitch + cu];
-      im[u] = t[cs + ru * pitch + cu];
+      re[u] = t[is + du[u]];
+      im[u] = t[cs + is + du[u]];
     }
     store_run<V>(C, plane, base + al + ah, re, im, split);
   }
