@@ -368,19 +368,23 @@ def run_ours(args):
 
 
 def run_batch_bench(args):
-    """Many small networks: 4096 Ising partition functions on random 3-regular graphs
-    (20-60 spins, J = +-1, beta = 0.5), FP32 with exponent scaling, one persistent
-    graph-replayed launch (launch shape from the autotuner), against one tn_contract
-    launch sequence per network. Metric: networks/s."""
+    """Many small networks in one persistent graph-replayed launch (launch shape from the
+    autotuner), against one tn_contract launch sequence per network. Metric: networks/s.
+      ising3r    : 4096 Ising partition functions on random 3-regular graphs (20-60 spins,
+                   J = +-1, beta = 0.5), FP32 with exponent scaling;
+      kingsbatch : 4096 maximum independent sets of King's subgraphs (L 4-7, density
+                   0.8), the max-plus semiring."""
     import torch
     import paper_2606_01852_gb300 as tn
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     count = args.networks
-    wl = workloads.ising3r(count, seed=3)
+    maxplus = args.workload == "kingsbatch"
+    semiring = "maxplus" if maxplus else "standard"
+    wl = workloads.kings_batch(count) if maxplus else workloads.ising3r(count, seed=3)
     nets, paths = [w.net for w in wl], [w.path for w in wl]
-    b = tn.Batch(nets, paths, complex_=False, exp_scaling=True)
+    b = tn.Batch(nets, paths, complex_=False, exp_scaling=not maxplus, semiring=semiring)
     packed = torch.tensor(b.pack(nets), device="cuda")
     vals = torch.zeros((count, 2), dtype=torch.float64, device="cuda")
     logs = torch.zeros(count, dtype=torch.float64, device="cuda")
@@ -399,7 +403,8 @@ def run_batch_bench(args):
     ck = clocks.stop()
     ms = statistics.mean(a.elapsed_time(c) for a, c in ev)
     # one launch sequence per network (the per-contraction baseline)
-    plans = [tn.Plan(n, p, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True) for n, p in zip(nets, paths)]
+    plans = [tn.Plan(n, p, prec=tn.TN_R32_FP32_SIMT, exp_scaling=not maxplus, semiring=semiring)
+             for n, p in zip(nets, paths)]
     dins = [[torch.tensor(np.asarray(t, dtype=np.float32), device="cuda") for t in n.tensors] for n in nets]
     outs = torch.zeros(count, dtype=torch.float64, device="cuda")
     lss = torch.zeros(count, dtype=torch.float64, device="cuda")
@@ -413,20 +418,27 @@ def run_batch_bench(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_seq = e0.elapsed_time(e1)
-    lnz_b = np.log(vals[:, 0].cpu().numpy()) + logs.cpu().numpy()
-    lnz_s = np.log(outs.cpu().numpy()) + lss.cpu().numpy()
+    if maxplus:  # both are exact integers
+        diff = float(np.max(np.abs(vals[:, 0].cpu().numpy() - outs.cpu().numpy())))
+    else:
+        lnz_b = np.log(vals[:, 0].cpu().numpy()) + logs.cpu().numpy()
+        lnz_s = np.log(outs.cpu().numpy()) + lss.cpu().numpy()
+        diff = float(np.max(np.abs(lnz_b - lnz_s)))
     t, c = b.launch_shape()
-    alu = SM_COUNT * FP32_LANES * 2 * load_peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    alu = SM_COUNT * FP32_LANES * (1 if maxplus else 2) * load_peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     line = {
         "metric": "networks/s", "value": ws * count / (ms / 1e3), "unit": "networks/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "ising3r", "networks": count, "desc": "Ising partition functions, random "
-                   "3-regular graphs, 20-60 spins, J=+-1, beta=0.5, FP32 + exponent scaling",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (max,+)" if maxplus else "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "networks": count,
+                   "desc": ("maximum independent sets of King's subgraphs, L 4-7, density 0.8, max-plus FP32"
+                            if maxplus else "Ising partition functions, random 3-regular graphs, 20-60 spins, "
+                            "J=+-1, beta=0.5, FP32 + exponent scaling"),
                    "launch_shape": {"threads": t, "ctas_per_sm": c}, "graph": True},
         "one_launch_per_contraction": {"ms": ms_seq, "networks_per_s": count / (ms_seq / 1e3),
                                        "speedup_of_persistent": ms_seq / ms},
-        "max_abs_lnz_diff_vs_per_contraction": float(np.max(np.abs(lnz_b - lnz_s))),
+        ("max_abs_diff_vs_per_contraction" if maxplus else "max_abs_lnz_diff_vs_per_contraction"): diff,
         "roofline": {"bound": "alu", "achieved": b.flops / (ms / 1e3) / 1e12, "peak": alu, "unit": "TFLOP/s",
                      "frac": b.flops / (ms / 1e3) / 1e12 / alu, "traffic": None, "kernel": "batch_kernel"},
         "gpu_launches": args.steps, "clocks": ck,
@@ -570,7 +582,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rc40", choices=sorted(workloads.BY_NAME) + ["ising3r", "serve"])
+    ap.add_argument("--workload", default="rc40",
+                    choices=sorted(workloads.BY_NAME) + ["ising3r", "kingsbatch", "serve"])
     ap.add_argument("--networks", type=int, default=4096, help="ising3r: networks per launch")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -585,7 +598,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.workload == "ising3r" and args.impl == "ours":
+    if args.workload in ("ising3r", "kingsbatch") and args.impl == "ours":
         return run_batch_bench(args)
     if args.workload == "serve" and args.impl == "ours":
         return run_serve_bench(args)

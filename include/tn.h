@@ -288,7 +288,9 @@ typedef struct tn_batch_s* tn_batch_t;
  * tn_plan (Sec. II-B, Sec. IV-A) and its own arena; one CTA contracts one network at a
  * time, taking networks from an atomic queue. policy.prec must be TN_C64_FP32_SIMT or
  * TN_R32_FP32_SIMT; policy.exp_scaling renormalises every tensor by an exact power of two
- * as it is made and sums the exponents per network in an int64. With
+ * as it is made and sums the exponents per network in an int64; policy.semiring may be
+ * TN_SEMIRING_MAXPLUS with R32 and no scaling (each value is then the network's max-plus
+ * value, log scale 0). With
  * TN_PLAN_HOST_ONLY no device memory is taken (tables only, for tn_batch_info). */
 tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* paths, tn_dtype_policy policy,
                         tn_batch_t* out);

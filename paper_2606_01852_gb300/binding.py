@@ -352,14 +352,14 @@ class Plan:
 class Batch:
     """Many small closed networks, one persistent launch (tn_batch_*)."""
 
-    def __init__(self, nets, paths, complex_=False, exp_scaling=True, host_only=False):
+    def __init__(self, nets, paths, complex_=False, exp_scaling=True, host_only=False, semiring="standard"):
         self._arrs = [_NetArrays([tuple(m) for m in n.modes], dict(n.extent), tuple(n.open_modes),
                                  p.pairs if hasattr(p, "pairs") else p) for n, p in zip(nets, paths)]
         self.n_nets = len(nets)
         self.complex = complex_
         netv = (tn_network * self.n_nets)(*[a.net for a in self._arrs])
         pathv = (tn_path * self.n_nets)(*[a.path for a in self._arrs])
-        pol = make_policy(TN_C64_FP32_SIMT if complex_ else TN_R32_FP32_SIMT, exp_scaling, 1, host_only)
+        pol = make_policy(TN_C64_FP32_SIMT if complex_ else TN_R32_FP32_SIMT, exp_scaling, 1, host_only, semiring)
         h = C.c_void_p()
         check(lib.tn_batch_plan(self.n_nets, netv, pathv, pol, C.byref(h)))
         self.handle = h

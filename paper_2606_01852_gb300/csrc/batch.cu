@@ -90,7 +90,7 @@ __device__ void renormalise(float* t, int size, int* smax, long long* slog) {
   __syncthreads();
 }
 
-template <bool CPLX>
+template <bool CPLX, bool MAXPLUS = false>
 __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restrict__ leaves,
                              const BStep* __restrict__ steps, int32_t n_nets, const float* __restrict__ in,
                              float* arena, int32_t* queue, int32_t scaling, double* values, double* logs) {
@@ -140,12 +140,15 @@ __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restr
         const int i = o / S.n, j = o - i * S.n;
         const float* A = ar + S.a + i * S.k;
         const float* B = ar + S.b + j * S.k;
-        float cr = 0.f, ci = 0.f;
+        // max-plus (real, unscaled): the semiring's zero is -inf, its product +
+        float cr = MAXPLUS ? __int_as_float(0xff800000) : 0.f, ci = 0.f;
         for (int t = 0; t < S.k; ++t) {
           if (CPLX) {
             const float xr = A[t], xi = A[S.a_size + t], yr = B[t], yi = B[S.b_size + t];
             cr = fmaf(xr, yr, fmaf(-xi, yi, cr));
             ci = fmaf(xr, yi, fmaf(xi, yr, ci));
+          } else if (MAXPLUS) {
+            cr = fmaxf(cr, A[t] + B[t]);
           } else {
             cr = fmaf(A[t], B[t], cr);
           }
@@ -182,7 +185,7 @@ using namespace tn;
 
 struct tn_batch_s {
   int32_t n_nets = 0;
-  bool cplx = false, scaling = false;
+  bool cplx = false, scaling = false, maxplus = false;
   std::vector<BNet> nets;
   std::vector<BLeaf> leaves;
   std::vector<BStep> steps;
@@ -216,6 +219,10 @@ tn_status launch_batch(tn_batch_s* B, const void* packed, double* values, double
     batch_kernel<true><<<grid, B->threads, 0, st>>>(B->d_nets, B->d_leaves, B->d_steps, B->n_nets,
                                                      static_cast<const float*>(packed), B->d_arena, B->d_queue,
                                                      B->scaling ? 1 : 0, values, logs);
+  else if (B->maxplus)
+    batch_kernel<false, true><<<grid, B->threads, 0, st>>>(B->d_nets, B->d_leaves, B->d_steps, B->n_nets,
+                                                            static_cast<const float*>(packed), B->d_arena,
+                                                            B->d_queue, 0, values, logs);
   else
     batch_kernel<false><<<grid, B->threads, 0, st>>>(B->d_nets, B->d_leaves, B->d_steps, B->n_nets,
                                                       static_cast<const float*>(packed), B->d_arena, B->d_queue,
@@ -245,6 +252,11 @@ tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* p
   B->n_nets = n_nets;
   B->cplx = policy.prec == TN_C64_FP32_SIMT;
   B->scaling = policy.exp_scaling != 0;
+  B->maxplus = policy.semiring == TN_SEMIRING_MAXPLUS;
+  if (B->maxplus && (B->cplx || B->scaling)) {
+    set_error("tn_batch_plan: the max-plus semiring runs R32 without exponent scaling");
+    return TN_ERR_UNSUPPORTED;
+  }
   const int np = B->cplx ? 2 : 1;
   int64_t in_off = 0;
   tn_dtype_policy hp = policy;

@@ -172,3 +172,15 @@ def test_maxplus_policy_checks():
         with pytest.raises(tn.TnError) as e:
             tn.Plan(net, path, semiring="maxplus", host_only=True, **kw)
         assert "TN_ERR_UNSUPPORTED" in str(e.value)
+
+
+def test_batch_maxplus_policy_checks():
+    tn = ensure_built()
+    ws = workloads.kings_batch(4, seed=2)
+    nets, paths = [w.net for w in ws], [w.path for w in ws]
+    b = tn.Batch(nets, paths, complex_=False, exp_scaling=False, semiring="maxplus", host_only=True)
+    assert b.flops > 0
+    b.destroy()
+    with pytest.raises(tn.TnError) as e:
+        tn.Batch(nets, paths, complex_=False, exp_scaling=True, semiring="maxplus", host_only=True)
+    assert "TN_ERR_UNSUPPORTED" in str(e.value)

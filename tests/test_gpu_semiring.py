@@ -100,3 +100,22 @@ def test_kings16_full(tn):
     got, _ = run_real(tn, plan, w.net)
     assert float(got) == gold[0] == 64.0
     plan.destroy()
+
+
+def test_batch_maxplus_vs_oracle(tn):
+    """48 King's subgraphs (L 4-7) in one persistent launch of the batch engine in the
+    max-plus semiring, each MIS size exact, graph replay included."""
+    ws = workloads.kings_batch(48, seed=11)
+    nets, paths = [w.net for w in ws], [w.path for w in ws]
+    b = tn.Batch(nets, paths, complex_=False, exp_scaling=False, semiring="maxplus")
+    packed = torch.tensor(b.pack(nets), device="cuda")
+    vals = torch.zeros((len(ws), 2), dtype=torch.float64, device="cuda")
+    logs = torch.zeros(len(ws), dtype=torch.float64, device="cuda")
+    want = np.array([float(oracle.contract(n, p, semiring="maxplus")) for n, p in zip(nets, paths)])
+    for graph in (False, True):
+        vals.zero_()
+        b.contract(packed, vals, logs, graph=graph)
+        torch.cuda.synchronize()
+        assert np.array_equal(vals[:, 0].cpu().numpy(), want)
+        assert np.all(logs.cpu().numpy() == 0.0)
+    b.destroy()

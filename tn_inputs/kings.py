@@ -86,3 +86,10 @@ def kings_network(L: int, rho: float, seed: int, semiring: str = "tropical") -> 
     net = independent_set_network(n, edges, semiring, name=f"kings_{L}x{L}_r{rho}_s{seed}_{semiring}")
     net.meta.update(L=L, rho=rho, seed=seed)
     return net
+
+
+def kings_ensemble(count: int, seed: int, sizes=(6, 10), rho: float = 0.8, semiring: str = "tropical"):
+    """`count` King's subgraph networks, L uniform in [sizes[0], sizes[1]], one seed each."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Ls = rng.integers(sizes[0], sizes[1] + 1, size=count)
+    return [kings_network(int(L), rho, seed * 100003 + i, semiring) for i, L in enumerate(Ls)]

@@ -16,6 +16,8 @@
   ktri44    : kicked Ising on a 4x4 triangular lattice, 8 Trotter steps;
   kings16   : maximum independent set of a 16x16 King's subgraph (site density 0.8, seed 1;
               209 vertices), contracted in the max-plus semiring (FP32, exact integers);
+  kings_batch: maximum independent sets of many King's subgraphs (L in [4, 7], density 0.8),
+              max-plus, for the one-launch batch engine;
   ising3r   : an ensemble of Ising partition functions on random 3-regular graphs.
 Smaller variants with the same structure serve as parity cases.
 
@@ -127,6 +129,16 @@ def ising_workload(net):
 
 def ising3r(count, seed=3):
     return [ising_workload(n) for n in ising_pf.ensemble(count, seed)]
+
+
+def kings_batch(count, seed=5):
+    """Maximum independent sets of `count` King's subgraphs, L in [4, 7], density 0.8."""
+    out = []
+    for n in kings.kings_ensemble(count, seed, sizes=(4, 7)):
+        wl = ising_workload(n)
+        wl.info["semiring"] = "maxplus"
+        out.append(wl)
+    return out
 
 
 BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40u": rc40u, "kising44": kising44, "rc40open": rc40open,
