@@ -55,6 +55,8 @@ StepArgs step_args(const Plan& P, const StepRec& st) {
   a.rec_c = P.rec_index[st.out];
   a.c_split = C.split ? 1 : 0;
   a.maxplus = P.policy.semiring == TN_SEMIRING_MAXPLUS ? 1 : 0;
+  a.ksplit = st.ksplit;
+  a.part = st.ksplit > 1 ? reinterpret_cast<float*>(P.dev + P.off_scratch) : nullptr;
   return a;
 }
 void* take_event(Plan& P) {

@@ -35,13 +35,19 @@ struct StepArgs {
   int32_t rec_a, rec_b, rec_c;
   int32_t c_split;                          // 1: write C in the split-BF16 form (complex)
   int32_t maxplus;                          // 1: (max, +) semiring (real, unscaled)
-  int32_t pad;
+  int32_t ksplit;                           // SIMT: k cut in ksplit parts (partials in `part`)
+  float* part;                              // ksplit * nb * planes * m * n floats, or null
 };
 
 void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int64_t slice_begin,
                          int32_t nb, bool only_batched, bool is_complex, ScaleRec* recs,
                          const int32_t* rec_index, cudaStream_t st);
+// With a.ksplit > 1 each part of k goes to its own CTAs and a second kernel combines the
+// partial tiles (in part order) and writes C.
 void launch_contract_simt(const StepArgs& a, int32_t nb, bool cplx, cudaStream_t st);
+// k parts for a SIMT step of m x n outputs per batch entry, `copies` entries, depth k on
+// num_sms SMs (1 = no split); scaled steps are never split
+int32_t simt_ksplit(int64_t m, int64_t n, int64_t k, int64_t copies, int num_sms, bool scaled);
 void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, cudaStream_t st);
 
 // split-K steps: at most kSplitMaxOut outputs, k cut in chunks of kSplitChunk; scratch

@@ -7,6 +7,7 @@
 //   contract_stream   : big x small steps (n*k tiny), one pass over the big operand
 //   accumulate_root   : compensated FP64 sum of the root over the slice batch
 //   finalize_output   : writes the FP64 result and its log scale
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -126,6 +127,9 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
   const float* A = a.A + b * a.a_bstride;
   const float* B = a.B + b * a.b_bstride;
   float* C = a.C + b * a.c_bstride;
+  // this CTA's part of k (all of it unless the step is split, blockIdx.z = part)
+  const int64_t kc = a.ksplit > 1 ? ((a.k + a.ksplit - 1) / a.ksplit + BK - 1) / BK * BK : a.k;
+  const int64_t kbeg = blockIdx.z * kc, kend = kbeg + kc < a.k ? kbeg + kc : a.k;
   float sa = 1.f, sb = 1.f;
   if (a.recs) {
     const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
     for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = kZero;
 
   const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: row lr, k lk..lk+3
-  for (int64_t k0 = 0; k0 < a.k; k0 += BK) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
 #pragma unroll
@@ -148,8 +152,8 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
         const int64_t kk = k0 + lk + q;
         const int64_t ra = m0 + lr, rb = n0 + lr;
         float va = kZero, vb = kZero;
-        if (ra < a.m && kk < a.k) va = A[p * a.a_plane + ra * a.k + kk] * sa;
-        if (rb < a.n && kk < a.k) vb = B[p * a.b_plane + rb * a.k + kk] * sb;
+        if (ra < a.m && kk < kend) va = A[p * a.a_plane + ra * a.k + kk] * sa;
+        if (rb < a.n && kk < kend) vb = B[p * a.b_plane + rb * a.k + kk] * sb;
         As[p][lk + q][lr] = va;
         Bs[p][lk + q][lr] = vb;
       }
@@ -184,6 +188,24 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
         }
     }
     __syncthreads();
+  }
+  if (a.ksplit > 1) {
+    // partial tile of this part of k, dense [part][b][plane][m][n]; combined and written
+    // through the offset maps by simt_combine_kernel
+    float* P0 = a.part + ((int64_t(blockIdx.z) * gridDim.y + b) * NP) * a.m * a.n;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t m = m0 + ty * 4 + i;
+      if (m >= a.m) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = n0 + tx + 16 * j;
+        if (n >= a.n) continue;
+        P0[m * a.n + n] = accr[i][j];
+        if (CPLX) P0[a.m * a.n + m * a.n + n] = acci[i][j];
+      }
+    }
+    return;
   }
   // epilogue through the offset maps
   int64_t coff[4];
@@ -297,12 +319,54 @@ __global__ void __launch_bounds__(256) contract_stream_kernel(StepArgs a) {
   }
 }
 
+// Combine the k parts of a split SIMT step in part order (sum, or max for max-plus) and
+// write C through the offset maps. One thread per output element of every batch entry.
+__global__ void simt_combine_kernel(StepArgs a, int32_t nb, int32_t cplx) {
+  const int64_t mn = a.m * a.n, np = cplx ? 2 : 1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nb * mn;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / mn, o = e - b * mn;
+    const float* P0 = a.part + b * np * mn + o;
+    const int64_t pstride = (int64_t)nb * np * mn;  // one part to the next
+    float vr = P0[0], vi = cplx ? P0[mn] : 0.f;
+    for (int s = 1; s < a.ksplit; ++s) {
+      const float xr = P0[s * pstride];
+      if (a.maxplus) {
+        vr = fmaxf(vr, xr);
+      } else {
+        vr += xr;
+        if (cplx) vi += P0[s * pstride + mn];
+      }
+    }
+    const int64_t i = o / a.n, j = o - i * a.n;
+    const int64_t off = map_offset(a.rows, i) + map_offset(a.cols, j);
+    float* C = a.C + b * a.c_bstride;
+    if (cplx) store_cplx(C, a.c_plane, off, vr, vi, a.c_split != 0);
+    else C[off] = vr;
+  }
+}
+
+int32_t simt_ksplit(int64_t m, int64_t n, int64_t k, int64_t copies, int num_sms, bool scaled) {
+  if (scaled || k < 2048) return 1;
+  const int64_t tiles = ((m + 63) / 64) * ((n + 63) / 64) * copies;
+  if (tiles >= 2 * int64_t(num_sms)) return 1;
+  int64_t s = (2 * int64_t(num_sms) + tiles - 1) / tiles;
+  s = std::min<int64_t>(s, k / 1024);
+  s = std::min<int64_t>(s, 32);
+  return s > 1 ? int32_t(s) : 1;
+}
+
 void launch_contract_simt(const StepArgs& a, int32_t nb, bool cplx, cudaStream_t st) {
   const int64_t tiles = ((a.m + 63) / 64) * ((a.n + 63) / 64);
-  dim3 grid((unsigned)tiles, (unsigned)nb);
+  dim3 grid((unsigned)tiles, (unsigned)nb, (unsigned)(a.ksplit > 1 ? a.ksplit : 1));
   if (cplx) contract_simt_kernel<true><<<grid, 256, 0, st>>>(a);
   else if (a.maxplus) contract_simt_kernel<false, true><<<grid, 256, 0, st>>>(a);
   else contract_simt_kernel<false><<<grid, 256, 0, st>>>(a);
+  if (a.ksplit > 1) {
+    const int64_t total = int64_t(nb) * a.m * a.n;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+    simt_combine_kernel<<<blocks, 256, 0, st>>>(a, nb, cplx ? 1 : 0);
+  }
 }
 
 void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, cudaStream_t st) {

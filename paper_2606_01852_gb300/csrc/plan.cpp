@@ -582,6 +582,14 @@ void assign_workspace(Plan& P, int64_t batch) {
   cur += kAlign;
   // split-K partials: the largest need of any split-K step (one pass)
   int64_t scratch = 0;
+  for (StepRec& st : P.steps) {
+    st.ksplit = st.cls == TN_CLASS_SIMT ? simt_ksplit(st.m, st.n, st.k, st.batched ? batch : 1, P.num_sms,
+                                                      P.policy.exp_scaling != 0)
+                                        : 1;
+    if (st.ksplit > 1)
+      scratch = std::max(scratch, int64_t(st.ksplit) * (st.batched ? batch : 1) * st.m * st.n *
+                                      (P.is_complex ? 2 : 1) * 4);
+  }
   for (const StepRec& st : P.steps)
     if (st.cls == TN_CLASS_SPLITK)
       scratch = std::max(scratch, (st.batched ? batch : 1) * ((st.k + kSplitChunk - 1) / kSplitChunk) *

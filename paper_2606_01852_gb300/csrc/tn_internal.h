@@ -61,6 +61,7 @@ struct StepRec {
   int32_t cls = TN_CLASS_SIMT;
   bool batched = false;
   OffsetMap rows{}, cols{};
+  int32_t ksplit = 1;  // SIMT steps too few tiles to fill the GPU: k cut in this many parts
 };
 
 struct Plan {

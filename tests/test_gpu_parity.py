@@ -16,6 +16,7 @@ import oracle
 from tests._lib import ensure_built
 from tests.test_oracle_pins import random_network
 from tn_inputs import circuits, greedy, ising_pf, kicked_ising, workloads
+from tn_inputs.network import Network, Path
 
 pytestmark = pytest.mark.gpu
 REL = 1e-5
@@ -229,3 +230,23 @@ def test_splitk_sliced_batch(tn):
     assert plan.step(0)["cls"] == tn.TN_CLASS_SPLITK and plan.step(0)["batched"] == 1
     got, _ = run(tn, plan, net)
     assert rel_err(got, oracle.contract(net, path, sliced)) < REL
+
+
+@pytest.mark.parametrize("k_bits", [11, 13])
+def test_simt_ksplit_underfilled_grid(tn, k_bits):
+    """A 64 x 96 output over k = 2^11 or 2^13: too few 64 x 64 tiles to fill the GPU, so the
+    CUDA-core kernel cuts k into parts and a second kernel combines them in part order."""
+    rng = np.random.default_rng(k_bits)
+    kd = (2,) * k_bits
+    A = rng.standard_normal((64,) + kd) + 1j * rng.standard_normal((64,) + kd)
+    B = rng.standard_normal((96,) + kd) + 1j * rng.standard_normal((96,) + kd)
+    K = tuple(range(2, 2 + k_bits))
+    ext = {0: 64, 1: 96, **{x: 2 for x in K}}
+    net = Network([A, B], [(0,) + K, (1,) + K], ext, (1, 0))
+    path = Path([(0, 1)])
+    plan = tn.Plan(net, path, prec="fp32")
+    assert plan.step(0)["cls"] == tn.TN_CLASS_SIMT
+    got, _ = run(tn, plan, net)
+    want = oracle.contract(net, path)
+    assert rel_err(got, want) < 1e-5
+    plan.destroy()

@@ -119,3 +119,20 @@ def test_batch_maxplus_vs_oracle(tn):
         assert np.array_equal(vals[:, 0].cpu().numpy(), want)
         assert np.all(logs.cpu().numpy() == 0.0)
     b.destroy()
+
+
+def test_maxplus_simt_ksplit(tn):
+    """max over k = 2^13 for a 64 x 96 output: the split CUDA-core path in max-plus (part
+    maxima, then the maximum over parts) is exact."""
+    rng = np.random.default_rng(9)
+    kd = (2,) * 13
+    A = np.floor(rng.standard_normal((64,) + kd) * 50)
+    B = np.floor(rng.standard_normal((96,) + kd) * 50)
+    K = tuple(range(2, 15))
+    net = Network([A, B], [(0,) + K, (1,) + K], {0: 64, 1: 96, **{x: 2 for x in K}}, (0, 1))
+    plan = tn.Plan(net, Path([(0, 1)]), prec=tn.TN_R32_FP32_SIMT, semiring="maxplus")
+    assert plan.step(0)["cls"] == tn.TN_CLASS_SIMT
+    got, _ = run_real(tn, plan, net)
+    want = np.max(A.reshape(64, -1)[:, None, :] + B.reshape(96, -1)[None, :, :], axis=2)
+    assert np.array_equal(got, want)
+    plan.destroy()
