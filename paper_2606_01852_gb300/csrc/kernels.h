@@ -46,7 +46,7 @@ void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int6
 // partial tiles (in part order) and writes C.
 void launch_contract_simt(const StepArgs& a, int32_t nb, bool cplx, cudaStream_t st);
 // k parts for a SIMT step of m x n outputs per batch entry, `copies` entries, depth k on
-// num_sms SMs (1 = no split); scaled steps are never split
+// num_sms SMs (1 = no split: at least 2 x num_sms tiles, k < 2048, or a scaled step)
 int32_t simt_ksplit(int64_t m, int64_t n, int64_t k, int64_t copies, int num_sms, bool scaled);
 void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, cudaStream_t st);
 

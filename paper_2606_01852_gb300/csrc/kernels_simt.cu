@@ -348,9 +348,10 @@ __global__ void simt_combine_kernel(StepArgs a, int32_t nb, int32_t cplx) {
 
 int32_t simt_ksplit(int64_t m, int64_t n, int64_t k, int64_t copies, int num_sms, bool scaled) {
   if (scaled || k < 2048) return 1;
+  // aim at four 256-thread CTAs per SM (the kernel's blocks are short-lived)
   const int64_t tiles = ((m + 63) / 64) * ((n + 63) / 64) * copies;
   if (tiles >= 2 * int64_t(num_sms)) return 1;
-  int64_t s = (2 * int64_t(num_sms) + tiles - 1) / tiles;
+  int64_t s = (4 * int64_t(num_sms) + tiles - 1) / tiles;
   s = std::min<int64_t>(s, k / 1024);
   s = std::min<int64_t>(s, 32);
   return s > 1 ? int32_t(s) : 1;
