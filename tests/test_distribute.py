@@ -211,3 +211,15 @@ def test_unsliced_40_qubit_amplitude_report():
     assert rep["projected_total"] == pytest.approx(rep["t_total"])  # one slice
     big = [st for st in steps if st["out_bytes"] >= 8 * 2**30]
     assert big and all(st["chain"] >= 0 for st in big)
+
+
+def test_report_cli(capsys):
+    """The report module prints one JSON line per device count with the Eq. 8-10 figures."""
+    import json
+    from paper_2606_01852_gb300 import distplan
+    distplan.main(["--workload", "rc12", "--gpus", "1", "4", "--large-gib", "1e-6"])
+    lines = [json.loads(x) for x in capsys.readouterr().out.strip().splitlines()]
+    assert [x["n_gpus"] for x in lines] == [1, 4]
+    assert lines[0]["n_chains"] == 0 and lines[0]["speedup"] == 1.0
+    assert lines[1]["n_chains"] >= 1 and lines[1]["schedule"]
+    assert lines[1]["extra_speedup"] == pytest.approx(lines[1]["speedup"] / 4)
