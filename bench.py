@@ -465,7 +465,7 @@ def run_serve_bench(args):
     rng = np.random.default_rng(2026)
     amp_w = workloads.rc12()
     pf_pool = workloads.ising3r(64, seed=5)
-    kis = workloads.kicked(5, 2)
+    kis = workloads.kising55()
     n_req = int(args.rate * args.serve_seconds)
     gaps = rng.exponential(1.0 / args.rate, size=n_req)
     arrive = np.cumsum(gaps)
@@ -553,11 +553,18 @@ def run_serve_bench(args):
             p.destroy()
         return out, results
 
-    mixed, r_mixed = serve(tn.TN_C64_3XTF32, args.serve_inflight, args.serve_streams)
+    mixed, r_mixed = serve(PREC[args.prec], args.serve_inflight, args.serve_streams)
     plain, r_plain = serve(tn.TN_C64_FP32_SIMT, 1, 1)
-    # the two forms must agree (3xTF32 vs FP32: same 1e-5 relative bar as the tests)
-    c0 = cls == 0
+    # the two forms must agree: amplitudes (CUDA-core steps in both forms) and the kicked-
+    # Ising expectations (tensor-core steps in the mixed form), relative differences
+    c0, c2 = cls == 0, cls == 2
     amp_err = float(np.max(np.abs(r_mixed[c0] - r_plain[c0]).sum(1) / (np.abs(r_plain[c0]).sum(1) + 2 ** -6)))
+    kis_err = float(np.max(np.abs(r_mixed[c2] - r_plain[c2]).sum(1) / np.abs(r_plain[c2]).sum(1))) if c2.any() else 0.0
+    kis_want = stored_oracle_value("kising55")
+    kis_vs_oracle = None
+    if kis_want is not None and c2.any():
+        kis_vs_oracle = {f: float(np.max(np.abs(r[c2, 0] + 1j * r[c2, 1] - kis_want)) / abs(kis_want))
+                         for f, r in (("mixed", r_mixed), ("plain_fp32", r_plain))}
     line = {
         "metric": "serve throughput (requests/s) and p50/p99 latency", "value": mixed["throughput_req_s"],
         "unit": "requests/s", "n_gpus": ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -565,11 +572,13 @@ def run_serve_bench(args):
         "config": {"workload": "serve-mix", "rate_req_s": args.rate, "seconds": args.serve_seconds,
                    "requests": n_req, "mix": {"amplitude_3x4_m8": 0.70, "ising_pf_3reg_20_60": 0.25,
                                               "kicked_ising_5x5_T2": 0.05},
-                   "form": "3xtf32 (FP32-accurate)", "max_inflight": args.serve_inflight,
+                   "form": args.prec, "max_inflight": args.serve_inflight,
                    "streams": args.serve_streams},
         "mixed": mixed, "plain_fp32_one_at_a_time": plain,
         "p99_speedup": plain["p99_ms"] / mixed["p99_ms"],
         "max_rel_diff_amplitudes_mixed_vs_plain": amp_err,
+        "max_rel_diff_kicked_ising_mixed_vs_plain": kis_err,
+        "kicked_ising_rel_err_vs_oracle": kis_vs_oracle,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -8,6 +8,7 @@ Calls only the oracle and the seeded input generators:
   * rc12 (12-qubit circuit): the full value;
   * khex45, ktri44 (kicked Ising on a honeycomb and a triangular lattice): the full values;
   * kings16 (King's subgraph, max-plus semiring): the maximum independent set size;
+  * kising55 (5x5 kicked Ising, 2 steps; the serving mix's large request): the full value;
   * rc40open (rc40 with four qubits left open): the [2,2,2,2] partial tensors of 4 slices
     drawn with a second fixed seed.
 Run from the repository root: python tests/golden/make_oracle_values.py
@@ -44,7 +45,7 @@ def main():
     _, parts = oracle.contract_slices(w.net, w.path, w.sliced, slice_ids=ids, return_partials=True)
     out["rc40open"] = {"slices": ids, "shape": list(np.shape(parts[0])),
                        "partials": [[[float(v.real), float(v.imag)] for v in np.ravel(p)] for p in parts]}
-    for name in ("kising44", "rc12", "khex45", "ktri44", "kings16"):
+    for name in ("kising44", "rc12", "khex45", "ktri44", "kings16", "kising55"):
         wl = workloads.BY_NAME[name]()
         v = complex(oracle.contract(wl.net, wl.path, wl.sliced, semiring=wl.info.get("semiring", "standard")))
         out[name] = {"value": [v.real, v.imag]}

@@ -85,10 +85,11 @@ def test_kising44_full(tn, prec, tol):
     assert abs(complex(out.cpu()) - want) / abs(want) < tol
 
 
-@pytest.mark.parametrize("name", ["khex45", "ktri44"])
+@pytest.mark.parametrize("name", ["khex45", "ktri44", "kising55"])
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("3xtf32", 1e-4), ("bf16x3", 1e-4), ("tf32", 1e-1)])
 def test_lattice_dynamics_full(tn, name, prec, tol):
-    """Kicked Ising on the honeycomb and triangular lattices: same bounds as the square one."""
+    """Kicked Ising on the honeycomb and triangular lattices, and on the 5 x 5 square lattice
+    of the serving mix: same bounds as the 4 x 4 square one."""
     w = workloads.BY_NAME[name]()
     plan = tn.Plan(w.net, w.path, prec=prec)
     if prec != "fp32":

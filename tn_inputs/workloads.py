@@ -97,6 +97,12 @@ def kising44():
     return kicked(4, 10)
 
 
+def kising55():
+    """Kicked Ising on a 5 x 5 lattice, 2 Trotter steps (greedy peak 2^26): the serving
+    mix's large request."""
+    return kicked(5, 2)
+
+
 def khex45():
     """Kicked Ising on a 4 x 5 honeycomb (brick-wall) lattice, 6 Trotter steps."""
     return kicked(4, 6, cols=5, lattice="hexagonal")
@@ -141,5 +147,6 @@ def kings_batch(count, seed=5):
     return out
 
 
-BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40u": rc40u, "kising44": kising44, "rc40open": rc40open,
+BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40u": rc40u, "kising44": kising44, "kising55": kising55,
+           "rc40open": rc40open,
            "khex45": khex45, "ktri44": ktri44, "kings16": kings16}
