@@ -553,7 +553,7 @@ def run_serve_bench(args):
             p.destroy()
         return out, results
 
-    mixed, r_mixed = serve(PREC[args.prec], args.serve_inflight, args.serve_streams)
+    mixed, r_mixed = serve(PREC[args.serve_prec], args.serve_inflight, args.serve_streams)
     plain, r_plain = serve(tn.TN_C64_FP32_SIMT, 1, 1)
     # the two forms must agree: amplitudes (CUDA-core steps in both forms) and the kicked-
     # Ising expectations (tensor-core steps in the mixed form), relative differences
@@ -572,7 +572,7 @@ def run_serve_bench(args):
         "config": {"workload": "serve-mix", "rate_req_s": args.rate, "seconds": args.serve_seconds,
                    "requests": n_req, "mix": {"amplitude_3x4_m8": 0.70, "ising_pf_3reg_20_60": 0.25,
                                               "kicked_ising_5x5_T2": 0.05},
-                   "form": args.prec, "max_inflight": args.serve_inflight,
+                   "form": args.serve_prec, "max_inflight": args.serve_inflight,
                    "streams": args.serve_streams},
         "mixed": mixed, "plain_fp32_one_at_a_time": plain,
         "p99_speedup": plain["p99_ms"] / mixed["p99_ms"],
@@ -598,6 +598,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-inflight", type=int, default=16)
     ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-prec", default="3xtf32", choices=sorted(PREC),
+                    help="serve: form of the mixed run (3xtf32: FP32-accurate on every request type)")
     ap.add_argument("--prec", default="bf16x3", choices=sorted(PREC),
                     help="GEMM form: bf16x3 (default), 3xtf32, tf32, fp32 (the plain CUDA-core form)")
     ap.add_argument("--max-slice-batch", type=int, default=0)

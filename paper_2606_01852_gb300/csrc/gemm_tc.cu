@@ -163,6 +163,12 @@ __device__ __forceinline__ int64_t map_off(const OffsetMap& om, int64_t idx) {
 }
 
 __device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
+// v rounded to the nearest value with 10 fraction bits (ties away from zero): half a unit in
+// the 10th fraction bit is added to the magnitude and the low 13 bits cleared (finite v
+// below the largest TF32-representable value; an overflow would carry into the exponent).
+__device__ __forceinline__ float tf32_rn(float v) {
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
+}
 
 // V consecutive 16-bit values (the low halves of x[]) as one store of 2V bytes.
 template <int V>
@@ -707,24 +713,31 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
         const int s = kb % STAGES;
         float4* src = reinterpret_cast<float4*>(smem + s * STAGE);
         float4* dst = reinterpret_cast<float4*>(lo_base + (kb & 1) * STAGE);
-        // kind::tf32 reads an FP32 operand by dropping its low 13 mantissa bits (checked by
-        // tests/test_gpu_tc.py::test_tf32_operand_rounding), so the staged value itself
-        // serves as hi and only lo = value - hi is written; for B_im also -value and -lo
-        // (truncation is symmetric, so the hardware reads -value as -hi)
+        // hi = value rounded to the nearest TF32 (written back in place), lo = value - hi
+        // (exact); for B_im also -hi and -lo. kind::tf32 reads an FP32 operand by dropping
+        // its low 13 mantissa bits (tests/test_gpu_tc.py::test_tf32_operand_rounding), so hi
+        // is read exactly and only lo is truncated -- by at most 2^-10 of |lo|, with the
+        // sign of lo, i.e. without a bias. (Using the staged value itself as hi would have
+        // the hardware truncate it: a bias toward zero in every product.)
         constexpr int NA = 2 * TILE_A / 16;  // float4s of A_re, A_im
 #pragma unroll 4
         for (int i = et; i < C3::TMA_BYTES / 16; i += 256) {
           const int f = i < NA ? i : i + TILE_B / 16;  // skip the -B_im slot
           const float4 v = src[f];
-          float4 l;
-          l.x = v.x - tf32_trunc(v.x);
-          l.y = v.y - tf32_trunc(v.y);
-          l.z = v.z - tf32_trunc(v.z);
-          l.w = v.w - tf32_trunc(v.w);
+          float4 h, l;
+          h.x = tf32_rn(v.x);
+          h.y = tf32_rn(v.y);
+          h.z = tf32_rn(v.z);
+          h.w = tf32_rn(v.w);
+          l.x = v.x - h.x;
+          l.y = v.y - h.y;
+          l.z = v.z - h.z;
+          l.w = v.w - h.w;
+          src[f] = h;
           dst[f] = l;
           if (f >= C3::OFF_BI / 16) {
             const int g = f - (C3::OFF_BI - C3::OFF_BNEG) / 16;
-            src[g] = make_float4(-v.x, -v.y, -v.z, -v.w);
+            src[g] = make_float4(-h.x, -h.y, -h.z, -h.w);
             dst[g] = make_float4(-l.x, -l.y, -l.z, -l.w);
           }
         }

@@ -134,9 +134,8 @@ def test_circuit_path_with_tc_steps(tn, prec, tol):
 def test_tf32_operand_rounding(tn):
     """How tcgen05 kind::tf32 reads an FP32 operand: with A = 1 + 3*2^-12 and B = 1,
     truncation to 10 mantissa bits gives 1, round-to-nearest 1 + 2^-10. The 3xTF32
-    kernel relies on truncation (it uses the staged FP32 value itself as hi and adds
-    lo = value - trunc(value)); if this ever read as round-to-nearest, its hi + lo would
-    no longer equal the value."""
+    kernel writes hi = RN_tf32(value) itself (read exactly) and lo = value - hi, which
+    the hardware truncates without a bias; the 3xTF32 product is exact here."""
     from tn_inputs.network import Network, Path
     ext = {0: 128, 1: 64, 2: 16}
     A = np.full((128, 16), 1.0 + 3.0 * 2.0**-12, dtype=np.complex128)
