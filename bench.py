@@ -55,7 +55,7 @@ DTYPE_NAME = {"fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16x3": "bf16
 # from the ncu launch-list capture of this same command (profiles/launches_rc40_*.md).
 # Only valid for the kernel build the capture was taken on: drop an entry when it changes.
 NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 41.709e9,
-                          ("rc40", "bf16x3", "contract_tc"): 52.31e9}
+                          ("rc40", "bf16x3", "contract_tc"): 53.84e9}
 # Full values of the CPU oracle stored by the scripts in tests/golden/ (they call only the
 # oracle): the 40-qubit sum over all slices, and the full values of the smaller workloads.
 GOLDEN = os.path.join(ROOT, "tests", "golden")
