@@ -1,22 +1,23 @@
 // Tensor-core path for the dense pairwise steps (sm_103a): planar complex GEMM
 //   C[b] = A[b] (m x k) . B[b] (n x k)^T      (complex, 4M real decomposition)
 // with both operands K-major, written through the separable row/column offset maps.
-//
-// One CTA computes a 128 x 128 output tile. Warp roles (192 threads):
-//   warp 0      : TMA producer -- A_re, A_im, B_re, B_im tiles (128 rows x BK fp32,
-//                 swizzled) into a ring of shared-memory stages, mbarrier tx-count signalled;
-//   warp 1      : allocates tensor memory and issues tcgen05.mma (kind::tf32) from one lane;
-//   warps 2..5  : (3xTF32 only) split each staged tile into hi = TF32-truncated value (in
-//                 place) and lo = value - hi (a double-buffered side buffer, so splitting
-//                 stage s+1 overlaps the MMAs of stage s); then the epilogue: tcgen05.ld of
-//                 the accumulators and the offset-mapped stores.
-// Accumulators in TMEM (fp32): D_rr = sum A_re B_re, D_ii = sum A_im B_im,
-// D_x = sum (A_re B_im + A_im B_re); Re C = D_rr - D_ii, Im C = D_x.
-// 3xTF32: a.b ~ ah.bh + al.bh + ah.bl (the al.bl term, ~2^-22 relative, is dropped).
-// TF32 form: BK = 32 (128-byte rows, 128-byte swizzle), 3 stages. 3xTF32 form: BK = 16
-// (64-byte rows, 64-byte swizzle), 4 stages + 2 lo buffers.
-// Every mbarrier wait is bounded by wall time; on expiry the CTA records an error code,
-// drains its copies, frees its tensor memory and returns.
+// Every kernel computes 128 x 128 output tiles with one elected thread issuing
+// tcgen05.mma from shared-memory descriptors, operands brought by TMA into a ring of
+// stages (mbarrier transaction counts), accumulators in tensor memory:
+//   contract_tc_kernel<1>          TF32 form: A_re, A_im, B_re, B_im fp32 tiles, 32-deep
+//                                  k-blocks, 3 stages, D_rr / D_ii / D_x accumulators
+//                                  (Re C = D_rr - D_ii, Im C = D_x); 192 threads;
+//   contract_tc3_kernel            3xTF32 form: eight warps split each staged tile into
+//                                  hi = RN_tf32(v) and lo = v - hi, hi.hi in 64-term chunks
+//                                  folded into round-to-nearest registers, cross terms in
+//                                  their own accumulator; 320 threads;
+//   contract_tcb_kernel            BF16x3 form: operands already split into BF16 hi/lo
+//                                  planes by their producers, kind::f16, 256-term chunks;
+//   contract_tcb_persistent_kernel BF16x3 for shallow steps (k <= 64): one CTA per SM over
+//                                  the tiles, stores of a tile overlapping the next tile.
+// The epilogues of the TF32 and BF16x3 kernels store each 32 x 32 block in address order
+// (store_block). Every mbarrier wait is bounded by wall time; on expiry the CTA records an
+// error code, drains its copies, frees its tensor memory and returns.
 #include <cstdint>
 
 #include <cuda.h>
