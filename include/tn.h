@@ -110,9 +110,12 @@ typedef struct tn_plan_s* tn_plan_t;
 
 /* Kernel class chosen for a step (Sec. IV-C cost model t = max(D_rw/B, FLOPs/F)). */
 typedef enum {
-  TN_CLASS_SIMT = 0,   /* tiled FP32 GEMM on the CUDA cores (any shape) */
+  TN_CLASS_SIMT = 0,   /* tiled FP32 GEMM on the CUDA cores (any shape; when its tiles
+                          cannot fill the GPU and k >= 2048, k is split across CTAs and
+                          the parts combined in order) */
   TN_CLASS_STREAM = 1, /* big x small: one pass over the big operand */
-  TN_CLASS_TC = 2,     /* tcgen05 tensor-core GEMM */
+  TN_CLASS_TC = 2,     /* tcgen05 tensor-core GEMM (rows >= 128, columns >= 16, k >= 8; a
+                          persistent variant for k <= 64 in the BF16X3 form) */
   TN_CLASS_SPLITK = 3  /* few outputs, long k: split-K partials in FP64, fixed-order sum */
 } tn_step_class;
 #define TN_N_CLASSES 4
