@@ -223,3 +223,103 @@ def test_report_cli(capsys):
     assert lines[0]["n_chains"] == 0 and lines[0]["speedup"] == 1.0
     assert lines[1]["n_chains"] >= 1 and lines[1]["schedule"]
     assert lines[1]["extra_speedup"] == pytest.approx(lines[1]["speedup"] / 4)
+
+
+def _einsum_pair(a, ma, b, mb, keep):
+    """Contract two labelled arrays over their shared labels (unless kept open)."""
+    letters = {x: chr(ord("a") + i) if i < 26 else chr(ord("A") + i - 26)
+               for i, x in enumerate(sorted(set(ma) | set(mb)))}
+    shared = [x for x in ma if x in mb and x not in keep]
+    mc = tuple(x for x in ma if x not in shared) + tuple(x for x in mb if x not in shared)
+    spec = "".join(letters[x] for x in ma) + "," + "".join(letters[x] for x in mb) + "->" + \
+        "".join(letters[x] for x in mc)
+    return np.einsum(spec, a, b), mc
+
+
+def _shard(arr, modes, split, dev, ext):
+    """Device `dev`'s part of a tensor split on the labels `split` (mixed radix, first label
+    most significant): those labels fixed, removed from the shard."""
+    vals, r = {}, dev
+    for x in reversed(split):
+        vals[x] = r % ext[x]
+        r //= ext[x]
+    idx = tuple(vals[x] if x in vals else slice(None) for x in modes)
+    return arr[idx], tuple(x for x in modes if x not in vals)
+
+
+def _assemble(shards, modes_shard, split, ext, full_modes):
+    """Inverse of _shard: the whole tensor (in full_modes order) from every device's part."""
+    shape = tuple(ext[x] for x in full_modes)
+    out = np.zeros(shape, dtype=shards[0].dtype)
+    for dev, s in enumerate(shards):
+        vals, r = {}, dev
+        for x in reversed(split):
+            vals[x] = r % ext[x]
+            r //= ext[x]
+        idx = tuple(vals[x] if x in vals else slice(None) for x in full_modes)
+        perm = [modes_shard.index(x) for x in full_modes if x not in vals]
+        out[idx] = np.transpose(s, perm)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("P", [4, 16])
+def test_schedule_executes_on_emulated_devices(seed, P):
+    """Run the planned schedule on P emulated devices with real data. A tensor made by a
+    chain step stays split -- P shards, one per assignment of its split labels -- while
+    its consumer is on the same chain; a chain step contracts each shard locally with the
+    other operand held whole; a redistribution reassembles and re-splits; a chain's last
+    output is gathered. The result must equal the oracle's: it would not if a split label
+    were ever contracted locally (each device would sum over its part only)."""
+    import oracle
+    tn = ensure_built()
+    net, path = caterpillar(seed)
+    rng = np.random.default_rng(1000 + seed)
+    net.tensors = [rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape) for t in net.tensors]
+    plan = tn.Plan(net, path, host_only=True)
+    _, steps = plan.distribute(P, **CFG)
+    ext, keep = dict(net.extent), set(net.open_modes)
+    T, S = len(net.tensors), len(path.pairs)
+    consumer = {}
+    for s_, (i, j) in enumerate(path.pairs):
+        consumer[i] = consumer[j] = s_
+    whole = {t: (np.asarray(net.tensors[t]), tuple(net.modes[t])) for t in range(T)}
+    split = {}  # tensor -> (shards, shard modes, split labels, full modes)
+    n_split_steps = 0
+    for s_, (i, j) in enumerate(path.pairs):
+        st, out = steps[s_], T + s_
+        carried = [t for t in (i, j) if t in split and steps[t - T]["chain"] == st["chain"] >= 0]
+        for t in (i, j):  # a split tensor whose chain ended before this step was gathered
+            if t in split and t not in carried:
+                sh, ms, sp, fm = split.pop(t)
+                whole[t] = (_assemble(sh, ms, sp, ext, fm), fm)
+        if carried:
+            assert len(carried) == 1 and st["state"] in ("keep", "redistribute", "gather")
+            tc = carried[0]
+            sh, ms, sp, fm = split.pop(tc)
+            b, mb = whole.pop(j if tc == i else i)
+            assert not set(sp) & set(mb), "a split label reached the other operand"
+            res = [_einsum_pair(x, ms, b, mb, keep) for x in sh]
+            cm = res[0][1]
+            full = _assemble([r[0] for r in res], cm, sp, ext, tuple(sp) + cm)
+            cfull = tuple(sp) + cm
+            if st["state"] == "keep":
+                assert sorted(st["dist_modes"]) == sorted(sp)
+            n_split_steps += 1
+        else:
+            assert st["state"] in ("none", "activate")
+            a, ma = whole.pop(i)
+            b, mb = whole.pop(j)
+            full, cfull = _einsum_pair(a, ma, b, mb, keep)
+        stays_split = st["chain"] >= 0 and out in consumer and steps[consumer[out]]["chain"] == st["chain"]
+        if stays_split:
+            D = list(st["dist_modes"])
+            split[out] = ([_shard(full, cfull, D, d, ext)[0] for d in range(P)], _shard(full, cfull, D, 0, ext)[1],
+                          D, cfull)
+        else:
+            whole[out] = (full, cfull)
+    assert n_split_steps > 0
+    got, gm = whole[T + S - 1]
+    got = np.transpose(got, [gm.index(x) for x in net.open_modes])
+    want = oracle.contract(net, path)
+    assert np.allclose(got, want, rtol=1e-10, atol=1e-12 * np.abs(want).max())
