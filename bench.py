@@ -163,6 +163,34 @@ def oracle_sample(w, budget_s, slice_id=0):
     return flops, time.perf_counter() - t0, done
 
 
+def path_roofline(plan, prec, semiring, peaks, ms_per_step, cplx=True):
+    """The path's roofline time: over the steps of one contraction (all slices), the sum of
+    t_roof = max(bytes / B, flops / F) -- Eq. 6 of Sec. IV-C with this GPU's measured
+    rates: B the HBM copy rate, F the peak of the step's kernel class (the form's tensor
+    peak for tensor-core steps, the FP32 or max-plus ALU peak otherwise) -- against the
+    measured time of the contraction. Bytes count each operand once per launch that reads
+    it (slice-invariant operands of sliced steps once per pass)."""
+    from paper_2606_01852_gb300 import TN_CLASS_TC
+    info = plan.info()
+    n_sl, n_pass = info["n_slices"], info["n_passes"]
+    e, fm = (8.0, 8.0) if cplx else (4.0, 2.0)
+    hbm = peaks["hbm_gbs"] * 1e9
+    bf = peaks["bf16_tflops_sustained"] * 1e12
+    tc_peak = {1: bf * NOMINAL_TF32_PER_BF16, 2: bf * NOMINAL_TF32_PER_BF16 / 3.0, 3: bf / 3.0}.get(prec)
+    alu = SM_COUNT * FP32_LANES * (1 if semiring == "maxplus" else 2) * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    total = 0.0
+    for s in range(info["n_steps"]):
+        st = plan.step(s)
+        copies = n_sl if st["batched"] else 1
+        reads = lambda t: n_sl if plan.tensor(t)["batched"] else (n_pass if st["batched"] else 1)
+        m, n, k = st["m"], st["n"], st["k"]
+        flops = fm * m * n * k * copies
+        nbytes = e * (m * k * reads(st["a_id"]) + n * k * reads(st["b_id"]) + m * n * copies)
+        peak = tc_peak if st["cls"] == TN_CLASS_TC else alu
+        total += max(nbytes / hbm, flops / peak)
+    return {"sum_t_roof_ms": total * 1e3, "ms_per_step": ms_per_step, "frac": total * 1e3 / ms_per_step}
+
+
 def replica_throughput(ms_local, units_local, dist=None, device="cpu"):
     """Whole-job throughput of independent replicas (one per rank, no data-path
     collective): the units all ranks processed over the slowest rank's time. Returns
@@ -305,6 +333,7 @@ def run_ours(args):
     roof["ms_per_launch"] = per_launch_ms
     roof["share_of_step"] = prof["ms"][cls] / sum(prof["ms"])
     roof["peak_source"] = peaks["_source"]
+    path_roof = path_roofline(plan, prec, semiring, peaks, ms_max, cplx)
 
     # end to end through the public C ABI with host buffers
     host_in = [np.ascontiguousarray(np.asarray(t, dtype=np.complex64 if cplx else np.float32))
@@ -337,6 +366,7 @@ def run_ours(args):
                    {"shape": list(result.shape), "sum_abs2": float(np.sum(np.abs(result) ** 2)),
                     "first": [float(result.flat[0].real), float(result.flat[0].imag)]}),
         "roofline": roof,
+        "path_roofline": path_roof,
         "per_class": {names[c]: {"launches": prof["launches"][c], "ms": prof["ms"][c],
                                  "flops": prof["flops"][c], "bytes": prof["bytes"][c]} for c in range(4)},
         "top_steps": top_steps,
