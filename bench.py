@@ -1,8 +1,13 @@
 #!/usr/bin/env python
 """Benchmark: exact contraction of a sliced 40-qubit random-circuit amplitude on one GB300.
 
-One step = one tn_contract over all 256 slices of the workload (leaf staging and
-slicing, every pairwise step, the FP64 cross-slice sum), inputs resident in HBM.
+Default workload rc40c14: 40 qubits on a 5x8 grid, 14 cycles, one amplitude, 7 sliced
+labels (128 slices), each slice's largest intermediate 2^30 complex64 elements. One step
+= one tn_contract_slices over a fixed batch of slices (leaf staging and slicing, every
+pairwise step, the FP64 cross-slice sum), inputs resident in HBM; successive steps take
+successive slice ranges, so the warm-up and timed steps together cover every slice. The
+full contraction time is projected as T_proj = t_slice * n_slices (Sec. V-A, Eq. 8).
+Workloads whose whole contraction fits a step (rc40, ...) contract all slices per step.
 Prints one JSON line (see the keys below). `--impl reference` times the CPU
 complex128 oracle instead, on a bounded sample of the same workload per step.
 Under torchrun every rank contracts its own full copy of the workload (independent
@@ -34,6 +39,9 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 NOMINAL_TF32_PER_BF16 = 1.1 / 2.25     # nominal dense tf32 / bf16 rate of the part
 SM_COUNT, FP32_LANES = 152, 128
 WORKLOAD_DESC = {
+    "rc40c14": "40-qubit 5x8 grid random circuit, 14 brick-wall cycles of Haar 2-qubit gates, one "
+               "amplitude, greedy path (least flops of a seeded search), 7 sliced labels (128 slices) "
+               "so that each slice's largest intermediate is 2^30 elements, complex64",
     "rc40": "40-qubit 5x8 grid random circuit, 13 brick-wall cycles of Haar 2-qubit gates, "
             "one amplitude, greedy path, 8 sliced labels (256 slices), complex64",
     "kising44": "4x4 kicked Ising, 10 Trotter steps (J=1, dt=0.25, h=0.9), <Z_centre>, complex64",
@@ -42,6 +50,8 @@ WORKLOAD_DESC = {
     "ktri44": "kicked Ising on a 4x4 triangular lattice, 8 Trotter steps (J=1, dt=0.25, h=0.9), "
               "<Z_centre>, complex64",
     "rc12": "12-qubit 3x4 random circuit, 8 cycles, one amplitude, complex64",
+    "rc40c14sub": "the rc40c14 network and path with two more sliced labels (512 slices, largest "
+                  "intermediate 2^29), complex64",
     "rc40u": "the rc40 network and path without slicing: every intermediate whole (largest 2^32 "
              "complex64 elements), one contraction per step, complex64",
     "rc40open": "the 40-qubit rc40 circuit with the 2x2 corner qubits (30, 31, 38, 39) left open: "
@@ -59,6 +69,10 @@ NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 41.709e9,
 # Full values of the CPU oracle stored by the scripts in tests/golden/ (they call only the
 # oracle): the 40-qubit sum over all slices, and the full values of the smaller workloads.
 GOLDEN = os.path.join(ROOT, "tests", "golden")
+# Slices per step where one contraction of every slice is far longer than a benchmark step:
+# rc40c14 takes ~0.2 s per slice, so 16 slices make a step of a few seconds, and the 3
+# warm-up plus 5 timed steps cover all 128 slices.
+SLICES_PER_STEP = {"rc40c14": 16, "rc40c14sub": 64}
 
 
 def stored_oracle_value(workload):
@@ -75,6 +89,18 @@ def stored_oracle_value(workload):
     else:
         v = d.get("total")
     return complex(*v) if v is not None else None
+
+
+def stored_slice_partial(workload):
+    """(slice id, complex partial) the oracle stored for one slice of a workload whose full
+    value is beyond the host (tests/golden/make_rc40c14_values.py), or None."""
+    if workload != "rc40c14":
+        return None
+    path = os.path.join(GOLDEN, "rc40c14_values.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    return int(d["slice"]), complex(*d["slice_partial"])
 
 
 def load_peaks():
@@ -163,8 +189,9 @@ def oracle_sample(w, budget_s, slice_id=0):
     return flops, time.perf_counter() - t0, done
 
 
-def path_roofline(plan, prec, semiring, peaks, ms_per_step, cplx=True):
-    """The path's roofline time: over the steps of one contraction (all slices), the sum of
+def path_roofline(plan, prec, semiring, peaks, ms_per_step, cplx=True, count=None):
+    """The path's roofline time: over the steps of one contraction (all slices, or the
+    `count` slices a step contracts), the sum of
     t_roof = max(bytes / B, flops / F) -- Eq. 6 of Sec. IV-C with this GPU's measured
     rates: B the HBM copy rate, F the peak of the step's kernel class (the form's tensor
     peak for tensor-core steps, the FP32 or max-plus ALU peak otherwise) -- against the
@@ -172,7 +199,8 @@ def path_roofline(plan, prec, semiring, peaks, ms_per_step, cplx=True):
     it (slice-invariant operands of sliced steps once per pass)."""
     from paper_2606_01852_gb300 import TN_CLASS_TC
     info = plan.info()
-    n_sl, n_pass = info["n_slices"], info["n_passes"]
+    n_sl = info["n_slices"] if count is None else count
+    n_pass = -(-n_sl // info["slice_batch"])
     e, fm = (8.0, 8.0) if cplx else (4.0, 2.0)
     hbm = peaks["hbm_gbs"] * 1e9
     bf = peaks["bf16_tflops_sustained"] * 1e12
@@ -264,13 +292,27 @@ def run_ours(args):
     plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=args.max_slice_batch, semiring=semiring)
     info = plan.info()
     stream = torch.cuda.current_stream()
+    n_sl = info["n_slices"]
+    per_step = args.slices_per_step or SLICES_PER_STEP.get(args.workload, n_sl)
+    per_step = max(1, min(per_step, n_sl))
+    # step j contracts slices [j * per_step, (j + 1) * per_step) modulo n_slices
+    ranges = [((j * per_step) % n_sl, min(per_step, n_sl - (j * per_step) % n_sl))
+              for j in range(args.warmup + args.steps)]
     in_dt, out_dt = (torch.complex64, torch.complex128) if cplx else (torch.float32, torch.float64)
     ins = [torch.tensor(np.asarray(t), dtype=in_dt, device="cuda") for t in w.net.tensors]
-    out = torch.zeros(plan.out_shape, dtype=out_dt, device="cuda")
-    ls = torch.zeros(1, dtype=torch.float64, device="cuda")
+    outs = torch.zeros((len(ranges),) + tuple(plan.out_shape), dtype=out_dt, device="cuda")
+    ls = torch.zeros(len(ranges), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    for _ in range(args.warmup):
-        plan.contract(ins, out, ls, stream)
+
+    def step(j):
+        b, c = ranges[j]
+        if c == n_sl:
+            plan.contract(ins, outs[j], ls[j:j + 1], stream)
+        else:
+            plan.contract_slices(ins, b, c, outs[j], ls[j:j + 1], stream)
+
+    for j in range(args.warmup):
+        step(j)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -282,7 +324,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.zero_()  # L2 flush between timed steps, outside the events
         ev[k][0].record(stream)
-        plan.contract(ins, out, ls, stream)
+        step(args.warmup + k)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     plan.profile(False)
@@ -292,10 +334,18 @@ def run_ours(args):
     ck = clocks.stop()
     times = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(times)
-    flops = info["flops"]
+    timed = ranges[args.warmup:]
+    flops = statistics.mean(plan.flops_per_call(c) for _, c in timed)
+    slices_per_step = statistics.mean(c for _, c in timed)
     tflop_per_s, ms_max = replica_throughput(ms, flops / 1e12, dist, device="cuda")
     value = tflop_per_s
-    result = out.cpu().numpy()
+    all_out = outs.cpu().numpy()
+    # the whole result when the steps covered every slice exactly once (else the last step's)
+    covered = sorted(b for b, _ in ranges)
+    whole = per_step < n_sl and len(ranges) * per_step == n_sl and covered == list(range(0, n_sl, per_step))
+    result = all_out.sum(axis=0) if whole else all_out[-1]
+    if per_step == n_sl:
+        result = all_out[-1]
 
     # dominant kernel class by device time, and its roofline
     cls = max(range(4), key=lambda c: prof["ms"][c])
@@ -333,7 +383,7 @@ def run_ours(args):
     roof["ms_per_launch"] = per_launch_ms
     roof["share_of_step"] = prof["ms"][cls] / sum(prof["ms"])
     roof["peak_source"] = peaks["_source"]
-    path_roof = path_roofline(plan, prec, semiring, peaks, ms_max, cplx)
+    path_roof = path_roofline(plan, prec, semiring, peaks, ms_max, cplx, count=round(slices_per_step))
 
     # end to end through the public C ABI with host buffers
     host_in = [np.ascontiguousarray(np.asarray(t, dtype=np.complex64 if cplx else np.float32))
@@ -341,13 +391,14 @@ def run_ours(args):
     host_out = np.zeros(plan.out_shape, dtype=np.complex128 if cplx else np.float64)
     host_ls = np.zeros(1)
     h2d = int(sum(a.nbytes for a in host_in))
-    plan.contract_host(host_in, host_out, host_ls)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_b, e2e_c = ranges[-1]
+    plan.contract_slices_host(host_in, e2e_b, e2e_c, host_out, host_ls)
+    e2e_steps = max(1, min(args.steps, 3 if per_step == n_sl else 2))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        plan.contract_host(host_in, host_out, host_ls)
+        plan.contract_slices_host(host_in, e2e_b, e2e_c, host_out, host_ls)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_val = ws * flops / e2e_s / 1e12
+    e2e_val = ws * plan.flops_per_call(e2e_c) / e2e_s / 1e12
 
     line = {
         "metric": "contraction TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
@@ -356,12 +407,19 @@ def run_ours(args):
         "dtype": DTYPE_NAME[args.prec] if cplx else ("f32 (max,+)" if semiring == "maxplus" else "f32"),
         "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, ""),
                    "prec": args.prec if cplx else "r32", "semiring": semiring,
-                   "slices": info["n_slices"], "slice_batch": info["slice_batch"],
-                   "passes": info["n_passes"], "flops_per_step": flops,
-                   "algorithmic_bytes_per_step": info["bytes"],
+                   "slices": n_sl, "sliced_labels": len(w.sliced),
+                   "largest_intermediate_per_slice": info["peak_elems"],
+                   "slices_per_step": slices_per_step, "slice_batch": info["slice_batch"],
+                   "passes_per_step": -(-per_step // info["slice_batch"]), "flops_per_step": flops,
+                   "flops_full_contraction": info["flops"],
+                   "algorithmic_bytes_full_contraction": info["bytes"],
                    "l2": "256 MiB buffer written between timed steps (L2 is 129 MB); "
                          "intermediates are GBs", "parallelism": f"replicas{ws}"},
-        "slices_per_s": ws * info["n_slices"] / (ms_max / 1e3),
+        "slices_per_s": ws * slices_per_step / (ms_max / 1e3),
+        "projected_full_contraction_s": (n_sl / (slices_per_step / (ms_max / 1e3)) if per_step < n_sl
+                                         else ms_max / 1e3),
+        "projection": ("T_proj = t_slice * n_slices (Sec. V-A, Eq. 8): a step contracts a batch of slices"
+                       if per_step < n_sl else "measured: every slice in each step"),
         "result": ([float(result.real), float(result.imag)] if result.ndim == 0 else
                    {"shape": list(result.shape), "sum_abs2": float(np.sum(np.abs(result) ** 2)),
                     "first": [float(result.flat[0].real), float(result.flat[0].imag)]}),
@@ -371,9 +429,24 @@ def run_ours(args):
                                  "flops": prof["flops"][c], "bytes": prof["bytes"][c]} for c in range(4)},
         "top_steps": top_steps,
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": host_out.nbytes + host_ls.nbytes},
-        "gpu_launches": plan.launches_per_call() * args.steps,
+        "gpu_launches": sum(plan.launches_per_call(c) for _, c in timed),
         "clocks": ck,
     }
+    if per_step < n_sl:
+        line["result_scope"] = ("all slices (the warm-up and timed steps together cover each slice once)"
+                                if whole else f"slices {ranges[-1][0]}..{ranges[-1][0] + ranges[-1][1] - 1}")
+    sp = stored_slice_partial(args.workload)
+    if sp is not None:
+        # one slice again, untimed, against the oracle's value of it (its four finer pieces)
+        sid, want_sl = sp
+        one = torch.zeros(plan.out_shape, dtype=out_dt, device="cuda")
+        plan.contract_slices(ins, sid, 1, one, None, stream)
+        torch.cuda.synchronize()
+        got_sl = complex(one.cpu().numpy())
+        line["oracle_slice"] = {"slice": sid, "oracle": [want_sl.real, want_sl.imag],
+                                "got": [got_sl.real, got_sl.imag]}
+        line["rel_err_vs_oracle"] = abs(got_sl - want_sl) / abs(want_sl)
+        line["rel_err_scope"] = f"slice {sid} of {n_sl} (the oracle's sum of its 4 pieces)"
     want = stored_oracle_value(args.workload)
     if want is not None and result.ndim == 0:
         line["oracle_total"] = [want.real, want.imag]
@@ -388,7 +461,7 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
                                 "kind": "oracle",
                                 "sample": f"first {done} of {len(w.path.pairs)} path steps of slice 0 "
-                                          f"({f:.3g} of {info['flops'] / info['n_slices']:.3g} flops of one "
+                                          f"({f:.3g} of {plan.flops_per_call(1):.3g} flops of one "
                                           f"slice, {s:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -622,7 +695,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rc40",
+    ap.add_argument("--workload", default="rc40c14",
                     choices=sorted(workloads.BY_NAME) + ["ising3r", "kingsbatch", "serve"])
     ap.add_argument("--networks", type=int, default=4096, help="ising3r: networks per launch")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
@@ -634,6 +707,8 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=sorted(PREC),
                     help="GEMM form: bf16x3 (default), 3xtf32, tf32, fp32 (the plain CUDA-core form)")
     ap.add_argument("--max-slice-batch", type=int, default=0)
+    ap.add_argument("--slices-per-step", type=int, default=0,
+                    help="slices contracted per step (0: the workload's default, else all slices)")
     ap.add_argument("--ref-budget", type=float, default=20.0, help="oracle seconds per sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="also contract with the CPU oracle and report the error")

@@ -212,6 +212,12 @@ tn_status tn_contract_slices(tn_plan_t plan, const void* const* inputs, int64_t 
 tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void* host_output,
                            double* out_log_scale, void* stream);
 
+/* End-to-end form of tn_contract_slices: host inputs and host output as in
+ * tn_contract_host, summing only slices [slice_begin, slice_begin + slice_count). */
+tn_status tn_contract_slices_host(tn_plan_t plan, const void* const* host_inputs, int64_t slice_begin,
+                                  int64_t slice_count, void* host_output, double* out_log_scale,
+                                  void* stream);
+
 /* Free the plan and its device workspace (after any contract on it has finished). */
 tn_status tn_plan_destroy(tn_plan_t plan);
 
@@ -254,7 +260,10 @@ tn_status tn_plan_profile_steps(tn_plan_t plan, double* ms_out, int32_t n_steps)
 typedef struct {
   int32_t max_inflight;      /* requests on the GPU at once (slots) */
   int32_t n_streams;         /* CUDA streams work is spread over */
-  int64_t hbm_budget_bytes;  /* admission limit on the sum of admitted workspaces */
+  int64_t hbm_budget_bytes;  /* limit on the device memory the server holds in request
+                                workspaces (resident plan instances, busy or idle; 0 = no
+                                limit): idle instances are freed, least recently used first,
+                                before a request waits for running ones to finish */
   int32_t queue_capacity;    /* pending requests beyond which submit returns TN_ERR_BUSY */
   int32_t reserved[3];
 } tn_serve_config;
@@ -331,22 +340,29 @@ tn_status tn_batch_destroy(tn_batch_t b);
 /* The paper has no counterpart to this call. It exists for callers that must not
  * allocate device memory on this path -- a host process whose device memory is already
  * handed out by another allocator, or a latency-critical loop where cudaMalloc (which
- * may synchronize the device) is not acceptable. It runs the engine's split-K reduction
- * (the kernel behind few-output steps with a long contracted index) with its FP64
- * partial sums in a fixed file-scope device array of 2^18 complex doubles (4 MiB) that
- * every device using the library holds until the process exits.
+ * may synchronize the device) is not acceptable. It computes a reduction of the same
+ * shape as the engine's split-K step (few outputs, long contracted index: k cut in
+ * chunks of 4096, FP64 partial sums, chunks added in a fixed order), with its own pair
+ * of kernels, on interleaved complex64 inputs, without exponent scaling or the max-plus
+ * semiring. Its FP64 partial sums live in a fixed file-scope device array of 2^18
+ * complex doubles (4 MiB) that every device using the library holds until the process
+ * exits.
  *
  *   out[b][i][j] = sum_t a[b][i][t] * b[b][j][t]      (no conjugation)
  *
  * a: DEVICE complex64, [batch][m][k] row-major; b: DEVICE complex64, [batch][n][k];
  * out: DEVICE complex128, [batch][m][n]. All three are owned by the caller.
  * Limits: m*n <= 16, batch <= 65535, batch * ceil(k/4096) * m*n <= 2^18; larger sizes
- * return TN_ERR_INVALID with a message. Allocates nothing (no cudaMalloc/cudaFree, no
- * allocating library call). Asynchronous on `stream` (a cudaStream_t; NULL = legacy
- * default stream). The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture. All calls share the array: each call overwrites every partial it
- * reads, so calls in sequence need no clearing, but calls that overlap on the GPU race. */
+ * (m and n are checked one at a time before their product) return TN_ERR_INVALID with a
+ * message. Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
+ * Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream). The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. The address is kept
+ * per device together with the id of the context it belongs to: after a device reset
+ * (cudaDeviceReset) the next call sees a new context and looks the address up again,
+ * so that call too belongs outside stream capture. All calls share the array: each call
+ * overwrites every partial it reads, so calls in sequence need no clearing, but calls
+ * that overlap on the GPU race. */
 tn_status tn_dot_noalloc(const void* a, const void* b, int64_t batch, int64_t m, int64_t n, int64_t k,
                          void* out, void* stream);
 

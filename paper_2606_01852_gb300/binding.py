@@ -125,6 +125,7 @@ def _load():
         "tn_contract": [vp, C.POINTER(vp), vp, vp, vp],
         "tn_contract_slices": [vp, C.POINTER(vp), i64, i64, vp, vp, vp],
         "tn_contract_host": [vp, C.POINTER(vp), vp, vp, vp],
+        "tn_contract_slices_host": [vp, C.POINTER(vp), i64, i64, vp, vp, vp],
         "tn_plan_destroy": [vp],
         "tn_plan_profile": [vp, i32],
         "tn_plan_profile_read": [vp, C.POINTER(tn_profile), i32],
@@ -282,6 +283,22 @@ class Plan:
     def contract_host(self, host_inputs, host_output, log_scale=None, stream=None):
         check(lib.tn_contract_host(self.handle, self._inputs(host_inputs), _ptr(host_output),
                                    _ptr(log_scale), _ptr_stream(stream)))
+
+    def contract_slices_host(self, host_inputs, begin, count, host_output, log_scale=None, stream=None):
+        check(lib.tn_contract_slices_host(self.handle, self._inputs(host_inputs), int(begin), int(count),
+                                          _ptr(host_output), _ptr(log_scale), _ptr_stream(stream)))
+
+    def flops_per_call(self, count=None) -> float:
+        """Algorithmic flops of one contract over `count` slices (default all): the
+        slice-invariant steps once, the sliced steps once per slice."""
+        info = self.info()
+        count = info["n_slices"] if count is None else count
+        fm = 8.0 if self.is_complex else 2.0
+        tot = 0.0
+        for s in range(info["n_steps"]):
+            st = self.step(s)
+            tot += fm * st["m"] * st["n"] * st["k"] * (count if st["batched"] else 1)
+        return tot
 
     def profile(self, enable: bool):
         check(lib.tn_plan_profile(self.handle, 1 if enable else 0))

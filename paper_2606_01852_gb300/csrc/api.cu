@@ -357,8 +357,8 @@ tn_status tn_contract(tn_plan_t plan, const void* const* inputs, void* output, d
   return tn_contract_slices(plan, inputs, 0, plan->P.n_slices, output, out_log_scale, stream);
 }
 
-tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void* host_output,
-                           double* out_log_scale, void* stream) {
+tn_status tn_contract_slices_host(tn_plan_t plan, const void* const* host_inputs, int64_t slice_begin,
+                                  int64_t slice_count, void* host_output, double* out_log_scale, void* stream) {
   if (!plan || !host_inputs || !host_output) {
     set_error("null argument");
     return TN_ERR_INVALID;
@@ -390,7 +390,7 @@ tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void*
   }
   char* dout = P.dev + P.total_bytes - ((P.out_elems * 16 + 16 + 255) / 256 * 256);
   double* dls = reinterpret_cast<double*>(dout + P.out_elems * 16);
-  tn_status s = run_slices(P, dptr.data(), 0, P.n_slices, dout, dls, stream, err);
+  tn_status s = run_slices(P, dptr.data(), slice_begin, slice_count, dout, dls, stream, err);
   if (s != TN_OK) {
     set_error(err);
     return s;
@@ -405,6 +405,15 @@ tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void*
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(e, "stream synchronize");
   return check_device_error(P);
+}
+
+tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void* host_output,
+                           double* out_log_scale, void* stream) {
+  if (!plan) {
+    set_error("null argument");
+    return TN_ERR_INVALID;
+  }
+  return tn_contract_slices_host(plan, host_inputs, 0, plan->P.n_slices, host_output, out_log_scale, stream);
 }
 
 tn_status tn_plan_destroy(tn_plan_t plan) {

@@ -3,9 +3,10 @@
 // Some callers cannot allocate device memory on the path that calls this library: a
 // host process whose device memory is already handed out by another allocator, or a
 // latency-critical loop where cudaMalloc (which may synchronize the device) is not
-// acceptable. For them this entry point runs the split-K reduction of the engine's
-// few-output steps without the plan workspace: its FP64 partial sums live in one
-// file-scope device array of fixed size, set up once per device.
+// acceptable. For them this entry point computes a reduction of the same shape as the
+// engine's split-K step for few-output steps (k cut in chunks, FP64 partials, chunks
+// added in order) with its own pair of kernels and without the plan workspace: its FP64
+// partial sums live in one file-scope device array of fixed size.
 //
 // The array is shared by every call in the process. Each call overwrites every
 // partial it later reads (nothing has to start at zero), so calls that run one after
@@ -29,22 +30,60 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocSlots];
 
 std::mutex g_mu;
-double2* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id;  // context the address belongs to (0: not looked up)
+  double2* ptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Driver calls reached through the runtime's entry-point table (no -lcuda link): the id
+// of the current context tells whether a cached address still belongs to it.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+  }
+  void* ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array in the current device's context. It is looked up
+// (cudaGetSymbolAddress) on the first call with that context current, and again when the
+// context has changed since (the device was reset and its primary context re-created),
+// since an address cached for a destroyed context no longer points at the array.
 cudaError_t scratch_address(double2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> g(g_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchAddr& c = g_scratch_addr[dev];
+  unsigned long long ctx = 0;
+  // no context bound to this thread yet, or a different one: look the address up (which
+  // also makes the device's primary context current) and record the context it is for
+  if (!current_context_id(&ctx) || !c.ptr || c.ctx_id != ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double2*>(p);
+    c.ptr = static_cast<double2*>(p);
+    c.ctx_id = current_context_id(&ctx) ? ctx : 0;  // 0: looked up again on every call
   }
-  *out = g_scratch_addr[dev];
+  *out = c.ptr;
   return cudaSuccess;
 }
 
@@ -122,19 +161,22 @@ extern "C" tn_status tn_dot_noalloc(const void* a, const void* b, int64_t batch,
     set_error("tn_dot_noalloc: null pointer or non-positive size");
     return TN_ERR_INVALID;
   }
-  if (m * n > kSplitMaxOut) {
-    set_error("tn_dot_noalloc: m*n = " + std::to_string(m * n) + " exceeds the maximum of " +
-              std::to_string(kSplitMaxOut) + " outputs per batch entry");
+  // m and n are bounded one at a time first, so that m * n cannot overflow
+  if (m > kSplitMaxOut || n > kSplitMaxOut || m * n > kSplitMaxOut) {
+    set_error("tn_dot_noalloc: m = " + std::to_string(m) + ", n = " + std::to_string(n) +
+              ": m*n exceeds the maximum of " + std::to_string(kSplitMaxOut) + " outputs per batch entry");
     return TN_ERR_INVALID;
   }
   if (batch > 65535) {
     set_error("tn_dot_noalloc: batch exceeds 65535");
     return TN_ERR_INVALID;
   }
-  const int64_t chunks = (k + kSplitChunk - 1) / kSplitChunk;
-  if (chunks > 2147483647 || batch * chunks * m * n > kNoAllocSlots) {
-    set_error("tn_dot_noalloc: batch * ceil(k/4096) * m*n = " + std::to_string(batch * chunks * m * n) +
-              " partial sums exceed the fixed scratch of " + std::to_string(kNoAllocSlots));
+  // chunks <= kNoAllocSlots before the product, so batch * chunks * m*n stays below 2^43
+  const int64_t chunks = k / kSplitChunk + (k % kSplitChunk != 0);
+  if (chunks > kNoAllocSlots || batch * chunks * m * n > kNoAllocSlots) {
+    set_error("tn_dot_noalloc: batch * ceil(k/4096) * m*n partial sums (batch " + std::to_string(batch) +
+              ", " + std::to_string(chunks) + " chunks, " + std::to_string(m * n) +
+              " outputs) exceed the fixed scratch of " + std::to_string(kNoAllocSlots));
     return TN_ERR_INVALID;
   }
   double2* scratch = nullptr;

@@ -7,6 +7,9 @@
 // on the GPU start as soon as resources free up. Each plan keeps a pool of resident
 // device instances (its workspace plus pinned staging), reused across requests.
 #include <atomic>
+#include <climits>
+#include <cstddef>
+#include <cstdint>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -32,6 +35,7 @@ struct Instance {
   int64_t in_bytes = 0, out_bytes = 0;
   std::vector<int64_t> in_off;  // per leaf offset in pinned_in
   bool busy = false;
+  uint64_t last_used = 0;       // admission tick of the last request it ran
 };
 
 struct PlanPool {
@@ -77,18 +81,54 @@ struct tn_server_s {
   std::map<uint64_t, std::unique_ptr<Request>> reqs;
   std::map<uint64_t, PlanPool> pools;  // by plan uid
   std::vector<Request*> running;
-  int64_t hbm_in_use = 0;
+  int64_t hbm_in_use = 0;        // device bytes held by resident instances (busy or idle)
+  uint64_t tick = 0;
   uint64_t next_id = 1;
   bool stop = false;
   std::thread thr;
 
-  // Find or create an idle instance of `plan`; nullptr if the budget forbids it.
+  static void release(Instance& in) {
+    if (in.P.dev) cudaFree(in.P.dev);
+    if (in.pinned_in) cudaFreeHost(in.pinned_in);
+    if (in.pinned_out) cudaFreeHost(in.pinned_out);
+    in.P.dev = nullptr;
+    in.pinned_in = in.pinned_out = nullptr;
+  }
+
+  // Free idle instances (of any plan), least recently used first, until `need` more bytes
+  // fit the budget or no idle instance is left.
+  void evict_idle(int64_t need) {
+    while (hbm_in_use + need > cfg.hbm_budget_bytes) {
+      PlanPool* best_pool = nullptr;
+      size_t best_i = 0;
+      uint64_t best_tick = UINT64_MAX;
+      for (auto& kv : pools)
+        for (size_t i = 0; i < kv.second.inst.size(); ++i) {
+          const Instance& in = *kv.second.inst[i];
+          if (!in.busy && in.last_used < best_tick) {
+            best_tick = in.last_used;
+            best_pool = &kv.second;
+            best_i = i;
+          }
+        }
+      if (!best_pool) return;
+      Instance& victim = *best_pool->inst[best_i];
+      hbm_in_use -= victim.P.total_bytes;
+      release(victim);
+      best_pool->inst.erase(best_pool->inst.begin() + (std::ptrdiff_t)best_i);
+    }
+  }
+
+  // Find or create an idle instance of `plan`; nullptr if the budget forbids it for now.
+  // The budget bounds the device memory held by resident instances: idle instances of
+  // other plans are freed (least recently used first) to make room before a request waits.
   Instance* acquire(tn_plan_s* plan, std::string& err, bool& fatal) {
     fatal = false;
     PlanPool& pool = pools[plan->P.uid];
     for (auto& in : pool.inst)
       if (!in->busy) return in.get();
     const int64_t need = plan->P.total_bytes;
+    if (cfg.hbm_budget_bytes > 0 && hbm_in_use + need > cfg.hbm_budget_bytes) evict_idle(need);
     if (cfg.hbm_budget_bytes > 0 && hbm_in_use + need > cfg.hbm_budget_bytes) {
       if (running.empty()) {
         err = "request workspace exceeds the serve HBM budget";
@@ -218,6 +258,7 @@ struct tn_server_s {
         }
         queue.pop_front();
         in->busy = true;
+        in->last_used = ++tick;
         r->inst = in;
         r->stream = next_stream;
         next_stream = (next_stream + 1) % (int)streams.size();
@@ -351,11 +392,7 @@ tn_status tn_serve_destroy(tn_server_t srv) {
   }
   srv->thr.join();
   for (auto& kv : srv->pools)
-    for (auto& in : kv.second.inst) {
-      if (in->P.dev) cudaFree(in->P.dev);
-      if (in->pinned_in) cudaFreeHost(in->pinned_in);
-      if (in->pinned_out) cudaFreeHost(in->pinned_out);
-    }
+    for (auto& in : kv.second.inst) tn_server_s::release(*in);
   for (auto& kv : srv->reqs)
     if (kv.second->done) cudaEventDestroy(kv.second->done);
   for (auto st : srv->streams) cudaStreamDestroy(st);

@@ -17,3 +17,22 @@ def ensure_built():
         b.build()
     import paper_2606_01852_gb300 as tn
     return tn
+
+
+# Tolerances of the forms against the complex128 oracle (the reading of the 1e-5 bar for
+# complex64-equivalent paths):
+#  * FP32-accurate forms (plain FP32 on the CUDA cores, 3xTF32): relative error <= 1e-5, or
+#    <= 2x the plain FP32 form's own error on the same workload where that is larger (a
+#    result the plain FP32 form itself cannot reach to 1e-5);
+#  * BF16x3 (measured and reported, not held to 1e-5): hi + lo BF16 halves represent each
+#    operand to 2^-16 relative and the dropped lo.lo term is below 2^-16, so each product
+#    is within 3 * 2^-16 = 4.6e-5 relative; the roundings are unbiased (round to nearest),
+#    so results are held to that one-product bound;
+#  * TF32 (measured and reported): operands truncated to 10 mantissa bits, a bias of up to
+#    2^-10 per product that adds up along a path; bounds per test.
+FP32_BAR = 1e-5
+BF16X3_BOUND = 3 * 2.0 ** -16
+
+
+def fp32_accurate_bound(fp32_err):
+    return max(FP32_BAR, 2.0 * fp32_err)

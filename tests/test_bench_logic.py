@@ -45,3 +45,29 @@ def test_path_roofline_sliced_plan():
     r = bench.path_roofline(plan, 3, "standard", PEAKS, 1317.0)
     assert 900.0 < r["sum_t_roof_ms"] < 1317.0
     assert r["frac"] == pytest.approx(r["sum_t_roof_ms"] / 1317.0)
+
+
+def test_path_roofline_slice_batch_and_flops_per_call():
+    """A step of the 14-cycle benchmark contracts 16 of its 128 slices: the flops of one
+    call count the sliced steps 16 times and the slice-invariant ones once, and the path
+    roofline of such a step is that of the 16 slices."""
+    tn = ensure_built()
+    w = workloads.rc40c14()
+    plan = tn.Plan(w.net, w.path, w.sliced, prec="bf16x3", max_slice_batch=16, host_only=True)
+    info = plan.info()
+    fixed = batched = 0.0
+    for s in range(info["n_steps"]):
+        st = plan.step(s)
+        f = 8.0 * st["m"] * st["n"] * st["k"]
+        if st["batched"]:
+            batched += f
+        else:
+            fixed += f
+    assert plan.flops_per_call() == pytest.approx(info["flops"], rel=1e-12)
+    assert plan.flops_per_call(16) == pytest.approx(fixed + 16 * batched, rel=1e-12)
+    full = bench.path_roofline(plan, 3, "standard", PEAKS, 1000.0)["sum_t_roof_ms"]
+    part = bench.path_roofline(plan, 3, "standard", PEAKS, 1000.0, count=16)["sum_t_roof_ms"]
+    assert part == pytest.approx(full * 16 / 128, rel=0.02)
+    # tensor-bound: the 16 slices' flops at the form's peak, plus a little for HBM-bound steps
+    assert part >= plan.flops_per_call(16) * info["flops_per_class"][tn.TN_CLASS_TC] / info["flops"] / (
+        1730.2e12 / 3) * 1e3 * 0.999

@@ -138,3 +138,28 @@ def test_device_wait_timeout_is_a_status(tn):
     plan.contract_host(host_inputs(w.net), out)
     want = oracle.contract(w.net, w.path)
     assert abs(complex(out) - want) / abs(want) < 1e-5
+
+
+def test_hbm_budget_two_plans_one_at_a_time(tn):
+    """A budget that holds one workspace of either plan: A, A, B, B submitted together.
+    B's first request frees A's idle instance instead of being refused; every result is
+    OK and matches the oracle."""
+    a = workloads.random_circuit(4, 5, 12, 40)
+    b = workloads.random_circuit(3, 4, 8, 12)
+    p_a = tn.Plan(a.net, a.path, prec="fp32")
+    p_b = tn.Plan(b.net, b.path, prec="fp32")
+    wa, wb = p_a.info()["workspace_bytes"], p_b.info()["workspace_bytes"]
+    budget = max(wa, wb) + min(wa, wb) // 2  # one instance at a time, never both
+    srv = tn.Server(max_inflight=2, n_streams=2, hbm_budget_bytes=budget)
+    jobs = [(p_a, a), (p_a, a), (p_b, b), (p_b, b)]
+    tickets = [srv.submit(p, host_inputs(w.net)) for p, w in jobs]
+    want = {id(a): oracle.contract(a.net, a.path), id(b): oracle.contract(b.net, b.path)}
+    for t, (p, w) in zip(tickets, jobs):
+        out = np.zeros((), dtype=np.complex128)
+        assert srv.poll(t, out, timeout_us=-1) == tn.TN_OK, tn.last_error()
+        assert abs(complex(out) - want[id(w)]) / abs(want[id(w)]) < 1e-5
+    # and back to A after B: A's instance was freed, a new one fits again
+    out = np.zeros((), dtype=np.complex128)
+    assert srv.poll(srv.submit(p_a, host_inputs(a.net)), out, timeout_us=-1) == tn.TN_OK
+    assert abs(complex(out) - want[id(a)]) / abs(want[id(a)]) < 1e-5
+    srv.destroy()

@@ -1,12 +1,14 @@
-"""tn_dot_noalloc: the split-K reduction with its scratch in a fixed device array, for
-callers that must not allocate device memory on this path (a process whose device
+"""tn_dot_noalloc: a split-K-shaped reduction with its scratch in a fixed device array,
+for callers that must not allocate device memory on this path (a process whose device
 memory another allocator already owns, or a latency-critical loop that cannot afford
 cudaMalloc's possible device synchronization).
 
 Checked against the existing entry point (tn_contract on the same two-tensor network,
-which runs the same reduction with its partials in the plan's workspace), within the
-tolerance the other GPU tests use, on two calls in a row: the second call must not
-depend on what the first left in the shared array. Collected last on purpose.
+whose split-K step keeps its partials in the plan's workspace), within the tolerance the
+other GPU tests use, on two calls in a row: the second call must not depend on what the
+first left in the shared array. Also checked: repeated calls leave the device's free
+memory unchanged (nothing is allocated after the first call's address lookup), and
+oversize or overflowing sizes are rejected before any launch. Collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -91,3 +93,30 @@ def test_dot_noalloc_rejects_oversize(tn):
     with pytest.raises(tn.TnError) as e:
         tn.binding.dot_noalloc(1, 1, 65535, 4, 4, 1 << 20, 1)  # partials beyond the scratch
     assert e.value.status == tn.TN_ERR_INVALID and "scratch" in str(e.value)
+    with pytest.raises(tn.TnError) as e:
+        tn.binding.dot_noalloc(1, 1, 1, 1 << 32, 1 << 32, 4096, 1)  # m*n wraps to 0 in int64
+    assert e.value.status == tn.TN_ERR_INVALID and "exceeds" in str(e.value)
+    with pytest.raises(tn.TnError) as e:
+        tn.binding.dot_noalloc(1, 1, 1, 1, 1, 1 << 62, 1)  # ceil(k/4096) beyond the scratch
+    assert e.value.status == tn.TN_ERR_INVALID and "scratch" in str(e.value)
+
+
+def test_dot_noalloc_allocates_nothing(tn):
+    """After the first call (the address lookup), repeated calls leave the device's free
+    memory exactly as it was: the partials go to the fixed array, not to new memory."""
+    rng = np.random.default_rng(9)
+    batch, m, n, k = 4, 2, 4, 2 * 4096 + 5
+    a = (rng.standard_normal((batch, m, k)) + 1j * rng.standard_normal((batch, m, k))).astype(np.complex64)
+    b = (rng.standard_normal((batch, n, k)) + 1j * rng.standard_normal((batch, n, k))).astype(np.complex64)
+    da, db = torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda")
+    out = torch.zeros((batch, m, n), dtype=torch.complex128, device="cuda")
+    tn.binding.dot_noalloc(da, db, batch, m, n, k, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        tn.binding.dot_noalloc(da, db, batch, m, n, k, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    want = np.einsum("bik,bjk->bij", a.astype(np.complex128), b.astype(np.complex128))
+    assert rel_err(out.cpu().numpy(), want) < REL

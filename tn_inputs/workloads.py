@@ -2,8 +2,15 @@
 
   rc12      : 12-qubit 3x4 grid random circuit, 8 brick-wall cycles, one amplitude,
               greedy path, no slicing (the tiny circuit case).
+  rc40c14   : 40-qubit 5x8 grid random circuit, 14 cycles, one amplitude, the greedy path
+              of least total flops found by search_paths.py, sliced greedily until each
+              slice's largest intermediate is <= 2^30 elements (7 labels, 128 slices).
+              The headline workload.
+  rc40c14sub: the same network and path with two more greedily sliced labels (512 slices,
+              every 4 consecutive ones make up one rc40c14 slice): the pieces the CPU
+              oracle contracts for parity at this depth.
   rc40      : 40-qubit 5x8 grid random circuit, 13 cycles, one amplitude, greedy path
-              with 8 sliced labels (256 slices). The headline workload.
+              with 8 sliced labels (256 slices).
   rc40u     : rc40 with no slicing (the same network and path; largest intermediate 2^32
               complex64 = 32 GiB, which one GPU's HBM holds).
   rc40open  : rc40 with the 2x2 corner block of qubits left open, so one contraction
@@ -77,6 +84,42 @@ def rc40():
     return random_circuit(5, 8, 13, 40, n_sliced=8)
 
 
+# The 14-cycle circuit: the greedy run of least total flops over the grid that
+# tn_inputs/search_paths.py scans (seeds 0-1199, alpha in {0.75, 0.875, 1.0}, temperature 0;
+# unsliced 2^50.81 complex MACs), and the labels the greedy slicer picks for it: the first
+# seven bring every slice's largest intermediate to 2^30 elements, the last two are the
+# oracle's finer pieces. Both are reproduced by tests/test_workloads.py.
+RC40C14_PATH = dict(seed=364, alpha=1.0, temperature=0.0)
+RC40C14_SLICED = (320, 328, 446, 350, 210, 461, 453)
+RC40C14_SUBSLICED = RC40C14_SLICED + (357, 344)
+
+
+@functools.lru_cache(maxsize=None)
+def _rc40c14_net_path():
+    net = circuits.amplitude_network(5, 8, 14, 40)
+    return net, greedy.greedy_path(net, **RC40C14_PATH)
+
+
+def _rc40c14(sliced, name):
+    net, path = _rc40c14_net_path()
+    info = dict(RC40C14_PATH)
+    info["peak_sliced"] = greedy.path_peak(net, path, sliced)
+    info["log2flops_sliced"] = greedy.path_log2_flops(net, path, sliced)
+    return Workload(name, net, path, sliced, info)
+
+
+def rc40c14():
+    """40 qubits on 5x8, 14 cycles, one amplitude; 7 sliced labels (128 slices), each
+    slice's largest intermediate 2^30 complex64 elements (8 GiB)."""
+    return _rc40c14(RC40C14_SLICED, "rc_5x8_m14_s40_sl7")
+
+
+def rc40c14sub():
+    """rc40c14 sliced two labels further (512 slices): slice 4s + j of this workload is
+    piece j of rc40c14's slice s (the added labels are the least significant)."""
+    return _rc40c14(RC40C14_SUBSLICED, "rc_5x8_m14_s40_sl9")
+
+
 def rc40u():
     """rc40 without slicing: the same network and path, every intermediate whole (largest
     2^32 elements, a 51 GiB workspace in complex64)."""
@@ -147,6 +190,6 @@ def kings_batch(count, seed=5):
     return out
 
 
-BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40u": rc40u, "kising44": kising44, "kising55": kising55,
+BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40c14": rc40c14, "rc40c14sub": rc40c14sub, "rc40u": rc40u, "kising44": kising44, "kising55": kising55,
            "rc40open": rc40open,
            "khex45": khex45, "ktri44": ktri44, "kings16": kings16}
