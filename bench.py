@@ -70,9 +70,10 @@ NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 41.709e9,
 # oracle): the 40-qubit sum over all slices, and the full values of the smaller workloads.
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 # Slices per step where one contraction of every slice is far longer than a benchmark step:
-# rc40c14 takes ~0.2 s per slice, so 16 slices make a step of a few seconds, and the 3
-# warm-up plus 5 timed steps cover all 128 slices.
-SLICES_PER_STEP = {"rc40c14": 16, "rc40c14sub": 64}
+# rc40c14 takes ~0.2 s per slice, so 8 slices make a step of under two seconds; successive
+# steps take successive slice ranges, and once 16 steps have run every slice has been
+# contracted once (their sum is the whole amplitude).
+SLICES_PER_STEP = {"rc40c14": 8, "rc40c14sub": 32}
 
 
 def stored_oracle_value(workload):
@@ -101,6 +102,71 @@ def stored_slice_partial(workload):
         return None
     d = json.load(open(path))
     return int(d["slice"]), complex(*d["slice_partial"])
+
+
+def measure_local_peaks(tn, seconds=2.0):
+    """Peaks MEASURED_PEAKS.json does not hold, measured here the same way on this GPU: the
+    dense TF32 rate (torch.matmul of 8192^2 FP32 matrices with TF32 allowed, 2 * 8192^3
+    flops) and the FP32 FMA rate (tn_measure_ffma: 8 independent FMA chains per thread,
+    4 x 256 threads per SM), each as a burst (best of 10 CUDA-event timings) and sustained
+    (back to back for `seconds`, the mean), with the SM clock sampled meanwhile."""
+    import torch
+    out = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    n = 8192
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    c = a @ b
+    best = 0.0
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3))
+    reps = max(1, int(seconds * best / (2.0 * n ** 3)))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        torch.matmul(a, b, out=c)
+    e1.record()
+    torch.cuda.synchronize()
+    out["tf32_tflops"] = best / 1e12
+    out["tf32_tflops_sustained"] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del a, b, c
+    rates = [tn.binding.measure_ffma(1 << 18)[0] for _ in range(10)]
+    f1, ms1 = tn.binding.measure_ffma(1 << 18)
+    iters = max(1 << 18, min(1 << 24, int((1 << 18) * seconds * 1e3 / max(ms1, 1e-3))))
+    out["ffma_tflops"] = max(rates) / 1e12
+    out["ffma_tflops_sustained"] = tn.binding.measure_ffma(iters)[0] / 1e12
+    ck = clocks.stop()
+    out["sm_mhz_median"] = ck.get("sm_mhz")
+    out["reasons"] = ck.get("reasons")
+    out["how"] = ("tf32: torch.matmul 8192^3 FP32 with TF32 allowed, best of 10 (burst) and back to back "
+                  f"for {seconds:g} s (sustained); ffma: tn_measure_ffma, best of 10 (burst) and one "
+                  f"{seconds:g} s launch (sustained); CUDA events")
+    return out
+
+
+def form_peaks(peaks):
+    """Peaks (flop/s) the roofline fractions divide by: each tensor-core form's algorithmic
+    peak (three BF16 or TF32 products per algorithmic product for the split forms) from the
+    sustained dense rates, and the FP32 ALU peak (FFMA, 2 flops per lane-cycle; max-plus: an
+    FADD and an FMNMX per term, half the flop rate) -- measured on this GPU where
+    measure_local_peaks ran, else derived (nominal TF32/BF16 ratio, 128 lanes x 152 SMs at
+    the maximum clock), each labelled with its source."""
+    bf = peaks["bf16_tflops_sustained"] * 1e12
+    tf = peaks.get("tf32_tflops_sustained")
+    tf32 = tf * 1e12 if tf else bf * NOMINAL_TF32_PER_BF16
+    ff = peaks.get("ffma_tflops_sustained")
+    alu = ff * 1e12 if ff else SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    return {"tc": {1: tf32, 2: tf32 / 3.0, 3: bf / 3.0}, "alu": alu, "maxplus": alu / 2.0,
+            "source": {"tc_bf16": peaks["_source"], "tf32": "measured here" if tf else "derived (nominal ratio)",
+                       "alu": "measured here" if ff else "derived (max clock)"}}
 
 
 def load_peaks():
@@ -203,9 +269,9 @@ def path_roofline(plan, prec, semiring, peaks, ms_per_step, cplx=True, count=Non
     n_pass = -(-n_sl // info["slice_batch"])
     e, fm = (8.0, 8.0) if cplx else (4.0, 2.0)
     hbm = peaks["hbm_gbs"] * 1e9
-    bf = peaks["bf16_tflops_sustained"] * 1e12
-    tc_peak = {1: bf * NOMINAL_TF32_PER_BF16, 2: bf * NOMINAL_TF32_PER_BF16 / 3.0, 3: bf / 3.0}.get(prec)
-    alu = SM_COUNT * FP32_LANES * (1 if semiring == "maxplus" else 2) * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    fp = form_peaks(peaks)
+    tc_peak = fp["tc"].get(prec)
+    alu = fp["maxplus"] if semiring == "maxplus" else fp["alu"]
     total = 0.0
     for s in range(info["n_steps"]):
         st = plan.step(s)
@@ -284,17 +350,23 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     peaks = load_peaks()
+    peaks.update(measure_local_peaks(tn))
+    fpk = form_peaks(peaks)
+    # the planner's Eq. 6 rates: this GPU's measured peaks
+    tn.binding.set_cost_model(peaks["hbm_gbs"] * 1e9, fpk["alu"], [fpk["tc"][1], fpk["tc"][2], fpk["tc"][3]])
     w = workloads.BY_NAME[args.workload]()
     semiring = w.info.get("semiring", "standard")
     cplx = w.net.is_complex
     # real networks (the max-plus workloads) run the R32 FP32 form
     prec = PREC[args.prec] if cplx else tn.TN_R32_FP32_SIMT
-    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=args.max_slice_batch, semiring=semiring)
-    info = plan.info()
-    stream = torch.cuda.current_stream()
-    n_sl = info["n_slices"]
+    n_sl = w.n_slices
     per_step = args.slices_per_step or SLICES_PER_STEP.get(args.workload, n_sl)
     per_step = max(1, min(per_step, n_sl))
+    # a slice-batched step runs its slices in one pass unless told otherwise
+    batch = args.max_slice_batch or (per_step if per_step < n_sl else 0)
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=batch, semiring=semiring)
+    info = plan.info()
+    stream = torch.cuda.current_stream()
     # step j contracts slices [j * per_step, (j + 1) * per_step) modulo n_slices
     ranges = [((j * per_step) % n_sl, min(per_step, n_sl - (j * per_step) % n_sl))
               for j in range(args.warmup + args.steps)]
@@ -340,12 +412,11 @@ def run_ours(args):
     tflop_per_s, ms_max = replica_throughput(ms, flops / 1e12, dist, device="cuda")
     value = tflop_per_s
     all_out = outs.cpu().numpy()
-    # the whole result when the steps covered every slice exactly once (else the last step's)
-    covered = sorted(b for b, _ in ranges)
-    whole = per_step < n_sl and len(ranges) * per_step == n_sl and covered == list(range(0, n_sl, per_step))
-    result = all_out.sum(axis=0) if whole else all_out[-1]
-    if per_step == n_sl:
-        result = all_out[-1]
+    # the whole result once the steps have covered every slice: the first n_sl / per_step
+    # ranges tile the slices exactly (else the last step's partial)
+    tiles = n_sl // per_step
+    whole = per_step < n_sl and n_sl % per_step == 0 and len(ranges) >= tiles
+    result = all_out[:tiles].sum(axis=0) if whole else all_out[-1]
 
     # dominant kernel class by device time, and its roofline
     cls = max(range(4), key=lambda c: prof["ms"][c])
@@ -363,16 +434,10 @@ def run_ours(args):
         achieved = prof["bytes"][cls] / (prof["ms"][cls] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     elif cls == 2:
-        bf = peaks["bf16_tflops_sustained"]
-        tf32 = bf * NOMINAL_TF32_PER_BF16
-        form_peak = {1: tf32, 2: tf32 / 3.0, 3: bf / 3.0}[prec]
         achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": form_peak, "unit": "TFLOP/s"}
+        roof = {"bound": "tensor", "achieved": achieved, "peak": fpk["tc"][prec] / 1e12, "unit": "TFLOP/s"}
     else:
-        # FFMA: 2 flops per lane per cycle; max-plus: an FADD and an FMNMX per term, i.e. the
-        # 2 counted ops take 2 lane-cycles
-        ops_per_lane = 1 if semiring == "maxplus" else 2
-        alu = SM_COUNT * FP32_LANES * ops_per_lane * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        alu = (fpk["maxplus"] if semiring == "maxplus" else fpk["alu"]) / 1e12
         achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -382,7 +447,8 @@ def run_ours(args):
     roof["launches_per_step"] = launches / args.steps
     roof["ms_per_launch"] = per_launch_ms
     roof["share_of_step"] = prof["ms"][cls] / sum(prof["ms"])
-    roof["peak_source"] = peaks["_source"]
+    roof["peak_source"] = {1: fpk["source"]["tf32"], 2: fpk["source"]["tf32"], 3: fpk["source"]["tc_bf16"]}.get(
+        prec, fpk["source"]["alu"]) if cls == 2 else (peaks["_source"] if cls in (1, 3) else fpk["source"]["alu"])
     path_roof = path_roofline(plan, prec, semiring, peaks, ms_max, cplx, count=round(slices_per_step))
 
     # end to end through the public C ABI with host buffers
@@ -431,9 +497,10 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": host_out.nbytes + host_ls.nbytes},
         "gpu_launches": sum(plan.launches_per_call(c) for _, c in timed),
         "clocks": ck,
+        "peaks": {k: v for k, v in peaks.items() if not k.startswith("_") and k not in ("when", "image", "torch")},
     }
     if per_step < n_sl:
-        line["result_scope"] = ("all slices (the warm-up and timed steps together cover each slice once)"
+        line["result_scope"] = (f"all {n_sl} slices (the sum of the first {tiles} steps' slice ranges)"
                                 if whole else f"slices {ranges[-1][0]}..{ranges[-1][0] + ranges[-1][1] - 1}")
     sp = stored_slice_partial(args.workload)
     if sp is not None:
@@ -484,6 +551,8 @@ def run_batch_bench(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     count = args.networks
+    peaks = load_peaks()
+    peaks.update(measure_local_peaks(tn))
     maxplus = args.workload == "kingsbatch"
     semiring = "maxplus" if maxplus else "standard"
     wl = workloads.kings_batch(count) if maxplus else workloads.ising3r(count, seed=3)
@@ -529,7 +598,8 @@ def run_batch_bench(args):
         lnz_s = np.log(outs.cpu().numpy()) + lss.cpu().numpy()
         diff = float(np.max(np.abs(lnz_b - lnz_s)))
     t, c = b.launch_shape()
-    alu = SM_COUNT * FP32_LANES * (1 if maxplus else 2) * load_peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fpk = form_peaks(peaks)
+    alu = (fpk["maxplus"] if maxplus else fpk["alu"]) / 1e12
     line = {
         "metric": "networks/s", "value": ws * count / (ms / 1e3), "unit": "networks/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -546,6 +616,7 @@ def run_batch_bench(args):
         "roofline": {"bound": "alu", "achieved": b.flops / (ms / 1e3) / 1e12, "peak": alu, "unit": "TFLOP/s",
                      "frac": b.flops / (ms / 1e3) / 1e12 / alu, "traffic": None, "kernel": "batch_kernel"},
         "gpu_launches": args.steps, "clocks": ck,
+        "peaks": {k: v for k, v in peaks.items() if k.startswith(("ffma", "tf32", "sm_mhz"))},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -48,7 +48,10 @@ typedef enum {
  *               hi.lo + lo.hi (complex only; relative error per product <= ~3 * 2^-16),
  *               FP32 accumulation.
  * Steps too small or too thin for a tensor-core tile run on the FP32 SIMT kernels
- * whatever the form. */
+ * whatever the form (tn_plan_step reports each step's kernel). The real tensor-core forms
+ * (R32_TF32, R32_3XTF32, R32_BF16X3) are not built, and exponent scaling runs in the
+ * FP32_SIMT forms only: tn_plan returns TN_ERR_UNSUPPORTED for those requests rather
+ * than running another form. */
 typedef enum {
   TN_C64_FP32_SIMT = 0,
   TN_C64_TF32 = 1,
@@ -76,7 +79,8 @@ typedef enum { TN_SEMIRING_STANDARD = 0, TN_SEMIRING_MAXPLUS = 1 } tn_semiring;
 typedef struct {
   int32_t prec;            /* tn_precision */
   int32_t complex_mult;    /* 4 (4M) -- the only form built; 3 is rejected */
-  int32_t exp_scaling;     /* 1: per-intermediate power-of-two scaling, log scale in FP64 */
+  int32_t exp_scaling;     /* 1: per-intermediate power-of-two scaling, log scale in FP64
+                              (FP32_SIMT forms only) */
   int32_t max_slice_batch; /* slices per device pass; 0 = as many as fit in free HBM */
   uint32_t flags;          /* TN_PLAN_* */
   int32_t semiring;        /* tn_semiring */
@@ -164,6 +168,30 @@ typedef struct {
   int32_t format;          /* tn_storage_format of the tensor's copies */
   int32_t reserved;
 } tn_tensor_info;
+
+/* Rates of the kernel choice, the roofline cost model of Sec. IV-C Eq. 6: a step's time
+ * under a kernel family is max(bytes / hbm_bytes_per_s, flops / F) with F that family's
+ * peak in algorithmic flops (8 per complex MAC, 2 per real MAC). Process-wide; plans built
+ * after tn_cost_model_set use the new rates. Defaults: 6.8e12 B/s, FP32 FMA 152 SMs x 128
+ * lanes x 2 x 1.9 GHz, and from a sustained dense BF16 rate of 1.7e15 flop/s: TF32 at
+ * 1.1/2.25 of it, 3xTF32 a third of TF32, BF16x3 a third of BF16. */
+typedef struct {
+  double hbm_bytes_per_s;  /* B */
+  double simt_flops;       /* F of the CUDA-core kernels (FP32 FMA) */
+  double tc_flops[3];      /* F of the tensor-core forms: [TF32, 3XTF32, BF16X3] */
+} tn_cost_model;
+
+/* Replace the rates (every field > 0, else TN_ERR_INVALID). Not thread-safe against
+ * concurrent tn_plan calls. */
+tn_status tn_cost_model_set(const tn_cost_model* m);
+tn_status tn_cost_model_get(tn_cost_model* out);
+
+/* Measure the FP32 FMA peak of the current device (the paper has no counterpart; it is the
+ * denominator of the CUDA-core kernels' roofline): a kernel whose every thread runs
+ * `iters` rounds of 8 independent FMA chains, 4 CTAs of 256 threads per SM, timed with CUDA
+ * events on `stream`. Writes the rate in flop/s (2 per FMA) and the elapsed milliseconds.
+ * Synchronous; 0 < iters <= 2^24. */
+tn_status tn_measure_ffma(int64_t iters, double* flops_per_s, double* ms, void* stream);
 
 /* Build a plan: validate, analyse each step (Sec. II-B), run the backward mode
  * reordering pass (Sec. IV-A), choose a kernel per step, assign every tensor a

@@ -87,6 +87,10 @@ class tn_serve_config(C.Structure):
                 ("reserved", C.c_int32 * 3)]
 
 
+class tn_cost_model(C.Structure):
+    _fields_ = [("hbm_bytes_per_s", C.c_double), ("simt_flops", C.c_double), ("tc_flops", C.c_double * 3)]
+
+
 class tn_dist_config(C.Structure):
     _fields_ = [("n_gpus", C.c_int32), ("reserved0", C.c_int32), ("large_bytes", C.c_double),
                 ("gather_bytes", C.c_double), ("dev_bw", C.c_double), ("dev_flops", C.c_double),
@@ -143,6 +147,9 @@ def _load():
         "tn_batch_autotune": [vp, vp, vp, vp, vp],
         "tn_batch_destroy": [vp],
         "tn_plan_distribute": [vp, C.POINTER(tn_dist_config), C.POINTER(tn_dist_report), C.POINTER(tn_dist_step)],
+        "tn_cost_model_set": [C.POINTER(tn_cost_model)],
+        "tn_cost_model_get": [C.POINTER(tn_cost_model)],
+        "tn_measure_ffma": [i64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -421,6 +428,26 @@ class Batch:
             self.destroy()
         except Exception:
             pass
+
+
+def cost_model() -> dict:
+    """The planner's Eq. 6 rates (tn_cost_model_get)."""
+    m = tn_cost_model()
+    check(lib.tn_cost_model_get(C.byref(m)))
+    return {"hbm_bytes_per_s": m.hbm_bytes_per_s, "simt_flops": m.simt_flops, "tc_flops": list(m.tc_flops)}
+
+
+def set_cost_model(hbm_bytes_per_s, simt_flops, tc_flops):
+    """Replace the planner's Eq. 6 rates (tn_cost_model_set); tc_flops = [TF32, 3xTF32, BF16x3]."""
+    m = tn_cost_model(hbm_bytes_per_s, simt_flops, (C.c_double * 3)(*tc_flops))
+    check(lib.tn_cost_model_set(C.byref(m)))
+
+
+def measure_ffma(iters=1 << 18, stream=None):
+    """FP32 FMA rate of the current device (tn_measure_ffma): (flop/s, ms)."""
+    f, ms = C.c_double(), C.c_double()
+    check(lib.tn_measure_ffma(int(iters), C.byref(f), C.byref(ms), _ptr_stream(stream)))
+    return f.value, ms.value
 
 
 def dot_noalloc(a, b, batch, m, n, k, out, stream=None):

@@ -187,6 +187,23 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
   return TN_OK;
 }
 
+// FP32 FMA peak probe: 8 independent chains x <- x * m + c per thread (the fixed point
+// c / (1 - m) keeps every value normal); the sum is stored only if it hits an impossible
+// value, so the chains stay live without memory traffic.
+__global__ void __launch_bounds__(256) ffma_probe_kernel(int64_t iters, float m, float c, float* out) {
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 0.05f + 1e-3f * j + 1e-6f * threadIdx.x;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fmaf(x[j], m, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  if (s == -1.0f) out[blockIdx.x] = s;
+}
+
 }  // namespace tn
 
 using namespace tn;
@@ -459,6 +476,58 @@ tn_status tn_selftest_bounded_wait(tn_plan_t plan, int32_t arrive, int64_t limit
     return TN_ERR_CUDA;
   }
   return check_device_error(P);
+}
+
+tn_status tn_cost_model_set(const tn_cost_model* m) {
+  if (!m || !(m->hbm_bytes_per_s > 0) || !(m->simt_flops > 0) || !(m->tc_flops[0] > 0) ||
+      !(m->tc_flops[1] > 0) || !(m->tc_flops[2] > 0)) {
+    set_error("tn_cost_model_set: every rate must be positive");
+    return TN_ERR_INVALID;
+  }
+  g_cost = *m;
+  return TN_OK;
+}
+
+tn_status tn_cost_model_get(tn_cost_model* out) {
+  if (!out) {
+    set_error("null argument");
+    return TN_ERR_INVALID;
+  }
+  *out = g_cost;
+  return TN_OK;
+}
+
+tn_status tn_measure_ffma(int64_t iters, double* flops_per_s, double* ms, void* stream) {
+  if (iters <= 0 || iters > (int64_t(1) << 24) || !flops_per_s) {
+    set_error("tn_measure_ffma: needs 0 < iters <= 2^24 and an output pointer");
+    return TN_ERR_INVALID;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int grid = 4 * sms;
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) {
+    ffma_probe_kernel<<<grid, 256, 0, st>>>(iters, 0.999999f, 1e-7f, nullptr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    set_error(std::string("tn_measure_ffma: ") + cudaGetErrorString(e));
+    return TN_ERR_CUDA;
+  }
+  *flops_per_s = 2.0 * 8.0 * double(iters) * double(grid) * 256.0 / (double(t) * 1e-3);
+  if (ms) *ms = t;
+  return TN_OK;
 }
 
 tn_status tn_plan_profile(tn_plan_t plan, int32_t enable) {

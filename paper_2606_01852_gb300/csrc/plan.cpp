@@ -18,12 +18,6 @@ namespace {
 constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-// Roofline constants for the kernel choice (t = max(bytes/B, flops/F), Sec. IV-C Eq. 6).
-// B is the measured copy bandwidth; F per form is the algorithmic rate each kernel
-// family sustains (complex 4M counts 8 flops per complex MAC).
-constexpr double kHbm = 6.6e12;
-constexpr double kSimtFlops = 45e12;
-
 bool tc_prec_built(int32_t p) { return p == TN_C64_TF32 || p == TN_C64_3XTF32 || p == TN_C64_BF16X3; }
 
 bool is_tc_prec(int32_t p) {
@@ -31,11 +25,23 @@ bool is_tc_prec(int32_t p) {
          p == TN_R32_3XTF32 || p == TN_R32_BF16X3;
 }
 
+}  // namespace
+
+// Rates of the kernel choice (t = max(bytes/B, flops/F), Sec. IV-C Eq. 6): B the HBM copy
+// rate, F per kernel family its peak in algorithmic flops (8 per complex MAC). Defaults:
+// this part's measured copy rate and sustained dense BF16 rate (the BF16x3 form does three
+// BF16 products per algorithmic one; TF32 is 1.1/2.25 of BF16, 3xTF32 a third of that) and
+// the FP32 FMA rate of 152 SMs x 128 lanes at 1.9 GHz. tn_cost_model_set replaces them.
+tn_cost_model g_cost = {6.8e12, 152.0 * 128.0 * 2.0 * 1.9e9, {1.7e15 * 1.1 / 2.25, 1.7e15 * 1.1 / 2.25 / 3.0,
+                                                             1.7e15 / 3.0}};
+
+namespace {
+
 double tc_flops(int32_t p) {
   switch (p) {
-    case TN_C64_TF32: case TN_R32_TF32: return 700e12;
-    case TN_C64_3XTF32: case TN_R32_3XTF32: return 250e12;
-    case TN_C64_BF16X3: case TN_R32_BF16X3: return 450e12;
+    case TN_C64_TF32: case TN_R32_TF32: return g_cost.tc_flops[0];
+    case TN_C64_3XTF32: case TN_R32_3XTF32: return g_cost.tc_flops[1];
+    case TN_C64_BF16X3: case TN_R32_BF16X3: return g_cost.tc_flops[2];
     default: return 0;
   }
 }
@@ -92,6 +98,15 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
   }
   if (pol.semiring == TN_SEMIRING_MAXPLUS && (pol.prec != TN_R32_FP32_SIMT || pol.exp_scaling)) {
     err = "the max-plus semiring runs in the R32 FP32 form without exponent scaling";
+    return TN_ERR_UNSUPPORTED;
+  }
+  if (pol.prec == TN_R32_TF32 || pol.prec == TN_R32_3XTF32 || pol.prec == TN_R32_BF16X3) {
+    err = "the real tensor-core forms are not built: real networks run in TN_R32_FP32_SIMT";
+    return TN_ERR_UNSUPPORTED;
+  }
+  if (is_tc_prec(pol.prec) && pol.exp_scaling) {
+    err = "exponent scaling runs in the CUDA-core forms only (TN_C64_FP32_SIMT, TN_R32_FP32_SIMT): "
+          "the tensor-core kernels do not rescale their operands";
     return TN_ERR_UNSUPPORTED;
   }
   if (pol.complex_mult != 0 && pol.complex_mult != 4) {
@@ -331,8 +346,7 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     }
     // The tensor-core kernel tiles 128 rows: give the row role to the operand that
     // fills them when only one orientation qualifies.
-    const bool tc_form_here = tc_form && P.is_complex && !pol.exp_scaling && tc_prec_built(pol.prec) &&
-                              tc_supported();
+    const bool tc_form_here = tc_form && P.is_complex && tc_prec_built(pol.prec) && tc_supported();
     if (tc_form_here && !tc_step_ok(st.m, st.n, st.k, pol.prec) && tc_step_ok(st.n, st.m, st.k, pol.prec)) {
       std::swap(st.a, st.b);
       std::swap(st.M, st.N);
@@ -345,12 +359,12 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     }
     const double flops = fm * double(st.m) * double(st.n) * double(st.k);
     const double bytes = eb * (double(st.m) * st.k + double(st.n) * st.k + double(st.m) * st.n);
-    const double t_simt = std::max(bytes / kHbm, flops / kSimtFlops);
+    const double t_simt = std::max(bytes / g_cost.hbm_bytes_per_s, flops / g_cost.simt_flops);
     st.cls = TN_CLASS_SIMT;
     if (tc_form_here && tc_step_ok(st.m, st.n, st.k, pol.prec)) {
       // a step narrower than the 128-column tile uses that fraction of the tensor core
       const double fill = std::min(1.0, double(st.n) / 128.0);
-      const double t_tc = std::max(bytes / kHbm, flops / (tc_flops(pol.prec) * fill));
+      const double t_tc = std::max(bytes / g_cost.hbm_bytes_per_s, flops / (tc_flops(pol.prec) * fill));
       // ties (both bound by the same HBM bytes) go to the tensor-core kernel, whose
       // epilogue stores are the better coalesced
       if (t_tc <= t_simt) st.cls = TN_CLASS_TC;

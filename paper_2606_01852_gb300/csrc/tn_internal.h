@@ -117,6 +117,9 @@ struct Plan {
   tn_plan_stats stats{};
 };
 
+// rates of the planner's kernel choice (process-wide; tn_cost_model_set)
+extern tn_cost_model g_cost;
+
 // planner (host only)
 tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* sliced,
                      int32_t n_sliced, const tn_dtype_policy& pol, Plan& P, std::string& err);

@@ -184,3 +184,48 @@ def test_batch_maxplus_policy_checks():
     with pytest.raises(tn.TnError) as e:
         tn.Batch(nets, paths, complex_=False, exp_scaling=True, semiring="maxplus", host_only=True)
     assert "TN_ERR_UNSUPPORTED" in str(e.value)
+
+
+def test_unbuilt_forms_are_refused_not_substituted():
+    """A request the engine cannot run as asked is a status, not a silent change of form:
+    the real tensor-core forms are not built, and exponent scaling runs only in the
+    CUDA-core forms."""
+    tn = ensure_built()
+    from tn_inputs import ising_pf
+    net = ising_pf.random_3regular_network(20, 1, beta=0.5)
+    path = greedy.greedy_path(net, seed=0, alpha=1.0)
+    for prec in (tn.TN_R32_TF32, tn.TN_R32_3XTF32, tn.TN_R32_BF16X3):
+        with pytest.raises(tn.TnError) as e:
+            tn.Plan(net, path, prec=prec, exp_scaling=True, host_only=True)
+        assert e.value.status == tn.TN_ERR_UNSUPPORTED and "not built" in str(e.value)
+    w = workloads.rc12()
+    for prec in ("tf32", "3xtf32", "bf16x3"):
+        with pytest.raises(tn.TnError) as e:
+            tn.Plan(w.net, w.path, prec=prec, exp_scaling=True, host_only=True)
+        assert e.value.status == tn.TN_ERR_UNSUPPORTED and "scaling" in str(e.value)
+    # the CUDA-core forms take scaling
+    tn.Plan(net, path, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True, host_only=True).destroy()
+    tn.Plan(w.net, w.path, prec="fp32", exp_scaling=True, host_only=True).destroy()
+
+
+def test_cost_model_rates_drive_the_kernel_choice():
+    """Eq. 6 with the configured rates: a 4096^2 x 4096 complex step goes to the tensor
+    cores at the default rates and to the CUDA cores when the tensor-core rate is set far
+    below the FMA rate; bad rates are refused."""
+    tn = ensure_built()
+    from tn_inputs.network import Network as N2
+    ext = {0: 4096, 1: 4096, 2: 4096}
+    z = np.zeros((1, 1), np.complex128)
+    net = N2([z, z], [(0, 2), (1, 2)], ext, (0, 1))
+    old = tn.binding.cost_model()
+    try:
+        assert tn.Plan(net, Path([(0, 1)]), prec="bf16x3", host_only=True).step(0)["cls"] == tn.TN_CLASS_TC
+        tn.binding.set_cost_model(old["hbm_bytes_per_s"], old["simt_flops"], [1e9, 1e9, 1e9])
+        assert tn.binding.cost_model()["tc_flops"] == [1e9, 1e9, 1e9]
+        assert tn.Plan(net, Path([(0, 1)]), prec="bf16x3", host_only=True).step(0)["cls"] == tn.TN_CLASS_SIMT
+        with pytest.raises(tn.TnError) as e:
+            tn.binding.set_cost_model(0.0, 1.0, [1.0, 1.0, 1.0])
+        assert e.value.status == tn.TN_ERR_INVALID
+    finally:
+        tn.binding.set_cost_model(old["hbm_bytes_per_s"], old["simt_flops"], old["tc_flops"])
+    assert tn.binding.cost_model() == old

@@ -13,7 +13,7 @@ from tn_inputs.network import Network, Path
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-PEAKS = {"hbm_gbs": 6684.8, "bf16_tflops_sustained": 1730.2, "sm_max_mhz": 2070.0}
+PEAKS = {"hbm_gbs": 6684.8, "bf16_tflops_sustained": 1730.2, "sm_max_mhz": 2070.0, "_source": "measured"}
 
 
 def test_path_roofline_single_gemm_by_hand():
