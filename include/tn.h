@@ -120,9 +120,11 @@ typedef enum {
   TN_CLASS_STREAM = 1, /* big x small: one pass over the big operand */
   TN_CLASS_TC = 2,     /* tcgen05 tensor-core GEMM (rows >= 128, columns >= 16, k >= 8; a
                           persistent variant for k <= 64 in the BF16X3 form) */
-  TN_CLASS_SPLITK = 3  /* few outputs, long k: split-K partials in FP64, fixed-order sum */
+  TN_CLASS_SPLITK = 3, /* few outputs, long k: split-K partials in FP64, fixed-order sum */
+  TN_CLASS_PERM = 4    /* not a step class: leaf staging (a leaf permuted from its declared
+                          order into its planned order); in tn_profile only */
 } tn_step_class;
-#define TN_N_CLASSES 4
+#define TN_N_CLASSES 5
 
 typedef struct {
   int64_t n_steps, n_leaves, n_slices, slice_batch, n_passes;
@@ -147,6 +149,8 @@ typedef struct {
    * rows(r) + cols(c) of the output's planned layout. */
   int32_t n_row_dims, n_col_dims;
   int64_t row_ext[12], row_stride[12], col_ext[12], col_stride[12];
+  int32_t ksplit;          /* SIMT steps: k cut in this many parts (then two launches) */
+  int32_t reserved;
 } tn_step_info;
 
 /* How a tensor's copies are stored in the workspace. PLANAR: FP32 (complex: the real
@@ -166,7 +170,8 @@ typedef struct {
   int32_t producer;        /* step index, -1 for a leaf */
   int32_t consumer;        /* step index, -1 for the root */
   int32_t format;          /* tn_storage_format of the tensor's copies */
-  int32_t reserved;
+  int32_t tiled;           /* leaves: staged by the tiled permutation kernel (one launch per
+                              pass that stages it) rather than the per-leaf kernel */
 } tn_tensor_info;
 
 /* Rates of the kernel choice, the roofline cost model of Sec. IV-C Eq. 6: a step's time
@@ -204,6 +209,15 @@ tn_status tn_plan(const tn_network* net, const tn_path* path, const int32_t* sli
 
 /* Plan statistics (host only). */
 tn_status tn_plan_info(tn_plan_t plan, tn_plan_stats* out);
+
+/* Host-side check of the tiled leaf staging (no device work; the paper has no
+ * counterpart): replays the index arithmetic of the tiled permutation kernel for every
+ * large leaf and up to max_slices slice ids, and checks that every source index lies in
+ * the declared tensor and is the element the declared order places at each staged
+ * position, that every staged element is written exactly once, and that the paired
+ * 16-byte loads read adjacent elements. TN_OK, or TN_ERR_INVALID naming the first
+ * mismatch. */
+tn_status tn_plan_check_staging(tn_plan_t plan, int64_t max_slices);
 
 /* Planned mode order of tensor `id` (SSA id; leaves and intermediates, sliced labels
  * removed). modes_out must hold at least the tensor's rank; *rank_out gets the rank.
@@ -254,7 +268,9 @@ tn_status tn_plan_destroy(tn_plan_t plan);
 /* Per kernel class (index tn_step_class): launches, device milliseconds measured with
  * CUDA events recorded on the contract's stream around each step launch, and the
  * algorithmic flops (8mnk complex, 2mnk real) and bytes (e(mk+kn+mn), each operand
- * and the output counted once per batch entry that reads or writes it). */
+ * and the output counted once per batch entry that reads or writes it). Entry
+ * TN_CLASS_PERM covers the leaf staging of each pass: no flops, bytes = the staged
+ * leaves read and written once per copy (2 e |leaf| per copy). */
 typedef struct {
   int64_t launches[TN_N_CLASSES];
   double ms[TN_N_CLASSES];

@@ -8,6 +8,7 @@ from .binding import (Plan, Server, Batch, TnError, check, last_error, make_poli
                       TN_ERR_BUSY, TN_ERR_TIMEOUT, TN_ERR_NOT_READY,
                       TN_C64_FP32_SIMT, TN_C64_TF32, TN_C64_3XTF32, TN_C64_BF16X3,
                       TN_R32_FP32_SIMT, TN_R32_TF32, TN_R32_3XTF32, TN_R32_BF16X3,
-                      TN_CLASS_SIMT, TN_CLASS_STREAM, TN_CLASS_TC, TN_CLASS_SPLITK, CLASS_NAMES)
+                      TN_CLASS_SIMT, TN_CLASS_STREAM, TN_CLASS_TC, TN_CLASS_SPLITK, TN_CLASS_PERM,
+                      CLASS_NAMES)
 
 __all__ = ["Plan", "Server", "TnError", "check", "last_error", "make_policy", "lib", "LIB_PATH"]

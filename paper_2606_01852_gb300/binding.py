@@ -24,8 +24,9 @@ TN_C64_FP32_SIMT, TN_C64_TF32, TN_C64_3XTF32, TN_C64_BF16X3, TN_R32_FP32_SIMT, T
     TN_R32_3XTF32, TN_R32_BF16X3 = range(8)
 PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
 TN_PLAN_HOST_ONLY = 1
-TN_CLASS_SIMT, TN_CLASS_STREAM, TN_CLASS_TC, TN_CLASS_SPLITK = range(4)
-CLASS_NAMES = ["contract_simt", "contract_stream", "contract_tc", "contract_splitk"]
+TN_CLASS_SIMT, TN_CLASS_STREAM, TN_CLASS_TC, TN_CLASS_SPLITK, TN_CLASS_PERM = range(5)
+N_CLASSES = 5
+CLASS_NAMES = ["contract_simt", "contract_stream", "contract_tc", "contract_splitk", "stage_leaves"]
 
 
 class TnError(RuntimeError):
@@ -56,7 +57,7 @@ class tn_plan_stats(C.Structure):
                 ("slice_batch", C.c_int64), ("n_passes", C.c_int64), ("flops", C.c_double),
                 ("bytes", C.c_double), ("Ct", C.c_double), ("Cm", C.c_double), ("Cs", C.c_double),
                 ("peak_elems", C.c_int64), ("workspace_bytes", C.c_int64),
-                ("steps_per_class", C.c_int64 * 4), ("flops_per_class", C.c_double * 4),
+                ("steps_per_class", C.c_int64 * 5), ("flops_per_class", C.c_double * 5),
                 ("leaf_permutes", C.c_int64)]
 
 
@@ -65,7 +66,8 @@ class tn_step_info(C.Structure):
                 ("b_id", C.c_int32), ("cls", C.c_int32), ("batched", C.c_int32),
                 ("n_row_dims", C.c_int32), ("n_col_dims", C.c_int32),
                 ("row_ext", C.c_int64 * 12), ("row_stride", C.c_int64 * 12),
-                ("col_ext", C.c_int64 * 12), ("col_stride", C.c_int64 * 12)]
+                ("col_ext", C.c_int64 * 12), ("col_stride", C.c_int64 * 12),
+                ("ksplit", C.c_int32), ("reserved", C.c_int32)]
 
 
 class tn_tensor_info(C.Structure):
@@ -73,12 +75,12 @@ class tn_tensor_info(C.Structure):
                 ("batched", C.c_int32), ("pinned", C.c_int32), ("producer", C.c_int32),
                 ("consumer", C.c_int32),
                 ("format", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("tiled", C.c_int32)]
 
 
 class tn_profile(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4), ("flops", C.c_double * 4),
-                ("bytes", C.c_double * 4)]
+    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5), ("flops", C.c_double * 5),
+                ("bytes", C.c_double * 5)]
 
 
 class tn_serve_config(C.Structure):
@@ -148,6 +150,7 @@ def _load():
         "tn_batch_destroy": [vp],
         "tn_plan_distribute": [vp, C.POINTER(tn_dist_config), C.POINTER(tn_dist_report), C.POINTER(tn_dist_step)],
         "tn_cost_model_set": [C.POINTER(tn_cost_model)],
+        "tn_plan_check_staging": [vp, i64],
         "tn_cost_model_get": [C.POINTER(tn_cost_model)],
         "tn_measure_ffma": [i64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
     }
@@ -263,6 +266,7 @@ class Plan:
         i = tn_step_info()
         check(lib.tn_plan_step(self.handle, s, C.byref(i)))
         d = {f: getattr(i, f) for f, _ in tn_step_info._fields_[:7]}
+        d["ksplit"] = i.ksplit
         d["rows"] = [(i.row_ext[x], i.row_stride[x]) for x in range(i.n_row_dims)]
         d["cols"] = [(i.col_ext[x], i.col_stride[x]) for x in range(i.n_col_dims)]
         return d
@@ -306,6 +310,10 @@ class Plan:
             st = self.step(s)
             tot += fm * st["m"] * st["n"] * st["k"] * (count if st["batched"] else 1)
         return tot
+
+    def check_staging(self, max_slices=4):
+        """Host replay of the tiled staging kernel's index arithmetic (tn_plan_check_staging)."""
+        check(lib.tn_plan_check_staging(self.handle, int(max_slices)))
 
     def profile(self, enable: bool):
         check(lib.tn_plan_profile(self.handle, 1 if enable else 0))
@@ -356,10 +364,14 @@ class Plan:
         passes = (count + b - 1) // b
         S = info["n_steps"]
         steps = [self.step(s) for s in range(S)]
-        per = [2 if st["cls"] == TN_CLASS_SPLITK else 1 for st in steps]
+        per = [2 if (st["cls"] == TN_CLASS_SPLITK or st["ksplit"] > 1) else 1 for st in steps]
         batched = sum(p for p, st in zip(per, steps) if st["batched"])
-        # per pass: staging + steps + root accumulation; once: the output write
-        return passes * 2 + sum(per) + (passes - 1) * batched + 1
+        leaves = [self.tensor(t) for t in range(self.n_leaves)]
+        tiled = sum(1 for x in leaves if x["tiled"])
+        tiled_b = sum(1 for x in leaves if x["tiled"] and x["batched"])
+        # per pass: staging (+ one launch per tiled leaf) + steps + root accumulation; once:
+        # the output write
+        return (passes * 2 + sum(per) + (passes - 1) * batched + 1 + tiled + (passes - 1) * tiled_b)
 
     def destroy(self):
         if getattr(self, "handle", None):

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "staging.cuh"
 #include "tn_internal.h"
 
 namespace tn {
@@ -143,7 +144,26 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
         TN_CUDA_TRY(cudaMemsetAsync(recs + P.n_rec_unbatched, 0x80,
                                     sizeof(ScaleRec) * (P.n_rec_total - P.n_rec_unbatched), st));
     }
-    launch_stage_leaves(descs, T, P.dev, sb, nb, p > 0, cplx, recs, recidx, st);
+    Plan::ProfRec sp{};
+    if (P.prof_on) {
+      sp.e0 = take_event(P);
+      sp.e1 = take_event(P);
+      sp.cls = TN_CLASS_PERM;
+      sp.step = -1;
+      double staged = 0.0;
+      for (int32_t t = 0; t < T; ++t) {
+        const TensorRec& R = P.tensors[t];
+        if (p > 0 && !R.batched) continue;
+        staged += double(R.size) * (R.batched ? nb : 1);
+      }
+      sp.bytes = 2.0 * (cplx ? 8.0 : 4.0) * staged;
+      TN_CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(sp.e0), st));
+    }
+    launch_stage_leaves(descs, P.leafdesc.data(), T, P.dev, sb, nb, p > 0, cplx, recs, recidx, st);
+    if (P.prof_on) {
+      TN_CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(sp.e1), st));
+      P.prof_pending.push_back(sp);
+    }
     for (int32_t s = 0; s < S; ++s) {
       const StepRec& sr = P.steps[s];
       if (!sr.batched && p > 0) continue;  // slice-invariant: computed once, kept
@@ -332,6 +352,8 @@ tn_status tn_plan_step(tn_plan_t plan, int32_t s, tn_step_info* out) {
     out->col_ext[d] = d < st.cols.n ? st.cols.ext[d] : 0;
     out->col_stride[d] = d < st.cols.n ? st.cols.stride[d] : 0;
   }
+  out->ksplit = st.ksplit;
+  out->reserved = 0;
   return TN_OK;
 }
 
@@ -349,7 +371,7 @@ tn_status tn_plan_tensor(tn_plan_t plan, int32_t id, tn_tensor_info* out) {
   out->producer = R.producer;
   out->consumer = R.consumer;
   out->format = R.split ? TN_FORMAT_SPLIT_BF16 : TN_FORMAT_PLANAR;
-  out->reserved = 0;
+  out->tiled = id < plan->P.n_leaves ? plan->P.leafdesc[id].tiled : 0;
   return TN_OK;
 }
 
@@ -478,6 +500,69 @@ tn_status tn_selftest_bounded_wait(tn_plan_t plan, int32_t arrive, int64_t limit
   return check_device_error(P);
 }
 
+tn_status tn_plan_check_staging(tn_plan_t plan, int64_t max_slices) {
+  if (!plan || max_slices < 1) {
+    set_error("tn_plan_check_staging: bad arguments");
+    return TN_ERR_INVALID;
+  }
+  const Plan& P = plan->P;
+  for (int32_t t = 0; t < P.n_leaves; ++t) {
+    const LeafDesc& d = P.leafdesc[t];
+    if (!d.tiled) continue;
+    const TensorRec& R = P.tensors[t];
+    int64_t src_elems = 1;
+    for (int32_t x : R.decl) src_elems *= P.extent[x];
+    const int64_t tiles = d.Pr * ((d.Po + 31) / 32) * ((d.Pi + 31) / 32);
+    if (tiles > 0x7fffffffll || d.Po * d.Pi * d.Pr != d.size) {
+      set_error("tiled staging of leaf " + std::to_string(t) + ": bad grid or group sizes");
+      return TN_ERR_INVALID;
+    }
+    const int64_t n_sid = d.batched ? std::min<int64_t>(P.n_slices, max_slices) : 1;
+    for (int64_t q = 0; q < n_sid; ++q) {
+      // slices 0, n-1, and evenly spread ones between
+      const int64_t sid = n_sid == 1 ? 0 : q * (P.n_slices - 1) / (n_sid - 1);
+      std::vector<char> seen(d.size, 0);
+      for (int64_t blk = 0; blk < tiles; ++blk) {
+        const TileBase tb = tile_base(d, blk, sid);
+        for (int ti = 0; ti < 32; ++ti) {
+          const int64_t gi = tb.gi0 + ti;
+          if (gi >= d.Pi) continue;
+          const int64_t row = tile_dst_row(d, tb, gi);
+          for (int to = 0; to < 32; ++to) {
+            const int64_t go = tb.go0 + to;
+            if (go >= d.Po) continue;
+            const int64_t so = tile_src(d, tb, gi, go), el = row + to;
+            // what the per-leaf kernel reads for staged element el
+            int64_t want = 0, e = el;
+            for (int r = d.rank - 1; r >= 0; --r) {
+              want += (e % d.ext[r]) * d.sstride[r];
+              e /= d.ext[r];
+            }
+            for (int k = 0; k < d.n_sl; ++k) want += ((sid / d.sl_div[k]) % d.sl_ext[k]) * d.sl_stride[k];
+            bool ok = el >= 0 && el < d.size && so == want && so >= 0 && so < src_elems && !seen[el];
+            if (ok && d.vec_load && (ti % 2) == 0) ok = so % 2 == 0 && tile_src(d, tb, gi + 1, go) == so + 1;
+            if (!ok) {
+              set_error("tiled staging of leaf " + std::to_string(t) + ": tile " + std::to_string(blk) +
+                        " entry (" + std::to_string(ti) + ", " + std::to_string(to) + ") maps source " +
+                        std::to_string(so) + " to element " + std::to_string(el) + " (expected source " +
+                        std::to_string(want) + ")");
+              return TN_ERR_INVALID;
+            }
+            seen[el] = 1;
+          }
+        }
+      }
+      for (int64_t el = 0; el < d.size; ++el)
+        if (!seen[el]) {
+          set_error("tiled staging of leaf " + std::to_string(t) + ": element " + std::to_string(el) +
+                    " is never written");
+          return TN_ERR_INVALID;
+        }
+    }
+  }
+  return TN_OK;
+}
+
 tn_status tn_cost_model_set(const tn_cost_model* m) {
   if (!m || !(m->hbm_bytes_per_s > 0) || !(m->simt_flops > 0) || !(m->tc_flops[0] > 0) ||
       !(m->tc_flops[1] > 0) || !(m->tc_flops[2] > 0)) {
@@ -556,7 +641,7 @@ tn_status tn_plan_profile_read(tn_plan_t plan, tn_profile* out, int32_t reset) {
     }
     P.prof_acc.launches[r.cls] += 1;
     if (P.prof_step_ms.size() != P.steps.size()) P.prof_step_ms.assign(P.steps.size(), 0.0);
-    P.prof_step_ms[r.step] += ms;
+    if (r.step >= 0) P.prof_step_ms[r.step] += ms;
     P.prof_acc.ms[r.cls] += ms;
     P.prof_acc.flops[r.cls] += r.flops;
     P.prof_acc.bytes[r.cls] += r.bytes;

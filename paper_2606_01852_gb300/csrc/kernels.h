@@ -39,8 +39,10 @@ struct StepArgs {
   float* part;                              // ksplit * nb * planes * m * n floats, or null
 };
 
-void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int64_t slice_begin,
-                         int32_t nb, bool only_batched, bool is_complex, ScaleRec* recs,
+// Small leaves: one CTA per leaf. Large leaves (LeafDesc::tiled): the tiled permutation
+// kernel, one launch per leaf; host_descs is the host copy of the table (grid sizes).
+void launch_stage_leaves(const LeafDesc* descs, const LeafDesc* host_descs, int32_t n_leaves, char* ws,
+                         int64_t slice_begin, int32_t nb, bool only_batched, bool is_complex, ScaleRec* recs,
                          const int32_t* rec_index, cudaStream_t st);
 // With a.ksplit > 1 each part of k goes to its own CTAs and a second kernel combines the
 // partial tiles (in part order) and writes C.

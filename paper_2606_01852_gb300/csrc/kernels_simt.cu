@@ -14,6 +14,7 @@
 
 #include "kernels.h"
 #include "split_bf16.cuh"
+#include "staging.cuh"
 
 namespace tn {
 
@@ -54,7 +55,7 @@ __global__ void stage_leaves_kernel(const LeafDesc* __restrict__ descs, char* __
                                     int32_t is_complex, ScaleRec* recs, const int32_t* rec_index,
                                     int32_t rec_batched_base) {
   const LeafDesc& d = descs[blockIdx.x];
-  if (only_batched && !d.batched) return;
+  if (d.tiled || (only_batched && !d.batched)) return;
   const int32_t copies = d.batched ? nb : 1;
   const int64_t total = d.size * copies;
   int lmax = -127;
@@ -98,12 +99,151 @@ __global__ void stage_leaves_kernel(const LeafDesc* __restrict__ descs, char* __
   }
 }
 
-void launch_stage_leaves(const LeafDesc* descs, int32_t n_leaves, char* ws, int64_t slice_begin,
-                         int32_t nb, bool only_batched, bool is_complex, ScaleRec* recs,
+// Tiled permutation of one large leaf (K-PERM): one CTA per (rest index, 32 x 32 tile of
+// output-group index x input-group index), blockIdx.y = batch copy. Loads run along the
+// input group (its fastest position is the declared order's innermost, so a warp reads
+// contiguous source addresses; two complex64 elements per 16-byte load where the stride
+// is 1 and the extent even), the tile goes through shared memory, and stores run along
+// the output group (contiguous in the staged copy: four FP32 values per 16-byte store and
+// plane, or eight BF16 values per plane in the split form). When the declared innermost
+// position is itself in the output group, loads run along the output group instead.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) stage_leaf_tiled_kernel(const LeafDesc* __restrict__ descs, int32_t leaf,
+                                                               char* __restrict__ ws, int64_t slice_begin,
+                                                               ScaleRec* recs, const int32_t* rec_index) {
+  const LeafDesc& d = descs[leaf];
+  __shared__ float tre[32][33];
+  __shared__ float tim[CPLX ? 32 : 1][33];
+  const int tid = threadIdx.x;
+  const int b = blockIdx.y;
+  const TileBase tb = tile_base(d, blockIdx.x, slice_begin + b);
+  const int64_t go0 = tb.go0, gi0 = tb.gi0;
+  int lmax = -127;
+  // ---- load the tile: tre[ti][to] = element (output-group go0 + to, input-group gi0 + ti)
+  if (CPLX && d.vec_load && (reinterpret_cast<uintptr_t>(d.src) & 15) == 0) {
+    const float4* src4 = reinterpret_cast<const float4*>(d.src);
+    const int ti = 2 * (tid & 15);
+    const int64_t gi = gi0 + ti;
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+      const int to = (tid >> 4) + 16 * rep;
+      const int64_t go = go0 + to;
+      if (gi < d.Pi && go < d.Po) {
+        // elements gi and gi + 1 differ in the fastest position only (gi even, extent even)
+        const int64_t so = tile_src(d, tb, gi, go);
+        const float4 v = src4[so >> 1];
+        tre[ti][to] = v.x;
+        tim[ti][to] = v.y;
+        tre[ti + 1][to] = v.z;
+        tim[ti + 1][to] = v.w;
+        lmax = max(lmax, exp_of(fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)))));
+      }
+    }
+  } else {
+    // one element per load; lanes along the input group, or along the output group when
+    // the declared innermost position is there
+    for (int rep = 0; rep < 4; ++rep) {
+      const int a0 = tid & 31, a1 = (tid >> 5) + 8 * rep;
+      const int ti = d.load_o ? a1 : a0, to = d.load_o ? a0 : a1;
+      const int64_t gi = gi0 + ti, go = go0 + to;
+      if (gi < d.Pi && go < d.Po) {
+        const int64_t so = tile_src(d, tb, gi, go);
+        if (CPLX) {
+          const float2 v = reinterpret_cast<const float2*>(d.src)[so];
+          tre[ti][to] = v.x;
+          tim[ti][to] = v.y;
+          lmax = max(lmax, exp_of(fmaxf(fabsf(v.x), fabsf(v.y))));
+        } else {
+          const float v = reinterpret_cast<const float*>(d.src)[so];
+          tre[ti][to] = v;
+          lmax = max(lmax, exp_of(fabsf(v)));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // ---- store: a row of the tile (fixed input-group index) is contiguous in the staged copy
+  const int np = CPLX ? 2 : 1;
+  float* base = reinterpret_cast<float*>(ws + d.dst) + int64_t(b) * np * d.size;
+  if (CPLX && d.split) {
+    // eight consecutive elements per thread and plane: 16-byte stores of BF16
+    const int q = tid & 3, ti = tid >> 2;
+    const int64_t gi = gi0 + ti;
+    if (ti < 32 && gi < d.Pi) {
+      const int64_t row = tile_dst_row(d, tb, gi);
+      const int to = 8 * q;
+      if (go0 + to + 7 < d.Po && ((row + to) & 7) == 0 && (d.size & 7) == 0) {
+        uint32_t hr[8], hi_[8], lr[8], li[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float vr = tre[ti][to + u], vi = tim[ti][to + u];
+          const __nv_bfloat16 a = __float2bfloat16_rn(vr), c = __float2bfloat16_rn(vi);
+          hr[u] = __bfloat16_as_ushort(a);
+          hi_[u] = __bfloat16_as_ushort(c);
+          lr[u] = __bfloat16_as_ushort(__float2bfloat16_rn(vr - __bfloat162float(a)));
+          li[u] = __bfloat16_as_ushort(__float2bfloat16_rn(vi - __bfloat162float(c)));
+        }
+        uint16_t* S = reinterpret_cast<uint16_t*>(base) + row + to;
+        auto pack = [](const uint32_t* x) {
+          return make_uint4(x[0] | (x[1] << 16), x[2] | (x[3] << 16), x[4] | (x[5] << 16), x[6] | (x[7] << 16));
+        };
+        *reinterpret_cast<uint4*>(S) = pack(hr);
+        *reinterpret_cast<uint4*>(S + d.size) = pack(hi_);
+        *reinterpret_cast<uint4*>(S + 2 * d.size) = pack(lr);
+        *reinterpret_cast<uint4*>(S + 3 * d.size) = pack(li);
+      } else {
+        for (int u = 0; u < 8; ++u)
+          if (go0 + to + u < d.Po) store_cplx(base, d.size, row + to + u, tre[ti][to + u], tim[ti][to + u], true);
+      }
+    }
+  } else {
+    // four consecutive FP32 values per thread and plane: 16-byte stores
+    const int q = tid & 7, ti = tid >> 3;
+    const int64_t gi = gi0 + ti;
+    if (gi < d.Pi) {
+      const int64_t row = tile_dst_row(d, tb, gi);
+      const int to = 4 * q;
+      if (go0 + to + 3 < d.Po && ((row + to) & 3) == 0 && (d.size & 3) == 0) {
+        *reinterpret_cast<float4*>(base + row + to) =
+            make_float4(tre[ti][to], tre[ti][to + 1], tre[ti][to + 2], tre[ti][to + 3]);
+        if (CPLX)
+          *reinterpret_cast<float4*>(base + d.size + row + to) =
+              make_float4(tim[ti][to], tim[ti][to + 1], tim[ti][to + 2], tim[ti][to + 3]);
+      } else {
+        for (int u = 0; u < 4; ++u)
+          if (go0 + to + u < d.Po) {
+            base[row + to + u] = tre[ti][to + u];
+            if (CPLX) base[d.size + row + to + u] = tim[ti][to + u];
+          }
+      }
+    }
+  }
+  if (recs) {
+    // exponent record of this copy: the largest exponent over the tiles (the records
+    // start at the atomicMax identity every pass)
+    for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    ScaleRec* rec = recs + rec_index[leaf] + (d.batched ? b : 0);
+    if ((tid & 31) == 0) atomicMax(&rec->emax, lmax);
+    if (blockIdx.x == 0 && tid == 0) rec->log2 = 0;
+  }
+}
+
+void launch_stage_leaves(const LeafDesc* descs, const LeafDesc* host_descs, int32_t n_leaves, char* ws,
+                         int64_t slice_begin, int32_t nb, bool only_batched, bool is_complex, ScaleRec* recs,
                          const int32_t* rec_index, cudaStream_t st) {
   if (n_leaves <= 0) return;
   stage_leaves_kernel<<<n_leaves, 128, 0, st>>>(descs, ws, slice_begin, nb, only_batched ? 1 : 0,
                                                 is_complex ? 1 : 0, recs, rec_index, 0);
+  for (int32_t t = 0; t < n_leaves; ++t) {
+    const LeafDesc& h = host_descs[t];
+    if (!h.tiled || (only_batched && !h.batched)) continue;
+    const int64_t tiles = h.Pr * ((h.Po + 31) / 32) * ((h.Pi + 31) / 32);
+    dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(h.batched ? nb : 1));
+    if (is_complex)
+      stage_leaf_tiled_kernel<true><<<grid, 256, 0, st>>>(descs, t, ws, slice_begin, recs, rec_index);
+    else
+      stage_leaf_tiled_kernel<false><<<grid, 256, 0, st>>>(descs, t, ws, slice_begin, recs, rec_index);
+  }
 }
 
 // ---------------------------------------------------------------------------------

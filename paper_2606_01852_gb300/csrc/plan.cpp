@@ -438,6 +438,50 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     for (int32_t x : R.decl)
       if (!is_sliced[x]) undecl.push_back(x);
     if (undecl != R.modes) ++leaf_permutes;
+    // tiled permutation groups (large leaves): output group = shortest suffix of the planned
+    // order holding >= 32 elements; input group = the declared order's fastest remaining
+    // positions up to >= 32 elements; the rest in planned order
+    {
+      int64_t ds = 1;
+      for (int i = d.rank - 1; i >= 0; --i) {
+        d.dstride[i] = ds;
+        ds *= d.ext[i];
+      }
+      d.tiled = (d.size >= kTiledLeafElems && d.rank >= 1) ? 1 : 0;
+      std::vector<char> in_o(d.rank, 0), in_i(d.rank, 0);
+      d.no = 0;
+      d.Po = 1;
+      for (int i = d.rank - 1; i >= 0 && d.Po < 32; --i) {
+        in_o[i] = 1;
+        d.Po *= d.ext[i];
+        ++d.no;
+      }
+      d.ni = 0;
+      d.Pi = 1;
+      std::vector<int> ip;  // fastest first
+      for (int j = (int)undecl.size() - 1; j >= 0 && d.Pi < 32; --j) {
+        const int pos = int(std::find(R.modes.begin(), R.modes.end(), undecl[j]) - R.modes.begin());
+        if (in_o[pos]) continue;
+        in_i[pos] = 1;
+        ip.push_back(pos);
+        d.Pi *= d.ext[pos];
+      }
+      d.ni = (int32_t)ip.size();
+      for (int q = 0; q < d.ni; ++q) d.ipos[q] = (int8_t)ip[d.ni - 1 - q];  // slowest first
+      d.nr = 0;
+      d.Pr = 1;
+      for (int i = 0; i < d.rank; ++i)
+        if (!in_o[i] && !in_i[i]) {
+          d.rpos[d.nr++] = (int8_t)i;
+          d.Pr *= d.ext[i];
+        }
+      const int inner = undecl.empty() ? -1
+                                       : int(std::find(R.modes.begin(), R.modes.end(), undecl.back()) -
+                                             R.modes.begin());
+      d.load_o = (inner >= 0 && in_o[inner]) ? 1 : 0;
+      d.vec_load = (!d.load_o && d.ni > 0 && d.sstride[d.ipos[d.ni - 1]] == 1 && d.ext[d.ipos[d.ni - 1]] % 2 == 0)
+                       ? 1 : 0;
+    }
   }
   // ---- statistics (Sec. II-B Eqs. 1-3, per slice; algorithmic flops and bytes)
   tn_plan_stats& S0 = P.stats;

@@ -39,7 +39,24 @@ struct LeafDesc {
   int64_t sl_div[kMaxSliced];      // slice id -> label value: (sid / div) % ext
   uint32_t sl_ext[kMaxSliced];
   int64_t sl_stride[kMaxSliced];   // source stride of that sliced label
+  // Tiled permutation (large leaves): the planned positions split into three groups --
+  // the output group (the trailing `no` planned positions, contiguous in the staged
+  // copy), the input group (ipos[0..ni-1], the fastest-varying positions of the declared
+  // order outside the output group, slowest first) and the rest (rpos[0..nr-1]). A CTA
+  // moves one 32 x 32 tile (output-group index x input-group index) through shared
+  // memory, reading along the input group and writing along the output group.
+  int32_t tiled;                   // staged by the tiled kernel (else by the per-leaf kernel)
+  int32_t no, ni, nr;
+  int32_t load_o;                  // the declared order's innermost position is in the
+                                   // output group: load along it instead
+  int32_t vec_load;                // input group's fastest position has source stride 1
+                                   // and an even extent: two elements per 16-byte load
+  int64_t Po, Pi, Pr;              // extents of the three groups
+  int8_t ipos[kMaxLeafRank], rpos[kMaxLeafRank];
+  int64_t dstride[kMaxLeafRank];   // stride of each planned position in the staged copy
 };
+// leaves of at least this many elements (per copy) are staged by the tiled kernel
+constexpr int64_t kTiledLeafElems = 2048;
 
 struct TensorRec {
   std::vector<int32_t> decl;   // declared modes (leaves only; incl. sliced)

@@ -51,9 +51,9 @@ def slice_partials(tn, w, prec, ids, batch):
     return np.array(got)
 
 
-def full_value(tn, w, prec):
+def full_value(tn, w, prec, expect_tc=True):
     plan = tn.Plan(w.net, w.path, w.sliced, prec=prec)
-    if prec != "fp32":
+    if prec != "fp32" and expect_tc:
         assert plan.info()["steps_per_class"][tn.TN_CLASS_TC] > 0
     out = torch.zeros((), dtype=torch.complex128, device="cuda")
     plan.contract(dev(w.net), out)
@@ -234,4 +234,4 @@ def test_rc40_unsliced_equals_sliced_sum(tn, prec):
 def test_rc12_full(tn):
     w = workloads.rc12()
     want = complex(*GOLD["rc12"]["value"])
-    assert abs(full_value(tn, w, "3xtf32") - want) / abs(want) < FP32_BAR
+    assert abs(full_value(tn, w, "3xtf32", expect_tc=False) - want) / abs(want) < FP32_BAR

@@ -31,6 +31,17 @@ def tn():
     return ensure_built()
 
 
+@pytest.fixture(autouse=True)
+def tensor_core_rates(tn):
+    """These tests exercise the tensor-core kernels on narrow and ragged tiles (down to a
+    quarter of the 128-column tile), which the Eq. 6 choice at the peak rates can hand to
+    the CUDA cores instead: the tensor-core rates are raised for the duration of a test."""
+    old = tn.binding.cost_model()
+    tn.binding.set_cost_model(old["hbm_bytes_per_s"], old["simt_flops"], [10 * f for f in old["tc_flops"]])
+    yield
+    tn.binding.set_cost_model(old["hbm_bytes_per_s"], old["simt_flops"], old["tc_flops"])
+
+
 def gemm_network(dims_m, dims_n, dims_k, out_order, seed=0, sliced_dim=None, vec_slice=None):
     """A[m..., k...] x B[n..., k...] with the open result in `out_order` (labels)."""
     rng = np.random.default_rng(seed)

@@ -93,3 +93,49 @@ def amplitude_network(rows: int, cols: int, cycles: int, seed: int, bitstring=No
                             gates=gates, open_qubits=tuple(open_qubits)))
     net.check()
     return net
+
+
+def state_network(n_qubits: int, n_gates: int, seed: int, shuffle: bool = True, extents=None,
+                  gate_pairs=None) -> Network:
+    """An n-qubit input state (a seeded complex Gaussian tensor, one large leaf) whose
+    declared mode order is a seeded permutation of its qubits when `shuffle`, followed by
+    `n_gates` Haar-random two-qubit gates on seeded qubit pairs (or `gate_pairs`); the
+    output is the final state with its qubits open in order. `extents` (per qubit) replaces
+    the qubit dimension 2 by other sizes (gates then act on dimension d0*d1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ext = list(extents) if extents is not None else [2] * n_qubits
+    b = _Builder()
+    wire = []
+    for q in range(n_qubits):
+        x = b.new_label()
+        b.extent[x] = ext[q]
+        wire.append(x)
+    order = list(rng.permutation(n_qubits)) if shuffle else list(range(n_qubits))
+    shape = tuple(ext[q] for q in order)
+    psi = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2.0)
+    b.add(psi, tuple(wire[q] for q in order))
+    pairs = gate_pairs if gate_pairs is not None else [
+        tuple(int(v) for v in rng.choice(n_qubits, size=2, replace=False)) for _ in range(n_gates)]
+    for (q0, q1) in pairs:
+        d = ext[q0] * ext[q1]
+        u = haar_unitary(rng, d).reshape(ext[q0], ext[q1], ext[q0], ext[q1])
+        o0, o1 = b.new_label(), b.new_label()
+        b.extent[o0], b.extent[o1] = ext[q0], ext[q1]
+        b.add(u, (o0, o1, wire[q0], wire[q1]))
+        wire[q0], wire[q1] = o0, o1
+    net = Network(b.tensors, b.modes, b.extent, tuple(wire),
+                  name=f"state_{n_qubits}q_g{len(pairs)}_s{seed}" + ("_shuf" if shuffle else ""),
+                  meta=dict(n_qubits=n_qubits, seed=seed, order=order, pairs=pairs))
+    net.check()
+    return net
+
+
+def state_path(net: Network):
+    """The state-vector order for state_network: the state absorbs the gates one by one."""
+    from .network import Path
+    pairs, cur = [], 0
+    n = len(net.modes)
+    for g in range(1, n):
+        pairs.append((cur, g))
+        cur = n + g - 1
+    return Path(pairs)

@@ -21,6 +21,8 @@
   khex45    : kicked Ising, same couplings, on a 4x5 honeycomb lattice (brick-wall form),
               6 Trotter steps;
   ktri44    : kicked Ising on a 4x4 triangular lattice, 8 Trotter steps;
+  sv26      : a 2^26-element state leaf in a shuffled declared order absorbing 4 gates (the
+              large-leaf permutation case);
   kings16   : maximum independent set of a 16x16 King's subgraph (site density 0.8, seed 1;
               209 vertices), contracted in the max-plus semiring (FP32, exact integers);
   kings_batch: maximum independent sets of many King's subgraphs (L in [4, 7], density 0.8),
@@ -136,6 +138,15 @@ def rc40open():
     return random_circuit(5, 8, 13, 40, n_sliced=8, open_qubits=RC40_OPEN)
 
 
+@functools.lru_cache(maxsize=None)
+def sv26():
+    """A 26-qubit state (one 2^26-element leaf, 512 MiB in complex64) declared in a shuffled
+    qubit order, absorbing four Haar-random two-qubit gates; the open output is the new
+    state in qubit order. Its leaf is the permutation the staging kernel exists for."""
+    net = circuits.state_network(26, 4, 26)
+    return Workload(net.name, net, circuits.state_path(net), (), {})
+
+
 def kising44():
     return kicked(4, 10)
 
@@ -192,4 +203,4 @@ def kings_batch(count, seed=5):
 
 BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40c14": rc40c14, "rc40c14sub": rc40c14sub, "rc40u": rc40u, "kising44": kising44, "kising55": kising55,
            "rc40open": rc40open,
-           "khex45": khex45, "ktri44": ktri44, "kings16": kings16}
+           "khex45": khex45, "ktri44": ktri44, "kings16": kings16, "sv26": sv26}
