@@ -10,7 +10,7 @@
 namespace tn {
 
 constexpr int kMaxDims = 12;     // merged output-offset dims per GEMM side
-constexpr int kMaxLeafRank = 24; // planned rank of a leaf the staging kernel handles
+constexpr int kMaxLeafRank = 32; // planned rank of a leaf the staging kernels handle
 constexpr int kMaxSliced = 24;   // sliced labels carried by one leaf
 
 // Maps a GEMM row (or column) index to an output offset: the index is read as

@@ -64,3 +64,11 @@ def test_large_leaf_2_to_20(tn):
     net = circuits.state_network(20, 2, 11)
     plan = plan_of(tn, net, prec="bf16x3")
     plan.check_staging()
+
+
+def test_large_leaf_2_to_26(tn):
+    """The size of the GPU staging test and of the sv26 benchmark leaf (rank 26)."""
+    net = circuits.state_network(26, 3, 26)
+    plan = plan_of(tn, net)
+    assert plan.tensor(0)["tiled"] == 1
+    plan.check_staging()
