@@ -60,9 +60,11 @@ WORKLOAD_DESC = {
                 "16 correlated amplitudes per contraction, greedy path, 8 sliced labels (256 slices), "
                 "complex64",
 }
-PREC = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
+PREC = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x3m": 3}
+# forms run with the 3M complex product (three real products per complex MAC, not four)
+THREE_M = {"bf16x3m"}
 # arithmetic of each form (complex64 storage; products as named, FP32 accumulation)
-DTYPE_NAME = {"fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16x3": "bf16x3"}
+DTYPE_NAME = {"fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16x3": "bf16x3", "bf16x3m": "bf16x3 (3M)"}
 # DRAM bytes (read + write) per launch of the dominant kernel, averaged over its launches,
 # from the ncu launch-list capture of this same command (profiles/launches_rc40_*.md).
 # Only valid for the kernel build the capture was taken on: drop an entry when it changes.
@@ -166,7 +168,11 @@ def form_peaks(peaks):
     tf32 = tf * 1e12 if tf else bf * NOMINAL_TF32_PER_BF16
     ff = peaks.get("ffma_tflops_sustained")
     alu = ff * 1e12 if ff else SM_COUNT * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
-    return {"tc": {1: tf32, 2: tf32 / 3.0, 3: bf / 3.0}, "alu": alu, "maxplus": alu / 2.0,
+    # per form: algorithmic flops (8 per complex MAC) per hardware flop -- 4M: 4 real products
+    # (8 flops) per complex MAC, 3xTF32 / BF16x3 three per real product; 3M: 3 real products
+    tc = {"tf32": tf32, "3xtf32": tf32 / 3.0, "bf16x3": bf / 3.0, "bf16x3m": bf * 8.0 / 18.0}
+    tc.update({1: tc["tf32"], 2: tc["3xtf32"], 3: tc["bf16x3"]})
+    return {"tc": tc, "alu": alu, "maxplus": alu / 2.0,
             "source": {"tc_bf16": peaks["_source"], "tf32": "measured here" if tf else "derived (nominal ratio)",
                        "alu": "measured here" if ff else "derived (max clock)"}}
 
@@ -257,7 +263,7 @@ def oracle_sample(w, budget_s, slice_id=0):
     return flops, time.perf_counter() - t0, done
 
 
-def path_roofline(plan, prec, semiring, peaks, ms_per_step, cplx=True, count=None):
+def path_roofline(plan, prec, semiring, peaks, ms_per_step, cplx=True, count=None, form=None):
     """The path's roofline time: over the steps of one contraction (all slices, or the
     `count` slices a step contracts), the sum of
     t_roof = max(bytes / B, flops / F) -- Eq. 6 of Sec. IV-C with this GPU's measured
@@ -272,7 +278,7 @@ def path_roofline(plan, prec, semiring, peaks, ms_per_step, cplx=True, count=Non
     e, fm = (8.0, 8.0) if cplx else (4.0, 2.0)
     hbm = peaks["hbm_gbs"] * 1e9
     fp = form_peaks(peaks)
-    tc_peak = fp["tc"].get(prec)
+    tc_peak = fp["tc"].get(form if form is not None else prec)
     alu = fp["maxplus"] if semiring == "maxplus" else fp["alu"]
     total = 0.0
     for s in range(info["n_steps"]):
@@ -361,12 +367,15 @@ def run_ours(args):
     cplx = w.net.is_complex
     # real networks (the max-plus workloads) run the R32 FP32 form
     prec = PREC[args.prec] if cplx else tn.TN_R32_FP32_SIMT
+    cmult = 3 if (cplx and args.prec in THREE_M) else 4
+    form = args.prec if cplx else "fp32"
     n_sl = w.n_slices
     per_step = args.slices_per_step or SLICES_PER_STEP.get(args.workload, n_sl)
     per_step = max(1, min(per_step, n_sl))
     # a slice-batched step runs its slices in one pass unless told otherwise
     batch = args.max_slice_batch or (per_step if per_step < n_sl else 0)
-    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=batch, semiring=semiring)
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=batch, semiring=semiring,
+                   complex_mult=cmult)
     info = plan.info()
     stream = torch.cuda.current_stream()
     # step j contracts slices [j * per_step, (j + 1) * per_step) modulo n_slices
@@ -437,7 +446,11 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     elif cls == 2:
         achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": fpk["tc"][prec] / 1e12, "unit": "TFLOP/s"}
+        roof = {"bound": "tensor", "achieved": achieved, "peak": fpk["tc"][form] / 1e12, "unit": "TFLOP/s"}
+        if form == "bf16x3m":
+            # the 4M form's peak for comparison (the 3M form does 3/4 of its tensor work)
+            roof["peak_4m"] = fpk["tc"]["bf16x3"] / 1e12
+            roof["frac_of_4m_peak"] = achieved / roof["peak_4m"]
     else:
         alu = (fpk["maxplus"] if semiring == "maxplus" else fpk["alu"]) / 1e12
         achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
@@ -451,7 +464,7 @@ def run_ours(args):
     roof["share_of_step"] = prof["ms"][cls] / sum(prof["ms"])
     roof["peak_source"] = {1: fpk["source"]["tf32"], 2: fpk["source"]["tf32"], 3: fpk["source"]["tc_bf16"]}.get(
         prec, fpk["source"]["alu"]) if cls == 2 else (peaks["_source"] if cls in (1, 3, 4) else fpk["source"]["alu"])
-    path_roof = path_roofline(plan, prec, semiring, peaks, ms_max, cplx, count=round(slices_per_step))
+    path_roof = path_roofline(plan, prec, semiring, peaks, ms_max, cplx, count=round(slices_per_step), form=form)
     perm = None
     if prof["launches"][4] > 0 and prof["ms"][4] > 0:
         # leaf staging (the permutation kernels): staged bytes read + written over its event time

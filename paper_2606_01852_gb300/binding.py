@@ -22,7 +22,9 @@ STATUS_NAMES = ["TN_OK", "TN_ERR_INVALID", "TN_ERR_UNSUPPORTED", "TN_ERR_OOM", "
 # tn_precision
 TN_C64_FP32_SIMT, TN_C64_TF32, TN_C64_3XTF32, TN_C64_BF16X3, TN_R32_FP32_SIMT, TN_R32_TF32, \
     TN_R32_3XTF32, TN_R32_BF16X3 = range(8)
-PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
+PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x3m": 3}
+# forms named with the 3M complex product (three real products per complex MAC)
+THREE_M = {"bf16x3m"}
 TN_PLAN_HOST_ONLY = 1
 TN_CLASS_SIMT, TN_CLASS_STREAM, TN_CLASS_TC, TN_CLASS_SPLITK, TN_CLASS_PERM = range(5)
 N_CLASSES = 5
@@ -191,13 +193,17 @@ def _ptr(x):
 SEMIRINGS = {"standard": 0, "maxplus": 1}
 
 
-def make_policy(prec=TN_C64_FP32_SIMT, exp_scaling=False, max_slice_batch=0, host_only=False, semiring="standard"):
+def make_policy(prec=TN_C64_FP32_SIMT, exp_scaling=False, max_slice_batch=0, host_only=False, semiring="standard",
+                complex_mult=4):
+    """prec: a tn_precision or a form name ("bf16x3m" = BF16X3 with the 3M product)."""
     if isinstance(prec, str):
+        if prec in THREE_M:
+            complex_mult = 3
         prec = PREC_NAMES[prec]
     p = tn_dtype_policy()
     p.semiring = SEMIRINGS[semiring]
     p.prec = int(prec)
-    p.complex_mult = 4
+    p.complex_mult = int(complex_mult)
     p.exp_scaling = 1 if exp_scaling else 0
     p.max_slice_batch = int(max_slice_batch)
     p.flags = TN_PLAN_HOST_ONLY if host_only else 0
@@ -230,13 +236,13 @@ class Plan:
     `path` is a list of SSA pairs or an object with .pairs."""
 
     def __init__(self, net, path, sliced=(), prec=TN_C64_FP32_SIMT, exp_scaling=False,
-                 max_slice_batch=0, host_only=False, semiring="standard"):
+                 max_slice_batch=0, host_only=False, semiring="standard", complex_mult=4):
         pairs = path.pairs if hasattr(path, "pairs") else path
         self._arr = _NetArrays([tuple(m) for m in net.modes], dict(net.extent), tuple(net.open_modes),
                                pairs)
         sl = list(sliced)
         self._sl = (C.c_int32 * max(1, len(sl)))(*sl)
-        self.policy = make_policy(prec, exp_scaling, max_slice_batch, host_only, semiring)
+        self.policy = make_policy(prec, exp_scaling, max_slice_batch, host_only, semiring, complex_mult)
         self.is_complex = self.policy.prec <= TN_C64_BF16X3
         self.n_leaves = len(net.modes)
         self.n_open = len(net.open_modes)

@@ -45,16 +45,18 @@ StepArgs step_args(const Plan& P, const StepRec& st) {
   a.a_plane = A.size;
   a.b_plane = B.size;
   a.c_plane = C.size;
-  a.a_bstride = A.batched ? np * A.size : 0;
-  a.b_bstride = B.batched ? np * B.size : 0;
-  a.c_bstride = C.batched ? np * C.size : 0;
+  // floats per element of each stored copy: 1 real, 2 complex, 3 in the 3M split form
+  const auto fl = [&](const TensorRec& R) { return np == 1 ? int64_t(1) : (R.split == 2 ? int64_t(3) : int64_t(2)); };
+  a.a_bstride = A.batched ? fl(A) * A.size : 0;
+  a.b_bstride = B.batched ? fl(B) * B.size : 0;
+  a.c_bstride = C.batched ? fl(C) * C.size : 0;
   a.rows = st.rows;
   a.cols = st.cols;
   a.recs = P.policy.exp_scaling ? reinterpret_cast<ScaleRec*>(P.dev + P.off_scale) : nullptr;
   a.rec_a = P.rec_index[st.a];
   a.rec_b = P.rec_index[st.b];
   a.rec_c = P.rec_index[st.out];
-  a.c_split = C.split ? 1 : 0;
+  a.c_split = C.split;
   a.maxplus = P.policy.semiring == TN_SEMIRING_MAXPLUS ? 1 : 0;
   a.ksplit = st.ksplit;
   a.part = st.ksplit > 1 ? reinterpret_cast<float*>(P.dev + P.off_scratch) : nullptr;
@@ -182,7 +184,9 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
         TN_CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(pr.e0), st));
       }
       if (sr.cls == TN_CLASS_TC) {
-        TN_CUDA_TRY(launch_contract_tc(a, nbs, P.policy.prec, cplx, errw, st));
+        const int32_t form = (P.policy.prec == TN_C64_BF16X3 && P.policy.complex_mult == 3) ? kPrecBF16x3M
+                                                                                              : P.policy.prec;
+        TN_CUDA_TRY(launch_contract_tc(a, nbs, form, cplx, errw, st));
       } else if (sr.cls == TN_CLASS_STREAM) {
         launch_contract_stream(a, nbs, cplx, P.num_sms, st);
       } else if (sr.cls == TN_CLASS_SPLITK) {
@@ -370,7 +374,7 @@ tn_status tn_plan_tensor(tn_plan_t plan, int32_t id, tn_tensor_info* out) {
   out->pinned = R.pinned ? 1 : 0;
   out->producer = R.producer;
   out->consumer = R.consumer;
-  out->format = R.split ? TN_FORMAT_SPLIT_BF16 : TN_FORMAT_PLANAR;
+  out->format = R.split;
   out->tiled = id < plan->P.n_leaves ? plan->P.leafdesc[id].tiled : 0;
   return TN_OK;
 }

@@ -187,12 +187,13 @@ __device__ __forceinline__ void store_halves(uint16_t* d, const uint32_t (&x)[V]
 }
 
 // V consecutive elements (V = 1, 2, 4, 8) of an address-ordered run: Re values re[],
-// Im values im[], stored at element `off` of a tensor copy that starts at C, planar FP32
-// or split BF16, one vector store per plane (off and the planes are V-aligned).
+// Im values im[], stored at element `off` of a tensor copy that starts at C, in storage
+// mode fmt (planar FP32, split BF16, or split BF16 with the 3M sum planes), one vector
+// store per plane (off and the planes are V-aligned).
 template <int V>
 __device__ __forceinline__ void store_run(float* C, int64_t plane, int64_t off, const float* re, const float* im,
-                                          bool split) {
-  if (!split) {
+                                          int fmt) {
+  if (fmt == kFmtPlanar) {
     if constexpr (V == 1) {
       C[off] = re[0];
       C[plane + off] = im[0];
@@ -208,28 +209,47 @@ __device__ __forceinline__ void store_run(float* C, int64_t plane, int64_t off, 
     }
     return;
   }
-  // split: hi = RN_bf16(v), lo = RN_bf16(v - hi); planes re_hi, im_hi, re_lo, im_lo
+  // hi = RN_bf16(v), lo = RN_bf16(v - hi) of re, im (and s = re + im in the 3M form)
   uint32_t hr[V], hi_[V], lr[V], li[V];
 #pragma unroll
   for (int u = 0; u < V; ++u) {
-    const __nv_bfloat16 a = __float2bfloat16_rn(re[u]), b = __float2bfloat16_rn(im[u]);
+    __nv_bfloat16 a, b, c, d;
+    split_pair(re[u], a, c);
+    split_pair(im[u], b, d);
     hr[u] = __bfloat16_as_ushort(a);
     hi_[u] = __bfloat16_as_ushort(b);
-    lr[u] = __bfloat16_as_ushort(__float2bfloat16_rn(re[u] - __bfloat162float(a)));
-    li[u] = __bfloat16_as_ushort(__float2bfloat16_rn(im[u] - __bfloat162float(b)));
+    lr[u] = __bfloat16_as_ushort(c);
+    li[u] = __bfloat16_as_ushort(d);
   }
   uint16_t* S = reinterpret_cast<uint16_t*>(C) + off;
+  if (fmt == kFmtSplit) {
+    store_halves<V>(S, hr);
+    store_halves<V>(S + plane, hi_);
+    store_halves<V>(S + 2 * plane, lr);
+    store_halves<V>(S + 3 * plane, li);
+    return;
+  }
+  uint32_t hs[V], ls[V];
+#pragma unroll
+  for (int u = 0; u < V; ++u) {
+    __nv_bfloat16 a, c;
+    split_pair(re[u] + im[u], a, c);
+    hs[u] = __bfloat16_as_ushort(a);
+    ls[u] = __bfloat16_as_ushort(c);
+  }
   store_halves<V>(S, hr);
-  store_halves<V>(S + plane, hi_);
-  store_halves<V>(S + 2 * plane, lr);
+  store_halves<V>(S + plane, lr);
+  store_halves<V>(S + 2 * plane, hi_);
   store_halves<V>(S + 3 * plane, li);
+  store_halves<V>(S + 4 * plane, hs);
+  store_halves<V>(S + 5 * plane, ls);
 }
 
 // The address-ordered stores of one block, lanes taking V = 2^VB consecutive addresses.
 // e[k], src[k]: the k-th smallest bit weight (log2) and which bit of r (0-4) or c (5-9)
 // carries it; the VB smallest weights are 1, 2, ..., 2^(VB-1).
 template <int VB>
-__device__ __forceinline__ void store_sorted(float* C, int64_t plane, bool split, const float* t, int pitch, int cs,
+__device__ __forceinline__ void store_sorted(float* C, int64_t plane, int split, const float* t, int pitch, int cs,
                                              int64_t base, const int* e, const int* src, int lane) {
   constexpr int V = 1 << VB;
   // r and c take disjoint bits, so t's index r * pitch + c is a sum of one increment per
@@ -282,7 +302,7 @@ __device__ __forceinline__ void store_sorted(float* C, int64_t plane, bool split
 // the following weights continue the sequence (interleaved row/column layouts included).
 // Otherwise (ragged block, other extents) it falls back to one row per store. ro / co:
 // this lane's row / column offset; row_ok / col_ok: in range.
-__device__ __forceinline__ void store_block(float* C, int64_t plane, bool split, const float* t, int pitch,
+__device__ __forceinline__ void store_block(float* C, int64_t plane, int split, const float* t, int pitch,
                                             int cs, int64_t ro, int64_t co, bool row_ok, bool col_ok, int lane) {
   const int64_t ro0 = __shfl_sync(0xffffffffu, ro, 0), co0 = __shfl_sync(0xffffffffu, co, 0);
   // log2 of each bit's weight (bits 0-4: row, 5-9: column); -1 if not a power of two
@@ -520,7 +540,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       __syncwarp();
       const int64_t n = nb0 + lane;
       const bool col_ok = ok && n < a.n;
-      store_block(C, a.c_plane, false, tr, 33, 32 * 33, ro, col_ok ? map_off(a.cols, n) : 0, row_ok, col_ok, lane);
+      store_block(C, a.c_plane, kFmtPlanar, tr, 33, 32 * 33, ro, col_ok ? map_off(a.cols, n) : 0, row_ok, col_ok,
+                  lane);
       __syncwarp();
     }
   }
@@ -1042,7 +1063,7 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
     const bool row_ok = ok && m < a.m;
     const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
-    const bool split = a.c_split != 0;
+    const int split = a.c_split;
     // The stage buffers are free here: the last fold waited for the final MMA, which
     // consumed every staged tile; no TMA load is outstanding.
     // this warp's 32 x 64 results, Re then Im, rows of 65 floats: the registers are free
@@ -1066,6 +1087,219 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CB::COLS));
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// BF16x3 form with the 3M complex product (Gauss): with s = a_re + a_im and t = b_re + b_im,
+//   P1 = a_re.b_re,  P2 = a_im.b_im,  P3 = s.t;   Re = P1 - P2,  Im = P3 - P1 - P2,
+// three real products per complex MAC instead of four, each as hi.hi + hi.lo + lo.hi of
+// the BF16 halves: 9 MMAs (128 x 128 x 16) per 16-deep k-atom instead of 12. The operands
+// arrive in the 3M split form (split_bf16.cuh: [re_h | re_l | im_h | im_l | s_h | s_l], the
+// sums written by the producers), so one product's two planes of one operand are one TMA
+// box. The ring holds (k-block, product) slots of [A_h | A_l | B_h | B_l] (32 deep, 32 KiB);
+// product j accumulates in tensor-memory columns 128 j. The three accumulators are
+// folded into round-to-nearest register totals of Re and Im every CK k-blocks (256 terms),
+// as in contract_tcb_kernel; the MMAs of the next chunk wait for the fold. Warps: 0 TMA,
+// 1 MMA + TMEM, 2-9 fold / epilogue (320 threads).
+struct CB3 {
+  static constexpr int BK = 32, ROWB = 64, CK = 8;
+  static constexpr int PLANE = BM * ROWB;                   // 8 KiB
+  static constexpr int OFF_B = 2 * PLANE;
+  static constexpr int SLOT = 4 * PLANE;                    // 32 KiB: [A_h | A_l | B_h | B_l]
+  static constexpr int SLOTS = 6;                           // two k-blocks of three products
+  static constexpr int THREADS = 320;
+  static constexpr int SMEM = SLOTS * SLOT + 1024 + 1024;
+  static constexpr uint32_t COLS = 512;                     // P1 @0, P2 @128, P3 @256
+};
+static_assert(CB3::SMEM <= 232448, "shared memory per CTA");
+static_assert(8 * 2 * 32 * 65 * 4 <= CB3::SLOTS * CB3::SLOT, "epilogue transposes fit the ring");
+
+// 16 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(CB3::THREADS, 1)
+    contract_tcb3m_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                          StepArgs a, int* err) {
+  constexpr int SLOTS = CB3::SLOTS, BK = CB3::BK, ROWB = CB3::ROWB, CK = CB3::CK;
+  constexpr int PLANE = CB3::PLANE, SLOT = CB3::SLOT;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SLOTS * SLOT);
+  uint64_t* full = bars;                 // [SLOTS]
+  uint64_t* empty = bars + SLOTS;        // [SLOTS]
+  uint64_t* acc_full = bars + 2 * SLOTS;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
+  const int64_t t = blockIdx.x;
+  const int64_t per_group = GROUP_M * tiles_n;
+  const int64_t first_m = (t / per_group) * GROUP_M;
+  const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
+  const int64_t tm = first_m + (t % per_group) % gm, tn = (t % per_group) / gm;
+  const int m0 = static_cast<int>(tm * BM), n0 = static_cast<int>(tn * BN);
+  const int b = blockIdx.y;
+  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);
+  const int n_chunks = (num_kb + CK - 1) / CK;
+  const int pa = a.a_bstride ? 6 * b : 0, pb = a.b_bstride ? 6 * b : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SLOTS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 8);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(CB3::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int n_items = 3 * num_kb;  // (k-block, product) slots in order
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < n_items; ++it) {
+        const int s = it % SLOTS;
+        if (!mbar_wait(&empty[s], ((it / SLOTS) & 1) ^ 1)) {
+          atomicExch(err, 31);
+          break;
+        }
+        mbar_expect_tx(&full[s], SLOT);
+        uint8_t* st = smem + s * SLOT;
+        const int k0 = (it / 3) * BK, j = it % 3;
+        tma_load_3d(st, &tmA, &full[s], k0, m0, pa + 2 * j);
+        tma_load_3d(st + CB3::OFF_B, &tmB, &full[s], k0, n0, pb + 2 * j);
+        issued = it + 1;
+      }
+      for (int it = issued > SLOTS ? issued - SLOTS : 0; it < issued; ++it)
+        if (!mbar_wait(&full[it % SLOTS], (it / SLOTS) & 1)) atomicExch(err, 32);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t id_n = idesc_bf16(BM, BN);
+      bool ok = true;
+      for (int c = 0; c < n_chunks && ok; ++c) {
+        const int kb_end = min(num_kb, (c + 1) * CK);
+        for (int kb = c * CK; kb < kb_end && ok; ++kb) {
+          for (int j = 0; j < 3; ++j) {
+            const int it = 3 * kb + j, s = it % SLOTS;
+            if (!mbar_wait(&full[s], (it / SLOTS) & 1)) {
+              atomicExch(err, 33);
+              ok = false;
+              break;
+            }
+            if (kb == c * CK && j == 0) {
+              // the accumulators must have been folded before this chunk overwrites them
+              if (!mbar_wait(acc_empty, (c & 1) ^ 1)) {
+                atomicExch(err, 34);
+                ok = false;
+                mma_commit(&empty[s]);
+                break;
+              }
+            }
+            fence_after();
+            const uint32_t sa = su32(smem + s * SLOT), sb = sa + CB3::OFF_B;
+            const uint32_t d = tmem + 128 * j;
+#pragma unroll
+            for (int q = 0; q < BK / 16; ++q) {
+              const uint32_t o = q * 32;
+              const uint64_t ah = smem_desc<ROWB>(sa + o), al = smem_desc<ROWB>(sa + PLANE + o);
+              const uint64_t bh = smem_desc<ROWB>(sb + o), bl = smem_desc<ROWB>(sb + PLANE + o);
+              const uint32_t acc = (kb > c * CK || q > 0) ? 1u : 0u;
+              mma_bf16(d, ah, bh, id_n, acc);   // hi.hi
+              mma_bf16(d, ah, bl, id_n, 1u);    // hi.lo
+              mma_bf16(d, al, bh, id_n, 1u);    // lo.hi
+            }
+            mma_commit(&empty[s]);
+          }
+        }
+        mma_commit(acc_full);  // also on error, so the fold sees issued MMAs retire
+      }
+    }
+  } else {
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    float run_re[64], run_im[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) run_re[i] = run_im[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < n_chunks && ok; ++c) {
+      if (!mbar_wait(acc_full, c & 1)) {
+        atomicExch(err, 35);
+        ok = false;
+        break;
+      }
+      fence_after();
+      float v1[16], v2[16];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const uint32_t col = lane_base + half * 64 + p * 16;
+        tmem_ld16(tmem + col, v1);
+        tmem_ld16(tmem + 128 + col, v2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          run_re[p * 16 + i] += v1[i] - v2[i];
+          v1[i] += v2[i];  // P1 + P2
+        }
+        tmem_ld16(tmem + 256 + col, v2);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) run_im[p * 16 + i] += v2[i] - v1[i];
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+    }
+    // epilogue: thread = TMEM lane (row); this warp's 64 columns
+    const int row = q * 32 + lane;
+    const int64_t m = static_cast<int64_t>(m0) + row;
+    const bool row_ok = ok && m < a.m;
+    const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
+    float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
+    const int split = a.c_split;
+    // The ring is free here: the last fold waited for the final MMA, which consumed every
+    // staged slot; no TMA load is outstanding.
+    float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 65;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      tr[lane * 65 + j] = run_re[j];
+      tr[32 * 65 + lane * 65 + j] = run_im[j];
+    }
+    __syncwarp();
+    for (int cb = 0; cb < 2; ++cb) {
+      const int64_t n = static_cast<int64_t>(n0) + half * 64 + cb * 32 + lane;
+      const bool col_ok = ok && n < a.n;
+      store_block(C, a.c_plane, split, tr + cb * 32, 65, 32 * 65, ro, col_ok ? map_off(a.cols, n) : 0, row_ok,
+                  col_ok, lane);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CB3::COLS));
   }
 }
 
@@ -1219,7 +1453,7 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
     const int q4 = warp & 3, half = (warp - 2) >> 2;
     const uint32_t lane_base = static_cast<uint32_t>(q4 * 32) << 16;
     float* tr = epi + (warp - 2) * 2 * 32 * 33;  // this warp's Re and Im transpose blocks
-    const bool split = a.c_split != 0;
+    const int split = a.c_split;
     int64_t q = 0;  // tiles folded
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++q) {
       const TileCoord tc = tile_of(w, tiles_m, tiles_n);
@@ -1323,6 +1557,43 @@ bool make_map_split(CUtensorMap* map, const float* base, int64_t rows, int64_t k
   return r == CUDA_SUCCESS;
 }
 
+// 3-D map over a 3M split-BF16 operand: (k, rows, plane), plane = 6*copy + {re_h, re_l,
+// im_h, im_l, s_h, s_l}; box 32 x rows x 2 planes (one product's hi and lo), 64-byte swizzle.
+bool make_map_split3m(CUtensorMap* map, const float* base, int64_t rows, int64_t k, int64_t copies,
+                      int64_t plane_elems, int box_rows) {
+  auto enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows),
+                        static_cast<cuuint64_t>(6 * copies)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(k * 2), static_cast<cuuint64_t>(plane_elems * 2)};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(CB3::BK), static_cast<cuuint32_t>(box_rows), 2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<float*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_tcb3m(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(contract_tcb3m_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB3::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  CUtensorMap ta, tb;
+  const int64_t ca = a.a_bstride ? static_cast<int64_t>(nb) : 1;
+  const int64_t cb = a.b_bstride ? static_cast<int64_t>(nb) : 1;
+  if (!make_map_split3m(&ta, a.A, a.m, a.k, ca, a.a_plane, BM) ||
+      !make_map_split3m(&tb, a.B, a.n, a.k, cb, a.b_plane, BN))
+    return cudaErrorInvalidValue;
+  const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
+  dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));
+  contract_tcb3m_kernel<<<grid, CB3::THREADS, CB3::SMEM, st>>>(ta, tb, a, err);
+  return cudaGetLastError();
+}
+
 template <int SPLIT>
 cudaError_t launch_split(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
   static bool configured = false;
@@ -1419,6 +1690,7 @@ bool tc_step_ok(int64_t m, int64_t n, int64_t k, int32_t prec) {
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
                                cudaStream_t st) {
   if (!cplx || a.recs) return cudaErrorNotSupported;
+  if (prec == kPrecBF16x3M) return launch_tcb3m(a, nb, err, st);
   if (prec == TN_C64_TF32) return launch_split<1>(a, nb, err, st);
   if (prec == TN_C64_3XTF32) return launch_tc3(a, nb, err, st);
   if (prec == TN_C64_BF16X3) return launch_tcb(a, nb, err, st);

@@ -21,8 +21,10 @@ struct ScaleRec {
 // One pairwise step C[b] = A[b] (m x k, row-major) . B[b] (n x k, row-major)^T.
 // Planar complex: the imaginary plane of each tensor copy follows its real plane at
 // +*_plane floats. C is written at rows(m) + cols(n). Batch strides are 0 for tensors
-// that do not depend on a sliced label. With c_split, C is written as the four BF16
-// planes of the split form (split_bf16.cuh): the operand layout of a BF16x3 step.
+// that do not depend on a sliced label. c_split is C's storage mode (split_bf16.cuh):
+// planar FP32, the four BF16 planes of the split form (the operand layout of a 4M BF16x3
+// step) or the six planes of the 3M split form; batch strides count floats (2 or 3 per
+// complex element).
 struct StepArgs {
   const float* A;
   const float* B;
@@ -33,7 +35,7 @@ struct StepArgs {
   OffsetMap rows, cols;
   ScaleRec* recs;                           // null: no exponent scaling
   int32_t rec_a, rec_b, rec_c;
-  int32_t c_split;                          // 1: write C in the split-BF16 form (complex)
+  int32_t c_split;                          // C's storage mode: 0 planar, 1 split, 2 split 3M
   int32_t maxplus;                          // 1: (max, +) semiring (real, unscaled)
   int32_t ksplit;                           // SIMT: k cut in ksplit parts (partials in `part`)
   float* part;                              // ksplit * nb * planes * m * n floats, or null
@@ -69,7 +71,9 @@ void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* ou
 // tensor-core path (tcgen05); returns false if the step cannot take it
 bool tc_supported();
 cudaError_t launch_bounded_wait_selftest(int arrive, uint64_t limit_ns, int* err, cudaStream_t st);
-// A and B of a BF16X3 step are in the split-BF16 form.
+// A and B of a BF16X3 step are in the split-BF16 form; prec = kPrecBF16x3M selects the 3M
+// kernel (operands in the 3M split form).
+constexpr int32_t kPrecBF16x3M = 103;
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
                                cudaStream_t st);
 

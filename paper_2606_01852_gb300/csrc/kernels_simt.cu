@@ -73,8 +73,8 @@ __global__ void stage_leaves_kernel(const LeafDesc* __restrict__ descs, char* __
     const int64_t el = i - b * d.size;
     if (is_complex) {
       const float2 v = reinterpret_cast<const float2*>(d.src)[src];
-      float* dst = reinterpret_cast<float*>(ws + d.dst) + b * 2 * d.size;
-      store_cplx(dst, d.size, el, v.x, v.y, d.split != 0);
+      float* dst = reinterpret_cast<float*>(ws + d.dst) + b * cplx_floats(d.split) * d.size;
+      store_cplx(dst, d.size, el, v.x, v.y, d.split);
       if (recs) lmax = max(lmax, exp_of(fmaxf(fabsf(v.x), fabsf(v.y))));
     } else {
       const float v = reinterpret_cast<const float*>(d.src)[src];
@@ -114,10 +114,29 @@ __global__ void __launch_bounds__(256) stage_leaf_tiled_kernel(const LeafDesc* _
   const LeafDesc& d = descs[leaf];
   __shared__ float tre[32][33];
   __shared__ float tim[CPLX ? 32 : 1][33];
+  // per-tile offset tables: source offset of each input-group and output-group index of the
+  // tile, and staged offset of each input-group row (the mixed-radix digits are taken once
+  // per tile, not per element)
+  __shared__ int64_t s_isrc[32], s_osrc[32], s_irow[32];
+  __shared__ TileBase s_tb;
   const int tid = threadIdx.x;
   const int b = blockIdx.y;
-  const TileBase tb = tile_base(d, blockIdx.x, slice_begin + b);
+  if (tid == 0) s_tb = tile_base(d, blockIdx.x, slice_begin + b);
+  __syncthreads();
+  const TileBase tb = s_tb;
   const int64_t go0 = tb.go0, gi0 = tb.gi0;
+  if (tid < 32) {
+    const int64_t gi = gi0 + tid;
+    s_isrc[tid] = gi < d.Pi ? tb.src0 + group_offset(gi, d.ipos, d.ni, d.ext, d.sstride) : 0;
+  } else if (tid < 64) {
+    const int64_t go = go0 + (tid - 32);
+    s_osrc[tid - 32] = go < d.Po ? tail_offset(go, d.rank, d.no, d.ext, d.sstride) : 0;
+  } else if (tid < 96) {
+    const int64_t gi = gi0 + (tid - 64);
+    s_irow[tid - 64] = gi < d.Pi ? tile_dst_row(d, tb, gi) : 0;
+  }
+  __syncthreads();
+  const int64_t Pi = d.Pi, Po = d.Po;
   int lmax = -127;
   // ---- load the tile: tre[ti][to] = element (output-group go0 + to, input-group gi0 + ti)
   if (CPLX && d.vec_load && (reinterpret_cast<uintptr_t>(d.src) & 15) == 0) {
@@ -128,10 +147,10 @@ __global__ void __launch_bounds__(256) stage_leaf_tiled_kernel(const LeafDesc* _
     for (int rep = 0; rep < 2; ++rep) {
       const int to = (tid >> 4) + 16 * rep;
       const int64_t go = go0 + to;
-      if (gi < d.Pi && go < d.Po) {
+      if (gi < Pi && go < Po) {
         // elements gi and gi + 1 differ in the fastest position only (gi even, extent even)
-        const int64_t so = tile_src(d, tb, gi, go);
-        const float4 v = src4[so >> 1];
+        const int64_t so = s_isrc[ti] + s_osrc[to];
+        const float4 v = __ldg(src4 + (so >> 1));
         tre[ti][to] = v.x;
         tim[ti][to] = v.y;
         tre[ti + 1][to] = v.z;
@@ -146,15 +165,15 @@ __global__ void __launch_bounds__(256) stage_leaf_tiled_kernel(const LeafDesc* _
       const int a0 = tid & 31, a1 = (tid >> 5) + 8 * rep;
       const int ti = d.load_o ? a1 : a0, to = d.load_o ? a0 : a1;
       const int64_t gi = gi0 + ti, go = go0 + to;
-      if (gi < d.Pi && go < d.Po) {
-        const int64_t so = tile_src(d, tb, gi, go);
+      if (gi < Pi && go < Po) {
+        const int64_t so = s_isrc[ti] + s_osrc[to];
         if (CPLX) {
-          const float2 v = reinterpret_cast<const float2*>(d.src)[so];
+          const float2 v = __ldg(reinterpret_cast<const float2*>(d.src) + so);
           tre[ti][to] = v.x;
           tim[ti][to] = v.y;
           lmax = max(lmax, exp_of(fmaxf(fabsf(v.x), fabsf(v.y))));
         } else {
-          const float v = reinterpret_cast<const float*>(d.src)[so];
+          const float v = __ldg(reinterpret_cast<const float*>(d.src) + so);
           tre[ti][to] = v;
           lmax = max(lmax, exp_of(fabsf(v)));
         }
@@ -163,37 +182,43 @@ __global__ void __launch_bounds__(256) stage_leaf_tiled_kernel(const LeafDesc* _
   }
   __syncthreads();
   // ---- store: a row of the tile (fixed input-group index) is contiguous in the staged copy
-  const int np = CPLX ? 2 : 1;
+  const int64_t np = CPLX ? cplx_floats(d.split) : 1;
   float* base = reinterpret_cast<float*>(ws + d.dst) + int64_t(b) * np * d.size;
   if (CPLX && d.split) {
     // eight consecutive elements per thread and plane: 16-byte stores of BF16
     const int q = tid & 3, ti = tid >> 2;
     const int64_t gi = gi0 + ti;
     if (ti < 32 && gi < d.Pi) {
-      const int64_t row = tile_dst_row(d, tb, gi);
+      const int64_t row = s_irow[ti];
       const int to = 8 * q;
       if (go0 + to + 7 < d.Po && ((row + to) & 7) == 0 && (d.size & 7) == 0) {
-        uint32_t hr[8], hi_[8], lr[8], li[8];
+        // planes in storage order: split form [rh | ih | rl | il], 3M form [rh | rl | ih | il | sh | sl]
+        uint32_t pl[6][8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const float vr = tre[ti][to + u], vi = tim[ti][to + u];
-          const __nv_bfloat16 a = __float2bfloat16_rn(vr), c = __float2bfloat16_rn(vi);
-          hr[u] = __bfloat16_as_ushort(a);
-          hi_[u] = __bfloat16_as_ushort(c);
-          lr[u] = __bfloat16_as_ushort(__float2bfloat16_rn(vr - __bfloat162float(a)));
-          li[u] = __bfloat16_as_ushort(__float2bfloat16_rn(vi - __bfloat162float(c)));
+          __nv_bfloat16 rh, rl, ih, il, sh, sl;
+          split_pair(vr, rh, rl);
+          split_pair(vi, ih, il);
+          split_pair(vr + vi, sh, sl);
+          const bool m3 = d.split == kFmtSplit3M;
+          pl[0][u] = __bfloat16_as_ushort(rh);
+          pl[1][u] = __bfloat16_as_ushort(m3 ? rl : ih);
+          pl[2][u] = __bfloat16_as_ushort(m3 ? ih : rl);
+          pl[3][u] = __bfloat16_as_ushort(il);
+          pl[4][u] = __bfloat16_as_ushort(sh);
+          pl[5][u] = __bfloat16_as_ushort(sl);
         }
         uint16_t* S = reinterpret_cast<uint16_t*>(base) + row + to;
         auto pack = [](const uint32_t* x) {
           return make_uint4(x[0] | (x[1] << 16), x[2] | (x[3] << 16), x[4] | (x[5] << 16), x[6] | (x[7] << 16));
         };
-        *reinterpret_cast<uint4*>(S) = pack(hr);
-        *reinterpret_cast<uint4*>(S + d.size) = pack(hi_);
-        *reinterpret_cast<uint4*>(S + 2 * d.size) = pack(lr);
-        *reinterpret_cast<uint4*>(S + 3 * d.size) = pack(li);
+        const int planes = d.split == kFmtSplit3M ? 6 : 4;
+        for (int p = 0; p < planes; ++p) *reinterpret_cast<uint4*>(S + p * d.size) = pack(pl[p]);
       } else {
         for (int u = 0; u < 8; ++u)
-          if (go0 + to + u < d.Po) store_cplx(base, d.size, row + to + u, tre[ti][to + u], tim[ti][to + u], true);
+          if (go0 + to + u < d.Po)
+            store_cplx(base, d.size, row + to + u, tre[ti][to + u], tim[ti][to + u], d.split);
       }
     }
   } else {
@@ -201,7 +226,7 @@ __global__ void __launch_bounds__(256) stage_leaf_tiled_kernel(const LeafDesc* _
     const int q = tid & 7, ti = tid >> 3;
     const int64_t gi = gi0 + ti;
     if (gi < d.Pi) {
-      const int64_t row = tile_dst_row(d, tb, gi);
+      const int64_t row = s_irow[ti];
       const int to = 4 * q;
       if (go0 + to + 3 < d.Po && ((row + to) & 3) == 0 && (d.size & 3) == 0) {
         *reinterpret_cast<float4*>(base + row + to) =
@@ -365,7 +390,7 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (!cok[j]) continue;
-      if (CPLX) store_cplx(C, a.c_plane, ro + coff[j], accr[i][j], acci[i][j], a.c_split != 0);
+      if (CPLX) store_cplx(C, a.c_plane, ro + coff[j], accr[i][j], acci[i][j], a.c_split);
       else C[ro + coff[j]] = accr[i][j];
       if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(accr[i][j]), fabsf(acci[i][j]))
                                                : fabsf(accr[i][j])));
@@ -440,7 +465,7 @@ __global__ void __launch_bounds__(256) contract_stream_kernel(StepArgs a) {
 #pragma unroll
     for (int j = 0; j < NMAX; ++j) {
       if (j < n) {
-        if (CPLX) store_cplx(C, a.c_plane, ro + coff[j], cr[j], ci[j], a.c_split != 0);
+        if (CPLX) store_cplx(C, a.c_plane, ro + coff[j], cr[j], ci[j], a.c_split);
         else C[ro + coff[j]] = cr[j];
         if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(cr[j]), fabsf(ci[j])) : fabsf(cr[j])));
       }
@@ -481,7 +506,7 @@ __global__ void simt_combine_kernel(StepArgs a, int32_t nb, int32_t cplx) {
     const int64_t i = o / a.n, j = o - i * a.n;
     const int64_t off = map_offset(a.rows, i) + map_offset(a.cols, j);
     float* C = a.C + b * a.c_bstride;
-    if (cplx) store_cplx(C, a.c_plane, off, vr, vi, a.c_split != 0);
+    if (cplx) store_cplx(C, a.c_plane, off, vr, vi, a.c_split);
     else C[off] = vr;
   }
 }
@@ -783,7 +808,7 @@ __global__ void __launch_bounds__(kFinalThreads) splitk_final_kernel(StepArgs a,
     if (threadIdx.x == 0) {
       const int i = o / n, j = o % n;
       const int64_t off = map_offset(a.rows, i) + map_offset(a.cols, j);
-      if (cplx) store_cplx(C, a.c_plane, off, (float)vr, (float)vi, a.c_split != 0);
+      if (cplx) store_cplx(C, a.c_plane, off, (float)vr, (float)vi, a.c_split);
       else C[off] = (float)vr;
       if (a.recs) lmax = max(lmax, exp_of(cplx ? fmaxf(fabsf((float)vr), fabsf((float)vi)) : fabsf((float)vr)));
     }

@@ -42,6 +42,7 @@ double tc_flops(int32_t p) {
     case TN_C64_TF32: case TN_R32_TF32: return g_cost.tc_flops[0];
     case TN_C64_3XTF32: case TN_R32_3XTF32: return g_cost.tc_flops[1];
     case TN_C64_BF16X3: case TN_R32_BF16X3: return g_cost.tc_flops[2];
+    case -3: return g_cost.tc_flops[2] * 4.0 / 3.0;  // BF16x3, 3M: 9 BF16 products per complex MAC, not 12
     default: return 0;
   }
 }
@@ -109,8 +110,12 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
           "the tensor-core kernels do not rescale their operands";
     return TN_ERR_UNSUPPORTED;
   }
-  if (pol.complex_mult != 0 && pol.complex_mult != 4) {
-    err = "only the 4M complex form is built (complex_mult must be 4 or 0)";
+  if (pol.complex_mult != 0 && pol.complex_mult != 4 && pol.complex_mult != 3) {
+    err = "complex_mult must be 4 (4M), 3 (3M) or 0 (4M)";
+    return TN_ERR_INVALID;
+  }
+  if (pol.complex_mult == 3 && pol.prec != TN_C64_BF16X3) {
+    err = "the 3M complex product is built for the BF16X3 form only";
     return TN_ERR_UNSUPPORTED;
   }
   const int32_t T = net->n_tensors, L = net->n_labels;
@@ -364,7 +369,8 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     if (tc_form_here && tc_step_ok(st.m, st.n, st.k, pol.prec)) {
       // a step narrower than the 128-column tile uses that fraction of the tensor core
       const double fill = std::min(1.0, double(st.n) / 128.0);
-      const double t_tc = std::max(bytes / g_cost.hbm_bytes_per_s, flops / (tc_flops(pol.prec) * fill));
+      const double rate = tc_flops(pol.complex_mult == 3 ? -3 : pol.prec);
+      const double t_tc = std::max(bytes / g_cost.hbm_bytes_per_s, flops / (rate * fill));
       // ties (both bound by the same HBM bytes) go to the tensor-core kernel, whose
       // epilogue stores are the better coalesced
       if (t_tc <= t_simt) st.cls = TN_CLASS_TC;
@@ -387,11 +393,12 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
   // ---- split-BF16 operands: a BF16x3 tensor-core step reads both operands in the split
   // form, so their producers (leaf staging or the producing step) write that form
   if (pol.prec == TN_C64_BF16X3) {
+    const int32_t mode = pol.complex_mult == 3 ? 2 : 1;
     for (int32_t s = 0; s < S; ++s) {
       const StepRec& st = P.steps[s];
       if (st.cls != TN_CLASS_TC) continue;
-      P.tensors[st.a].split = true;
-      P.tensors[st.b].split = true;
+      P.tensors[st.a].split = mode;
+      P.tensors[st.b].split = mode;
     }
   }
   // ---- leaf descriptors (sources filled per call)
@@ -413,7 +420,7 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     d.rank = (int32_t)R.modes.size();
     d.size = R.size;
     d.batched = R.batched ? 1 : 0;
-    d.split = R.split ? 1 : 0;
+    d.split = R.split;
     for (int i = 0; i < d.rank; ++i) {
       int32_t x = R.modes[i];
       int pos = int(std::find(R.decl.begin(), R.decl.end(), x) - R.decl.begin());
@@ -542,7 +549,7 @@ void assign_workspace(Plan& P, int64_t batch) {
       birth[t] = -1;
       death[t] = kInf;
     }
-    R.bytes = align_up(std::max<int64_t>(1, R.size) * eb * (R.batched ? batch : 1), kAlign);
+    R.bytes = align_up(std::max<int64_t>(1, R.size) * stored_bytes(P, R) * (R.batched ? batch : 1), kAlign);
   }
   std::vector<int32_t> order(N);
   std::iota(order.begin(), order.end(), 0);

@@ -1,4 +1,4 @@
-// The split-BF16 storage form of a complex tensor (device side).
+// The split-BF16 storage forms of a complex tensor (device side).
 //
 // A tensor that feeds a BF16x3 tensor-core step is written by its producer as four
 // BF16 planes of E elements each, [re_hi | im_hi | re_lo | im_lo], in place of the two
@@ -13,21 +13,48 @@
 
 namespace tn {
 
+// Storage modes of a complex tensor copy (tn_storage_format): 0 planar FP32 [re | im];
+// 1 split BF16 [re_hi | im_hi | re_lo | im_lo] (operands of 4M BF16x3 steps); 2 split BF16
+// with the sum plane of the 3M product, [re_hi | re_lo | im_hi | im_lo | s_hi | s_lo] with
+// s = re + im rounded to FP32 (operands of 3M BF16x3 steps; 12 bytes per element, each
+// hi/lo pair adjacent so that one product's operand planes are one TMA box).
+constexpr int kFmtPlanar = 0, kFmtSplit = 1, kFmtSplit3M = 2;
+
+// floats per element of a complex copy in storage mode `fmt` (batch strides)
+__host__ __device__ inline int64_t cplx_floats(int fmt) { return fmt == kFmtSplit3M ? 3 : 2; }
+
+__device__ __forceinline__ void split_pair(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 // Store one complex value at element `off` of a tensor copy that starts at `C`
-// (the copy's first float): planar FP32, or split BF16 when `split` is set.
-__device__ __forceinline__ void store_cplx(float* C, int64_t plane, int64_t off, float re, float im,
-                                           bool split) {
-  if (!split) {
+// (the copy's first float), in storage mode `fmt`.
+__device__ __forceinline__ void store_cplx(float* C, int64_t plane, int64_t off, float re, float im, int fmt) {
+  if (fmt == kFmtPlanar) {
     C[off] = re;
     C[plane + off] = im;
     return;
   }
   __nv_bfloat16* S = reinterpret_cast<__nv_bfloat16*>(C);
-  const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi = __float2bfloat16_rn(im);
-  S[off] = hr;
-  S[plane + off] = hi;
-  S[2 * plane + off] = __float2bfloat16_rn(re - __bfloat162float(hr));
-  S[3 * plane + off] = __float2bfloat16_rn(im - __bfloat162float(hi));
+  __nv_bfloat16 rh, rl, ih, il;
+  split_pair(re, rh, rl);
+  split_pair(im, ih, il);
+  if (fmt == kFmtSplit) {
+    S[off] = rh;
+    S[plane + off] = ih;
+    S[2 * plane + off] = rl;
+    S[3 * plane + off] = il;
+    return;
+  }
+  __nv_bfloat16 sh, sl;
+  split_pair(re + im, sh, sl);
+  S[off] = rh;
+  S[plane + off] = rl;
+  S[2 * plane + off] = ih;
+  S[3 * plane + off] = il;
+  S[4 * plane + off] = sh;
+  S[5 * plane + off] = sl;
 }
 
 }  // namespace tn

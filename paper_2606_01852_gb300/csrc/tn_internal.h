@@ -33,7 +33,7 @@ struct LeafDesc {
   int32_t rank;             // planned rank
   int32_t batched;          // carries a sliced label
   int32_t n_sl;             // sliced labels on this leaf
-  int32_t split;            // stage in the split-BF16 form (operand of a BF16x3 step)
+  int32_t split;            // storage mode of the staged copy (0 planar, 1 split, 2 split 3M)
   uint32_t ext[kMaxLeafRank];      // planned extents
   int64_t sstride[kMaxLeafRank];   // source stride (elements) of each planned position
   int64_t sl_div[kMaxSliced];      // slice id -> label value: (sid / div) % ext
@@ -66,7 +66,9 @@ struct TensorRec {
   int32_t producer = -1;       // step, or -1 for a leaf
   int32_t consumer = -1;       // step, or -1 for the root
   bool pinned = false;         // unbatched, consumed by a batched step: kept for all passes
-  bool split = false;          // stored as split BF16 (its consumer is a BF16x3 TC step)
+  int32_t split = 0;           // storage mode (split_bf16.cuh): 0 planar FP32, 1 split BF16
+                               // (its consumer is a 4M BF16x3 step), 2 split BF16 with the
+                               // 3M sum planes (its consumer is a 3M BF16x3 step)
   int64_t offset = 0;          // byte offset in the workspace
   int64_t bytes = 0;           // bytes including the batch copies
 };
@@ -156,6 +158,10 @@ bool tc_supported();
 bool tc_step_ok(int64_t m, int64_t n, int64_t k, int32_t prec);
 
 inline int64_t elem_bytes(const Plan& P) { return P.is_complex ? 8 : 4; }
+// bytes per element of a tensor's stored copies (the 3M split form holds 12)
+inline int64_t stored_bytes(const Plan& P, const TensorRec& R) {
+  return P.is_complex ? (R.split == 2 ? 12 : 8) : 4;
+}
 
 }  // namespace tn
 

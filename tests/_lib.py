@@ -30,8 +30,12 @@ def ensure_built():
 #    so results are held to that one-product bound;
 #  * TF32 (measured and reported): operands truncated to 10 mantissa bits, a bias of up to
 #    2^-10 per product that adds up along a path; bounds per test.
+#  * BF16x3 with the 3M product: Im = P3 - P1 - P2 with P3 = (a_re + a_im)(b_re + b_im), whose
+#    terms are up to twice |a||b|: each of the three products within 3 * 2^-16 of its own
+#    magnitude, 4 |a||b| in all, so 12 * 2^-16 = 1.8e-4 relative to |a||b|.
 FP32_BAR = 1e-5
 BF16X3_BOUND = 3 * 2.0 ** -16
+BF16X3M_BOUND = 12 * 2.0 ** -16
 
 
 def fp32_accurate_bound(fp32_err):

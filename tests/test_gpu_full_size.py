@@ -20,7 +20,9 @@ import numpy as np
 import pytest
 import torch
 
-from tests._lib import BF16X3_BOUND, FP32_BAR, ROOT, ensure_built, fp32_accurate_bound
+from tests._lib import BF16X3_BOUND, BF16X3M_BOUND, FP32_BAR, ROOT, ensure_built, fp32_accurate_bound
+
+FAST_BOUND = {"bf16x3": BF16X3_BOUND, "bf16x3m": BF16X3M_BOUND}
 from tn_inputs import workloads
 
 pytestmark = pytest.mark.gpu
@@ -82,14 +84,14 @@ def test_rc40c14_pieces_fp32(tn):
     assert _c14_pieces_err("fp32") < FP32_BAR
 
 
-@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3", "bf16x3m"])
 def test_rc40c14_pieces_fast_forms(tn, prec):
     err, fp32 = _c14_pieces_err(prec), _c14_pieces_err("fp32")
-    bound = fp32_accurate_bound(fp32) if prec == "3xtf32" else BF16X3_BOUND
+    bound = fp32_accurate_bound(fp32) if prec == "3xtf32" else FAST_BOUND[prec]
     assert err < bound, (prec, err, fp32)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x3m", "3xtf32"])
 def test_rc40c14_slice_bench_config(tn, prec):
     """The benchmark's plan (7 sliced labels, 8 slices per pass): the stored slice against
     the oracle's sum of its four pieces (Sec. II-C: slicing partitions the sum exactly), and
@@ -106,7 +108,7 @@ def test_rc40c14_slice_bench_config(tn, prec):
     torch.cuda.synchronize()
     want = complex(*gold["slice_partial"])
     typical = np.sqrt(np.mean(np.abs([complex(*p) for p in gold["pieces"]]) ** 2))
-    bound = BF16X3_BOUND if prec == "bf16x3" else fp32_accurate_bound(_c14_pieces_err("fp32"))
+    bound = FAST_BOUND[prec] if prec in FAST_BOUND else fp32_accurate_bound(_c14_pieces_err("fp32"))
     assert abs(complex(out.cpu()) - want) / typical < bound
     b0 = (sid // 8) * 8
     plan.contract_slices(ins, b0, 8, out)
@@ -145,7 +147,7 @@ def _rc40_slices_err(prec, name):
 
 
 @pytest.mark.parametrize("name", ["rc40", "rc40open"])
-@pytest.mark.parametrize("prec", ["fp32", "3xtf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "3xtf32", "bf16x3", "bf16x3m"])
 def test_rc40_sampled_slices_bench_config(tn, name, prec):
     """Four sampled slices at the benchmark launch configuration (128 slices per pass);
     rc40open's slices are [2,2,2,2] tensors of partial amplitudes: Frobenius and
@@ -156,7 +158,7 @@ def test_rc40_sampled_slices_bench_config(tn, name, prec):
     elif prec == "3xtf32":
         bound = fp32_accurate_bound(max(_rc40_slices_err("fp32", name)))
     else:
-        bound = BF16X3_BOUND
+        bound = FAST_BOUND[prec]
     assert frob < bound and elem < bound, (name, prec, frob, elem)
 
 
@@ -185,12 +187,12 @@ def test_dynamics_fp32(tn, name):
 
 
 @pytest.mark.parametrize("name", ["kising44", "khex45", "ktri44", "kising55"])
-@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3", "bf16x3m", "tf32"])
 def test_dynamics_fast_forms(tn, name, prec):
     """Kicked Ising on the square (4x4, and the serving mix's 5x5), honeycomb and
     triangular lattices. TF32 (biased truncation over hundreds of steps) is held to 1e-1."""
     err = _dyn_err(name, prec)
-    bound = {"3xtf32": fp32_accurate_bound(_dyn_err(name, "fp32")), "bf16x3": BF16X3_BOUND, "tf32": 1e-1}[prec]
+    bound = {"3xtf32": fp32_accurate_bound(_dyn_err(name, "fp32")), "tf32": 1e-1, **FAST_BOUND}[prec]
     bound = KNOWN_MISSES.get((name, prec), bound)
     assert err < bound, (name, prec, err, _dyn_err(name, "fp32"))
 
@@ -199,7 +201,7 @@ def _rc40_total():
     return complex(*json.load(open(os.path.join(ROOT, "tests", "golden", "rc40_total.json")))["total"])
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x3m", "3xtf32"])
 def test_rc40_full_sum_bench_config(tn, prec):
     """All 256 slices at 128 slices per launch (two passes, FP64 Neumaier sum across
     slices) against the oracle's full sum, within 1e-5 (measured: 3.3e-6 BF16x3, 3.6e-6

@@ -31,14 +31,17 @@ def replay(plan, net, sliced, begin=0, count=None, cplx=True):
     T, S = net.n_tensors, info["n_steps"]
     B = info["slice_batch"]
     count = info["n_slices"] if count is None else count
-    nplanes = 2 if cplx else 1
     ws = np.full(info["workspace_bytes"] // 4 + 1, np.nan)  # poisoned: unwritten reads show
     tens = [plan.tensor(t) for t in range(T + S)]
     steps = [plan.step(s) for s in range(S)]
     layout = [plan.layout(t) for t in range(T)]
 
+    # floats per element of a stored copy: 1 real, 2 complex, 3 in the 3M split form (whose
+    # planes this float replay does not reproduce, only their footprint)
+    fpe = [1 if not cplx else (3 if x["format"] == 2 else 2) for x in tens]
+
     def base(t, b, p):
-        return tens[t]["offset"] // 4 + (b * nplanes + p) * tens[t]["size"]
+        return tens[t]["offset"] // 4 + (b * fpe[t] + p) * tens[t]["size"]
 
     def read(t, b, shape):
         sz = tens[t]["size"]
@@ -104,6 +107,24 @@ def test_replay_many_pinned(tn, batch):
     plan = tn.Plan(w.net, w.path, w.sliced, prec="3xtf32", max_slice_batch=batch, host_only=True)
     pinned = sum(plan.tensor(t)["pinned"] for t in range(w.net.n_tensors + len(w.path.pairs)))
     assert pinned > 0
+    got = replay(plan, w.net, w.sliced)
+    assert rel_err(got, oracle.contract(w.net, w.path, w.sliced)) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x3m"])
+@pytest.mark.parametrize("batch", [1, 3])
+def test_replay_split_forms(tn, prec, batch):
+    """Plans whose tensor-core operands are stored split (4 BF16 planes in 8 bytes, or the
+    3M form's 6 planes in 12 bytes per element): every copy inside its reserved bytes and no
+    live overlap, replayed against the oracle."""
+    w = workloads.random_circuit(4, 5, 12, 40, n_sliced=3)
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=batch, host_only=True)
+    fmts = {plan.tensor(t)["format"] for t in range(w.net.n_tensors + len(w.path.pairs))}
+    assert fmts == {0, 2 if prec == "bf16x3m" else 1}
+    for t in range(w.net.n_tensors + len(w.path.pairs)):
+        x = plan.tensor(t)
+        per = 12 if x["format"] == 2 else 8
+        assert x["bytes"] >= x["size"] * per * (batch if x["batched"] else 1)
     got = replay(plan, w.net, w.sliced)
     assert rel_err(got, oracle.contract(w.net, w.path, w.sliced)) < 1e-12
 
