@@ -526,8 +526,17 @@ tn_status tn_plan_check_staging(tn_plan_t plan, int64_t max_slices) {
       // slices 0, n-1, and evenly spread ones between
       const int64_t sid = n_sid == 1 ? 0 : q * (P.n_slices - 1) / (n_sid - 1);
       std::vector<char> seen(d.size, 0);
+      TileCursor cur{};
       for (int64_t blk = 0; blk < tiles; ++blk) {
+        // the CTA's walk: a fresh cursor every kTilesPerCta tiles, advanced in between
+        if (blk % kTilesPerCta == 0) cursor_start(d, blk, sid, cur);
+        else cursor_next(d, cur);
         const TileBase tb = tile_base(d, blk, sid);
+        if (cur.co * 32 != tb.go0 || cur.ci * 32 != tb.gi0 || cur.src0 != tb.src0 || cur.dst0 != tb.dst0) {
+          set_error("tiled staging of leaf " + std::to_string(t) + ": the tile cursor disagrees with tile " +
+                    std::to_string(blk));
+          return TN_ERR_INVALID;
+        }
         for (int ti = 0; ti < 32; ++ti) {
           const int64_t gi = tb.gi0 + ti;
           if (gi >= d.Pi) continue;

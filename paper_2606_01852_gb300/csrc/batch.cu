@@ -24,41 +24,12 @@
 
 #include <cuda_runtime.h>
 
+#include "batch.h"
 #include "kernels.h"
 #include "tn_internal.h"
 
 namespace tn {
 namespace {
-
-constexpr int kBMaxDims = 8;    // merged offset dims per side in the batch tables
-constexpr int kBMaxRank = 8;    // planned leaf rank in the batch tables
-
-struct BLeaf {
-  int64_t src;                  // element offset in the packed input buffer
-  int32_t dst;                  // float offset in the network's arena (real plane)
-  int32_t size;
-  int32_t rank;
-  int32_t pad;
-  int32_t ext[kBMaxRank];
-  int32_t sstride[kBMaxRank];   // declared stride of each planned position
-};
-
-struct BStep {
-  int32_t a, b, c;              // float offsets in the arena (real planes)
-  int32_t a_size, b_size, c_size;
-  int32_t m, n, k;
-  int8_t nr, nc;
-  int16_t pad;
-  int32_t rext[kBMaxDims], rstr[kBMaxDims];
-  int32_t cext[kBMaxDims], cstr[kBMaxDims];
-};
-
-struct BNet {
-  int64_t arena;                // float offset of the network's arena in the batch arena
-  int32_t leaf0, n_leaves;      // index range in the leaf table
-  int32_t step0, n_steps;       // index range in the step table
-  int32_t root, root_size;      // float offset and size of the result tensor
-};
 
 __device__ __forceinline__ int bexp_of(float v) { return ((__float_as_int(v) >> 23) & 0xff) - 127; }
 __device__ __forceinline__ float bpow2_neg(int e) {
@@ -210,27 +181,105 @@ struct tn_batch_s {
   cudaStream_t g_stream = nullptr;
 };
 
+namespace tn {
+
+cudaError_t launch_batch_kernel(const BNet* nets, const BLeaf* leaves, const BStep* steps, int32_t n_nets,
+                                const void* packed, float* arena, int32_t* queue, bool cplx, bool scaling,
+                                bool maxplus, int threads, int grid, double* values, double* logs,
+                                cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  const float* in = static_cast<const float*>(packed);
+  if (cplx)
+    batch_kernel<true><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue, scaling ? 1 : 0,
+                                                 values, logs);
+  else if (maxplus)
+    batch_kernel<false, true><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue, 0, values,
+                                                        logs);
+  else
+    batch_kernel<false><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue, scaling ? 1 : 0,
+                                                  values, logs);
+  return cudaGetLastError();
+}
+
+bool batch_template(const Plan& P, BatchTemplate& T, std::string& err) {
+  if (P.n_slices != 1) {
+    err = "sliced networks are not batched";
+    return false;
+  }
+  if (!P.open_modes.empty()) {
+    err = "open labels (closed networks only)";
+    return false;
+  }
+  if (P.arena_bytes / 4 > (int64_t(1) << 30)) {
+    err = "network too large for the batched kernel";
+    return false;
+  }
+  auto foff = [&](int32_t t) { return static_cast<int32_t>(P.tensors[t].offset / 4); };
+  T = BatchTemplate{};
+  const int32_t root = P.n_leaves + (int32_t)P.steps.size() - 1;
+  T.root = foff(root);
+  T.root_size = (int32_t)P.tensors[root].size;
+  for (int32_t t = 0; t < P.n_leaves; ++t) {
+    const TensorRec& R = P.tensors[t];
+    const LeafDesc& d = P.leafdesc[t];
+    if (d.rank > kBMaxRank || R.split) {
+      err = d.rank > kBMaxRank ? "leaf rank too large" : "split-BF16 operands (tensor-core steps)";
+      return false;
+    }
+    BLeaf L{};
+    L.src = T.input_elems;
+    L.dst = foff(t);
+    L.size = (int32_t)R.size;
+    L.rank = d.rank;
+    for (int r = 0; r < d.rank; ++r) {
+      L.ext[r] = (int32_t)d.ext[r];
+      L.sstride[r] = (int32_t)d.sstride[r];
+    }
+    int64_t full = 1;
+    for (int32_t x : R.decl) full *= P.extent[x];
+    T.input_elems += full;
+    T.leaves.push_back(L);
+  }
+  for (const StepRec& st : P.steps) {
+    if (st.rows.n > kBMaxDims || st.cols.n > kBMaxDims || st.cls == TN_CLASS_TC) {
+      err = st.cls == TN_CLASS_TC ? "tensor-core steps" : "output interleaving too fine";
+      return false;
+    }
+    BStep S{};
+    S.a = foff(st.a);
+    S.b = foff(st.b);
+    S.c = foff(st.out);
+    S.a_size = (int32_t)P.tensors[st.a].size;
+    S.b_size = (int32_t)P.tensors[st.b].size;
+    S.c_size = (int32_t)P.tensors[st.out].size;
+    S.m = (int32_t)st.m;
+    S.n = (int32_t)st.n;
+    S.k = (int32_t)st.k;
+    S.nr = (int8_t)st.rows.n;
+    S.nc = (int8_t)st.cols.n;
+    for (int d = 0; d < st.rows.n; ++d) {
+      S.rext[d] = (int32_t)st.rows.ext[d];
+      S.rstr[d] = (int32_t)st.rows.stride[d];
+    }
+    for (int d = 0; d < st.cols.n; ++d) {
+      S.cext[d] = (int32_t)st.cols.ext[d];
+      S.cstr[d] = (int32_t)st.cols.stride[d];
+    }
+    T.steps.push_back(S);
+    T.flops += (P.is_complex ? 8.0 : 2.0) * double(st.m) * double(st.n) * double(st.k);
+  }
+  T.arena_floats = (P.arena_bytes + 255) / 256 * 64;  // keep every arena 256-byte aligned
+  return true;
+}
+
+}  // namespace tn
+
 namespace {
 tn_status launch_batch(tn_batch_s* B, const void* packed, double* values, double* logs, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(B->d_queue, 0, sizeof(int32_t), st);
-  if (e != cudaSuccess) {
-    set_error(std::string("batch queue reset: ") + cudaGetErrorString(e));
-    return TN_ERR_CUDA;
-  }
   const int grid = std::min<int64_t>(B->n_nets, (int64_t)B->num_sms * B->ctas_per_sm);
-  if (B->cplx)
-    batch_kernel<true><<<grid, B->threads, 0, st>>>(B->d_nets, B->d_leaves, B->d_steps, B->n_nets,
-                                                     static_cast<const float*>(packed), B->d_arena, B->d_queue,
-                                                     B->scaling ? 1 : 0, values, logs);
-  else if (B->maxplus)
-    batch_kernel<false, true><<<grid, B->threads, 0, st>>>(B->d_nets, B->d_leaves, B->d_steps, B->n_nets,
-                                                            static_cast<const float*>(packed), B->d_arena,
-                                                            B->d_queue, 0, values, logs);
-  else
-    batch_kernel<false><<<grid, B->threads, 0, st>>>(B->d_nets, B->d_leaves, B->d_steps, B->n_nets,
-                                                      static_cast<const float*>(packed), B->d_arena, B->d_queue,
-                                                      B->scaling ? 1 : 0, values, logs);
-  e = cudaGetLastError();
+  cudaError_t e = launch_batch_kernel(B->d_nets, B->d_leaves, B->d_steps, B->n_nets, packed, B->d_arena, B->d_queue,
+                                      B->cplx, B->scaling, B->maxplus, B->threads, grid, values, logs, st);
   if (e != cudaSuccess) {
     set_error(std::string("batch kernel launch: ") + cudaGetErrorString(e));
     return TN_ERR_CUDA;
@@ -260,7 +309,6 @@ tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* p
     set_error("tn_batch_plan: the max-plus semiring runs R32 without exponent scaling");
     return TN_ERR_UNSUPPORTED;
   }
-  const int np = B->cplx ? 2 : 1;
   int64_t in_off = 0;
   tn_dtype_policy hp = policy;
   hp.flags |= TN_PLAN_HOST_ONLY;
@@ -282,75 +330,29 @@ tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* p
       set_error("tn_batch_plan: workspace self-check failed");
       return TN_ERR_INVALID;
     }
-    const int64_t eb = elem_bytes(P);
-    if (P.arena_bytes / 4 > (int64_t(1) << 30)) {
-      set_error("tn_batch_plan: network too large for the batched kernel");
+    BatchTemplate T;
+    std::string why;
+    if (!batch_template(P, T, why)) {
+      set_error("tn_batch_plan: network " + std::to_string(w) + ": " + why);
       return TN_ERR_UNSUPPORTED;
     }
-    // float offsets of each tensor's real plane (tensor bytes are eb per element)
-    auto foff = [&](int32_t t) { return static_cast<int32_t>(P.tensors[t].offset / 4); };
     BNet bn{};
     bn.arena = B->arena_floats;
     bn.leaf0 = (int32_t)B->leaves.size();
-    bn.n_leaves = P.n_leaves;
+    bn.n_leaves = (int32_t)T.leaves.size();
     bn.step0 = (int32_t)B->steps.size();
-    bn.n_steps = (int32_t)P.steps.size();
-    const int32_t root = P.n_leaves + (int32_t)P.steps.size() - 1;
-    bn.root = foff(root);
-    bn.root_size = (int32_t)P.tensors[root].size;
-    for (int32_t t = 0; t < P.n_leaves; ++t) {
-      const TensorRec& R = P.tensors[t];
-      const LeafDesc& d = P.leafdesc[t];
-      if (d.rank > kBMaxRank) {
-        set_error("tn_batch_plan: leaf rank too large");
-        return TN_ERR_UNSUPPORTED;
-      }
-      BLeaf L{};
-      L.src = in_off;
-      L.dst = foff(t);
-      L.size = (int32_t)R.size;
-      L.rank = d.rank;
-      for (int r = 0; r < d.rank; ++r) {
-        L.ext[r] = (int32_t)d.ext[r];
-        L.sstride[r] = (int32_t)d.sstride[r];
-      }
-      B->leaf_offset.push_back(in_off);
-      int64_t full = 1;
-      for (int32_t x : R.decl) full *= P.extent[x];
-      in_off += full;
+    bn.n_steps = (int32_t)T.steps.size();
+    bn.root = T.root;
+    bn.root_size = T.root_size;
+    for (BLeaf L : T.leaves) {
+      B->leaf_offset.push_back(in_off + L.src);
+      L.src += in_off;
       B->leaves.push_back(L);
     }
-    for (const StepRec& st : P.steps) {
-      if (st.rows.n > kBMaxDims || st.cols.n > kBMaxDims) {
-        set_error("tn_batch_plan: output interleaving too fine");
-        return TN_ERR_UNSUPPORTED;
-      }
-      BStep S{};
-      S.a = foff(st.a);
-      S.b = foff(st.b);
-      S.c = foff(st.out);
-      S.a_size = (int32_t)P.tensors[st.a].size;
-      S.b_size = (int32_t)P.tensors[st.b].size;
-      S.c_size = (int32_t)P.tensors[st.out].size;
-      S.m = (int32_t)st.m;
-      S.n = (int32_t)st.n;
-      S.k = (int32_t)st.k;
-      S.nr = (int8_t)st.rows.n;
-      S.nc = (int8_t)st.cols.n;
-      for (int d = 0; d < st.rows.n; ++d) {
-        S.rext[d] = (int32_t)st.rows.ext[d];
-        S.rstr[d] = (int32_t)st.rows.stride[d];
-      }
-      for (int d = 0; d < st.cols.n; ++d) {
-        S.cext[d] = (int32_t)st.cols.ext[d];
-        S.cstr[d] = (int32_t)st.cols.stride[d];
-      }
-      B->steps.push_back(S);
-      B->flops += (B->cplx ? 8.0 : 2.0) * double(st.m) * double(st.n) * double(st.k);
-    }
-    (void)eb;
-    (void)np;
-    B->arena_floats += (P.arena_bytes + 255) / 256 * 64;  // keep every arena 256-byte aligned
+    in_off += T.input_elems;
+    B->steps.insert(B->steps.end(), T.steps.begin(), T.steps.end());
+    B->flops += T.flops;
+    B->arena_floats += T.arena_floats;
     B->nets.push_back(bn);
   }
   B->leaf_offset.push_back(in_off);

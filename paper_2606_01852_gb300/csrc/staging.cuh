@@ -70,6 +70,52 @@ __host__ __device__ inline TileBase tile_base(const LeafDesc& d, int64_t blk, in
   return t;
 }
 
+// A CTA of the tiled kernel walks consecutive tiles: the cursor holds the chunk indices and
+// the digits of the rest index, and advancing it updates the offsets by the stride of the
+// digits that change (amortised one digit per tile), equal to tile_base of the next tile.
+struct TileCursor {
+  int64_t co, ci;                  // output-group and input-group chunk of the tile
+  int64_t src0, dst0;              // offsets of the rest index (src0 with the slice's)
+  uint32_t dig[kMaxLeafRank];      // digits of the rest index over rpos, last fastest
+};
+
+__host__ __device__ inline void cursor_start(const LeafDesc& d, int64_t blk, int64_t sid, TileCursor& c) {
+  const int64_t nco = (d.Po + 31) / 32, nci = (d.Pi + 31) / 32;
+  c.co = blk % nco;
+  blk /= nco;
+  c.ci = blk % nci;
+  int64_t r = blk / nci;
+  c.src0 = 0;
+  c.dst0 = 0;
+  for (int q = d.nr - 1; q >= 0; --q) {
+    const int p = d.rpos[q];
+    c.dig[q] = static_cast<uint32_t>(r % d.ext[p]);
+    r /= d.ext[p];
+    c.src0 += int64_t(c.dig[q]) * d.sstride[p];
+    c.dst0 += int64_t(c.dig[q]) * d.dstride[p];
+  }
+  for (int q = 0; q < d.n_sl; ++q) c.src0 += ((sid / d.sl_div[q]) % d.sl_ext[q]) * d.sl_stride[q];
+}
+
+__host__ __device__ inline void cursor_next(const LeafDesc& d, TileCursor& c) {
+  if (++c.co < (d.Po + 31) / 32) return;
+  c.co = 0;
+  if (++c.ci < (d.Pi + 31) / 32) return;
+  c.ci = 0;
+  for (int q = d.nr - 1; q >= 0; --q) {
+    const int p = d.rpos[q];
+    c.src0 += d.sstride[p];
+    c.dst0 += d.dstride[p];
+    if (++c.dig[q] < d.ext[p]) return;
+    c.src0 -= int64_t(d.ext[p]) * d.sstride[p];
+    c.dst0 -= int64_t(d.ext[p]) * d.dstride[p];
+    c.dig[q] = 0;
+  }
+}
+
+// tiles one CTA of the tiled kernel walks
+constexpr int kTilesPerCta = 8;
+
 // Source element (declared order) and staged element of tile entry (ti, to).
 __host__ __device__ inline int64_t tile_src(const LeafDesc& d, const TileBase& t, int64_t gi, int64_t go) {
   return t.src0 + group_offset(gi, d.ipos, d.ni, d.ext, d.sstride) + tail_offset(go, d.rank, d.no, d.ext, d.sstride);
