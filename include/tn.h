@@ -302,14 +302,19 @@ tn_status tn_plan_profile_steps(tn_plan_t plan, double* ms_out, int32_t n_steps)
 /* ---- serving: continuous batching of contraction requests ------------------------ */
 
 typedef struct {
-  int32_t max_inflight;      /* requests on the GPU at once (slots) */
+  int32_t max_inflight;      /* launches on the GPU at once (slots; a pack takes one) */
   int32_t n_streams;         /* CUDA streams work is spread over */
   int64_t hbm_budget_bytes;  /* limit on the device memory the server holds in request
                                 workspaces (resident plan instances, busy or idle; 0 = no
                                 limit): idle instances are freed, least recently used first,
                                 before a request waits for running ones to finish */
   int32_t queue_capacity;    /* pending requests beyond which submit returns TN_ERR_BUSY */
-  int32_t reserved[3];
+  int32_t pack_max;          /* > 0: queued requests on small closed unsliced plans without
+                                tensor-core steps (the same arithmetic kind: complex, real with
+                                or without scaling, max-plus) are packed, up to pack_max per
+                                launch, into one launch of the batched small-network kernel (one
+                                CTA per request); 0: every request runs its own plan launch */
+  int32_t reserved[2];
 } tn_serve_config;
 
 typedef struct tn_server_s* tn_server_t;
@@ -320,8 +325,11 @@ tn_status tn_serve_create(const tn_serve_config* cfg, tn_server_t* out);
 /* Submit a request: contract `plan` (all slices) on HOST inputs. The server copies the
  * inputs before returning, so the caller may reuse its buffers. Admission waits until a
  * slot and the plan's workspace fit the HBM budget. Returns TN_ERR_BUSY when the queue
- * is full. The plan must stay alive until the ticket is polled to completion, and one
- * plan must not have two requests in flight (its workspace is shared). */
+ * is full. The plan must stay alive until the ticket is polled to completion. Requests on
+ * one plan run on separate resident instances of it (or packed together, see pack_max).
+ * A packed request's result comes from the batched kernel: identical whatever else is in
+ * its pack (one CTA computes it, in a fixed order), and within rounding of the plan's own
+ * kernels. */
 tn_status tn_serve_submit(tn_server_t srv, tn_plan_t plan, const void* const* host_inputs,
                           uint64_t* ticket);
 
@@ -331,6 +339,18 @@ tn_status tn_serve_submit(tn_server_t srv, tn_plan_t plan, const void* const* ho
  * flight after the wait; TN_ERR_INVALID for an unknown ticket. */
 tn_status tn_serve_poll(tn_server_t srv, uint64_t ticket, void* result, double* log_scale,
                         int32_t timeout_us);
+
+/* Counters of a server since its creation (the paper has no counterpart). */
+typedef struct {
+  int64_t completed;        /* requests retired (any status) */
+  int64_t plan_launches;    /* requests run as their own plan launch */
+  int64_t packs;            /* packed launches of the batched kernel */
+  int64_t packed_requests;  /* requests run inside packed launches */
+  int64_t max_pack;         /* largest pack so far */
+  int64_t hbm_in_use;       /* device bytes held by resident instances and pack buffers */
+} tn_serve_stats;
+
+tn_status tn_serve_stats_get(tn_server_t srv, tn_serve_stats* out);
 
 /* Stop the scheduler (finishing admitted work) and free the server. */
 tn_status tn_serve_destroy(tn_server_t srv);

@@ -88,7 +88,12 @@ class tn_profile(C.Structure):
 class tn_serve_config(C.Structure):
     _fields_ = [("max_inflight", C.c_int32), ("n_streams", C.c_int32),
                 ("hbm_budget_bytes", C.c_int64), ("queue_capacity", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("pack_max", C.c_int32), ("reserved", C.c_int32 * 2)]
+
+
+class tn_serve_stats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("plan_launches", C.c_int64), ("packs", C.c_int64),
+                ("packed_requests", C.c_int64), ("max_pack", C.c_int64), ("hbm_in_use", C.c_int64)]
 
 
 class tn_cost_model(C.Structure):
@@ -143,6 +148,7 @@ def _load():
         "tn_serve_submit": [vp, vp, C.POINTER(vp), C.POINTER(u64)],
         "tn_serve_poll": [vp, u64, vp, vp, i32],
         "tn_serve_destroy": [vp],
+        "tn_serve_stats_get": [vp, C.POINTER(tn_serve_stats)],
         "tn_dot_noalloc": [vp, vp, i64, i64, i64, i64, vp, vp],
         "tn_batch_plan": [i32, C.POINTER(tn_network), C.POINTER(tn_path), tn_dtype_policy, C.POINTER(vp)],
         "tn_batch_info": [vp, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i32)],
@@ -486,12 +492,13 @@ def _ptr_stream(stream):
 class Server:
     """Continuous-batching request loop (tn_serve_*)."""
 
-    def __init__(self, max_inflight=8, n_streams=4, hbm_budget_bytes=0, queue_capacity=4096):
+    def __init__(self, max_inflight=8, n_streams=4, hbm_budget_bytes=0, queue_capacity=4096, pack_max=0):
         cfg = tn_serve_config()
         cfg.max_inflight = max_inflight
         cfg.n_streams = n_streams
         cfg.hbm_budget_bytes = hbm_budget_bytes
         cfg.queue_capacity = queue_capacity
+        cfg.pack_max = pack_max
         h = C.c_void_p()
         check(lib.tn_serve_create(C.byref(cfg), C.byref(h)))
         self.handle = h
@@ -509,6 +516,11 @@ class Server:
     def poll(self, ticket, result, log_scale=None, timeout_us=-1):
         return lib.tn_serve_poll(self.handle, C.c_uint64(ticket), _ptr(result), _ptr(log_scale),
                                  int(timeout_us))
+
+    def stats(self) -> dict:
+        s = tn_serve_stats()
+        check(lib.tn_serve_stats_get(self.handle, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in tn_serve_stats._fields_}
 
     def destroy(self):
         if getattr(self, "handle", None):

@@ -108,155 +108,181 @@ __global__ void stage_leaves_kernel(const LeafDesc* __restrict__ descs, char* __
 // plane, or eight BF16 values per plane in the split form). When the declared innermost
 // position is itself in the output group, loads run along the output group instead.
 template <bool CPLX>
-__global__ void __launch_bounds__(256) stage_leaf_tiled_kernel(const LeafDesc* __restrict__ descs, int32_t leaf,
+__global__ void __launch_bounds__(256, 4) stage_leaf_tiled_kernel(const LeafDesc* __restrict__ descs, int32_t leaf,
                                                                char* __restrict__ ws, int64_t slice_begin,
                                                                ScaleRec* recs, const int32_t* rec_index) {
+  constexpr int TT = 2;  // tiles in flight per CTA iteration (loads of both before any store)
   const LeafDesc& d = descs[leaf];
-  __shared__ float tre[32][33];
-  __shared__ float tim[CPLX ? 32 : 1][33];
+  __shared__ float tre[TT][32][33];
+  __shared__ float tim[TT][CPLX ? 32 : 1][33];
   // per-tile offset tables: source offset of each input-group and output-group index of the
   // tile (without the rest index), and staged offset of each input-group row; rebuilt only
   // when the tile's chunk indices change (never, when each group fits one 32-wide chunk)
-  __shared__ int64_t s_isrc[32], s_osrc[32], s_irow[32];
-  __shared__ TileCursor s_cur;
-  __shared__ int s_rebuild;
+  __shared__ int64_t s_isrc[TT][32], s_osrc[TT][32], s_irow[TT][32];
+  __shared__ TileCursor s_cur[TT];
+  __shared__ int s_rebuild[TT];
   const int tid = threadIdx.x;
   const int b = blockIdx.y;
   const int64_t tiles = d.Pr * ((d.Po + 31) / 32) * ((d.Pi + 31) / 32);
   const int64_t blk0 = int64_t(blockIdx.x) * kTilesPerCta;
   const int64_t blk1 = blk0 + kTilesPerCta < tiles ? blk0 + kTilesPerCta : tiles;
   const int64_t Pi = d.Pi, Po = d.Po;
+  const bool vec = CPLX && d.vec_load && (reinterpret_cast<uintptr_t>(d.src) & 15) == 0;
+  const int64_t np = CPLX ? cplx_floats(d.split) : 1;
+  float* base = reinterpret_cast<float*>(ws + d.dst) + int64_t(b) * np * d.size;
   int lmax = -127;
-  int64_t prev_co = -1, prev_ci = -1;
-  for (int64_t blk = blk0; blk < blk1; ++blk) {
+  for (int64_t blk = blk0; blk < blk1; blk += TT) {
+    const int nt = blk1 - blk < TT ? static_cast<int>(blk1 - blk) : TT;
     if (tid == 0) {
-      if (blk == blk0) cursor_start(d, blk, slice_begin + b, s_cur);
-      else cursor_next(d, s_cur);
-      s_rebuild = (s_cur.co != prev_co || s_cur.ci != prev_ci) ? 1 : 0;
+      for (int u = 0; u < nt; ++u) {
+        const int64_t pco = u == 0 ? (blk == blk0 ? -1 : s_cur[TT - 1].co) : s_cur[u - 1].co;
+        const int64_t pci = u == 0 ? (blk == blk0 ? -1 : s_cur[TT - 1].ci) : s_cur[u - 1].ci;
+        if (u == 0 && blk == blk0) {
+          cursor_start(d, blk, slice_begin + b, s_cur[0]);
+        } else {
+          s_cur[u] = s_cur[u == 0 ? TT - 1 : u - 1];
+          cursor_next(d, s_cur[u]);
+        }
+        s_rebuild[u] = (s_cur[u].co != pco || s_cur[u].ci != pci) ? 1 : 0;
+      }
     }
     __syncthreads();
-    const int64_t go0 = s_cur.co * 32, gi0 = s_cur.ci * 32, src0 = s_cur.src0, dst0 = s_cur.dst0;
-    if (s_rebuild) {
-      if (tid < 32) {
-        const int64_t gi = gi0 + tid;
-        s_isrc[tid] = gi < Pi ? group_offset(gi, d.ipos, d.ni, d.ext, d.sstride) : 0;
-      } else if (tid < 64) {
-        const int64_t go = go0 + (tid - 32);
-        s_osrc[tid - 32] = go < Po ? tail_offset(go, d.rank, d.no, d.ext, d.sstride) : 0;
-      } else if (tid < 96) {
-        const int64_t gi = gi0 + (tid - 64);
-        s_irow[tid - 64] = gi < Pi ? group_offset(gi, d.ipos, d.ni, d.ext, d.dstride) + go0 : 0;
+    // offset tables of the tiles whose chunks changed (threads 96 u .. 96 u + 95 for tile u)
+    bool any = false;
+    for (int u = 0; u < nt; ++u) any = any || s_rebuild[u];
+    if (any) {
+      const int u = tid / 96, r = tid % 96;
+      if (u < nt && s_rebuild[u]) {
+        const int64_t go0 = s_cur[u].co * 32, gi0 = s_cur[u].ci * 32;
+        if (r < 32) {
+          const int64_t gi = gi0 + r;
+          s_isrc[u][r] = gi < Pi ? group_offset(gi, d.ipos, d.ni, d.ext, d.sstride) : 0;
+        } else if (r < 64) {
+          const int64_t go = go0 + (r - 32);
+          s_osrc[u][r - 32] = go < Po ? tail_offset(go, d.rank, d.no, d.ext, d.sstride) : 0;
+        } else {
+          const int64_t gi = gi0 + (r - 64);
+          s_irow[u][r - 64] = gi < Pi ? group_offset(gi, d.ipos, d.ni, d.ext, d.dstride) + go0 : 0;
+        }
       }
       __syncthreads();
     }
-    prev_co = s_cur.co;
-    prev_ci = s_cur.ci;
-    // ---- load the tile: tre[ti][to] = element (output-group go0 + to, input-group gi0 + ti)
-    if (CPLX && d.vec_load && (reinterpret_cast<uintptr_t>(d.src) & 15) == 0) {
+    // ---- load the tiles: tre[u][ti][to] = element (output-group go0 + to, input-group gi0 + ti)
+    if (vec) {
       const float4* src4 = reinterpret_cast<const float4*>(d.src);
       const int ti = 2 * (tid & 15);
-      const int64_t gi = gi0 + ti;
-  #pragma unroll
-      for (int rep = 0; rep < 2; ++rep) {
-        const int to = (tid >> 4) + 16 * rep;
-        const int64_t go = go0 + to;
-        if (gi < Pi && go < Po) {
+      float4 v[TT][2];
+#pragma unroll
+      for (int u = 0; u < TT; ++u)
+#pragma unroll
+        for (int rep = 0; rep < 2; ++rep) {
+          const int to = (tid >> 4) + 16 * rep;
+          const int64_t gi = s_cur[u].ci * 32 + ti, go = s_cur[u].co * 32 + to;
+          v[u][rep] = make_float4(0.f, 0.f, 0.f, 0.f);
           // elements gi and gi + 1 differ in the fastest position only (gi even, extent even)
-          const int64_t so = src0 + s_isrc[ti] + s_osrc[to];
-          const float4 v = __ldg(src4 + (so >> 1));
-          tre[ti][to] = v.x;
-          tim[ti][to] = v.y;
-          tre[ti + 1][to] = v.z;
-          tim[ti + 1][to] = v.w;
-          lmax = max(lmax, exp_of(fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)))));
+          if (u < nt && gi < Pi && go < Po)
+            v[u][rep] = __ldg(src4 + ((s_cur[u].src0 + s_isrc[u][ti] + s_osrc[u][to]) >> 1));
         }
-      }
+#pragma unroll
+      for (int u = 0; u < TT; ++u)
+#pragma unroll
+        for (int rep = 0; rep < 2; ++rep) {
+          const int to = (tid >> 4) + 16 * rep;
+          const float4 w = v[u][rep];
+          tre[u][ti][to] = w.x;
+          tim[u][ti][to] = w.y;
+          tre[u][ti + 1][to] = w.z;
+          tim[u][ti + 1][to] = w.w;
+          lmax = max(lmax, exp_of(fmaxf(fmaxf(fabsf(w.x), fabsf(w.y)), fmaxf(fabsf(w.z), fabsf(w.w)))));
+        }
     } else {
       // one element per load; lanes along the input group, or along the output group when
       // the declared innermost position is there
-      for (int rep = 0; rep < 4; ++rep) {
-        const int a0 = tid & 31, a1 = (tid >> 5) + 8 * rep;
-        const int ti = d.load_o ? a1 : a0, to = d.load_o ? a0 : a1;
-        const int64_t gi = gi0 + ti, go = go0 + to;
-        if (gi < Pi && go < Po) {
-          const int64_t so = src0 + s_isrc[ti] + s_osrc[to];
-          if (CPLX) {
-            const float2 v = __ldg(reinterpret_cast<const float2*>(d.src) + so);
-            tre[ti][to] = v.x;
-            tim[ti][to] = v.y;
-            lmax = max(lmax, exp_of(fmaxf(fabsf(v.x), fabsf(v.y))));
-          } else {
-            const float v = __ldg(reinterpret_cast<const float*>(d.src) + so);
-            tre[ti][to] = v;
-            lmax = max(lmax, exp_of(fabsf(v)));
+      for (int u = 0; u < nt; ++u)
+        for (int rep = 0; rep < 4; ++rep) {
+          const int a0 = tid & 31, a1 = (tid >> 5) + 8 * rep;
+          const int ti = d.load_o ? a1 : a0, to = d.load_o ? a0 : a1;
+          const int64_t gi = s_cur[u].ci * 32 + ti, go = s_cur[u].co * 32 + to;
+          if (gi < Pi && go < Po) {
+            const int64_t so = s_cur[u].src0 + s_isrc[u][ti] + s_osrc[u][to];
+            if (CPLX) {
+              const float2 w = __ldg(reinterpret_cast<const float2*>(d.src) + so);
+              tre[u][ti][to] = w.x;
+              tim[u][ti][to] = w.y;
+              lmax = max(lmax, exp_of(fmaxf(fabsf(w.x), fabsf(w.y))));
+            } else {
+              const float w = __ldg(reinterpret_cast<const float*>(d.src) + so);
+              tre[u][ti][to] = w;
+              lmax = max(lmax, exp_of(fabsf(w)));
+            }
           }
         }
-      }
     }
     __syncthreads();
-    // ---- store: a row of the tile (fixed input-group index) is contiguous in the staged copy
-    const int64_t np = CPLX ? cplx_floats(d.split) : 1;
-    float* base = reinterpret_cast<float*>(ws + d.dst) + int64_t(b) * np * d.size;
-    if (CPLX && d.split) {
-      // eight consecutive elements per thread and plane: 16-byte stores of BF16
-      const int q = tid & 3, ti = tid >> 2;
-      const int64_t gi = gi0 + ti;
-      if (ti < 32 && gi < d.Pi) {
-        const int64_t row = dst0 + s_irow[ti];
-        const int to = 8 * q;
-        if (go0 + to + 7 < d.Po && ((row + to) & 7) == 0 && (d.size & 7) == 0) {
-          // planes in storage order: split form [rh | ih | rl | il], 3M form [rh | rl | ih | il | sh | sl]
-          uint32_t pl[6][8];
-  #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const float vr = tre[ti][to + u], vi = tim[ti][to + u];
-            __nv_bfloat16 rh, rl, ih, il, sh, sl;
-            split_pair(vr, rh, rl);
-            split_pair(vi, ih, il);
-            split_pair(vr + vi, sh, sl);
-            const bool m3 = d.split == kFmtSplit3M;
-            pl[0][u] = __bfloat16_as_ushort(rh);
-            pl[1][u] = __bfloat16_as_ushort(m3 ? rl : ih);
-            pl[2][u] = __bfloat16_as_ushort(m3 ? ih : rl);
-            pl[3][u] = __bfloat16_as_ushort(il);
-            pl[4][u] = __bfloat16_as_ushort(sh);
-            pl[5][u] = __bfloat16_as_ushort(sl);
-          }
-          uint16_t* S = reinterpret_cast<uint16_t*>(base) + row + to;
-          auto pack = [](const uint32_t* x) {
-            return make_uint4(x[0] | (x[1] << 16), x[2] | (x[3] << 16), x[4] | (x[5] << 16), x[6] | (x[7] << 16));
-          };
-          const int planes = d.split == kFmtSplit3M ? 6 : 4;
-          for (int p = 0; p < planes; ++p) *reinterpret_cast<uint4*>(S + p * d.size) = pack(pl[p]);
-        } else {
-          for (int u = 0; u < 8; ++u)
-            if (go0 + to + u < d.Po)
-              store_cplx(base, d.size, row + to + u, tre[ti][to + u], tim[ti][to + u], d.split);
-        }
-      }
-    } else {
-      // four consecutive FP32 values per thread and plane: 16-byte stores
-      const int q = tid & 7, ti = tid >> 3;
-      const int64_t gi = gi0 + ti;
-      if (gi < d.Pi) {
-        const int64_t row = dst0 + s_irow[ti];
-        const int to = 4 * q;
-        if (go0 + to + 3 < d.Po && ((row + to) & 3) == 0 && (d.size & 3) == 0) {
-          *reinterpret_cast<float4*>(base + row + to) =
-              make_float4(tre[ti][to], tre[ti][to + 1], tre[ti][to + 2], tre[ti][to + 3]);
-          if (CPLX)
-            *reinterpret_cast<float4*>(base + d.size + row + to) =
-                make_float4(tim[ti][to], tim[ti][to + 1], tim[ti][to + 2], tim[ti][to + 3]);
-        } else {
-          for (int u = 0; u < 4; ++u)
-            if (go0 + to + u < d.Po) {
-              base[row + to + u] = tre[ti][to + u];
-              if (CPLX) base[d.size + row + to + u] = tim[ti][to + u];
+    // ---- store: a row of a tile (fixed input-group index) is contiguous in the staged copy
+    for (int u = 0; u < nt; ++u) {
+      const int64_t go0 = s_cur[u].co * 32, gi0 = s_cur[u].ci * 32, dst0 = s_cur[u].dst0;
+      if (CPLX && d.split) {
+        // eight consecutive elements per thread and plane: 16-byte stores of BF16
+        const int q = tid & 3, ti = tid >> 2;
+        const int64_t gi = gi0 + ti;
+        if (ti < 32 && gi < Pi) {
+          const int64_t row = dst0 + s_irow[u][ti];
+          const int to = 8 * q;
+          if (go0 + to + 7 < Po && ((row + to) & 7) == 0 && (d.size & 7) == 0) {
+            // planes in storage order: split form [rh | ih | rl | il], 3M form [rh | rl | ih | il | sh | sl]
+            uint32_t pl[6][8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const float vr = tre[u][ti][to + e], vi = tim[u][ti][to + e];
+              __nv_bfloat16 rh, rl, ih, il, sh, sl;
+              split_pair(vr, rh, rl);
+              split_pair(vi, ih, il);
+              split_pair(vr + vi, sh, sl);
+              const bool m3 = d.split == kFmtSplit3M;
+              pl[0][e] = __bfloat16_as_ushort(rh);
+              pl[1][e] = __bfloat16_as_ushort(m3 ? rl : ih);
+              pl[2][e] = __bfloat16_as_ushort(m3 ? ih : rl);
+              pl[3][e] = __bfloat16_as_ushort(il);
+              pl[4][e] = __bfloat16_as_ushort(sh);
+              pl[5][e] = __bfloat16_as_ushort(sl);
             }
+            uint16_t* S = reinterpret_cast<uint16_t*>(base) + row + to;
+            auto pack = [](const uint32_t* x) {
+              return make_uint4(x[0] | (x[1] << 16), x[2] | (x[3] << 16), x[4] | (x[5] << 16), x[6] | (x[7] << 16));
+            };
+            const int planes = d.split == kFmtSplit3M ? 6 : 4;
+            for (int p = 0; p < planes; ++p) *reinterpret_cast<uint4*>(S + p * d.size) = pack(pl[p]);
+          } else {
+            for (int e = 0; e < 8; ++e)
+              if (go0 + to + e < Po)
+                store_cplx(base, d.size, row + to + e, tre[u][ti][to + e], tim[u][ti][to + e], d.split);
+          }
+        }
+      } else {
+        // four consecutive FP32 values per thread and plane: 16-byte stores
+        const int q = tid & 7, ti = tid >> 3;
+        const int64_t gi = gi0 + ti;
+        if (gi < Pi) {
+          const int64_t row = dst0 + s_irow[u][ti];
+          const int to = 4 * q;
+          if (go0 + to + 3 < Po && ((row + to) & 3) == 0 && (d.size & 3) == 0) {
+            *reinterpret_cast<float4*>(base + row + to) =
+                make_float4(tre[u][ti][to], tre[u][ti][to + 1], tre[u][ti][to + 2], tre[u][ti][to + 3]);
+            if (CPLX)
+              *reinterpret_cast<float4*>(base + d.size + row + to) =
+                  make_float4(tim[u][ti][to], tim[u][ti][to + 1], tim[u][ti][to + 2], tim[u][ti][to + 3]);
+          } else {
+            for (int e = 0; e < 4; ++e)
+              if (go0 + to + e < Po) {
+                base[row + to + e] = tre[u][ti][to + e];
+                if (CPLX) base[d.size + row + to + e] = tim[u][ti][to + e];
+              }
+          }
         }
       }
     }
-    __syncthreads();  // the tile buffers and tables are rewritten by the next tile
+    __syncthreads();  // the tile buffers, tables and cursors are rewritten by the next iteration
   }
   if (recs) {
     // exponent record of this copy: the largest exponent over the tiles (the records

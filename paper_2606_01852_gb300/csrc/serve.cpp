@@ -6,6 +6,15 @@
 // concurrently on a ring of CUDA streams, so requests that arrive while others are
 // on the GPU start as soon as resources free up. Each plan keeps a pool of resident
 // device instances (its workspace plus pinned staging), reused across requests.
+//
+// Packing (tn_serve_config.pack_max > 0): requests on small closed unsliced plans whose
+// steps all run on the CUDA cores share one launch of the batched small-network kernel
+// (batch.cu; one CTA per request). The admission step takes the queue's first request and
+// every later queued request of the same arithmetic kind, up to pack_max, concatenates the
+// plans' per-network tables (computed once per plan) and the requests' inputs into one
+// pinned buffer, copies it to a resident device buffer, launches the kernel, and copies the
+// values and log scales back; the pack holds one in-flight slot.
+#include <algorithm>
 #include <atomic>
 #include <climits>
 #include <cstddef>
@@ -23,6 +32,7 @@
 
 #include <cuda_runtime.h>
 
+#include "batch.h"
 #include "tn_internal.h"
 
 namespace tn {
@@ -42,6 +52,31 @@ struct PlanPool {
   std::vector<std::unique_ptr<Instance>> inst;
 };
 
+// Device and pinned buffers of one packed launch, reused by later packs.
+struct PackBuf {
+  char* dev = nullptr;
+  char* pin = nullptr;
+  size_t dev_bytes = 0, pin_bytes = 0;
+  bool busy = false;
+};
+
+// The batched kernel's tables of a plan (computed once), or why it cannot be packed.
+struct PackTemplate {
+  bool ok = false;
+  BatchTemplate T;
+  int kind = 0;  // 1 complex, 2 real, 3 real with scaling, 4 max-plus
+};
+
+struct Request;
+
+struct Pack {
+  std::vector<Request*> reqs;
+  PackBuf* buf = nullptr;
+  cudaEvent_t done = nullptr;
+  size_t out_off = 0;   // values then logs, in the pinned buffer
+  bool cplx = false;
+};
+
 enum class RState { Queued, Running, Done };
 
 struct Request {
@@ -57,6 +92,7 @@ struct Request {
   double log_scale = 0.0;
   tn_status status = TN_OK;
   std::string err;
+  Pack* pack = nullptr;           // set while it runs in a packed launch
 };
 
 int64_t leaf_bytes(const Plan& P, int32_t t) {
@@ -81,7 +117,12 @@ struct tn_server_s {
   std::map<uint64_t, std::unique_ptr<Request>> reqs;
   std::map<uint64_t, PlanPool> pools;  // by plan uid
   std::vector<Request*> running;
-  int64_t hbm_in_use = 0;        // device bytes held by resident instances (busy or idle)
+  std::vector<Pack*> running_packs;
+  std::map<uint64_t, PackTemplate> templates;  // by plan uid
+  std::vector<std::unique_ptr<PackBuf>> packbufs;
+  int num_sms = 148;
+  int64_t hbm_in_use = 0;        // device bytes held by resident instances and pack buffers
+  tn_serve_stats stats{};
   uint64_t tick = 0;
   uint64_t next_id = 1;
   bool stop = false;
@@ -111,12 +152,198 @@ struct tn_server_s {
             best_i = i;
           }
         }
-      if (!best_pool) return;
+      if (!best_pool) {
+        // then idle pack buffers
+        for (size_t i = 0; i < packbufs.size(); ++i)
+          if (!packbufs[i]->busy) {
+            hbm_in_use -= (int64_t)packbufs[i]->dev_bytes;
+            release_packbuf(*packbufs[i]);
+            packbufs.erase(packbufs.begin() + (std::ptrdiff_t)i);
+            break;
+          }
+        bool any_idle = false;
+        for (auto& pb : packbufs) any_idle = any_idle || !pb->busy;
+        if (hbm_in_use + need > cfg.hbm_budget_bytes && !any_idle) return;
+        continue;
+      }
       Instance& victim = *best_pool->inst[best_i];
       hbm_in_use -= victim.P.total_bytes;
       release(victim);
       best_pool->inst.erase(best_pool->inst.begin() + (std::ptrdiff_t)best_i);
     }
+  }
+
+  static void release_packbuf(PackBuf& b) {
+    if (b.dev) cudaFree(b.dev);
+    if (b.pin) cudaFreeHost(b.pin);
+    b.dev = b.pin = nullptr;
+  }
+
+  // The batched-kernel tables of `plan` (built on first use).
+  const PackTemplate& pack_template(tn_plan_s* plan) {
+    auto it = templates.find(plan->P.uid);
+    if (it != templates.end()) return it->second;
+    PackTemplate pt;
+    const Plan& P = plan->P;
+    const bool simt_only = std::all_of(P.steps.begin(), P.steps.end(),
+                                       [](const StepRec& st) { return st.cls != TN_CLASS_TC; });
+    std::string why;
+    if (simt_only && P.batch == 1 && batch_template(P, pt.T, why)) {
+      pt.ok = true;
+      const bool maxplus = P.policy.semiring == TN_SEMIRING_MAXPLUS;
+      pt.kind = P.is_complex ? 1 : (maxplus ? 4 : (P.policy.exp_scaling ? 3 : 2));
+      if (P.is_complex && P.policy.exp_scaling) pt.ok = false;  // the complex batched kernel is unscaled
+    }
+    return templates.emplace(P.uid, std::move(pt)).first->second;
+  }
+
+  // A free pack buffer of at least the given sizes (freeing a smaller idle one, under the
+  // budget); nullptr if the budget forbids it for now, with `fatal` if it never will.
+  PackBuf* acquire_packbuf(size_t dev_bytes, size_t pin_bytes, std::string& err, bool& fatal) {
+    fatal = false;
+    for (auto& b : packbufs)
+      if (!b->busy && b->dev_bytes >= dev_bytes && b->pin_bytes >= pin_bytes) return b.get();
+    for (size_t i = 0; i < packbufs.size(); ++i)
+      if (!packbufs[i]->busy) {  // too small: give its memory back
+        hbm_in_use -= (int64_t)packbufs[i]->dev_bytes;
+        release_packbuf(*packbufs[i]);
+        packbufs.erase(packbufs.begin() + (std::ptrdiff_t)i);
+        --i;
+      }
+    if (cfg.hbm_budget_bytes > 0 && hbm_in_use + (int64_t)dev_bytes > cfg.hbm_budget_bytes) evict_idle((int64_t)dev_bytes);
+    if (cfg.hbm_budget_bytes > 0 && hbm_in_use + (int64_t)dev_bytes > cfg.hbm_budget_bytes) {
+      if (running.empty() && running_packs.empty()) {
+        err = "a packed launch exceeds the serve HBM budget";
+        fatal = true;
+      }
+      return nullptr;
+    }
+    auto b = std::make_unique<PackBuf>();
+    if (cudaMalloc(&b->dev, dev_bytes) != cudaSuccess || cudaMallocHost(&b->pin, pin_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      release_packbuf(*b);
+      if (running.empty() && running_packs.empty()) {
+        err = "allocation of a pack buffer failed";
+        fatal = true;
+      }
+      return nullptr;
+    }
+    b->dev_bytes = dev_bytes;
+    b->pin_bytes = pin_bytes;
+    hbm_in_use += (int64_t)dev_bytes;
+    packbufs.push_back(std::move(b));
+    return packbufs.back().get();
+  }
+
+  // Launch `group` (requests of one kind) as one batched-kernel launch; false if the
+  // buffers are not available yet (the requests stay queued), fatal errors retire them.
+  bool launch_pack(const std::vector<Request*>& group, bool& fatal, std::string& err) {
+    const PackTemplate& first = pack_template(group[0]->plan);
+    const bool cplx = first.kind == 1;
+    const size_t eb = cplx ? 8 : 4;
+    std::vector<BNet> nets;
+    std::vector<BLeaf> leaves;
+    std::vector<BStep> steps;
+    int64_t arena = 0, in_elems = 0;
+    for (Request* r : group) {
+      const PackTemplate& pt = pack_template(r->plan);
+      BNet bn{};
+      bn.arena = arena;
+      bn.leaf0 = (int32_t)leaves.size();
+      bn.n_leaves = (int32_t)pt.T.leaves.size();
+      bn.step0 = (int32_t)steps.size();
+      bn.n_steps = (int32_t)pt.T.steps.size();
+      bn.root = pt.T.root;
+      bn.root_size = pt.T.root_size;
+      for (BLeaf L : pt.T.leaves) {
+        L.src += in_elems;
+        leaves.push_back(L);
+      }
+      steps.insert(steps.end(), pt.T.steps.begin(), pt.T.steps.end());
+      in_elems += pt.T.input_elems;
+      arena += pt.T.arena_floats;
+      nets.push_back(bn);
+    }
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t n = group.size();
+    const size_t b_nets = al(sizeof(BNet) * n), b_leaves = al(sizeof(BLeaf) * leaves.size());
+    const size_t b_steps = al(sizeof(BStep) * std::max<size_t>(1, steps.size()));
+    const size_t b_in = al(eb * (size_t)in_elems), b_out = al(sizeof(double) * 3 * n);
+    const size_t up = b_nets + b_leaves + b_steps + b_in;            // copied to the device
+    const size_t dev_bytes = up + al(sizeof(float) * (size_t)arena) + b_out + 256;
+    const size_t pin_bytes = up + b_out;
+    PackBuf* buf = acquire_packbuf(dev_bytes, pin_bytes, err, fatal);
+    if (!buf) return false;
+    char* h = buf->pin;
+    std::memcpy(h, nets.data(), sizeof(BNet) * n);
+    std::memcpy(h + b_nets, leaves.data(), sizeof(BLeaf) * leaves.size());
+    if (!steps.empty()) std::memcpy(h + b_nets + b_leaves, steps.data(), sizeof(BStep) * steps.size());
+    size_t pos = b_nets + b_leaves + b_steps;
+    for (Request* r : group) {
+      std::memcpy(h + pos, r->inputs.data(), r->inputs.size());
+      pos += r->inputs.size();
+    }
+    char* d = buf->dev;
+    const size_t off_arena = up, off_out = up + al(sizeof(float) * (size_t)arena), off_q = off_out + b_out;
+    cudaStream_t st = streams[next_stream];
+    next_stream = (next_stream + 1) % (int)streams.size();
+    auto* pk = new Pack();
+    pk->reqs = group;
+    pk->buf = buf;
+    pk->cplx = cplx;
+    pk->out_off = up;
+    cudaError_t e = cudaEventCreateWithFlags(&pk->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h, up, cudaMemcpyHostToDevice, st);
+    const int threads = 128;
+    const int grid = (int)std::min<size_t>(n, (size_t)num_sms * 4);
+    double* vals = reinterpret_cast<double*>(d + off_out);
+    double* logs = vals + 2 * n;
+    if (e == cudaSuccess)
+      e = launch_batch_kernel(reinterpret_cast<BNet*>(d), reinterpret_cast<BLeaf*>(d + b_nets),
+                              reinterpret_cast<BStep*>(d + b_nets + b_leaves), (int32_t)n,
+                              d + b_nets + b_leaves + b_steps, reinterpret_cast<float*>(d + off_arena),
+                              reinterpret_cast<int32_t*>(d + off_q), cplx, first.kind == 3, first.kind == 4,
+                              threads, grid, vals, logs, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h + up, d + off_out, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(pk->done, st);
+    buf->busy = true;
+    for (Request* r : group) {
+      r->pack = pk;
+      r->state = RState::Running;
+      r->status = e == cudaSuccess ? TN_OK : TN_ERR_CUDA;
+      if (e != cudaSuccess) r->err = std::string("packed launch: ") + cudaGetErrorString(e);
+    }
+    running_packs.push_back(pk);
+    stats.packs += 1;
+    stats.packed_requests += (int64_t)n;
+    stats.max_pack = std::max<int64_t>(stats.max_pack, (int64_t)n);
+    return true;
+  }
+
+  void finish_pack(Pack* pk) {
+    cudaError_t e = pk->reqs.front()->status == TN_OK ? cudaEventSynchronize(pk->done) : cudaSuccess;
+    const double* vals = reinterpret_cast<const double*>(pk->buf->pin + pk->out_off);
+    const size_t n = pk->reqs.size();
+    for (size_t i = 0; i < n; ++i) {
+      Request* r = pk->reqs[i];
+      if (r->status == TN_OK && e != cudaSuccess) {
+        r->status = TN_ERR_CUDA;
+        r->err = cudaGetErrorString(e);
+      }
+      if (r->status == TN_OK) {
+        const size_t ob = pk->cplx ? 16 : 8;
+        r->result.assign(reinterpret_cast<const char*>(vals + 2 * i), reinterpret_cast<const char*>(vals + 2 * i) + ob);
+        r->log_scale = vals[2 * n + i];
+      }
+      r->pack = nullptr;
+      r->state = RState::Done;
+      stats.completed += 1;
+      r->inputs.clear();
+      r->inputs.shrink_to_fit();
+    }
+    pk->buf->busy = false;
+    if (pk->done) cudaEventDestroy(pk->done);
+    delete pk;
   }
 
   // Find or create an idle instance of `plan`; nullptr if the budget forbids it for now.
@@ -217,6 +444,7 @@ struct tn_server_s {
     in->busy = false;
     r->inst = nullptr;
     r->state = RState::Done;
+    stats.completed += 1;
     r->inputs.clear();
     r->inputs.shrink_to_fit();
   }
@@ -238,10 +466,53 @@ struct tn_server_s {
           ++i;
         }
       }
+      for (size_t i = 0; i < running_packs.size();) {
+        Pack* pk = running_packs[i];
+        if (pk->reqs.front()->status != TN_OK || cudaEventQuery(pk->done) != cudaErrorNotReady) {
+          finish_pack(pk);
+          running_packs[i] = running_packs.back();
+          running_packs.pop_back();
+          progressed = true;
+        } else {
+          ++i;
+        }
+      }
       if (progressed) cv_done.notify_all();
       // admit in arrival order while slots and memory allow
-      while (!queue.empty() && (int)running.size() < cfg.max_inflight) {
+      while (!queue.empty() && (int)(running.size() + running_packs.size()) < cfg.max_inflight) {
         Request* r = reqs[queue.front()].get();
+        if (cfg.pack_max > 0 && pack_template(r->plan).ok) {
+          // the first request and every later queued one of the same kind, up to pack_max
+          const int kind = pack_template(r->plan).kind;
+          std::vector<Request*> group;
+          std::vector<size_t> idx;
+          for (size_t i = 0; i < queue.size() && (int)group.size() < cfg.pack_max; ++i) {
+            Request* q2 = reqs[queue[i]].get();
+            const PackTemplate& pt = pack_template(q2->plan);
+            if (pt.ok && pt.kind == kind) {
+              group.push_back(q2);
+              idx.push_back(i);
+            }
+          }
+          bool fatal = false;
+          std::string err;
+          const bool launched = launch_pack(group, fatal, err);
+          if (launched || fatal) {
+            for (size_t k = idx.size(); k-- > 0;) queue.erase(queue.begin() + (std::ptrdiff_t)idx[k]);
+          }
+          if (fatal) {
+            for (Request* q2 : group) {
+              q2->status = TN_ERR_OOM;
+              q2->err = err;
+              q2->state = RState::Done;
+            }
+            cv_done.notify_all();
+            continue;
+          }
+          if (!launched) break;  // wait for running work to release memory
+          progressed = true;
+          continue;
+        }
         std::string err;
         bool fatal = false;
         Instance* in = acquire(r->plan, err, fatal);
@@ -263,11 +534,12 @@ struct tn_server_s {
         r->stream = next_stream;
         next_stream = (next_stream + 1) % (int)streams.size();
         launch(r);
+        stats.plan_launches += 1;
         running.push_back(r);
         progressed = true;
       }
-      if (stop && queue.empty() && running.empty()) break;
-      if (running.empty() && queue.empty()) {
+      if (stop && queue.empty() && running.empty() && running_packs.empty()) break;
+      if (running.empty() && running_packs.empty() && queue.empty()) {
         cv_work.wait(lk);
       } else if (!progressed) {
         // in-flight work: poll completions without holding the lock
@@ -288,7 +560,13 @@ tn_status tn_serve_create(const tn_serve_config* cfg, tn_server_t* out) {
   }
   auto* s = new tn_server_s();
   s->cfg = *cfg;
-  if (cudaGetDevice(&s->device) != cudaSuccess) {
+  if (cfg->pack_max < 0) {
+    delete s;
+    set_error("bad serve config: pack_max < 0");
+    return TN_ERR_INVALID;
+  }
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
     delete s;
     set_error("no CUDA device");
     return TN_ERR_CUDA;
@@ -383,6 +661,17 @@ tn_status tn_serve_poll(tn_server_t srv, uint64_t ticket, void* result, double* 
   return s;
 }
 
+tn_status tn_serve_stats_get(tn_server_t srv, tn_serve_stats* out) {
+  if (!srv || !out) {
+    set_error("null argument");
+    return TN_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> g(srv->mu);
+  *out = srv->stats;
+  out->hbm_in_use = srv->hbm_in_use;
+  return TN_OK;
+}
+
 tn_status tn_serve_destroy(tn_server_t srv) {
   if (!srv) return TN_OK;
   {
@@ -393,6 +682,7 @@ tn_status tn_serve_destroy(tn_server_t srv) {
   srv->thr.join();
   for (auto& kv : srv->pools)
     for (auto& in : kv.second.inst) tn_server_s::release(*in);
+  for (auto& b : srv->packbufs) tn_server_s::release_packbuf(*b);
   for (auto& kv : srv->reqs)
     if (kv.second->done) cudaEventDestroy(kv.second->done);
   for (auto st : srv->streams) cudaStreamDestroy(st);

@@ -163,3 +163,79 @@ def test_hbm_budget_two_plans_one_at_a_time(tn):
     assert srv.poll(srv.submit(p_a, host_inputs(a.net)), out, timeout_us=-1) == tn.TN_OK
     assert abs(complex(out) - want[id(a)]) / abs(want[id(a)]) < 1e-5
     srv.destroy()
+
+
+def _pack_jobs(tn):
+    amps = amp_requests(40, seed=4)
+    path = greedy.greedy_path(amps[0], seed=0, alpha=1.0)
+    p_amp = tn.Plan(amps[0], path, prec="3xtf32")  # no step is large enough for the tensor cores
+    assert all(p_amp.step(s)["cls"] != tn.TN_CLASS_TC for s in range(len(path.pairs)))
+    ising = [ising_pf.random_3regular_network(n, s) for n, s in ((20, 5), (32, 6), (48, 7))]
+    i_paths = [greedy.greedy_path(n, seed=0, alpha=1.0) for n in ising]
+    p_ising = [tn.Plan(n, p, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True) for n, p in zip(ising, i_paths)]
+    big = workloads.random_circuit(4, 5, 12, 40)
+    p_big = tn.Plan(big.net, big.path, prec="3xtf32")  # tensor-core steps: never packed
+    jobs = [(p_amp, n, True) for n in amps] + [(p, n, False) for p, n in zip(p_ising, ising)] * 3
+    jobs += [(p_big, big.net, True)] * 2
+    order = np.random.default_rng(8).permutation(len(jobs))
+    return [jobs[j] for j in order], (amps, path, ising, i_paths, big)
+
+
+def test_packed_results_identical_alone_and_in_mix(tn):
+    """With packing on, a request gives the same bits served alone (a pack of one) and in a
+    mix where it shares a launch with others (one CTA per request, fixed order within it),
+    and the values match the oracle."""
+    jobs, (amps, path, ising, i_paths, big) = _pack_jobs(tn)
+
+    def serve_all(one_at_a_time):
+        srv = tn.Server(max_inflight=4, n_streams=2, pack_max=64)
+        res = []
+        if one_at_a_time:
+            for plan, net, cplx in jobs:
+                out = np.zeros((), dtype=np.complex128 if cplx else np.float64)
+                ls = np.zeros(1)
+                assert srv.poll(srv.submit(plan, host_inputs(net, cplx)), out, ls, timeout_us=-1) == tn.TN_OK
+                res.append((out.copy(), ls[0]))
+        else:
+            ts = [srv.submit(plan, host_inputs(net, cplx)) for plan, net, cplx in jobs]
+            for t, (plan, net, cplx) in zip(ts, jobs):
+                out = np.zeros((), dtype=np.complex128 if cplx else np.float64)
+                ls = np.zeros(1)
+                assert srv.poll(t, out, ls, timeout_us=-1) == tn.TN_OK, tn.last_error()
+                res.append((out.copy(), ls[0]))
+        st = srv.stats()
+        srv.destroy()
+        return res, st
+
+    alone, st_alone = serve_all(True)
+    mixed, st_mixed = serve_all(False)
+    n_small = len(jobs) - 2
+    assert st_alone["packed_requests"] == n_small and st_alone["max_pack"] == 1
+    assert st_mixed["packed_requests"] == n_small and st_mixed["max_pack"] > 1
+    assert st_mixed["plan_launches"] == 2 and st_mixed["completed"] == len(jobs)
+    for (a, la), (m, lm) in zip(alone, mixed):
+        assert a == m and la == lm
+    # the values: amplitudes, partition functions (ln Z), and the unpacked circuit
+    want_amp = {id(n): oracle.contract(n, path) for n in amps}
+    want_z = {id(n): np.log(oracle.contract(n, p)) for n, p in zip(ising, i_paths)}
+    want_big = oracle.contract(big.net, big.path)
+    for (plan, net, cplx), (v, ls) in zip(jobs, mixed):
+        if id(net) in want_amp:
+            w = want_amp[id(net)]
+            assert abs(complex(v) - w) / abs(w) < 1e-5
+        elif id(net) in want_z:
+            assert abs(np.log(float(v)) + ls - want_z[id(net)]) < 1e-5
+        else:
+            assert abs(complex(v) - want_big) / abs(want_big) < 1e-5
+
+
+def test_packed_under_budget(tn):
+    """Packing with an HBM budget that also holds the plans' instances: every result OK."""
+    jobs, _ = _pack_jobs(tn)
+    srv = tn.Server(max_inflight=2, n_streams=2, pack_max=16, hbm_budget_bytes=64 << 20)
+    ts = [srv.submit(plan, host_inputs(net, cplx)) for plan, net, cplx in jobs]
+    for t, (plan, net, cplx) in zip(ts, jobs):
+        out = np.zeros((), dtype=np.complex128 if cplx else np.float64)
+        assert srv.poll(t, out, None, timeout_us=-1) == tn.TN_OK, tn.last_error()
+    assert srv.stats()["hbm_in_use"] <= 64 << 20
+    srv.destroy()
