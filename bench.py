@@ -689,12 +689,13 @@ def run_serve_bench(args):
             return pf_in[pf_idx[i]]
         return kis_in
 
-    def serve(prec, max_inflight, n_streams):
+    def serve(prec, max_inflight, n_streams, pack_max=0, budget=0):
         p_amp = tn.Plan(amp_w.net, amp_w.path, prec=prec)
         p_pf = [tn.Plan(w.net, w.path, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True) for w in pf_pool]
         p_kis = tn.Plan(kis.net, kis.path, prec=prec)
         plan_of = lambda i: p_amp if cls[i] == 0 else (p_pf[pf_idx[i]] if cls[i] == 1 else p_kis)
-        srv = tn.Server(max_inflight=max_inflight, n_streams=n_streams, queue_capacity=1 << 20)
+        srv = tn.Server(max_inflight=max_inflight, n_streams=n_streams, queue_capacity=1 << 20, pack_max=pack_max,
+                        hbm_budget_bytes=budget)
         for i in range(min(n_req, 64)):  # warm every plan's first instance
             t = srv.submit(plan_of(i), inputs(i))
             srv.poll(t, np.zeros(2), None, -1)
@@ -740,11 +741,16 @@ def run_serve_bench(args):
                 n_done += 1
             time.sleep(0.0001)
         th.join()
+        stats = srv.stats()
         srv.destroy()
         lat = (done_t - sub_t) * 1e3
         span = done_t.max() - sub_t.min()
         out = {"throughput_req_s": n_req / span, "p50_ms": float(np.percentile(lat, 50)),
-               "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+               "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+               "pack_max": pack_max, "hbm_budget_bytes": budget,
+               "launches": stats["plan_launches"] + stats["packs"], "packs": stats["packs"],
+               "packed_requests": stats["packed_requests"], "max_pack": stats["max_pack"],
+               "hbm_held_bytes": stats["hbm_in_use"]}
         for c, name in enumerate(["amplitude", "partition_function", "kicked_ising_5x5"]):
             sel = lat[cls == c]
             out[name] = {"n": int(sel.size), "p50_ms": float(np.percentile(sel, 50)),
@@ -753,7 +759,9 @@ def run_serve_bench(args):
             p.destroy()
         return out, results
 
-    mixed, r_mixed = serve(PREC[args.serve_prec], args.serve_inflight, args.serve_streams)
+    budget = int(args.serve_budget_gib * 2 ** 30)
+    mixed, r_mixed = serve(PREC[args.serve_prec], args.serve_inflight, args.serve_streams, args.serve_pack, budget)
+    unpacked, r_unpacked = serve(PREC[args.serve_prec], args.serve_inflight, args.serve_streams, 0, budget)
     plain, r_plain = serve(tn.TN_C64_FP32_SIMT, 1, 1)
     # the two forms must agree: amplitudes (CUDA-core steps in both forms) and the kicked-
     # Ising expectations (tensor-core steps in the mixed form), relative differences
@@ -773,9 +781,12 @@ def run_serve_bench(args):
                    "requests": n_req, "mix": {"amplitude_3x4_m8": 0.70, "ising_pf_3reg_20_60": 0.25,
                                               "kicked_ising_5x5_T2": 0.05},
                    "form": args.serve_prec, "max_inflight": args.serve_inflight,
-                   "streams": args.serve_streams},
-        "mixed": mixed, "plain_fp32_one_at_a_time": plain,
+                   "streams": args.serve_streams, "pack_max": args.serve_pack, "hbm_budget_bytes": budget},
+        "mixed": mixed, "mixed_without_packing": unpacked, "plain_fp32_one_at_a_time": plain,
         "p99_speedup": plain["p99_ms"] / mixed["p99_ms"],
+        "p99_speedup_of_packing": unpacked["p99_ms"] / mixed["p99_ms"],
+        "max_rel_diff_amplitudes_packed_vs_unpacked": float(np.max(
+            np.abs(r_mixed[cls == 0] - r_unpacked[cls == 0]).sum(1) / (np.abs(r_unpacked[cls == 0]).sum(1) + 2 ** -6))),
         "max_rel_diff_amplitudes_mixed_vs_plain": amp_err,
         "max_rel_diff_kicked_ising_mixed_vs_plain": kis_err,
         "kicked_ising_rel_err_vs_oracle": kis_vs_oracle,
@@ -798,6 +809,10 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-inflight", type=int, default=16)
     ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-pack", type=int, default=256,
+                    help="serve: requests per packed launch of the batched kernel (0: no packing)")
+    ap.add_argument("--serve-budget-gib", type=float, default=8.0,
+                    help="serve: HBM budget of the request workspaces and pack buffers")
     ap.add_argument("--serve-prec", default="3xtf32", choices=sorted(PREC),
                     help="serve: form of the mixed run (3xtf32: FP32-accurate on every request type)")
     ap.add_argument("--prec", default="bf16x3", choices=sorted(PREC),
