@@ -622,7 +622,7 @@ def run_batch_bench(args):
         lnz_b = np.log(vals[:, 0].cpu().numpy()) + logs.cpu().numpy()
         lnz_s = np.log(outs.cpu().numpy()) + lss.cpu().numpy()
         diff = float(np.max(np.abs(lnz_b - lnz_s)))
-    t, c = b.launch_shape()
+    t, c, g = b.launch_shape()
     fpk = form_peaks(peaks)
     alu = (fpk["maxplus"] if maxplus else fpk["alu"]) / 1e12
     line = {
@@ -634,7 +634,9 @@ def run_batch_bench(args):
                    "desc": ("maximum independent sets of King's subgraphs, L 4-7, density 0.8, max-plus FP32"
                             if maxplus else "Ising partition functions, random 3-regular graphs, 20-60 spins, "
                             "J=+-1, beta=0.5, FP32 + exponent scaling"),
-                   "launch_shape": {"threads": t, "ctas_per_sm": c}, "graph": True},
+                   "launch_shape": {"threads_per_network": t, "ctas_per_sm": c, "networks_per_cta": g,
+                                    "form": "warp per network" if g > 1 else "CTA per network"},
+                   "graph": True},
         "one_launch_per_contraction": {"ms": ms_seq, "networks_per_s": count / (ms_seq / 1e3),
                                        "speedup_of_persistent": ms_seq / ms},
         ("max_abs_diff_vs_per_contraction" if maxplus else "max_abs_lnz_diff_vs_per_contraction"): diff,

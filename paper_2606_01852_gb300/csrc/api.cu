@@ -526,42 +526,58 @@ tn_status tn_plan_check_staging(tn_plan_t plan, int64_t max_slices) {
       // slices 0, n-1, and evenly spread ones between
       const int64_t sid = n_sid == 1 ? 0 : q * (P.n_slices - 1) / (n_sid - 1);
       std::vector<char> seen(d.size, 0);
-      TileCursor cur{};
-      for (int64_t blk = 0; blk < tiles; ++blk) {
-        // the CTA's walk: a fresh cursor every kTilesPerCta tiles, advanced in between
-        if (blk % kTilesPerCta == 0) cursor_start(d, blk, sid, cur);
-        else cursor_next(d, cur);
-        const TileBase tb = tile_base(d, blk, sid);
-        if (cur.co * 32 != tb.go0 || cur.ci * 32 != tb.gi0 || cur.src0 != tb.src0 || cur.dst0 != tb.dst0) {
-          set_error("tiled staging of leaf " + std::to_string(t) + ": the tile cursor disagrees with tile " +
-                    std::to_string(blk));
-          return TN_ERR_INVALID;
-        }
-        for (int ti = 0; ti < 32; ++ti) {
-          const int64_t gi = tb.gi0 + ti;
-          if (gi >= d.Pi) continue;
-          const int64_t row = tile_dst_row(d, tb, gi);
-          for (int to = 0; to < 32; ++to) {
-            const int64_t go = tb.go0 + to;
-            if (go >= d.Po) continue;
-            const int64_t so = tile_src(d, tb, gi, go), el = row + to;
-            // what the per-leaf kernel reads for staged element el
-            int64_t want = 0, e = el;
-            for (int r = d.rank - 1; r >= 0; --r) {
-              want += (e % d.ext[r]) * d.sstride[r];
-              e /= d.ext[r];
-            }
-            for (int k = 0; k < d.n_sl; ++k) want += ((sid / d.sl_div[k]) % d.sl_ext[k]) * d.sl_stride[k];
-            bool ok = el >= 0 && el < d.size && so == want && so >= 0 && so < src_elems && !seen[el];
-            if (ok && d.vec_load && (ti % 2) == 0) ok = so % 2 == 0 && tile_src(d, tb, gi + 1, go) == so + 1;
-            if (!ok) {
-              set_error("tiled staging of leaf " + std::to_string(t) + ": tile " + std::to_string(blk) +
-                        " entry (" + std::to_string(ti) + ", " + std::to_string(to) + ") maps source " +
-                        std::to_string(so) + " to element " + std::to_string(el) + " (expected source " +
-                        std::to_string(want) + ")");
+      // each CTA as the kernel runs it: iterations of kTilesInFlight tiles, slot tables
+      // rebuilt only when iteration_tiles says so, element offsets read from the tables
+      constexpr int TT = kTilesInFlight;
+      for (int64_t blk0 = 0; blk0 < tiles; blk0 += kTilesPerCta) {
+        const int64_t blk1 = std::min<int64_t>(blk0 + kTilesPerCta, tiles);
+        TileCursor cur[TT];
+        int64_t built[TT][2] = {{-1, -1}, {-1, -1}};
+        int rebuild[TT] = {0, 0};
+        int64_t isrc[TT][32] = {}, osrc[TT][32] = {}, irow[TT][32] = {};
+        for (int64_t blk = blk0; blk < blk1; blk += TT) {
+          const int nt = iteration_tiles(d, blk, blk0, blk1, sid, cur, built, rebuild);
+          for (int u = 0; u < nt; ++u) {
+            const TileBase tb = tile_base(d, blk + u, sid);
+            if (cur[u].co * 32 != tb.go0 || cur[u].ci * 32 != tb.gi0 || cur[u].src0 != tb.src0 ||
+                cur[u].dst0 != tb.dst0) {
+              set_error("tiled staging of leaf " + std::to_string(t) + ": the tile cursor disagrees with tile " +
+                        std::to_string(blk + u));
               return TN_ERR_INVALID;
             }
-            seen[el] = 1;
+            if (rebuild[u])
+              for (int r = 0; r < 32; ++r) table_entry(d, tb.go0, tb.gi0, r, isrc[u][r], osrc[u][r], irow[u][r]);
+          }
+          for (int u = 0; u < nt; ++u) {
+            const TileBase tb = tile_base(d, blk + u, sid);
+            for (int ti = 0; ti < 32; ++ti) {
+              const int64_t gi = tb.gi0 + ti;
+              if (gi >= d.Pi) continue;
+              for (int to = 0; to < 32; ++to) {
+                const int64_t go = tb.go0 + to;
+                if (go >= d.Po) continue;
+                const int64_t so = cur[u].src0 + isrc[u][ti] + osrc[u][to], el = cur[u].dst0 + irow[u][ti] + to;
+                // what the per-leaf kernel reads for staged element el
+                int64_t want = 0, e = el;
+                for (int r = d.rank - 1; r >= 0; --r) {
+                  want += (e % d.ext[r]) * d.sstride[r];
+                  e /= d.ext[r];
+                }
+                for (int k = 0; k < d.n_sl; ++k) want += ((sid / d.sl_div[k]) % d.sl_ext[k]) * d.sl_stride[k];
+                bool ok = el >= 0 && el < d.size && so == want && so >= 0 && so < src_elems && !seen[el] &&
+                          so == tile_src(d, tb, gi, go) && el == tile_dst_row(d, tb, gi) + to;
+                if (ok && d.vec_load && (ti % 2) == 0)
+                  ok = so % 2 == 0 && cur[u].src0 + isrc[u][ti + 1] + osrc[u][to] == so + 1;
+                if (!ok) {
+                  set_error("tiled staging of leaf " + std::to_string(t) + ": tile " + std::to_string(blk + u) +
+                            " entry (" + std::to_string(ti) + ", " + std::to_string(to) + ") maps source " +
+                            std::to_string(so) + " to element " + std::to_string(el) + " (expected source " +
+                            std::to_string(want) + ")");
+                  return TN_ERR_INVALID;
+                }
+                seen[el] = 1;
+              }
+            }
           }
         }
       }

@@ -152,6 +152,111 @@ __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restr
   }
 }
 
+// The warp-per-network form of batch_kernel (K-FUSE): each warp takes networks from the
+// queue and runs a whole path with warp-synchronous steps -- no block barriers between
+// steps, and as many networks in flight per SM as resident warps. The same tables, the
+// same arithmetic per output element (one lane, k in order) and the same exact power-of-two
+// renormalisation, so a network's value does not depend on the form that computed it.
+template <bool CPLX>
+__device__ int warp_renormalise(float* t, int size, int lane) {
+  int lmax = -127;
+  for (int i = lane; i < size; i += 32) {
+    float v = fabsf(t[i]);
+    if (CPLX) v = fmaxf(v, fabsf(t[size + i]));
+    lmax = max(lmax, bexp_of(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  const int e = lmax < -126 ? 0 : lmax;  // an all-zero tensor is left as is
+  if (e != 0) {
+    const float sc = bpow2_neg(e);
+    for (int i = lane; i < size; i += 32) {
+      t[i] *= sc;
+      if (CPLX) t[size + i] *= sc;
+    }
+  }
+  __syncwarp();
+  return e;
+}
+
+template <bool CPLX, bool MAXPLUS = false>
+__global__ void batch_warp_kernel(const BNet* __restrict__ nets, const BLeaf* __restrict__ leaves,
+                                  const BStep* __restrict__ steps, int32_t n_nets, const float* __restrict__ in,
+                                  float* arena, int32_t* queue, int32_t scaling, double* values, double* logs) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(queue, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= n_nets) break;
+    const BNet net = nets[w];
+    float* ar = arena + net.arena;
+    long long slog = 0;
+    for (int l = 0; l < net.n_leaves; ++l) {
+      const BLeaf& L = leaves[net.leaf0 + l];
+      for (int e = lane; e < L.size; e += 32) {
+        int r = e, src = 0;
+        for (int d = L.rank - 1; d >= 0; --d) {
+          src += (r % L.ext[d]) * L.sstride[d];
+          r /= L.ext[d];
+        }
+        if (CPLX) {
+          const float2 v = reinterpret_cast<const float2*>(in)[L.src + src];
+          ar[L.dst + e] = v.x;
+          ar[L.dst + L.size + e] = v.y;
+        } else {
+          ar[L.dst + e] = in[L.src + src];
+        }
+      }
+    }
+    __syncwarp();
+    if (scaling)
+      for (int l = 0; l < net.n_leaves; ++l) {
+        const BLeaf& L = leaves[net.leaf0 + l];
+        slog += warp_renormalise<CPLX>(ar + L.dst, L.size, lane);
+      }
+    for (int s = 0; s < net.n_steps; ++s) {
+      const BStep& S = steps[net.step0 + s];
+      const int mn = S.m * S.n;
+      for (int o = lane; o < mn; o += 32) {
+        const int i = o / S.n, j = o - i * S.n;
+        const float* A = ar + S.a + i * S.k;
+        const float* B = ar + S.b + j * S.k;
+        float cr = MAXPLUS ? __int_as_float(0xff800000) : 0.f, ci = 0.f;
+        for (int t = 0; t < S.k; ++t) {
+          if (CPLX) {
+            const float xr = A[t], xi = A[S.a_size + t], yr = B[t], yi = B[S.b_size + t];
+            cr = fmaf(xr, yr, fmaf(-xi, yi, cr));
+            ci = fmaf(xr, yi, fmaf(xi, yr, ci));
+          } else if (MAXPLUS) {
+            cr = fmaxf(cr, A[t] + B[t]);
+          } else {
+            cr = fmaf(A[t], B[t], cr);
+          }
+        }
+        int ro = 0, co = 0, r = i, c = j;
+        for (int d = S.nr - 1; d >= 0; --d) {
+          ro += (r % S.rext[d]) * S.rstr[d];
+          r /= S.rext[d];
+        }
+        for (int d = S.nc - 1; d >= 0; --d) {
+          co += (c % S.cext[d]) * S.cstr[d];
+          c /= S.cext[d];
+        }
+        ar[S.c + ro + co] = cr;
+        if (CPLX) ar[S.c + S.c_size + ro + co] = ci;
+      }
+      __syncwarp();
+      if (scaling) slog += warp_renormalise<CPLX>(ar + S.c, S.c_size, lane);
+    }
+    if (lane == 0) {
+      values[2 * (int64_t)w] = ar[net.root];
+      values[2 * (int64_t)w + 1] = CPLX ? ar[net.root + net.root_size] : 0.0;
+      logs[w] = double(slog) * 0.69314718055994530942;
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
 }  // namespace tn
 
@@ -172,6 +277,7 @@ struct tn_batch_s {
   float* d_arena = nullptr;
   int32_t* d_queue = nullptr;
   int threads = 128, ctas_per_sm = 4, num_sms = 148;
+  int nets_per_cta = 1;              // > 1: one warp per network, this many warps per CTA
   double flops = 0;
   // graph cache
   cudaGraphExec_t gexec = nullptr;
@@ -186,10 +292,22 @@ namespace tn {
 cudaError_t launch_batch_kernel(const BNet* nets, const BLeaf* leaves, const BStep* steps, int32_t n_nets,
                                 const void* packed, float* arena, int32_t* queue, bool cplx, bool scaling,
                                 bool maxplus, int threads, int grid, double* values, double* logs,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool warp) {
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   const float* in = static_cast<const float*>(packed);
+  if (warp) {
+    if (cplx)
+      batch_warp_kernel<true><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue,
+                                                        scaling ? 1 : 0, values, logs);
+    else if (maxplus)
+      batch_warp_kernel<false, true><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue, 0,
+                                                               values, logs);
+    else
+      batch_warp_kernel<false><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue,
+                                                         scaling ? 1 : 0, values, logs);
+    return cudaGetLastError();
+  }
   if (cplx)
     batch_kernel<true><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue, scaling ? 1 : 0,
                                                  values, logs);
@@ -277,9 +395,12 @@ bool batch_template(const Plan& P, BatchTemplate& T, std::string& err) {
 
 namespace {
 tn_status launch_batch(tn_batch_s* B, const void* packed, double* values, double* logs, cudaStream_t st) {
-  const int grid = std::min<int64_t>(B->n_nets, (int64_t)B->num_sms * B->ctas_per_sm);
+  const bool warp = B->nets_per_cta > 1;
+  const int64_t ctas_needed = warp ? (B->n_nets + B->nets_per_cta - 1) / B->nets_per_cta : B->n_nets;
+  const int grid = std::min<int64_t>(ctas_needed, (int64_t)B->num_sms * B->ctas_per_sm);
+  const int threads = warp ? 32 * B->nets_per_cta : B->threads;
   cudaError_t e = launch_batch_kernel(B->d_nets, B->d_leaves, B->d_steps, B->n_nets, packed, B->d_arena, B->d_queue,
-                                      B->cplx, B->scaling, B->maxplus, B->threads, grid, values, logs, st);
+                                      B->cplx, B->scaling, B->maxplus, threads, grid, values, logs, st, warp);
   if (e != cudaSuccess) {
     set_error(std::string("batch kernel launch: ") + cudaGetErrorString(e));
     return TN_ERR_CUDA;
@@ -395,7 +516,7 @@ tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* p
 }
 
 tn_status tn_batch_info(tn_batch_t b, int64_t* leaf_offsets, double* flops, int32_t* threads,
-                        int32_t* ctas_per_sm) {
+                        int32_t* ctas_per_sm, int32_t* nets_per_cta) {
   if (!b) {
     set_error("null batch");
     return TN_ERR_INVALID;
@@ -404,6 +525,7 @@ tn_status tn_batch_info(tn_batch_t b, int64_t* leaf_offsets, double* flops, int3
   if (flops) *flops = b->flops;
   if (threads) *threads = b->threads;
   if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  if (nets_per_cta) *nets_per_cta = b->nets_per_cta;
   return TN_OK;
 }
 
@@ -471,11 +593,20 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int bt = b->threads, bc = b->ctas_per_sm;
-  for (int t : cand_threads)
+  int bt = b->threads, bc = b->ctas_per_sm, bg = b->nets_per_cta;
+  // (threads per network, networks per CTA): a CTA per network at 32-256 threads, or a warp
+  // per network with 4 or 8 warps per CTA
+  struct Shape { int t, g; };
+  std::vector<Shape> shapes;
+  for (int t : cand_threads) shapes.push_back({t, 1});
+  shapes.push_back({32, 4});
+  shapes.push_back({32, 8});
+  for (const Shape& sh : shapes)
     for (int c : cand_ctas) {
-      if (t * c > 2048) continue;
-      b->threads = t;
+      const int cta_threads = sh.g > 1 ? 32 * sh.g : sh.t;
+      if (cta_threads * c > 2048) continue;
+      b->threads = sh.t;
+      b->nets_per_cta = sh.g;
       b->ctas_per_sm = c;
       float ms_best = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
@@ -494,11 +625,13 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
       }
       if (ms_best < best) {
         best = ms_best;
-        bt = t;
+        bt = sh.t;
+        bg = sh.g;
         bc = c;
       }
     }
   b->threads = bt;
+  b->nets_per_cta = bg;
   b->ctas_per_sm = bc;
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
@@ -506,6 +639,24 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  return TN_OK;
+}
+
+tn_status tn_batch_set_shape(tn_batch_t b, int32_t threads, int32_t ctas_per_sm, int32_t nets_per_cta) {
+  const bool warp = nets_per_cta > 1;
+  const int cta_threads = warp ? 32 * nets_per_cta : threads;
+  if (!b || ctas_per_sm < 1 || nets_per_cta < 1 || (warp && threads != 32) || cta_threads < 32 ||
+      cta_threads > 1024 || cta_threads % 32 != 0 || cta_threads * ctas_per_sm > 2048) {
+    set_error("tn_batch_set_shape: bad launch shape");
+    return TN_ERR_INVALID;
+  }
+  b->threads = threads;
+  b->ctas_per_sm = ctas_per_sm;
+  b->nets_per_cta = nets_per_cta;
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
   return TN_OK;
 }
 

@@ -57,10 +57,11 @@ struct BatchTemplate {
 // tensor-core steps); false with a reason when the batched kernel cannot run it.
 bool batch_template(const Plan& P, BatchTemplate& T, std::string& err);
 
-// Launch the persistent kernel over n_nets networks (queue reset included).
+// Launch the persistent kernel over n_nets networks (queue reset included): a CTA of
+// `threads` per network, or with `warp` a warp per network (threads = 32 x warps per CTA).
 cudaError_t launch_batch_kernel(const BNet* nets, const BLeaf* leaves, const BStep* steps, int32_t n_nets,
                                 const void* packed, float* arena, int32_t* queue, bool cplx, bool scaling,
                                 bool maxplus, int threads, int grid, double* values, double* logs,
-                                cudaStream_t st);
+                                cudaStream_t st, bool warp = false);
 
 }  // namespace tn

@@ -111,16 +111,17 @@ template <bool CPLX>
 __global__ void __launch_bounds__(256, 4) stage_leaf_tiled_kernel(const LeafDesc* __restrict__ descs, int32_t leaf,
                                                                char* __restrict__ ws, int64_t slice_begin,
                                                                ScaleRec* recs, const int32_t* rec_index) {
-  constexpr int TT = 2;  // tiles in flight per CTA iteration (loads of both before any store)
+  constexpr int TT = kTilesInFlight;  // tiles per CTA iteration (loads of all before any store)
   const LeafDesc& d = descs[leaf];
   __shared__ float tre[TT][32][33];
   __shared__ float tim[TT][CPLX ? 32 : 1][33];
-  // per-tile offset tables: source offset of each input-group and output-group index of the
-  // tile (without the rest index), and staged offset of each input-group row; rebuilt only
-  // when the tile's chunk indices change (never, when each group fits one 32-wide chunk)
+  // per-tile offset tables (table_entry): rebuilt only when a slot's chunk indices change
+  // (never, when each group fits one 32-wide chunk)
   __shared__ int64_t s_isrc[TT][32], s_osrc[TT][32], s_irow[TT][32];
   __shared__ TileCursor s_cur[TT];
   __shared__ int s_rebuild[TT];
+  __shared__ int64_t s_built[TT][2];
+  __shared__ int s_nt;
   const int tid = threadIdx.x;
   const int b = blockIdx.y;
   const int64_t tiles = d.Pr * ((d.Po + 31) / 32) * ((d.Pi + 31) / 32);
@@ -130,41 +131,19 @@ __global__ void __launch_bounds__(256, 4) stage_leaf_tiled_kernel(const LeafDesc
   const bool vec = CPLX && d.vec_load && (reinterpret_cast<uintptr_t>(d.src) & 15) == 0;
   const int64_t np = CPLX ? cplx_floats(d.split) : 1;
   float* base = reinterpret_cast<float*>(ws + d.dst) + int64_t(b) * np * d.size;
+  if (tid < TT) s_built[tid][0] = s_built[tid][1] = -1;
   int lmax = -127;
   for (int64_t blk = blk0; blk < blk1; blk += TT) {
-    const int nt = blk1 - blk < TT ? static_cast<int>(blk1 - blk) : TT;
-    if (tid == 0) {
-      for (int u = 0; u < nt; ++u) {
-        const int64_t pco = u == 0 ? (blk == blk0 ? -1 : s_cur[TT - 1].co) : s_cur[u - 1].co;
-        const int64_t pci = u == 0 ? (blk == blk0 ? -1 : s_cur[TT - 1].ci) : s_cur[u - 1].ci;
-        if (u == 0 && blk == blk0) {
-          cursor_start(d, blk, slice_begin + b, s_cur[0]);
-        } else {
-          s_cur[u] = s_cur[u == 0 ? TT - 1 : u - 1];
-          cursor_next(d, s_cur[u]);
-        }
-        s_rebuild[u] = (s_cur[u].co != pco || s_cur[u].ci != pci) ? 1 : 0;
-      }
-    }
+    __syncthreads();  // slot state of the previous iteration is no longer read
+    if (tid == 0) s_nt = iteration_tiles(d, blk, blk0, blk1, slice_begin + b, s_cur, s_built, s_rebuild);
     __syncthreads();
-    // offset tables of the tiles whose chunks changed (threads 96 u .. 96 u + 95 for tile u)
+    const int nt = s_nt;
     bool any = false;
     for (int u = 0; u < nt; ++u) any = any || s_rebuild[u];
     if (any) {
-      const int u = tid / 96, r = tid % 96;
-      if (u < nt && s_rebuild[u]) {
-        const int64_t go0 = s_cur[u].co * 32, gi0 = s_cur[u].ci * 32;
-        if (r < 32) {
-          const int64_t gi = gi0 + r;
-          s_isrc[u][r] = gi < Pi ? group_offset(gi, d.ipos, d.ni, d.ext, d.sstride) : 0;
-        } else if (r < 64) {
-          const int64_t go = go0 + (r - 32);
-          s_osrc[u][r - 32] = go < Po ? tail_offset(go, d.rank, d.no, d.ext, d.sstride) : 0;
-        } else {
-          const int64_t gi = gi0 + (r - 64);
-          s_irow[u][r - 64] = gi < Pi ? group_offset(gi, d.ipos, d.ni, d.ext, d.dstride) + go0 : 0;
-        }
-      }
+      const int u = tid >> 5, r = tid & 31;
+      if (u < nt && s_rebuild[u])
+        table_entry(d, s_cur[u].co * 32, s_cur[u].ci * 32, r, s_isrc[u][r], s_osrc[u][r], s_irow[u][r]);
       __syncthreads();
     }
     // ---- load the tiles: tre[u][ti][to] = element (output-group go0 + to, input-group gi0 + ti)
@@ -282,7 +261,6 @@ __global__ void __launch_bounds__(256, 4) stage_leaf_tiled_kernel(const LeafDesc
         }
       }
     }
-    __syncthreads();  // the tile buffers, tables and cursors are rewritten by the next iteration
   }
   if (recs) {
     // exponent record of this copy: the largest exponent over the tiles (the records

@@ -113,8 +113,41 @@ __host__ __device__ inline void cursor_next(const LeafDesc& d, TileCursor& c) {
   }
 }
 
-// tiles one CTA of the tiled kernel walks
+// tiles one CTA of the tiled kernel walks, and tiles it holds in flight per iteration
 constexpr int kTilesPerCta = 8;
+constexpr int kTilesInFlight = 2;
+
+// One iteration of a CTA at tile blk (its tiles blk0 .. blk1-1): advance the cursors of
+// the iteration's tiles (slot u holds tile blk + u) and decide which slots' offset tables
+// must be rebuilt -- those whose chunk indices differ from the ones the slot's table was
+// last built for (built[u], -1 before the first build). Returns the number of tiles.
+__host__ __device__ inline int iteration_tiles(const LeafDesc& d, int64_t blk, int64_t blk0, int64_t blk1,
+                                               int64_t sid, TileCursor* cur, int64_t (*built)[2], int* rebuild) {
+  const int nt = blk1 - blk < kTilesInFlight ? static_cast<int>(blk1 - blk) : kTilesInFlight;
+  for (int u = 0; u < nt; ++u) {
+    if (u == 0 && blk == blk0) {
+      cursor_start(d, blk, sid, cur[0]);
+    } else {
+      cur[u] = cur[u == 0 ? kTilesInFlight - 1 : u - 1];
+      cursor_next(d, cur[u]);
+    }
+    rebuild[u] = (cur[u].co != built[u][0] || cur[u].ci != built[u][1]) ? 1 : 0;
+    built[u][0] = cur[u].co;
+    built[u][1] = cur[u].ci;
+  }
+  return nt;
+}
+
+// Entry r (0..31) of a tile's offset tables: source offset of input-group index gi0 + r and
+// of output-group index go0 + r (both without the rest index), and staged offset of the
+// row of input-group index gi0 + r (0 past the group's end).
+__host__ __device__ inline void table_entry(const LeafDesc& d, int64_t go0, int64_t gi0, int r, int64_t& isrc,
+                                            int64_t& osrc, int64_t& irow) {
+  const int64_t gi = gi0 + r, go = go0 + r;
+  isrc = gi < d.Pi ? group_offset(gi, d.ipos, d.ni, d.ext, d.sstride) : 0;
+  osrc = go < d.Po ? tail_offset(go, d.rank, d.no, d.ext, d.sstride) : 0;
+  irow = gi < d.Pi ? group_offset(gi, d.ipos, d.ni, d.ext, d.dstride) + go0 : 0;
+}
 
 // Source element (declared order) and staged element of tile entry (ti, to).
 __host__ __device__ inline int64_t tile_src(const LeafDesc& d, const TileBase& t, int64_t gi, int64_t go) {

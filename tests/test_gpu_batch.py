@@ -20,9 +20,10 @@ def tn():
     return ensure_built()
 
 
-def run_batch(tn, nets, paths, complex_=False, scaling=True, graph=False, autotune=False):
-    b = tn.Batch(nets, paths, complex_=complex_, exp_scaling=scaling)
+def run_batch(tn, nets, paths, complex_=False, scaling=True, graph=False, autotune=False, semiring="standard"):
+    b = tn.Batch(nets, paths, complex_=complex_, exp_scaling=scaling, semiring=semiring)
     packed = torch.tensor(b.pack(nets), device="cuda")
+    b._packed = packed
     vals = torch.zeros((len(nets), 2), dtype=torch.float64, device="cuda")
     logs = torch.zeros(len(nets), dtype=torch.float64, device="cuda")
     if autotune:
@@ -80,8 +81,40 @@ def test_graph_replay_and_autotune_match(tn):
     _, v0, l0 = run_batch(tn, nets, paths)
     _, v1, l1 = run_batch(tn, nets, paths, graph=True)
     b2, v2, l2 = run_batch(tn, nets, paths, autotune=True, graph=True)
-    t, c = b2.launch_shape()
-    assert t in (32, 64, 128, 256) and c in (2, 4, 8, 16)
+    t, c, g = b2.launch_shape()
+    assert t in (32, 64, 128, 256) and c in (2, 4, 8, 16) and g in (1, 4, 8)
     # same per-network arithmetic whatever the launch shape: bitwise equal
     assert np.array_equal(v0, v1) and np.array_equal(l0, l1)
     assert np.array_equal(v0, v2) and np.array_equal(l0, l2)
+
+
+@pytest.mark.parametrize("kind", ["ising", "complex", "maxplus"])
+def test_warp_per_network_form_bitwise_equal(tn, kind):
+    """The warp-per-network form (warp-synchronous steps, several networks per CTA) gives
+    the same bits as the CTA-per-network form: one lane computes each output element with
+    k in order, and the renormalisation is an exact power of two chosen from the same
+    maximum. Checked on partition functions (scaled), complex amplitudes and max-plus
+    independent sets, with a ragged last CTA (networks not a multiple of the warps per CTA)."""
+    from tn_inputs import kings
+    if kind == "ising":
+        ws = workloads.ising3r(45, seed=21)
+        nets, paths = [w.net for w in ws], [w.path for w in ws]
+        kw = dict(complex_=False, scaling=True)
+    elif kind == "complex":
+        nets = [circuits.amplitude_network(3, 3, 8, 300 + s) for s in range(13)]
+        paths = [greedy.greedy_path(n, seed=0, alpha=1.0) for n in nets]
+        kw = dict(complex_=True, scaling=False)
+    else:
+        ws = workloads.kings_batch(19, seed=4)
+        nets, paths = [w.net for w in ws], [w.path for w in ws]
+        kw = dict(complex_=False, scaling=False, semiring="maxplus")
+    b, v0, l0 = run_batch(tn, nets, paths, **kw)
+    for shape in ((32, 4, 4), (32, 8, 8), (32, 16, 1), (256, 2, 1)):
+        b.set_launch_shape(*shape)
+        v = torch.zeros_like(torch.tensor(v0)).cuda()
+        l = torch.zeros_like(torch.tensor(l0)).cuda()
+        b.contract(b._packed, v, l)
+        torch.cuda.synchronize()
+        assert np.array_equal(v.cpu().numpy(), v0) and np.array_equal(l.cpu().numpy(), l0), shape
+    with pytest.raises(tn.TnError):
+        b.set_launch_shape(64, 4, 4)  # a warp per network takes 32 threads
