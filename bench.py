@@ -50,6 +50,8 @@ WORKLOAD_DESC = {
     "ktri44": "kicked Ising on a 4x4 triangular lattice, 8 Trotter steps (J=1, dt=0.25, h=0.9), "
               "<Z_centre>, complex64",
     "rc12": "12-qubit 3x4 random circuit, 8 cycles, one amplitude, complex64",
+    "tcgemm": "one dense complex step A[2^14 x 2^13] . B[2^14 x 2^13]^T closed by two vectors (the 14-cycle "
+              "circuit's dominant step shape at k = 2^13), complex64",
     "sv26": "a 26-qubit state (2^26-element leaf, complex64) declared in a shuffled qubit order, "
             "absorbing 4 Haar 2-qubit gates; open output (the state), complex64",
     "rc40c14sub": "the rc40c14 network and path with two more sliced labels (512 slices, largest "
@@ -622,7 +624,7 @@ def run_batch_bench(args):
         lnz_b = np.log(vals[:, 0].cpu().numpy()) + logs.cpu().numpy()
         lnz_s = np.log(outs.cpu().numpy()) + lss.cpu().numpy()
         diff = float(np.max(np.abs(lnz_b - lnz_s)))
-    t, c, g = b.launch_shape()
+    t, c, g, sm = b.launch_shape()
     fpk = form_peaks(peaks)
     alu = (fpk["maxplus"] if maxplus else fpk["alu"]) / 1e12
     line = {
@@ -635,7 +637,8 @@ def run_batch_bench(args):
                             if maxplus else "Ising partition functions, random 3-regular graphs, 20-60 spins, "
                             "J=+-1, beta=0.5, FP32 + exponent scaling"),
                    "launch_shape": {"threads_per_network": t, "ctas_per_sm": c, "networks_per_cta": g,
-                                    "form": "warp per network" if g > 1 else "CTA per network"},
+                                    "form": "warp per network" if g > 1 else "CTA per network",
+                                    "arenas": "shared memory" if sm else "global memory"},
                    "graph": True},
         "one_launch_per_contraction": {"ms": ms_seq, "networks_per_s": count / (ms_seq / 1e3),
                                        "speedup_of_persistent": ms_seq / ms},
@@ -761,7 +764,32 @@ def run_serve_bench(args):
             p.destroy()
         return out, results
 
+    def burst(pack_max, n_burst=2048):
+        """n_burst small requests (amplitudes and partition functions) submitted at once:
+        requests/s from the first submission to the last completion."""
+        p_amp = tn.Plan(amp_w.net, amp_w.path, prec=PREC[args.serve_prec])
+        p_pf = [tn.Plan(w.net, w.path, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True) for w in pf_pool]
+        small = [i for i in range(n_req) if cls[i] != 2][:n_burst]
+        plan_of = lambda i: p_amp if cls[i] == 0 else p_pf[pf_idx[i]]
+        srv = tn.Server(max_inflight=args.serve_inflight, n_streams=args.serve_streams, queue_capacity=1 << 20,
+                        pack_max=pack_max)
+        for i in small[:64]:
+            srv.poll(srv.submit(plan_of(i), inputs(i)), np.zeros(2), None, -1)
+        ins = [inputs(i) for i in small]
+        t0 = time.perf_counter()
+        ts = [srv.submit(plan_of(i), x) for i, x in zip(small, ins)]
+        for t in ts:
+            srv.poll(t, np.zeros(2), None, -1)
+        dt = time.perf_counter() - t0
+        st = srv.stats()
+        srv.destroy()
+        for p in [p_amp] + p_pf:
+            p.destroy()
+        return {"requests": len(small), "seconds": dt, "requests_per_s": len(small) / dt,
+                "launches": st["plan_launches"] + st["packs"] - 64, "max_pack": st["max_pack"]}
+
     budget = int(args.serve_budget_gib * 2 ** 30)
+    burst_packed, burst_unpacked = burst(args.serve_pack), burst(0)
     mixed, r_mixed = serve(PREC[args.serve_prec], args.serve_inflight, args.serve_streams, args.serve_pack, budget)
     unpacked, r_unpacked = serve(PREC[args.serve_prec], args.serve_inflight, args.serve_streams, 0, budget)
     plain, r_plain = serve(tn.TN_C64_FP32_SIMT, 1, 1)
@@ -787,6 +815,9 @@ def run_serve_bench(args):
         "mixed": mixed, "mixed_without_packing": unpacked, "plain_fp32_one_at_a_time": plain,
         "p99_speedup": plain["p99_ms"] / mixed["p99_ms"],
         "p99_speedup_of_packing": unpacked["p99_ms"] / mixed["p99_ms"],
+        "burst_of_small_requests": {"packed": burst_packed, "unpacked": burst_unpacked,
+                                    "speedup_of_packing": burst_packed["requests_per_s"] /
+                                    burst_unpacked["requests_per_s"]},
         "max_rel_diff_amplitudes_packed_vs_unpacked": float(np.max(
             np.abs(r_mixed[cls == 0] - r_unpacked[cls == 0]).sum(1) / (np.abs(r_unpacked[cls == 0]).sum(1) + 2 ** -6))),
         "max_rel_diff_amplitudes_mixed_vs_plain": amp_err,

@@ -152,11 +152,11 @@ def _load():
         "tn_dot_noalloc": [vp, vp, i64, i64, i64, i64, vp, vp],
         "tn_batch_plan": [i32, C.POINTER(tn_network), C.POINTER(tn_path), tn_dtype_policy, C.POINTER(vp)],
         "tn_batch_info": [vp, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i32),
-                          C.POINTER(i32)],
+                          C.POINTER(i32), C.POINTER(i32)],
         "tn_batch_contract": [vp, vp, vp, vp, vp],
         "tn_batch_contract_graph": [vp, vp, vp, vp, vp],
         "tn_batch_autotune": [vp, vp, vp, vp, vp],
-        "tn_batch_set_shape": [vp, i32, i32, i32],
+        "tn_batch_set_shape": [vp, i32, i32, i32, i32],
         "tn_batch_destroy": [vp],
         "tn_plan_distribute": [vp, C.POINTER(tn_dist_config), C.POINTER(tn_dist_report), C.POINTER(tn_dist_step)],
         "tn_cost_model_set": [C.POINTER(tn_cost_model)],
@@ -416,7 +416,7 @@ class Batch:
         self.n_leaves = sum(len(n.modes) for n in nets)
         off = (C.c_int64 * (self.n_leaves + 1))()
         fl = C.c_double()
-        check(lib.tn_batch_info(h, off, C.byref(fl), None, None, None))
+        check(lib.tn_batch_info(h, off, C.byref(fl), None, None, None, None))
         self.leaf_offsets = list(off)
         self.flops = fl.value
 
@@ -433,14 +433,15 @@ class Batch:
         return out
 
     def launch_shape(self):
-        """(threads per network, CTAs per SM, networks per CTA)."""
-        t, c, g = C.c_int32(), C.c_int32(), C.c_int32()
-        check(lib.tn_batch_info(self.handle, None, None, C.byref(t), C.byref(c), C.byref(g)))
-        return t.value, c.value, g.value
+        """(threads per network, CTAs per SM, networks per CTA, arenas in shared memory)."""
+        t, c, g, m = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        check(lib.tn_batch_info(self.handle, None, None, C.byref(t), C.byref(c), C.byref(g), C.byref(m)))
+        return t.value, c.value, g.value, bool(m.value)
 
-    def set_launch_shape(self, threads, ctas_per_sm, nets_per_cta=1):
+    def set_launch_shape(self, threads, ctas_per_sm, nets_per_cta=1, smem_arena=False):
         """Choose a launch shape by hand (tn_batch_set_shape)."""
-        check(lib.tn_batch_set_shape(self.handle, int(threads), int(ctas_per_sm), int(nets_per_cta)))
+        check(lib.tn_batch_set_shape(self.handle, int(threads), int(ctas_per_sm), int(nets_per_cta),
+                                     1 if smem_arena else 0))
 
     def contract(self, packed, values, logs, stream=None, graph=False):
         f = lib.tn_batch_contract_graph if graph else lib.tn_batch_contract

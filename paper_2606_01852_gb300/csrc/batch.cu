@@ -67,7 +67,9 @@ __device__ void renormalise(float* t, int size, int* smax, long long* slog) {
 template <bool CPLX, bool MAXPLUS = false>
 __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restrict__ leaves,
                              const BStep* __restrict__ steps, int32_t n_nets, const float* __restrict__ in,
-                             float* arena, int32_t* queue, int32_t scaling, double* values, double* logs) {
+                             float* arena, int32_t* queue, int32_t scaling, double* values, double* logs,
+                             int32_t smem_arena) {
+  extern __shared__ float s_arena[];
   __shared__ int s_net;
   __shared__ int s_max;
   __shared__ long long s_log;
@@ -82,7 +84,9 @@ __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restr
     const int w = s_net;
     if (w >= n_nets) break;
     const BNet net = nets[w];
-    float* ar = arena + net.arena;
+    // the network's arena: in shared memory when every arena of the batch fits (smem_arena
+    // floats per CTA), else its own slice of the global batch arena
+    float* ar = smem_arena ? s_arena : arena + net.arena;
     // stage the leaves (declared order -> planned order; complex64 -> planar)
     for (int l = 0; l < net.n_leaves; ++l) {
       const BLeaf& L = leaves[net.leaf0 + l];
@@ -181,7 +185,9 @@ __device__ int warp_renormalise(float* t, int size, int lane) {
 template <bool CPLX, bool MAXPLUS = false>
 __global__ void batch_warp_kernel(const BNet* __restrict__ nets, const BLeaf* __restrict__ leaves,
                                   const BStep* __restrict__ steps, int32_t n_nets, const float* __restrict__ in,
-                                  float* arena, int32_t* queue, int32_t scaling, double* values, double* logs) {
+                                  float* arena, int32_t* queue, int32_t scaling, double* values, double* logs,
+                                  int32_t smem_arena) {
+  extern __shared__ float s_arena[];
   const int lane = threadIdx.x & 31;
   while (true) {
     int w = 0;
@@ -189,7 +195,7 @@ __global__ void batch_warp_kernel(const BNet* __restrict__ nets, const BLeaf* __
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_nets) break;
     const BNet net = nets[w];
-    float* ar = arena + net.arena;
+    float* ar = smem_arena ? s_arena + (threadIdx.x >> 5) * smem_arena : arena + net.arena;
     long long slog = 0;
     for (int l = 0; l < net.n_leaves; ++l) {
       const BLeaf& L = leaves[net.leaf0 + l];
@@ -278,6 +284,8 @@ struct tn_batch_s {
   int32_t* d_queue = nullptr;
   int threads = 128, ctas_per_sm = 4, num_sms = 148;
   int nets_per_cta = 1;              // > 1: one warp per network, this many warps per CTA
+  bool smem_arena = false;           // arenas in shared memory (every network's fits)
+  int64_t max_arena_floats = 0;      // largest network arena
   double flops = 0;
   // graph cache
   cudaGraphExec_t gexec = nullptr;
@@ -289,34 +297,50 @@ struct tn_batch_s {
 
 namespace tn {
 
+template <typename K>
+cudaError_t set_smem(K kernel, int bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 cudaError_t launch_batch_kernel(const BNet* nets, const BLeaf* leaves, const BStep* steps, int32_t n_nets,
                                 const void* packed, float* arena, int32_t* queue, bool cplx, bool scaling,
                                 bool maxplus, int threads, int grid, double* values, double* logs,
-                                cudaStream_t st, bool warp) {
+                                cudaStream_t st, bool warp, int32_t smem_arena) {
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   const float* in = static_cast<const float*>(packed);
+  const int sc = scaling ? 1 : 0;
+  // dynamic shared memory: one arena per CTA, or one per warp in the warp form
+  const int smem = smem_arena ? smem_arena * 4 * (warp ? threads / 32 : 1) : 0;
   if (warp) {
-    if (cplx)
-      batch_warp_kernel<true><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue,
-                                                        scaling ? 1 : 0, values, logs);
-    else if (maxplus)
-      batch_warp_kernel<false, true><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue, 0,
-                                                               values, logs);
-    else
-      batch_warp_kernel<false><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue,
-                                                         scaling ? 1 : 0, values, logs);
+    if (cplx) {
+      if (smem && (e = set_smem(batch_warp_kernel<true>, smem)) != cudaSuccess) return e;
+      batch_warp_kernel<true><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, sc, values,
+                                                           logs, smem_arena);
+    } else if (maxplus) {
+      if (smem && (e = set_smem(batch_warp_kernel<false, true>, smem)) != cudaSuccess) return e;
+      batch_warp_kernel<false, true><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, 0,
+                                                                  values, logs, smem_arena);
+    } else {
+      if (smem && (e = set_smem(batch_warp_kernel<false>, smem)) != cudaSuccess) return e;
+      batch_warp_kernel<false><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, sc,
+                                                            values, logs, smem_arena);
+    }
     return cudaGetLastError();
   }
-  if (cplx)
-    batch_kernel<true><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue, scaling ? 1 : 0,
-                                                 values, logs);
-  else if (maxplus)
-    batch_kernel<false, true><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue, 0, values,
-                                                        logs);
-  else
-    batch_kernel<false><<<grid, threads, 0, st>>>(nets, leaves, steps, n_nets, in, arena, queue, scaling ? 1 : 0,
-                                                  values, logs);
+  if (cplx) {
+    if (smem && (e = set_smem(batch_kernel<true>, smem)) != cudaSuccess) return e;
+    batch_kernel<true><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, sc, values, logs,
+                                                    smem_arena);
+  } else if (maxplus) {
+    if (smem && (e = set_smem(batch_kernel<false, true>, smem)) != cudaSuccess) return e;
+    batch_kernel<false, true><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, 0, values,
+                                                           logs, smem_arena);
+  } else {
+    if (smem && (e = set_smem(batch_kernel<false>, smem)) != cudaSuccess) return e;
+    batch_kernel<false><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, sc, values,
+                                                     logs, smem_arena);
+  }
   return cudaGetLastError();
 }
 
@@ -394,13 +418,17 @@ bool batch_template(const Plan& P, BatchTemplate& T, std::string& err) {
 }  // namespace tn
 
 namespace {
+constexpr int64_t kMaxSmemPerCta = 227 * 1024;  // dynamic shared memory one CTA may take
+constexpr int64_t kSmemPerSm = 224 * 1024;      // what the SM's resident CTAs share (with headroom)
+
 tn_status launch_batch(tn_batch_s* B, const void* packed, double* values, double* logs, cudaStream_t st) {
   const bool warp = B->nets_per_cta > 1;
   const int64_t ctas_needed = warp ? (B->n_nets + B->nets_per_cta - 1) / B->nets_per_cta : B->n_nets;
   const int grid = std::min<int64_t>(ctas_needed, (int64_t)B->num_sms * B->ctas_per_sm);
   const int threads = warp ? 32 * B->nets_per_cta : B->threads;
   cudaError_t e = launch_batch_kernel(B->d_nets, B->d_leaves, B->d_steps, B->n_nets, packed, B->d_arena, B->d_queue,
-                                      B->cplx, B->scaling, B->maxplus, threads, grid, values, logs, st, warp);
+                                      B->cplx, B->scaling, B->maxplus, threads, grid, values, logs, st, warp,
+                                      B->smem_arena ? static_cast<int32_t>(B->max_arena_floats) : 0);
   if (e != cudaSuccess) {
     set_error(std::string("batch kernel launch: ") + cudaGetErrorString(e));
     return TN_ERR_CUDA;
@@ -474,6 +502,7 @@ tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* p
     B->steps.insert(B->steps.end(), T.steps.begin(), T.steps.end());
     B->flops += T.flops;
     B->arena_floats += T.arena_floats;
+    B->max_arena_floats = std::max(B->max_arena_floats, T.arena_floats);
     B->nets.push_back(bn);
   }
   B->leaf_offset.push_back(in_off);
@@ -516,7 +545,7 @@ tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* p
 }
 
 tn_status tn_batch_info(tn_batch_t b, int64_t* leaf_offsets, double* flops, int32_t* threads,
-                        int32_t* ctas_per_sm, int32_t* nets_per_cta) {
+                        int32_t* ctas_per_sm, int32_t* nets_per_cta, int32_t* smem_arena) {
   if (!b) {
     set_error("null batch");
     return TN_ERR_INVALID;
@@ -526,6 +555,7 @@ tn_status tn_batch_info(tn_batch_t b, int64_t* leaf_offsets, double* flops, int3
   if (threads) *threads = b->threads;
   if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
   if (nets_per_cta) *nets_per_cta = b->nets_per_cta;
+  if (smem_arena) *smem_arena = b->smem_arena ? 1 : 0;
   return TN_OK;
 }
 
@@ -594,6 +624,7 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
   cudaEventCreate(&e1);
   float best = 1e30f;
   int bt = b->threads, bc = b->ctas_per_sm, bg = b->nets_per_cta;
+  bool bs = b->smem_arena;
   // (threads per network, networks per CTA): a CTA per network at 32-256 threads, or a warp
   // per network with 4 or 8 warps per CTA
   struct Shape { int t, g; };
@@ -602,12 +633,17 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
   shapes.push_back({32, 4});
   shapes.push_back({32, 8});
   for (const Shape& sh : shapes)
-    for (int c : cand_ctas) {
+    for (int c : cand_ctas)
+      for (int sm = 0; sm < 2; ++sm) {
       const int cta_threads = sh.g > 1 ? 32 * sh.g : sh.t;
       if (cta_threads * c > 2048) continue;
+      // arenas in shared memory only where c CTAs of them fit an SM
+      const int64_t smem = b->max_arena_floats * 4 * sh.g;
+      if (sm && (smem > kMaxSmemPerCta || smem * c > kSmemPerSm)) continue;
       b->threads = sh.t;
       b->nets_per_cta = sh.g;
       b->ctas_per_sm = c;
+      b->smem_arena = sm != 0;
       float ms_best = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(e0, st);
@@ -628,11 +664,13 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
         bt = sh.t;
         bg = sh.g;
         bc = c;
+        bs = sm != 0;
       }
     }
   b->threads = bt;
   b->nets_per_cta = bg;
   b->ctas_per_sm = bc;
+  b->smem_arena = bs;
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
@@ -642,17 +680,21 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
   return TN_OK;
 }
 
-tn_status tn_batch_set_shape(tn_batch_t b, int32_t threads, int32_t ctas_per_sm, int32_t nets_per_cta) {
+tn_status tn_batch_set_shape(tn_batch_t b, int32_t threads, int32_t ctas_per_sm, int32_t nets_per_cta,
+                             int32_t smem_arena) {
   const bool warp = nets_per_cta > 1;
   const int cta_threads = warp ? 32 * nets_per_cta : threads;
   if (!b || ctas_per_sm < 1 || nets_per_cta < 1 || (warp && threads != 32) || cta_threads < 32 ||
-      cta_threads > 1024 || cta_threads % 32 != 0 || cta_threads * ctas_per_sm > 2048) {
+      cta_threads > 1024 || cta_threads % 32 != 0 || cta_threads * ctas_per_sm > 2048 ||
+      (smem_arena && (b->max_arena_floats * 4 * nets_per_cta > kMaxSmemPerCta ||
+                      b->max_arena_floats * 4 * nets_per_cta * ctas_per_sm > kSmemPerSm))) {
     set_error("tn_batch_set_shape: bad launch shape");
     return TN_ERR_INVALID;
   }
   b->threads = threads;
   b->ctas_per_sm = ctas_per_sm;
   b->nets_per_cta = nets_per_cta;
+  b->smem_arena = smem_arena != 0;
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;

@@ -59,9 +59,11 @@ bool batch_template(const Plan& P, BatchTemplate& T, std::string& err);
 
 // Launch the persistent kernel over n_nets networks (queue reset included): a CTA of
 // `threads` per network, or with `warp` a warp per network (threads = 32 x warps per CTA).
+// smem_arena > 0: every network's arena (at most smem_arena floats) lives in shared memory,
+// one per CTA (or per warp), instead of in `arena`.
 cudaError_t launch_batch_kernel(const BNet* nets, const BLeaf* leaves, const BStep* steps, int32_t n_nets,
                                 const void* packed, float* arena, int32_t* queue, bool cplx, bool scaling,
                                 bool maxplus, int threads, int grid, double* values, double* logs,
-                                cudaStream_t st, bool warp = false);
+                                cudaStream_t st, bool warp = false, int32_t smem_arena = 0);
 
 }  // namespace tn

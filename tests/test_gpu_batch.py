@@ -81,7 +81,7 @@ def test_graph_replay_and_autotune_match(tn):
     _, v0, l0 = run_batch(tn, nets, paths)
     _, v1, l1 = run_batch(tn, nets, paths, graph=True)
     b2, v2, l2 = run_batch(tn, nets, paths, autotune=True, graph=True)
-    t, c, g = b2.launch_shape()
+    t, c, g, sm = b2.launch_shape()
     assert t in (32, 64, 128, 256) and c in (2, 4, 8, 16) and g in (1, 4, 8)
     # same per-network arithmetic whatever the launch shape: bitwise equal
     assert np.array_equal(v0, v1) and np.array_equal(l0, l1)
@@ -90,10 +90,10 @@ def test_graph_replay_and_autotune_match(tn):
 
 @pytest.mark.parametrize("kind", ["ising", "complex", "maxplus"])
 def test_warp_per_network_form_bitwise_equal(tn, kind):
-    """The warp-per-network form (warp-synchronous steps, several networks per CTA) gives
-    the same bits as the CTA-per-network form: one lane computes each output element with
-    k in order, and the renormalisation is an exact power of two chosen from the same
-    maximum. Checked on partition functions (scaled), complex amplitudes and max-plus
+    """The warp-per-network form (warp-synchronous steps, several networks per CTA) and the
+    arenas in shared memory give the same bits as the CTA-per-network form with global
+    arenas: one lane computes each output element with k in order, and the renormalisation
+    is an exact power of two chosen from the same maximum. Checked on partition functions (scaled), complex amplitudes and max-plus
     independent sets, with a ragged last CTA (networks not a multiple of the warps per CTA)."""
     from tn_inputs import kings
     if kind == "ising":
@@ -109,8 +109,12 @@ def test_warp_per_network_form_bitwise_equal(tn, kind):
         nets, paths = [w.net for w in ws], [w.path for w in ws]
         kw = dict(complex_=False, scaling=False, semiring="maxplus")
     b, v0, l0 = run_batch(tn, nets, paths, **kw)
-    for shape in ((32, 4, 4), (32, 8, 8), (32, 16, 1), (256, 2, 1)):
-        b.set_launch_shape(*shape)
+    for shape in ((32, 4, 4), (32, 8, 8), (32, 16, 1), (256, 2, 1), (256, 2, 1, True), (32, 2, 4, True)):
+        try:
+            b.set_launch_shape(*shape)
+        except tn.TnError:
+            assert len(shape) == 4 and kind == "maxplus"  # the largest King's arenas exceed shared memory
+            continue
         v = torch.zeros_like(torch.tensor(v0)).cuda()
         l = torch.zeros_like(torch.tensor(l0)).cuda()
         b.contract(b._packed, v, l)

@@ -21,6 +21,8 @@
   khex45    : kicked Ising, same couplings, on a 4x5 honeycomb lattice (brick-wall form),
               6 Trotter steps;
   ktri44    : kicked Ising on a 4x4 triangular lattice, 8 Trotter steps;
+  tcgemm    : one dense step of the 14-cycle circuit's shape (2^14 x 2^14 outputs, k = 2^13), the
+              small case the tensor-core kernel is profiled on;
   sv26      : a 2^26-element state leaf in a shuffled declared order absorbing 4 gates (the
               large-leaf permutation case);
   kings16   : maximum independent set of a 16x16 King's subgraph (site density 0.8, seed 1;
@@ -37,7 +39,9 @@ from __future__ import annotations
 
 import functools
 
-from . import circuits, kicked_ising, ising_pf, greedy, kings
+import numpy as np
+
+from . import circuits, kicked_ising, ising_pf, greedy, kings, network
 
 PATH_SEEDS = range(6)
 PATH_ALPHAS = (0.0, 0.5, 1.0)
@@ -147,6 +151,27 @@ def sv26():
     return Workload(net.name, net, circuits.state_path(net), (), {})
 
 
+@functools.lru_cache(maxsize=None)
+def tcgemm(m_bits=14, n_bits=14, k_bits=13, seed=5):
+    """One dense pairwise step of the 14-cycle circuit's shape at a size that fits a small
+    profiling case: A[M, K] . B[N, K] with 2^14 x 2^14 outputs over k = 2^13 (complex64: 1 GiB
+    per operand), closed by two vectors (the steps after it are tiny)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M = list(range(m_bits))
+    N = list(range(m_bits, m_bits + n_bits))
+    K = list(range(m_bits + n_bits, m_bits + n_bits + k_bits))
+    ext = {x: 2 for x in M + N + K}
+    gauss = lambda shape: (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2.0)
+    A = gauss((2,) * (m_bits + k_bits))
+    B = gauss((2,) * (n_bits + k_bits))
+    u = gauss((2,) * m_bits)
+    v = gauss((2,) * n_bits)
+    net = network.Network([A, B, u, v], [tuple(M + K), tuple(N + K), tuple(M), tuple(N)], ext, (),
+                          name=f"gemm_m{m_bits}_n{n_bits}_k{k_bits}")
+    net.check()
+    return Workload(net.name, net, network.Path([(0, 1), (4, 2), (5, 3)]), (), {})
+
+
 def kising44():
     return kicked(4, 10)
 
@@ -203,4 +228,4 @@ def kings_batch(count, seed=5):
 
 BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40c14": rc40c14, "rc40c14sub": rc40c14sub, "rc40u": rc40u, "kising44": kising44, "kising55": kising55,
            "rc40open": rc40open,
-           "khex45": khex45, "ktri44": ktri44, "kings16": kings16, "sv26": sv26}
+           "khex45": khex45, "ktri44": ktri44, "kings16": kings16, "sv26": sv26, "tcgemm": tcgemm}
