@@ -113,7 +113,7 @@ def test_warp_per_network_form_bitwise_equal(tn, kind):
         try:
             b.set_launch_shape(*shape)
         except tn.TnError:
-            assert len(shape) == 4 and kind == "maxplus"  # the largest King's arenas exceed shared memory
+            assert len(shape) == 4  # only shared-memory arenas can be refused: the largest does not fit
             continue
         v = torch.zeros_like(torch.tensor(v0)).cuda()
         l = torch.zeros_like(torch.tensor(l0)).cuda()
