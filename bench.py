@@ -67,11 +67,12 @@ PREC = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x3m": 3}
 THREE_M = {"bf16x3m"}
 # arithmetic of each form (complex64 storage; products as named, FP32 accumulation)
 DTYPE_NAME = {"fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16x3": "bf16x3", "bf16x3m": "bf16x3 (3M)"}
-# DRAM bytes (read + write) per launch of the dominant kernel, averaged over its launches,
-# from the ncu launch-list capture of this same command (profiles/launches_rc40_*.md).
-# Only valid for the kernel build the capture was taken on: drop an entry when it changes.
-NCU_TRAFFIC_PER_LAUNCH = {("rc40", "3xtf32", "contract_tc"): 41.709e9,
-                          ("rc40", "bf16x3", "contract_tc"): 53.84e9}
+# DRAM bytes (read + write) of the dominant tensor-core launch (the step below), from the
+# single-kernel capture in profiles/contract_tcb_bf16x3_tcgemm_m14n14k13.md (m = n = 2^14,
+# k = 2^13, one slice: 61.7 GB read, 2.24 GB written) scaled to the launch: panel reads grow
+# with k (x4), output writes do not, 8 slices per launch. Valid for the kernel build it was
+# taken on: drop an entry when that kernel changes.
+NCU_TRAFFIC_DOMINANT_LAUNCH = {("rc40c14", "bf16x3"): {"step": 310, "bytes": 8 * (4 * 61.7e9 + 2.24e9)}}
 # Full values of the CPU oracle stored by the scripts in tests/golden/ (they call only the
 # oracle): the 40-qubit sum over all slices, and the full values of the smaller workloads.
 GOLDEN = os.path.join(ROOT, "tests", "golden")
@@ -458,8 +459,27 @@ def run_ours(args):
         achieved = prof["flops"][cls] / (prof["ms"][cls] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": alu, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = NCU_TRAFFIC_PER_LAUNCH.get((args.workload, args.prec, names[cls]))
+    roof["traffic"] = None
     roof["algorithmic_bytes_per_launch"] = prof["bytes"][cls] / max(1, launches)
+    # the class's longest launch (one step over the slices of a pass) with its own rate and
+    # its DRAM traffic where a capture of that kernel build covers it
+    s_top = max(range(len(step_ms)), key=lambda s: step_ms[s])
+    st_top = plan.step(s_top)
+    nb_top = info["slice_batch"] if st_top["batched"] else 1
+    f_top = (8.0 if cplx else 2.0) * st_top["m"] * st_top["n"] * st_top["k"] * nb_top
+    e_top = 8.0 if cplx else 4.0
+    b_top = e_top * nb_top * (st_top["m"] * st_top["k"] + st_top["n"] * st_top["k"] + st_top["m"] * st_top["n"])
+    ms_top = step_ms[s_top] / max(1, args.steps) / max(1, -(-per_step // info["slice_batch"]))
+    cap = NCU_TRAFFIC_DOMINANT_LAUNCH.get((args.workload, args.prec))
+    roof["dominant_launch"] = {"step": s_top, "m": st_top["m"], "n": st_top["n"], "k": st_top["k"],
+                               "copies": nb_top, "ms": ms_top, "flops": f_top,
+                               "achieved": f_top / (ms_top / 1e3) / 1e12 if cls == 2 else None,
+                               "algorithmic_bytes": b_top,
+                               "traffic": cap["bytes"] if cap and cap["step"] == s_top else None}
+    if cap and cap["step"] == s_top:
+        roof["traffic"] = cap["bytes"]
+        roof["traffic_scope"] = ("DRAM bytes of the dominant launch (step %d), scaled from a single-kernel "
+                                 "capture of the same kernel on a smaller case of its shape" % s_top)
     roof["kernel"] = names[cls]
     roof["launches_per_step"] = launches / args.steps
     roof["ms_per_launch"] = per_launch_ms
@@ -638,7 +658,7 @@ def run_batch_bench(args):
                             "J=+-1, beta=0.5, FP32 + exponent scaling"),
                    "launch_shape": {"threads_per_network": t, "ctas_per_sm": c, "networks_per_cta": g,
                                     "form": "warp per network" if g > 1 else "CTA per network",
-                                    "arenas": "shared memory" if sm else "global memory"},
+                                    "smem_arena_bytes_per_network": 4 * sm},
                    "graph": True},
         "one_launch_per_contraction": {"ms": ms_seq, "networks_per_s": count / (ms_seq / 1e3),
                                        "speedup_of_persistent": ms_seq / ms},

@@ -377,8 +377,9 @@ tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* p
  * flops (or NULL): algorithmic flops of one launch. threads / ctas_per_sm / nets_per_cta
  * (or NULL): the launch shape currently chosen (see tn_batch_autotune) -- threads per
  * network, resident CTAs per SM, networks per CTA (1: a CTA per network with block
- * barriers between steps; > 1: a warp per network, warp-synchronous steps), and whether
- * the networks' arenas live in shared memory (1) or global memory (0). */
+ * barriers between steps; > 1: a warp per network, warp-synchronous steps), and the
+ * shared-memory arena per network slot in floats (0: every arena in global memory; a
+ * network whose arena is larger keeps its global arena). */
 tn_status tn_batch_info(tn_batch_t b, int64_t* leaf_offsets, double* flops, int32_t* threads,
                         int32_t* ctas_per_sm, int32_t* nets_per_cta, int32_t* smem_arena);
 
@@ -395,15 +396,17 @@ tn_status tn_batch_contract_graph(tn_batch_t b, const void* packed_inputs, doubl
                                   void* stream);
 
 /* Time the batch under candidate launch shapes -- a CTA per network at 32-256 threads, or
- * a warp per network at 4 or 8 per CTA, each at 2-16 CTAs per SM, with the arenas in global
- * or (where they fit) shared memory -- and keep the fastest for later calls. Writes results into values/log_scales as a side effect. Synchronous. */
+ * a warp per network at 4 or 8 per CTA, each at 2-16 CTAs per SM, with every arena in
+ * global memory or the arenas up to the largest size the shape leaves room for in shared
+ * memory -- and keep the fastest for later calls. Writes results into values/log_scales as a side effect. Synchronous. */
 tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* values, double* log_scales,
                             void* stream);
 
 /* Set the launch shape by hand: threads per network (a multiple of 32, <= 1024), CTAs per
- * SM, networks per CTA (> 1 needs threads = 32: a warp per network), and smem_arena (1:
- * each network's arena in shared memory -- the largest arena x networks per CTA must fit
- * a CTA's shared memory, and ctas_per_sm of those an SM's); at most 2048 threads per SM.
+ * SM, networks per CTA (> 1 needs threads = 32: a warp per network), and smem_arena (the
+ * shared-memory arena per network slot in floats, 0 for none: smem_arena x 4 bytes x
+ * networks per CTA must fit a CTA's shared memory, and ctas_per_sm of those an SM's;
+ * networks whose arena is larger run in global memory); at most 2048 threads per SM.
  * TN_ERR_INVALID otherwise. */
 tn_status tn_batch_set_shape(tn_batch_t b, int32_t threads, int32_t ctas_per_sm, int32_t nets_per_cta,
                              int32_t smem_arena);

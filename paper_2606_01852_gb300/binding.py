@@ -433,15 +433,16 @@ class Batch:
         return out
 
     def launch_shape(self):
-        """(threads per network, CTAs per SM, networks per CTA, arenas in shared memory)."""
+        """(threads per network, CTAs per SM, networks per CTA, shared-memory arena floats)."""
         t, c, g, m = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         check(lib.tn_batch_info(self.handle, None, None, C.byref(t), C.byref(c), C.byref(g), C.byref(m)))
-        return t.value, c.value, g.value, bool(m.value)
+        return t.value, c.value, g.value, m.value
 
-    def set_launch_shape(self, threads, ctas_per_sm, nets_per_cta=1, smem_arena=False):
-        """Choose a launch shape by hand (tn_batch_set_shape)."""
+    def set_launch_shape(self, threads, ctas_per_sm, nets_per_cta=1, smem_arena=0):
+        """Choose a launch shape by hand (tn_batch_set_shape); smem_arena: floats of shared
+        memory per network slot (0: global arenas only)."""
         check(lib.tn_batch_set_shape(self.handle, int(threads), int(ctas_per_sm), int(nets_per_cta),
-                                     1 if smem_arena else 0))
+                                     int(smem_arena)))
 
     def contract(self, packed, values, logs, stream=None, graph=False):
         f = lib.tn_batch_contract_graph if graph else lib.tn_batch_contract

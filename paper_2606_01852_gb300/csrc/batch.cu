@@ -84,9 +84,9 @@ __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restr
     const int w = s_net;
     if (w >= n_nets) break;
     const BNet net = nets[w];
-    // the network's arena: in shared memory when every arena of the batch fits (smem_arena
-    // floats per CTA), else its own slice of the global batch arena
-    float* ar = smem_arena ? s_arena : arena + net.arena;
+    // the network's arena: in shared memory when it fits the launch's shared-memory arena
+    // (smem_arena floats per CTA), else its own slice of the global batch arena
+    float* ar = net.arena_floats <= smem_arena ? s_arena : arena + net.arena;
     // stage the leaves (declared order -> planned order; complex64 -> planar)
     for (int l = 0; l < net.n_leaves; ++l) {
       const BLeaf& L = leaves[net.leaf0 + l];
@@ -195,7 +195,7 @@ __global__ void batch_warp_kernel(const BNet* __restrict__ nets, const BLeaf* __
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_nets) break;
     const BNet net = nets[w];
-    float* ar = smem_arena ? s_arena + (threadIdx.x >> 5) * smem_arena : arena + net.arena;
+    float* ar = net.arena_floats <= smem_arena ? s_arena + (threadIdx.x >> 5) * smem_arena : arena + net.arena;
     long long slog = 0;
     for (int l = 0; l < net.n_leaves; ++l) {
       const BLeaf& L = leaves[net.leaf0 + l];
@@ -284,7 +284,7 @@ struct tn_batch_s {
   int32_t* d_queue = nullptr;
   int threads = 128, ctas_per_sm = 4, num_sms = 148;
   int nets_per_cta = 1;              // > 1: one warp per network, this many warps per CTA
-  bool smem_arena = false;           // arenas in shared memory (every network's fits)
+  int32_t smem_arena = 0;            // shared-memory arena per network slot (floats; 0: none)
   int64_t max_arena_floats = 0;      // largest network arena
   double flops = 0;
   // graph cache
@@ -428,7 +428,7 @@ tn_status launch_batch(tn_batch_s* B, const void* packed, double* values, double
   const int threads = warp ? 32 * B->nets_per_cta : B->threads;
   cudaError_t e = launch_batch_kernel(B->d_nets, B->d_leaves, B->d_steps, B->n_nets, packed, B->d_arena, B->d_queue,
                                       B->cplx, B->scaling, B->maxplus, threads, grid, values, logs, st, warp,
-                                      B->smem_arena ? static_cast<int32_t>(B->max_arena_floats) : 0);
+                                      B->smem_arena);
   if (e != cudaSuccess) {
     set_error(std::string("batch kernel launch: ") + cudaGetErrorString(e));
     return TN_ERR_CUDA;
@@ -493,6 +493,7 @@ tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* p
     bn.n_steps = (int32_t)T.steps.size();
     bn.root = T.root;
     bn.root_size = T.root_size;
+    bn.arena_floats = static_cast<int32_t>(T.arena_floats);
     for (BLeaf L : T.leaves) {
       B->leaf_offset.push_back(in_off + L.src);
       L.src += in_off;
@@ -555,7 +556,7 @@ tn_status tn_batch_info(tn_batch_t b, int64_t* leaf_offsets, double* flops, int3
   if (threads) *threads = b->threads;
   if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
   if (nets_per_cta) *nets_per_cta = b->nets_per_cta;
-  if (smem_arena) *smem_arena = b->smem_arena ? 1 : 0;
+  if (smem_arena) *smem_arena = b->smem_arena;
   return TN_OK;
 }
 
@@ -624,7 +625,7 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
   cudaEventCreate(&e1);
   float best = 1e30f;
   int bt = b->threads, bc = b->ctas_per_sm, bg = b->nets_per_cta;
-  bool bs = b->smem_arena;
+  int32_t bs = b->smem_arena;
   // (threads per network, networks per CTA): a CTA per network at 32-256 threads, or a warp
   // per network with 4 or 8 warps per CTA
   struct Shape { int t, g; };
@@ -632,18 +633,23 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
   for (int t : cand_threads) shapes.push_back({t, 1});
   shapes.push_back({32, 4});
   shapes.push_back({32, 8});
+  // shared-memory arena per network slot: none, or the largest that c CTAs of g slots fit
+  // (networks above it keep their global arenas), no larger than the largest arena
   for (const Shape& sh : shapes)
     for (int c : cand_ctas)
       for (int sm = 0; sm < 2; ++sm) {
       const int cta_threads = sh.g > 1 ? 32 * sh.g : sh.t;
       if (cta_threads * c > 2048) continue;
-      // arenas in shared memory only where c CTAs of them fit an SM
-      const int64_t smem = b->max_arena_floats * 4 * sh.g;
-      if (sm && (smem > kMaxSmemPerCta || smem * c > kSmemPerSm)) continue;
+      int64_t cap = 0;
+      if (sm) {
+        cap = std::min<int64_t>(kSmemPerSm / (4 * sh.g * c), kMaxSmemPerCta / (4 * sh.g));
+        cap = std::min<int64_t>(cap, b->max_arena_floats) / 64 * 64;
+        if (cap < 64) continue;
+      }
       b->threads = sh.t;
       b->nets_per_cta = sh.g;
       b->ctas_per_sm = c;
-      b->smem_arena = sm != 0;
+      b->smem_arena = static_cast<int32_t>(cap);
       float ms_best = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(e0, st);
@@ -664,7 +670,7 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
         bt = sh.t;
         bg = sh.g;
         bc = c;
-        bs = sm != 0;
+        bs = b->smem_arena;
       }
     }
   b->threads = bt;
@@ -686,15 +692,15 @@ tn_status tn_batch_set_shape(tn_batch_t b, int32_t threads, int32_t ctas_per_sm,
   const int cta_threads = warp ? 32 * nets_per_cta : threads;
   if (!b || ctas_per_sm < 1 || nets_per_cta < 1 || (warp && threads != 32) || cta_threads < 32 ||
       cta_threads > 1024 || cta_threads % 32 != 0 || cta_threads * ctas_per_sm > 2048 ||
-      (smem_arena && (b->max_arena_floats * 4 * nets_per_cta > kMaxSmemPerCta ||
-                      b->max_arena_floats * 4 * nets_per_cta * ctas_per_sm > kSmemPerSm))) {
+      smem_arena < 0 || int64_t(smem_arena) * 4 * nets_per_cta > kMaxSmemPerCta ||
+      int64_t(smem_arena) * 4 * nets_per_cta * ctas_per_sm > kSmemPerSm) {
     set_error("tn_batch_set_shape: bad launch shape");
     return TN_ERR_INVALID;
   }
   b->threads = threads;
   b->ctas_per_sm = ctas_per_sm;
   b->nets_per_cta = nets_per_cta;
-  b->smem_arena = smem_arena != 0;
+  b->smem_arena = smem_arena;
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;

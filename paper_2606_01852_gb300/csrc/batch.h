@@ -40,6 +40,8 @@ struct BNet {
   int32_t leaf0, n_leaves;      // index range in the leaf table
   int32_t step0, n_steps;       // index range in the step table
   int32_t root, root_size;      // float offset and size of the result tensor
+  int32_t arena_floats;         // size of the network's arena
+  int32_t pad;
 };
 
 // One network's tables, offsets relative to the network itself (arena floats from 0,
@@ -59,8 +61,8 @@ bool batch_template(const Plan& P, BatchTemplate& T, std::string& err);
 
 // Launch the persistent kernel over n_nets networks (queue reset included): a CTA of
 // `threads` per network, or with `warp` a warp per network (threads = 32 x warps per CTA).
-// smem_arena > 0: every network's arena (at most smem_arena floats) lives in shared memory,
-// one per CTA (or per warp), instead of in `arena`.
+// smem_arena > 0: a network whose arena holds at most smem_arena floats runs in a
+// shared-memory arena of that size (one per CTA, or per warp), the others in `arena`.
 cudaError_t launch_batch_kernel(const BNet* nets, const BLeaf* leaves, const BStep* steps, int32_t n_nets,
                                 const void* packed, float* arena, int32_t* queue, bool cplx, bool scaling,
                                 bool maxplus, int threads, int grid, double* values, double* logs,

@@ -255,6 +255,7 @@ struct tn_server_s {
       bn.n_steps = (int32_t)pt.T.steps.size();
       bn.root = pt.T.root;
       bn.root_size = pt.T.root_size;
+      bn.arena_floats = static_cast<int32_t>(pt.T.arena_floats);
       for (BLeaf L : pt.T.leaves) {
         L.src += in_elems;
         leaves.push_back(L);

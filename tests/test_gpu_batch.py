@@ -109,12 +109,11 @@ def test_warp_per_network_form_bitwise_equal(tn, kind):
         nets, paths = [w.net for w in ws], [w.path for w in ws]
         kw = dict(complex_=False, scaling=False, semiring="maxplus")
     b, v0, l0 = run_batch(tn, nets, paths, **kw)
-    for shape in ((32, 4, 4), (32, 8, 8), (32, 16, 1), (256, 2, 1), (256, 2, 1, True), (32, 2, 4, True)):
-        try:
-            b.set_launch_shape(*shape)
-        except tn.TnError:
-            assert len(shape) == 4  # only shared-memory arenas can be refused: the largest does not fit
-            continue
+    # shared-memory arenas of 1 Ki, 4 Ki and 12 Ki floats: the networks above the size keep
+    # their global arenas, so one launch mixes both
+    for shape in ((32, 4, 4), (32, 8, 8), (32, 16, 1), (256, 2, 1), (256, 2, 1, 12288), (32, 2, 4, 4096),
+                  (128, 4, 1, 1024)):
+        b.set_launch_shape(*shape)
         v = torch.zeros_like(torch.tensor(v0)).cuda()
         l = torch.zeros_like(torch.tensor(l0)).cuda()
         b.contract(b._packed, v, l)
@@ -122,3 +121,5 @@ def test_warp_per_network_form_bitwise_equal(tn, kind):
         assert np.array_equal(v.cpu().numpy(), v0) and np.array_equal(l.cpu().numpy(), l0), shape
     with pytest.raises(tn.TnError):
         b.set_launch_shape(64, 4, 4)  # a warp per network takes 32 threads
+    with pytest.raises(tn.TnError):
+        b.set_launch_shape(32, 8, 8, 8192)  # 8 x 8 slots of 32 KiB exceed an SM's shared memory
