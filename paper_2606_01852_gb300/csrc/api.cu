@@ -532,8 +532,9 @@ tn_status tn_plan_check_staging(tn_plan_t plan, int64_t max_slices) {
       for (int64_t blk0 = 0; blk0 < tiles; blk0 += kTilesPerCta) {
         const int64_t blk1 = std::min<int64_t>(blk0 + kTilesPerCta, tiles);
         TileCursor cur[TT];
-        int64_t built[TT][2] = {{-1, -1}, {-1, -1}};
-        int rebuild[TT] = {0, 0};
+        int64_t built[TT][2];
+        int rebuild[TT] = {};
+        for (int u = 0; u < TT; ++u) built[u][0] = built[u][1] = -1;
         int64_t isrc[TT][32] = {}, osrc[TT][32] = {}, irow[TT][32] = {};
         for (int64_t blk = blk0; blk < blk1; blk += TT) {
           const int nt = iteration_tiles(d, blk, blk0, blk1, sid, cur, built, rebuild);

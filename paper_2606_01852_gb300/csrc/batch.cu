@@ -64,12 +64,33 @@ __device__ void renormalise(float* t, int size, int* smax, long long* slog) {
   __syncthreads();
 }
 
+// Output offset of row x (x < m) or of column x - m (x >= m) of step S: the mixed-radix
+// digits over the merged dims, each times its stride.
+__device__ __forceinline__ int step_offset(const BStep& S, int x) {
+  int off = 0;
+  if (x < S.m) {
+    for (int d = S.nr - 1; d >= 0; --d) {
+      off += (x % S.rext[d]) * S.rstr[d];
+      x /= S.rext[d];
+    }
+  } else {
+    x -= S.m;
+    for (int d = S.nc - 1; d >= 0; --d) {
+      off += (x % S.cext[d]) * S.cstr[d];
+      x /= S.cext[d];
+    }
+  }
+  return off;
+}
+
 template <bool CPLX, bool MAXPLUS = false>
 __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restrict__ leaves,
                              const BStep* __restrict__ steps, int32_t n_nets, const float* __restrict__ in,
                              float* arena, int32_t* queue, int32_t scaling, double* values, double* logs,
-                             int32_t smem_arena) {
+                             int32_t smem_arena, int32_t tab_ints) {
+  // dynamic shared memory: [arena: smem_arena floats | offset table: tab_ints ints]
   extern __shared__ float s_arena[];
+  int* s_tab = reinterpret_cast<int*>(s_arena + smem_arena);
   __shared__ int s_net;
   __shared__ int s_max;
   __shared__ long long s_log;
@@ -114,6 +135,12 @@ __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restr
     for (int s = 0; s < net.n_steps; ++s) {
       const BStep& S = steps[net.step0 + s];
       const int mn = S.m * S.n;
+      // the output offset of every row and column, once per step (not once per element)
+      const bool tab = S.m + S.n <= tab_ints;
+      if (tab) {
+        for (int x = threadIdx.x; x < S.m + S.n; x += blockDim.x) s_tab[x] = step_offset(S, x);
+        __syncthreads();
+      }
       for (int o = threadIdx.x; o < mn; o += blockDim.x) {
         const int i = o / S.n, j = o - i * S.n;
         const float* A = ar + S.a + i * S.k;
@@ -131,17 +158,9 @@ __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restr
             cr = fmaf(A[t], B[t], cr);
           }
         }
-        int ro = 0, co = 0, r = i, c = j;
-        for (int d = S.nr - 1; d >= 0; --d) {
-          ro += (r % S.rext[d]) * S.rstr[d];
-          r /= S.rext[d];
-        }
-        for (int d = S.nc - 1; d >= 0; --d) {
-          co += (c % S.cext[d]) * S.cstr[d];
-          c /= S.cext[d];
-        }
-        ar[S.c + ro + co] = cr;
-        if (CPLX) ar[S.c + S.c_size + ro + co] = ci;
+        const int off = tab ? s_tab[i] + s_tab[S.m + j] : step_offset(S, i) + step_offset(S, S.m + j);
+        ar[S.c + off] = cr;
+        if (CPLX) ar[S.c + S.c_size + off] = ci;
       }
       __syncthreads();
       if (scaling) renormalise<CPLX>(ar + S.c, S.c_size, &s_max, &s_log);
@@ -186,9 +205,11 @@ template <bool CPLX, bool MAXPLUS = false>
 __global__ void batch_warp_kernel(const BNet* __restrict__ nets, const BLeaf* __restrict__ leaves,
                                   const BStep* __restrict__ steps, int32_t n_nets, const float* __restrict__ in,
                                   float* arena, int32_t* queue, int32_t scaling, double* values, double* logs,
-                                  int32_t smem_arena) {
+                                  int32_t smem_arena, int32_t tab_ints) {
+  // dynamic shared memory: [arenas: smem_arena floats per warp | tables: tab_ints ints per warp]
   extern __shared__ float s_arena[];
   const int lane = threadIdx.x & 31;
+  int* s_tab = reinterpret_cast<int*>(s_arena + smem_arena * (blockDim.x >> 5)) + (threadIdx.x >> 5) * tab_ints;
   while (true) {
     int w = 0;
     if (lane == 0) w = atomicAdd(queue, 1);
@@ -223,6 +244,11 @@ __global__ void batch_warp_kernel(const BNet* __restrict__ nets, const BLeaf* __
     for (int s = 0; s < net.n_steps; ++s) {
       const BStep& S = steps[net.step0 + s];
       const int mn = S.m * S.n;
+      const bool tab = S.m + S.n <= tab_ints;
+      if (tab) {
+        for (int x = lane; x < S.m + S.n; x += 32) s_tab[x] = step_offset(S, x);
+        __syncwarp();
+      }
       for (int o = lane; o < mn; o += 32) {
         const int i = o / S.n, j = o - i * S.n;
         const float* A = ar + S.a + i * S.k;
@@ -239,17 +265,9 @@ __global__ void batch_warp_kernel(const BNet* __restrict__ nets, const BLeaf* __
             cr = fmaf(A[t], B[t], cr);
           }
         }
-        int ro = 0, co = 0, r = i, c = j;
-        for (int d = S.nr - 1; d >= 0; --d) {
-          ro += (r % S.rext[d]) * S.rstr[d];
-          r /= S.rext[d];
-        }
-        for (int d = S.nc - 1; d >= 0; --d) {
-          co += (c % S.cext[d]) * S.cstr[d];
-          c /= S.cext[d];
-        }
-        ar[S.c + ro + co] = cr;
-        if (CPLX) ar[S.c + S.c_size + ro + co] = ci;
+        const int off = tab ? s_tab[i] + s_tab[S.m + j] : step_offset(S, i) + step_offset(S, S.m + j);
+        ar[S.c + off] = cr;
+        if (CPLX) ar[S.c + S.c_size + off] = ci;
       }
       __syncwarp();
       if (scaling) slog += warp_renormalise<CPLX>(ar + S.c, S.c_size, lane);
@@ -286,6 +304,7 @@ struct tn_batch_s {
   int nets_per_cta = 1;              // > 1: one warp per network, this many warps per CTA
   int32_t smem_arena = 0;            // shared-memory arena per network slot (floats; 0: none)
   int64_t max_arena_floats = 0;      // largest network arena
+  int32_t tab_ints = 0;              // offset-table ints per network slot
   double flops = 0;
   // graph cache
   cudaGraphExec_t gexec = nullptr;
@@ -305,41 +324,41 @@ cudaError_t set_smem(K kernel, int bytes) {
 cudaError_t launch_batch_kernel(const BNet* nets, const BLeaf* leaves, const BStep* steps, int32_t n_nets,
                                 const void* packed, float* arena, int32_t* queue, bool cplx, bool scaling,
                                 bool maxplus, int threads, int grid, double* values, double* logs,
-                                cudaStream_t st, bool warp, int32_t smem_arena) {
+                                cudaStream_t st, bool warp, int32_t smem_arena, int32_t tab_ints) {
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   const float* in = static_cast<const float*>(packed);
   const int sc = scaling ? 1 : 0;
-  // dynamic shared memory: one arena per CTA, or one per warp in the warp form
-  const int smem = smem_arena ? smem_arena * 4 * (warp ? threads / 32 : 1) : 0;
+  // dynamic shared memory: an arena and an offset table per CTA, or per warp in the warp form
+  const int smem = (smem_arena + tab_ints) * 4 * (warp ? threads / 32 : 1);
   if (warp) {
     if (cplx) {
       if (smem && (e = set_smem(batch_warp_kernel<true>, smem)) != cudaSuccess) return e;
       batch_warp_kernel<true><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, sc, values,
-                                                           logs, smem_arena);
+                                                           logs, smem_arena, tab_ints);
     } else if (maxplus) {
       if (smem && (e = set_smem(batch_warp_kernel<false, true>, smem)) != cudaSuccess) return e;
       batch_warp_kernel<false, true><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, 0,
-                                                                  values, logs, smem_arena);
+                                                                  values, logs, smem_arena, tab_ints);
     } else {
       if (smem && (e = set_smem(batch_warp_kernel<false>, smem)) != cudaSuccess) return e;
       batch_warp_kernel<false><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, sc,
-                                                            values, logs, smem_arena);
+                                                            values, logs, smem_arena, tab_ints);
     }
     return cudaGetLastError();
   }
   if (cplx) {
     if (smem && (e = set_smem(batch_kernel<true>, smem)) != cudaSuccess) return e;
     batch_kernel<true><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, sc, values, logs,
-                                                    smem_arena);
+                                                    smem_arena, tab_ints);
   } else if (maxplus) {
     if (smem && (e = set_smem(batch_kernel<false, true>, smem)) != cudaSuccess) return e;
     batch_kernel<false, true><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, 0, values,
-                                                           logs, smem_arena);
+                                                           logs, smem_arena, tab_ints);
   } else {
     if (smem && (e = set_smem(batch_kernel<false>, smem)) != cudaSuccess) return e;
     batch_kernel<false><<<grid, threads, smem, st>>>(nets, leaves, steps, n_nets, in, arena, queue, sc, values,
-                                                     logs, smem_arena);
+                                                     logs, smem_arena, tab_ints);
   }
   return cudaGetLastError();
 }
@@ -409,6 +428,7 @@ bool batch_template(const Plan& P, BatchTemplate& T, std::string& err) {
       S.cstr[d] = (int32_t)st.cols.stride[d];
     }
     T.steps.push_back(S);
+    T.max_tab = std::max<int32_t>(T.max_tab, static_cast<int32_t>(st.m + st.n));
     T.flops += (P.is_complex ? 8.0 : 2.0) * double(st.m) * double(st.n) * double(st.k);
   }
   T.arena_floats = (P.arena_bytes + 255) / 256 * 64;  // keep every arena 256-byte aligned
@@ -428,7 +448,7 @@ tn_status launch_batch(tn_batch_s* B, const void* packed, double* values, double
   const int threads = warp ? 32 * B->nets_per_cta : B->threads;
   cudaError_t e = launch_batch_kernel(B->d_nets, B->d_leaves, B->d_steps, B->n_nets, packed, B->d_arena, B->d_queue,
                                       B->cplx, B->scaling, B->maxplus, threads, grid, values, logs, st, warp,
-                                      B->smem_arena);
+                                      B->smem_arena, B->tab_ints);
   if (e != cudaSuccess) {
     set_error(std::string("batch kernel launch: ") + cudaGetErrorString(e));
     return TN_ERR_CUDA;
@@ -504,6 +524,7 @@ tn_status tn_batch_plan(int32_t n_nets, const tn_network* nets, const tn_path* p
     B->flops += T.flops;
     B->arena_floats += T.arena_floats;
     B->max_arena_floats = std::max(B->max_arena_floats, T.arena_floats);
+    B->tab_ints = std::max(B->tab_ints, std::min(T.max_tab, kMaxTabInts));
     B->nets.push_back(bn);
   }
   B->leaf_offset.push_back(in_off);
@@ -641,9 +662,10 @@ tn_status tn_batch_autotune(tn_batch_t b, const void* packed_inputs, double* val
       const int cta_threads = sh.g > 1 ? 32 * sh.g : sh.t;
       if (cta_threads * c > 2048) continue;
       int64_t cap = 0;
+      const int64_t per_slot = std::min<int64_t>(kSmemPerSm / (4 * sh.g * c), kMaxSmemPerCta / (4 * sh.g));
+      if (per_slot < b->tab_ints) continue;  // the offset tables alone do not fit this shape
       if (sm) {
-        cap = std::min<int64_t>(kSmemPerSm / (4 * sh.g * c), kMaxSmemPerCta / (4 * sh.g));
-        cap = std::min<int64_t>(cap, b->max_arena_floats) / 64 * 64;
+        cap = std::min<int64_t>(per_slot - b->tab_ints, b->max_arena_floats) / 64 * 64;
         if (cap < 64) continue;
       }
       b->threads = sh.t;
@@ -692,8 +714,8 @@ tn_status tn_batch_set_shape(tn_batch_t b, int32_t threads, int32_t ctas_per_sm,
   const int cta_threads = warp ? 32 * nets_per_cta : threads;
   if (!b || ctas_per_sm < 1 || nets_per_cta < 1 || (warp && threads != 32) || cta_threads < 32 ||
       cta_threads > 1024 || cta_threads % 32 != 0 || cta_threads * ctas_per_sm > 2048 ||
-      smem_arena < 0 || int64_t(smem_arena) * 4 * nets_per_cta > kMaxSmemPerCta ||
-      int64_t(smem_arena) * 4 * nets_per_cta * ctas_per_sm > kSmemPerSm) {
+      smem_arena < 0 || int64_t(smem_arena + b->tab_ints) * 4 * nets_per_cta > kMaxSmemPerCta ||
+      int64_t(smem_arena + b->tab_ints) * 4 * nets_per_cta * ctas_per_sm > kSmemPerSm) {
     set_error("tn_batch_set_shape: bad launch shape");
     return TN_ERR_INVALID;
   }

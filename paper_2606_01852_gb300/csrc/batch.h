@@ -52,8 +52,13 @@ struct BatchTemplate {
   int64_t arena_floats = 0;     // 256-byte aligned
   int64_t input_elems = 0;      // elements of the network's packed inputs
   int32_t root = 0, root_size = 0;
+  int32_t max_tab = 0;          // largest m + n of its steps (the offset table it needs)
   double flops = 0;
 };
+
+// offset-table entries per network slot at most (steps with larger m + n compute offsets
+// element by element)
+constexpr int32_t kMaxTabInts = 4096;
 
 // Tables of a closed, unsliced network from its plan (workspace assigned for one copy, no
 // tensor-core steps); false with a reason when the batched kernel cannot run it.
@@ -63,9 +68,11 @@ bool batch_template(const Plan& P, BatchTemplate& T, std::string& err);
 // `threads` per network, or with `warp` a warp per network (threads = 32 x warps per CTA).
 // smem_arena > 0: a network whose arena holds at most smem_arena floats runs in a
 // shared-memory arena of that size (one per CTA, or per warp), the others in `arena`.
+// tab_ints > 0: each slot also gets a shared-memory table of that many ints for the output
+// offsets of a step's rows and columns (steps with m + n above it compute them per element).
 cudaError_t launch_batch_kernel(const BNet* nets, const BLeaf* leaves, const BStep* steps, int32_t n_nets,
                                 const void* packed, float* arena, int32_t* queue, bool cplx, bool scaling,
                                 bool maxplus, int threads, int grid, double* values, double* logs,
-                                cudaStream_t st, bool warp = false, int32_t smem_arena = 0);
+                                cudaStream_t st, bool warp = false, int32_t smem_arena = 0, int32_t tab_ints = 0);
 
 }  // namespace tn

@@ -245,8 +245,10 @@ struct tn_server_s {
     std::vector<BLeaf> leaves;
     std::vector<BStep> steps;
     int64_t arena = 0, in_elems = 0;
+    int32_t tab_ints = 0;
     for (Request* r : group) {
       const PackTemplate& pt = pack_template(r->plan);
+      tab_ints = std::max(tab_ints, std::min(pt.T.max_tab, kMaxTabInts));
       BNet bn{};
       bn.arena = arena;
       bn.leaf0 = (int32_t)leaves.size();
@@ -304,7 +306,7 @@ struct tn_server_s {
                               reinterpret_cast<BStep*>(d + b_nets + b_leaves), (int32_t)n,
                               d + b_nets + b_leaves + b_steps, reinterpret_cast<float*>(d + off_arena),
                               reinterpret_cast<int32_t*>(d + off_q), cplx, first.kind == 3, first.kind == 4,
-                              threads, grid, vals, logs, st);
+                              threads, grid, vals, logs, st, false, 0, tab_ints);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h + up, d + off_out, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaEventRecord(pk->done, st);
     buf->busy = true;

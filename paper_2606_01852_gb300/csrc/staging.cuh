@@ -114,8 +114,8 @@ __host__ __device__ inline void cursor_next(const LeafDesc& d, TileCursor& c) {
 }
 
 // tiles one CTA of the tiled kernel walks, and tiles it holds in flight per iteration
-constexpr int kTilesPerCta = 8;
-constexpr int kTilesInFlight = 2;
+constexpr int kTilesPerCta = 16;
+constexpr int kTilesInFlight = 4;
 
 // One iteration of a CTA at tile blk (its tiles blk0 .. blk1-1): advance the cursors of
 // the iteration's tiles (slot u holds tile blk + u) and decide which slots' offset tables
