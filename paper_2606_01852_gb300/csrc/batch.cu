@@ -64,6 +64,9 @@ __device__ void renormalise(float* t, int size, int* smax, long long* slog) {
   __syncthreads();
 }
 
+// leaves whose exponents one pass takes together (networks with more renormalise leaf by leaf)
+constexpr int kLeafExpCap = 256;
+
 // Output offset of row x (x < m) or of column x - m (x >= m) of step S: the mixed-radix
 // digits over the merged dims, each times its stride.
 __device__ __forceinline__ int step_offset(const BStep& S, int x) {
@@ -91,6 +94,7 @@ __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restr
   // dynamic shared memory: [arena: smem_arena floats | offset table: tab_ints ints]
   extern __shared__ float s_arena[];
   int* s_tab = reinterpret_cast<int*>(s_arena + smem_arena);
+  __shared__ int s_lexp[kLeafExpCap];  // per-leaf maximum exponents
   __shared__ int s_net;
   __shared__ int s_max;
   __shared__ long long s_log;
@@ -127,11 +131,43 @@ __global__ void batch_kernel(const BNet* __restrict__ nets, const BLeaf* __restr
       }
     }
     __syncthreads();
-    if (scaling)
+    if (scaling && net.n_leaves <= kLeafExpCap) {
+      // every leaf renormalised in one pass: per-leaf maxima by shared-memory atomics, then
+      // each leaf scaled by its own exact power of two (the same exponents as one leaf at a
+      // time, with three barriers instead of three per leaf)
+      for (int l = threadIdx.x; l < net.n_leaves; l += blockDim.x) s_lexp[l] = -127;
+      __syncthreads();
+      for (int l = 0; l < net.n_leaves; ++l) {
+        const BLeaf& L = leaves[net.leaf0 + l];
+        int lmax = -127;
+        for (int i = threadIdx.x; i < L.size; i += blockDim.x) {
+          float v = fabsf(ar[L.dst + i]);
+          if (CPLX) v = fmaxf(v, fabsf(ar[L.dst + L.size + i]));
+          lmax = max(lmax, bexp_of(v));
+        }
+        if (lmax > -127) atomicMax(&s_lexp[l], lmax);
+      }
+      __syncthreads();
+      long long sum = 0;
+      for (int l = 0; l < net.n_leaves; ++l) {
+        const BLeaf& L = leaves[net.leaf0 + l];
+        const int e = s_lexp[l] < -126 ? 0 : s_lexp[l];  // an all-zero leaf is left as is
+        sum += e;
+        if (e == 0) continue;
+        const float sc = bpow2_neg(e);
+        for (int i = threadIdx.x; i < L.size; i += blockDim.x) {
+          ar[L.dst + i] *= sc;
+          if (CPLX) ar[L.dst + L.size + i] *= sc;
+        }
+      }
+      if (threadIdx.x == 0) s_log += sum;
+      __syncthreads();
+    } else if (scaling) {
       for (int l = 0; l < net.n_leaves; ++l) {
         const BLeaf& L = leaves[net.leaf0 + l];
         renormalise<CPLX>(ar + L.dst, L.size, &s_max, &s_log);
       }
+    }
     for (int s = 0; s < net.n_steps; ++s) {
       const BStep& S = steps[net.step0 + s];
       const int mn = S.m * S.n;
