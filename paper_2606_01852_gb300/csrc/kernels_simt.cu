@@ -108,7 +108,7 @@ __global__ void stage_leaves_kernel(const LeafDesc* __restrict__ descs, char* __
 // plane, or eight BF16 values per plane in the split form). When the declared innermost
 // position is itself in the output group, loads run along the output group instead.
 template <bool CPLX>
-__global__ void __launch_bounds__(256, 4) stage_leaf_tiled_kernel(const LeafDesc* __restrict__ descs, int32_t leaf,
+__global__ void __launch_bounds__(256, 5) stage_leaf_tiled_kernel(const LeafDesc* __restrict__ descs, int32_t leaf,
                                                                char* __restrict__ ws, int64_t slice_begin,
                                                                ScaleRec* recs, const int32_t* rec_index) {
   constexpr int TT = kTilesInFlight;  // tiles per CTA iteration (loads of all before any store)
