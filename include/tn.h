@@ -119,7 +119,7 @@ typedef enum {
                           the parts combined in order) */
   TN_CLASS_STREAM = 1, /* big x small: one pass over the big operand */
   TN_CLASS_TC = 2,     /* tcgen05 tensor-core GEMM (rows >= 128, columns >= 16, k >= 8; a
-                          persistent variant for k <= 64 in the BF16X3 form) */
+                          persistent variant for k <= 256 in the 4M BF16X3 form) */
   TN_CLASS_SPLITK = 3, /* few outputs, long k: split-K partials in FP64, fixed-order sum */
   TN_CLASS_PERM = 4    /* not a step class: leaf staging (a leaf permuted from its declared
                           order into its planned order); in tn_profile only */
@@ -171,7 +171,9 @@ typedef struct {
   int32_t consumer;        /* step index, -1 for the root */
   int32_t format;          /* tn_storage_format of the tensor's copies */
   int32_t tiled;           /* leaves: staged by the tiled permutation kernel (one launch per
-                              pass that stages it) rather than the per-leaf kernel */
+                              pass that stages it) rather than the per-leaf kernel: 1 its
+                              general form, 2 its pipelined form (each index group one 32-wide
+                              chunk, 16-byte loads; used when the source is 16-byte aligned) */
 } tn_tensor_info;
 
 /* Rates of the kernel choice, the roofline cost model of Sec. IV-C Eq. 6: a step's time

@@ -375,7 +375,7 @@ tn_status tn_plan_tensor(tn_plan_t plan, int32_t id, tn_tensor_info* out) {
   out->producer = R.producer;
   out->consumer = R.consumer;
   out->format = R.split;
-  out->tiled = id < plan->P.n_leaves ? plan->P.leafdesc[id].tiled : 0;
+  out->tiled = id < plan->P.n_leaves ? (plan->P.leafdesc[id].tiled ? (plan->P.leafdesc[id].fast ? 2 : 1) : 0) : 0;
   return TN_OK;
 }
 
@@ -525,6 +525,25 @@ tn_status tn_plan_check_staging(tn_plan_t plan, int64_t max_slices) {
     for (int64_t q = 0; q < n_sid; ++q) {
       // slices 0, n-1, and evenly spread ones between
       const int64_t sid = n_sid == 1 ? 0 : q * (P.n_slices - 1) / (n_sid - 1);
+      if (d.fast) {
+        // the pipelined form's offsets: every tile's rest offset as its CTA's high part plus
+        // the tile's low part, the tables of chunk (0, 0) -- equal to the cursor form's
+        if (d.Po != 32 || d.Pi != 32 || tiles % kTilesPerCta != 0 || !d.vec_load) {
+          set_error("tiled staging of leaf " + std::to_string(t) + ": pipelined form on an unfit leaf");
+          return TN_ERR_INVALID;
+        }
+        for (int64_t blk = 0; blk < tiles; ++blk) {
+          int64_t hs, hd, ls, ld;
+          rest_hi_offsets(d, blk / kTilesPerCta, sid, hs, hd);
+          rest_lo_offsets(d, blk % kTilesPerCta, ls, ld);
+          const TileBase tb = tile_base(d, blk, sid);
+          if (tb.go0 != 0 || tb.gi0 != 0 || hs + ls != tb.src0 || hd + ld != tb.dst0) {
+            set_error("tiled staging of leaf " + std::to_string(t) + ": pipelined offsets disagree with tile " +
+                      std::to_string(blk));
+            return TN_ERR_INVALID;
+          }
+        }
+      }
       std::vector<char> seen(d.size, 0);
       // each CTA as the kernel runs it: iterations of kTilesInFlight tiles, slot tables
       // rebuilt only when iteration_tiles says so, element offsets read from the tables

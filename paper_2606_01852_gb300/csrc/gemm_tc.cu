@@ -13,7 +13,7 @@
 //                                  their own accumulator; 320 threads;
 //   contract_tcb_kernel            BF16x3 form: operands already split into BF16 hi/lo
 //                                  planes by their producers, kind::f16, 256-term chunks;
-//   contract_tcb_persistent_kernel BF16x3 for shallow steps (k <= 64): one CTA per SM over
+//   contract_tcb_persistent_kernel BF16x3 for shallow steps (k <= 256): one CTA per SM over
 //                                  the tiles, stores of a tile overlapping the next tile.
 // The epilogues of the TF32 and BF16x3 kernels store each 32 x 32 block in address order
 // (store_block). Every mbarrier wait is bounded by wall time; on expiry the CTA records an
@@ -1304,8 +1304,9 @@ __global__ void __launch_bounds__(CB3::THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------------
-// BF16x3, persistent, for shallow steps (k <= 64: one or two k-blocks per tile). Such a
-// step is bound by its output stores, not by the tensor core; with one tile per CTA most
+// BF16x3, persistent, for shallow steps (k <= 256: at most one fold chunk per tile, so the
+// numerics are those of contract_tcb_kernel). Such a step is bound by its output stores,
+// not by the tensor core; with one tile per CTA most
 // of a CTA's life is set-up, pipeline fill and the epilogue, serialised. Here one CTA per
 // SM walks the (batch entry, tile) items with a stride of the grid; the stage ring,
 // barrier phases and tensor memory carry over, and the fold warps release the
@@ -1319,7 +1320,7 @@ struct CBP {
   static constexpr int EPI = 8 * 2 * 32 * 33 * 4;          // per fold warp: Re and Im of one 32 x 32 block
   static constexpr int BARS = 256;
   static constexpr int SMEM = STAGES * CB::STAGE + EPI + BARS + 1024 /*align*/;
-  static constexpr int MAX_K = 2 * CB::BK;                  // used for k <= 64
+  static constexpr int MAX_K = CB::CK * CB::BK;            // used for k <= 256: one fold chunk per tile
 };
 static_assert(CBP::SMEM <= 232448, "shared memory per CTA");
 
@@ -1356,7 +1357,7 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
   const int64_t total = tiles_m * tiles_n * nb;
-  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);  // 1 or 2: one chunk per tile
+  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);  // <= CK: one fold chunk per tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {

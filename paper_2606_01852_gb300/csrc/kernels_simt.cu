@@ -272,6 +272,103 @@ __global__ void __launch_bounds__(256, 5) stage_leaf_tiled_kernel(const LeafDesc
   }
 }
 
+// Pipelined form of the tiled staging kernel (LeafDesc::fast: each group one 32-wide chunk,
+// 16-byte loads, the CTA's 16 tiles spanning the rest index's fastest positions): the
+// offset tables and the tiles' rest offsets are built once per CTA, and the loads of tile
+// i + 1 are in flight while tile i is stored (two tile buffers, one barrier per tile).
+template <int SPLIT>
+__device__ __forceinline__ void store_tile_row(float* base, int64_t size, int64_t row, int tid, const float (*tre)[33],
+                                               const float (*tim)[33]) {
+  if (SPLIT) {
+    const int q = tid & 3, ti = tid >> 2, to = 8 * q;
+    if (ti >= 32) return;
+    uint32_t pl[6][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float vr = tre[ti][to + e], vi = tim[ti][to + e];
+      __nv_bfloat16 rh, rl, ih, il, sh, sl;
+      split_pair(vr, rh, rl);
+      split_pair(vi, ih, il);
+      split_pair(vr + vi, sh, sl);
+      pl[0][e] = __bfloat16_as_ushort(rh);
+      pl[1][e] = __bfloat16_as_ushort(SPLIT == kFmtSplit3M ? rl : ih);
+      pl[2][e] = __bfloat16_as_ushort(SPLIT == kFmtSplit3M ? ih : rl);
+      pl[3][e] = __bfloat16_as_ushort(il);
+      pl[4][e] = __bfloat16_as_ushort(sh);
+      pl[5][e] = __bfloat16_as_ushort(sl);
+    }
+    uint16_t* S = reinterpret_cast<uint16_t*>(base) + row + to;
+    constexpr int planes = SPLIT == kFmtSplit3M ? 6 : 4;
+#pragma unroll
+    for (int p = 0; p < planes; ++p)
+      *reinterpret_cast<uint4*>(S + p * size) =
+          make_uint4(pl[p][0] | (pl[p][1] << 16), pl[p][2] | (pl[p][3] << 16), pl[p][4] | (pl[p][5] << 16),
+                     pl[p][6] | (pl[p][7] << 16));
+  } else {
+    const int q = tid & 7, ti = tid >> 3, to = 4 * q;
+    *reinterpret_cast<float4*>(base + row + to) =
+        make_float4(tre[ti][to], tre[ti][to + 1], tre[ti][to + 2], tre[ti][to + 3]);
+    *reinterpret_cast<float4*>(base + size + row + to) =
+        make_float4(tim[ti][to], tim[ti][to + 1], tim[ti][to + 2], tim[ti][to + 3]);
+  }
+}
+
+template <int SPLIT>
+__global__ void __launch_bounds__(256, 4) stage_leaf_fast_kernel(const LeafDesc* __restrict__ descs, int32_t leaf,
+                                                                 char* __restrict__ ws, int64_t slice_begin,
+                                                                 ScaleRec* recs, const int32_t* rec_index) {
+  const LeafDesc& d = descs[leaf];
+  __shared__ float tre[2][32][33], tim[2][32][33];
+  __shared__ int64_t s_isrc[32], s_osrc[32], s_irow[32], s_lsrc[kTilesPerCta], s_ldst[kTilesPerCta];
+  __shared__ int64_t s_hi[2];
+  const int tid = threadIdx.x, b = blockIdx.y;
+  if (tid < 32) {
+    int64_t osrc, irow;
+    table_entry(d, 0, 0, tid, s_isrc[tid], osrc, irow);
+    s_osrc[tid] = osrc;
+    s_irow[tid] = irow;
+  } else if (tid < 32 + kTilesPerCta) {
+    rest_lo_offsets(d, tid - 32, s_lsrc[tid - 32], s_ldst[tid - 32]);
+  } else if (tid == 64) {
+    rest_hi_offsets(d, blockIdx.x, slice_begin + b, s_hi[0], s_hi[1]);
+  }
+  __syncthreads();
+  const int64_t hsrc = s_hi[0], hdst = s_hi[1];
+  const float4* src4 = reinterpret_cast<const float4*>(d.src);
+  float* base = reinterpret_cast<float*>(ws + d.dst) + int64_t(b) * cplx_floats(d.split) * d.size;
+  const int ti = 2 * (tid & 15), to0 = tid >> 4;
+  const int64_t sa = s_isrc[ti] + s_osrc[to0], sb = s_isrc[ti] + s_osrc[to0 + 16];
+  int lmax = -127;
+  float4 v0 = __ldg(src4 + ((hsrc + s_lsrc[0] + sa) >> 1)), v1 = __ldg(src4 + ((hsrc + s_lsrc[0] + sb) >> 1));
+  for (int i = 0; i < kTilesPerCta; ++i) {
+    float (*br)[33] = tre[i & 1];
+    float (*bi)[33] = tim[i & 1];
+    br[ti][to0] = v0.x;
+    bi[ti][to0] = v0.y;
+    br[ti + 1][to0] = v0.z;
+    bi[ti + 1][to0] = v0.w;
+    br[ti][to0 + 16] = v1.x;
+    bi[ti][to0 + 16] = v1.y;
+    br[ti + 1][to0 + 16] = v1.z;
+    bi[ti + 1][to0 + 16] = v1.w;
+    lmax = max(lmax, exp_of(fmaxf(fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)), fmaxf(fabsf(v0.z), fabsf(v0.w))),
+                                  fmaxf(fmaxf(fabsf(v1.x), fabsf(v1.y)), fmaxf(fabsf(v1.z), fabsf(v1.w))))));
+    __syncthreads();  // tile i is in shared memory; the stores of tile i - 1 are done
+    if (i + 1 < kTilesPerCta) {
+      v0 = __ldg(src4 + ((hsrc + s_lsrc[i + 1] + sa) >> 1));
+      v1 = __ldg(src4 + ((hsrc + s_lsrc[i + 1] + sb) >> 1));
+    }
+    const int rti = SPLIT ? (tid >> 2) : (tid >> 3);
+    if (rti < 32) store_tile_row<SPLIT>(base, d.size, hdst + s_ldst[i] + s_irow[rti], tid, br, bi);
+  }
+  if (recs) {
+    for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    ScaleRec* rec = recs + rec_index[leaf] + (d.batched ? b : 0);
+    if ((tid & 31) == 0) atomicMax(&rec->emax, lmax);
+    if (blockIdx.x == 0 && tid == 0) rec->log2 = 0;
+  }
+}
+
 void launch_stage_leaves(const LeafDesc* descs, const LeafDesc* host_descs, int32_t n_leaves, char* ws,
                          int64_t slice_begin, int32_t nb, bool only_batched, bool is_complex, ScaleRec* recs,
                          const int32_t* rec_index, cudaStream_t st) {
@@ -284,6 +381,15 @@ void launch_stage_leaves(const LeafDesc* descs, const LeafDesc* host_descs, int3
     const int64_t tiles = h.Pr * ((h.Po + 31) / 32) * ((h.Pi + 31) / 32);
     const int64_t ctas = (tiles + kTilesPerCta - 1) / kTilesPerCta;
     dim3 grid(static_cast<unsigned>(ctas), static_cast<unsigned>(h.batched ? nb : 1));
+    if (h.fast && (reinterpret_cast<uintptr_t>(h.src) & 15) == 0) {  // 16-byte loads need an aligned source
+      if (h.split == kFmtSplit3M)
+        stage_leaf_fast_kernel<kFmtSplit3M><<<grid, 256, 0, st>>>(descs, t, ws, slice_begin, recs, rec_index);
+      else if (h.split == kFmtSplit)
+        stage_leaf_fast_kernel<kFmtSplit><<<grid, 256, 0, st>>>(descs, t, ws, slice_begin, recs, rec_index);
+      else
+        stage_leaf_fast_kernel<kFmtPlanar><<<grid, 256, 0, st>>>(descs, t, ws, slice_begin, recs, rec_index);
+      continue;
+    }
     if (is_complex)
       stage_leaf_tiled_kernel<true><<<grid, 256, 0, st>>>(descs, t, ws, slice_begin, recs, rec_index);
     else

@@ -9,6 +9,7 @@
 #include <sstream>
 
 #include "kernels.h"
+#include "staging.cuh"
 #include "tn_internal.h"
 
 namespace tn {
@@ -488,6 +489,19 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
       d.load_o = (inner >= 0 && in_o[inner]) ? 1 : 0;
       d.vec_load = (!d.load_o && d.ni > 0 && d.sstride[d.ipos[d.ni - 1]] == 1 && d.ext[d.ipos[d.ni - 1]] % 2 == 0)
                        ? 1 : 0;
+      // pipelined form: each group one 32-wide chunk, 16-byte loads, and the rest index's
+      // fastest positions multiplying to exactly the tiles one CTA walks
+      d.fast = 0;
+      d.nlo = 0;
+      if (d.tiled && d.Po == 32 && d.Pi == 32 && d.vec_load && P.is_complex) {
+        int64_t lo = 1;
+        int nlo = 0;
+        while (nlo < d.nr && lo < kTilesPerCta) lo *= d.ext[d.rpos[d.nr - 1 - nlo++]];
+        if (lo == kTilesPerCta) {
+          d.fast = 1;
+          d.nlo = nlo;
+        }
+      }
     }
   }
   // ---- statistics (Sec. II-B Eqs. 1-3, per slice; algorithmic flops and bytes)

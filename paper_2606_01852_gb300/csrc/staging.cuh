@@ -149,6 +149,31 @@ __host__ __device__ inline void table_entry(const LeafDesc& d, int64_t go0, int6
   irow = gi < d.Pi ? group_offset(gi, d.ipos, d.ni, d.ext, d.dstride) + go0 : 0;
 }
 
+// Pipelined form (LeafDesc::fast): CTA c walks tiles 16 c .. 16 c + 15, whose rest index is
+// 16 c + i; its offsets split into the low part (i over the last nlo rest positions, the
+// same for every CTA) and the high part (c over the others, plus the slice's offset).
+__host__ __device__ inline void rest_lo_offsets(const LeafDesc& d, int64_t lo, int64_t& src, int64_t& dst) {
+  src = dst = 0;
+  for (int q = d.nr - 1; q >= d.nr - d.nlo; --q) {
+    const int p = d.rpos[q];
+    const int64_t g = lo % d.ext[p];
+    lo /= d.ext[p];
+    src += g * d.sstride[p];
+    dst += g * d.dstride[p];
+  }
+}
+__host__ __device__ inline void rest_hi_offsets(const LeafDesc& d, int64_t hi, int64_t sid, int64_t& src, int64_t& dst) {
+  src = dst = 0;
+  for (int q = d.nr - d.nlo - 1; q >= 0; --q) {
+    const int p = d.rpos[q];
+    const int64_t g = hi % d.ext[p];
+    hi /= d.ext[p];
+    src += g * d.sstride[p];
+    dst += g * d.dstride[p];
+  }
+  for (int q = 0; q < d.n_sl; ++q) src += ((sid / d.sl_div[q]) % d.sl_ext[q]) * d.sl_stride[q];
+}
+
 // Source element (declared order) and staged element of tile entry (ti, to).
 __host__ __device__ inline int64_t tile_src(const LeafDesc& d, const TileBase& t, int64_t gi, int64_t go) {
   return t.src0 + group_offset(gi, d.ipos, d.ni, d.ext, d.sstride) + tail_offset(go, d.rank, d.no, d.ext, d.sstride);

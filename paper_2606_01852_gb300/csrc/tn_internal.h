@@ -52,6 +52,9 @@ struct LeafDesc {
   int32_t vec_load;                // input group's fastest position has source stride 1
                                    // and an even extent: two elements per 16-byte load
   int64_t Po, Pi, Pr;              // extents of the three groups
+  int32_t fast;                    // the pipelined form applies: Po = Pi = 32, 16-byte loads, and
+                                   // the last `nlo` rest positions span exactly the tiles of a CTA
+  int32_t nlo;
   int8_t ipos[kMaxLeafRank], rpos[kMaxLeafRank];
   int64_t dstride[kMaxLeafRank];   // stride of each planned position in the staged copy
 };

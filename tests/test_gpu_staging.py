@@ -23,7 +23,7 @@ def tn():
 def run(tn, net, path, sliced=(), prec="fp32", batch=0):
     plan = tn.Plan(net, path, sliced, prec=prec, max_slice_batch=batch)
     plan.check_staging()
-    assert plan.tensor(0)["tiled"] == 1
+    assert plan.tensor(0)["tiled"] >= 1
     ins = [torch.tensor(np.asarray(t), dtype=torch.complex64, device="cuda") for t in net.tensors]
     out = torch.zeros(tuple(net.extent[x] for x in net.open_modes), dtype=torch.complex128, device="cuda")
     plan.contract(ins, out)
