@@ -230,8 +230,10 @@ def oracle_sample(w, budget_s, slice_id=0):
     """The CPU oracle, as it stands, on one slice of the workload, step by step in path
     order until `budget_s` of CPU time: returns (flops done, seconds, steps done). A step
     predicted to overrun the budget is not started (one step of an unsliced large network
-    can take minutes): the prediction uses the host's matrix-product rate, timed here, or
-    for the max-plus loop the rate of the steps done so far."""
+    can take minutes): the prediction takes the longer of the step's flops at the host's
+    matrix-product rate (timed here; for the max-plus loop the rate of the steps done so far)
+    and its bytes (operands permuted and copied, result written, complex128) at the host's
+    copy rate (timed here)."""
     import oracle
     from oracle import core
     vals = core.slice_assignment(w.net, w.sliced, slice_id)
@@ -249,11 +251,20 @@ def oracle_sample(w, budget_s, slice_id=0):
     for _ in range(4):
         probe = probe @ probe * 1e-3
     host_rate = 4 * fm * 512.0 ** 3 / (time.perf_counter() - tp)
+    big = np.ones(1 << 24, dtype=ts[0].dtype)
+    tp = time.perf_counter()
+    big2 = big.reshape(4096, -1).T.copy()
+    host_bw = 2.0 * big.nbytes / (time.perf_counter() - tp)  # a transposed copy: read + write
+    del big, big2
+    eb = 16.0 if w.net.is_complex else 8.0
     t0 = time.perf_counter()
     for s, (i, j) in enumerate(w.path.pairs):
         el = time.perf_counter() - t0
         rate = host_rate if semiring == "standard" else (flops / el if flops > 0 and el > 0 else None)
-        if done > 0 and rate and el + fm * costs[s]["Ct"] / rate > budget_s:
+        # permuted copies of both operands, the product's read of them, its result
+        moved = eb * (3.0 * costs[s]["m"] * costs[s]["k"] + 3.0 * costs[s]["n"] * costs[s]["k"] +
+                      2.0 * costs[s]["m"] * costs[s]["n"])
+        if done > 0 and rate and el + max(fm * costs[s]["Ct"] / rate, moved / host_bw) > budget_s:
             break
         c, mc = core.pairwise(ts[i], ms[i], ts[j], ms[j], keep, semiring)
         ts.append(c)
@@ -322,7 +333,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = workloads.BY_NAME[args.workload]()
-    budget = args.ref_budget
+    # each step a bounded sample: the whole run (warm-up of 1 s per step) stays near 2.5 min
+    budget = args.ref_budget if args.ref_budget else max(3.0, 150.0 / max(1, args.steps))
     for _ in range(args.warmup):
         oracle_sample(w, min(1.0, budget))
     vals, secs, samples = [], [], []
@@ -571,7 +583,7 @@ def run_ours(args):
         line["oracle"] = [float(want.flat[0].real), float(want.flat[0].imag)]
         line["rel_err_vs_oracle"] = float(np.max(np.abs(result - want)) / np.max(np.abs(want)))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        f, s, done = oracle_sample(w, args.ref_budget)
+        f, s, done = oracle_sample(w, args.ref_budget or 20.0)
         line["cpu_baseline"] = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
                                 "kind": "oracle",
                                 "sample": f"first {done} of {len(w.path.pairs)} path steps of slice 0 "
@@ -873,7 +885,9 @@ def main():
     ap.add_argument("--max-slice-batch", type=int, default=0)
     ap.add_argument("--slices-per-step", type=int, default=0,
                     help="slices contracted per step (0: the workload's default, else all slices)")
-    ap.add_argument("--ref-budget", type=float, default=20.0, help="oracle seconds per sample")
+    ap.add_argument("--ref-budget", type=float, default=0.0,
+                    help="oracle seconds per sample (0: 20 s for the cpu_baseline; for --impl reference, "
+                         "150 s spread over the timed steps, at least 3 s each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="also contract with the CPU oracle and report the error")
     args = ap.parse_args()
