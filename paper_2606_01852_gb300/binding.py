@@ -383,9 +383,9 @@ class Plan:
         leaves = [self.tensor(t) for t in range(self.n_leaves)]
         tiled = sum(1 for x in leaves if x["tiled"])
         tiled_b = sum(1 for x in leaves if x["tiled"] and x["batched"])
-        # per pass: staging (+ one launch per tiled leaf) + steps + root accumulation; once:
-        # the output write
-        return (passes * 2 + sum(per) + (passes - 1) * batched + 1 + tiled + (passes - 1) * tiled_b)
+        # per pass: staging (+ one launch per tiled leaf) + steps + root accumulation (the
+        # last pass's also writes the output)
+        return (passes * 2 + sum(per) + (passes - 1) * batched + tiled + (passes - 1) * tiled_b)
 
     def destroy(self):
         if getattr(self, "handle", None):

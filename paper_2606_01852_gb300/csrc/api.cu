@@ -203,10 +203,9 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
     const int64_t np = cplx ? 2 : 1;
     launch_accumulate_root(reinterpret_cast<const float*>(P.dev + R.offset), R.size,
                            R.batched ? nb : 1, R.batched ? np * R.size : 0, R.size, cplx, acc, recs,
-                           P.rec_index[root], R.batched, ref, p == 0,
-                           P.policy.semiring == TN_SEMIRING_MAXPLUS, st);
+                           P.rec_index[root], R.batched, ref, p == 0, p == npass - 1,
+                           P.policy.semiring == TN_SEMIRING_MAXPLUS, output, log_scale, P.num_sms, st);
   }
-  launch_finalize_output(acc, P.out_elems, cplx, output, log_scale, scaling ? ref : nullptr, st);
   TN_CUDA_TRY(cudaGetLastError());
   return TN_OK;
 }

@@ -153,16 +153,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 #undef TN_R8
 
-__device__ __forceinline__ int64_t map_off(const OffsetMap& om, int64_t idx) {
-  int64_t off = 0;
-  for (int d = om.n - 1; d >= 0; --d) {
-    const uint32_t e = om.ext[d];
-    off += (idx % e) * om.stride[d];
-    idx /= e;
-  }
-  return off;
-}
-
 __device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
 // v rounded to the nearest value with 10 fraction bits (ties away from zero): half a unit in
 // the 10th fraction bit is added to the magnitude and the low 13 bits cleared (finite v
@@ -519,7 +509,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int row = q * 32 + lane;
     const int64_t m = static_cast<int64_t>(m0) + row;
     const bool row_ok = ok && m < a.m;
-    const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
+    const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
     const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
     // Each 32 x 32 block goes through shared memory (the drained stage buffers) and is
@@ -540,7 +530,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       __syncwarp();
       const int64_t n = nb0 + lane;
       const bool col_ok = ok && n < a.n;
-      store_block(C, a.c_plane, kFmtPlanar, tr, 33, 32 * 33, ro, col_ok ? map_off(a.cols, n) : 0, row_ok, col_ok,
+      store_block(C, a.c_plane, kFmtPlanar, tr, 33, 32 * 33, ro, col_ok ? map_offset(a.cols, n) : 0, row_ok, col_ok,
                   lane);
       __syncwarp();
     }
@@ -801,7 +791,7 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
     const int row = q * 32 + lane;
     const int64_t m = static_cast<int64_t>(m0) + row;
     const bool row_ok = ok && m < a.m;
-    const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
+    const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
     // The stage buffers are free here: this warp's last drain waited for the final MMA,
     // which waited for every warp's last split; no TMA load is outstanding.
@@ -819,7 +809,7 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
           for (int j = 0; j < 32; ++j) {
             const int64_t n = nb0 + j;
             if (n < a.n) {
-              const int64_t off = ro + map_off(a.cols, n);
+              const int64_t off = ro + map_offset(a.cols, n);
               C[off] = run_re[cb * 32 + j];
               C[a.c_plane + off] = run_im[cb * 32 + j];
             }
@@ -834,7 +824,7 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
         __syncwarp();
         const int64_t n = nb0 + lane;
         const bool col_ok = ok && n < a.n;
-        const int64_t co = col_ok ? map_off(a.cols, n) : 0;
+        const int64_t co = col_ok ? map_offset(a.cols, n) : 0;
         for (int r = 0; r < 32; ++r) {
           const int64_t ro_r = __shfl_sync(0xffffffffu, ro, r);
           const bool ok_r = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, r) != 0;
@@ -1061,7 +1051,7 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
     const int row = q * 32 + lane;
     const int64_t m = static_cast<int64_t>(m0) + row;
     const bool row_ok = ok && m < a.m;
-    const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
+    const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
     const int split = a.c_split;
     // The stage buffers are free here: the last fold waited for the final MMA, which
@@ -1078,7 +1068,7 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
     for (int cb = 0; cb < 2; ++cb) {
       const int64_t n = static_cast<int64_t>(n0) + half * 64 + cb * 32 + lane;
       const bool col_ok = ok && n < a.n;
-      store_block(C, a.c_plane, split, tr + cb * 32, 65, 32 * 65, ro, col_ok ? map_off(a.cols, n) : 0, row_ok,
+      store_block(C, a.c_plane, split, tr + cb * 32, 65, 32 * 65, ro, col_ok ? map_offset(a.cols, n) : 0, row_ok,
                   col_ok, lane);
     }
   }
@@ -1276,7 +1266,7 @@ __global__ void __launch_bounds__(CB3::THREADS, 1)
     const int row = q * 32 + lane;
     const int64_t m = static_cast<int64_t>(m0) + row;
     const bool row_ok = ok && m < a.m;
-    const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
+    const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
     float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
     const int split = a.c_split;
     // The ring is free here: the last fold waited for the final MMA, which consumed every
@@ -1291,7 +1281,7 @@ __global__ void __launch_bounds__(CB3::THREADS, 1)
     for (int cb = 0; cb < 2; ++cb) {
       const int64_t n = static_cast<int64_t>(n0) + half * 64 + cb * 32 + lane;
       const bool col_ok = ok && n < a.n;
-      store_block(C, a.c_plane, split, tr + cb * 32, 65, 32 * 65, ro, col_ok ? map_off(a.cols, n) : 0, row_ok,
+      store_block(C, a.c_plane, split, tr + cb * 32, 65, 32 * 65, ro, col_ok ? map_offset(a.cols, n) : 0, row_ok,
                   col_ok, lane);
     }
   }
@@ -1486,7 +1476,7 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
       // epilogue from registers: thread = TMEM lane (row); this warp's 64 columns
       const int64_t m = static_cast<int64_t>(tc.m0) + q4 * 32 + lane;
       const bool row_ok = m < a.m;
-      const int64_t ro = row_ok ? map_off(a.rows, m) : 0;
+      const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
       float* C = a.C + static_cast<int64_t>(tc.b) * a.c_bstride;
 #pragma unroll
       for (int cb = 0; cb < 2; ++cb) {
@@ -1498,7 +1488,7 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
         __syncwarp();
         const int64_t n = static_cast<int64_t>(tc.n0) + half * 64 + cb * 32 + lane;
         const bool col_ok = n < a.n;
-        store_block(C, a.c_plane, split, tr, 33, 32 * 33, ro, col_ok ? map_off(a.cols, n) : 0, row_ok, col_ok, lane);
+        store_block(C, a.c_plane, split, tr, 33, 32 * 33, ro, col_ok ? map_offset(a.cols, n) : 0, row_ok, col_ok, lane);
         __syncwarp();
       }
     }

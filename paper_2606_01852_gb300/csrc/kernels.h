@@ -9,6 +9,42 @@
 
 namespace tn {
 
+// Output offset of GEMM row (or column) idx under a separable offset map: the mixed-radix
+// digits of idx over the map's extents (last fastest), each times its stride. Indices
+// below 2^32 take 32-bit digits, and a power-of-two extent a shift and a mask, instead of
+// 64-bit division (the same values, a fraction of the instructions).
+__host__ __device__ inline int64_t map_offset(const OffsetMap& om, int64_t idx) {
+  int64_t off = 0;
+  if (idx >= 0 && idx <= int64_t(0xffffffff)) {
+    uint32_t i = static_cast<uint32_t>(idx);
+    for (int d = om.n - 1; d >= 0; --d) {
+      const uint32_t e = om.ext[d];
+      uint32_t q, r;
+      if ((e & (e - 1u)) == 0u) {
+#ifdef __CUDA_ARCH__
+        const int sh = __ffs(static_cast<int>(e)) - 1;
+#else
+        const int sh = __builtin_ctz(e);
+#endif
+        q = i >> sh;
+        r = i & (e - 1u);
+      } else {
+        q = i / e;
+        r = i - q * e;
+      }
+      off += int64_t(r) * om.stride[d];
+      i = q;
+    }
+    return off;
+  }
+  for (int d = om.n - 1; d >= 0; --d) {
+    const uint32_t e = om.ext[d];
+    off += (idx % e) * om.stride[d];
+    idx /= e;
+  }
+  return off;
+}
+
 // Per tensor (and per batch entry of a batched tensor): the largest binary exponent
 // of the stored values, and the power of two the stored values must be multiplied by
 // to give the true tensor (exponent scaling).
@@ -60,13 +96,12 @@ constexpr int kSplitMaxOut = 16;
 constexpr int64_t kSplitChunk = 4096;
 int32_t splitk_chunks(int64_t k);
 void launch_contract_splitk(const StepArgs& a, int32_t nb, bool cplx, double* scratch, cudaStream_t st);
-// maxplus: the slices combine by maximum instead of the compensated sum
+// maxplus: the slices combine by maximum instead of the compensated sum; last: this pass
+// writes the result (FP64, complex interleaved) to out and the log scale, not to acc
 void launch_accumulate_root(const float* root, int64_t size, int32_t nb, int64_t bstride,
                             int64_t plane, bool cplx, double* acc, const ScaleRec* recs,
-                            int32_t rec_root, bool root_batched, int64_t* ref_exp, bool first,
-                            bool maxplus, cudaStream_t st);
-void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* out, double* log_scale,
-                            const int64_t* ref_exp, cudaStream_t st);
+                            int32_t rec_root, bool root_batched, int64_t* ref_exp, bool first, bool last,
+                            bool maxplus, void* out, double* log_scale, int num_sms, cudaStream_t st);
 
 // tensor-core path (tcgen05); returns false if the step cannot take it
 bool tc_supported();

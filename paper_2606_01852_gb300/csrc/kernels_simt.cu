@@ -5,8 +5,8 @@
 //   contract_simt     : any pairwise step C[b] = A[b](m x k) . B[b](n x k)^T, FP32 FMA,
 //                       written through the separable row/column offset maps
 //   contract_stream   : big x small steps (n*k tiny), one pass over the big operand
-//   accumulate_root   : compensated FP64 sum of the root over the slice batch
-//   finalize_output   : writes the FP64 result and its log scale
+//   accumulate_root   : compensated FP64 sum of the root over the slice batch; the last
+//                       pass writes the FP64 result and its log scale
 #include <algorithm>
 #include <cstdint>
 
@@ -20,16 +20,6 @@ namespace tn {
 
 // ---------------------------------------------------------------------------------
 // helpers
-
-__device__ __forceinline__ int64_t map_offset(const OffsetMap& om, int64_t idx) {
-  int64_t off = 0;
-  for (int d = om.n - 1; d >= 0; --d) {
-    const uint32_t e = om.ext[d];
-    off += (idx % e) * om.stride[d];
-    idx /= e;
-  }
-  return off;
-}
 
 // floor(log2 |v|) from the IEEE-754 exponent field; very small values map to -127.
 __device__ __forceinline__ int exp_of(float v) {
@@ -537,13 +527,16 @@ __global__ void __launch_bounds__(256) contract_simt_kernel(StepArgs a) {
 
 // ---------------------------------------------------------------------------------
 // big x small steps (n*k <= 256, n <= 16): the small operand sits in shared memory
-// and every thread streams rows of the big one; one HBM pass over A and C.
+// and every thread streams rows of the big one; one HBM pass over A and C. A warp's 32
+// rows are 32 * k consecutive floats of each plane: read as float4 (one 16-byte load per
+// lane per four k, so a warp load covers whole 128-byte lines) when k is a multiple of 4
+// and the planes are 16-byte aligned, else one float at a time.
 
 template <bool CPLX, int NMAX>
 __global__ void __launch_bounds__(256) contract_stream_kernel(StepArgs a) {
   __shared__ float Bs[2][256];
   const int b = blockIdx.y;
-  const float* A = a.A + b * a.a_bstride;
+  const float* __restrict__ A = a.A + b * a.a_bstride;
   const float* Bp = a.B + b * a.b_bstride;
   float* C = a.C + b * a.c_bstride;
   float sa = 1.f, sb = 1.f;
@@ -561,39 +554,82 @@ __global__ void __launch_bounds__(256) contract_stream_kernel(StepArgs a) {
   int64_t coff[NMAX];
 #pragma unroll
   for (int j = 0; j < NMAX; ++j) coff[j] = j < n ? map_offset(a.cols, j) : 0;
+  const bool v4 = (k & 3) == 0 &&
+                  ((reinterpret_cast<uintptr_t>(A) | static_cast<uintptr_t>(CPLX ? a.a_plane * 4 : 0)) & 15) == 0;
   int lmax = -127;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.m;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    float cr[NMAX], ci[NMAX];
+  // ROWS rows per thread per iteration (r0 + i * G): their loads are issued together, so
+  // more bytes are in flight per SM at the occupancy the registers allow
+  constexpr int ROWS = NMAX <= 4 ? 2 : 1;
+  const int64_t G = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r0 < a.m; r0 += ROWS * G) {
+    float cr[ROWS][NMAX], ci[ROWS][NMAX];
+    bool live[ROWS];
 #pragma unroll
-    for (int j = 0; j < NMAX; ++j) cr[j] = ci[j] = 0.f;
-    const float* arow = A + r * k;
-    for (int kk = 0; kk < k; ++kk) {
-      const float xr = arow[kk] * sa;
-      const float xi = CPLX ? arow[a.a_plane + kk] * sa : 0.f;
+    for (int i = 0; i < ROWS; ++i) {
+      live[i] = r0 + i * G < a.m;
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) cr[i][j] = ci[i][j] = 0.f;
+    }
+    // one term of row i: x (scaled) times column kk of the small operand
+    auto mac = [&](int i, float xr, float xi, int kk) {
+      xr *= sa;
+      xi *= sa;
 #pragma unroll
       for (int j = 0; j < NMAX; ++j) {
         if (j < n) {
           const float yr = Bs[0][j * k + kk];
           if (CPLX) {
             const float yi = Bs[1][j * k + kk];
-            cr[j] = fmaf(xr, yr, cr[j]);
-            cr[j] = fmaf(-xi, yi, cr[j]);
-            ci[j] = fmaf(xr, yi, ci[j]);
-            ci[j] = fmaf(xi, yr, ci[j]);
+            cr[i][j] = fmaf(xr, yr, cr[i][j]);
+            cr[i][j] = fmaf(-xi, yi, cr[i][j]);
+            ci[i][j] = fmaf(xr, yi, ci[i][j]);
+            ci[i][j] = fmaf(xi, yr, ci[i][j]);
           } else {
-            cr[j] = fmaf(xr, yr, cr[j]);
+            cr[i][j] = fmaf(xr, yr, cr[i][j]);
           }
         }
       }
-    }
-    const int64_t ro = map_offset(a.rows, r);
+    };
+    if (v4) {
+      for (int kk = 0; kk < k; kk += 4) {
+        float4 xr[ROWS], xi[ROWS];
 #pragma unroll
-    for (int j = 0; j < NMAX; ++j) {
-      if (j < n) {
-        if (CPLX) store_cplx(C, a.c_plane, ro + coff[j], cr[j], ci[j], a.c_split);
-        else C[ro + coff[j]] = cr[j];
-        if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(cr[j]), fabsf(ci[j])) : fabsf(cr[j])));
+        for (int i = 0; i < ROWS; ++i) {
+          xr[i] = xi[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (live[i]) {
+            const float* arow = A + (r0 + i * G) * k + kk;
+            xr[i] = __ldg(reinterpret_cast<const float4*>(arow));
+            if (CPLX) xi[i] = __ldg(reinterpret_cast<const float4*>(arow + a.a_plane));
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+          mac(i, xr[i].x, xi[i].x, kk);
+          mac(i, xr[i].y, xi[i].y, kk + 1);
+          mac(i, xr[i].z, xi[i].z, kk + 2);
+          mac(i, xr[i].w, xi[i].w, kk + 3);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i) {
+        if (!live[i]) continue;
+        const float* arow = A + (r0 + i * G) * k;
+        for (int kk = 0; kk < k; ++kk) mac(i, __ldg(arow + kk), CPLX ? __ldg(arow + a.a_plane + kk) : 0.f, kk);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) {
+      if (!live[i]) continue;
+      const int64_t ro = map_offset(a.rows, r0 + i * G);
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+          if (CPLX) store_cplx(C, a.c_plane, ro + coff[j], cr[i][j], ci[i][j], a.c_split);
+          else C[ro + coff[j]] = cr[i][j];
+          if (a.recs)
+            lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(cr[i][j]), fabsf(ci[i][j])) : fabsf(cr[i][j])));
+        }
       }
     }
   }
@@ -680,22 +716,55 @@ void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sm
 }
 
 // ---------------------------------------------------------------------------------
-// cross-slice accumulation (a7): per output element, add the nb slice results of
-// this pass in slice order with Neumaier compensation; with exponent scaling each
-// slice's value is brought to the reference exponent of the first slice ever added.
+// cross-slice accumulation (a7) and output (a8): per output element, add the nb slice
+// results of this pass in slice order with Neumaier compensation; with exponent scaling
+// each slice's value is brought to the reference exponent of the first slice ever added.
+// Passes before the last keep [sum re, sum im, comp re, comp im] in FP64 per element; the
+// last pass writes sum + comp straight to the caller's output (and the log scale), so a
+// one-pass call never touches the accumulator, and a one-slice call (widen_root_kernel)
+// does no FP64 arithmetic at all.
+
+// The binary64 value of a binary32 value, exactly, from the two formats' fields with integer
+// operations only (this GPU's FP64 pipe is narrow; a conversion per output element would
+// bound a one-slice open output): the exponent is rebiased from 127 to 1023 and the 23
+// fraction bits move to the top of the 52; subnormal inputs are normalised; zeros and
+// infinities keep their sign, and a NaN its sign and payload with the quiet bit set (as an
+// IEEE 754 conversion returns a signaling NaN quieted).
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = static_cast<uint64_t>(u >> 31) << 63;
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  uint64_t bits;
+  if (e == 0xffu) {
+    bits = sign | (uint64_t(0x7ff) << 52) | (uint64_t(m) << 29) | (m ? uint64_t(1) << 51 : 0);
+  } else if (e != 0u) {
+    bits = sign | (uint64_t(e + (1023 - 127)) << 52) | (uint64_t(m) << 29);
+  } else if (m == 0u) {
+    bits = sign;
+  } else {  // m * 2^-149 with the leading one at bit p: exponent p - 149, fraction below it
+    const int p = 31 - __clz(static_cast<int>(m));
+    bits = sign | (uint64_t(p - 149 + 1023) << 52) | ((uint64_t(m) << (52 - p)) & ((uint64_t(1) << 52) - 1));
+  }
+  return __longlong_as_double(static_cast<long long>(bits));
+}
 
 __global__ void accumulate_root_kernel(const float* __restrict__ root, int64_t size, int32_t nb,
                                        int64_t bstride, int64_t plane, int32_t cplx, double* acc,
                                        const ScaleRec* recs, int32_t rec_root, int32_t root_batched,
-                                       int64_t* ref_exp, int32_t first, int32_t maxplus) {
+                                       int64_t* ref_exp, int32_t first, int32_t last, int32_t maxplus,
+                                       void* out, double* log_scale) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= size) return;
-  double* s = acc + e * 4;  // [sum re, sum im, comp re, comp im]
-  if (maxplus) {  // slices combine by maximum (real, unscaled); comp stays 0
+  double* s = acc + e * 4;
+  if (maxplus) {  // slices combine by maximum (real, unscaled)
     double best = first ? __longlong_as_double(static_cast<long long>(0xfff0000000000000ull)) : s[0];
     for (int b = 0; b < nb; ++b) best = fmax(best, (double)root[b * bstride + e]);
-    s[0] = best;
-    s[1] = s[2] = s[3] = 0.0;
+    if (last) {
+      reinterpret_cast<double*>(out)[e] = best;
+      if (e == 0 && log_scale) *log_scale = 0.0;
+    } else {
+      s[0] = best;
+    }
     return;
   }
   double sr = first ? 0.0 : s[0], si = first ? 0.0 : s[1];
@@ -722,6 +791,12 @@ __global__ void accumulate_root_kernel(const float* __restrict__ root, int64_t s
     ci += fabs(si) >= fabs(vi) ? (si - t) + vi : (vi - t) + si;
     si = t;
   }
+  if (last) {
+    if (cplx) reinterpret_cast<double2*>(out)[e] = make_double2(sr + cr, si + ci);
+    else reinterpret_cast<double*>(out)[e] = sr + cr;
+    if (e == 0 && log_scale) *log_scale = recs ? double(ref) * 0.69314718055994530942 : 0.0;
+    return;
+  }
   s[0] = sr;
   s[1] = si;
   s[2] = cr;
@@ -729,36 +804,49 @@ __global__ void accumulate_root_kernel(const float* __restrict__ root, int64_t s
   if (recs && first && e == 0) *ref_exp = ref;
 }
 
+// One slice in one pass: the output is that slice's value, widened exactly; no FP64
+// arithmetic. Grid-stride, two elements (e, e + G) per thread per iteration.
+__global__ void __launch_bounds__(256) widen_root_kernel(const float* __restrict__ root, int64_t size,
+                                                         int64_t plane, int32_t cplx, void* out,
+                                                         const ScaleRec* rec, double* log_scale) {
+  const int64_t G = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e0 < size; e0 += 2 * G) {
+    float re[2], im[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int64_t e = e0 + i * G;
+      re[i] = e < size ? __ldg(root + e) : 0.f;
+      im[i] = cplx && e < size ? __ldg(root + plane + e) : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int64_t e = e0 + i * G;
+      if (e >= size) continue;
+      if (cplx) reinterpret_cast<double2*>(out)[e] = make_double2(f64_of_f32(re[i]), f64_of_f32(im[i]));
+      else reinterpret_cast<double*>(out)[e] = f64_of_f32(re[i]);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && log_scale)
+    *log_scale = rec ? double(rec->log2) * 0.69314718055994530942 : 0.0;
+}
+
 void launch_accumulate_root(const float* root, int64_t size, int32_t nb, int64_t bstride,
                             int64_t plane, bool cplx, double* acc, const ScaleRec* recs,
-                            int32_t rec_root, bool root_batched, int64_t* ref_exp, bool first,
-                            bool maxplus, cudaStream_t st) {
+                            int32_t rec_root, bool root_batched, int64_t* ref_exp, bool first, bool last,
+                            bool maxplus, void* out, double* log_scale, int num_sms, cudaStream_t st) {
+  if (first && last && nb == 1) {
+    const int64_t want = (size + 511) / 512;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, int64_t(num_sms) * 8));
+    widen_root_kernel<<<blocks, 256, 0, st>>>(root, size, plane, cplx ? 1 : 0, out,
+                                              recs && !maxplus ? recs + rec_root : nullptr, log_scale);
+    return;
+  }
   const int threads = 128;
   const unsigned blocks = (unsigned)((size + threads - 1) / threads);
   accumulate_root_kernel<<<blocks, threads, 0, st>>>(root, size, nb, bstride, plane, cplx ? 1 : 0, acc,
                                                      recs, rec_root, root_batched ? 1 : 0, ref_exp,
-                                                     first ? 1 : 0, maxplus ? 1 : 0);
-}
-
-__global__ void finalize_output_kernel(const double* acc, int64_t size, int32_t cplx, void* out,
-                                       double* log_scale, const int64_t* ref_exp) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < size) {
-    const double* s = acc + e * 4;
-    if (cplx) {
-      reinterpret_cast<double2*>(out)[e] = make_double2(s[0] + s[2], s[1] + s[3]);
-    } else {
-      reinterpret_cast<double*>(out)[e] = s[0] + s[2];
-    }
-  }
-  if (e == 0 && log_scale) *log_scale = ref_exp ? double(*ref_exp) * 0.69314718055994530942 : 0.0;
-}
-
-void launch_finalize_output(const double* acc, int64_t size, bool cplx, void* out, double* log_scale,
-                            const int64_t* ref_exp, cudaStream_t st) {
-  const int threads = 128;
-  const unsigned blocks = (unsigned)((size + threads - 1) / threads);
-  finalize_output_kernel<<<blocks, threads, 0, st>>>(acc, size, cplx ? 1 : 0, out, log_scale, ref_exp);
+                                                     first ? 1 : 0, last ? 1 : 0, maxplus ? 1 : 0, out,
+                                                     log_scale);
 }
 
 // ---------------------------------------------------------------------------------

@@ -636,8 +636,10 @@ void assign_workspace(Plan& P, int64_t batch) {
     }
   }
   int64_t cur = P.arena_bytes;
+  // cross-slice accumulator [sum re, sum im, comp re, comp im] per output element: only
+  // calls of more than one pass keep it between passes (the last pass writes the output)
   P.off_acc = cur;
-  cur += align_up(P.out_elems * 4 * (int64_t)sizeof(double), kAlign);
+  if (P.n_slices > batch) cur += align_up(P.out_elems * 4 * (int64_t)sizeof(double), kAlign);
   // scale records: unbatched tensors first (reset once per call), then batched ones
   // (reset every pass)
   P.rec_index.assign(N, 0);

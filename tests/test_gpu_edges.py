@@ -94,3 +94,61 @@ def test_last_slice_and_refused_ranges(tn):
         with pytest.raises(tn.TnError) as e:
             plan.contract_slices(ins, begin, count, out)
         assert e.value.status == tn.TN_ERR_INVALID
+
+
+@pytest.mark.parametrize("batch", [1, 3, 4])
+def test_scaled_ring_sliced_passes(tn, batch):
+    """Exponent scaling across passes: the 300-spin Ising ring (Z ~ 1e146, beyond FP32)
+    sliced on two edges (4 slices) at 1, 3 (ragged: 3 + 1) and 4 slices per pass. The
+    reference exponent of the first slice carries over the passes and the last pass writes
+    the value and its log scale: ln Z within 1e-5 relative of the transfer-matrix closed
+    form."""
+    n = 300
+    net = ising_pf.ring_network(n, 1.0, 1.0)
+    path = greedy.greedy_path(net, seed=0)
+    plan = tn.Plan(net, path, [0, n // 2], prec=tn.TN_R32_FP32_SIMT, exp_scaling=True, max_slice_batch=batch)
+    assert plan.info()["n_passes"] == -(-4 // batch)
+    got, ls = run(tn, plan, net, cplx=False)
+    want_ln = n * np.log(2 * np.cosh(1.0)) + np.log1p(np.tanh(1.0) ** n)
+    assert abs(np.log(got) + ls - want_ln) < 1e-5 * abs(want_ln)
+    plan.destroy()
+
+
+@pytest.mark.parametrize("batch", [1, 5, 16])
+def test_open_output_sliced_passes(tn, batch):
+    """An open 2^5-amplitude output over 16 slices in 16, 4 (ragged: 5+5+5+1) and 1 passes:
+    the earlier passes keep the FP64 compensated sums, the last one writes the tensor.
+    Element by element against the oracle's sum of slices."""
+    w = workloads.random_circuit(3, 4, 8, 5, n_sliced=4, open_qubits=(0, 3, 5, 8, 11))
+    plan = tn.Plan(w.net, w.path, w.sliced, max_slice_batch=batch)
+    assert plan.info()["n_passes"] == -(-16 // batch)
+    got, _ = run(tn, plan, w.net)
+    want = oracle.contract(w.net, w.path, w.sliced)
+    assert got.shape == want.shape
+    assert np.abs(got - want).max() / np.abs(want).max() < FP32_BAR
+    plan.destroy()
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_one_slice_output_exact_fp64(tn, cplx):
+    """A one-tensor network (no steps, one slice, one pass): the output is the staged leaf
+    widened to FP64, and every FP32 class (normal, subnormal, signed zeros, infinities,
+    NaN, the extremes) comes out as the same value, bit for bit."""
+    vals = np.array([1.0, -2.5, 3.4028235e38, 1.1754944e-38, 1e-45, -3e-42, 7.0e-40, 0.0, -0.0,
+                     np.inf, -np.inf, np.nan, 1 / 3, -1e-30, 65504.0, -2.0 ** -126], dtype=np.float32)
+    want = vals.astype(np.float64).reshape(4, 4)
+    t = want.copy()
+    if cplx:  # set the parts directly: 1j * inf would put a NaN in the real part
+        t = np.empty((4, 4), dtype=np.complex128)
+        t.real, t.imag = want, want[::-1, ::-1]
+    net = Network([t], [(0, 1)], {0: 4, 1: 4}, (1, 0))
+    plan = tn.Plan(net, Path([]), prec=0 if cplx else tn.TN_R32_FP32_SIMT)
+    got, ls = run(tn, plan, net, cplx=cplx)
+    assert ls == 0.0
+    if cplx:
+        parts = [(got.real, want.T), (got.imag, want[::-1, ::-1].T)]
+    else:
+        parts = [(got, want.T)]
+    for g, w in parts:
+        assert np.array_equal(np.ascontiguousarray(g).view(np.uint64), np.ascontiguousarray(w).view(np.uint64))
+    plan.destroy()

@@ -93,6 +93,20 @@ def test_disconnected_outer_product(tn):
     assert rel_err(got, oracle.contract(net, path)) < REL
 
 
+@pytest.mark.parametrize("arity,real", [(1, False), (2, True), (3, False), (4, False)])
+def test_stream_gate_widths(tn, arity, real):
+    """The streaming kernel's two read forms: k = 2 (one float at a time) and k = 4, 8, 16
+    (float4 rows), complex and real, on a 2^16 state; element by element against the
+    oracle (largest error relative to the largest amplitude)."""
+    net, path = gate_chain_network(n_qubits=16, n_gates=6, seed=10 + arity, arity=arity, real=real)
+    plan = tn.Plan(net, path, prec=tn.TN_R32_FP32_SIMT if real else 0)
+    classes = [plan.step(s)["cls"] for s in range(len(path.pairs))]
+    assert classes.count(tn.TN_CLASS_STREAM) == len(classes)
+    got, _ = run(tn, plan, net, cplx=not real)
+    want = oracle.contract(net, path)
+    assert np.abs(got - want).max() / np.abs(want).max() < 1e-5
+
+
 @pytest.mark.parametrize("batch", [1, 3, 16, 0])
 def test_sliced_sum_and_partials(tn, batch):
     w = workloads.random_circuit(3, 4, 8, 3, n_sliced=4)
@@ -116,22 +130,26 @@ def test_kicked_ising_small(tn):
     assert abs(got - want) < REL * max(1.0, abs(want))
 
 
-def gate_chain_network(n_qubits=12, n_gates=10, seed=4):
-    """A 2^n state tensor absorbing a chain of two-qubit gates (state-vector style
+def gate_chain_network(n_qubits=12, n_gates=10, seed=4, arity=2, real=False):
+    """A 2^n state tensor absorbing a chain of `arity`-qubit gates (state-vector style
     path): every step is big x small, with the gate's new modes landing at arbitrary
-    positions of the open result."""
+    positions of the open result. real: a real state and orthogonal gates."""
     from tn_inputs.network import Network, Path
     rng = np.random.default_rng(seed)
-    psi = rng.standard_normal((2,) * n_qubits) + 1j * rng.standard_normal((2,) * n_qubits)
+    psi = rng.standard_normal((2,) * n_qubits)
+    if not real:
+        psi = psi + 1j * rng.standard_normal((2,) * n_qubits)
     wire = list(range(n_qubits))
     tensors, modes, nxt = [psi], [tuple(wire)], n_qubits
+    d = 2 ** arity
     for _ in range(n_gates):
-        q0, q1 = (int(x) for x in rng.choice(n_qubits, size=2, replace=False))
-        g = circuits.haar_unitary(rng, 4).reshape(2, 2, 2, 2)
-        tensors.append(g)
-        modes.append((nxt, nxt + 1, wire[q0], wire[q1]))
-        wire[q0], wire[q1] = nxt, nxt + 1
-        nxt += 2
+        qs = [int(x) for x in rng.choice(n_qubits, size=arity, replace=False)]
+        u = np.linalg.qr(rng.standard_normal((d, d)))[0] if real else circuits.haar_unitary(rng, d)
+        tensors.append(u.reshape((2,) * (2 * arity)))
+        modes.append(tuple(range(nxt, nxt + arity)) + tuple(wire[q] for q in qs))
+        for i, q in enumerate(qs):
+            wire[q] = nxt + i
+        nxt += arity
     net = Network(tensors, modes, {x: 2 for x in range(nxt)}, tuple(wire))
     net.check()
     pairs, cur = [], 0
