@@ -204,3 +204,29 @@ def test_sliced_circuit_open_qubits(tn, prec, tol):
     assert plan.out_shape == (2, 2, 2, 2)
     got, _ = run(tn, plan, w.net)
     assert rel_err(got, oracle.contract(w.net, w.path, w.sliced)) < tol
+
+
+@pytest.mark.parametrize("prec,bound", [("bf16x3", 5e-5), ("bf16x3m", 1e-4), ("3xtf32", 1e-5)])
+def test_stream_step_feeding_tensor_core_step(tn, prec, bound):
+    """A 2^22-element state absorbs a two-qubit gate (a streaming big x small step) and the
+    result is contracted with a 2^21-element tensor over 14 labels (a tensor-core step,
+    256 x 128 outputs, k = 2^14). The streaming kernel writes its output in the form the
+    tensor-core step reads (split BF16 planes for BF16x3, the six planes of the 3M form);
+    the open result against the oracle in the Frobenius norm and element by element."""
+    rng = np.random.default_rng(7)
+    psi = rng.standard_normal((2,) * 22) + 1j * rng.standard_normal((2,) * 22)
+    g = (rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))).reshape(2, 2, 2, 2)
+    x = rng.standard_normal((2,) * 21) + 1j * rng.standard_normal((2,) * 21)
+    # psi(0..21); gate(22, 23, 0, 1) -> new labels 22, 23 for qubits 0, 1; x(22, 23, 2..13, 24..30)
+    modes = [tuple(range(22)), (22, 23, 0, 1), (22, 23) + tuple(range(2, 14)) + tuple(range(24, 31))]
+    out = tuple(range(14, 22)) + tuple(range(24, 31))
+    net = Network([psi, g, x], modes, {q: 2 for q in range(31)}, out)
+    net.check()
+    path = Path([(0, 1), (2, 3)])
+    plan = tn.Plan(net, path, prec=prec, complex_mult=3 if prec == "bf16x3m" else 4)
+    assert plan.step(0)["cls"] == tn.TN_CLASS_STREAM and plan.step(1)["cls"] == tn.TN_CLASS_TC
+    got, _ = run(tn, plan, net)
+    want = oracle.contract(net, path)
+    assert rel_err(got, want) < bound
+    assert np.abs(got - want).max() / np.abs(want).max() < 4 * bound
+    plan.destroy()
