@@ -188,7 +188,7 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
                                                                                               : P.policy.prec;
         TN_CUDA_TRY(launch_contract_tc(a, nbs, form, cplx, errw, st));
       } else if (sr.cls == TN_CLASS_STREAM) {
-        launch_contract_stream(a, nbs, cplx, P.num_sms, st);
+        launch_contract_stream(a, nbs, cplx, P.num_sms, errw, st);
       } else if (sr.cls == TN_CLASS_SPLITK) {
         launch_contract_splitk(a, nbs, cplx, reinterpret_cast<double*>(P.dev + P.off_scratch), st);
       } else {

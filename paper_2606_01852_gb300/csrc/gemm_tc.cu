@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "mbarrier.cuh"
 #include "split_bf16.cuh"
 
 namespace tn {
@@ -34,7 +35,6 @@ constexpr int BM = 128, BN = 128;
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;                         // D_rr @0, D_ii @128, D_x @256
 constexpr int GROUP_M = 16;                                 // raster: tiles grouped along M
-constexpr uint64_t kWaitNs = 4000000000ull;                 // 4 s bound on any wait
 
 template <int SPLIT>
 struct Cfg {
@@ -47,45 +47,6 @@ struct Cfg {
   static constexpr int LO = SPLIT == 1 ? 0 : 2;             // lo buffers
   static constexpr int SMEM = (STAGES + LO) * STAGE + 1024 /*barriers*/ + 1024 /*align*/;
 };
-
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t gtime() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for the phase of parity `parity` to complete; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns = kWaitNs) {
-  if (mbar_test(b, parity)) return true;
-  const uint64_t t0 = gtime();
-  while (true) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_test(b, parity)) return true;
-    if (gtime() - t0 > limit_ns) return false;
-  }
-}
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that is completed only
 // if `arrive` is set. Without the arrival the wait runs out after limit_ns, the kernel

@@ -88,7 +88,8 @@ void launch_contract_simt(const StepArgs& a, int32_t nb, bool cplx, cudaStream_t
 // k parts for a SIMT step of m x n outputs per batch entry, `copies` entries, depth k on
 // num_sms SMs (1 = no split: at least 2 x num_sms tiles, k < 2048, or a scaled step)
 int32_t simt_ksplit(int64_t m, int64_t n, int64_t k, int64_t copies, int num_sms, bool scaled);
-void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, cudaStream_t st);
+// err: the plan's error word (the bulk-copy form records an expired wait there)
+void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, int* err, cudaStream_t st);
 
 // split-K steps: at most kSplitMaxOut outputs, k cut in chunks of kSplitChunk; scratch
 // holds nb * splitk_chunks(k) * m*n complex doubles

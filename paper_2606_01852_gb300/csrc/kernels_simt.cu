@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "mbarrier.cuh"
 #include "split_bf16.cuh"
 #include "staging.cuh"
 
@@ -646,6 +647,155 @@ __global__ void __launch_bounds__(256) contract_stream_kernel(StepArgs a) {
   }
 }
 
+// Big x small steps with k = 4, 8 or 16 and a 16-byte-aligned big operand: its rows reach
+// shared memory by bulk copies (cp.async.bulk, one per plane per 256-row tile) through a
+// ring of S tiles per CTA, so the bytes in flight per SM are set by the ring, not by the
+// registers of the threads; each thread then computes one row of a tile and stores its n
+// outputs. Persistent: CTA c takes tiles c, c + gridDim.x, ...; thread 0 issues the copies,
+// refilling a tile's slot once every thread has read it. The waits are bounded: an expired
+// one records code 41 in err, and the CTA waits (bounded) for its copies in flight and
+// stops.
+template <int K, bool CPLX>
+struct StreamTma {
+  static constexpr int TR = 256;                     // rows per tile (one per thread)
+  static constexpr int PL = CPLX ? 2 : 1;
+  static constexpr int TILE = TR * K;                // floats of one plane of one tile
+  static constexpr int S = K <= 4 ? 6 : (K <= 8 ? 4 : 3);
+  static constexpr int SMEM = S * PL * TILE * 4 + 2 * 256 * 4 + S * 8;
+};
+
+template <bool CPLX, int NMAX, int K>
+__global__ void __launch_bounds__(256) contract_stream_tma_kernel(StepArgs a, int* err) {
+  using G = StreamTma<K, CPLX>;
+  constexpr int TR = G::TR, TILE = G::TILE, S = G::S, PL = G::PL;
+  extern __shared__ __align__(128) float sm[];
+  float* ring = sm;                                  // [S][PL][TR * K]
+  float* Bs = sm + S * PL * TILE;                    // [2][256]
+  uint64_t* full = reinterpret_cast<uint64_t*>(Bs + 2 * 256);
+  const int tid = threadIdx.x;
+  const int b = blockIdx.y;
+  const float* A = a.A + b * a.a_bstride;
+  const float* Bp = a.B + b * a.b_bstride;
+  float* C = a.C + b * a.c_bstride;
+  float sa = 1.f, sb = 1.f;
+  if (a.recs) {
+    sa = pow2_neg(scale_exp(a.recs + a.rec_a + (a.a_bstride ? b : 0)));
+    sb = pow2_neg(scale_exp(a.recs + a.rec_b + (a.b_bstride ? b : 0)));
+  }
+  const int n = (int)a.n;
+  for (int i = tid; i < n * K; i += blockDim.x) {
+    Bs[i] = Bp[i] * sb;
+    if (CPLX) Bs[256 + i] = Bp[a.b_plane + i] * sb;
+  }
+  const int64_t tiles = (a.m + TR - 1) / TR;
+  const int64_t mine = tiles > blockIdx.x ? (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  auto issue = [&](int64_t i) {  // local tile i into slot i % S (thread 0)
+    const int slot = static_cast<int>(i % S);
+    const int64_t r0 = (blockIdx.x + i * gridDim.x) * TR;
+    const int64_t rows = a.m - r0 < TR ? a.m - r0 : TR;
+    const uint32_t bytes = static_cast<uint32_t>(rows * K * 4);
+    float* dst = ring + slot * PL * TILE;
+    mbar_expect_tx(&full[slot], PL * bytes);
+    bulk_load(dst, A + r0 * K, bytes, &full[slot]);
+    if (CPLX) bulk_load(dst + TILE, A + a.a_plane + r0 * K, bytes, &full[slot]);
+  };
+  int64_t issued = 0;
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) mbar_init(&full[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (; issued < S && issued < mine; ++issued) issue(issued);
+  }
+  __syncthreads();
+  int64_t coff[NMAX];
+#pragma unroll
+  for (int j = 0; j < NMAX; ++j) coff[j] = j < n ? map_offset(a.cols, j) : 0;
+  int lmax = -127;
+  int64_t i = 0;
+  for (; i < mine; ++i) {
+    const int slot = static_cast<int>(i % S);
+    const bool ok = __syncthreads_and(mbar_wait(&full[slot], static_cast<uint32_t>((i / S) & 1)) ? 1 : 0);
+    if (!ok) {
+      if (tid == 0) atomicExch(err, 41);
+      break;
+    }
+    const int64_t r = (blockIdx.x + i * gridDim.x) * TR + tid;
+    if (r < a.m) {
+      const float* xr_s = ring + slot * PL * TILE + tid * K;
+      float cr[NMAX], ci[NMAX];
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) cr[j] = ci[j] = 0.f;
+#pragma unroll
+      for (int k4 = 0; k4 < K; k4 += 4) {
+        const float4 xr = *reinterpret_cast<const float4*>(xr_s + k4);
+        const float4 xi = CPLX ? *reinterpret_cast<const float4*>(xr_s + TILE + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float vr[4] = {xr.x * sa, xr.y * sa, xr.z * sa, xr.w * sa};
+        const float vi[4] = {xi.x * sa, xi.y * sa, xi.z * sa, xi.w * sa};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+          for (int j = 0; j < NMAX; ++j) {
+            if (j < n) {
+              const float yr = Bs[j * K + k4 + q];
+              if (CPLX) {
+                const float yi = Bs[256 + j * K + k4 + q];
+                cr[j] = fmaf(vr[q], yr, cr[j]);
+                cr[j] = fmaf(-vi[q], yi, cr[j]);
+                ci[j] = fmaf(vr[q], yi, ci[j]);
+                ci[j] = fmaf(vi[q], yr, ci[j]);
+              } else {
+                cr[j] = fmaf(vr[q], yr, cr[j]);
+              }
+            }
+          }
+        }
+      }
+      const int64_t ro = map_offset(a.rows, r);
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+          if (CPLX) store_cplx(C, a.c_plane, ro + coff[j], cr[j], ci[j], a.c_split);
+          else C[ro + coff[j]] = cr[j];
+          if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(cr[j]), fabsf(ci[j])) : fabsf(cr[j])));
+        }
+      }
+    }
+    __syncthreads();  // every thread has read the slot: refill it
+    if (tid == 0 && issued < mine) issue(issued++);
+  }
+  if (tid == 0) {  // after an expired wait: let the copies in flight land before exiting
+    for (int64_t j = i; j < issued; ++j)
+      if (!mbar_wait(&full[j % S], static_cast<uint32_t>((j / S) & 1))) break;
+  }
+  if (a.recs) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    ScaleRec* rc = a.recs + a.rec_c + (a.c_bstride ? b : 0);
+    if ((tid & 31) == 0) atomicMax(&rc->emax, lmax);
+    if (blockIdx.x == 0 && tid == 0) {
+      const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
+      const ScaleRec* rb = a.recs + a.rec_b + (a.b_bstride ? b : 0);
+      rc->log2 = ra->log2 + rb->log2 + scale_exp(ra) + scale_exp(rb);
+    }
+  }
+}
+
+template <bool CPLX, int NMAX, int K>
+void launch_stream_tma(const StepArgs& a, int32_t nb, int num_sms, int* err, cudaStream_t st) {
+  constexpr int smem = StreamTma<K, CPLX>::SMEM;
+  static int per_sm = 0;  // resident CTAs per SM, looked up once per form
+  if (per_sm == 0) {
+    cudaFuncSetAttribute(contract_stream_tma_kernel<CPLX, NMAX, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, contract_stream_tma_kernel<CPLX, NMAX, K>, 256, smem);
+    per_sm = occ > 0 ? occ : 1;
+  }
+  const int64_t tiles = (a.m + 255) / 256;
+  int64_t gx = (int64_t(num_sms) * per_sm + nb - 1) / nb;
+  gx = std::max<int64_t>(1, std::min<int64_t>(gx, tiles));
+  contract_stream_tma_kernel<CPLX, NMAX, K><<<dim3((unsigned)gx, (unsigned)nb), 256, smem, st>>>(a, err);
+}
+
 // Combine the k parts of a split SIMT step in part order (sum, or max for max-plus) and
 // write C through the offset maps. One thread per output element of every batch entry.
 __global__ void simt_combine_kernel(StepArgs a, int32_t nb, int32_t cplx) {
@@ -697,7 +847,32 @@ void launch_contract_simt(const StepArgs& a, int32_t nb, bool cplx, cudaStream_t
   }
 }
 
-void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, cudaStream_t st) {
+// The bulk-copy form takes k = 4, 8, 16 with the big operand's planes and batch entries
+// 16-byte aligned and at least 32 tiles of rows; the register form everything else.
+bool stream_tma_ok(const StepArgs& a) {
+  const bool kk = a.k == 4 || a.k == 8 || a.k == 16;
+  const bool al = (reinterpret_cast<uintptr_t>(a.A) & 15) == 0 && (a.a_plane & 3) == 0 && (a.a_bstride & 3) == 0;
+  return kk && al && a.n <= 16 && a.m >= 32 * 256;
+}
+
+void launch_contract_stream(const StepArgs& a, int32_t nb, bool cplx, int num_sms, int* err, cudaStream_t st) {
+  if (stream_tma_ok(a)) {
+#define TN_STREAM_TMA(KK)                                                                   \
+  if (a.k == KK) {                                                                          \
+    if (a.n <= 4) {                                                                         \
+      if (cplx) launch_stream_tma<true, 4, KK>(a, nb, num_sms, err, st);                    \
+      else launch_stream_tma<false, 4, KK>(a, nb, num_sms, err, st);                        \
+    } else {                                                                                \
+      if (cplx) launch_stream_tma<true, 16, KK>(a, nb, num_sms, err, st);                   \
+      else launch_stream_tma<false, 16, KK>(a, nb, num_sms, err, st);                       \
+    }                                                                                       \
+    return;                                                                                 \
+  }
+    TN_STREAM_TMA(4)
+    TN_STREAM_TMA(8)
+    TN_STREAM_TMA(16)
+#undef TN_STREAM_TMA
+  }
   int64_t blocks = (a.m + 255) / 256;
   const int64_t cap = (int64_t)num_sms * 8;
   if (blocks > cap) blocks = cap;

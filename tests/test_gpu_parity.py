@@ -93,17 +93,32 @@ def test_disconnected_outer_product(tn):
     assert rel_err(got, oracle.contract(net, path)) < REL
 
 
-@pytest.mark.parametrize("arity,real", [(1, False), (2, True), (3, False), (4, False)])
+@pytest.mark.parametrize("arity,real", [(1, False), (2, True), (2, False), (3, False), (4, False), (4, True)])
 def test_stream_gate_widths(tn, arity, real):
-    """The streaming kernel's two read forms: k = 2 (one float at a time) and k = 4, 8, 16
-    (float4 rows), complex and real, on a 2^16 state; element by element against the
-    oracle (largest error relative to the largest amplitude)."""
-    net, path = gate_chain_network(n_qubits=16, n_gates=6, seed=10 + arity, arity=arity, real=real)
+    """The streaming kernel's forms on a 2^18 state: k = 2 (registers, one float at a
+    time) and k = 4, 8, 16 (rows staged in shared memory by bulk copies; n = 4, 8, 16),
+    complex and real; element by element against the oracle (largest error relative to the
+    largest amplitude)."""
+    net, path = gate_chain_network(n_qubits=18, n_gates=6, seed=10 + arity, arity=arity, real=real)
     plan = tn.Plan(net, path, prec=tn.TN_R32_FP32_SIMT if real else 0)
     classes = [plan.step(s)["cls"] for s in range(len(path.pairs))]
     assert classes.count(tn.TN_CLASS_STREAM) == len(classes)
     got, _ = run(tn, plan, net, cplx=not real)
     want = oracle.contract(net, path)
+    assert np.abs(got - want).max() / np.abs(want).max() < 1e-5
+
+
+@pytest.mark.parametrize("batch", [1, 2, 4])
+def test_stream_sliced_big_operand(tn, batch):
+    """A gate chain with the original label of a gated qubit sliced (4 slices over two
+    labels): the state and the first gates are batched, so the streaming steps read a
+    batched big operand (batch stride between slices) at 1, 2 and 4 slices per pass."""
+    net, path = gate_chain_network(n_qubits=18, n_gates=6, seed=21, arity=2)
+    sliced = [net.modes[1][2], net.modes[1][3]]
+    plan = tn.Plan(net, path, sliced, max_slice_batch=batch)
+    assert plan.step(0)["cls"] == tn.TN_CLASS_STREAM and plan.step(0)["batched"] == 1
+    got, _ = run(tn, plan, net)
+    want = oracle.contract(net, path, sliced)
     assert np.abs(got - want).max() / np.abs(want).max() < 1e-5
 
 
