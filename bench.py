@@ -797,8 +797,8 @@ def run_serve_bench(args):
         return out, results
 
     def burst(pack_max, n_burst=2048):
-        """n_burst small requests (amplitudes and partition functions) submitted at once:
-        requests/s from the first submission to the last completion."""
+        """n_burst small requests (amplitudes and partition functions) submitted at once (one
+        tn_serve_submit_batch): requests/s from the submission to the last completion."""
         p_amp = tn.Plan(amp_w.net, amp_w.path, prec=PREC[args.serve_prec])
         p_pf = [tn.Plan(w.net, w.path, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True) for w in pf_pool]
         small = [i for i in range(n_req) if cls[i] != 2][:n_burst]
@@ -809,7 +809,7 @@ def run_serve_bench(args):
             srv.poll(srv.submit(plan_of(i), inputs(i)), np.zeros(2), None, -1)
         ins = [inputs(i) for i in small]
         t0 = time.perf_counter()
-        ts = [srv.submit(plan_of(i), x) for i, x in zip(small, ins)]
+        ts = srv.submit_batch([(plan_of(i), x) for i, x in zip(small, ins)])
         for t in ts:
             srv.poll(t, np.zeros(2), None, -1)
         dt = time.perf_counter() - t0

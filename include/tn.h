@@ -335,6 +335,16 @@ tn_status tn_serve_create(const tn_serve_config* cfg, tn_server_t* out);
 tn_status tn_serve_submit(tn_server_t srv, tn_plan_t plan, const void* const* host_inputs,
                           uint64_t* ticket);
 
+/* Submit n requests at once: request j contracts plans[j] on host_inputs[j] (one host
+ * pointer per leaf of that plan, as for tn_serve_submit); its ticket goes to tickets[j].
+ * All are queued together, in order, under one acquisition of the server's queue, so the
+ * scheduler sees them side by side and can pack compatible ones into one launch (a burst
+ * submitted one by one may be admitted request by request). All or nothing: on an error
+ * (TN_ERR_INVALID for a null argument, TN_ERR_BUSY when the queue cannot take all n) no
+ * request is queued. */
+tn_status tn_serve_submit_batch(tn_server_t srv, int32_t n, const tn_plan_t* plans,
+                                const void* const* const* host_inputs, uint64_t* tickets);
+
 /* Wait up to timeout_us (0 = do not wait, <0 = forever) for a ticket. On TN_OK writes
  * the result (complex128 or float64, |open| elements) to host `result`, the log scale
  * to *log_scale if non-NULL, and retires the ticket. TN_ERR_NOT_READY if still in

@@ -146,6 +146,7 @@ def _load():
         "tn_selftest_bounded_wait": [vp, i32, i64, vp],
         "tn_serve_create": [C.POINTER(tn_serve_config), C.POINTER(vp)],
         "tn_serve_submit": [vp, vp, C.POINTER(vp), C.POINTER(u64)],
+        "tn_serve_submit_batch": [vp, i32, C.POINTER(vp), C.POINTER(C.POINTER(vp)), C.POINTER(u64)],
         "tn_serve_poll": [vp, u64, vp, vp, i32],
         "tn_serve_destroy": [vp],
         "tn_serve_stats_get": [vp, C.POINTER(tn_serve_stats)],
@@ -516,6 +517,17 @@ class Server:
         t = C.c_uint64()
         check(lib.tn_serve_submit(self.handle, plan.handle, plan._inputs(host_inputs), C.byref(t)))
         return t.value
+
+    def submit_batch(self, requests) -> list:
+        """Queue [(plan, host_inputs), ...] together (tn_serve_submit_batch); the tickets."""
+        n = len(requests)
+        plans = (C.c_void_p * max(1, n))(*[p.handle.value if hasattr(p.handle, "value") else p.handle
+                                          for p, _ in requests])
+        arrs = [p._inputs(x) for p, x in requests]
+        ins = (C.POINTER(C.c_void_p) * max(1, n))(*[C.cast(a, C.POINTER(C.c_void_p)) for a in arrs])
+        tickets = (C.c_uint64 * max(1, n))()
+        check(lib.tn_serve_submit_batch(self.handle, n, plans, ins, tickets))
+        return list(tickets)[:n]
 
     def try_submit(self, plan: Plan, host_inputs):
         t = C.c_uint64()

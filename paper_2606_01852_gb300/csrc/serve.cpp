@@ -591,43 +591,70 @@ tn_status tn_serve_create(const tn_serve_config* cfg, tn_server_t* out) {
 
 tn_status tn_serve_submit(tn_server_t srv, tn_plan_t plan, const void* const* host_inputs,
                           uint64_t* ticket) {
-  if (!srv || !plan || !host_inputs || !ticket) {
+  return tn_serve_submit_batch(srv, 1, &plan, &host_inputs, ticket);
+}
+
+tn_status tn_serve_submit_batch(tn_server_t srv, int32_t n, const tn_plan_t* plans,
+                                const void* const* const* host_inputs, uint64_t* tickets) {
+  if (!srv || n < 0 || (n > 0 && (!plans || !host_inputs || !tickets))) {
     set_error("null argument");
     return TN_ERR_INVALID;
   }
-  if (!plan->P.dev) {
-    set_error("plan was built with TN_PLAN_HOST_ONLY");
-    return TN_ERR_INVALID;
-  }
-  auto r = std::make_unique<Request>();
-  r->plan = plan;
-  int64_t tot = 0;
-  r->in_off.resize(plan->P.n_leaves);
-  for (int32_t t = 0; t < plan->P.n_leaves; ++t) {
-    if (!host_inputs[t]) {
-      set_error("null input pointer");
+  // copy every request's inputs before taking the lock; nothing is queued on an error
+  std::vector<std::unique_ptr<Request>> made;
+  made.reserve((size_t)n);
+  auto drop = [&made]() {
+    for (auto& r : made) cudaEventDestroy(r->done);
+  };
+  for (int32_t j = 0; j < n; ++j) {
+    tn_plan_t plan = plans[j];
+    const void* const* in = host_inputs[j];
+    if (!plan || !in) {
+      drop();
+      set_error("null argument");
       return TN_ERR_INVALID;
     }
-    r->in_off[t] = tot;
-    tot += leaf_bytes(plan->P, t);
-  }
-  r->inputs.resize((size_t)tot);
-  for (int32_t t = 0; t < plan->P.n_leaves; ++t)
-    std::memcpy(r->inputs.data() + r->in_off[t], host_inputs[t], (size_t)leaf_bytes(plan->P, t));
-  if (cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess) {
-    set_error("event creation failed");
-    return TN_ERR_CUDA;
+    if (!plan->P.dev) {
+      drop();
+      set_error("plan was built with TN_PLAN_HOST_ONLY");
+      return TN_ERR_INVALID;
+    }
+    auto r = std::make_unique<Request>();
+    r->plan = plan;
+    int64_t tot = 0;
+    r->in_off.resize(plan->P.n_leaves);
+    for (int32_t t = 0; t < plan->P.n_leaves; ++t) {
+      if (!in[t]) {
+        drop();
+        set_error("null input pointer");
+        return TN_ERR_INVALID;
+      }
+      r->in_off[t] = tot;
+      tot += leaf_bytes(plan->P, t);
+    }
+    r->inputs.resize((size_t)tot);
+    for (int32_t t = 0; t < plan->P.n_leaves; ++t)
+      std::memcpy(r->inputs.data() + r->in_off[t], in[t], (size_t)leaf_bytes(plan->P, t));
+    if (cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess) {
+      drop();
+      set_error("event creation failed");
+      return TN_ERR_CUDA;
+    }
+    made.push_back(std::move(r));
   }
   std::lock_guard<std::mutex> g(srv->mu);
-  if ((int)srv->queue.size() >= srv->cfg.queue_capacity) {
-    cudaEventDestroy(r->done);
+  if ((int64_t)srv->queue.size() + n > srv->cfg.queue_capacity) {
+    drop();
     set_error("serve queue full");
     return TN_ERR_BUSY;
   }
-  r->id = srv->next_id++;
-  *ticket = r->id;
-  srv->queue.push_back(r->id);
-  srv->reqs[r->id] = std::move(r);
+  for (int32_t j = 0; j < n; ++j) {
+    std::unique_ptr<Request>& r = made[(size_t)j];
+    r->id = srv->next_id++;
+    tickets[j] = r->id;
+    srv->queue.push_back(r->id);
+    srv->reqs[r->id] = std::move(r);
+  }
   srv->cv_work.notify_one();
   return TN_OK;
 }

@@ -184,7 +184,8 @@ def _pack_jobs(tn):
 def test_packed_results_identical_alone_and_in_mix(tn):
     """With packing on, a request gives the same bits served alone (a pack of one) and in a
     mix where it shares a launch with others (one CTA per request, fixed order within it),
-    and the values match the oracle."""
+    and the values match the oracle. The mix is queued by one tn_serve_submit_batch, so the
+    packs form whatever the timing."""
     jobs, (amps, path, ising, i_paths, big) = _pack_jobs(tn)
 
     def serve_all(one_at_a_time):
@@ -196,8 +197,8 @@ def test_packed_results_identical_alone_and_in_mix(tn):
                 ls = np.zeros(1)
                 assert srv.poll(srv.submit(plan, host_inputs(net, cplx)), out, ls, timeout_us=-1) == tn.TN_OK
                 res.append((out.copy(), ls[0]))
-        else:
-            ts = [srv.submit(plan, host_inputs(net, cplx)) for plan, net, cplx in jobs]
+        else:  # queued together (one submit_batch): the scheduler sees the whole mix
+            ts = srv.submit_batch([(plan, host_inputs(net, cplx)) for plan, net, cplx in jobs])
             for t, (plan, net, cplx) in zip(ts, jobs):
                 out = np.zeros((), dtype=np.complex128 if cplx else np.float64)
                 ls = np.zeros(1)
@@ -238,4 +239,27 @@ def test_packed_under_budget(tn):
         out = np.zeros((), dtype=np.complex128 if cplx else np.float64)
         assert srv.poll(t, out, None, timeout_us=-1) == tn.TN_OK, tn.last_error()
     assert srv.stats()["hbm_in_use"] <= 64 << 20
+    srv.destroy()
+
+
+def test_submit_batch_all_or_nothing(tn):
+    """tn_serve_submit_batch queues all n requests or none: a batch larger than the free
+    queue space is refused with TN_ERR_BUSY and leaves nothing queued; a batch that fits
+    returns n tickets in order, each completing with its own result."""
+    amps = amp_requests(6, seed=11)
+    path = greedy.greedy_path(amps[0], seed=0, alpha=1.0)
+    plan = tn.Plan(amps[0], path, prec="3xtf32")
+    srv = tn.Server(max_inflight=1, n_streams=1, queue_capacity=4, pack_max=8)
+    reqs = [(plan, host_inputs(n)) for n in amps]
+    with pytest.raises(tn.binding.TnError):
+        srv.submit_batch(reqs[:5])
+    assert srv.stats()["completed"] == 0
+    ts = srv.submit_batch(reqs[:4])
+    assert len(ts) == 4 and ts == sorted(ts)
+    for t, n in zip(ts, amps):
+        out = np.zeros((), dtype=np.complex128)
+        assert srv.poll(t, out, timeout_us=-1) == tn.TN_OK
+        want = oracle.contract(n, path)
+        assert abs(complex(out) - want) / abs(want) < 1e-5
+    assert srv.stats()["completed"] == 4
     srv.destroy()
