@@ -390,7 +390,7 @@ def run_ours(args):
     # a slice-batched step runs its slices in one pass unless told otherwise
     batch = args.max_slice_batch or (per_step if per_step < n_sl else 0)
     plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=batch, semiring=semiring,
-                   complex_mult=cmult)
+                   complex_mult=cmult, single_sm_tiles=args.single_sm_tiles)
     info = plan.info()
     stream = torch.cuda.current_stream()
     # step j contracts slices [j * per_step, (j + 1) * per_step) modulo n_slices
@@ -883,6 +883,8 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=sorted(PREC),
                     help="GEMM form: bf16x3 (default), 3xtf32, tf32, fp32 (the plain CUDA-core form)")
     ap.add_argument("--max-slice-batch", type=int, default=0)
+    ap.add_argument("--single-sm-tiles", action="store_true",
+                    help="BF16x3 4M steps on one SM per output tile (no paired-SM kernel)")
     ap.add_argument("--slices-per-step", type=int, default=0,
                     help="slices contracted per step (0: the workload's default, else all slices)")
     ap.add_argument("--ref-budget", type=float, default=0.0,

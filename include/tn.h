@@ -75,10 +75,13 @@ typedef enum { TN_SEMIRING_STANDARD = 0, TN_SEMIRING_MAXPLUS = 1 } tn_semiring;
 
 /* Plan flags. */
 #define TN_PLAN_HOST_ONLY 1u     /* plan and query only: no device memory, no contract */
+#define TN_PLAN_SINGLE_SM_TILES 2u /* BF16x3 4M steps keep one SM per output tile (by default
+                                      a step with m >= 256 and k > 256 runs 256 x 128 tiles
+                                      on pairs of SMs); the results are the same bits */
 
 typedef struct {
   int32_t prec;            /* tn_precision */
-  int32_t complex_mult;    /* 4 (4M) -- the only form built; 3 is rejected */
+  int32_t complex_mult;    /* 4 (4M); 3 (3M, Gauss) with TN_C64_BF16X3 only, else rejected */
   int32_t exp_scaling;     /* 1: per-intermediate power-of-two scaling, log scale in FP64
                               (FP32_SIMT forms only) */
   int32_t max_slice_batch; /* slices per device pass; 0 = as many as fit in free HBM */

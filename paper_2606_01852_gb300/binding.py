@@ -26,6 +26,7 @@ PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x3m": 3}
 # forms named with the 3M complex product (three real products per complex MAC)
 THREE_M = {"bf16x3m"}
 TN_PLAN_HOST_ONLY = 1
+TN_PLAN_SINGLE_SM_TILES = 2
 TN_CLASS_SIMT, TN_CLASS_STREAM, TN_CLASS_TC, TN_CLASS_SPLITK, TN_CLASS_PERM = range(5)
 N_CLASSES = 5
 CLASS_NAMES = ["contract_simt", "contract_stream", "contract_tc", "contract_splitk", "stage_leaves"]
@@ -203,7 +204,7 @@ SEMIRINGS = {"standard": 0, "maxplus": 1}
 
 
 def make_policy(prec=TN_C64_FP32_SIMT, exp_scaling=False, max_slice_batch=0, host_only=False, semiring="standard",
-                complex_mult=4):
+                complex_mult=4, single_sm_tiles=False):
     """prec: a tn_precision or a form name ("bf16x3m" = BF16X3 with the 3M product)."""
     if isinstance(prec, str):
         if prec in THREE_M:
@@ -215,7 +216,7 @@ def make_policy(prec=TN_C64_FP32_SIMT, exp_scaling=False, max_slice_batch=0, hos
     p.complex_mult = int(complex_mult)
     p.exp_scaling = 1 if exp_scaling else 0
     p.max_slice_batch = int(max_slice_batch)
-    p.flags = TN_PLAN_HOST_ONLY if host_only else 0
+    p.flags = (TN_PLAN_HOST_ONLY if host_only else 0) | (TN_PLAN_SINGLE_SM_TILES if single_sm_tiles else 0)
     return p
 
 
@@ -245,13 +246,14 @@ class Plan:
     `path` is a list of SSA pairs or an object with .pairs."""
 
     def __init__(self, net, path, sliced=(), prec=TN_C64_FP32_SIMT, exp_scaling=False,
-                 max_slice_batch=0, host_only=False, semiring="standard", complex_mult=4):
+                 max_slice_batch=0, host_only=False, semiring="standard", complex_mult=4, single_sm_tiles=False):
         pairs = path.pairs if hasattr(path, "pairs") else path
         self._arr = _NetArrays([tuple(m) for m in net.modes], dict(net.extent), tuple(net.open_modes),
                                pairs)
         sl = list(sliced)
         self._sl = (C.c_int32 * max(1, len(sl)))(*sl)
-        self.policy = make_policy(prec, exp_scaling, max_slice_batch, host_only, semiring, complex_mult)
+        self.policy = make_policy(prec, exp_scaling, max_slice_batch, host_only, semiring, complex_mult,
+                                  single_sm_tiles)
         self.is_complex = self.policy.prec <= TN_C64_BF16X3
         self.n_leaves = len(net.modes)
         self.n_open = len(net.open_modes)

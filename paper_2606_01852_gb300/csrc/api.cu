@@ -186,7 +186,8 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
       if (sr.cls == TN_CLASS_TC) {
         const int32_t form = (P.policy.prec == TN_C64_BF16X3 && P.policy.complex_mult == 3) ? kPrecBF16x3M
                                                                                               : P.policy.prec;
-        TN_CUDA_TRY(launch_contract_tc(a, nbs, form, cplx, errw, st));
+        TN_CUDA_TRY(launch_contract_tc(a, nbs, form, cplx, errw, st,
+                                       (P.policy.flags & TN_PLAN_SINGLE_SM_TILES) == 0));
       } else if (sr.cls == TN_CLASS_STREAM) {
         launch_contract_stream(a, nbs, cplx, P.num_sms, errw, st);
       } else if (sr.cls == TN_CLASS_SPLITK) {

@@ -1042,6 +1042,324 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------------
+// BF16x3 4M on paired SMs (tcgen05 cta_group::2). A cluster of two CTAs computes one
+// 256 x 128 output tile: CTA r (rank in the pair) loads A rows m0 + 128 r .. + 127 and B
+// rows n0 + 64 r .. + 63 (all four split planes, 32 deep per k-block) into its own shared
+// memory by TMA, and CTA 0 issues M = 256, N = 128 MMAs that read A and B from both. Per
+// SM and 16-deep atom the MMAs read 72 KiB (4 KiB of A and 2 KiB of B per MMA) and TMA
+// writes 24 KiB, against 84 and 32 KiB on one SM: shared-memory bandwidth, which bounds the
+// single-SM kernel, drops below the tensor pipe's need. The accumulation is that of
+// contract_tcb_kernel term for term (hi.hi chunk accumulator folded into round-to-nearest
+// registers every 256 terms, the cross terms over all of k), with the four real products of
+// each complex product as separate N = 128 MMAs in the same order per accumulator, so each
+// output row gets the same bits as there. Each CTA's tensor memory holds its 128 rows.
+// Protocol: CTA 1's loads complete on its own barriers; one of its threads forwards each
+// completed stage to CTA 0 (remote mbarrier arrive); CTA 0's commits arrive on both CTAs'
+// barriers (multicast); the fold warps of both CTAs release the accumulators to CTA 0.
+// Every wait is bounded; after an expired wait the CTA records a code (51-59), stops
+// issuing and reaches the common teardown (cluster barriers, the pair's collective TMEM
+// release), which every thread of both CTAs always executes. A pair started after an
+// error skips its work (the leader's reading of the error word is shared with its peer).
+struct CB2 {
+  static constexpr int BK = 32, ROWB = 64, CK = 8;
+  static constexpr int PLANE_A = 128 * ROWB;               // 8 KiB: one plane of this CTA's A rows
+  static constexpr int PLANE_B = 64 * ROWB;                // 4 KiB: one plane of this CTA's B rows
+  static constexpr int OFF_B = 4 * PLANE_A;
+  static constexpr int STAGE = 4 * PLANE_A + 4 * PLANE_B;  // 48 KiB
+  static constexpr int STAGES = 4;
+  static constexpr int THREADS = 320;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 1024;
+  static constexpr uint32_t COLS = 512;                    // hi: re @0, im @128; lo: re @256, im @384
+  static constexpr int GROUP = 8;                          // raster: pair tiles grouped along M
+};
+
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// arrive on `bar` of both CTAs of the pair when the MMAs issued so far complete
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          su32(bar)),
+      "h"(static_cast<uint16_t>(3))
+      : "memory");
+}
+// arrive on the barrier at the same offset in CTA 0 of the cluster
+__device__ __forceinline__ void mbar_arrive_leader(uint64_t* bar) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(su32(bar)), "r"(0));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_leader_u32(const uint32_t* p) {
+  uint32_t remote, v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(su32(p)), "r"(0));
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(remote) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
+    contract_tcb2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                         StepArgs a, int* err) {
+  constexpr int STAGES = CB2::STAGES, BK = CB2::BK, ROWB = CB2::ROWB, CK = CB2::CK;
+  constexpr int PA = CB2::PLANE_A, PB = CB2::PLANE_B, STAGE = CB2::STAGE;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint64_t* full = bars;                  // [STAGES] this CTA's loads landed
+  uint64_t* ready = bars + STAGES;        // [STAGES] (CTA 0) CTA 1's loads landed
+  uint64_t* empty = bars + 2 * STAGES;    // [STAGES] the stage's MMAs completed
+  uint64_t* acc_full = bars + 3 * STAGES;
+  uint64_t* acc_empty = acc_full + 1;     // (CTA 0) both CTAs' fold warps read the chunk
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  uint32_t* skip_slot = tmem_slot + 1;
+
+  uint32_t rank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles_m = (a.m + 2 * BM - 1) / (2 * BM), tiles_n = (a.n + BN - 1) / BN;
+  const int64_t t = blockIdx.x >> 1;
+  const int64_t per_group = CB2::GROUP * tiles_n;
+  const int64_t first_m = (t / per_group) * CB2::GROUP;
+  const int64_t gm = tiles_m - first_m < CB2::GROUP ? tiles_m - first_m : CB2::GROUP;
+  const int64_t tm = first_m + (t % per_group) % gm, tn = (t % per_group) / gm;
+  const int m0 = static_cast<int>(tm * 2 * BM), n0 = static_cast<int>(tn * BN);
+  const int b = blockIdx.y;
+  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);
+  const int n_chunks = (num_kb + CK - 1) / CK;
+  const int pa = a.a_bstride ? 4 * b : 0, pb = a.b_bstride ? 4 * b : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&ready[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 16);
+    *skip_slot = *reinterpret_cast<volatile int*>(err) != 0 ? 1u : 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(CB2::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  cluster_sync_all();  // both CTAs' barriers initialised and the pair's TMEM allocated
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const bool skip = ld_leader_u32(skip_slot) != 0;  // one decision for the pair
+
+  if (skip) {
+    // an earlier CTA gave up a wait: no work, only the common teardown
+  } else if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < num_kb; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) {
+          atomicExch(err, 51);
+          break;
+        }
+        mbar_expect_tx(&full[s], STAGE);
+        uint8_t* st = smem + s * STAGE;
+        const int k0 = kb * BK;
+        tma_load_3d(st, &tmA, &full[s], k0, m0 + 128 * static_cast<int>(rank), pa);
+        tma_load_3d(st + CB2::OFF_B, &tmB, &full[s], k0, n0 + 64 * static_cast<int>(rank), pb);
+        issued = kb + 1;
+      }
+      // before exit: every load landed, and every commit of CTA 0 for them arrived here
+      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb) {
+        if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) atomicExch(err, 52);
+        if (!mbar_wait(&empty[kb % STAGES], (kb / STAGES) & 1)) atomicExch(err, 53);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 1) {
+      // forward each landed stage to CTA 0, in order
+      for (int kb = 0; kb < num_kb; ++kb) {
+        if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) {
+          atomicExch(err, 54);
+          break;
+        }
+        mbar_arrive_leader(&ready[kb % STAGES]);
+      }
+    } else if (lane == 0) {
+      constexpr uint32_t id = idesc_bf16(2 * BM, BN);
+      const uint32_t d_hi = tmem, d_lo = tmem + 256;
+      // the cross terms (into D_lo) of one k-block: 8 MMAs per 16-deep atom
+      auto cross = [&](uint32_t sa, uint32_t sb, bool first_kb) {
+#pragma unroll
+        for (int j = 0; j < BK / 16; ++j) {
+          const uint32_t o = j * 32;
+          const uint64_t ar_h = smem_desc<ROWB>(sa + o), ai_h = smem_desc<ROWB>(sa + PA + o);
+          const uint64_t ar_l = smem_desc<ROWB>(sa + 2 * PA + o), ai_l = smem_desc<ROWB>(sa + 3 * PA + o);
+          const uint64_t br_h = smem_desc<ROWB>(sb + o), bi_h = smem_desc<ROWB>(sb + PB + o);
+          const uint64_t br_l = smem_desc<ROWB>(sb + 2 * PB + o), bi_l = smem_desc<ROWB>(sb + 3 * PB + o);
+          const uint32_t first = (!first_kb || j > 0) ? 1u : 0u;
+          mma_bf16_pair(d_lo, ar_l, br_h, id, first);           // Re += A_re_lo . B_re_h
+          mma_bf16_pair(d_lo, ai_l, bi_h, id | kNegateA, 1u);   // Re -= A_im_lo . B_im_h
+          mma_bf16_pair(d_lo + 128, ar_l, bi_h, id, first);     // Im += A_re_lo . B_im_h
+          mma_bf16_pair(d_lo + 128, ai_l, br_h, id, 1u);        // Im += A_im_lo . B_re_h
+          mma_bf16_pair(d_lo, ar_h, br_l, id, 1u);
+          mma_bf16_pair(d_lo, ai_h, bi_l, id | kNegateA, 1u);
+          mma_bf16_pair(d_lo + 128, ar_h, bi_l, id, 1u);
+          mma_bf16_pair(d_lo + 128, ai_h, br_l, id, 1u);
+        }
+      };
+      // hi . hi of one k-block into the chunk accumulator D_hi: 4 MMAs per atom
+      auto hihi = [&](uint32_t sa, uint32_t sb, bool first_kb) {
+#pragma unroll
+        for (int j = 0; j < BK / 16; ++j) {
+          const uint32_t o = j * 32;
+          const uint64_t ar_h = smem_desc<ROWB>(sa + o), ai_h = smem_desc<ROWB>(sa + PA + o);
+          const uint64_t br_h = smem_desc<ROWB>(sb + o), bi_h = smem_desc<ROWB>(sb + PB + o);
+          const uint32_t acc = (!first_kb || j > 0) ? 1u : 0u;
+          mma_bf16_pair(d_hi, ar_h, br_h, id, acc);
+          mma_bf16_pair(d_hi, ai_h, bi_h, id | kNegateA, 1u);
+          mma_bf16_pair(d_hi + 128, ar_h, bi_h, id, acc);
+          mma_bf16_pair(d_hi + 128, ai_h, br_h, id, 1u);
+        }
+      };
+      auto stage_a = [&](int kb) { return su32(smem + (kb % STAGES) * STAGE); };
+      auto landed = [&](int kb) {
+        return mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1) && mbar_wait(&ready[kb % STAGES], (kb / STAGES) & 1);
+      };
+      // Per chunk: the cross terms of its first LEAD k-blocks are issued before the wait for
+      // the previous chunk's fold (which both CTAs' warps must report, one of them across
+      // the pair), so the fold and its remote release overlap tensor work; then the hi.hi
+      // MMAs of those k-blocks, and the rest of the chunk k-block by k-block. Each
+      // accumulator receives its MMAs in k order either way.
+      constexpr int LEAD = 2;
+      bool ok = true;
+      for (int c = 0; c < n_chunks && ok; ++c) {
+        const int kb0 = c * CK, kb_end = min(num_kb, (c + 1) * CK);
+        const int lead_end = min(kb_end, kb0 + LEAD);
+        for (int kb = kb0; kb < lead_end && ok; ++kb) {
+          if (!landed(kb)) {
+            atomicExch(err, 55);
+            ok = false;
+            break;
+          }
+          fence_after();
+          cross(stage_a(kb), stage_a(kb) + CB2::OFF_B, kb == 0);
+        }
+        if (ok && !mbar_wait(acc_empty, (c & 1) ^ 1)) {  // the chunk accumulator is free
+          atomicExch(err, 56);
+          ok = false;
+        }
+        if (!ok) {
+          mma_commit_pair(acc_full);  // let the fold see the issued MMAs retire
+          break;
+        }
+        fence_after();
+        for (int kb = kb0; kb < lead_end; ++kb) {
+          hihi(stage_a(kb), stage_a(kb) + CB2::OFF_B, kb == kb0);
+          mma_commit_pair(&empty[kb % STAGES]);
+        }
+        for (int kb = lead_end; kb < kb_end; ++kb) {
+          if (!landed(kb)) {
+            atomicExch(err, 55);
+            ok = false;
+            break;
+          }
+          fence_after();
+          cross(stage_a(kb), stage_a(kb) + CB2::OFF_B, false);
+          hihi(stage_a(kb), stage_a(kb) + CB2::OFF_B, false);
+          mma_commit_pair(&empty[kb % STAGES]);
+        }
+        mma_commit_pair(acc_full);  // also on error, so the fold sees issued MMAs retire
+      }
+    }
+  } else {
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    float run_re[64], run_im[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) run_re[i] = run_im[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < n_chunks && ok; ++c) {
+      if (!mbar_wait(acc_full, c & 1)) {
+        atomicExch(err, 57);
+        ok = false;
+        break;
+      }
+      fence_after();
+      float v[32];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const uint32_t col = lane_base + half * 64 + p * 32;
+        tmem_ld32(tmem + col, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+        tmem_ld32(tmem + 128 + col, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+        if (c == n_chunks - 1) {
+          tmem_ld32(tmem + 256 + col, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+          tmem_ld32(tmem + 384 + col, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (rank == 0) mbar_arrive(acc_empty);
+        else mbar_arrive_leader(acc_empty);
+      }
+    }
+    // epilogue: thread = TMEM lane = row m0 + 128 rank + 32 q + lane; this warp's 64 columns
+    const int row = q * 32 + lane;
+    const int64_t m = static_cast<int64_t>(m0) + 128 * static_cast<int64_t>(rank) + row;
+    const bool row_ok = ok && m < a.m;
+    const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
+    float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
+    const int split = a.c_split;
+    // the stage buffers are free: the last fold waited for the final MMA, which read every
+    // staged tile of both CTAs (the producer's tail waits keep its copies from landing later)
+    float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 65;
+    if (ok) {
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        tr[lane * 65 + j] = run_re[j];
+        tr[32 * 65 + lane * 65 + j] = run_im[j];
+      }
+    }
+    __syncwarp();
+    if (ok) {
+      for (int cb = 0; cb < 2; ++cb) {
+        const int64_t n = static_cast<int64_t>(n0) + half * 64 + cb * 32 + lane;
+        const bool col_ok = n < a.n;
+        store_block(C, a.c_plane, split, tr + cb * 32, 65, 32 * 65, ro, col_ok ? map_offset(a.cols, n) : 0, row_ok,
+                    col_ok, lane);
+      }
+    }
+  }
+  // common teardown: every thread of both CTAs
+  fence_before();
+  __syncthreads();
+  cluster_sync_all();  // both CTAs done with TMEM and with each other's barriers
+  fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CB2::COLS));
+  __syncthreads();
+  cluster_sync_all();
+}
+
+// ---------------------------------------------------------------------------------
 // BF16x3 form with the 3M complex product (Gauss): with s = a_re + a_im and t = b_re + b_im,
 //   P1 = a_re.b_re,  P2 = a_im.b_im,  P3 = s.t;   Re = P1 - P2,  Im = P3 - P1 - P2,
 // three real products per complex MAC instead of four, each as hi.hi + hi.lo + lo.hi of
@@ -1587,7 +1905,7 @@ cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
   return cudaGetLastError();
 }
 
-cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
+cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st, bool pairs) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e =
@@ -1595,12 +1913,24 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(contract_tcb_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                CBP::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(contract_tcb2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB2::SMEM);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   CUtensorMap ta, tb;
   const int64_t ca = a.a_bstride ? static_cast<int64_t>(nb) : 1;
   const int64_t cb = a.b_bstride ? static_cast<int64_t>(nb) : 1;
+  if (pairs && a.k > CBP::MAX_K && a.m >= 2 * BM) {
+    // paired SMs: this CTA's 128 rows of A and 64 rows of B per box
+    if (!make_map_split(&ta, a.A, a.m, a.k, ca, a.a_plane, BM) ||
+        !make_map_split(&tb, a.B, a.n, a.k, cb, a.b_plane, BN / 2))
+      return cudaErrorInvalidValue;
+    const int64_t pair_tiles = ((a.m + 2 * BM - 1) / (2 * BM)) * ((a.n + BN - 1) / BN);
+    dim3 grid(static_cast<unsigned>(2 * pair_tiles), static_cast<unsigned>(nb));
+    contract_tcb2_kernel<<<grid, CB2::THREADS, CB2::SMEM, st>>>(ta, tb, a, err);
+    return cudaGetLastError();
+  }
   if (!make_map_split(&ta, a.A, a.m, a.k, ca, a.a_plane, BM) || !make_map_split(&tb, a.B, a.n, a.k, cb, a.b_plane, BN))
     return cudaErrorInvalidValue;
   const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
@@ -1640,12 +1970,12 @@ bool tc_step_ok(int64_t m, int64_t n, int64_t k, int32_t prec) {
 }
 
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool pairs) {
   if (!cplx || a.recs) return cudaErrorNotSupported;
   if (prec == kPrecBF16x3M) return launch_tcb3m(a, nb, err, st);
   if (prec == TN_C64_TF32) return launch_split<1>(a, nb, err, st);
   if (prec == TN_C64_3XTF32) return launch_tc3(a, nb, err, st);
-  if (prec == TN_C64_BF16X3) return launch_tcb(a, nb, err, st);
+  if (prec == TN_C64_BF16X3) return launch_tcb(a, nb, err, st, pairs);
   return cudaErrorNotSupported;
 }
 

@@ -110,7 +110,9 @@ cudaError_t launch_bounded_wait_selftest(int arrive, uint64_t limit_ns, int* err
 // A and B of a BF16X3 step are in the split-BF16 form; prec = kPrecBF16x3M selects the 3M
 // kernel (operands in the 3M split form).
 constexpr int32_t kPrecBF16x3M = 103;
+// pairs: BF16x3 4M steps with m >= 256 and k above the persistent kernel's range run on
+// pairs of SMs (contract_tcb2_kernel)
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
-                               cudaStream_t st);
+                               cudaStream_t st, bool pairs = true);
 
 }  // namespace tn

@@ -110,6 +110,37 @@ def test_single_gemm_step(tn, prec, tol, case):
     assert rel_err(got, oracle.contract(net, path)) < tol
 
 
+PAIR_CASES = [
+    # (m dims, n dims, k dims, output order, sliced extent): m >= 256 and k > 256
+    ((2, 256), (128,), (512,), [("m", 0), ("m", 1), ("n", 0)], None),            # two fold chunks
+    ((384,), (136,), (776,), [("m", 0), ("n", 0)], None),                        # 1.5 pair tiles, n and k tails
+    ((3, 100), (2, 64), (24, 16), [("m", 0), ("n", 0), ("m", 1), ("n", 1)], None),  # m = 300, interleaved
+    ((512,), (256,), (264,), [("m", 0), ("n", 0)], 3),                           # batched, k just above 256
+]
+
+
+@pytest.mark.parametrize("case", range(len(PAIR_CASES)))
+def test_paired_sm_tiles_same_bits(tn, case):
+    """BF16x3 4M steps with m >= 256 and k > 256 run 256 x 128 output tiles on pairs of SMs
+    (tcgen05 cta_group::2, one cluster of two CTAs per tile). Every output has the same bits
+    as from the single-SM kernel (TN_PLAN_SINGLE_SM_TILES: the same products accumulated in
+    the same order), and matches the oracle within the BF16x3 bound."""
+    dm, dn, dk, order, sl = PAIR_CASES[case]
+    net, path, sliced = gemm_network(dm, dn, dk, order, seed=30 + case, sliced_dim=sl)
+    pair = tn.Plan(net, path, sliced, prec="bf16x3")
+    one = tn.Plan(net, path, sliced, prec="bf16x3", single_sm_tiles=True)
+    st = pair.step(0)
+    assert st["cls"] == tn.TN_CLASS_TC and st["m"] >= 256 and st["k"] > 256
+    got, _ = run(tn, pair, net)
+    ref, _ = run(tn, one, net)
+    g, r = np.ascontiguousarray(got), np.ascontiguousarray(ref)
+    assert np.array_equal(g.view(np.uint64), r.view(np.uint64))
+    want = oracle.contract(net, path, sliced) if sliced else oracle.contract(net, path)
+    assert rel_err(got, want) < 5e-5
+    pair.destroy()
+    one.destroy()
+
+
 @pytest.mark.parametrize("prec,tol", [("tf32", 5e-3), ("3xtf32", 1e-5), ("bf16x3", 5e-5), ("bf16x3m", 1e-4)])
 def test_batched_both_operands(tn, prec, tol):
     """A sliced label on both operands: the batch runs as TMA planes of both maps."""
