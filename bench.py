@@ -68,11 +68,12 @@ THREE_M = {"bf16x3m"}
 # arithmetic of each form (complex64 storage; products as named, FP32 accumulation)
 DTYPE_NAME = {"fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16x3": "bf16x3", "bf16x3m": "bf16x3 (3M)"}
 # DRAM bytes (read + write) of the dominant tensor-core launch (the step below), from the
-# single-kernel capture in profiles/contract_tcb_bf16x3_tcgemm_m14n14k13.md (m = n = 2^14,
-# k = 2^13, one slice: 61.7 GB read, 2.24 GB written) scaled to the launch: panel reads grow
-# with k (x4), output writes do not, 8 slices per launch. Valid for the kernel build it was
-# taken on: drop an entry when that kernel changes.
-NCU_TRAFFIC_DOMINANT_LAUNCH = {("rc40c14", "bf16x3"): {"step": 310, "bytes": 8 * (4 * 61.7e9 + 2.24e9)}}
+# single-kernel capture of the paired-SM kernel in
+# profiles/contract_tcb2_bf16x3_tcgemm_m14n14k13.md (m = n = 2^14, k = 2^13, one slice:
+# 26.9 GB read, 2.24 GB written) scaled to the launch: panel reads grow with k (x4), output
+# writes do not, 8 slices per launch. Valid for the kernel build it was taken on: drop an
+# entry when that kernel changes.
+NCU_TRAFFIC_DOMINANT_LAUNCH = {("rc40c14", "bf16x3"): {"step": 310, "bytes": 8 * (4 * 26.9e9 + 2.24e9)}}
 # Full values of the CPU oracle stored by the scripts in tests/golden/ (they call only the
 # oracle): the 40-qubit sum over all slices, and the full values of the smaller workloads.
 GOLDEN = os.path.join(ROOT, "tests", "golden")
