@@ -253,51 +253,80 @@ __device__ __forceinline__ void store_sorted(float* C, int64_t plane, int split,
 // the following weights continue the sequence (interleaved row/column layouts included).
 // Otherwise (ragged block, other extents) it falls back to one row per store. ro / co:
 // this lane's row / column offset; row_ok / col_ok: in range.
-__device__ __forceinline__ void store_block(float* C, int64_t plane, int split, const float* t, int pitch,
-                                            int cs, int64_t ro, int64_t co, bool row_ok, bool col_ok, int lane) {
-  const int64_t ro0 = __shfl_sync(0xffffffffu, ro, 0), co0 = __shfl_sync(0xffffffffu, co, 0);
-  // log2 of each bit's weight (bits 0-4: row, 5-9: column); -1 if not a power of two
-  int e[10];
-  bool lin = row_ok && col_ok;
+// The address order of a 32 x 32 block: the ten bit weights (log2; bits 0-4 of the row,
+// 5-9 of the column index) sorted ascending, with the bit each comes from; ok when the
+// block's offsets are linear in those bits with power-of-two weights. ro_rel / co_rel: this
+// lane's row / column offset relative to the block's first row / column.
+struct BlockOrder {
+  int e[10], src[10];
+  bool ok;
+};
+__device__ __forceinline__ BlockOrder block_order(int64_t ro_rel, int64_t co_rel, bool in_range, int lane) {
+  BlockOrder o;
+  bool lin = in_range;
   int64_t pr = 0, pc = 0;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const int64_t wr = __shfl_sync(0xffffffffu, ro, 1 << i) - ro0;
-    const int64_t wc = __shfl_sync(0xffffffffu, co, 1 << i) - co0;
-    e[i] = (wr > 0 && (wr & (wr - 1)) == 0) ? 63 - __clzll(wr) : -1;
-    e[5 + i] = (wc > 0 && (wc & (wc - 1)) == 0) ? 63 - __clzll(wc) : -1;
-    lin = lin && e[i] >= 0 && e[5 + i] >= 0;
+    const int64_t wr = __shfl_sync(0xffffffffu, ro_rel, 1 << i);
+    const int64_t wc = __shfl_sync(0xffffffffu, co_rel, 1 << i);
+    o.e[i] = (wr > 0 && (wr & (wr - 1)) == 0) ? 63 - __clzll(wr) : -1;
+    o.e[5 + i] = (wc > 0 && (wc & (wc - 1)) == 0) ? 63 - __clzll(wc) : -1;
+    lin = lin && o.e[i] >= 0 && o.e[5 + i] >= 0;
     pr += ((lane >> i) & 1) * wr;
     pc += ((lane >> i) & 1) * wc;
   }
-  lin = lin && pr == ro - ro0 && pc == co - co0;
-  if (__all_sync(0xffffffffu, lin)) {
-    // sort the ten bit weights ascending, carrying which bit of r (0-4) or c (5-9) each is
-    int src[10];
+  lin = lin && pr == ro_rel && pc == co_rel;
+  o.ok = __all_sync(0xffffffffu, lin);
 #pragma unroll
-    for (int i = 0; i < 10; ++i) src[i] = i;
+  for (int i = 0; i < 10; ++i) o.src[i] = i;
+  if (o.ok) {
 #pragma unroll
     for (int i = 1; i < 10; ++i)
 #pragma unroll
       for (int j = i; j > 0; --j)
-        if (e[j] < e[j - 1]) {
-          const int te = e[j];
-          e[j] = e[j - 1];
-          e[j - 1] = te;
-          const int ts = src[j];
-          src[j] = src[j - 1];
-          src[j - 1] = ts;
+        if (o.e[j] < o.e[j - 1]) {
+          const int te = o.e[j];
+          o.e[j] = o.e[j - 1];
+          o.e[j - 1] = te;
+          const int ts = o.src[j];
+          o.src[j] = o.src[j - 1];
+          o.src[j - 1] = ts;
         }
-    // elements per lane: as many of the smallest weights as are 1, 2, 4, ... (16 bytes at
-    // most), with the block base and the plane size aligned to that many elements
-    const int64_t base = ro0 + co0;
-    int vb = 0;
-    while (vb < (split ? 3 : 2) && e[vb] == vb) ++vb;
-    while (vb > 0 && ((base | plane) & ((int64_t(1) << vb) - 1)) != 0) --vb;
-    if (vb == 3) store_sorted<3>(C, plane, split, t, pitch, cs, base, e, src, lane);
-    else if (vb == 2) store_sorted<2>(C, plane, split, t, pitch, cs, base, e, src, lane);
-    else if (vb == 1) store_sorted<1>(C, plane, split, t, pitch, cs, base, e, src, lane);
-    else store_sorted<0>(C, plane, split, t, pitch, cs, base, e, src, lane);
+  }
+  return o;
+}
+
+// The address-ordered stores of a block whose order is `o` (o.ok) and whose first element
+// is at `base`: each lane writes V consecutive addresses with one vector store per plane
+// (V as far as the smallest weights are 1, 2, 4, ... and base and the plane size are
+// V-aligned; 16 bytes at most).
+__device__ __forceinline__ void store_ordered(float* C, int64_t plane, int split, const float* t, int pitch, int cs,
+                                              int64_t base, const BlockOrder& o, int lane) {
+  int vb = 0;
+  while (vb < (split ? 3 : 2) && o.e[vb] == vb) ++vb;
+  while (vb > 0 && ((base | plane) & ((int64_t(1) << vb) - 1)) != 0) --vb;
+  if (vb == 3) store_sorted<3>(C, plane, split, t, pitch, cs, base, o.e, o.src, lane);
+  else if (vb == 2) store_sorted<2>(C, plane, split, t, pitch, cs, base, o.e, o.src, lane);
+  else if (vb == 1) store_sorted<1>(C, plane, split, t, pitch, cs, base, o.e, o.src, lane);
+  else store_sorted<0>(C, plane, split, t, pitch, cs, base, o.e, o.src, lane);
+}
+
+// Store one 32 x 32 block of a result tile from shared memory (t[r * pitch + c] = Re,
+// t[cs + r * pitch + c] = Im; row r is lane r's row, column c lane c's column) in the
+// order of its addresses. When the block's offsets are linear in the bits of (r, c) with
+// power-of-two weights -- every row and column extent of the offset maps a power of two,
+// as in every network with extent-2 modes -- off(r, c) = off(0, 0) + sum of per-bit
+// weights, and the ten weights sorted ascending give the block's elements in address
+// order (block_order); a warp store then covers 32 V consecutive elements when the
+// following weights continue the sequence (interleaved row/column layouts included).
+// Otherwise (ragged block, other extents) it falls back to one row per store. ro / co:
+// this lane's row / column offset; row_ok / col_ok: in range.
+__device__ __forceinline__ void store_block(float* C, int64_t plane, int split, const float* t, int pitch,
+                                            int cs, int64_t ro, int64_t co, bool row_ok, bool col_ok, int lane) {
+  const int64_t ro0 = __shfl_sync(0xffffffffu, ro, 0), co0 = __shfl_sync(0xffffffffu, co, 0);
+  const BlockOrder o = block_order(ro - ro0, co - co0, row_ok && col_ok, lane);
+  if (o.ok) {
+    store_ordered(C, plane, split, t, pitch, cs, ro0 + co0, o, lane);
     return;
   }
   for (int r = 0; r < 32; ++r) {
@@ -1724,6 +1753,14 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
     const uint32_t lane_base = static_cast<uint32_t>(q4 * 32) << 16;
     float* tr = epi + (warp - 2) * 2 * 32 * 33;  // this warp's Re and Im transpose blocks
     const int split = a.c_split;
+    // When every extent of the offset maps is a power of two, every full 32 x 32 block of
+    // the step has the address order of the first one: it is computed once here, and a
+    // full block only adds its base offset (the other blocks take store_block's checks).
+    bool pow2 = a.m >= 32 && a.n >= 32;
+    for (int d = 0; d < a.rows.n; ++d) pow2 = pow2 && (a.rows.ext[d] & (a.rows.ext[d] - 1u)) == 0u;
+    for (int d = 0; d < a.cols.n; ++d) pow2 = pow2 && (a.cols.ext[d] & (a.cols.ext[d] - 1u)) == 0u;
+    const BlockOrder ord = block_order(pow2 ? map_offset(a.rows, lane) : 0, pow2 ? map_offset(a.cols, lane) : 0,
+                                       pow2, lane);
     int64_t q = 0;  // tiles folded
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++q) {
       const TileCoord tc = tile_of(w, tiles_m, tiles_n);
@@ -1767,7 +1804,13 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
         __syncwarp();
         const int64_t n = static_cast<int64_t>(tc.n0) + half * 64 + cb * 32 + lane;
         const bool col_ok = n < a.n;
-        store_block(C, a.c_plane, split, tr, 33, 32 * 33, ro, col_ok ? map_offset(a.cols, n) : 0, row_ok, col_ok, lane);
+        const int64_t co = col_ok ? map_offset(a.cols, n) : 0;
+        if (ord.ok && __all_sync(0xffffffffu, row_ok && col_ok)) {
+          const int64_t base = __shfl_sync(0xffffffffu, ro, 0) + __shfl_sync(0xffffffffu, co, 0);
+          store_ordered(C, a.c_plane, split, tr, 33, 32 * 33, base, ord, lane);
+        } else {
+          store_block(C, a.c_plane, split, tr, 33, 32 * 33, ro, co, row_ok, col_ok, lane);
+        }
         __syncwarp();
       }
     }
@@ -1845,13 +1888,10 @@ bool make_map_split3m(CUtensorMap* map, const float* base, int64_t rows, int64_t
 }
 
 cudaError_t launch_tcb3m(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(contract_tcb3m_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB3::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // the shared-memory opt-in, once per process (thread-safe static initialisation)
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(contract_tcb3m_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB3::SMEM);
+  if (configured != cudaSuccess) return configured;
   CUtensorMap ta, tb;
   const int64_t ca = a.a_bstride ? static_cast<int64_t>(nb) : 1;
   const int64_t cb = a.b_bstride ? static_cast<int64_t>(nb) : 1;
@@ -1866,13 +1906,9 @@ cudaError_t launch_tcb3m(const StepArgs& a, int32_t nb, int* err, cudaStream_t s
 
 template <int SPLIT>
 cudaError_t launch_split(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg<SPLIT>::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(contract_tc_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<SPLIT>::SMEM);
+  if (configured != cudaSuccess) return configured;
   CUtensorMap ta, tb;
   const int64_t pa = a.a_bstride ? 2 * static_cast<int64_t>(nb) : 2;
   const int64_t pb = a.b_bstride ? 2 * static_cast<int64_t>(nb) : 2;
@@ -1886,13 +1922,9 @@ cudaError_t launch_split(const StepArgs& a, int32_t nb, int* err, cudaStream_t s
 }
 
 cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(contract_tc3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C3::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(contract_tc3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C3::SMEM);
+  if (configured != cudaSuccess) return configured;
   CUtensorMap ta, tb;
   const int64_t pa = a.a_bstride ? 2 * static_cast<int64_t>(nb) : 2;
   const int64_t pb = a.b_bstride ? 2 * static_cast<int64_t>(nb) : 2;
@@ -1906,18 +1938,16 @@ cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
 }
 
 cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st, bool pairs) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(contract_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB::SMEM);
+  static const cudaError_t configured = [] {
+    cudaError_t e = cudaFuncSetAttribute(contract_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB::SMEM);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(contract_tcb_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                CBP::SMEM);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(contract_tcb2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB2::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+    return e;
+  }();
+  if (configured != cudaSuccess) return configured;
   CUtensorMap ta, tb;
   const int64_t ca = a.a_bstride ? static_cast<int64_t>(nb) : 1;
   const int64_t cb = a.b_bstride ? static_cast<int64_t>(nb) : 1;

@@ -782,14 +782,14 @@ __global__ void __launch_bounds__(256) contract_stream_tma_kernel(StepArgs a, in
 template <bool CPLX, int NMAX, int K>
 void launch_stream_tma(const StepArgs& a, int32_t nb, int num_sms, int* err, cudaStream_t st) {
   constexpr int smem = StreamTma<K, CPLX>::SMEM;
-  static int per_sm = 0;  // resident CTAs per SM, looked up once per form
-  if (per_sm == 0) {
+  // resident CTAs per SM, looked up once per form (thread-safe static initialisation)
+  static const int per_sm = [] {
     cudaFuncSetAttribute(contract_stream_tma_kernel<CPLX, NMAX, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, contract_stream_tma_kernel<CPLX, NMAX, K>, 256, smem);
-    per_sm = occ > 0 ? occ : 1;
-  }
+    return occ > 0 ? occ : 1;
+  }();
   const int64_t tiles = (a.m + 255) / 256;
   int64_t gx = (int64_t(num_sms) * per_sm + nb - 1) / nb;
   gx = std::max<int64_t>(1, std::min<int64_t>(gx, tiles));
