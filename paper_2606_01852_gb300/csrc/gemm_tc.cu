@@ -261,6 +261,7 @@ struct BlockOrder {
   int e[10], src[10];
   bool ok;
 };
+static_assert(sizeof(BlockOrder) <= 128, "a fold warp's block order slot");
 __device__ __forceinline__ BlockOrder block_order(int64_t ro_rel, int64_t co_rel, bool in_range, int lane) {
   BlockOrder o;
   bool lin = in_range;
@@ -1389,6 +1390,317 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------------
+// The paired-SM BF16x3 kernel in persistent form: each cluster of two CTAs walks the
+// (batch entry, 256 x 128 tile) items c, c + G, ... (G clusters, as many as are resident).
+// The k-block ring runs on across items, and after the last fold of an item the fold warps
+// release the accumulators before storing the item from registers (through their own
+// shared-memory blocks, not the ring), so the next item's MMAs overlap the epilogue and no
+// CTA is started or torn down per tile: what a one-tile-per-cluster launch pays per tile
+// (TMEM allocation, pipeline fill, epilogue) is paid once. The arithmetic, the roles and the
+// protocol are those of contract_tcb2_kernel; barrier phases count k-blocks and chunks over
+// all items of the cluster. A new item's cross-term MMAs (which restart D_lo) wait for the
+// previous item's last fold.
+// Paired-SM steps with k up to this run the persistent kernel; deeper ones one cluster per
+// tile. Measured on the 14-cycle circuit: at k = 512 and 1024 the persistent form is 1.5x
+// and 1.15x faster (no per-tile start-up and epilogue), at k >= 16384 the per-tile form is
+// 4-8 % faster (four ring stages instead of three, the per-tile cost being small there).
+constexpr int64_t kPairsPersistentMaxK = 4096;
+struct CB2P {
+  static constexpr int STAGES = 3;
+  // per fold warp: Re and Im of one 32 x 32 block, then the fold warps' block orders
+  static constexpr int EPI = 8 * 2 * 32 * 33 * 4 + 8 * 128;
+  static constexpr int SMEM = STAGES * CB2::STAGE + EPI + 1024 + 1024;
+};
+static_assert(CB2P::SMEM <= 232448, "shared memory per CTA");
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
+    contract_tcb2p_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                          StepArgs a, int32_t nb, int* err) {
+  constexpr int STAGES = CB2P::STAGES, BK = CB2::BK, ROWB = CB2::ROWB, CK = CB2::CK;
+  constexpr int PA = CB2::PLANE_A, PB = CB2::PLANE_B, STAGE = CB2::STAGE;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* epi = reinterpret_cast<float*>(smem + STAGES * STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE + CB2P::EPI);
+  uint64_t* full = bars;                  // [STAGES] this CTA's loads landed
+  uint64_t* ready = bars + STAGES;        // [STAGES] (CTA 0) CTA 1's loads landed
+  uint64_t* empty = bars + 2 * STAGES;    // [STAGES] the stage's MMAs completed
+  uint64_t* acc_full = bars + 3 * STAGES;
+  uint64_t* acc_empty = acc_full + 1;     // (CTA 0) both CTAs' fold warps read the chunk
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  uint32_t* skip_slot = tmem_slot + 1;
+
+  uint32_t rank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles_m = (a.m + 2 * BM - 1) / (2 * BM), tiles_n = (a.n + BN - 1) / BN;
+  const int64_t tiles = tiles_m * tiles_n, total = tiles * nb;
+  const int64_t cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
+  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);
+  const int n_chunks = (num_kb + CK - 1) / CK;
+  // item w -> batch entry and the tile's first row and column (grouped raster per entry)
+  auto item = [&](int64_t w, int& b, int& m0, int& n0) {
+    const int64_t t = w % tiles;
+    const int64_t per_group = CB2::GROUP * tiles_n;
+    const int64_t first_m = (t / per_group) * CB2::GROUP;
+    const int64_t gm = tiles_m - first_m < CB2::GROUP ? tiles_m - first_m : CB2::GROUP;
+    const int64_t tm = first_m + (t % per_group) % gm, tn = (t % per_group) / gm;
+    b = static_cast<int>(w / tiles);
+    m0 = static_cast<int>(tm * 2 * BM);
+    n0 = static_cast<int>(tn * BN);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&ready[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 16);
+    *skip_slot = *reinterpret_cast<volatile int*>(err) != 0 ? 1u : 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(CB2::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const bool skip = ld_leader_u32(skip_slot) != 0;
+
+  if (skip) {
+    // an earlier CTA gave up a wait: no work, only the common teardown
+  } else if (warp == 0) {
+    if (lane == 0) {
+      int64_t g = 0;  // k-blocks issued by this CTA over all its items
+      bool ok = true;
+      for (int64_t w = cluster; w < total && ok; w += n_clusters) {
+        int b, m0, n0;
+        item(w, b, m0, n0);
+        const int pa = a.a_bstride ? 4 * b : 0, pb = a.b_bstride ? 4 * b : 0;
+        for (int kb = 0; kb < num_kb; ++kb, ++g) {
+          const int s = static_cast<int>(g % STAGES);
+          if (!mbar_wait(&empty[s], static_cast<uint32_t>((g / STAGES) & 1) ^ 1)) {
+            atomicExch(err, 51);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], STAGE);
+          uint8_t* st = smem + s * STAGE;
+          tma_load_3d(st, &tmA, &full[s], kb * BK, m0 + 128 * static_cast<int>(rank), pa);
+          tma_load_3d(st + CB2::OFF_B, &tmB, &full[s], kb * BK, n0 + 64 * static_cast<int>(rank), pb);
+        }
+      }
+      // before exit: every load landed, and every commit of CTA 0 for them arrived here
+      for (int64_t j = g > STAGES ? g - STAGES : 0; j < g; ++j) {
+        if (!mbar_wait(&full[j % STAGES], static_cast<uint32_t>((j / STAGES) & 1))) atomicExch(err, 52);
+        if (!mbar_wait(&empty[j % STAGES], static_cast<uint32_t>((j / STAGES) & 1))) atomicExch(err, 53);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 1) {
+      // forward each landed stage to CTA 0, in order
+      const int64_t mine = total > cluster ? (total - cluster + n_clusters - 1) / n_clusters : 0;
+      const int64_t blocks = mine * num_kb;
+      for (int64_t g = 0; g < blocks; ++g) {
+        if (!mbar_wait(&full[g % STAGES], static_cast<uint32_t>((g / STAGES) & 1))) {
+          atomicExch(err, 54);
+          break;
+        }
+        mbar_arrive_leader(&ready[g % STAGES]);
+      }
+    } else if (lane == 0) {
+      constexpr uint32_t id = idesc_bf16(2 * BM, BN);
+      const uint32_t d_hi = tmem, d_lo = tmem + 256;
+      auto cross = [&](uint32_t sa, uint32_t sb, bool first_kb) {
+#pragma unroll
+        for (int j = 0; j < BK / 16; ++j) {
+          const uint32_t o = j * 32;
+          const uint64_t ar_h = smem_desc<ROWB>(sa + o), ai_h = smem_desc<ROWB>(sa + PA + o);
+          const uint64_t ar_l = smem_desc<ROWB>(sa + 2 * PA + o), ai_l = smem_desc<ROWB>(sa + 3 * PA + o);
+          const uint64_t br_h = smem_desc<ROWB>(sb + o), bi_h = smem_desc<ROWB>(sb + PB + o);
+          const uint64_t br_l = smem_desc<ROWB>(sb + 2 * PB + o), bi_l = smem_desc<ROWB>(sb + 3 * PB + o);
+          const uint32_t first = (!first_kb || j > 0) ? 1u : 0u;
+          mma_bf16_pair(d_lo, ar_l, br_h, id, first);
+          mma_bf16_pair(d_lo, ai_l, bi_h, id | kNegateA, 1u);
+          mma_bf16_pair(d_lo + 128, ar_l, bi_h, id, first);
+          mma_bf16_pair(d_lo + 128, ai_l, br_h, id, 1u);
+          mma_bf16_pair(d_lo, ar_h, br_l, id, 1u);
+          mma_bf16_pair(d_lo, ai_h, bi_l, id | kNegateA, 1u);
+          mma_bf16_pair(d_lo + 128, ar_h, bi_l, id, 1u);
+          mma_bf16_pair(d_lo + 128, ai_h, br_l, id, 1u);
+        }
+      };
+      auto hihi = [&](uint32_t sa, uint32_t sb, bool first_kb) {
+#pragma unroll
+        for (int j = 0; j < BK / 16; ++j) {
+          const uint32_t o = j * 32;
+          const uint64_t ar_h = smem_desc<ROWB>(sa + o), ai_h = smem_desc<ROWB>(sa + PA + o);
+          const uint64_t br_h = smem_desc<ROWB>(sb + o), bi_h = smem_desc<ROWB>(sb + PB + o);
+          const uint32_t acc = (!first_kb || j > 0) ? 1u : 0u;
+          mma_bf16_pair(d_hi, ar_h, br_h, id, acc);
+          mma_bf16_pair(d_hi, ai_h, bi_h, id | kNegateA, 1u);
+          mma_bf16_pair(d_hi + 128, ar_h, bi_h, id, acc);
+          mma_bf16_pair(d_hi + 128, ai_h, br_h, id, 1u);
+        }
+      };
+      int64_t g = 0;   // k-blocks consumed over all items
+      int64_t G = 0;   // chunks over all items
+      auto stage_of = [&](int64_t gg) { return su32(smem + (gg % STAGES) * STAGE); };
+      auto landed = [&](int64_t gg) {
+        const uint32_t ph = static_cast<uint32_t>((gg / STAGES) & 1);
+        return mbar_wait(&full[gg % STAGES], ph) && mbar_wait(&ready[gg % STAGES], ph);
+      };
+      constexpr int LEAD = 2;
+      bool ok = true;
+      for (int64_t w = cluster; w < total && ok; w += n_clusters) {
+        for (int c = 0; c < n_chunks && ok; ++c, ++G) {
+          const int kb0 = c * CK, kb_end = min(num_kb, (c + 1) * CK);
+          // a new item restarts D_lo: its cross terms wait for the previous item's last fold
+          const int lead_end = c == 0 ? kb0 : min(kb_end, kb0 + LEAD);
+          for (int kb = kb0; kb < lead_end && ok; ++kb) {
+            if (!landed(g + (kb - kb0))) {
+              atomicExch(err, 55);
+              ok = false;
+              break;
+            }
+            fence_after();
+            cross(stage_of(g + (kb - kb0)), stage_of(g + (kb - kb0)) + CB2::OFF_B, false);
+          }
+          if (ok && !mbar_wait(acc_empty, static_cast<uint32_t>(G & 1) ^ 1)) {
+            atomicExch(err, 56);
+            ok = false;
+          }
+          if (!ok) {
+            mma_commit_pair(acc_full);
+            break;
+          }
+          fence_after();
+          for (int kb = kb0; kb < lead_end; ++kb) {
+            hihi(stage_of(g), stage_of(g) + CB2::OFF_B, kb == kb0);
+            mma_commit_pair(&empty[g % STAGES]);
+            ++g;
+          }
+          for (int kb = lead_end; kb < kb_end; ++kb) {
+            if (!landed(g)) {
+              atomicExch(err, 55);
+              ok = false;
+              break;
+            }
+            fence_after();
+            cross(stage_of(g), stage_of(g) + CB2::OFF_B, kb == 0);
+            hihi(stage_of(g), stage_of(g) + CB2::OFF_B, kb == kb0);
+            mma_commit_pair(&empty[g % STAGES]);
+            ++g;
+          }
+          mma_commit_pair(acc_full);  // also on error, so the fold sees issued MMAs retire
+        }
+      }
+    }
+  } else {
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    float* tr = epi + (warp - 2) * 2 * 32 * 33;  // this warp's Re and Im transpose blocks
+    const int split = a.c_split;
+    bool pow2 = a.m >= 32 && a.n >= 32;
+    for (int d = 0; d < a.rows.n; ++d) pow2 = pow2 && (a.rows.ext[d] & (a.rows.ext[d] - 1u)) == 0u;
+    for (int d = 0; d < a.cols.n; ++d) pow2 = pow2 && (a.cols.ext[d] & (a.cols.ext[d] - 1u)) == 0u;
+    // kept in shared memory (the same for every lane), not in registers
+    BlockOrder& ord = reinterpret_cast<BlockOrder*>(epi + 8 * 2 * 32 * 33)[warp - 2];
+    {
+      const BlockOrder o = block_order(pow2 ? map_offset(a.rows, lane) : 0, pow2 ? map_offset(a.cols, lane) : 0,
+                                       pow2, lane);
+      if (lane == 0) ord = o;
+      __syncwarp();
+    }
+    int64_t G = 0;  // chunks folded over all items
+    bool ok = true;
+    for (int64_t w = cluster; w < total && ok; w += n_clusters) {
+      int b, m0, n0;
+      item(w, b, m0, n0);
+      float run_re[64], run_im[64];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) run_re[i] = run_im[i] = 0.f;
+      for (int c = 0; c < n_chunks; ++c, ++G) {
+        if (!mbar_wait(acc_full, static_cast<uint32_t>(G & 1))) {
+          atomicExch(err, 57);
+          ok = false;
+          break;
+        }
+        fence_after();
+        float v[32];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const uint32_t col = lane_base + half * 64 + p * 32;
+          tmem_ld32(tmem + col, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+          tmem_ld32(tmem + 128 + col, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+          if (c == n_chunks - 1) {
+            tmem_ld32(tmem + 256 + col, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
+            tmem_ld32(tmem + 384 + col, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (rank == 0) mbar_arrive(acc_empty);
+          else mbar_arrive_leader(acc_empty);
+        }
+      }
+      if (!ok) break;
+      // epilogue from registers while the next item's MMAs run: thread = row
+      // m0 + 128 rank + 32 q + lane; this warp's 64 columns, one 32 x 32 block at a time
+      const int64_t m = static_cast<int64_t>(m0) + 128 * static_cast<int64_t>(rank) + q * 32 + lane;
+      const bool row_ok = m < a.m;
+      const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
+      float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
+#pragma unroll
+      for (int cb = 0; cb < 2; ++cb) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          tr[lane * 33 + j] = run_re[cb * 32 + j];
+          tr[32 * 33 + lane * 33 + j] = run_im[cb * 32 + j];
+        }
+        __syncwarp();
+        const int64_t n = static_cast<int64_t>(n0) + half * 64 + cb * 32 + lane;
+        const bool col_ok = n < a.n;
+        const int64_t co = col_ok ? map_offset(a.cols, n) : 0;
+        if (ord.ok && __all_sync(0xffffffffu, row_ok && col_ok)) {
+          const int64_t base = __shfl_sync(0xffffffffu, ro, 0) + __shfl_sync(0xffffffffu, co, 0);
+          store_ordered(C, a.c_plane, split, tr, 33, 32 * 33, base, ord, lane);
+        } else {
+          store_block(C, a.c_plane, split, tr, 33, 32 * 33, ro, co, row_ok, col_ok, lane);
+        }
+        __syncwarp();
+      }
+    }
+  }
+  // common teardown: every thread of both CTAs
+  fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CB2::COLS));
+  __syncthreads();
+  cluster_sync_all();
+}
+
+// ---------------------------------------------------------------------------------
 // BF16x3 form with the 3M complex product (Gauss): with s = a_re + a_im and t = b_re + b_im,
 //   P1 = a_re.b_re,  P2 = a_im.b_im,  P3 = s.t;   Re = P1 - P2,  Im = P3 - P1 - P2,
 // three real products per complex MAC instead of four, each as hi.hi + hi.lo + lo.hi of
@@ -1615,7 +1927,8 @@ __global__ void __launch_bounds__(CB3::THREADS, 1)
 // block per fold warp for the epilogue.
 struct CBP {
   static constexpr int STAGES = 2;
-  static constexpr int EPI = 8 * 2 * 32 * 33 * 4;          // per fold warp: Re and Im of one 32 x 32 block
+  // per fold warp: Re and Im of one 32 x 32 block, then the fold warps' block orders
+  static constexpr int EPI = 8 * 2 * 32 * 33 * 4 + 8 * 128;
   static constexpr int BARS = 256;
   static constexpr int SMEM = STAGES * CB::STAGE + EPI + BARS + 1024 /*align*/;
   static constexpr int MAX_K = CB::CK * CB::BK;            // used for k <= 256: one fold chunk per tile
@@ -1759,8 +2072,14 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
     bool pow2 = a.m >= 32 && a.n >= 32;
     for (int d = 0; d < a.rows.n; ++d) pow2 = pow2 && (a.rows.ext[d] & (a.rows.ext[d] - 1u)) == 0u;
     for (int d = 0; d < a.cols.n; ++d) pow2 = pow2 && (a.cols.ext[d] & (a.cols.ext[d] - 1u)) == 0u;
-    const BlockOrder ord = block_order(pow2 ? map_offset(a.rows, lane) : 0, pow2 ? map_offset(a.cols, lane) : 0,
+    // kept in shared memory (the same for every lane), not in registers
+    BlockOrder& ord = reinterpret_cast<BlockOrder*>(epi + 8 * 2 * 32 * 33)[warp - 2];
+    {
+      const BlockOrder o = block_order(pow2 ? map_offset(a.rows, lane) : 0, pow2 ? map_offset(a.cols, lane) : 0,
                                        pow2, lane);
+      if (lane == 0) ord = o;
+      __syncwarp();
+    }
     int64_t q = 0;  // tiles folded
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++q) {
       const TileCoord tc = tile_of(w, tiles_m, tiles_n);
@@ -1945,6 +2264,8 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st,
                                CBP::SMEM);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(contract_tcb2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB2::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(contract_tcb2p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB2P::SMEM);
     return e;
   }();
   if (configured != cudaSuccess) return configured;
@@ -1957,6 +2278,24 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st,
         !make_map_split(&tb, a.B, a.n, a.k, cb, a.b_plane, BN / 2))
       return cudaErrorInvalidValue;
     const int64_t pair_tiles = ((a.m + 2 * BM - 1) / (2 * BM)) * ((a.n + BN - 1) / BN);
+    if (a.k <= kPairsPersistentMaxK) {
+      // persistent: as many clusters as are resident at once, each walking its items
+      static const int clusters = [] {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2, 1, 1);
+        cfg.blockDim = dim3(CB2::THREADS, 1, 1);
+        cfg.dynamicSmemBytes = CB2P::SMEM;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, contract_tcb2p_kernel, &cfg) != cudaSuccess || n <= 0) n = 0;
+        return n;
+      }();
+      if (clusters > 0) {
+        const int64_t items = pair_tiles * static_cast<int64_t>(nb);
+        const int64_t g = items < clusters ? items : clusters;
+        contract_tcb2p_kernel<<<static_cast<unsigned>(2 * g), CB2::THREADS, CB2P::SMEM, st>>>(ta, tb, a, nb, err);
+        return cudaGetLastError();
+      }
+    }
     dim3 grid(static_cast<unsigned>(2 * pair_tiles), static_cast<unsigned>(nb));
     contract_tcb2_kernel<<<grid, CB2::THREADS, CB2::SMEM, st>>>(ta, tb, a, err);
     return cudaGetLastError();
