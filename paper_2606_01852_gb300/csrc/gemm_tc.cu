@@ -1076,9 +1076,9 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
 // 256 x 128 output tile: CTA r (rank in the pair) loads A rows m0 + 128 r .. + 127 and B
 // rows n0 + 64 r .. + 63 (all four split planes, 32 deep per k-block) into its own shared
 // memory by TMA, and CTA 0 issues M = 256, N = 128 MMAs that read A and B from both. Per
-// SM and 16-deep atom the MMAs read 72 KiB (4 KiB of A and 2 KiB of B per MMA) and TMA
-// writes 24 KiB, against 84 and 32 KiB on one SM: shared-memory bandwidth, which bounds the
-// single-SM kernel, drops below the tensor pipe's need. The accumulation is that of
+// SM and 16-deep atom TMA writes 24 KiB instead of 32 KiB and each SM fetches half of its B
+// panel, so the L2 and DRAM operand traffic per output halves; the data moved per flop, and
+// with it the power drawn, drops, which under the power limit buys clock. The accumulation is that of
 // contract_tcb_kernel term for term (hi.hi chunk accumulator folded into round-to-nearest
 // registers every 256 terms, the cross terms over all of k), with the four real products of
 // each complex product as separate N = 128 MMAs in the same order per accumulator, so each
