@@ -160,6 +160,45 @@ __device__ __forceinline__ void store_run(float* C, int64_t plane, int64_t off, 
     }
     return;
   }
+  if constexpr (V >= 2) {
+    if (fmt == kFmtSplit) {
+      // hi = RN_bf16(v), lo = RN_bf16(v - hi), two values per conversion (the same values
+      // as split_pair's one at a time); 32-bit word w holds elements 2w (low) and 2w + 1
+      constexpr int W = V / 2;
+      uint32_t hr[W], hi_[W], lr[W], li[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(re[2 * w], re[2 * w + 1]);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(im[2 * w], im[2 * w + 1]);
+        const __nv_bfloat162 c =
+            __floats2bfloat162_rn(re[2 * w] - __low2float(a), re[2 * w + 1] - __high2float(a));
+        const __nv_bfloat162 d =
+            __floats2bfloat162_rn(im[2 * w] - __low2float(b), im[2 * w + 1] - __high2float(b));
+        hr[w] = uint32_t(__bfloat16_as_ushort(a.x)) | (uint32_t(__bfloat16_as_ushort(a.y)) << 16);
+        hi_[w] = uint32_t(__bfloat16_as_ushort(b.x)) | (uint32_t(__bfloat16_as_ushort(b.y)) << 16);
+        lr[w] = uint32_t(__bfloat16_as_ushort(c.x)) | (uint32_t(__bfloat16_as_ushort(c.y)) << 16);
+        li[w] = uint32_t(__bfloat16_as_ushort(d.x)) | (uint32_t(__bfloat16_as_ushort(d.y)) << 16);
+      }
+      uint16_t* S = reinterpret_cast<uint16_t*>(C) + off;
+      if constexpr (W == 1) {
+        *reinterpret_cast<uint32_t*>(S) = hr[0];
+        *reinterpret_cast<uint32_t*>(S + plane) = hi_[0];
+        *reinterpret_cast<uint32_t*>(S + 2 * plane) = lr[0];
+        *reinterpret_cast<uint32_t*>(S + 3 * plane) = li[0];
+      } else if constexpr (W == 2) {
+        *reinterpret_cast<uint2*>(S) = make_uint2(hr[0], hr[1]);
+        *reinterpret_cast<uint2*>(S + plane) = make_uint2(hi_[0], hi_[1]);
+        *reinterpret_cast<uint2*>(S + 2 * plane) = make_uint2(lr[0], lr[1]);
+        *reinterpret_cast<uint2*>(S + 3 * plane) = make_uint2(li[0], li[1]);
+      } else {
+        *reinterpret_cast<uint4*>(S) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+        *reinterpret_cast<uint4*>(S + plane) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+        *reinterpret_cast<uint4*>(S + 2 * plane) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+        *reinterpret_cast<uint4*>(S + 3 * plane) = make_uint4(li[0], li[1], li[2], li[3]);
+      }
+      return;
+    }
+  }
   // hi = RN_bf16(v), lo = RN_bf16(v - hi) of re, im (and s = re + im in the 3M form)
   uint32_t hr[V], hi_[V], lr[V], li[V];
 #pragma unroll
@@ -1405,6 +1444,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
 // and 1.15x faster (no per-tile start-up and epilogue), at k >= 16384 the per-tile form is
 // 4-8 % faster (four ring stages instead of three, the per-tile cost being small there).
 constexpr int64_t kPairsPersistentMaxK = 4096;
+// steps with k <= 64 run contract_tcb_shallow_kernel
+constexpr bool kShallowKernel = true;
 struct CB2P {
   static constexpr int STAGES = 3;
   // per fold warp: Re and Im of one 32 x 32 block, then the fold warps' block orders
@@ -2142,6 +2183,188 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Shallow steps (k <= 64, BF16x3 4M): the result tile is stored for every one or two
+// k-blocks of MMA work, so the epilogue sets the pace. Persistent like
+// contract_tcb_persistent_kernel, but with sixteen fold/epilogue warps (a 32 x 32 block each
+// per tile: twice the warps to hide the transpose, split and store latencies) and a single
+// ring stage (its 64 KiB pay for the warps' transpose blocks); loading and the MMAs of the
+// next tile run while the previous tile is stored. Warps: 0 TMA, 1 MMA + TMEM, 2-17 fold and
+// epilogue. Bounded waits as in the other kernels (codes 61-65).
+struct CBS {
+  static constexpr int EPI_WARPS = 16;
+  static constexpr int THREADS = 32 * (2 + EPI_WARPS);
+  static constexpr int MAX_K = 2 * CB::BK;                 // two k-blocks per tile at most
+  static constexpr int EPI = EPI_WARPS * 2 * 32 * 33 * 4 + EPI_WARPS * 128;
+  static constexpr int SMEM = CB::STAGE + EPI + 256 + 1024;
+};
+static_assert(CBS::SMEM <= 232448, "shared memory per CTA");
+
+__global__ void __launch_bounds__(CBS::THREADS, 1)
+    contract_tcb_shallow_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                                StepArgs a, int32_t nb, int* err) {
+  constexpr int BK = CB::BK, ROWB = CB::ROWB, PLANE = CB::PLANE, STAGE = CB::STAGE;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* epi = reinterpret_cast<float*>(smem + STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGE + CBS::EPI);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + 1;
+  uint64_t* acc_full = bars + 2;
+  uint64_t* acc_empty = bars + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
+  const int64_t total = tiles_m * tiles_n * nb;
+  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);  // 1 or 2
+
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(empty, 1);
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, CBS::EPI_WARPS);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(CB::COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int64_t g = 0;  // k-blocks issued: phase g of the one stage
+      bool ok = true;
+      for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x) {
+        const TileCoord tc = tile_of(w, tiles_m, tiles_n);
+        const int pa = a.a_bstride ? 4 * tc.b : 0, pb = a.b_bstride ? 4 * tc.b : 0;
+        for (int kb = 0; kb < num_kb; ++kb, ++g) {
+          if (!mbar_wait(empty, static_cast<uint32_t>(g & 1) ^ 1)) {
+            atomicExch(err, 61);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full, STAGE);
+          tma_load_3d(smem, &tmA, full, kb * BK, tc.m0, pa);
+          tma_load_3d(smem + CB::OFF_B, &tmB, full, kb * BK, tc.n0, pb);
+        }
+      }
+      // every issued load has landed before the CTA can exit
+      if (g > 0 && !mbar_wait(full, static_cast<uint32_t>((g - 1) & 1))) atomicExch(err, 62);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t id_w = idesc_bf16(BM, 2 * BN);
+      constexpr uint32_t id_n = idesc_bf16(BM, BN);
+      const uint32_t d_hi = tmem, d_lo = tmem + 256;
+      int64_t g = 0, q = 0;
+      bool ok = true;
+      for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x, ++q) {
+        if (!mbar_wait(acc_empty, static_cast<uint32_t>(q & 1) ^ 1)) {  // the previous tile was read
+          atomicExch(err, 63);
+          break;
+        }
+        fence_after();
+        for (int kb = 0; kb < num_kb; ++kb, ++g) {
+          if (!mbar_wait(full, static_cast<uint32_t>(g & 1))) {
+            atomicExch(err, 64);
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sa = su32(smem), sb = sa + CB::OFF_B;
+#pragma unroll
+          for (int j = 0; j < BK / 16; ++j) {
+            const uint32_t o = j * 32;
+            const uint64_t ar_l = smem_desc<ROWB>(sa + 2 * PLANE + o), ai_l = smem_desc<ROWB>(sa + 3 * PLANE + o);
+            const uint64_t ar_h = smem_desc<ROWB>(sa + o), ai_h = smem_desc<ROWB>(sa + PLANE + o);
+            const uint64_t b_h = smem_desc<ROWB>(sb + o), bi_h = smem_desc<ROWB>(sb + PLANE + o);
+            const uint64_t b_l = smem_desc<ROWB>(sb + 2 * PLANE + o), bi_l = smem_desc<ROWB>(sb + 3 * PLANE + o);
+            const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
+            mma_bf16(d_lo, ar_l, b_h, id_w, acc);
+            mma_bf16(d_lo, ai_l, bi_h, id_n | kNegateA, 1u);
+            mma_bf16(d_lo + 128, ai_l, b_h, id_n, 1u);
+            mma_bf16(d_lo, ar_h, b_l, id_w, 1u);
+            mma_bf16(d_lo, ai_h, bi_l, id_n | kNegateA, 1u);
+            mma_bf16(d_lo + 128, ai_h, b_l, id_n, 1u);
+            mma_bf16(d_hi, ar_h, b_h, id_w, acc);
+            mma_bf16(d_hi, ai_h, bi_h, id_n | kNegateA, 1u);
+            mma_bf16(d_hi + 128, ai_h, b_h, id_n, 1u);
+          }
+          mma_commit(empty);
+        }
+        mma_commit(acc_full);  // also on error, so the fold sees issued MMAs retire
+      }
+    }
+  } else {
+    const int e = warp - 2;                        // 0..15
+    const int q4 = warp & 3, cq = e >> 2;          // TMEM lane quarter; 32-column group
+    const uint32_t lane_base = static_cast<uint32_t>(q4 * 32) << 16;
+    float* tr = epi + e * 2 * 32 * 33;             // this warp's Re and Im transpose block
+    const int split = a.c_split;
+    bool pow2 = a.m >= 32 && a.n >= 32;
+    for (int d = 0; d < a.rows.n; ++d) pow2 = pow2 && (a.rows.ext[d] & (a.rows.ext[d] - 1u)) == 0u;
+    for (int d = 0; d < a.cols.n; ++d) pow2 = pow2 && (a.cols.ext[d] & (a.cols.ext[d] - 1u)) == 0u;
+    BlockOrder& ord = reinterpret_cast<BlockOrder*>(epi + CBS::EPI_WARPS * 2 * 32 * 33)[e];
+    {
+      const BlockOrder o = block_order(pow2 ? map_offset(a.rows, lane) : 0, pow2 ? map_offset(a.cols, lane) : 0,
+                                       pow2, lane);
+      if (lane == 0) ord = o;
+      __syncwarp();
+    }
+    int64_t q = 0;
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++q) {
+      const TileCoord tc = tile_of(w, tiles_m, tiles_n);
+      if (!mbar_wait(acc_full, static_cast<uint32_t>(q & 1))) {
+        atomicExch(err, 65);
+        break;
+      }
+      fence_after();
+      // this warp's 32 columns: hi + lo of Re, then of Im, into the transpose block
+      float v[32], u[32];
+      const uint32_t col = lane_base + cq * 32;
+      tmem_ld32(tmem + col, v);
+      tmem_ld32(tmem + 256 + col, u);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tr[lane * 33 + j] = v[j] + u[j];
+      tmem_ld32(tmem + 128 + col, v);
+      tmem_ld32(tmem + 384 + col, u);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tr[32 * 33 + lane * 33 + j] = v[j] + u[j];
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);  // the accumulators are free for the next tile
+      const int64_t m = static_cast<int64_t>(tc.m0) + q4 * 32 + lane;
+      const bool row_ok = m < a.m;
+      const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
+      float* C = a.C + static_cast<int64_t>(tc.b) * a.c_bstride;
+      const int64_t n = static_cast<int64_t>(tc.n0) + cq * 32 + lane;
+      const bool col_ok = n < a.n;
+      const int64_t co = col_ok ? map_offset(a.cols, n) : 0;
+      if (ord.ok && __all_sync(0xffffffffu, row_ok && col_ok)) {
+        const int64_t base = __shfl_sync(0xffffffffu, ro, 0) + __shfl_sync(0xffffffffu, co, 0);
+        store_ordered(C, a.c_plane, split, tr, 33, 32 * 33, base, ord, lane);
+      } else {
+        store_block(C, a.c_plane, split, tr, 33, 32 * 33, ro, co, row_ok, col_ok, lane);
+      }
+      __syncwarp();
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CB::COLS));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -2266,6 +2489,8 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st,
       e = cudaFuncSetAttribute(contract_tcb2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB2::SMEM);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(contract_tcb2p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB2P::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(contract_tcb_shallow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CBS::SMEM);
     return e;
   }();
   if (configured != cudaSuccess) return configured;
@@ -2303,6 +2528,17 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st,
   if (!make_map_split(&ta, a.A, a.m, a.k, ca, a.a_plane, BM) || !make_map_split(&tb, a.B, a.n, a.k, cb, a.b_plane, BN))
     return cudaErrorInvalidValue;
   const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
+  if (a.k <= CBS::MAX_K && kShallowKernel) {
+    // shallowest steps: persistent, sixteen epilogue warps, one CTA per SM
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t items = tiles * static_cast<int64_t>(nb);
+    const unsigned grid = static_cast<unsigned>(items < sms ? items : sms);
+    contract_tcb_shallow_kernel<<<grid, CBS::THREADS, CBS::SMEM, st>>>(ta, tb, a, nb, err);
+    return cudaGetLastError();
+  }
   if (a.k <= CBP::MAX_K) {
     // shallow step: persistent, one CTA per SM (the shared memory admits one)
     int dev = 0, sms = 0;
