@@ -1,9 +1,10 @@
 // Tensor-core path for the dense pairwise steps (sm_103a): planar complex GEMM
 //   C[b] = A[b] (m x k) . B[b] (n x k)^T      (complex, 4M real decomposition)
 // with both operands K-major, written through the separable row/column offset maps.
-// Every kernel computes 128 x 128 output tiles with one elected thread issuing
-// tcgen05.mma from shared-memory descriptors, operands brought by TMA into a ring of
-// stages (mbarrier transaction counts), accumulators in tensor memory:
+// The kernels compute 128 x 128 output tiles per SM (256 x 128 per pair of SMs in the
+// cta_group::2 forms) with one elected thread issuing tcgen05.mma from shared-memory
+// descriptors, operands brought by TMA into a ring of stages (mbarrier transaction counts),
+// accumulators in tensor memory:
 //   contract_tc_kernel<1>          TF32 form: A_re, A_im, B_re, B_im fp32 tiles, 32-deep
 //                                  k-blocks, 3 stages, D_rr / D_ii / D_x accumulators
 //                                  (Re C = D_rr - D_ii, Im C = D_x); 192 threads;
@@ -13,8 +14,13 @@
 //                                  their own accumulator; 320 threads;
 //   contract_tcb_kernel            BF16x3 form: operands already split into BF16 hi/lo
 //                                  planes by their producers, kind::f16, 256-term chunks;
+//   contract_tcb2_kernel           BF16x3 on paired SMs (m >= 256, k > 4096): one two-CTA
+//                                  cluster per 256 x 128 tile, M = 256 MMAs;
+//   contract_tcb2p_kernel          the same, persistent clusters (256 < k <= 4096);
+//   contract_tcb3m_kernel          BF16x3 with the 3M complex product;
 //   contract_tcb_persistent_kernel BF16x3 for shallow steps (k <= 256): one CTA per SM over
-//                                  the tiles, stores of a tile overlapping the next tile.
+//                                  the tiles, stores of a tile overlapping the next tile;
+//   contract_tcb_shallow_kernel    the same for k <= 64 with sixteen epilogue warps.
 // The epilogues of the TF32 and BF16x3 kernels store each 32 x 32 block in address order
 // (store_block). Every mbarrier wait is bounded by wall time; on expiry the CTA records an
 // error code, drains its copies, frees its tensor memory and returns.
