@@ -145,6 +145,23 @@ def test_paired_sm_tiles_same_bits(tn, case):
     one.destroy()
 
 
+def test_paired_sm_tiles_row_operand_batched(tn):
+    """Paired-SM tiles when only the row operand depends on the slice (the column operand
+    shared by every batch entry), 3 slices per pass: the same bits as on one SM."""
+    net, path, sliced = gemm_network((512,), (384,), (512,), [("m", 0), ("n", 0)], seed=41, vec_slice=4)
+    pair = tn.Plan(net, path, sliced, prec="bf16x3", max_slice_batch=3)
+    one = tn.Plan(net, path, sliced, prec="bf16x3", max_slice_batch=3, single_sm_tiles=True)
+    st = pair.step(1)
+    assert st["cls"] == tn.TN_CLASS_TC and st["batched"] == 1 and st["m"] >= 256 and st["k"] > 256
+    got, _ = run(tn, pair, net)
+    ref, _ = run(tn, one, net)
+    g, r = np.ascontiguousarray(got), np.ascontiguousarray(ref)
+    assert np.array_equal(g.view(np.uint64), r.view(np.uint64))
+    assert rel_err(got, oracle.contract(net, path, sliced)) < 5e-5
+    pair.destroy()
+    one.destroy()
+
+
 @pytest.mark.parametrize("prec,tol", [("tf32", 5e-3), ("3xtf32", 1e-5), ("bf16x3", 5e-5), ("bf16x3m", 1e-4)])
 def test_batched_both_operands(tn, prec, tol):
     """A sliced label on both operands: the batch runs as TMA planes of both maps."""
