@@ -246,6 +246,19 @@ tn_status tn_plan_tensor(tn_plan_t plan, int32_t id, tn_tensor_info* out);
 tn_status tn_contract(tn_plan_t plan, const void* const* inputs, void* output,
                       double* out_log_scale, void* stream);
 
+/* As tn_contract (all slices, device buffers), with the call's launches replayed from a
+ * CUDA graph: the first call with a given set of input pointers, output, log_scale and
+ * stream runs the contraction as tn_contract does and then captures the same call on a
+ * private stream; later calls with the same pointers and stream launch the captured graph
+ * (one launch instead of one per step and pass), with the same results bit for bit. A call
+ * with other pointers or another stream re-captures (after the previous graph's last launch
+ * has finished). The first call allocates the graph and a pinned copy of the leaf
+ * descriptors; tn_plan_destroy frees them. The inputs are read at launch time, so new values
+ * in the same buffers are contracted by a replay. TN_ERR_INVALID while per-step profiling is
+ * on (tn_plan_profile) or for a host-only plan; TN_ERR_CUDA if capture fails. */
+tn_status tn_contract_graph(tn_plan_t plan, const void* const* inputs, void* output, double* out_log_scale,
+                            void* stream);
+
 /* As tn_contract, summing only slices [slice_begin, slice_begin + slice_count). With
  * slice_count = 1 the output is that slice's partial result (Sec. V-A projection: time
  * per slice). */

@@ -137,6 +137,7 @@ def _load():
         "tn_plan_step": [vp, i32, C.POINTER(tn_step_info)],
         "tn_plan_tensor": [vp, i32, C.POINTER(tn_tensor_info)],
         "tn_contract": [vp, C.POINTER(vp), vp, vp, vp],
+        "tn_contract_graph": [vp, C.POINTER(vp), vp, vp, vp],
         "tn_contract_slices": [vp, C.POINTER(vp), i64, i64, vp, vp, vp],
         "tn_contract_host": [vp, C.POINTER(vp), vp, vp, vp],
         "tn_contract_slices_host": [vp, C.POINTER(vp), i64, i64, vp, vp, vp],
@@ -303,6 +304,12 @@ class Plan:
     def contract(self, inputs, output, log_scale=None, stream=None):
         check(lib.tn_contract(self.handle, self._inputs(inputs), _ptr(output), _ptr(log_scale),
                               _ptr_stream(stream)))
+
+    def contract_graph(self, inputs, output, log_scale=None, stream=None):
+        """tn_contract_graph: as contract, replayed from a CUDA graph captured on the first call
+        with these pointers and stream."""
+        check(lib.tn_contract_graph(self.handle, self._inputs(inputs), _ptr(output), _ptr(log_scale),
+                                    _ptr_stream(stream)))
 
     def contract_slices(self, inputs, begin, count, output, log_scale=None, stream=None):
         check(lib.tn_contract_slices(self.handle, self._inputs(inputs), int(begin), int(count),

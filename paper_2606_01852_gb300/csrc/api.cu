@@ -93,7 +93,7 @@ tn_status check_device_error(Plan& P) {
 }
 
 tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t count, void* output,
-                     double* log_scale, void* stream, std::string& err) {
+                     double* log_scale, void* stream, std::string& err, void* pinned) {
   if (!P.dev) {
     err = "plan was built with TN_PLAN_HOST_ONLY (no device workspace)";
     return TN_ERR_INVALID;
@@ -120,15 +120,22 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
     P.leafdesc[t].src = inputs[t];
     P.leafdesc[t].dst = P.tensors[t].offset;
   }
-  // descriptors from pageable memory: the copy is staged before the call returns
-  TN_CUDA_TRY(cudaMemcpyAsync(P.dev + P.off_leafdesc, P.leafdesc.data(),
-                              sizeof(LeafDesc) * P.leafdesc.size(), cudaMemcpyHostToDevice, st));
+  // descriptors from pageable memory (the copy is staged before the call returns), or from
+  // the caller's pinned buffer
+  const void* desc_src = P.leafdesc.data();
+  const void* rec_src = P.rec_index.data();
+  if (pinned) {
+    char* pb = static_cast<char*>(pinned);
+    std::memcpy(pb, P.leafdesc.data(), sizeof(LeafDesc) * P.leafdesc.size());
+    std::memcpy(pb + sizeof(LeafDesc) * T, P.rec_index.data(), sizeof(int32_t) * T);
+    desc_src = pb;
+    rec_src = pb + sizeof(LeafDesc) * T;
+  }
+  TN_CUDA_TRY(cudaMemcpyAsync(P.dev + P.off_leafdesc, desc_src, sizeof(LeafDesc) * P.leafdesc.size(),
+                              cudaMemcpyHostToDevice, st));
   ScaleRec* recs = scaling ? reinterpret_cast<ScaleRec*>(P.dev + P.off_scale) : nullptr;
   int32_t* recidx = reinterpret_cast<int32_t*>(P.dev + P.off_recidx);
-  if (scaling) {
-    TN_CUDA_TRY(cudaMemcpyAsync(recidx, P.rec_index.data(), sizeof(int32_t) * T,
-                                cudaMemcpyHostToDevice, st));
-  }
+  if (scaling) TN_CUDA_TRY(cudaMemcpyAsync(recidx, rec_src, sizeof(int32_t) * T, cudaMemcpyHostToDevice, st));
   const LeafDesc* descs = reinterpret_cast<const LeafDesc*>(P.dev + P.off_leafdesc);
   double* acc = reinterpret_cast<double*>(P.dev + P.off_acc);
   int64_t* ref = reinterpret_cast<int64_t*>(P.dev + P.off_ref);
@@ -400,6 +407,82 @@ tn_status tn_contract(tn_plan_t plan, const void* const* inputs, void* output, d
   return tn_contract_slices(plan, inputs, 0, plan->P.n_slices, output, out_log_scale, stream);
 }
 
+tn_status tn_contract_graph(tn_plan_t plan, const void* const* inputs, void* output, double* out_log_scale,
+                            void* stream) {
+  if (!plan || !inputs || !output) {
+    set_error("null plan, inputs or output");
+    return TN_ERR_INVALID;
+  }
+  Plan& P = plan->P;
+  if (!P.dev) {
+    set_error("plan was built with TN_PLAN_HOST_ONLY (no device workspace)");
+    return TN_ERR_INVALID;
+  }
+  if (P.prof_on) {
+    set_error("tn_contract_graph: per-step profiling is on (tn_plan_profile)");
+    return TN_ERR_INVALID;
+  }
+  const int32_t T = P.n_leaves;
+  bool same = P.g_exec && P.g_out == output && P.g_ls == out_log_scale && P.g_stream == stream &&
+              (int32_t)P.g_inputs.size() == T;
+  for (int32_t t = 0; same && t < T; ++t) same = P.g_inputs[t] == inputs[t];
+  if (same) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGraphLaunch(static_cast<cudaGraphExec_t>(P.g_exec), st);
+    if (e == cudaSuccess) e = cudaEventRecord(static_cast<cudaEvent_t>(P.g_done), st);
+    if (e != cudaSuccess) {
+      set_error(std::string("graph launch: ") + cudaGetErrorString(e));
+      return TN_ERR_CUDA;
+    }
+    return TN_OK;
+  }
+  // new pointers or stream: run the call as usual (which also performs any one-time
+  // kernel configuration), then capture the same call on a private stream
+  tn_status s = tn_contract(plan, inputs, output, out_log_scale, stream);
+  if (s != TN_OK) return s;
+  if (P.g_done) {
+    // the previous graph's copy nodes read the pinned buffer: let its last launch finish
+    cudaEventSynchronize(static_cast<cudaEvent_t>(P.g_done));
+  } else if (cudaEventCreateWithFlags(reinterpret_cast<cudaEvent_t*>(&P.g_done), cudaEventDisableTiming) !=
+             cudaSuccess) {
+    set_error("event creation failed");
+    return TN_ERR_CUDA;
+  }
+  if (P.g_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(P.g_exec));
+  P.g_exec = nullptr;
+  if (!P.g_pinned && cudaMallocHost(&P.g_pinned, (sizeof(LeafDesc) + sizeof(int32_t)) * T + 16) != cudaSuccess) {
+    P.g_pinned = nullptr;
+    set_error("pinned descriptor buffer");
+    return TN_ERR_OOM;
+  }
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("graph capture stream");
+    return TN_ERR_CUDA;
+  }
+  cudaGraph_t g = nullptr;
+  std::string err;
+  s = TN_OK;
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) s = TN_ERR_CUDA;
+  if (s == TN_OK) s = run_slices(P, inputs, 0, P.n_slices, output, out_log_scale, cap, err, P.g_pinned);
+  cudaError_t e = cudaStreamEndCapture(cap, &g);
+  cudaGraphExec_t ge = nullptr;
+  if (s == TN_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  if (s != TN_OK || e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("graph capture failed: ") + (err.empty() ? cudaGetErrorString(e) : err));
+    return TN_ERR_CUDA;
+  }
+  P.g_exec = ge;
+  P.g_inputs.assign(inputs, inputs + T);
+  P.g_out = output;
+  P.g_ls = out_log_scale;
+  P.g_stream = stream;
+  return TN_OK;
+}
+
 tn_status tn_contract_slices_host(tn_plan_t plan, const void* const* host_inputs, int64_t slice_begin,
                                   int64_t slice_count, void* host_output, double* out_log_scale, void* stream) {
   if (!plan || !host_inputs || !host_output) {
@@ -461,6 +544,12 @@ tn_status tn_contract_host(tn_plan_t plan, const void* const* host_inputs, void*
 
 tn_status tn_plan_destroy(tn_plan_t plan) {
   if (!plan) return TN_OK;
+  if (plan->P.g_done) {
+    cudaEventSynchronize(static_cast<cudaEvent_t>(plan->P.g_done));
+    cudaEventDestroy(static_cast<cudaEvent_t>(plan->P.g_done));
+  }
+  if (plan->P.g_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(plan->P.g_exec));
+  if (plan->P.g_pinned) cudaFreeHost(plan->P.g_pinned);
   if (plan->P.dev) cudaFree(plan->P.dev);
   for (auto& r : plan->P.prof_pending) {
     cudaEventDestroy(static_cast<cudaEvent_t>(r.e0));

@@ -135,6 +135,17 @@ struct Plan {
   tn_profile prof_acc{};
   std::vector<double> prof_step_ms, prof_last_step_ms;
   uint64_t uid = 0;                 // unique per plan (serve pools key on it)
+  // tn_contract_graph: the captured call (graph exec), the pointers and stream it was
+  // captured for, a pinned copy of the leaf descriptors and scale-record indices its copy
+  // nodes read, and an event after its last launch (the pinned copy is rewritten only
+  // after that event)
+  void* g_exec = nullptr;
+  std::vector<const void*> g_inputs;
+  void* g_out = nullptr;
+  double* g_ls = nullptr;
+  void* g_stream = nullptr;
+  void* g_pinned = nullptr;
+  void* g_done = nullptr;
   // stats
   tn_plan_stats stats{};
 };
@@ -149,8 +160,12 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
 void assign_workspace(Plan& P, int64_t batch);
 
 // executor
+// pinned: null (descriptors copied from pageable host memory, staged before the call
+// returns), or a pinned buffer of sizeof(LeafDesc) x n_leaves + 4 x n_leaves bytes that the
+// descriptor and record-index copies read from (capturable in a CUDA graph)
 tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t count,
-                     void* output, double* log_scale, void* stream, std::string& err);
+                     void* output, double* log_scale, void* stream, std::string& err,
+                     void* pinned = nullptr);
 
 void set_error(const std::string& msg);
 tn_status check_device_error(Plan& P);
