@@ -1446,10 +1446,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
 // all items of the cluster. A new item's cross-term MMAs (which restart D_lo) wait for the
 // previous item's last fold.
 // Paired-SM steps with k up to this run the persistent kernel; deeper ones one cluster per
-// tile. Measured on the 14-cycle circuit: at k = 512 and 1024 the persistent form is 1.5x
-// and 1.15x faster (no per-tile start-up and epilogue), at k >= 16384 the per-tile form is
-// 4-8 % faster (four ring stages instead of three, the per-tile cost being small there).
-constexpr int64_t kPairsPersistentMaxK = 4096;
+// tile. Measured on the 14- and 13-cycle circuits: at k = 512 and 1024 the persistent form
+// is 1.5x and 1.15x faster (no per-tile start-up and epilogue); at k = 4096 the two are
+// within 1.5 % (the per-tile form ahead), at k >= 16384 the per-tile form is 4-8 % faster
+// (four ring stages instead of three, the per-tile cost being small there).
+constexpr int64_t kPairsPersistentMaxK = 2048;
 // steps with k <= 64 run contract_tcb_shallow_kernel
 constexpr bool kShallowKernel = true;
 struct CB2P {

@@ -118,14 +118,14 @@ PAIR_CASES = [
     ((512,), (256,), (264,), [("m", 0), ("n", 0)], 3),                           # batched, k just above 256
     ((4096,), (2048,), (512,), [("m", 0), ("n", 0)], None),                      # 256 tiles: several per cluster
     ((1000,), (1000,), (320,), [("n", 0), ("m", 0)], 4),                         # ragged, 4 entries, 128 tiles
-    ((2, 256), (136,), (4104,), [("m", 0), ("m", 1), ("n", 0)], None),          # k > 4096: a cluster per tile
+    ((2, 256), (136,), (4104,), [("m", 0), ("m", 1), ("n", 0)], None),          # k > 2048: a cluster per tile
 ]
 
 
 @pytest.mark.parametrize("case", range(len(PAIR_CASES)))
 def test_paired_sm_tiles_same_bits(tn, case):
     """BF16x3 4M steps with m >= 256 and k > 256 run 256 x 128 output tiles on pairs of SMs
-    (tcgen05 cta_group::2; up to k = 4096 persistent clusters, each walking several tiles in
+    (tcgen05 cta_group::2; up to k = 2048 persistent clusters, each walking several tiles in
     the larger cases, beyond it one cluster per tile). Every output has the same bits as from the single-SM kernel
     (TN_PLAN_SINGLE_SM_TILES: the same products accumulated in the same order), and matches
     the oracle within the BF16x3 bound."""
