@@ -282,3 +282,28 @@ def test_stream_step_feeding_tensor_core_step(tn, prec, bound):
     assert rel_err(got, want) < bound
     assert np.abs(got - want).max() / np.abs(want).max() < 4 * bound
     plan.destroy()
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_paired_sm_tiles_random_shapes(tn, seed):
+    """Seeded random shapes through the paired-SM kernels (rows 256-1500, columns 16-700,
+    depth 264-5000 in steps of 8, with and without a sliced label on both operands): the
+    same bits as the single-SM kernel every time."""
+    rng = np.random.default_rng(1000 + seed)
+    m = int(rng.integers(256, 1501))
+    n = int(rng.integers(16, 701))
+    k = 8 * int(rng.integers(33, 626))
+    sl = int(rng.integers(2, 4)) if seed % 2 else None
+    net, path, sliced = gemm_network((m,), (n,), (k,), [("m", 0), ("n", 0)], seed=seed, sliced_dim=sl)
+    pair = tn.Plan(net, path, sliced, prec="bf16x3", max_slice_batch=2 if sl else 0)
+    one = tn.Plan(net, path, sliced, prec="bf16x3", max_slice_batch=2 if sl else 0, single_sm_tiles=True)
+    st = pair.step(0)
+    assert st["cls"] == tn.TN_CLASS_TC and st["m"] >= 256
+    got, _ = run(tn, pair, net)
+    ref, _ = run(tn, one, net)
+    g, r = np.ascontiguousarray(got), np.ascontiguousarray(ref)
+    assert np.array_equal(g.view(np.uint64), r.view(np.uint64)), (m, n, k, sl)
+    if seed < 3:
+        assert rel_err(got, oracle.contract(net, path, sliced)) < 5e-5
+    pair.destroy()
+    one.destroy()
