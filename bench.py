@@ -67,11 +67,12 @@ PREC = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x3m": 3}
 THREE_M = {"bf16x3m"}
 # arithmetic of each form (complex64 storage; products as named, FP32 accumulation)
 DTYPE_NAME = {"fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16x3": "bf16x3", "bf16x3m": "bf16x3 (3M)"}
-# DRAM bytes (read + write) of the dominant tensor-core launch (the step below), captured
-# on that launch itself (one metric group, one pass: 1930.6 GB read, 18.0 GB written; see
-# profiles/contract_tcb2_bf16x3_rc40c14_step310_dram.md). Valid for the kernel build it was
+# DRAM bytes (read + write) of the dominant tensor-core step (below) over the slices of a
+# pass, captured on that step itself: its 108 launches (bands of the paired-SM kernel's
+# tiles), one metric group, one pass each: 787.7 GB read, 15.9 GB written; see
+# profiles/contract_tcb2_bf16x3_rc40c14_step310_dram.md. Valid for the kernel build it was
 # taken on: drop an entry when that kernel changes.
-NCU_TRAFFIC_DOMINANT_LAUNCH = {("rc40c14", "bf16x3"): {"step": 310, "bytes": 1930.577e9 + 18.015784e9}}
+NCU_TRAFFIC_DOMINANT_LAUNCH = {("rc40c14", "bf16x3"): {"step": 310, "bytes": 787.698e9 + 15.940e9}}
 # Full values of the CPU oracle stored by the scripts in tests/golden/ (they call only the
 # oracle): the 40-qubit sum over all slices, and the full values of the smaller workloads.
 GOLDEN = os.path.join(ROOT, "tests", "golden")
@@ -507,8 +508,8 @@ def run_ours(args):
                                "traffic": cap["bytes"] if cap and cap["step"] == s_top else None}
     if cap and cap["step"] == s_top:
         roof["traffic"] = cap["bytes"]
-        roof["traffic_scope"] = ("DRAM bytes of the dominant launch (step %d), from a one-pass capture "
-                                 "of that launch" % s_top)
+        roof["traffic_scope"] = ("DRAM bytes of the dominant step (%d) over the slices of a pass, from a "
+                                 "one-pass capture of its launches" % s_top)
     roof["kernel"] = names[cls]
     roof["launches_per_step"] = launches / args.steps
     roof["ms_per_launch"] = per_launch_ms

@@ -229,6 +229,11 @@ tn_status tn_plan_check_staging(tn_plan_t plan, int64_t max_slices);
  * This is the layout the backward pass of Sec. IV-A assigns. */
 tn_status tn_plan_layout(tn_plan_t plan, int32_t id, int32_t* modes_out, int32_t* rank_out);
 
+/* The number of kernel launches one tn_contract_slices call over slice_count slices makes
+ * (the same for any first slice): staging, every step (two for split-k steps, several for a
+ * deep step on paired SMs, launched in bands of tiles), and the slice sum, per pass. */
+tn_status tn_plan_launches(tn_plan_t plan, int64_t slice_count, int64_t* out);
+
 /* Description of step s (host only). */
 tn_status tn_plan_step(tn_plan_t plan, int32_t s, tn_step_info* out);
 

@@ -135,6 +135,7 @@ def _load():
         "tn_plan_info": [vp, C.POINTER(tn_plan_stats)],
         "tn_plan_layout": [vp, i32, C.POINTER(i32), C.POINTER(i32)],
         "tn_plan_step": [vp, i32, C.POINTER(tn_step_info)],
+        "tn_plan_launches": [vp, i64, C.POINTER(i64)],
         "tn_plan_tensor": [vp, i32, C.POINTER(tn_tensor_info)],
         "tn_contract": [vp, C.POINTER(vp), vp, vp, vp],
         "tn_contract_graph": [vp, C.POINTER(vp), vp, vp, vp],
@@ -381,21 +382,11 @@ class Plan:
         return report, steps
 
     def launches_per_call(self, count=None) -> int:
-        """Kernel launches of one contract over `count` slices (default all)."""
-        info = self.info()
-        count = info["n_slices"] if count is None else count
-        b = info["slice_batch"]
-        passes = (count + b - 1) // b
-        S = info["n_steps"]
-        steps = [self.step(s) for s in range(S)]
-        per = [2 if (st["cls"] == TN_CLASS_SPLITK or st["ksplit"] > 1) else 1 for st in steps]
-        batched = sum(p for p, st in zip(per, steps) if st["batched"])
-        leaves = [self.tensor(t) for t in range(self.n_leaves)]
-        tiled = sum(1 for x in leaves if x["tiled"])
-        tiled_b = sum(1 for x in leaves if x["tiled"] and x["batched"])
-        # per pass: staging (+ one launch per tiled leaf) + steps + root accumulation (the
-        # last pass's also writes the output)
-        return (passes * 2 + sum(per) + (passes - 1) * batched + tiled + (passes - 1) * tiled_b)
+        """Kernel launches of one contract over `count` slices (default all): tn_plan_launches."""
+        count = self.info()["n_slices"] if count is None else count
+        n = C.c_int64()
+        check(lib.tn_plan_launches(self.handle, int(count), C.byref(n)))
+        return n.value
 
     def destroy(self):
         if getattr(self, "handle", None):

@@ -342,6 +342,37 @@ tn_status tn_plan_layout(tn_plan_t plan, int32_t id, int32_t* modes_out, int32_t
   return TN_OK;
 }
 
+tn_status tn_plan_launches(tn_plan_t plan, int64_t slice_count, int64_t* out) {
+  if (!plan || !out || slice_count <= 0 || slice_count > plan->P.n_slices) {
+    set_error("bad plan, slice count or output");
+    return TN_ERR_INVALID;
+  }
+  const Plan& P = plan->P;
+  const int32_t T = P.n_leaves;
+  const int64_t npass = (slice_count + P.batch - 1) / P.batch;
+  const bool pairs = (P.policy.flags & TN_PLAN_SINGLE_SM_TILES) == 0;
+  const int32_t form =
+      (P.policy.prec == TN_C64_BF16X3 && P.policy.complex_mult == 3) ? kPrecBF16x3M : P.policy.prec;
+  int64_t n = 0;
+  for (int64_t p = 0; p < npass; ++p) {
+    const int32_t nb = (int32_t)std::min<int64_t>(P.batch, slice_count - p * P.batch);
+    if (T > 0) n += 1;  // stage_leaves_kernel
+    for (int32_t t = 0; t < T; ++t)
+      if (P.leafdesc[t].tiled && !(p > 0 && !P.tensors[t].batched)) n += 1;
+    for (const StepRec& st : P.steps) {
+      if (!st.batched && p > 0) continue;
+      const int32_t nbs = st.batched ? nb : 1;
+      if (st.cls == TN_CLASS_TC) n += tc_launches(st.m, st.n, st.k, nbs, form, pairs);
+      else if (st.cls == TN_CLASS_SPLITK) n += 2;
+      else if (st.cls == TN_CLASS_SIMT) n += st.ksplit > 1 ? 2 : 1;
+      else n += 1;
+    }
+    n += 1;  // the slice sum (or the output widening)
+  }
+  *out = n;
+  return TN_OK;
+}
+
 tn_status tn_plan_step(tn_plan_t plan, int32_t s, tn_step_info* out) {
   if (!plan || !out || s < 0 || s >= (int32_t)plan->P.steps.size()) {
     set_error("bad plan or step");

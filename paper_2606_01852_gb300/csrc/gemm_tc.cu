@@ -1181,7 +1181,7 @@ __device__ __forceinline__ void cluster_sync_all() {
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
     contract_tcb2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                         StepArgs a, int* err) {
+                         StepArgs a, int64_t t_first, int* err) {
   constexpr int STAGES = CB2::STAGES, BK = CB2::BK, ROWB = CB2::ROWB, CK = CB2::CK;
   constexpr int PA = CB2::PLANE_A, PB = CB2::PLANE_B, STAGE = CB2::STAGE;
   extern __shared__ uint8_t smem_raw[];
@@ -1199,7 +1199,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tiles_m = (a.m + 2 * BM - 1) / (2 * BM), tiles_n = (a.n + BN - 1) / BN;
-  const int64_t t = blockIdx.x >> 1;
+  const int64_t t = t_first + (blockIdx.x >> 1);  // this launch's tiles start at t_first
   const int64_t per_group = CB2::GROUP * tiles_n;
   const int64_t first_m = (t / per_group) * CB2::GROUP;
   const int64_t gm = tiles_m - first_m < CB2::GROUP ? tiles_m - first_m : CB2::GROUP;
@@ -1451,6 +1451,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
 // within 1.5 % (the per-tile form ahead), at k >= 16384 the per-tile form is 4-8 % faster
 // (four ring stages instead of three, the per-tile cost being small there).
 constexpr int64_t kPairsPersistentMaxK = 2048;
+// waves of resident clusters per launch of the per-tile paired kernel (0: one launch)
+constexpr int kPairWaves = 8;
 // steps with k <= 64 run contract_tcb_shallow_kernel
 constexpr bool kShallowKernel = true;
 struct CB2P {
@@ -2486,6 +2488,26 @@ cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// Tiles per batch entry in one launch of the per-tile paired kernel: about kPairWaves waves
+// of the clusters that can be resident at once. The clusters of a launch start together and
+// stay near each other in k, so the panels they share come from DRAM about once per wave
+// (one launch for a whole deep step let them drift apart: 2.4x the DRAM traffic).
+int64_t pair_band_tiles(int64_t pair_tiles, int32_t nb) {
+  static const int clusters = [] {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(CB2::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = CB2::SMEM;
+    cudaFuncSetAttribute(contract_tcb2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB2::SMEM);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, contract_tcb2_kernel, &cfg) != cudaSuccess || n <= 0) n = 0;
+    return n;
+  }();
+  if (kPairWaves <= 0 || clusters <= 0 || nb <= 0) return pair_tiles;
+  const int64_t want = (int64_t(clusters) * kPairWaves + nb - 1) / nb;
+  return want < pair_tiles ? want : pair_tiles;
+}
+
 cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st, bool pairs) {
   static const cudaError_t configured = [] {
     cudaError_t e = cudaFuncSetAttribute(contract_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB::SMEM);
@@ -2528,9 +2550,15 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st,
         return cudaGetLastError();
       }
     }
-    dim3 grid(static_cast<unsigned>(2 * pair_tiles), static_cast<unsigned>(nb));
-    contract_tcb2_kernel<<<grid, CB2::THREADS, CB2::SMEM, st>>>(ta, tb, a, err);
-    return cudaGetLastError();
+    const int64_t per_launch = pair_band_tiles(pair_tiles, nb);
+    for (int64_t t0 = 0; t0 < pair_tiles; t0 += per_launch) {
+      const int64_t cnt = pair_tiles - t0 < per_launch ? pair_tiles - t0 : per_launch;
+      dim3 grid(static_cast<unsigned>(2 * cnt), static_cast<unsigned>(nb));
+      contract_tcb2_kernel<<<grid, CB2::THREADS, CB2::SMEM, st>>>(ta, tb, a, t0, err);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   if (!make_map_split(&ta, a.A, a.m, a.k, ca, a.a_plane, BM) || !make_map_split(&tb, a.B, a.n, a.k, cb, a.b_plane, BN))
     return cudaErrorInvalidValue;
@@ -2579,6 +2607,13 @@ bool tc_step_ok(int64_t m, int64_t n, int64_t k, int32_t prec) {
   // masks the columns): a quarter-filled tile still beats the CUDA cores several-fold
   return m >= BM && n >= 16 && k >= 8 && k % kq == 0 && k <= (int64_t(1) << 30) && m < (int64_t(1) << 31) &&
          n < (int64_t(1) << 31);
+}
+
+int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, bool pairs) {
+  if (prec != TN_C64_BF16X3 || !pairs || k <= CBP::MAX_K || m < 2 * BM || k <= kPairsPersistentMaxK) return 1;
+  const int64_t pair_tiles = ((m + 2 * BM - 1) / (2 * BM)) * ((n + BN - 1) / BN);
+  const int64_t per = pair_band_tiles(pair_tiles, nb);
+  return (pair_tiles + per - 1) / per;
 }
 
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,

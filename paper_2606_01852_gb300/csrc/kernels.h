@@ -114,5 +114,8 @@ constexpr int32_t kPrecBF16x3M = 103;
 // pairs of SMs (contract_tcb2_kernel)
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
                                cudaStream_t st, bool pairs = true);
+// kernel launches launch_contract_tc makes for such a step (more than one for the deep
+// paired-SM steps, launched in bands of tiles)
+int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, bool pairs);
 
 }  // namespace tn
