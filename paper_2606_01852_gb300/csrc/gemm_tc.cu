@@ -385,7 +385,7 @@ __device__ __forceinline__ void store_block(float* C, int64_t plane, int split, 
 template <int SPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                       StepArgs a, int* err) {
+                       StepArgs a, int64_t t_first, int* err) {
   using G = Cfg<SPLIT>;
   constexpr int STAGES = G::STAGES, BK = G::BK, ROWB = G::ROWB;
   constexpr int TILE_A = G::TILE_A, TILE_B = G::TILE_B, STAGE = G::STAGE;
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // grouped raster over output tiles for L2 reuse of A and B tiles
   const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
-  const int64_t t = blockIdx.x;
+  const int64_t t = t_first + blockIdx.x;  // this launch's tiles start at t_first
   const int64_t per_group = GROUP_M * tiles_n;
   const int64_t first_m = (t / per_group) * GROUP_M;
   const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
@@ -615,7 +615,7 @@ struct C3 {
 
 __global__ void __launch_bounds__(C3::THREADS, 1)
     contract_tc3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                        StepArgs a, int* err) {
+                        StepArgs a, int64_t t_first, int* err) {
   constexpr int STAGES = C3::STAGES, BK = C3::BK, ROWB = C3::ROWB, CK = C3::CK;
   constexpr int TILE_A = C3::TILE_A, TILE_B = C3::TILE_B, STAGE = C3::STAGE;
   extern __shared__ uint8_t smem_raw[];
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
-  const int64_t t = blockIdx.x;
+  const int64_t t = t_first + blockIdx.x;  // this launch's tiles start at t_first
   const int64_t per_group = GROUP_M * tiles_n;
   const int64_t first_m = (t / per_group) * GROUP_M;
   const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
@@ -924,7 +924,7 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
 
 __global__ void __launch_bounds__(CB::THREADS, 1)
     contract_tcb_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                        StepArgs a, int* err) {
+                        StepArgs a, int64_t t_first, int* err) {
   constexpr int STAGES = CB::STAGES, BK = CB::BK, ROWB = CB::ROWB, CK = CB::CK;
   constexpr int PLANE = CB::PLANE, STAGE = CB::STAGE;
   extern __shared__ uint8_t smem_raw[];
@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
-  const int64_t t = blockIdx.x;
+  const int64_t t = t_first + blockIdx.x;  // this launch's tiles start at t_first
   const int64_t per_group = GROUP_M * tiles_n;
   const int64_t first_m = (t / per_group) * GROUP_M;
   const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
@@ -1451,8 +1451,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
 // within 1.5 % (the per-tile form ahead), at k >= 16384 the per-tile form is 4-8 % faster
 // (four ring stages instead of three, the per-tile cost being small there).
 constexpr int64_t kPairsPersistentMaxK = 2048;
-// waves of resident clusters per launch of the per-tile paired kernel (0: one launch)
-constexpr int kPairWaves = 8;
+// waves of resident CTAs (or CTA pairs) per launch of the one-tile-per-CTA kernels, which
+// launch a deep step in bands of tiles (0: one launch for the step)
+constexpr int kBandWaves = 8;
 // steps with k <= 64 run contract_tcb_shallow_kernel
 constexpr bool kShallowKernel = true;
 struct CB2P {
@@ -1791,7 +1792,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 __global__ void __launch_bounds__(CB3::THREADS, 1)
     contract_tcb3m_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                          StepArgs a, int* err) {
+                          StepArgs a, int64_t t_first, int* err) {
   constexpr int SLOTS = CB3::SLOTS, BK = CB3::BK, ROWB = CB3::ROWB, CK = CB3::CK;
   constexpr int PLANE = CB3::PLANE, SLOT = CB3::SLOT;
   extern __shared__ uint8_t smem_raw[];
@@ -1805,7 +1806,7 @@ __global__ void __launch_bounds__(CB3::THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
-  const int64_t t = blockIdx.x;
+  const int64_t t = t_first + blockIdx.x;  // this launch's tiles start at t_first
   const int64_t per_group = GROUP_M * tiles_n;
   const int64_t first_m = (t / per_group) * GROUP_M;
   const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
@@ -2438,6 +2439,36 @@ bool make_map_split3m(CUtensorMap* map, const float* base, int64_t rows, int64_t
   return r == CUDA_SUCCESS;
 }
 
+// Tiles per batch entry in one launch of a one-tile-per-CTA kernel (one CTA per SM by its
+// shared memory): about kBandWaves waves of the SMs, for the reason given at
+// pair_band_tiles.
+int64_t sm_band_tiles(int64_t tiles, int32_t nb) {
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+      n = 0;
+    return n;
+  }();
+  if (kBandWaves <= 0 || sms <= 0 || nb <= 0) return tiles;
+  const int64_t want = (int64_t(sms) * kBandWaves + nb - 1) / nb;
+  return want < tiles ? want : tiles;
+}
+
+// Launch kern over `tiles` tiles x nb batch entries in bands of sm_band_tiles.
+template <typename Kern, typename... Args>
+cudaError_t launch_bands(Kern kern, int64_t tiles, int32_t nb, int threads, int smem, cudaStream_t st,
+                         const CUtensorMap& ta, const CUtensorMap& tb, const StepArgs& a, int* err) {
+  const int64_t per = sm_band_tiles(tiles, nb);
+  for (int64_t t0 = 0; t0 < tiles; t0 += per) {
+    const int64_t cnt = tiles - t0 < per ? tiles - t0 : per;
+    kern<<<dim3(static_cast<unsigned>(cnt), static_cast<unsigned>(nb)), threads, smem, st>>>(ta, tb, a, t0, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_tcb3m(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
   // the shared-memory opt-in, once per process (thread-safe static initialisation)
   static const cudaError_t configured =
@@ -2450,9 +2481,7 @@ cudaError_t launch_tcb3m(const StepArgs& a, int32_t nb, int* err, cudaStream_t s
       !make_map_split3m(&tb, a.B, a.n, a.k, cb, a.b_plane, BN))
     return cudaErrorInvalidValue;
   const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
-  dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));
-  contract_tcb3m_kernel<<<grid, CB3::THREADS, CB3::SMEM, st>>>(ta, tb, a, err);
-  return cudaGetLastError();
+  return launch_bands(contract_tcb3m_kernel, tiles, nb, CB3::THREADS, CB3::SMEM, st, ta, tb, a, err);
 }
 
 template <int SPLIT>
@@ -2467,9 +2496,7 @@ cudaError_t launch_split(const StepArgs& a, int32_t nb, int* err, cudaStream_t s
   if (!make_map(&ta, a.A, a.m, a.k, pa, a.a_plane, BM, bk) || !make_map(&tb, a.B, a.n, a.k, pb, a.b_plane, BN, bk))
     return cudaErrorInvalidValue;
   const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
-  dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));
-  contract_tc_kernel<SPLIT><<<grid, NTHREADS, Cfg<SPLIT>::SMEM, st>>>(ta, tb, a, err);
-  return cudaGetLastError();
+  return launch_bands(contract_tc_kernel<SPLIT>, tiles, nb, NTHREADS, Cfg<SPLIT>::SMEM, st, ta, tb, a, err);
 }
 
 cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
@@ -2483,12 +2510,10 @@ cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st)
       !make_map(&tb, a.B, a.n, a.k, pb, a.b_plane, BN, C3::BK))
     return cudaErrorInvalidValue;
   const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
-  dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));
-  contract_tc3_kernel<<<grid, C3::THREADS, C3::SMEM, st>>>(ta, tb, a, err);
-  return cudaGetLastError();
+  return launch_bands(contract_tc3_kernel, tiles, nb, C3::THREADS, C3::SMEM, st, ta, tb, a, err);
 }
 
-// Tiles per batch entry in one launch of the per-tile paired kernel: about kPairWaves waves
+// Tiles per batch entry in one launch of the per-tile paired kernel: about kBandWaves waves
 // of the clusters that can be resident at once. The clusters of a launch start together and
 // stay near each other in k, so the panels they share come from DRAM about once per wave
 // (one launch for a whole deep step let them drift apart: 2.4x the DRAM traffic).
@@ -2503,8 +2528,8 @@ int64_t pair_band_tiles(int64_t pair_tiles, int32_t nb) {
     if (cudaOccupancyMaxActiveClusters(&n, contract_tcb2_kernel, &cfg) != cudaSuccess || n <= 0) n = 0;
     return n;
   }();
-  if (kPairWaves <= 0 || clusters <= 0 || nb <= 0) return pair_tiles;
-  const int64_t want = (int64_t(clusters) * kPairWaves + nb - 1) / nb;
+  if (kBandWaves <= 0 || clusters <= 0 || nb <= 0) return pair_tiles;
+  const int64_t want = (int64_t(clusters) * kBandWaves + nb - 1) / nb;
   return want < pair_tiles ? want : pair_tiles;
 }
 
@@ -2585,9 +2610,7 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st,
     contract_tcb_persistent_kernel<<<grid, CB::THREADS, CBP::SMEM, st>>>(ta, tb, a, nb, err);
     return cudaGetLastError();
   }
-  dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(nb));
-  contract_tcb_kernel<<<grid, CB::THREADS, CB::SMEM, st>>>(ta, tb, a, err);
-  return cudaGetLastError();
+  return launch_bands(contract_tcb_kernel, tiles, nb, CB::THREADS, CB::SMEM, st, ta, tb, a, err);
 }
 
 }  // namespace
@@ -2610,10 +2633,18 @@ bool tc_step_ok(int64_t m, int64_t n, int64_t k, int32_t prec) {
 }
 
 int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, bool pairs) {
-  if (prec != TN_C64_BF16X3 || !pairs || k <= CBP::MAX_K || m < 2 * BM || k <= kPairsPersistentMaxK) return 1;
-  const int64_t pair_tiles = ((m + 2 * BM - 1) / (2 * BM)) * ((n + BN - 1) / BN);
-  const int64_t per = pair_band_tiles(pair_tiles, nb);
-  return (pair_tiles + per - 1) / per;
+  if (prec == TN_C64_BF16X3) {
+    if (k <= CBP::MAX_K) return 1;  // persistent kernels
+    if (pairs && m >= 2 * BM) {
+      if (k <= kPairsPersistentMaxK) return 1;
+      const int64_t pair_tiles = ((m + 2 * BM - 1) / (2 * BM)) * ((n + BN - 1) / BN);
+      const int64_t per = pair_band_tiles(pair_tiles, nb);
+      return (pair_tiles + per - 1) / per;
+    }
+  }
+  const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+  const int64_t per = sm_band_tiles(tiles, nb);
+  return (tiles + per - 1) / per;
 }
 
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
