@@ -229,3 +229,25 @@ def test_cost_model_rates_drive_the_kernel_choice():
     finally:
         tn.binding.set_cost_model(old["hbm_bytes_per_s"], old["simt_flops"], old["tc_flops"])
     assert tn.binding.cost_model() == old
+
+
+def test_plan_launches_counts_the_call():
+    """tn_plan_launches on host-only plans (no paired-SM bands without a device): per pass one
+    staging launch, one per tiled leaf, one per step (two for split-k and k-split steps; the
+    slice-invariant steps only in the first pass) and one for the slice sum."""
+    tn = ensure_built()
+    w = workloads.random_circuit(3, 4, 8, 3, n_sliced=4)
+    for batch in (16, 3):
+        plan = tn.Plan(w.net, w.path, w.sliced, max_slice_batch=batch, host_only=True)
+        info = plan.info()
+        steps = [plan.step(s) for s in range(info["n_steps"])]
+        per = [2 if (st["cls"] == tn.TN_CLASS_SPLITK or st["ksplit"] > 1) else 1 for st in steps]
+        leaves = [plan.tensor(t) for t in range(plan.n_leaves)]
+        tiled = sum(1 for x in leaves if x["tiled"])
+        tiled_b = sum(1 for x in leaves if x["tiled"] and x["batched"])
+        for count in (1, 5, 16):
+            passes = -(-count // info["slice_batch"])
+            batched = sum(p for p, st in zip(per, steps) if st["batched"])
+            want = passes * 2 + sum(per) + (passes - 1) * batched + tiled + (passes - 1) * tiled_b
+            assert plan.launches_per_call(count) == want, (batch, count)
+        plan.destroy()
