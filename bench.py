@@ -116,7 +116,8 @@ def measure_local_peaks(tn, seconds=2.0):
     dense TF32 rate (torch.matmul of 8192^2 FP32 matrices with TF32 allowed, 2 * 8192^3
     flops) and the FP32 FMA rate (tn_measure_ffma: 8 independent FMA chains per thread,
     4 x 256 threads per SM), each as a burst (best of 10 CUDA-event timings) and sustained
-    (back to back for `seconds`, the mean), with the SM clock sampled meanwhile."""
+    (back to back for `seconds`, the mean), and the FP64 FMA rate (tn_measure_dfma, the same
+    probe in double precision, burst), with the SM clock sampled meanwhile."""
     import torch
     out = {}
     clocks = ClockSampler(torch.cuda.current_device())
@@ -150,12 +151,14 @@ def measure_local_peaks(tn, seconds=2.0):
     iters = max(1 << 18, min(1 << 24, int((1 << 18) * seconds * 1e3 / max(ms1, 1e-3))))
     out["ffma_tflops"] = max(rates) / 1e12
     out["ffma_tflops_sustained"] = tn.binding.measure_ffma(iters)[0] / 1e12
+    # FP64 (the cross-slice sum's arithmetic), best of 5 short launches
+    out["dfma_tflops"] = max(tn.binding.measure_dfma(1 << 12)[0] for _ in range(5)) / 1e12
     ck = clocks.stop()
     out["sm_mhz_median"] = ck.get("sm_mhz")
     out["reasons"] = ck.get("reasons")
     out["how"] = ("tf32: torch.matmul 8192^3 FP32 with TF32 allowed, best of 10 (burst) and back to back "
                   f"for {seconds:g} s (sustained); ffma: tn_measure_ffma, best of 10 (burst) and one "
-                  f"{seconds:g} s launch (sustained); CUDA events")
+                  f"{seconds:g} s launch (sustained); dfma: tn_measure_dfma, best of 5; CUDA events")
     return out
 
 

@@ -203,6 +203,10 @@ tn_status tn_cost_model_get(tn_cost_model* out);
  * Synchronous; 0 < iters <= 2^24. */
 tn_status tn_measure_ffma(int64_t iters, double* flops_per_s, double* ms, void* stream);
 
+/* The same probe in FP64 (double FMA chains): this GPU's FP64 rate, which the cross-slice
+ * sum runs at. Synchronous; 0 < iters <= 2^24. */
+tn_status tn_measure_dfma(int64_t iters, double* flops_per_s, double* ms, void* stream);
+
 /* Build a plan: validate, analyse each step (Sec. II-B), run the backward mode
  * reordering pass (Sec. IV-A), choose a kernel per step, assign every tensor a
  * place in one workspace by liveness, and (unless TN_PLAN_HOST_ONLY) allocate that

@@ -167,6 +167,7 @@ def _load():
         "tn_plan_check_staging": [vp, i64],
         "tn_cost_model_get": [C.POINTER(tn_cost_model)],
         "tn_measure_ffma": [i64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
+        "tn_measure_dfma": [i64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -475,6 +476,13 @@ def set_cost_model(hbm_bytes_per_s, simt_flops, tc_flops):
     """Replace the planner's Eq. 6 rates (tn_cost_model_set); tc_flops = [TF32, 3xTF32, BF16x3]."""
     m = tn_cost_model(hbm_bytes_per_s, simt_flops, (C.c_double * 3)(*tc_flops))
     check(lib.tn_cost_model_set(C.byref(m)))
+
+
+def measure_dfma(iters=1 << 14, stream=None):
+    """FP64 FMA rate of the current device (tn_measure_dfma): (flop/s, ms)."""
+    f, ms = C.c_double(), C.c_double()
+    check(lib.tn_measure_dfma(int(iters), C.byref(f), C.byref(ms), _ptr_stream(stream)))
+    return f.value, ms.value
 
 
 def measure_ffma(iters=1 << 18, stream=None):

@@ -235,6 +235,21 @@ __global__ void __launch_bounds__(256) ffma_probe_kernel(int64_t iters, float m,
   if (s == -1.0f) out[blockIdx.x] = s;
 }
 
+// FP64 FMA rate probe: the same form as ffma_probe_kernel in double precision.
+__global__ void __launch_bounds__(256) dfma_probe_kernel(int64_t iters, double m, double c, double* out) {
+  double x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 0.05 + 1e-3 * j + 1e-6 * threadIdx.x;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fma(x[j], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  if (s == -1.0) out[blockIdx.x] = s;
+}
+
 }  // namespace tn
 
 using namespace tn;
@@ -751,9 +766,11 @@ tn_status tn_cost_model_get(tn_cost_model* out) {
   return TN_OK;
 }
 
-tn_status tn_measure_ffma(int64_t iters, double* flops_per_s, double* ms, void* stream) {
+// Time one FMA-chain probe launch (4 CTAs of 256 threads per SM, 8 chains per thread).
+static tn_status measure_fma(bool fp64, int64_t iters, double* flops_per_s, double* ms, void* stream) {
+  const char* name = fp64 ? "tn_measure_dfma" : "tn_measure_ffma";
   if (iters <= 0 || iters > (int64_t(1) << 24) || !flops_per_s) {
-    set_error("tn_measure_ffma: needs 0 < iters <= 2^24 and an output pointer");
+    set_error(std::string(name) + ": needs 0 < iters <= 2^24 and an output pointer");
     return TN_ERR_INVALID;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -766,7 +783,8 @@ tn_status tn_measure_ffma(int64_t iters, double* flops_per_s, double* ms, void* 
   const int grid = 4 * sms;
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
   if (e == cudaSuccess) {
-    ffma_probe_kernel<<<grid, 256, 0, st>>>(iters, 0.999999f, 1e-7f, nullptr);
+    if (fp64) dfma_probe_kernel<<<grid, 256, 0, st>>>(iters, 0.999999999, 1e-10, nullptr);
+    else ffma_probe_kernel<<<grid, 256, 0, st>>>(iters, 0.999999f, 1e-7f, nullptr);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -776,12 +794,20 @@ tn_status tn_measure_ffma(int64_t iters, double* flops_per_s, double* ms, void* 
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) {
-    set_error(std::string("tn_measure_ffma: ") + cudaGetErrorString(e));
+    set_error(std::string(name) + ": " + cudaGetErrorString(e));
     return TN_ERR_CUDA;
   }
   *flops_per_s = 2.0 * 8.0 * double(iters) * double(grid) * 256.0 / (double(t) * 1e-3);
   if (ms) *ms = t;
   return TN_OK;
+}
+
+tn_status tn_measure_ffma(int64_t iters, double* flops_per_s, double* ms, void* stream) {
+  return measure_fma(false, iters, flops_per_s, ms, stream);
+}
+
+tn_status tn_measure_dfma(int64_t iters, double* flops_per_s, double* ms, void* stream) {
+  return measure_fma(true, iters, flops_per_s, ms, stream);
 }
 
 tn_status tn_plan_profile(tn_plan_t plan, int32_t enable) {

@@ -152,3 +152,14 @@ def test_one_slice_output_exact_fp64(tn, cplx):
     for g, w in parts:
         assert np.array_equal(np.ascontiguousarray(g).view(np.uint64), np.ascontiguousarray(w).view(np.uint64))
     plan.destroy()
+
+
+def test_fma_rate_probes(tn):
+    """The FP32 and FP64 FMA probes return positive rates below what the SMs could issue at
+    the maximum clock (152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s), and FP64
+    well below FP32 on this part (the cross-slice sum's arithmetic)."""
+    f32, ms32 = tn.binding.measure_ffma(1 << 16)
+    f64, ms64 = tn.binding.measure_dfma(1 << 10)
+    assert ms32 > 0 and ms64 > 0
+    assert 1e12 < f32 < 81e12
+    assert 0 < f64 < f32
