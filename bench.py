@@ -418,6 +418,10 @@ def run_ours(args):
         else:
             plan.contract_slices(ins, b, c, outs[j], ls[j:j + 1], stream)
 
+    if args.autotune:
+        # per paired-SM step, the faster of paired SMs and one SM per tile (the same bits)
+        plan.autotune(ins, outs[0], stream)
+        torch.cuda.synchronize()
     for j in range(args.warmup):
         step(j)
     torch.cuda.synchronize()
@@ -561,7 +565,9 @@ def run_ours(args):
                          "intermediates are GBs", "parallelism": f"replicas{ws}",
                    **({"graph": "each step one replay of a CUDA graph of the call (tn_contract_graph)"}
                       if use_graph else {}),
-                   **({"tiles": "one SM per tensor-core tile"} if args.single_sm_tiles else {})},
+                   **({"tiles": "one SM per tensor-core tile"} if args.single_sm_tiles else {}),
+                   **({"autotune": [plan.step(s)["single_sm"] for s in range(info["n_steps"])
+                                    if plan.step(s)["cls"] == tn.TN_CLASS_TC]} if args.autotune else {})},
         "slices_per_s": ws * slices_per_step / (ms_max / 1e3),
         "projected_full_contraction_s": (n_sl / (slices_per_step / (ms_max / 1e3)) if per_step < n_sl
                                          else ms_max / 1e3),
@@ -908,6 +914,8 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=sorted(PREC),
                     help="GEMM form: bf16x3 (default), 3xtf32, tf32, fp32 (the plain CUDA-core form)")
     ap.add_argument("--max-slice-batch", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="time paired SMs against one SM per tile for each such step first (tn_plan_autotune)")
     ap.add_argument("--graph", action="store_true",
                     help="whole-contraction workloads: replay each step from a CUDA graph (tn_contract_graph)")
     ap.add_argument("--single-sm-tiles", action="store_true",

@@ -153,7 +153,7 @@ typedef struct {
   int32_t n_row_dims, n_col_dims;
   int64_t row_ext[12], row_stride[12], col_ext[12], col_stride[12];
   int32_t ksplit;          /* SIMT steps: k cut in this many parts (then two launches) */
-  int32_t reserved;
+  int32_t single_sm;       /* tensor-core steps: 1 if kept on one SM per tile (tn_plan_autotune) */
 } tn_step_info;
 
 /* How a tensor's copies are stored in the workspace. PLANAR: FP32 (complex: the real
@@ -254,6 +254,14 @@ tn_status tn_plan_tensor(tn_plan_t plan, int32_t id, tn_tensor_info* out);
  * NULL = legacy default stream). Calls on one plan must not overlap in time. */
 tn_status tn_contract(tn_plan_t plan, const void* const* inputs, void* output,
                       double* out_log_scale, void* stream);
+
+/* Choose, per BF16x3 (4M) tensor-core step that the paired-SM kernels take, between paired
+ * SMs and one SM per tile by timing both: two runs of the plan's first pass (its first
+ * slice_batch slices) in each form, per-step CUDA-event times, the faster kept for later
+ * calls. Both forms give the same bits, so results do not change. Writes into output (the
+ * caller's, sized as for tn_contract) as a side effect; the caller's per-step profile is set
+ * aside and restored. Synchronous. A no-op for other forms or with TN_PLAN_SINGLE_SM_TILES. */
+tn_status tn_plan_autotune(tn_plan_t plan, const void* const* inputs, void* output, void* stream);
 
 /* As tn_contract (all slices, device buffers), with the call's launches replayed from a
  * CUDA graph: the first call with a given set of input pointers, output, log_scale and

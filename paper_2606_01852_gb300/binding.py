@@ -70,7 +70,7 @@ class tn_step_info(C.Structure):
                 ("n_row_dims", C.c_int32), ("n_col_dims", C.c_int32),
                 ("row_ext", C.c_int64 * 12), ("row_stride", C.c_int64 * 12),
                 ("col_ext", C.c_int64 * 12), ("col_stride", C.c_int64 * 12),
-                ("ksplit", C.c_int32), ("reserved", C.c_int32)]
+                ("ksplit", C.c_int32), ("single_sm", C.c_int32)]
 
 
 class tn_tensor_info(C.Structure):
@@ -139,6 +139,7 @@ def _load():
         "tn_plan_tensor": [vp, i32, C.POINTER(tn_tensor_info)],
         "tn_contract": [vp, C.POINTER(vp), vp, vp, vp],
         "tn_contract_graph": [vp, C.POINTER(vp), vp, vp, vp],
+        "tn_plan_autotune": [vp, C.POINTER(vp), vp, vp],
         "tn_contract_slices": [vp, C.POINTER(vp), i64, i64, vp, vp, vp],
         "tn_contract_host": [vp, C.POINTER(vp), vp, vp, vp],
         "tn_contract_slices_host": [vp, C.POINTER(vp), i64, i64, vp, vp, vp],
@@ -287,6 +288,7 @@ class Plan:
         check(lib.tn_plan_step(self.handle, s, C.byref(i)))
         d = {f: getattr(i, f) for f, _ in tn_step_info._fields_[:7]}
         d["ksplit"] = i.ksplit
+        d["single_sm"] = i.single_sm
         d["rows"] = [(i.row_ext[x], i.row_stride[x]) for x in range(i.n_row_dims)]
         d["cols"] = [(i.col_ext[x], i.col_stride[x]) for x in range(i.n_col_dims)]
         return d
@@ -306,6 +308,10 @@ class Plan:
     def contract(self, inputs, output, log_scale=None, stream=None):
         check(lib.tn_contract(self.handle, self._inputs(inputs), _ptr(output), _ptr(log_scale),
                               _ptr_stream(stream)))
+
+    def autotune(self, inputs, output, stream=None):
+        """tn_plan_autotune: per paired-SM step, keep the faster of paired SMs and one SM."""
+        check(lib.tn_plan_autotune(self.handle, self._inputs(inputs), _ptr(output), _ptr_stream(stream)))
 
     def contract_graph(self, inputs, output, log_scale=None, stream=None):
         """tn_contract_graph: as contract, replayed from a CUDA graph captured on the first call

@@ -194,7 +194,7 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
         const int32_t form = (P.policy.prec == TN_C64_BF16X3 && P.policy.complex_mult == 3) ? kPrecBF16x3M
                                                                                               : P.policy.prec;
         TN_CUDA_TRY(launch_contract_tc(a, nbs, form, cplx, errw, st,
-                                       (P.policy.flags & TN_PLAN_SINGLE_SM_TILES) == 0));
+                                       (P.policy.flags & TN_PLAN_SINGLE_SM_TILES) == 0 && !sr.single_sm));
       } else if (sr.cls == TN_CLASS_STREAM) {
         launch_contract_stream(a, nbs, cplx, P.num_sms, errw, st);
       } else if (sr.cls == TN_CLASS_SPLITK) {
@@ -377,7 +377,7 @@ tn_status tn_plan_launches(tn_plan_t plan, int64_t slice_count, int64_t* out) {
     for (const StepRec& st : P.steps) {
       if (!st.batched && p > 0) continue;
       const int32_t nbs = st.batched ? nb : 1;
-      if (st.cls == TN_CLASS_TC) n += tc_launches(st.m, st.n, st.k, nbs, form, pairs);
+      if (st.cls == TN_CLASS_TC) n += tc_launches(st.m, st.n, st.k, nbs, form, pairs && !st.single_sm);
       else if (st.cls == TN_CLASS_SPLITK) n += 2;
       else if (st.cls == TN_CLASS_SIMT) n += st.ksplit > 1 ? 2 : 1;
       else n += 1;
@@ -410,7 +410,7 @@ tn_status tn_plan_step(tn_plan_t plan, int32_t s, tn_step_info* out) {
     out->col_stride[d] = d < st.cols.n ? st.cols.stride[d] : 0;
   }
   out->ksplit = st.ksplit;
-  out->reserved = 0;
+  out->single_sm = st.single_sm ? 1 : 0;
   return TN_OK;
 }
 
@@ -451,6 +451,60 @@ tn_status tn_contract(tn_plan_t plan, const void* const* inputs, void* output, d
     return TN_ERR_INVALID;
   }
   return tn_contract_slices(plan, inputs, 0, plan->P.n_slices, output, out_log_scale, stream);
+}
+
+tn_status tn_plan_autotune(tn_plan_t plan, const void* const* inputs, void* output, void* stream) {
+  if (!plan || !inputs || !output) {
+    set_error("null plan, inputs or output");
+    return TN_ERR_INVALID;
+  }
+  Plan& P = plan->P;
+  if (!P.dev) {
+    set_error("plan was built with TN_PLAN_HOST_ONLY (no device workspace)");
+    return TN_ERR_INVALID;
+  }
+  // the steps with a choice: BF16x3 4M tensor-core steps that the paired-SM kernels take
+  std::vector<int32_t> cand;
+  const bool bf16x3_4m = P.policy.prec == TN_C64_BF16X3 && P.policy.complex_mult != 3;
+  if (bf16x3_4m && (P.policy.flags & TN_PLAN_SINGLE_SM_TILES) == 0)
+    for (int32_t s = 0; s < (int32_t)P.steps.size(); ++s) {
+      const StepRec& st = P.steps[s];
+      if (st.cls == TN_CLASS_TC && tc_launches(st.m, st.n, st.k, 1, TN_C64_BF16X3, true) >= 1 && st.m >= 256 &&
+          st.k > 256)
+        cand.push_back(s);
+    }
+  if (cand.empty()) return TN_OK;
+  // the caller's profile is set aside and restored
+  const bool prof_was = P.prof_on;
+  tn_profile acc_keep{};
+  tn_status s = tn_plan_profile_read(plan, &acc_keep, 1);
+  if (s != TN_OK) return s;
+  const std::vector<double> steps_keep = P.prof_last_step_ms;
+  const int64_t count = std::min<int64_t>(P.batch, P.n_slices);
+  std::vector<double> t[2];
+  std::string err;
+  for (int v = 0; v < 2 && s == TN_OK; ++v) {
+    for (int32_t c : cand) P.steps[c].single_sm = v == 1;
+    P.prof_on = false;
+    s = run_slices(P, inputs, 0, count, output, nullptr, stream, err);  // warm
+    if (s != TN_OK) break;
+    P.prof_on = true;
+    s = run_slices(P, inputs, 0, count, output, nullptr, stream, err);
+    if (s != TN_OK) break;
+    tn_profile tmp{};
+    s = tn_plan_profile_read(plan, &tmp, 1);
+    t[v] = P.prof_last_step_ms;
+  }
+  P.prof_on = prof_was;
+  P.prof_acc = acc_keep;
+  P.prof_last_step_ms = steps_keep;
+  if (s != TN_OK) {
+    for (int32_t c : cand) P.steps[c].single_sm = false;
+    if (!err.empty()) set_error(err);
+    return s;
+  }
+  for (int32_t c : cand) P.steps[c].single_sm = t[1][c] < t[0][c];
+  return TN_OK;
 }
 
 tn_status tn_contract_graph(tn_plan_t plan, const void* const* inputs, void* output, double* out_log_scale,

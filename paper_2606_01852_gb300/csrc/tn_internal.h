@@ -84,6 +84,7 @@ struct StepRec {
   bool batched = false;
   OffsetMap rows{}, cols{};
   int32_t ksplit = 1;  // SIMT steps too few tiles to fill the GPU: k cut in this many parts
+  bool single_sm = false;  // tensor-core step kept on one SM per tile (tn_plan_autotune's choice)
 };
 
 struct Plan {

@@ -307,3 +307,21 @@ def test_paired_sm_tiles_random_shapes(tn, seed):
         assert rel_err(got, oracle.contract(net, path, sliced)) < 5e-5
     pair.destroy()
     one.destroy()
+
+
+def test_autotune_keeps_the_bits(tn):
+    """tn_plan_autotune times paired SMs against one SM per tile for each paired-SM step and
+    keeps the faster; the result of the plan is the same bits before and after, and the launch
+    count follows the choice."""
+    net, path, sliced = gemm_network((4096,), (2048,), (4104,), [("m", 0), ("n", 0)], seed=51, sliced_dim=2)
+    plan = tn.Plan(net, path, sliced, prec="bf16x3")
+    assert plan.step(0)["cls"] == tn.TN_CLASS_TC and plan.step(0)["single_sm"] == 0
+    before, _ = run(tn, plan, net)
+    ins = [torch.tensor(np.asarray(t), dtype=torch.complex64, device="cuda") for t in net.tensors]
+    scratch = torch.zeros(plan.out_shape, dtype=torch.complex128, device="cuda")
+    plan.autotune(ins, scratch)
+    assert plan.step(0)["single_sm"] in (0, 1)
+    after, _ = run(tn, plan, net)
+    assert np.array_equal(np.ascontiguousarray(before).view(np.uint64), np.ascontiguousarray(after).view(np.uint64))
+    assert plan.launches_per_call() >= 4
+    plan.destroy()
