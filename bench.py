@@ -61,8 +61,13 @@ WORKLOAD_DESC = {
     "rc40open": "the 40-qubit rc40 circuit with the 2x2 corner qubits (30, 31, 38, 39) left open: "
                 "16 correlated amplitudes per contraction, greedy path, 8 sliced labels (256 slices), "
                 "complex64",
+    "isingsq20": "partition function of a +-J Ising spin glass on an open 20x20 square lattice (400 spins, "
+                 "beta 0.44), greedy path (largest intermediate 2^29), real FP32 storage with "
+                 "per-intermediate exponent scaling",
 }
 PREC = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x3m": 3}
+# the real forms (tn_precision R32_*) of a real network's --prec
+REAL_PREC = {"fp32": 4, "tf32": 5, "3xtf32": 6}
 # forms run with the 3M complex product (three real products per complex MAC, not four)
 THREE_M = {"bf16x3m"}
 # arithmetic of each form (complex64 storage; products as named, FP32 accumulation)
@@ -382,18 +387,26 @@ def run_ours(args):
     tn.binding.set_cost_model(peaks["hbm_gbs"] * 1e9, fpk["alu"], [fpk["tc"][1], fpk["tc"][2], fpk["tc"][3]])
     w = workloads.BY_NAME[args.workload]()
     semiring = w.info.get("semiring", "standard")
+    scaled = bool(w.info.get("exp_scaling", False))
     cplx = w.net.is_complex
-    # real networks (the max-plus workloads) run the R32 FP32 form
-    prec = PREC[args.prec] if cplx else tn.TN_R32_FP32_SIMT
+    # real networks: the max-plus workloads run the R32 FP32 form; the others the real form
+    # of --prec (fp32, tf32, 3xtf32; the complex-only BF16x3 forms, the default, read as
+    # 3xtf32)
+    if cplx:
+        prec, form = PREC[args.prec], args.prec
+    elif semiring == "maxplus":
+        prec, form = tn.TN_R32_FP32_SIMT, "fp32"
+    else:
+        form = args.prec if args.prec in REAL_PREC else "3xtf32"
+        prec = REAL_PREC[form]
     cmult = 3 if (cplx and args.prec in THREE_M) else 4
-    form = args.prec if cplx else "fp32"
     n_sl = w.n_slices
     per_step = args.slices_per_step or SLICES_PER_STEP.get(args.workload, n_sl)
     per_step = max(1, min(per_step, n_sl))
     # a slice-batched step runs its slices in one pass unless told otherwise
     batch = args.max_slice_batch or (per_step if per_step < n_sl else 0)
-    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, max_slice_batch=batch, semiring=semiring,
-                   complex_mult=cmult, single_sm_tiles=args.single_sm_tiles)
+    plan = tn.Plan(w.net, w.path, w.sliced, prec=prec, exp_scaling=scaled, max_slice_batch=batch,
+                   semiring=semiring, complex_mult=cmult, single_sm_tiles=args.single_sm_tiles)
     info = plan.info()
     stream = torch.cuda.current_stream()
     # step j contracts slices [j * per_step, (j + 1) * per_step) modulo n_slices
@@ -468,6 +481,7 @@ def run_ours(args):
     tiles = n_sl // per_step
     whole = per_step < n_sl and n_sl % per_step == 0 and len(ranges) >= tiles
     result = all_out[:tiles].sum(axis=0) if whole else all_out[-1]
+    result_ls = float(ls[-1].item())  # log scale of the last step's result (exponent scaling)
 
     # dominant kernel class by device time, and its roofline
     cls = max(range(len(prof["ms"])), key=lambda c: prof["ms"][c])
@@ -521,7 +535,8 @@ def run_ours(args):
     roof["launches_per_step"] = launches / args.steps
     roof["ms_per_launch"] = per_launch_ms
     roof["share_of_step"] = prof["ms"][cls] / sum(prof["ms"])
-    roof["peak_source"] = {1: fpk["source"]["tf32"], 2: fpk["source"]["tf32"], 3: fpk["source"]["tc_bf16"]}.get(
+    roof["peak_source"] = {1: fpk["source"]["tf32"], 2: fpk["source"]["tf32"], 3: fpk["source"]["tc_bf16"],
+                           5: fpk["source"]["tf32"], 6: fpk["source"]["tf32"]}.get(
         prec, fpk["source"]["alu"]) if cls == 2 else (peaks["_source"] if cls in (1, 3, 4) else fpk["source"]["alu"])
     path_roof = path_roofline(plan, prec, semiring, peaks, ms_max, cplx, count=round(slices_per_step), form=form)
     perm = None
@@ -552,9 +567,11 @@ def run_ours(args):
         "metric": "contraction TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "data": "synthetic",
-        "dtype": DTYPE_NAME[args.prec] if cplx else ("f32 (max,+)" if semiring == "maxplus" else "f32"),
+        "dtype": DTYPE_NAME[args.prec] if cplx else ("f32 (max,+)" if semiring == "maxplus" else
+                                                     {"fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32"}[form]),
         "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, ""),
-                   "prec": args.prec if cplx else "r32", "semiring": semiring,
+                   "prec": args.prec if cplx else "r32_" + form, "semiring": semiring,
+                   "exp_scaling": scaled,
                    "slices": n_sl, "sliced_labels": len(w.sliced),
                    "largest_intermediate_per_slice": info["peak_elems"],
                    "slices_per_step": slices_per_step, "slice_batch": info["slice_batch"],
@@ -613,6 +630,14 @@ def run_ours(args):
         want = np.asarray(oracle.contract(w.net, w.path, w.sliced, semiring=semiring))
         line["oracle"] = [float(want.flat[0].real), float(want.flat[0].imag)]
         line["rel_err_vs_oracle"] = float(np.max(np.abs(result - want)) / np.max(np.abs(want)))
+    if scaled and result.ndim == 0:
+        # the value is result * e^(log scale): report ln of it (|ln got - ln want| is the
+        # relative error of the value)
+        line["log_scale"] = result_ls
+        line["ln_result"] = float(np.log(abs(float(result.real)))) + result_ls
+        if args.check and covers_all:
+            line["ln_oracle"] = float(np.log(abs(float(np.asarray(want).flat[0].real))))
+            line["rel_err_vs_oracle"] = abs(line["ln_result"] - line["ln_oracle"])
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         f, s, done = oracle_sample(w, args.ref_budget or 20.0)
         line["cpu_baseline"] = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),

@@ -22,7 +22,8 @@ STATUS_NAMES = ["TN_OK", "TN_ERR_INVALID", "TN_ERR_UNSUPPORTED", "TN_ERR_OOM", "
 # tn_precision
 TN_C64_FP32_SIMT, TN_C64_TF32, TN_C64_3XTF32, TN_C64_BF16X3, TN_R32_FP32_SIMT, TN_R32_TF32, \
     TN_R32_3XTF32, TN_R32_BF16X3 = range(8)
-PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x3m": 3}
+PREC_NAMES = {"fp32": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3, "bf16x3m": 3,
+              "r32_fp32": 4, "r32_tf32": 5, "r32_3xtf32": 6, "r32_bf16x3": 7}
 # forms named with the 3M complex product (three real products per complex MAC)
 THREE_M = {"bf16x3m"}
 TN_PLAN_HOST_ONLY = 1

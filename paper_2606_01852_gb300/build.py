@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libtn_gb300.so")
-SOURCES = ["plan.cpp", "api.cu", "kernels_simt.cu", "gemm_tc.cu", "serve.cpp", "noalloc.cu", "batch.cu",
-           "distribute.cpp"]
+SOURCES = ["plan.cpp", "api.cu", "kernels_simt.cu", "gemm_tc.cu", "gemm_tf32.cu", "serve.cpp", "noalloc.cu",
+           "batch.cu", "distribute.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,29 +1,24 @@
-// Tensor-core path for the dense pairwise steps (sm_103a): planar complex GEMM
-//   C[b] = A[b] (m x k) . B[b] (n x k)^T      (complex, 4M real decomposition)
-// with both operands K-major, written through the separable row/column offset maps.
-// The kernels compute 128 x 128 output tiles per SM (256 x 128 per pair of SMs in the
-// cta_group::2 forms) with one elected thread issuing tcgen05.mma from shared-memory
-// descriptors, operands brought by TMA into a ring of stages (mbarrier transaction counts),
-// accumulators in tensor memory:
-//   contract_tc_kernel<1>          TF32 form: A_re, A_im, B_re, B_im fp32 tiles, 32-deep
-//                                  k-blocks, 3 stages, D_rr / D_ii / D_x accumulators
-//                                  (Re C = D_rr - D_ii, Im C = D_x); 192 threads;
-//   contract_tc3_kernel            3xTF32 form: eight warps split each staged tile into
-//                                  hi = RN_tf32(v) and lo = v - hi, hi.hi in 64-term chunks
-//                                  folded into round-to-nearest registers, cross terms in
-//                                  their own accumulator; 320 threads;
+// Tensor-core path for the dense pairwise steps (sm_103a), BF16x3 forms: planar complex
+// GEMM
+//   C[b] = A[b] (m x k) . B[b] (n x k)^T      (complex, 4M or 3M real decomposition)
+// with both operands K-major, written through the separable row/column offset maps (the
+// TF32 and 3xTF32 forms, complex and real, are in gemm_tf32.cu; the shared pieces in
+// tc_common.cuh). The kernels compute 128 x 128 output tiles per SM (256 x 128 per pair of
+// SMs in the cta_group::2 forms) with one elected thread issuing tcgen05.mma from
+// shared-memory descriptors, operands brought by TMA into a ring of stages (mbarrier
+// transaction counts), accumulators in tensor memory:
 //   contract_tcb_kernel            BF16x3 form: operands already split into BF16 hi/lo
 //                                  planes by their producers, kind::f16, 256-term chunks;
-//   contract_tcb2_kernel           BF16x3 on paired SMs (m >= 256, k > 4096): one two-CTA
+//   contract_tcb2_kernel           BF16x3 on paired SMs (m >= 256, k > 2048): one two-CTA
 //                                  cluster per 256 x 128 tile, M = 256 MMAs;
-//   contract_tcb2p_kernel          the same, persistent clusters (256 < k <= 4096);
+//   contract_tcb2p_kernel          the same, persistent clusters (256 < k <= 2048);
 //   contract_tcb3m_kernel          BF16x3 with the 3M complex product;
 //   contract_tcb_persistent_kernel BF16x3 for shallow steps (k <= 256): one CTA per SM over
 //                                  the tiles, stores of a tile overlapping the next tile;
 //   contract_tcb_shallow_kernel    the same for k <= 64 with sixteen epilogue warps.
-// The epilogues of the TF32 and BF16x3 kernels store each 32 x 32 block in address order
-// (store_block). Every mbarrier wait is bounded by wall time; on expiry the CTA records an
-// error code, drains its copies, frees its tensor memory and returns.
+// The epilogues store each 32 x 32 block in address order (store_block). Every mbarrier
+// wait is bounded by wall time; on expiry the CTA records an error code, drains its
+// copies, frees its tensor memory and returns.
 #include <cstdint>
 
 #include <cuda.h>
@@ -33,26 +28,10 @@
 #include "kernels.h"
 #include "mbarrier.cuh"
 #include "split_bf16.cuh"
+#include "tc_common.cuh"
 
 namespace tn {
 namespace {
-
-constexpr int BM = 128, BN = 128;
-constexpr int NTHREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;                         // D_rr @0, D_ii @128, D_x @256
-constexpr int GROUP_M = 16;                                 // raster: tiles grouped along M
-
-template <int SPLIT>
-struct Cfg {
-  static constexpr int BK = SPLIT == 1 ? 32 : 16;           // fp32 elements per k-block
-  static constexpr int ROWB = BK * 4;                       // bytes per tile row (= swizzle span)
-  static constexpr int TILE_A = BM * ROWB;
-  static constexpr int TILE_B = BN * ROWB;
-  static constexpr int STAGE = 2 * TILE_A + 2 * TILE_B;     // A_re A_im B_re B_im
-  static constexpr int STAGES = SPLIT == 1 ? 3 : 4;
-  static constexpr int LO = SPLIT == 1 ? 0 : 2;             // lo buffers
-  static constexpr int SMEM = (STAGES + LO) * STAGE + 1024 /*barriers*/ + 1024 /*align*/;
-};
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that is completed only
 // if `arrive` is set. Without the arrival the wait runs out after limit_ns, the kernel
@@ -64,821 +43,6 @@ __global__ void bounded_wait_selftest_kernel(int arrive, uint64_t limit_ns, int*
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   if (arrive) mbar_arrive(&bar);
   if (!mbar_wait(&bar, 0, limit_ns)) atomicExch(err, 99);
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                            int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-      "[%2];" ::"r"(su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-// Shared-memory matrix descriptor of a K-major tile whose rows are ROWB bytes with the
-// matching swizzle (128 B -> mode 2, 64 B -> mode 4); 8-row groups 8*ROWB bytes apart.
-template <int ROWB>
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFF) >> 4);
-  d |= static_cast<uint64_t>(1) << 16;                 // leading byte offset (unused here)
-  d |= static_cast<uint64_t>((8 * ROWB) >> 4) << 32;   // stride byte offset
-  d |= static_cast<uint64_t>(1) << 46;                 // descriptor version
-  d |= static_cast<uint64_t>(ROWB == 128 ? 2 : 4) << 61;
-  return d;
-}
-// Instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, shape M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-#define TN_R8(i) "=r"(r[i + 0]), "=r"(r[i + 1]), "=r"(r[i + 2]), "=r"(r[i + 3]), "=r"(r[i + 4]), \
-                 "=r"(r[i + 5]), "=r"(r[i + 6]), "=r"(r[i + 7])
-// 32 consecutive fp32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : TN_R8(0), TN_R8(8), TN_R8(16), TN_R8(24)
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-#undef TN_R8
-
-__device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
-// v rounded to the nearest value with 10 fraction bits (ties away from zero): half a unit in
-// the 10th fraction bit is added to the magnitude and the low 13 bits cleared (finite v
-// below the largest TF32-representable value; an overflow would carry into the exponent).
-__device__ __forceinline__ float tf32_rn(float v) {
-  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
-}
-
-// V consecutive 16-bit values (the low halves of x[]) as one store of 2V bytes.
-template <int V>
-__device__ __forceinline__ void store_halves(uint16_t* d, const uint32_t (&x)[V]) {
-  if constexpr (V == 1) {
-    d[0] = static_cast<uint16_t>(x[0]);
-  } else if constexpr (V == 2) {
-    *reinterpret_cast<uint32_t*>(d) = x[0] | (x[1] << 16);
-  } else if constexpr (V == 4) {
-    *reinterpret_cast<uint2*>(d) = make_uint2(x[0] | (x[1] << 16), x[2] | (x[3] << 16));
-  } else {
-    *reinterpret_cast<uint4*>(d) =
-        make_uint4(x[0] | (x[1] << 16), x[2] | (x[3] << 16), x[4] | (x[5] << 16), x[6] | (x[7] << 16));
-  }
-}
-
-// V consecutive elements (V = 1, 2, 4, 8) of an address-ordered run: Re values re[],
-// Im values im[], stored at element `off` of a tensor copy that starts at C, in storage
-// mode fmt (planar FP32, split BF16, or split BF16 with the 3M sum planes), one vector
-// store per plane (off and the planes are V-aligned).
-template <int V>
-__device__ __forceinline__ void store_run(float* C, int64_t plane, int64_t off, const float* re, const float* im,
-                                          int fmt) {
-  if (fmt == kFmtPlanar) {
-    if constexpr (V == 1) {
-      C[off] = re[0];
-      C[plane + off] = im[0];
-    } else if constexpr (V == 2) {
-      *reinterpret_cast<float2*>(C + off) = make_float2(re[0], re[1]);
-      *reinterpret_cast<float2*>(C + plane + off) = make_float2(im[0], im[1]);
-    } else {
-#pragma unroll
-      for (int h = 0; h < V; h += 4) {
-        *reinterpret_cast<float4*>(C + off + h) = make_float4(re[h], re[h + 1], re[h + 2], re[h + 3]);
-        *reinterpret_cast<float4*>(C + plane + off + h) = make_float4(im[h], im[h + 1], im[h + 2], im[h + 3]);
-      }
-    }
-    return;
-  }
-  if constexpr (V >= 2) {
-    if (fmt == kFmtSplit) {
-      // hi = RN_bf16(v), lo = RN_bf16(v - hi), two values per conversion (the same values
-      // as split_pair's one at a time); 32-bit word w holds elements 2w (low) and 2w + 1
-      constexpr int W = V / 2;
-      uint32_t hr[W], hi_[W], lr[W], li[W];
-#pragma unroll
-      for (int w = 0; w < W; ++w) {
-        const __nv_bfloat162 a = __floats2bfloat162_rn(re[2 * w], re[2 * w + 1]);
-        const __nv_bfloat162 b = __floats2bfloat162_rn(im[2 * w], im[2 * w + 1]);
-        const __nv_bfloat162 c =
-            __floats2bfloat162_rn(re[2 * w] - __low2float(a), re[2 * w + 1] - __high2float(a));
-        const __nv_bfloat162 d =
-            __floats2bfloat162_rn(im[2 * w] - __low2float(b), im[2 * w + 1] - __high2float(b));
-        hr[w] = uint32_t(__bfloat16_as_ushort(a.x)) | (uint32_t(__bfloat16_as_ushort(a.y)) << 16);
-        hi_[w] = uint32_t(__bfloat16_as_ushort(b.x)) | (uint32_t(__bfloat16_as_ushort(b.y)) << 16);
-        lr[w] = uint32_t(__bfloat16_as_ushort(c.x)) | (uint32_t(__bfloat16_as_ushort(c.y)) << 16);
-        li[w] = uint32_t(__bfloat16_as_ushort(d.x)) | (uint32_t(__bfloat16_as_ushort(d.y)) << 16);
-      }
-      uint16_t* S = reinterpret_cast<uint16_t*>(C) + off;
-      if constexpr (W == 1) {
-        *reinterpret_cast<uint32_t*>(S) = hr[0];
-        *reinterpret_cast<uint32_t*>(S + plane) = hi_[0];
-        *reinterpret_cast<uint32_t*>(S + 2 * plane) = lr[0];
-        *reinterpret_cast<uint32_t*>(S + 3 * plane) = li[0];
-      } else if constexpr (W == 2) {
-        *reinterpret_cast<uint2*>(S) = make_uint2(hr[0], hr[1]);
-        *reinterpret_cast<uint2*>(S + plane) = make_uint2(hi_[0], hi_[1]);
-        *reinterpret_cast<uint2*>(S + 2 * plane) = make_uint2(lr[0], lr[1]);
-        *reinterpret_cast<uint2*>(S + 3 * plane) = make_uint2(li[0], li[1]);
-      } else {
-        *reinterpret_cast<uint4*>(S) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-        *reinterpret_cast<uint4*>(S + plane) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
-        *reinterpret_cast<uint4*>(S + 2 * plane) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-        *reinterpret_cast<uint4*>(S + 3 * plane) = make_uint4(li[0], li[1], li[2], li[3]);
-      }
-      return;
-    }
-  }
-  // hi = RN_bf16(v), lo = RN_bf16(v - hi) of re, im (and s = re + im in the 3M form)
-  uint32_t hr[V], hi_[V], lr[V], li[V];
-#pragma unroll
-  for (int u = 0; u < V; ++u) {
-    __nv_bfloat16 a, b, c, d;
-    split_pair(re[u], a, c);
-    split_pair(im[u], b, d);
-    hr[u] = __bfloat16_as_ushort(a);
-    hi_[u] = __bfloat16_as_ushort(b);
-    lr[u] = __bfloat16_as_ushort(c);
-    li[u] = __bfloat16_as_ushort(d);
-  }
-  uint16_t* S = reinterpret_cast<uint16_t*>(C) + off;
-  if (fmt == kFmtSplit) {
-    store_halves<V>(S, hr);
-    store_halves<V>(S + plane, hi_);
-    store_halves<V>(S + 2 * plane, lr);
-    store_halves<V>(S + 3 * plane, li);
-    return;
-  }
-  uint32_t hs[V], ls[V];
-#pragma unroll
-  for (int u = 0; u < V; ++u) {
-    __nv_bfloat16 a, c;
-    split_pair(re[u] + im[u], a, c);
-    hs[u] = __bfloat16_as_ushort(a);
-    ls[u] = __bfloat16_as_ushort(c);
-  }
-  store_halves<V>(S, hr);
-  store_halves<V>(S + plane, lr);
-  store_halves<V>(S + 2 * plane, hi_);
-  store_halves<V>(S + 3 * plane, li);
-  store_halves<V>(S + 4 * plane, hs);
-  store_halves<V>(S + 5 * plane, ls);
-}
-
-// The address-ordered stores of one block, lanes taking V = 2^VB consecutive addresses.
-// e[k], src[k]: the k-th smallest bit weight (log2) and which bit of r (0-4) or c (5-9)
-// carries it; the VB smallest weights are 1, 2, ..., 2^(VB-1).
-template <int VB>
-__device__ __forceinline__ void store_sorted(float* C, int64_t plane, int split, const float* t, int pitch, int cs,
-                                             int64_t base, const int* e, const int* src, int lane) {
-  constexpr int V = 1 << VB;
-  // r and c take disjoint bits, so t's index r * pitch + c is a sum of one increment per
-  // set bit: the lane's part, the store's part and, per element of the run, du[u]
-  auto step = [&](int k) { return src[k] < 5 ? pitch << src[k] : 1 << (src[k] - 5); };
-  int du[V];
-#pragma unroll
-  for (int u = 0; u < V; ++u) {
-    du[u] = 0;
-#pragma unroll
-    for (int k = 0; k < VB; ++k)
-      if ((u >> k) & 1) du[u] += step(k);
-  }
-  int il = 0;
-  int64_t al = 0;
-#pragma unroll
-  for (int k = 0; k < 5; ++k)
-    if ((lane >> k) & 1) {
-      il += step(VB + k);
-      al += int64_t(1) << e[VB + k];
-    }
-  for (int s = 0; s < (32 >> VB); ++s) {
-    int is = il;
-    int64_t ah = 0;
-#pragma unroll
-    for (int k = 0; k < 5 - VB; ++k)
-      if ((s >> k) & 1) {
-        is += step(VB + 5 + k);
-        ah += int64_t(1) << e[VB + 5 + k];
-      }
-    float re[V], im[V];
-#pragma unroll
-    for (int u = 0; u < V; ++u) {
-      re[u] = t[is + du[u]];
-      im[u] = t[cs + is + du[u]];
-    }
-    store_run<V>(C, plane, base + al + ah, re, im, split);
-  }
-}
-
-// Store one 32 x 32 block of a result tile from shared memory (t[r * pitch + c] = Re,
-// t[cs + r * pitch + c] = Im; row r is lane r's row, column c lane c's column) in the
-// order of its addresses. When the block's offsets are linear in the bits of (r, c) with
-// power-of-two weights -- every row and column extent of the offset maps a power of two,
-// as in every network with extent-2 modes -- off(r, c) = off(0, 0) + sum of per-bit
-// weights, and the ten weights sorted ascending give the block's elements in address
-// order. Each lane then writes V consecutive addresses with one vector store per plane
-// (V up to 4 FP32 or 8 BF16 values, 16 bytes, as far as the smallest weights are 1, 2, 4,
-// ... and the block is aligned), and a warp store covers 32 V consecutive elements when
-// the following weights continue the sequence (interleaved row/column layouts included).
-// Otherwise (ragged block, other extents) it falls back to one row per store. ro / co:
-// this lane's row / column offset; row_ok / col_ok: in range.
-// The address order of a 32 x 32 block: the ten bit weights (log2; bits 0-4 of the row,
-// 5-9 of the column index) sorted ascending, with the bit each comes from; ok when the
-// block's offsets are linear in those bits with power-of-two weights. ro_rel / co_rel: this
-// lane's row / column offset relative to the block's first row / column.
-struct BlockOrder {
-  int e[10], src[10];
-  bool ok;
-};
-static_assert(sizeof(BlockOrder) <= 128, "a fold warp's block order slot");
-__device__ __forceinline__ BlockOrder block_order(int64_t ro_rel, int64_t co_rel, bool in_range, int lane) {
-  BlockOrder o;
-  bool lin = in_range;
-  int64_t pr = 0, pc = 0;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int64_t wr = __shfl_sync(0xffffffffu, ro_rel, 1 << i);
-    const int64_t wc = __shfl_sync(0xffffffffu, co_rel, 1 << i);
-    o.e[i] = (wr > 0 && (wr & (wr - 1)) == 0) ? 63 - __clzll(wr) : -1;
-    o.e[5 + i] = (wc > 0 && (wc & (wc - 1)) == 0) ? 63 - __clzll(wc) : -1;
-    lin = lin && o.e[i] >= 0 && o.e[5 + i] >= 0;
-    pr += ((lane >> i) & 1) * wr;
-    pc += ((lane >> i) & 1) * wc;
-  }
-  lin = lin && pr == ro_rel && pc == co_rel;
-  o.ok = __all_sync(0xffffffffu, lin);
-#pragma unroll
-  for (int i = 0; i < 10; ++i) o.src[i] = i;
-  if (o.ok) {
-#pragma unroll
-    for (int i = 1; i < 10; ++i)
-#pragma unroll
-      for (int j = i; j > 0; --j)
-        if (o.e[j] < o.e[j - 1]) {
-          const int te = o.e[j];
-          o.e[j] = o.e[j - 1];
-          o.e[j - 1] = te;
-          const int ts = o.src[j];
-          o.src[j] = o.src[j - 1];
-          o.src[j - 1] = ts;
-        }
-  }
-  return o;
-}
-
-// The address-ordered stores of a block whose order is `o` (o.ok) and whose first element
-// is at `base`: each lane writes V consecutive addresses with one vector store per plane
-// (V as far as the smallest weights are 1, 2, 4, ... and base and the plane size are
-// V-aligned; 16 bytes at most).
-__device__ __forceinline__ void store_ordered(float* C, int64_t plane, int split, const float* t, int pitch, int cs,
-                                              int64_t base, const BlockOrder& o, int lane) {
-  int vb = 0;
-  while (vb < (split ? 3 : 2) && o.e[vb] == vb) ++vb;
-  while (vb > 0 && ((base | plane) & ((int64_t(1) << vb) - 1)) != 0) --vb;
-  if (vb == 3) store_sorted<3>(C, plane, split, t, pitch, cs, base, o.e, o.src, lane);
-  else if (vb == 2) store_sorted<2>(C, plane, split, t, pitch, cs, base, o.e, o.src, lane);
-  else if (vb == 1) store_sorted<1>(C, plane, split, t, pitch, cs, base, o.e, o.src, lane);
-  else store_sorted<0>(C, plane, split, t, pitch, cs, base, o.e, o.src, lane);
-}
-
-// Store one 32 x 32 block of a result tile from shared memory (t[r * pitch + c] = Re,
-// t[cs + r * pitch + c] = Im; row r is lane r's row, column c lane c's column) in the
-// order of its addresses. When the block's offsets are linear in the bits of (r, c) with
-// power-of-two weights -- every row and column extent of the offset maps a power of two,
-// as in every network with extent-2 modes -- off(r, c) = off(0, 0) + sum of per-bit
-// weights, and the ten weights sorted ascending give the block's elements in address
-// order (block_order); a warp store then covers 32 V consecutive elements when the
-// following weights continue the sequence (interleaved row/column layouts included).
-// Otherwise (ragged block, other extents) it falls back to one row per store. ro / co:
-// this lane's row / column offset; row_ok / col_ok: in range.
-__device__ __forceinline__ void store_block(float* C, int64_t plane, int split, const float* t, int pitch,
-                                            int cs, int64_t ro, int64_t co, bool row_ok, bool col_ok, int lane) {
-  const int64_t ro0 = __shfl_sync(0xffffffffu, ro, 0), co0 = __shfl_sync(0xffffffffu, co, 0);
-  const BlockOrder o = block_order(ro - ro0, co - co0, row_ok && col_ok, lane);
-  if (o.ok) {
-    store_ordered(C, plane, split, t, pitch, cs, ro0 + co0, o, lane);
-    return;
-  }
-  for (int r = 0; r < 32; ++r) {
-    const int64_t ro_r = __shfl_sync(0xffffffffu, ro, r);
-    const bool ok_r = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, r) != 0;
-    if (ok_r && col_ok) store_cplx(C, plane, ro_r + co, t[r * pitch + lane], t[cs + r * pitch + lane], split);
-  }
-}
-
-template <int SPLIT>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    contract_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                       StepArgs a, int64_t t_first, int* err) {
-  using G = Cfg<SPLIT>;
-  constexpr int STAGES = G::STAGES, BK = G::BK, ROWB = G::ROWB;
-  constexpr int TILE_A = G::TILE_A, TILE_B = G::TILE_B, STAGE = G::STAGE;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* lo_base = smem + STAGES * STAGE;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(lo_base + G::LO * STAGE);
-  uint64_t* full = bars;                     // [STAGES]
-  uint64_t* empty = bars + STAGES;           // [STAGES]
-  uint64_t* conv_full = bars + 2 * STAGES;   // [2]
-  uint64_t* lo_empty = conv_full + 2;        // [2]
-  uint64_t* acc_full = lo_empty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grouped raster over output tiles for L2 reuse of A and B tiles
-  const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
-  const int64_t t = t_first + blockIdx.x;  // this launch's tiles start at t_first
-  const int64_t per_group = GROUP_M * tiles_n;
-  const int64_t first_m = (t / per_group) * GROUP_M;
-  const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
-  const int64_t tm = first_m + (t % per_group) % gm, tn = (t % per_group) / gm;
-  const int m0 = static_cast<int>(tm * BM), n0 = static_cast<int>(tn * BN);
-  const int b = blockIdx.y;
-  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);
-  const int pa = a.a_bstride ? 2 * b : 0, pb = a.b_bstride ? 2 * b : 0;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&conv_full[i], 128);
-      mbar_init(&lo_empty[i], 1);
-    }
-    mbar_init(acc_full, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                 "r"(TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(&empty[s], ph ^ 1)) {
-          atomicExch(err, 1);
-          break;
-        }
-        mbar_expect_tx(&full[s], STAGE);
-        uint8_t* st = smem + s * STAGE;
-        const int k0 = kb * BK;
-        tma_load_3d(st, &tmA, &full[s], k0, m0, pa);
-        tma_load_3d(st + TILE_A, &tmA, &full[s], k0, m0, pa + 1);
-        tma_load_3d(st + 2 * TILE_A, &tmB, &full[s], k0, n0, pb);
-        tma_load_3d(st + 2 * TILE_A + TILE_B, &tmB, &full[s], k0, n0, pb + 1);
-        issued = kb + 1;
-      }
-      // drain: every stage's last issued load has landed before the CTA can exit
-      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-        if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) atomicExch(err, 2);
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(BM, BN);
-      const uint32_t d_rr = tmem, d_ii = tmem + 128, d_x = tmem + 256;
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(&full[s], ph)) {
-          atomicExch(err, 3);
-          break;
-        }
-        if (SPLIT == 3 && !mbar_wait(&conv_full[kb & 1], (kb >> 1) & 1)) {
-          atomicExch(err, 4);
-          break;
-        }
-        fence_after();
-        const uint32_t st = su32(smem + s * STAGE);
-        const uint32_t lo = su32(lo_base + (kb & 1) * STAGE);
-#pragma unroll
-        for (int j = 0; j < BK / 8; ++j) {
-          const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
-          const uint64_t ar = smem_desc<ROWB>(st + j * 32), ai = smem_desc<ROWB>(st + TILE_A + j * 32);
-          const uint64_t br = smem_desc<ROWB>(st + 2 * TILE_A + j * 32);
-          const uint64_t bi = smem_desc<ROWB>(st + 2 * TILE_A + TILE_B + j * 32);
-          mma_tf32(d_rr, ar, br, idesc, acc);
-          mma_tf32(d_ii, ai, bi, idesc, acc);
-          mma_tf32(d_x, ar, bi, idesc, acc);
-          mma_tf32(d_x, ai, br, idesc, 1u);
-          if (SPLIT == 3) {
-            const uint64_t arl = smem_desc<ROWB>(lo + j * 32), ail = smem_desc<ROWB>(lo + TILE_A + j * 32);
-            const uint64_t brl = smem_desc<ROWB>(lo + 2 * TILE_A + j * 32);
-            const uint64_t bil = smem_desc<ROWB>(lo + 2 * TILE_A + TILE_B + j * 32);
-            mma_tf32(d_rr, arl, br, idesc, 1u);
-            mma_tf32(d_rr, ar, brl, idesc, 1u);
-            mma_tf32(d_ii, ail, bi, idesc, 1u);
-            mma_tf32(d_ii, ai, bil, idesc, 1u);
-            mma_tf32(d_x, arl, bi, idesc, 1u);
-            mma_tf32(d_x, ar, bil, idesc, 1u);
-            mma_tf32(d_x, ail, br, idesc, 1u);
-            mma_tf32(d_x, ai, brl, idesc, 1u);
-          }
-        }
-        mma_commit(&empty[s]);
-        if (SPLIT == 3) mma_commit(&lo_empty[kb & 1]);
-      }
-      mma_commit(acc_full);  // also on error: lets the epilogue see in-flight MMAs retire
-    }
-  } else {
-    const int et = threadIdx.x - 64;  // 0..127
-    if (SPLIT == 3) {
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(&lo_empty[kb & 1], ((kb >> 1) & 1) ^ 1)) {
-          atomicExch(err, 5);
-          break;
-        }
-        float4* src = reinterpret_cast<float4*>(smem + s * STAGE);
-        float4* dst = reinterpret_cast<float4*>(lo_base + (kb & 1) * STAGE);
-#pragma unroll 4
-        for (int i = et; i < STAGE / 16; i += 128) {
-          const float4 v = src[i];
-          float4 h, l;
-          h.x = tf32_trunc(v.x);
-          h.y = tf32_trunc(v.y);
-          h.z = tf32_trunc(v.z);
-          h.w = tf32_trunc(v.w);
-          l.x = v.x - h.x;
-          l.y = v.y - h.y;
-          l.z = v.z - h.z;
-          l.w = v.w - h.w;
-          src[i] = h;
-          dst[i] = l;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&conv_full[kb & 1]);
-      }
-    }
-    // epilogue: TMEM lane quarter of this warp = warp % 4
-    const bool ok = mbar_wait(acc_full, 0);
-    if (!ok) atomicExch(err, 6);
-    fence_after();
-    const int q = warp & 3;
-    const int row = q * 32 + lane;
-    const int64_t m = static_cast<int64_t>(m0) + row;
-    const bool row_ok = ok && m < a.m;
-    const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
-    float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
-    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
-    // Each 32 x 32 block goes through shared memory (the drained stage buffers) and is
-    // stored in address order (store_block): 32 consecutive elements per warp store for
-    // the usual layouts.
-    float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 33;  // [2][32][33]
-    for (int c = 0; c < BN / 32; ++c) {
-      float rr[32], ii[32], xx[32];
-      tmem_ld32(tmem + lane_base + c * 32, rr);
-      tmem_ld32(tmem + lane_base + 128 + c * 32, ii);
-      tmem_ld32(tmem + lane_base + 256 + c * 32, xx);
-      const int64_t nb0 = static_cast<int64_t>(n0) + c * 32;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        tr[lane * 33 + j] = rr[j] - ii[j];
-        tr[32 * 33 + lane * 33 + j] = xx[j];
-      }
-      __syncwarp();
-      const int64_t n = nb0 + lane;
-      const bool col_ok = ok && n < a.n;
-      store_block(C, a.c_plane, kFmtPlanar, tr, 33, 32 * 33, ro, col_ok ? map_offset(a.cols, n) : 0, row_ok, col_ok,
-                  lane);
-      __syncwarp();
-    }
-  }
-  fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
-  }
-}
-
-// ---------------------------------------------------------------------------------
-// 3xTF32 with round-to-nearest accumulation across k.
-//
-// The tensor core's FP32 accumulator truncates each addition, so a long TMEM
-// accumulation drifts toward zero by ~k * 2^-25 relative (measured). Here the MMAs
-// accumulate only CK k-blocks (CK * 16 terms) into the TMEM chunk accumulator
-// (re @0, im @128; Re uses the instruction's negate-A bit for -A_im.B_im); eight
-// warps then add the chunk into running totals held in their registers with ordinary
-// round-to-nearest FP32 additions, and release the accumulator for the next chunk.
-// The same eight warps split every staged tile into hi/lo (so the MMA pipe waits only
-// for the short drain), and finally write the totals out. 128 x 128 tiles: the kernel is
-// bound by shared-memory operand reads (each 3xTF32 MMA re-reads its tiles), so the
-// wide tile keeps reads per flop low.
-// Warps: 0 TMA, 1 MMA + TMEM, 2-9 split / drain / epilogue (320 threads); warp w of
-// 2-9 drains TMEM lane quarter w % 4, columns 64 * ((w - 2) / 4) .. +63.
-
-// Stage layout (raw values and, in the lo buffers, their lo parts), 8 KiB tiles:
-//   A_re | A_im | -B_im | B_re | B_im
-// so that [B_re | B_im] and [-B_im | B_re] are each one 256-row operand: per k-atom
-// A_re.[B_re|B_im] and A_im.[-B_im|B_re] add into (Re, Im) with one 128 x 256 MMA each.
-struct C3 {
-  static constexpr int BK = 16, ROWB = 64, CK = 4;
-  static constexpr int TILE_A = BM * ROWB;                  // 8 KiB
-  static constexpr int TILE_B = BN * ROWB;                  // 8 KiB
-  static constexpr int OFF_AI = TILE_A, OFF_BNEG = 2 * TILE_A;
-  static constexpr int OFF_BR = 2 * TILE_A + TILE_B, OFF_BI = 2 * TILE_A + 2 * TILE_B;
-  static constexpr int TMA_BYTES = 2 * TILE_A + 2 * TILE_B; // 32 KiB per stage by TMA
-  static constexpr int STAGE = 2 * TILE_A + 3 * TILE_B;     // 40 KiB
-  static constexpr int STAGES = 3, LO = 2;
-  static constexpr int THREADS = 320;
-  static constexpr int SMEM = (STAGES + LO) * STAGE + 1024 + 1024;
-  static constexpr uint32_t COLS = 512;  // re @0, im @128, re_lo @256, im_lo @384
-};
-
-__global__ void __launch_bounds__(C3::THREADS, 1)
-    contract_tc3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                        StepArgs a, int64_t t_first, int* err) {
-  constexpr int STAGES = C3::STAGES, BK = C3::BK, ROWB = C3::ROWB, CK = C3::CK;
-  constexpr int TILE_A = C3::TILE_A, TILE_B = C3::TILE_B, STAGE = C3::STAGE;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* lo_base = smem + STAGES * STAGE;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(lo_base + C3::LO * STAGE);
-  uint64_t* full = bars;                     // [STAGES]
-  uint64_t* empty = bars + STAGES;           // [STAGES]
-  uint64_t* conv_full = bars + 2 * STAGES;   // [2]
-  uint64_t* lo_empty = conv_full + 2;        // [2]
-  uint64_t* acc_full = lo_empty + 2;         // chunk accumulated
-  uint64_t* acc_empty = acc_full + 1;        // chunk drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tiles_m = (a.m + BM - 1) / BM, tiles_n = (a.n + BN - 1) / BN;
-  const int64_t t = t_first + blockIdx.x;  // this launch's tiles start at t_first
-  const int64_t per_group = GROUP_M * tiles_n;
-  const int64_t first_m = (t / per_group) * GROUP_M;
-  const int64_t gm = tiles_m - first_m < GROUP_M ? tiles_m - first_m : GROUP_M;
-  const int64_t tm = first_m + (t % per_group) % gm, tn = (t % per_group) / gm;
-  const int m0 = static_cast<int>(tm * BM), n0 = static_cast<int>(tn * BN);
-  const int b = blockIdx.y;
-  const int num_kb = static_cast<int>((a.k + BK - 1) / BK);
-  const int n_chunks = (num_kb + CK - 1) / CK;
-  const int pa = a.a_bstride ? 2 * b : 0, pb = a.b_bstride ? 2 * b : 0;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&conv_full[i], 256);
-      mbar_init(&lo_empty[i], 1);
-    }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 8);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                 "r"(C3::COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) {
-          atomicExch(err, 11);
-          break;
-        }
-        mbar_expect_tx(&full[s], C3::TMA_BYTES);
-        uint8_t* st = smem + s * STAGE;
-        const int k0 = kb * BK;
-        tma_load_3d(st, &tmA, &full[s], k0, m0, pa);
-        tma_load_3d(st + C3::OFF_AI, &tmA, &full[s], k0, m0, pa + 1);
-        tma_load_3d(st + C3::OFF_BR, &tmB, &full[s], k0, n0, pb);
-        tma_load_3d(st + C3::OFF_BI, &tmB, &full[s], k0, n0, pb + 1);
-        issued = kb + 1;
-      }
-      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-        if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) atomicExch(err, 12);
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(BM, 2 * BN);  // 128 x 256: (Re | Im) at once
-      const uint32_t d_hi = tmem, d_lo = tmem + 256;
-      bool ok = true;
-      for (int c = 0; c < n_chunks && ok; ++c) {
-        if (!mbar_wait(acc_empty, (c & 1) ^ 1)) {
-          atomicExch(err, 13);
-          break;
-        }
-        fence_after();
-        const int kb_end = min(num_kb, (c + 1) * CK);
-        for (int kb = c * CK; kb < kb_end; ++kb) {
-          const int s = kb % STAGES;
-          if (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(&conv_full[kb & 1], (kb >> 1) & 1)) {
-            atomicExch(err, 14);
-            ok = false;
-            break;
-          }
-          fence_after();
-          const uint32_t st = su32(smem + s * STAGE);
-          const uint32_t lo = su32(lo_base + (kb & 1) * STAGE);
-#pragma unroll
-          for (int j = 0; j < BK / 8; ++j) {
-            const uint32_t acc = (kb > c * CK || j > 0) ? 1u : 0u;
-            const uint64_t ar = smem_desc<ROWB>(st + j * 32), ai = smem_desc<ROWB>(st + C3::OFF_AI + j * 32);
-            const uint64_t b_ri = smem_desc<ROWB>(st + C3::OFF_BR + j * 32);    // [B_re | B_im]
-            const uint64_t b_nr = smem_desc<ROWB>(st + C3::OFF_BNEG + j * 32);  // [-B_im | B_re]
-            const uint64_t arl = smem_desc<ROWB>(lo + j * 32), ail = smem_desc<ROWB>(lo + C3::OFF_AI + j * 32);
-            const uint64_t bl_ri = smem_desc<ROWB>(lo + C3::OFF_BR + j * 32);
-            const uint64_t bl_nr = smem_desc<ROWB>(lo + C3::OFF_BNEG + j * 32);
-            // hi.hi products into the main accumulators (Re | Im); the small cross terms into
-            // their own, so the main sums take only two truncating additions per 8 terms
-            mma_tf32(d_hi, ar, b_ri, idesc, acc);
-            mma_tf32(d_hi, ai, b_nr, idesc, 1u);
-            // the cross-term accumulator runs over all of k (it is ~2^-11 of the result,
-            // so its own truncation is negligible) and is read once, after the last chunk
-            mma_tf32(d_lo, arl, b_ri, idesc, (kb > 0 || j > 0) ? 1u : 0u);
-            mma_tf32(d_lo, ail, b_nr, idesc, 1u);
-            mma_tf32(d_lo, ar, bl_ri, idesc, 1u);
-            mma_tf32(d_lo, ai, bl_nr, idesc, 1u);
-          }
-          mma_commit(&empty[s]);
-          mma_commit(&lo_empty[kb & 1]);
-        }
-        mma_commit(acc_full);  // also on error, so the drain sees issued MMAs retire
-      }
-    }
-  } else {
-    const int et = threadIdx.x - 64;  // 0..255
-    const int q = warp & 3, half = (warp - 2) >> 2;
-    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
-    float run_re[64], run_im[64];
-#pragma unroll
-    for (int i = 0; i < 64; ++i) run_re[i] = run_im[i] = 0.f;
-    bool ok = true;
-    for (int kb = 0; kb <= num_kb; ++kb) {
-      // Fold chunk dc of the TMEM accumulators into the register totals and release
-      // them: once one k-block into the next chunk is split (so the MMA pipe restarts at
-      // once), and after the last k-block.
-      const int dc = kb == num_kb ? n_chunks - 1 : (kb % CK == 0 && kb > 0 ? kb / CK - 1 : -1);
-      if (kb < num_kb) {
-        const int s = kb % STAGES;
-        if (ok && (!mbar_wait(&full[s], (kb / STAGES) & 1) || !mbar_wait(&lo_empty[kb & 1], ((kb >> 1) & 1) ^ 1))) {
-          atomicExch(err, 15);
-          ok = false;
-        }
-      }
-      if (kb < num_kb && ok) {
-        const int s = kb % STAGES;
-        float4* src = reinterpret_cast<float4*>(smem + s * STAGE);
-        float4* dst = reinterpret_cast<float4*>(lo_base + (kb & 1) * STAGE);
-        // hi = value rounded to the nearest TF32 (written back in place), lo = value - hi
-        // (exact); for B_im also -hi and -lo. kind::tf32 reads an FP32 operand by dropping
-        // its low 13 mantissa bits (tests/test_gpu_tc.py::test_tf32_operand_rounding), so hi
-        // is read exactly and only lo is truncated -- by at most 2^-10 of |lo|, with the
-        // sign of lo, i.e. without a bias. (Using the staged value itself as hi would have
-        // the hardware truncate it: a bias toward zero in every product.)
-        constexpr int NA = 2 * TILE_A / 16;  // float4s of A_re, A_im
-#pragma unroll 4
-        for (int i = et; i < C3::TMA_BYTES / 16; i += 256) {
-          const int f = i < NA ? i : i + TILE_B / 16;  // skip the -B_im slot
-          const float4 v = src[f];
-          float4 h, l;
-          h.x = tf32_rn(v.x);
-          h.y = tf32_rn(v.y);
-          h.z = tf32_rn(v.z);
-          h.w = tf32_rn(v.w);
-          l.x = v.x - h.x;
-          l.y = v.y - h.y;
-          l.z = v.z - h.z;
-          l.w = v.w - h.w;
-          src[f] = h;
-          dst[f] = l;
-          if (f >= C3::OFF_BI / 16) {
-            const int g = f - (C3::OFF_BI - C3::OFF_BNEG) / 16;
-            src[g] = make_float4(-h.x, -h.y, -h.z, -h.w);
-            dst[g] = make_float4(-l.x, -l.y, -l.z, -l.w);
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&conv_full[kb & 1]);
-      }
-      if (dc >= 0 && ok) {
-        if (!mbar_wait(acc_full, dc & 1)) {
-          atomicExch(err, 16);
-          ok = false;
-        } else {
-          fence_after();
-          float v[32];
-#pragma unroll
-          for (int p = 0; p < 2; ++p) {
-            const uint32_t col = lane_base + half * 64 + p * 32;
-            tmem_ld32(tmem + col, v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
-            tmem_ld32(tmem + 128 + col, v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
-            if (dc == n_chunks - 1) {  // last chunk: the cross terms too
-              tmem_ld32(tmem + 256 + col, v);
-#pragma unroll
-              for (int i = 0; i < 32; ++i) run_re[p * 32 + i] += v[i];
-              tmem_ld32(tmem + 384 + col, v);
-#pragma unroll
-              for (int i = 0; i < 32; ++i) run_im[p * 32 + i] += v[i];
-            }
-          }
-          fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(acc_empty);
-        }
-      }
-    }
-    // epilogue: thread = TMEM lane (row); this warp's 64 columns
-    const int row = q * 32 + lane;
-    const int64_t m = static_cast<int64_t>(m0) + row;
-    const bool row_ok = ok && m < a.m;
-    const int64_t ro = row_ok ? map_offset(a.rows, m) : 0;
-    float* C = a.C + static_cast<int64_t>(b) * a.c_bstride;
-    // The stage buffers are free here: this warp's last drain waited for the final MMA,
-    // which waited for every warp's last split; no TMA load is outstanding.
-    // Row-by-row stores (one row per warp store, through shared memory when the columns
-    // are the unit-stride side): the address-ordered block store costs this kernel
-    // registers its split loop needs.
-    const bool rows_unit = a.rows.n > 0 && a.rows.stride[a.rows.n - 1] == 1;
-    float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 33;  // [2][32][33]
-#pragma unroll
-    for (int cb = 0; cb < 2; ++cb) {
-      const int64_t nb0 = static_cast<int64_t>(n0) + half * 64 + cb * 32;
-      if (rows_unit) {
-        if (row_ok) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t n = nb0 + j;
-            if (n < a.n) {
-              const int64_t off = ro + map_offset(a.cols, n);
-              C[off] = run_re[cb * 32 + j];
-              C[a.c_plane + off] = run_im[cb * 32 + j];
-            }
-          }
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          tr[lane * 33 + j] = run_re[cb * 32 + j];
-          tr[32 * 33 + lane * 33 + j] = run_im[cb * 32 + j];
-        }
-        __syncwarp();
-        const int64_t n = nb0 + lane;
-        const bool col_ok = ok && n < a.n;
-        const int64_t co = col_ok ? map_offset(a.cols, n) : 0;
-        for (int r = 0; r < 32; ++r) {
-          const int64_t ro_r = __shfl_sync(0xffffffffu, ro, r);
-          const bool ok_r = __shfl_sync(0xffffffffu, row_ok ? 1 : 0, r) != 0;
-          if (ok_r && col_ok) {
-            C[ro_r + co] = tr[r * 33 + lane];
-            C[a.c_plane + ro_r + co] = tr[32 * 33 + r * 33 + lane];
-          }
-        }
-        __syncwarp();
-      }
-    }
-  }
-  fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C3::COLS));
-  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -1451,9 +615,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CB2::THREADS, 1)
 // within 1.5 % (the per-tile form ahead), at k >= 16384 the per-tile form is 4-8 % faster
 // (four ring stages instead of three, the per-tile cost being small there).
 constexpr int64_t kPairsPersistentMaxK = 2048;
-// waves of resident CTAs (or CTA pairs) per launch of the one-tile-per-CTA kernels, which
-// launch a deep step in bands of tiles (0: one launch for the step)
-constexpr int kBandWaves = 8;
 // steps with k <= 64 run contract_tcb_shallow_kernel
 constexpr bool kShallowKernel = true;
 struct CB2P {
@@ -2375,36 +1536,6 @@ __global__ void __launch_bounds__(CBS::THREADS, 1)
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-// 3-D map over one operand: (k, rows, plane), plane = 2*batch + {re, im}; box BK x rows.
-bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t k, int64_t planes, int64_t plane_elems,
-              int box_rows, int bk) {
-  auto enc = encoder();
-  if (!enc) return false;
-  cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows),
-                        static_cast<cuuint64_t>(planes)};
-  cuuint64_t strides[2] = {static_cast<cuuint64_t>(k * 4), static_cast<cuuint64_t>(plane_elems * 4)};
-  cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows), 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  const CUtensorMapSwizzle sw = bk * 4 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 // 3-D map over a split-BF16 operand: (k, rows, plane), plane = 4*copy + {re_hi, im_hi,
 // re_lo, im_lo}; box 32 x rows x 4 planes, 64-byte swizzle.
 bool make_map_split(CUtensorMap* map, const float* base, int64_t rows, int64_t k, int64_t copies,
@@ -2439,36 +1570,6 @@ bool make_map_split3m(CUtensorMap* map, const float* base, int64_t rows, int64_t
   return r == CUDA_SUCCESS;
 }
 
-// Tiles per batch entry in one launch of a one-tile-per-CTA kernel (one CTA per SM by its
-// shared memory): about kBandWaves waves of the SMs, for the reason given at
-// pair_band_tiles.
-int64_t sm_band_tiles(int64_t tiles, int32_t nb) {
-  static const int sms = [] {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess)
-      n = 0;
-    return n;
-  }();
-  if (kBandWaves <= 0 || sms <= 0 || nb <= 0) return tiles;
-  const int64_t want = (int64_t(sms) * kBandWaves + nb - 1) / nb;
-  return want < tiles ? want : tiles;
-}
-
-// Launch kern over `tiles` tiles x nb batch entries in bands of sm_band_tiles.
-template <typename Kern, typename... Args>
-cudaError_t launch_bands(Kern kern, int64_t tiles, int32_t nb, int threads, int smem, cudaStream_t st,
-                         const CUtensorMap& ta, const CUtensorMap& tb, const StepArgs& a, int* err) {
-  const int64_t per = sm_band_tiles(tiles, nb);
-  for (int64_t t0 = 0; t0 < tiles; t0 += per) {
-    const int64_t cnt = tiles - t0 < per ? tiles - t0 : per;
-    kern<<<dim3(static_cast<unsigned>(cnt), static_cast<unsigned>(nb)), threads, smem, st>>>(ta, tb, a, t0, err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
 cudaError_t launch_tcb3m(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
   // the shared-memory opt-in, once per process (thread-safe static initialisation)
   static const cudaError_t configured =
@@ -2482,35 +1583,6 @@ cudaError_t launch_tcb3m(const StepArgs& a, int32_t nb, int* err, cudaStream_t s
     return cudaErrorInvalidValue;
   const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
   return launch_bands(contract_tcb3m_kernel, tiles, nb, CB3::THREADS, CB3::SMEM, st, ta, tb, a, err);
-}
-
-template <int SPLIT>
-cudaError_t launch_split(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
-  static const cudaError_t configured =
-      cudaFuncSetAttribute(contract_tc_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<SPLIT>::SMEM);
-  if (configured != cudaSuccess) return configured;
-  CUtensorMap ta, tb;
-  const int64_t pa = a.a_bstride ? 2 * static_cast<int64_t>(nb) : 2;
-  const int64_t pb = a.b_bstride ? 2 * static_cast<int64_t>(nb) : 2;
-  constexpr int bk = Cfg<SPLIT>::BK;
-  if (!make_map(&ta, a.A, a.m, a.k, pa, a.a_plane, BM, bk) || !make_map(&tb, a.B, a.n, a.k, pb, a.b_plane, BN, bk))
-    return cudaErrorInvalidValue;
-  const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
-  return launch_bands(contract_tc_kernel<SPLIT>, tiles, nb, NTHREADS, Cfg<SPLIT>::SMEM, st, ta, tb, a, err);
-}
-
-cudaError_t launch_tc3(const StepArgs& a, int32_t nb, int* err, cudaStream_t st) {
-  static const cudaError_t configured =
-      cudaFuncSetAttribute(contract_tc3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C3::SMEM);
-  if (configured != cudaSuccess) return configured;
-  CUtensorMap ta, tb;
-  const int64_t pa = a.a_bstride ? 2 * static_cast<int64_t>(nb) : 2;
-  const int64_t pb = a.b_bstride ? 2 * static_cast<int64_t>(nb) : 2;
-  if (!make_map(&ta, a.A, a.m, a.k, pa, a.a_plane, BM, C3::BK) ||
-      !make_map(&tb, a.B, a.n, a.k, pb, a.b_plane, BN, C3::BK))
-    return cudaErrorInvalidValue;
-  const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
-  return launch_bands(contract_tc3_kernel, tiles, nb, C3::THREADS, C3::SMEM, st, ta, tb, a, err);
 }
 
 // Tiles per batch entry in one launch of the per-tile paired kernel: about kBandWaves waves
@@ -2642,6 +1714,8 @@ int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, b
       return (pair_tiles + per - 1) / per;
     }
   }
+  if (prec != TN_C64_BF16X3 && prec != kPrecBF16x3M)
+    return tf32_launches(m, n, nb, prec == TN_R32_TF32 || prec == TN_R32_3XTF32);
   const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
   const int64_t per = sm_band_tiles(tiles, nb);
   return (tiles + per - 1) / per;
@@ -2649,10 +1723,10 @@ int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, b
 
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
                                cudaStream_t st, bool pairs) {
-  if (!cplx || a.recs) return cudaErrorNotSupported;
+  if (a.maxplus) return cudaErrorNotSupported;
+  if (!cplx || prec == TN_C64_TF32 || prec == TN_C64_3XTF32) return launch_contract_tf32(a, nb, prec, cplx, err, st);
+  if (a.recs) return cudaErrorNotSupported;  // the BF16x3 kernels do not rescale
   if (prec == kPrecBF16x3M) return launch_tcb3m(a, nb, err, st);
-  if (prec == TN_C64_TF32) return launch_split<1>(a, nb, err, st);
-  if (prec == TN_C64_3XTF32) return launch_tc3(a, nb, err, st);
   if (prec == TN_C64_BF16X3) return launch_tcb(a, nb, err, st, pairs);
   return cudaErrorNotSupported;
 }

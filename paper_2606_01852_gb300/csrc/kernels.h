@@ -111,11 +111,18 @@ cudaError_t launch_bounded_wait_selftest(int arrive, uint64_t limit_ns, int* err
 // kernel (operands in the 3M split form).
 constexpr int32_t kPrecBF16x3M = 103;
 // pairs: BF16x3 4M steps with m >= 256 and k above the persistent kernel's range run on
-// pairs of SMs (contract_tcb2_kernel)
+// pairs of SMs (contract_tcb2_kernel). cplx false: a real step (TF32 and 3xTF32 forms).
+// a.recs (exponent scaling): TF32 and 3xTF32 forms only.
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
                                cudaStream_t st, bool pairs = true);
 // kernel launches launch_contract_tc makes for such a step (more than one for the deep
-// paired-SM steps, launched in bands of tiles)
+// steps, launched in bands of tiles)
 int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, bool pairs);
+// The TF32 and 3xTF32 forms (gemm_tf32.cu), complex (prec TN_C64_TF32 / TN_C64_3XTF32) or
+// real (TN_R32_TF32 / TN_R32_3XTF32, cplx false), with exponent scaling when a.recs is set;
+// and the launches such a step makes.
+cudaError_t launch_contract_tf32(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
+                                 cudaStream_t st);
+int64_t tf32_launches(int64_t m, int64_t n, int32_t nb, bool real);
 
 }  // namespace tn

@@ -19,7 +19,9 @@ namespace {
 constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-bool tc_prec_built(int32_t p) { return p == TN_C64_TF32 || p == TN_C64_3XTF32 || p == TN_C64_BF16X3; }
+bool tc_prec_built(int32_t p) {
+  return p == TN_C64_TF32 || p == TN_C64_3XTF32 || p == TN_C64_BF16X3 || p == TN_R32_TF32 || p == TN_R32_3XTF32;
+}
 
 bool is_tc_prec(int32_t p) {
   return p == TN_C64_TF32 || p == TN_C64_3XTF32 || p == TN_C64_BF16X3 || p == TN_R32_TF32 ||
@@ -102,13 +104,13 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     err = "the max-plus semiring runs in the R32 FP32 form without exponent scaling";
     return TN_ERR_UNSUPPORTED;
   }
-  if (pol.prec == TN_R32_TF32 || pol.prec == TN_R32_3XTF32 || pol.prec == TN_R32_BF16X3) {
-    err = "the real tensor-core forms are not built: real networks run in TN_R32_FP32_SIMT";
+  if (pol.prec == TN_R32_BF16X3) {
+    err = "the real BF16x3 form is not built: real networks take TN_R32_TF32, TN_R32_3XTF32 or TN_R32_FP32_SIMT";
     return TN_ERR_UNSUPPORTED;
   }
-  if (is_tc_prec(pol.prec) && pol.exp_scaling) {
-    err = "exponent scaling runs in the CUDA-core forms only (TN_C64_FP32_SIMT, TN_R32_FP32_SIMT): "
-          "the tensor-core kernels do not rescale their operands";
+  if (pol.prec == TN_C64_BF16X3 && pol.exp_scaling) {
+    err = "exponent scaling on tensor cores runs in the TF32 and 3xTF32 forms (and the CUDA-core forms): "
+          "the BF16x3 kernels do not rescale";
     return TN_ERR_UNSUPPORTED;
   }
   if (pol.complex_mult != 0 && pol.complex_mult != 4 && pol.complex_mult != 3) {
@@ -352,7 +354,7 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     }
     // The tensor-core kernel tiles 128 rows: give the row role to the operand that
     // fills them when only one orientation qualifies.
-    const bool tc_form_here = tc_form && P.is_complex && tc_prec_built(pol.prec) && tc_supported();
+    const bool tc_form_here = tc_form && tc_prec_built(pol.prec) && tc_supported();
     if (tc_form_here && !tc_step_ok(st.m, st.n, st.k, pol.prec) && tc_step_ok(st.n, st.m, st.k, pol.prec)) {
       std::swap(st.a, st.b);
       std::swap(st.M, st.N);
@@ -368,8 +370,9 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     const double t_simt = std::max(bytes / g_cost.hbm_bytes_per_s, flops / g_cost.simt_flops);
     st.cls = TN_CLASS_SIMT;
     if (tc_form_here && tc_step_ok(st.m, st.n, st.k, pol.prec)) {
-      // a step narrower than the 128-column tile uses that fraction of the tensor core
-      const double fill = std::min(1.0, double(st.n) / 128.0);
+      // a step narrower than the tile (128 columns, 256 for a real step) uses that fraction
+      // of the tensor core
+      const double fill = std::min(1.0, double(st.n) / (P.is_complex ? 128.0 : 256.0));
       const double rate = tc_flops(pol.complex_mult == 3 ? -3 : pol.prec);
       const double t_tc = std::max(bytes / g_cost.hbm_bytes_per_s, flops / (rate * fill));
       // ties (both bound by the same HBM bytes) go to the tensor-core kernel, whose

@@ -188,24 +188,53 @@ def test_batch_maxplus_policy_checks():
 
 def test_unbuilt_forms_are_refused_not_substituted():
     """A request the engine cannot run as asked is a status, not a silent change of form:
-    the real tensor-core forms are not built, and exponent scaling runs only in the
-    CUDA-core forms."""
+    the real BF16x3 form is not built, and the BF16x3 kernels do not rescale."""
     tn = ensure_built()
     from tn_inputs import ising_pf
     net = ising_pf.random_3regular_network(20, 1, beta=0.5)
     path = greedy.greedy_path(net, seed=0, alpha=1.0)
-    for prec in (tn.TN_R32_TF32, tn.TN_R32_3XTF32, tn.TN_R32_BF16X3):
+    for scaling in (False, True):
         with pytest.raises(tn.TnError) as e:
-            tn.Plan(net, path, prec=prec, exp_scaling=True, host_only=True)
+            tn.Plan(net, path, prec=tn.TN_R32_BF16X3, exp_scaling=scaling, host_only=True)
         assert e.value.status == tn.TN_ERR_UNSUPPORTED and "not built" in str(e.value)
     w = workloads.rc12()
-    for prec in ("tf32", "3xtf32", "bf16x3"):
+    for prec in ("bf16x3", "bf16x3m"):
         with pytest.raises(tn.TnError) as e:
             tn.Plan(w.net, w.path, prec=prec, exp_scaling=True, host_only=True)
         assert e.value.status == tn.TN_ERR_UNSUPPORTED and "scaling" in str(e.value)
-    # the CUDA-core forms take scaling
-    tn.Plan(net, path, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True, host_only=True).destroy()
-    tn.Plan(w.net, w.path, prec="fp32", exp_scaling=True, host_only=True).destroy()
+    # every other form takes scaling, real networks the TF32 and 3xTF32 forms
+    for prec in (tn.TN_R32_FP32_SIMT, tn.TN_R32_TF32, tn.TN_R32_3XTF32):
+        tn.Plan(net, path, prec=prec, exp_scaling=True, host_only=True).destroy()
+    for prec in ("fp32", "tf32", "3xtf32"):
+        tn.Plan(w.net, w.path, prec=prec, exp_scaling=True, host_only=True).destroy()
+
+
+def test_real_tensor_core_forms_take_the_large_steps():
+    """Eq. 6 on a real network: an Ising spin glass on a 16 x 16 lattice planned in the
+    real TF32 and 3xTF32 forms puts its large steps (the flops) on the tensor cores, in the
+    plain FP32 form on the CUDA cores; the step analysis is the same in every form."""
+    tn = ensure_built()
+    from tn_inputs import ising_pf
+    net = ising_pf.lattice_network(16, 16, 0.44, seed=1)
+    path = greedy.greedy_path(net, seed=0, alpha=1.0)
+    shapes = None
+    for prec in (tn.TN_R32_FP32_SIMT, tn.TN_R32_TF32, tn.TN_R32_3XTF32):
+        plan = tn.Plan(net, path, prec=prec, exp_scaling=True, host_only=True)
+        try:
+            steps = [plan.step(s) for s in range(len(path.pairs))]
+            info = plan.info()
+        finally:
+            plan.destroy()
+        sh = sorted((s["m"] * s["n"] * s["k"]) for s in steps)
+        shapes = shapes or sh
+        assert sh == shapes
+        tc_flops = info["flops_per_class"][tn.TN_CLASS_TC]
+        if prec == tn.TN_R32_FP32_SIMT:
+            assert tc_flops == 0
+        else:
+            assert tc_flops > 0.95 * info["flops"]
+            big = max(steps, key=lambda s: s["m"] * s["n"] * s["k"])
+            assert big["cls"] == tn.TN_CLASS_TC
 
 
 def test_cost_model_rates_drive_the_kernel_choice():

@@ -91,6 +91,27 @@ def ensemble(count: int, seed: int, n_min: int = 20, n_max: int = 60, beta: floa
     return [random_3regular_network(int(n), int(s), beta) for n, s in zip(sizes, seeds)]
 
 
+def lattice_network(rows: int, cols: int, beta: float, seed=None, J: float = 1.0) -> Network:
+    """Square lattice of rows x cols spins with open boundaries (nearest-neighbour bonds).
+    seed None: uniform coupling J (the ferromagnet); otherwise J_ij uniform in {-1, +1}
+    from a seeded generator (a +-J spin glass)."""
+    idx = lambda r, c: r * cols + c
+    edges = []
+    for r in range(rows):
+        for c in range(cols):
+            if c + 1 < cols:
+                edges.append((idx(r, c), idx(r, c + 1)))
+            if r + 1 < rows:
+                edges.append((idx(r, c), idx(r + 1, c)))
+    if seed is None:
+        Js = [J] * len(edges)
+    else:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        Js = list(rng.choice(np.array([-1.0, 1.0]), size=len(edges)))
+    return graph_network(rows * cols, edges, Js, beta,
+                         name=f"ising_lattice_{rows}x{cols}" + ("" if seed is None else f"_s{seed}"))
+
+
 def ring_network(n: int, J: float, beta: float) -> Network:
     edges = [(i, (i + 1) % n) for i in range(n)]
     edges = [(min(a, b), max(a, b)) for a, b in edges]

@@ -212,6 +212,18 @@ def ising_workload(net):
     return Workload(net.name, net, path, (), info)
 
 
+def isingsq20():
+    """Partition function of a +-J Ising spin glass on an open 20 x 20 square lattice
+    (400 spins, beta = 0.44, couplings from seed 1), real FP32 with per-intermediate
+    exponent scaling (ln Z ~ 350: Z is far beyond FP32), no slicing. Path: the greedy
+    search's seed 1, alpha 0 (2^40.1 flops, largest intermediate 2^29 elements, the least
+    flops of seeds 0-2 x alpha 0, 1 under a 2^30 cap)."""
+    net = ising_pf.lattice_network(20, 20, 0.44, seed=1)
+    w = Workload("isingsq20", net, greedy.greedy_path(net, seed=1, alpha=0.0))
+    w.info["exp_scaling"] = True
+    return w
+
+
 def ising3r(count, seed=3):
     return [ising_workload(n) for n in ising_pf.ensemble(count, seed)]
 
@@ -228,4 +240,5 @@ def kings_batch(count, seed=5):
 
 BY_NAME = {"rc12": rc12, "rc40": rc40, "rc40c14": rc40c14, "rc40c14sub": rc40c14sub, "rc40u": rc40u, "kising44": kising44, "kising55": kising55,
            "rc40open": rc40open,
-           "khex45": khex45, "ktri44": ktri44, "kings16": kings16, "sv26": sv26, "tcgemm": tcgemm}
+           "khex45": khex45, "ktri44": ktri44, "kings16": kings16, "sv26": sv26, "tcgemm": tcgemm,
+           "isingsq20": isingsq20}
