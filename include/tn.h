@@ -50,10 +50,11 @@ typedef enum {
  * Steps too small or too thin for a tensor-core tile run on the FP32 SIMT kernels
  * whatever the form (tn_plan_step reports each step's kernel). Real networks take the
  * TF32 and 3XTF32 forms on 128 x 256 tiles; R32_BF16X3 is not built. Exponent scaling
- * runs in every form but C64_BF16X3 (the tensor-core kernels apply the operands' exact
+ * runs in every form but the 3M product (the tensor-core kernels apply the operands' exact
  * power-of-two scales to the accumulated result, the same values as scaling the operands
- * on load). tn_plan returns TN_ERR_UNSUPPORTED for R32_BF16X3 and for C64_BF16X3 with
- * exponent scaling rather than running another form. */
+ * on load; scaled BF16X3 steps keep one SM per tile). tn_plan returns TN_ERR_UNSUPPORTED
+ * for R32_BF16X3 and for the 3M product with exponent scaling rather than running another
+ * form. */
 typedef enum {
   TN_C64_FP32_SIMT = 0,
   TN_C64_TF32 = 1,

@@ -377,7 +377,8 @@ tn_status tn_plan_launches(tn_plan_t plan, int64_t slice_count, int64_t* out) {
     for (const StepRec& st : P.steps) {
       if (!st.batched && p > 0) continue;
       const int32_t nbs = st.batched ? nb : 1;
-      if (st.cls == TN_CLASS_TC) n += tc_launches(st.m, st.n, st.k, nbs, form, pairs && !st.single_sm);
+      if (st.cls == TN_CLASS_TC)
+        n += tc_launches(st.m, st.n, st.k, nbs, form, pairs && !st.single_sm, P.policy.exp_scaling != 0);
       else if (st.cls == TN_CLASS_SPLITK) n += 2;
       else if (st.cls == TN_CLASS_SIMT) n += st.ksplit > 1 ? 2 : 1;
       else n += 1;
@@ -465,12 +466,13 @@ tn_status tn_plan_autotune(tn_plan_t plan, const void* const* inputs, void* outp
   }
   // the steps with a choice: BF16x3 4M tensor-core steps that the paired-SM kernels take
   std::vector<int32_t> cand;
-  const bool bf16x3_4m = P.policy.prec == TN_C64_BF16X3 && P.policy.complex_mult != 3;
+  // (scaled plans run every BF16x3 step on one SM per tile: no choice)
+  const bool bf16x3_4m = P.policy.prec == TN_C64_BF16X3 && P.policy.complex_mult != 3 && !P.policy.exp_scaling;
   if (bf16x3_4m && (P.policy.flags & TN_PLAN_SINGLE_SM_TILES) == 0)
     for (int32_t s = 0; s < (int32_t)P.steps.size(); ++s) {
       const StepRec& st = P.steps[s];
-      if (st.cls == TN_CLASS_TC && tc_launches(st.m, st.n, st.k, 1, TN_C64_BF16X3, true) >= 1 && st.m >= 256 &&
-          st.k > 256)
+      if (st.cls == TN_CLASS_TC && tc_launches(st.m, st.n, st.k, 1, TN_C64_BF16X3, true, false) >= 1 &&
+          st.m >= 256 && st.k > 256)
         cand.push_back(s);
     }
   if (cand.empty()) return TN_OK;

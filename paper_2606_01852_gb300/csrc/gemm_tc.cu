@@ -86,6 +86,9 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// SCALED: exponent scaling (a.recs): the epilogue applies the operands' scales and records
+// the result's exponent (tc_scale); every scaled BF16x3 4M step runs this kernel.
+template <bool SCALED>
 __global__ void __launch_bounds__(CB::THREADS, 1)
     contract_tcb_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         StepArgs a, int64_t t_first, int* err) {
@@ -259,6 +262,18 @@ __global__ void __launch_bounds__(CB::THREADS, 1)
     // this warp's 32 x 64 results, Re then Im, rows of 65 floats: the registers are free
     // before the stores begin
     float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 65;
+    if constexpr (SCALED) {
+      // (rows past m and columns past n hold zeros: their operands were zero-filled by TMA)
+      const TcScale sc = tc_scale(a, b);
+      int lmax = -127;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        run_re[j] = run_re[j] * sc.sa * sc.sb;
+        run_im[j] = run_im[j] * sc.sa * sc.sb;
+        lmax = max(lmax, exp_of(fmaxf(fabsf(run_re[j]), fabsf(run_im[j]))));
+      }
+      tc_scale_finish(a, b, lmax, t == 0 && threadIdx.x == 64);
+    }
 #pragma unroll
     for (int j = 0; j < 64; ++j) {
       tr[lane * 65 + j] = run_re[j];
@@ -1607,7 +1622,10 @@ int64_t pair_band_tiles(int64_t pair_tiles, int32_t nb) {
 
 cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st, bool pairs) {
   static const cudaError_t configured = [] {
-    cudaError_t e = cudaFuncSetAttribute(contract_tcb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB::SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(contract_tcb_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, CB::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(contract_tcb_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, CB::SMEM);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(contract_tcb_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                CBP::SMEM);
@@ -1623,6 +1641,14 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st,
   CUtensorMap ta, tb;
   const int64_t ca = a.a_bstride ? static_cast<int64_t>(nb) : 1;
   const int64_t cb = a.b_bstride ? static_cast<int64_t>(nb) : 1;
+  if (a.recs) {
+    // exponent scaling: one SM per tile, launched in bands, for every k
+    if (!make_map_split(&ta, a.A, a.m, a.k, ca, a.a_plane, BM) ||
+        !make_map_split(&tb, a.B, a.n, a.k, cb, a.b_plane, BN))
+      return cudaErrorInvalidValue;
+    const int64_t tiles = ((a.m + BM - 1) / BM) * ((a.n + BN - 1) / BN);
+    return launch_bands(contract_tcb_kernel<true>, tiles, nb, CB::THREADS, CB::SMEM, st, ta, tb, a, err);
+  }
   if (pairs && a.k > CBP::MAX_K && a.m >= 2 * BM) {
     // paired SMs: this CTA's 128 rows of A and 64 rows of B per box
     if (!make_map_split(&ta, a.A, a.m, a.k, ca, a.a_plane, BM) ||
@@ -1682,7 +1708,7 @@ cudaError_t launch_tcb(const StepArgs& a, int32_t nb, int* err, cudaStream_t st,
     contract_tcb_persistent_kernel<<<grid, CB::THREADS, CBP::SMEM, st>>>(ta, tb, a, nb, err);
     return cudaGetLastError();
   }
-  return launch_bands(contract_tcb_kernel, tiles, nb, CB::THREADS, CB::SMEM, st, ta, tb, a, err);
+  return launch_bands(contract_tcb_kernel<false>, tiles, nb, CB::THREADS, CB::SMEM, st, ta, tb, a, err);
 }
 
 }  // namespace
@@ -1704,8 +1730,8 @@ bool tc_step_ok(int64_t m, int64_t n, int64_t k, int32_t prec) {
          n < (int64_t(1) << 31);
 }
 
-int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, bool pairs) {
-  if (prec == TN_C64_BF16X3) {
+int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, bool pairs, bool scaled) {
+  if (prec == TN_C64_BF16X3 && !scaled) {
     if (k <= CBP::MAX_K) return 1;  // persistent kernels
     if (pairs && m >= 2 * BM) {
       if (k <= kPairsPersistentMaxK) return 1;
@@ -1725,8 +1751,7 @@ cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool
                                cudaStream_t st, bool pairs) {
   if (a.maxplus) return cudaErrorNotSupported;
   if (!cplx || prec == TN_C64_TF32 || prec == TN_C64_3XTF32) return launch_contract_tf32(a, nb, prec, cplx, err, st);
-  if (a.recs) return cudaErrorNotSupported;  // the BF16x3 kernels do not rescale
-  if (prec == kPrecBF16x3M) return launch_tcb3m(a, nb, err, st);
+  if (prec == kPrecBF16x3M) return a.recs ? cudaErrorNotSupported : launch_tcb3m(a, nb, err, st);
   if (prec == TN_C64_BF16X3) return launch_tcb(a, nb, err, st, pairs);
   return cudaErrorNotSupported;
 }

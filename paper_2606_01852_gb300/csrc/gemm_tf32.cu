@@ -25,12 +25,13 @@
 namespace tn {
 namespace {
 
-constexpr int NTHREADS = 192;
 
 // TF32 form (contract_tc_kernel). A complex stage holds A_re A_im B_re B_im (3 stages, one
-// CTA per SM; tensor memory D_rr @0, D_ii @128, D_x @256). A real one holds A B_0 B_1, the
-// two B tiles of a 256-column tile, in 2 stages, and its accumulator takes 256 columns: two
-// CTAs fit on an SM, so one's epilogue overlaps the other's MMAs.
+// CTA per SM; tensor memory D_rr @0, D_ii @128, D_x @256; warps 0 TMA, 1 MMA, 2-5 epilogue).
+// A real one holds A B_0 B_1, the two B tiles of a 256-column tile, in 2 stages, and its
+// accumulator takes 256 columns: two CTAs fit on an SM, so one's epilogue overlaps the
+// other's MMAs; eight epilogue warps (2-9: warp w drains TMEM lane quarter w % 4, columns
+// 128 ((w - 2) / 4) .. + 127) store its 32K results.
 template <bool REAL>
 struct Cfg {
   static constexpr int BK = 32;                             // fp32 elements per k-block
@@ -40,9 +41,11 @@ struct Cfg {
   static constexpr int OFF_B = REAL ? TILE_A : 2 * TILE_A;  // first B tile
   static constexpr int STAGE = REAL ? TILE_A + 2 * TILE_B : 2 * TILE_A + 2 * TILE_B;
   static constexpr int STAGES = REAL ? 2 : 3;
+  static constexpr int THREADS = REAL ? 320 : 192;
   static constexpr uint32_t TMEM_COLS = REAL ? 256 : 512;
   static constexpr int SMEM = STAGES * STAGE + 1024 /*barriers*/ + 1024 /*align*/;
   static_assert(SMEM <= 232448 && STAGE % 1024 == 0 && OFF_B % 1024 == 0, "stages fit, swizzle-aligned tiles");
+  static_assert((THREADS / 32 - 2) * 2 * 32 * 33 * 4 <= STAGES * STAGE, "epilogue transposes fit the stages");
 };
 
 // v rounded to the nearest value with 10 fraction bits (ties away from zero): half a unit in
@@ -52,44 +55,12 @@ __device__ __forceinline__ float tf32_rn(float v) {
   return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
 }
 
-// Exponent scaling on a tensor-core step. The operands are read as stored, so their
-// scales 2^-e_A and 2^-e_B multiply the accumulated result instead of each operand: the
-// same values as scaling on load, as a power of two commutes with every rounding in
-// between (the operand truncation to TF32, the products and the sums) as long as no value
-// leaves FP32's normal range. Stored intermediates are sums of products of renormalised
-// operands (a small multiple of k in magnitude), so their unscaled products stay far inside
-// it; leaves are read as given, so a leaf's entries times its partner's must stay inside it.
-struct TcScale {
-  float sa, sb;
-};
-__device__ __forceinline__ TcScale tc_scale(const StepArgs& a, int b) {
-  TcScale s{1.f, 1.f};
-  if (a.recs) {
-    s.sa = pow2_neg(scale_exp(a.recs + a.rec_a + (a.a_bstride ? b : 0)));
-    s.sb = pow2_neg(scale_exp(a.recs + a.rec_b + (a.b_bstride ? b : 0)));
-  }
-  return s;
-}
-// After a warp's stores (all 32 lanes): the warp's largest exponent into C's record, and
-// from one thread per batch entry C's log scale (its operands' log scales and exponents).
-__device__ __forceinline__ void tc_scale_finish(const StepArgs& a, int b, int lmax, bool log_thread) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-  ScaleRec* rc = a.recs + a.rec_c + (a.c_bstride ? b : 0);
-  if ((threadIdx.x & 31) == 0) atomicMax(&rc->emax, lmax);
-  if (log_thread) {
-    const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
-    const ScaleRec* rb = a.recs + a.rec_b + (a.b_bstride ? b : 0);
-    rc->log2 = ra->log2 + rb->log2 + scale_exp(ra) + scale_exp(rb);
-  }
-}
-
 // REAL: a real step. Its tile is 128 x 256: the stage's B_re and B_im slots hold the B
 // tiles of columns n0 .. n0 + 127 and n0 + 128 .. n0 + 255, one 128 x 256 MMA per k-atom
 // reads them as one operand (the A_im slot stays empty), and the accumulator's 256
 // columns are the tile's output columns in order. SCALED: exponent scaling (a.recs).
 template <bool REAL, bool SCALED>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(Cfg<REAL>::THREADS, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                        StepArgs a, int64_t t_first, int* err) {
   using G = Cfg<REAL>;
@@ -217,7 +188,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float* tr = reinterpret_cast<float*>(smem) + (warp - 2) * 2 * 32 * 33;  // [2][32][33]
     const TcScale sc = tc_scale(a, b);
     int lmax = -127;
-    for (int c = 0; c < TN / 32; ++c) {
+    // this warp's 32-column blocks: all of a complex tile's, half of a real tile's
+    constexpr int NCB = REAL ? TN / 64 : TN / 32;
+    const int c_first = REAL ? ((warp - 2) >> 2) * NCB : 0;
+    for (int c = c_first; c < c_first + NCB; ++c) {
       const int64_t nb0 = static_cast<int64_t>(n0) + c * 32;
       if constexpr (REAL) {
         float v[32];
@@ -653,7 +627,7 @@ cudaError_t launch_tf32(const StepArgs& a, int32_t nb, int* err, cudaStream_t st
   if (!make_map(&ta, a.A, a.m, a.k, map_planes(a.a_bstride != 0, nb, REAL), a.a_plane, BM, G::BK) ||
       !make_map(&tb, a.B, a.n, a.k, map_planes(a.b_bstride != 0, nb, REAL), a.b_plane, BN, G::BK))
     return cudaErrorInvalidValue;
-  return launch_bands(contract_tc_kernel<REAL, SCALED>, tf32_tiles(a.m, a.n, REAL), nb, NTHREADS, G::SMEM, st, ta,
+  return launch_bands(contract_tc_kernel<REAL, SCALED>, tf32_tiles(a.m, a.n, REAL), nb, G::THREADS, G::SMEM, st, ta,
                       tb, a, err);
 }
 

@@ -112,12 +112,13 @@ cudaError_t launch_bounded_wait_selftest(int arrive, uint64_t limit_ns, int* err
 constexpr int32_t kPrecBF16x3M = 103;
 // pairs: BF16x3 4M steps with m >= 256 and k above the persistent kernel's range run on
 // pairs of SMs (contract_tcb2_kernel). cplx false: a real step (TF32 and 3xTF32 forms).
-// a.recs (exponent scaling): TF32 and 3xTF32 forms only.
+// a.recs (exponent scaling): every form but the 3M product (a scaled BF16x3 4M step runs
+// contract_tcb_kernel, one SM per tile, for every k).
 cudaError_t launch_contract_tc(const StepArgs& a, int32_t nb, int32_t prec, bool cplx, int* err,
                                cudaStream_t st, bool pairs = true);
 // kernel launches launch_contract_tc makes for such a step (more than one for the deep
 // steps, launched in bands of tiles)
-int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, bool pairs);
+int64_t tc_launches(int64_t m, int64_t n, int64_t k, int32_t nb, int32_t prec, bool pairs, bool scaled);
 // The TF32 and 3xTF32 forms (gemm_tf32.cu), complex (prec TN_C64_TF32 / TN_C64_3XTF32) or
 // real (TN_R32_TF32 / TN_R32_3XTF32, cplx false), with exponent scaling when a.recs is set;
 // and the launches such a step makes.

@@ -108,9 +108,8 @@ tn_status build_plan(const tn_network* net, const tn_path* path, const int32_t* 
     err = "the real BF16x3 form is not built: real networks take TN_R32_TF32, TN_R32_3XTF32 or TN_R32_FP32_SIMT";
     return TN_ERR_UNSUPPORTED;
   }
-  if (pol.prec == TN_C64_BF16X3 && pol.exp_scaling) {
-    err = "exponent scaling on tensor cores runs in the TF32 and 3xTF32 forms (and the CUDA-core forms): "
-          "the BF16x3 kernels do not rescale";
+  if (pol.prec == TN_C64_BF16X3 && pol.complex_mult == 3 && pol.exp_scaling) {
+    err = "exponent scaling is not built for the 3M product: the 4M BF16x3 form (complex_mult 4) takes it";
     return TN_ERR_UNSUPPORTED;
   }
   if (pol.complex_mult != 0 && pol.complex_mult != 4 && pol.complex_mult != 3) {

@@ -11,6 +11,7 @@
 
 #include "kernels.h"
 #include "mbarrier.cuh"
+#include "scale.cuh"
 #include "split_bf16.cuh"
 
 namespace tn {
@@ -361,6 +362,38 @@ __device__ __forceinline__ void store_block(float* C, int64_t plane, int split, 
       if constexpr (REAL) C[ro_r + co] = t[r * pitch + lane];
       else store_cplx(C, plane, ro_r + co, t[r * pitch + lane], t[cs + r * pitch + lane], split);
     }
+  }
+}
+
+// Exponent scaling on a tensor-core step. The operands are read as stored, so their
+// scales 2^-e_A and 2^-e_B multiply the accumulated result instead of each operand: the
+// same values as scaling on load, as a power of two commutes with every rounding in
+// between (the operands' TF32 truncation or hi/lo split, the products and the sums) as long
+// as no value leaves FP32's normal range. Stored intermediates are sums of products of renormalised
+// operands (a small multiple of k in magnitude), so their unscaled products stay far inside
+// it; leaves are read as given, so a leaf's entries times its partner's must stay inside it.
+struct TcScale {
+  float sa, sb;
+};
+__device__ __forceinline__ TcScale tc_scale(const StepArgs& a, int b) {
+  TcScale s{1.f, 1.f};
+  if (a.recs) {
+    s.sa = pow2_neg(scale_exp(a.recs + a.rec_a + (a.a_bstride ? b : 0)));
+    s.sb = pow2_neg(scale_exp(a.recs + a.rec_b + (a.b_bstride ? b : 0)));
+  }
+  return s;
+}
+// After a warp's stores (all 32 lanes): the warp's largest exponent into C's record, and
+// from one thread per batch entry C's log scale (its operands' log scales and exponents).
+__device__ __forceinline__ void tc_scale_finish(const StepArgs& a, int b, int lmax, bool log_thread) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  ScaleRec* rc = a.recs + a.rec_c + (a.c_bstride ? b : 0);
+  if ((threadIdx.x & 31) == 0) atomicMax(&rc->emax, lmax);
+  if (log_thread) {
+    const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
+    const ScaleRec* rb = a.recs + a.rec_b + (a.b_bstride ? b : 0);
+    rc->log2 = ra->log2 + rb->log2 + scale_exp(ra) + scale_exp(rb);
   }
 }
 

@@ -188,7 +188,7 @@ def test_batch_maxplus_policy_checks():
 
 def test_unbuilt_forms_are_refused_not_substituted():
     """A request the engine cannot run as asked is a status, not a silent change of form:
-    the real BF16x3 form is not built, and the BF16x3 kernels do not rescale."""
+    the real BF16x3 form is not built, and the 3M product does not rescale."""
     tn = ensure_built()
     from tn_inputs import ising_pf
     net = ising_pf.random_3regular_network(20, 1, beta=0.5)
@@ -198,14 +198,13 @@ def test_unbuilt_forms_are_refused_not_substituted():
             tn.Plan(net, path, prec=tn.TN_R32_BF16X3, exp_scaling=scaling, host_only=True)
         assert e.value.status == tn.TN_ERR_UNSUPPORTED and "not built" in str(e.value)
     w = workloads.rc12()
-    for prec in ("bf16x3", "bf16x3m"):
-        with pytest.raises(tn.TnError) as e:
-            tn.Plan(w.net, w.path, prec=prec, exp_scaling=True, host_only=True)
-        assert e.value.status == tn.TN_ERR_UNSUPPORTED and "scaling" in str(e.value)
+    with pytest.raises(tn.TnError) as e:
+        tn.Plan(w.net, w.path, prec="bf16x3m", exp_scaling=True, host_only=True)
+    assert e.value.status == tn.TN_ERR_UNSUPPORTED and "scaling" in str(e.value)
     # every other form takes scaling, real networks the TF32 and 3xTF32 forms
     for prec in (tn.TN_R32_FP32_SIMT, tn.TN_R32_TF32, tn.TN_R32_3XTF32):
         tn.Plan(net, path, prec=prec, exp_scaling=True, host_only=True).destroy()
-    for prec in ("fp32", "tf32", "3xtf32"):
+    for prec in ("fp32", "tf32", "3xtf32", "bf16x3"):
         tn.Plan(w.net, w.path, prec=prec, exp_scaling=True, host_only=True).destroy()
 
 
