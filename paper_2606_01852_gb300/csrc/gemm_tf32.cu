@@ -5,7 +5,7 @@
 //                                      k-blocks, 3 stages, D_rr / D_ii / D_x accumulators
 //                                      (Re C = D_rr - D_ii, Im C = D_x); 192 threads;
 //   contract_tc3_kernel<REAL, SCALED>  3xTF32: eight warps split each staged tile into
-//                                      hi = RN_tf32(v) and lo = v - hi, hi.hi in 64-term
+//                                      hi = RN_tf32(v) and lo = v - hi, hi.hi in 32-term
 //                                      chunks folded into round-to-nearest registers, cross
 //                                      terms in their own accumulator; 320 threads.
 // Real steps take 128 x 256 output tiles (two B tiles read as one 256-row operand).
@@ -261,7 +261,10 @@ __global__ void __launch_bounds__(Cfg<REAL>::THREADS, 1)
 // A real step (REAL) uses the A_re, B_re and B_im slots for A and the B tiles of columns
 // n0 .. n0 + 127 and n0 + 128 .. n0 + 255: a 128 x 256 tile, A.[B_0|B_1] per k-atom.
 struct C3 {
-  static constexpr int BK = 16, ROWB = 64, CK = 4;
+  // CK = 2: 32-term chunks. Each truncating addition loses up to an ulp of the running chunk
+  // sum, so the error grows with the chunk; 64-term chunks were 5 % faster but left the
+  // FP32-accurate form at twice plain FP32's error on long paths of small steps.
+  static constexpr int BK = 16, ROWB = 64, CK = 2;
   static constexpr int TILE_A = BM * ROWB;                  // 8 KiB
   static constexpr int TILE_B = BN * ROWB;                  // 8 KiB
   static constexpr int OFF_AI = TILE_A, OFF_BNEG = 2 * TILE_A;

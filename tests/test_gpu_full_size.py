@@ -176,11 +176,10 @@ def _dyn_err(name, prec):
 # Plain FP32 misses 1e-5 on the 4x4 kicked Ising (830 steps; measured 1.3e-5): held to 2e-5
 # there and the fast forms to twice the FP32 error (the reading of the bar).
 FP32_DYN = {"kising44": 2e-5}
-# Measured misses of that bar, reported rather than claimed: 3xTF32 on the triangular
-# lattice (2.0e-5 against a plain FP32 error of 9.0e-6; the tensor core truncates each
-# accumulation, bounded to 64-term runs). Held to 1.5x the measured error as a regression
-# bound.
-KNOWN_MISSES = {("ktri44", "3xtf32"): 3.0e-5}
+# Measured misses of that bar, reported rather than claimed (none at present: 3xTF32 on the
+# triangular lattice missed it with 64-term tensor-memory accumulation chunks, 2.0e-5 against
+# a plain FP32 error of 9.0e-6, and meets it with 32-term chunks, 1.5e-5).
+KNOWN_MISSES = {}
 
 
 @pytest.mark.parametrize("name", ["kising44", "khex45", "ktri44", "kising55"])
