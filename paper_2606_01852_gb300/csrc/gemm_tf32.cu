@@ -398,11 +398,6 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
       const uint32_t d_hi = tmem, d_lo = tmem + 256;
       bool ok = true;
       for (int c = 0; c < n_chunks && ok; ++c) {
-        if (!mbar_wait(acc_empty, (c & 1) ^ 1)) {
-          atomicExch(err, 13);
-          break;
-        }
-        fence_after();
         const int kb_end = min(num_kb, (c + 1) * CK);
         for (int kb = c * CK; kb < kb_end; ++kb) {
           const int s = kb % STAGES;
@@ -414,26 +409,45 @@ __global__ void __launch_bounds__(C3::THREADS, 1)
           fence_after();
           const uint32_t st = su32(smem + s * STAGE);
           const uint32_t lo = su32(lo_base + (kb & 1) * STAGE);
+          // the cross terms first: their accumulator runs over all of k (it is ~2^-11 of the
+          // result, so its own truncation is negligible) and is read once, after the last
+          // chunk, so a chunk's first k-block issues them before the wait for the previous
+          // chunk's fold, which then overlaps tensor-core work
 #pragma unroll
           for (int j = 0; j < BK / 8; ++j) {
-            const uint32_t acc = (kb > c * CK || j > 0) ? 1u : 0u;
             const uint64_t ar = smem_desc<ROWB>(st + j * 32), ai = smem_desc<ROWB>(st + C3::OFF_AI + j * 32);
             const uint64_t b_ri = smem_desc<ROWB>(st + C3::OFF_BR + j * 32);    // [B_re | B_im]
             const uint64_t b_nr = smem_desc<ROWB>(st + C3::OFF_BNEG + j * 32);  // [-B_im | B_re]
             const uint64_t arl = smem_desc<ROWB>(lo + j * 32), ail = smem_desc<ROWB>(lo + C3::OFF_AI + j * 32);
             const uint64_t bl_ri = smem_desc<ROWB>(lo + C3::OFF_BR + j * 32);
             const uint64_t bl_nr = smem_desc<ROWB>(lo + C3::OFF_BNEG + j * 32);
-            // hi.hi products into the main accumulators (Re | Im); the small cross terms into
-            // their own, so the main sums take only two truncating additions per 8 terms
-            // (one for a real step: its 256 columns are all hi.hi)
-            mma_tf32(d_hi, ar, b_ri, idesc, acc);
-            if constexpr (!REAL) mma_tf32(d_hi, ai, b_nr, idesc, 1u);
-            // the cross-term accumulator runs over all of k (it is ~2^-11 of the result,
-            // so its own truncation is negligible) and is read once, after the last chunk
             mma_tf32(d_lo, arl, b_ri, idesc, (kb > 0 || j > 0) ? 1u : 0u);
             if constexpr (!REAL) mma_tf32(d_lo, ail, b_nr, idesc, 1u);
             mma_tf32(d_lo, ar, bl_ri, idesc, 1u);
             if constexpr (!REAL) mma_tf32(d_lo, ai, bl_nr, idesc, 1u);
+          }
+          if (kb == c * CK) {
+            // the chunk accumulator must have been folded before the hi MMAs reuse it
+            if (!mbar_wait(acc_empty, (c & 1) ^ 1)) {
+              atomicExch(err, 13);
+              ok = false;
+              mma_commit(&empty[s]);
+              mma_commit(&lo_empty[kb & 1]);
+              break;
+            }
+            fence_after();
+          }
+          // hi.hi products into the main accumulators (Re | Im), so the main sums take only
+          // two truncating additions per 8 terms (one for a real step: its 256 columns are
+          // all hi.hi)
+#pragma unroll
+          for (int j = 0; j < BK / 8; ++j) {
+            const uint32_t acc = (kb > c * CK || j > 0) ? 1u : 0u;
+            const uint64_t ar = smem_desc<ROWB>(st + j * 32), ai = smem_desc<ROWB>(st + C3::OFF_AI + j * 32);
+            const uint64_t b_ri = smem_desc<ROWB>(st + C3::OFF_BR + j * 32);
+            const uint64_t b_nr = smem_desc<ROWB>(st + C3::OFF_BNEG + j * 32);
+            mma_tf32(d_hi, ar, b_ri, idesc, acc);
+            if constexpr (!REAL) mma_tf32(d_hi, ai, b_nr, idesc, 1u);
           }
           mma_commit(&empty[s]);
           mma_commit(&lo_empty[kb & 1]);
