@@ -3,7 +3,8 @@
 // exponent scaling:
 //   contract_tc_kernel<REAL, SCALED>   TF32: A_re, A_im, B_re, B_im fp32 tiles, 32-deep
 //                                      k-blocks, 3 stages, D_rr / D_ii / D_x accumulators
-//                                      (Re C = D_rr - D_ii, Im C = D_x); 192 threads;
+//                                      (Re C = D_rr - D_ii, Im C = D_x); 192 threads (real
+//                                      tiles: 2 stages, 320 threads, two CTAs per SM);
 //   contract_tc3_kernel<REAL, SCALED>  3xTF32: eight warps split each staged tile into
 //                                      hi = RN_tf32(v) and lo = v - hi, hi.hi in 32-term
 //                                      chunks folded into round-to-nearest registers, cross
@@ -24,7 +25,6 @@
 
 namespace tn {
 namespace {
-
 
 // TF32 form (contract_tc_kernel). A complex stage holds A_re A_im B_re B_im (3 stages, one
 // CTA per SM; tensor memory D_rr @0, D_ii @128, D_x @256; warps 0 TMA, 1 MMA, 2-5 epilogue).
@@ -55,10 +55,10 @@ __device__ __forceinline__ float tf32_rn(float v) {
   return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xffffe000u);
 }
 
-// REAL: a real step. Its tile is 128 x 256: the stage's B_re and B_im slots hold the B
-// tiles of columns n0 .. n0 + 127 and n0 + 128 .. n0 + 255, one 128 x 256 MMA per k-atom
-// reads them as one operand (the A_im slot stays empty), and the accumulator's 256
-// columns are the tile's output columns in order. SCALED: exponent scaling (a.recs).
+// REAL: a real step. Its tile is 128 x 256: the stage holds A and the B tiles of columns
+// n0 .. n0 + 127 and n0 + 128 .. n0 + 255 side by side, one 128 x 256 MMA per k-atom reads
+// the two as one operand, and the accumulator's 256 columns are the tile's output columns
+// in order. SCALED: exponent scaling (a.recs).
 template <bool REAL, bool SCALED>
 __global__ void __launch_bounds__(Cfg<REAL>::THREADS, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
