@@ -86,7 +86,7 @@ typedef struct {
   int32_t prec;            /* tn_precision */
   int32_t complex_mult;    /* 4 (4M); 3 (3M, Gauss) with TN_C64_BF16X3 only, else rejected */
   int32_t exp_scaling;     /* 1: per-intermediate power-of-two scaling, log scale in FP64
-                              (FP32_SIMT forms only) */
+                              (every form but the 3M product) */
   int32_t max_slice_batch; /* slices per device pass; 0 = as many as fit in free HBM */
   uint32_t flags;          /* TN_PLAN_* */
   int32_t semiring;        /* tn_semiring */

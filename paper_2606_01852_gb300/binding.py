@@ -210,7 +210,8 @@ SEMIRINGS = {"standard": 0, "maxplus": 1}
 
 def make_policy(prec=TN_C64_FP32_SIMT, exp_scaling=False, max_slice_batch=0, host_only=False, semiring="standard",
                 complex_mult=4, single_sm_tiles=False):
-    """prec: a tn_precision or a form name ("bf16x3m" = BF16X3 with the 3M product)."""
+    """prec: a tn_precision or a form name ("bf16x3m" = BF16X3 with the 3M product; the
+    real forms "r32_fp32", "r32_tf32", "r32_3xtf32")."""
     if isinstance(prec, str):
         if prec in THREE_M:
             complex_mult = 3
