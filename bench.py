@@ -852,32 +852,42 @@ def run_serve_bench(args):
             p.destroy()
         return out, results
 
-    def burst(pack_max, n_burst=2048):
-        """n_burst small requests (amplitudes and partition functions) submitted at once (one
-        tn_serve_submit_batch): requests/s from the submission to the last completion."""
-        p_amp = tn.Plan(amp_w.net, amp_w.path, prec=PREC[args.serve_prec])
+    def burst(pack_max, n_burst=2048, prec=None, inflight=None, streams=None, large=False):
+        """n_burst requests submitted at once (one tn_serve_submit_batch): requests/s from the
+        submission to the last completion. large=False: the small ones (amplitudes and
+        partition functions); large=True: the mix as it arrives (the 5x5 kicked-Ising
+        expectations included)."""
+        prec = PREC[args.serve_prec] if prec is None else prec
+        p_amp = tn.Plan(amp_w.net, amp_w.path, prec=prec)
         p_pf = [tn.Plan(w.net, w.path, prec=tn.TN_R32_FP32_SIMT, exp_scaling=True) for w in pf_pool]
-        small = [i for i in range(n_req) if cls[i] != 2][:n_burst]
-        plan_of = lambda i: p_amp if cls[i] == 0 else p_pf[pf_idx[i]]
-        srv = tn.Server(max_inflight=args.serve_inflight, n_streams=args.serve_streams, queue_capacity=1 << 20,
-                        pack_max=pack_max)
-        for i in small[:64]:
+        p_kis = tn.Plan(kis.net, kis.path, prec=prec) if large else None
+        sel = [i for i in range(n_req) if large or cls[i] != 2][:n_burst]
+        plan_of = lambda i: p_amp if cls[i] == 0 else (p_pf[pf_idx[i]] if cls[i] == 1 else p_kis)
+        srv = tn.Server(max_inflight=inflight or args.serve_inflight, n_streams=streams or args.serve_streams,
+                        queue_capacity=1 << 20, pack_max=pack_max)
+        warm = sel[:64] + ([next(i for i in range(n_req) if cls[i] == 2)] if large else [])
+        for i in warm:
             srv.poll(srv.submit(plan_of(i), inputs(i)), np.zeros(2), None, -1)
-        ins = [inputs(i) for i in small]
+        ins = [inputs(i) for i in sel]
         t0 = time.perf_counter()
-        ts = srv.submit_batch([(plan_of(i), x) for i, x in zip(small, ins)])
+        ts = srv.submit_batch([(plan_of(i), x) for i, x in zip(sel, ins)])
         for t in ts:
             srv.poll(t, np.zeros(2), None, -1)
         dt = time.perf_counter() - t0
         st = srv.stats()
         srv.destroy()
-        for p in [p_amp] + p_pf:
+        for p in [p_amp] + p_pf + ([p_kis] if large else []):
             p.destroy()
-        return {"requests": len(small), "seconds": dt, "requests_per_s": len(small) / dt,
-                "launches": st["plan_launches"] + st["packs"] - 64, "max_pack": st["max_pack"]}
+        return {"requests": len(sel), "large_requests": int(sum(cls[i] == 2 for i in sel)), "seconds": dt,
+                "requests_per_s": len(sel) / dt, "launches": st["plan_launches"] + st["packs"] - len(warm),
+                "max_pack": st["max_pack"]}
 
     budget = int(args.serve_budget_gib * 2 ** 30)
     burst_packed, burst_unpacked = burst(args.serve_pack), burst(0)
+    # saturated throughput on the mix itself: the served mixed-precision form (continuous
+    # batching, packing) against the plain FP32 form served one request at a time
+    sat_mixed = burst(args.serve_pack, n_burst=1000, large=True)
+    sat_plain = burst(0, n_burst=1000, prec=tn.TN_C64_FP32_SIMT, inflight=1, streams=1, large=True)
     mixed, r_mixed = serve(PREC[args.serve_prec], args.serve_inflight, args.serve_streams, args.serve_pack, budget)
     unpacked, r_unpacked = serve(PREC[args.serve_prec], args.serve_inflight, args.serve_streams, 0, budget)
     plain, r_plain = serve(tn.TN_C64_FP32_SIMT, 1, 1)
@@ -906,6 +916,8 @@ def run_serve_bench(args):
         "burst_of_small_requests": {"packed": burst_packed, "unpacked": burst_unpacked,
                                     "speedup_of_packing": burst_packed["requests_per_s"] /
                                     burst_unpacked["requests_per_s"]},
+        "saturated_mix": {"mixed": sat_mixed, "plain_fp32_one_at_a_time": sat_plain,
+                          "speedup_vs_plain": sat_mixed["requests_per_s"] / sat_plain["requests_per_s"]},
         "max_rel_diff_amplitudes_packed_vs_unpacked": float(np.max(
             np.abs(r_mixed[cls == 0] - r_unpacked[cls == 0]).sum(1) / (np.abs(r_unpacked[cls == 0]).sum(1) + 2 ** -6))),
         "max_rel_diff_amplitudes_mixed_vs_plain": amp_err,
