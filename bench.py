@@ -357,9 +357,10 @@ def run_reference(args):
         "impl": "reference", "metric": "contraction TFLOP/s", "value": v, "unit": "TFLOP/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "vs_baseline": None, "dtype": "c128" if w.net.is_complex else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload, ""),
-                   "prec": "complex128 oracle", "semiring": w.info.get("semiring", "standard"),
+                   "prec": "complex128 oracle" if w.net.is_complex else "float64 oracle",
+                   "semiring": w.info.get("semiring", "standard"),
                    "slices": w.n_slices},
         "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": f"first {min(samples)}-{max(samples)} of {len(w.path.pairs)} path steps of "
