@@ -157,6 +157,10 @@ typedef struct {
   int64_t row_ext[12], row_stride[12], col_ext[12], col_stride[12];
   int32_t ksplit;          /* SIMT steps: k cut in this many parts (then two launches) */
   int32_t single_sm;       /* tensor-core steps: 1 if kept on one SM per tile (tn_plan_autotune) */
+  int32_t chain;           /* -1, or the step chain the step runs in: a run of consecutive tiny
+                              CUDA-core steps executed by one CTA in one launch (the profile
+                              attributes the chain's time to its first step) */
+  int32_t reserved;
 } tn_step_info;
 
 /* How a tensor's copies are stored in the workspace. PLANAR: FP32 (complex: the real
@@ -334,7 +338,9 @@ tn_status tn_plan_profile_read(tn_plan_t plan, tn_profile* out, int32_t reset);
 tn_status tn_selftest_bounded_wait(tn_plan_t plan, int32_t arrive, int64_t limit_us, void* stream);
 
 /* Device milliseconds per step accumulated by the same events (ms_out holds n_steps
- * doubles), for the recordings folded in by tn_plan_profile_read since its last reset. */
+ * doubles), for the recordings folded in by tn_plan_profile_read since its last reset. A
+ * step chain (tn_step_info.chain) is one launch: its time is reported at its first step and
+ * 0 at the others. */
 tn_status tn_plan_profile_steps(tn_plan_t plan, double* ms_out, int32_t n_steps);
 
 /* ---- serving: continuous batching of contraction requests ------------------------ */

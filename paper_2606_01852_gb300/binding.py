@@ -71,7 +71,7 @@ class tn_step_info(C.Structure):
                 ("n_row_dims", C.c_int32), ("n_col_dims", C.c_int32),
                 ("row_ext", C.c_int64 * 12), ("row_stride", C.c_int64 * 12),
                 ("col_ext", C.c_int64 * 12), ("col_stride", C.c_int64 * 12),
-                ("ksplit", C.c_int32), ("single_sm", C.c_int32)]
+                ("ksplit", C.c_int32), ("single_sm", C.c_int32), ("chain", C.c_int32), ("reserved", C.c_int32)]
 
 
 class tn_tensor_info(C.Structure):
@@ -291,6 +291,7 @@ class Plan:
         d = {f: getattr(i, f) for f, _ in tn_step_info._fields_[:7]}
         d["ksplit"] = i.ksplit
         d["single_sm"] = i.single_sm
+        d["chain"] = i.chain
         d["rows"] = [(i.row_ext[x], i.row_stride[x]) for x in range(i.n_row_dims)]
         d["cols"] = [(i.col_ext[x], i.col_stride[x]) for x in range(i.n_col_dims)]
         return d

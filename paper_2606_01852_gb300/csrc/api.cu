@@ -92,6 +92,25 @@ tn_status check_device_error(Plan& P) {
   return TN_OK;
 }
 
+tn_status upload_chain_table(Plan& P) {
+  if (P.chains.empty() || !P.dev) return TN_OK;
+  std::vector<ChainStep> table;
+  for (const ChainRec& c : P.chains)
+    for (int32_t q = c.first; q < c.first + c.n; ++q) {
+      ChainStep cs{};
+      cs.a = step_args(P, P.steps[q]);
+      cs.batched = P.steps[q].batched ? 1 : 0;
+      table.push_back(cs);
+    }
+  cudaError_t e = cudaMemcpy(P.dev + P.off_chain, table.data(), sizeof(ChainStep) * table.size(),
+                             cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_error(std::string("writing the step-chain table: ") + cudaGetErrorString(e));
+    return TN_ERR_CUDA;
+  }
+  return TN_OK;
+}
+
 tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t count, void* output,
                      double* log_scale, void* stream, std::string& err, void* pinned) {
   if (!P.dev) {
@@ -175,6 +194,34 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
     }
     for (int32_t s = 0; s < S; ++s) {
       const StepRec& sr = P.steps[s];
+      if (sr.chain >= 0) {
+        // a step chain: one launch for the run at its first step
+        const ChainRec& c = P.chains[sr.chain];
+        if (s != c.first || (p > 0 && !c.any_batched)) continue;
+        Plan::ProfRec pr{};
+        if (P.prof_on) {
+          pr.e0 = take_event(P);
+          pr.e1 = take_event(P);
+          pr.cls = TN_CLASS_SIMT;
+          pr.step = s;
+          for (int32_t q = c.first; q < c.first + c.n; ++q) {
+            const StepRec& qr = P.steps[q];
+            if (!qr.batched && p > 0) continue;
+            const double nq = qr.batched ? nb : 1, m = double(qr.m), n = double(qr.n), k = double(qr.k);
+            const TensorRec &QA = P.tensors[qr.a], &QB = P.tensors[qr.b];
+            pr.flops += (cplx ? 8.0 : 2.0) * m * n * k * nq;
+            pr.bytes += (cplx ? 8.0 : 4.0) * (m * k * (QA.batched ? nq : 1) + n * k * (QB.batched ? nq : 1) + m * n * nq);
+          }
+          TN_CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(pr.e0), st));
+        }
+        launch_contract_chain(reinterpret_cast<const ChainStep*>(P.dev + P.off_chain) + c.table, c.n, nb, p > 0,
+                              cplx, P.policy.semiring == TN_SEMIRING_MAXPLUS, st);
+        if (P.prof_on) {
+          TN_CUDA_TRY(cudaEventRecord(static_cast<cudaEvent_t>(pr.e1), st));
+          P.prof_pending.push_back(pr);
+        }
+        continue;
+      }
       if (!sr.batched && p > 0) continue;  // slice-invariant: computed once, kept
       StepArgs a = step_args(P, sr);
       const int32_t nbs = sr.batched ? nb : 1;
@@ -333,6 +380,12 @@ tn_status tn_plan(const tn_network* net, const tn_path* path, const int32_t* sli
     return TN_ERR_OOM;
   }
   P.dev = static_cast<char*>(mem);
+  const tn_status cs = upload_chain_table(P);
+  if (cs != TN_OK) {
+    cudaFree(mem);
+    delete h;
+    return cs;
+  }
   *out = h;
   return TN_OK;
 }
@@ -374,7 +427,13 @@ tn_status tn_plan_launches(tn_plan_t plan, int64_t slice_count, int64_t* out) {
     if (T > 0) n += 1;  // stage_leaves_kernel
     for (int32_t t = 0; t < T; ++t)
       if (P.leafdesc[t].tiled && !(p > 0 && !P.tensors[t].batched)) n += 1;
-    for (const StepRec& st : P.steps) {
+    for (int32_t q = 0; q < (int32_t)P.steps.size(); ++q) {
+      const StepRec& st = P.steps[q];
+      if (st.chain >= 0) {  // one launch per step chain, at its first step
+        const ChainRec& c = P.chains[st.chain];
+        if (q == c.first && (p == 0 || c.any_batched)) n += 1;
+        continue;
+      }
       if (!st.batched && p > 0) continue;
       const int32_t nbs = st.batched ? nb : 1;
       if (st.cls == TN_CLASS_TC)
@@ -412,6 +471,8 @@ tn_status tn_plan_step(tn_plan_t plan, int32_t s, tn_step_info* out) {
   }
   out->ksplit = st.ksplit;
   out->single_sm = st.single_sm ? 1 : 0;
+  out->chain = st.chain;
+  out->reserved = 0;
   return TN_OK;
 }
 

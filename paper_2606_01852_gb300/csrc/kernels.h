@@ -77,6 +77,22 @@ struct StepArgs {
   float* part;                              // ksplit * nb * planes * m * n floats, or null
 };
 
+// A run of consecutive tiny CUDA-core steps executed by one CTA in one launch (the step
+// chain): each step's StepArgs as for launch_contract_simt, and whether it is batched.
+struct ChainStep {
+  StepArgs a;
+  int32_t batched;
+  int32_t pad;
+};
+// A chain step's work bound: m n k (x the slice batch when batched) at most this many
+// multiply-adds (complex ones count four).
+constexpr int64_t kChainMaxWork = int64_t(1) << 16;
+// steps[0 .. n): the run, in path order; nb: slices of this pass; skip_unbatched: a pass
+// after the first (the slice-invariant steps were computed by the first and are kept).
+// Every step's outputs are the same bits as launch_contract_simt's (k summed in order by FMA).
+void launch_contract_chain(const ChainStep* steps, int32_t n, int32_t nb, bool skip_unbatched, bool cplx,
+                           bool maxplus, cudaStream_t st);
+
 // Small leaves: one CTA per leaf. Large leaves (LeafDesc::tiled): the tiled permutation
 // kernel, one launch per leaf; host_descs is the host copy of the table (grid sizes).
 void launch_stage_leaves(const LeafDesc* descs, const LeafDesc* host_descs, int32_t n_leaves, char* ws,

@@ -680,6 +680,36 @@ void assign_workspace(Plan& P, int64_t batch) {
   P.off_scratch = cur;
   P.scratch_bytes = scratch;
   cur += align_up(scratch, kAlign);
+  // step chains: maximal runs (two or more) of consecutive tiny CUDA-core steps, each run
+  // one launch of a single CTA instead of a launch per step (launch-bound paths)
+  P.chains.clear();
+  int32_t n_table = 0;
+  const int64_t cw = P.is_complex ? 4 : 1;
+  auto tiny = [&](const StepRec& st) {
+    return st.cls == TN_CLASS_SIMT && st.ksplit == 1 &&
+           double(st.m) * double(st.n) * double(st.k) * double(cw * (st.batched ? batch : 1)) <=
+               double(kChainMaxWork);
+  };
+  for (StepRec& st : P.steps) st.chain = -1;
+  for (int32_t s = 0; s < (int32_t)P.steps.size();) {
+    int32_t e = s;
+    while (e < (int32_t)P.steps.size() && tiny(P.steps[e])) ++e;
+    if (e - s >= 2) {
+      ChainRec c;
+      c.first = s;
+      c.n = e - s;
+      c.table = n_table;
+      for (int32_t q = s; q < e; ++q) {
+        P.steps[q].chain = (int32_t)P.chains.size();
+        c.any_batched = c.any_batched || P.steps[q].batched;
+      }
+      n_table += c.n;
+      P.chains.push_back(c);
+    }
+    s = e > s ? e : s + 1;
+  }
+  P.off_chain = cur;
+  cur += align_up(int64_t(n_table) * (int64_t)sizeof(ChainStep), kAlign);
   P.off_leafdesc = cur;
   cur += align_up(int64_t(T) * (int64_t)sizeof(LeafDesc), kAlign);
   P.off_stage_in = cur;

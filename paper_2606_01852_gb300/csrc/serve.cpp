@@ -379,6 +379,12 @@ struct tn_server_s {
       return nullptr;
     }
     in->P.dev = static_cast<char*>(mem);
+    if (upload_chain_table(in->P) != TN_OK) {
+      cudaFree(mem);
+      err = "writing a request workspace's step-chain table failed";
+      fatal = true;
+      return nullptr;
+    }
     in->in_off.resize(in->P.n_leaves);
     for (int32_t t = 0; t < in->P.n_leaves; ++t) {
       in->in_off[t] = in->in_bytes;

@@ -85,6 +85,14 @@ struct StepRec {
   OffsetMap rows{}, cols{};
   int32_t ksplit = 1;  // SIMT steps too few tiles to fill the GPU: k cut in this many parts
   bool single_sm = false;  // tensor-core step kept on one SM per tile (tn_plan_autotune's choice)
+  int32_t chain = -1;      // index of the step chain (a run of tiny CUDA-core steps) it is in
+};
+
+// A step chain: steps first .. first + n - 1 run in one launch (entries table .. table + n - 1
+// of the device table at off_chain)
+struct ChainRec {
+  int32_t first = 0, n = 0, table = 0;
+  bool any_batched = false;
 };
 
 struct Plan {
@@ -114,6 +122,8 @@ struct Plan {
   std::vector<int32_t> rec_index;   // per tensor: first scale record
   int64_t n_rec_unbatched = 0, n_rec_total = 0;
   int64_t off_leafdesc = 0;         // LeafDesc table
+  int64_t off_chain = 0;            // ChainStep table of the step chains
+  std::vector<ChainRec> chains;
   int64_t off_stage_in = 0;         // device copies of host inputs (tn_contract_host)
   std::vector<int64_t> stage_in_off;
   int64_t total_bytes = 0;
@@ -170,6 +180,8 @@ tn_status run_slices(Plan& P, const void* const* inputs, int64_t begin, int64_t 
 
 void set_error(const std::string& msg);
 tn_status check_device_error(Plan& P);
+// writes the step chains' ChainStep table into the workspace (once P.dev is set)
+tn_status upload_chain_table(Plan& P);
 
 // true when the tcgen05 kernels are compiled in
 bool tc_supported();

@@ -261,21 +261,57 @@ def test_cost_model_rates_drive_the_kernel_choice():
 
 def test_plan_launches_counts_the_call():
     """tn_plan_launches on host-only plans (no paired-SM bands without a device): per pass one
-    staging launch, one per tiled leaf, one per step (two for split-k and k-split steps; the
-    slice-invariant steps only in the first pass) and one for the slice sum."""
+    staging launch, one per tiled leaf, one per step outside step chains (two for split-k and
+    k-split steps; the slice-invariant steps only in the first pass), one per step chain (in
+    later passes only if it holds a batched step) and one for the slice sum."""
     tn = ensure_built()
     w = workloads.random_circuit(3, 4, 8, 3, n_sliced=4)
-    for batch in (16, 3):
+    for batch in (16, 3, 1):
         plan = tn.Plan(w.net, w.path, w.sliced, max_slice_batch=batch, host_only=True)
         info = plan.info()
         steps = [plan.step(s) for s in range(info["n_steps"])]
-        per = [2 if (st["cls"] == tn.TN_CLASS_SPLITK or st["ksplit"] > 1) else 1 for st in steps]
+        per = [0 if st["chain"] >= 0 else (2 if (st["cls"] == tn.TN_CLASS_SPLITK or st["ksplit"] > 1) else 1)
+               for st in steps]
+        chains = sorted({st["chain"] for st in steps if st["chain"] >= 0})
+        chain_b = sum(1 for c in chains if any(st["batched"] for st in steps if st["chain"] == c))
         leaves = [plan.tensor(t) for t in range(plan.n_leaves)]
         tiled = sum(1 for x in leaves if x["tiled"])
         tiled_b = sum(1 for x in leaves if x["tiled"] and x["batched"])
         for count in (1, 5, 16):
             passes = -(-count // info["slice_batch"])
             batched = sum(p for p, st in zip(per, steps) if st["batched"])
-            want = passes * 2 + sum(per) + (passes - 1) * batched + tiled + (passes - 1) * tiled_b
+            want = (passes * 2 + sum(per) + (passes - 1) * batched + tiled + (passes - 1) * tiled_b +
+                    len(chains) + (passes - 1) * chain_b)
             assert plan.launches_per_call(count) == want, (batch, count)
+        plan.destroy()
+
+
+def test_step_chains_are_runs_of_tiny_cuda_core_steps():
+    """The step chains: maximal runs (at least two) of consecutive CUDA-core steps, without a
+    k split, whose work (m n k, times the slice batch for batched steps, complex counted four
+    times) is at most 2^16 multiply-adds; every step outside a chain that is such a step
+    stands alone between steps that are not. A larger slice batch takes batched steps out."""
+    tn = ensure_built()
+    for w, kw in ((workloads.kising44(), {}), (workloads.rc12(), {}),
+                  (workloads.random_circuit(3, 4, 8, 3, n_sliced=4), {"max_slice_batch": 16})):
+        plan = tn.Plan(w.net, w.path, w.sliced, host_only=True, **kw)
+        info = plan.info()
+        steps = [plan.step(s) for s in range(info["n_steps"])]
+        nb = info["slice_batch"]
+        cw = 4 if plan.is_complex else 1
+        tiny = [st["cls"] == tn.TN_CLASS_SIMT and st["ksplit"] == 1 and
+                st["m"] * st["n"] * st["k"] * cw * (nb if st["batched"] else 1) <= 1 << 16 for st in steps]
+        chain = [st["chain"] for st in steps]
+        assert any(c >= 0 for c in chain)
+        for s, st in enumerate(steps):
+            if chain[s] >= 0:
+                assert tiny[s]
+                if s > 0 and chain[s - 1] >= 0:
+                    assert chain[s - 1] in (chain[s], chain[s] - 1)
+                if s > 0 and chain[s - 1] == chain[s] - 1 and chain[s - 1] >= 0:
+                    raise AssertionError("two chains back to back would be one run")
+            elif tiny[s]:
+                assert not (s > 0 and tiny[s - 1]) and not (s + 1 < len(steps) and tiny[s + 1])
+        ids = [c for c in chain if c >= 0]
+        assert ids == sorted(ids) and all(ids.count(c) >= 2 for c in set(ids))
         plan.destroy()
