@@ -518,60 +518,74 @@ template <bool CPLX, bool MAXPLUS>
 __global__ void __launch_bounds__(512) contract_chain_kernel(const ChainStep* __restrict__ steps, int32_t n_steps,
                                                              int32_t nb, int32_t skip_unbatched) {
   static_assert(!(CPLX && MAXPLUS), "the max-plus semiring is real");
+  static_assert(sizeof(ChainStep) % 4 == 0, "ChainStep copied as 32-bit words");
+  constexpr int kWords = sizeof(ChainStep) / 4;
   const float kZero = MAXPLUS ? __int_as_float(0xff800000) : 0.f;
+  // the step descriptors pass through shared memory, the next one fetched while the current
+  // step runs (double buffer)
+  __shared__ ChainStep cur[2];
+  auto fetch = [&](int32_t i) {
+    const int* src = reinterpret_cast<const int*>(steps + i);
+    int* dst = reinterpret_cast<int*>(&cur[i & 1]);
+    for (int w = threadIdx.x; w < kWords; w += blockDim.x) dst[w] = src[w];
+  };
+  if (n_steps > 0) fetch(0);
+  __syncthreads();
   for (int32_t i = 0; i < n_steps; ++i) {
-    const StepArgs& a = steps[i].a;
-    const bool batched = steps[i].batched != 0;
-    if (skip_unbatched && !batched) continue;  // (uniform over the CTA)
-    const int32_t nbs = batched ? nb : 1;
-    const int64_t mn = a.m * a.n;
-    for (int32_t b = 0; b < nbs; ++b) {
-      float sa = 1.f, sb = 1.f;
-      if (a.recs) {
-        sa = pow2_neg(scale_exp(a.recs + a.rec_a + (a.a_bstride ? b : 0)));
-        sb = pow2_neg(scale_exp(a.recs + a.rec_b + (a.b_bstride ? b : 0)));
-      }
-      const float* A = a.A + b * a.a_bstride;
-      const float* B = a.B + b * a.b_bstride;
-      float* C = a.C + b * a.c_bstride;
-      int lmax = -127;
-      for (int64_t idx = threadIdx.x; idx < mn; idx += blockDim.x) {
-        const int64_t r = idx / a.n, c = idx - r * a.n;
-        const float* ar = A + r * a.k;
-        const float* br = B + c * a.k;
-        float accr = kZero, acci = kZero;
-        for (int64_t kk = 0; kk < a.k; ++kk) {
-          const float xr = ar[kk] * sa, yr = br[kk] * sb;
-          if (CPLX) {
-            const float xi = ar[a.a_plane + kk] * sa, yi = br[a.b_plane + kk] * sb;
-            accr = fmaf(xr, yr, accr);
-            accr = fmaf(-xi, yi, accr);
-            acci = fmaf(xr, yi, acci);
-            acci = fmaf(xi, yr, acci);
-          } else if (MAXPLUS) {
-            accr = fmaxf(accr, xr + yr);
-          } else {
-            accr = fmaf(xr, yr, accr);
-          }
+    if (i + 1 < n_steps) fetch(i + 1);  // the buffer step i - 1 used: free since its barrier
+    const StepArgs& a = cur[i & 1].a;
+    const bool batched = cur[i & 1].batched != 0;
+    if (!(skip_unbatched && !batched)) {  // (uniform over the CTA)
+      const int32_t nbs = batched ? nb : 1;
+      const int64_t mn = a.m * a.n;
+      for (int32_t b = 0; b < nbs; ++b) {
+        float sa = 1.f, sb = 1.f;
+        if (a.recs) {
+          sa = pow2_neg(scale_exp(a.recs + a.rec_a + (a.a_bstride ? b : 0)));
+          sb = pow2_neg(scale_exp(a.recs + a.rec_b + (a.b_bstride ? b : 0)));
         }
-        const int64_t off = map_offset(a.rows, r) + map_offset(a.cols, c);
-        if (CPLX) store_cplx(C, a.c_plane, off, accr, acci, a.c_split);
-        else C[off] = accr;
-        if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(accr), fabsf(acci)) : fabsf(accr)));
-      }
-      if (a.recs) {
+        const float* A = a.A + b * a.a_bstride;
+        const float* B = a.B + b * a.b_bstride;
+        float* C = a.C + b * a.c_bstride;
+        int lmax = -127;
+        for (int64_t idx = threadIdx.x; idx < mn; idx += blockDim.x) {
+          const int64_t r = idx / a.n, c = idx - r * a.n;
+          const float* ar = A + r * a.k;
+          const float* br = B + c * a.k;
+          float accr = kZero, acci = kZero;
+          for (int64_t kk = 0; kk < a.k; ++kk) {
+            const float xr = ar[kk] * sa, yr = br[kk] * sb;
+            if (CPLX) {
+              const float xi = ar[a.a_plane + kk] * sa, yi = br[a.b_plane + kk] * sb;
+              accr = fmaf(xr, yr, accr);
+              accr = fmaf(-xi, yi, accr);
+              acci = fmaf(xr, yi, acci);
+              acci = fmaf(xi, yr, acci);
+            } else if (MAXPLUS) {
+              accr = fmaxf(accr, xr + yr);
+            } else {
+              accr = fmaf(xr, yr, accr);
+            }
+          }
+          const int64_t off = map_offset(a.rows, r) + map_offset(a.cols, c);
+          if (CPLX) store_cplx(C, a.c_plane, off, accr, acci, a.c_split);
+          else C[off] = accr;
+          if (a.recs) lmax = max(lmax, exp_of(CPLX ? fmaxf(fabsf(accr), fabsf(acci)) : fabsf(accr)));
+        }
+        if (a.recs) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        ScaleRec* rc = a.recs + a.rec_c + (a.c_bstride ? b : 0);
-        if ((threadIdx.x & 31) == 0) atomicMax(&rc->emax, lmax);
-        if (threadIdx.x == 0) {
-          const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
-          const ScaleRec* rb = a.recs + a.rec_b + (a.b_bstride ? b : 0);
-          rc->log2 = ra->log2 + rb->log2 + scale_exp(ra) + scale_exp(rb);
+          for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+          ScaleRec* rc = a.recs + a.rec_c + (a.c_bstride ? b : 0);
+          if ((threadIdx.x & 31) == 0) atomicMax(&rc->emax, lmax);
+          if (threadIdx.x == 0) {
+            const ScaleRec* ra = a.recs + a.rec_a + (a.a_bstride ? b : 0);
+            const ScaleRec* rb = a.recs + a.rec_b + (a.b_bstride ? b : 0);
+            rc->log2 = ra->log2 + rb->log2 + scale_exp(ra) + scale_exp(rb);
+          }
         }
       }
     }
-    __syncthreads();
+    __syncthreads();  // this step's stores and scale record before the next step's loads
   }
 }
 
